@@ -1,0 +1,116 @@
+"""Pins for the oracle's wavefunction models (paper Section 4)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle.lanczos import sector_states
+from oracle.models import bf16_round, in_sector
+from tests.common import oracle_model
+
+SMALL_TF = dict(arch="transformer", n=8, n_up=2, n_dn=1, hidden=16, layers=2, heads=2, seed=5)
+SMALL_MADE = dict(arch="made", n=8, n_up=2, n_dn=2, hidden=12, layers=2, seed=6)
+SMALL_PROD = dict(arch="product", n=8, n_up=1, n_dn=3, hidden=0, layers=0, seed=9)
+
+
+def _all_states(n):
+    return np.arange(1 << n, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("dims", [SMALL_TF, SMALL_MADE, SMALL_PROD, 1, 2])
+@pytest.mark.parametrize("beta", [0.0, 2.0])
+def test_normalised_over_sector_and_zero_outside(dims, beta):
+    # Section 4: the autoregressive product normalises; pihat "still normalize to one".
+    cfg = synth.get_config(dims) if isinstance(dims, int) else dims
+    model, _ = oracle_model(cfg, beta=beta)
+    n = model.n
+    x = _all_states(n)
+    la, _ = model.log_psi(x)
+    ok = in_sector(x, n, model.n_up, model.n_dn)
+    assert np.all(np.isneginf(la[~ok]))
+    assert abs(np.sum(np.exp(2 * la[ok])) - 1.0) < 1e-13
+
+
+def test_normalised_config3_sector():
+    cfg = synth.get_config(3)
+    model, _ = oracle_model(cfg, beta=0.5)
+    st = sector_states(cfg.n_orb, cfg.n_up, cfg.n_dn)
+    la, _ = model.log_psi(st)
+    assert abs(np.sum(np.exp(2 * la)) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("dims", [SMALL_TF, SMALL_MADE])
+def test_autoregressive_dependence(dims):
+    # conditional at position t must not depend on positions >= t
+    model, _ = oracle_model(dims, beta=1.0)
+    n = model.n
+    rng = np.random.default_rng(0)
+    X = torch.tensor(rng.integers(0, 2, size=(64, n)).astype(np.float64))
+    base = model.cond_p1(X)
+    for t in range(n):
+        Y = X.clone()
+        Y[:, t:] = 1.0 - Y[:, t:]
+        p = model.cond_p1(Y)
+        assert torch.allclose(p[:, : t + 1], base[:, : t + 1], atol=1e-14, rtol=0)
+
+
+def test_transformer_matches_torch_library_modules():
+    model, params = oracle_model(SMALL_TF, beta=1.0)
+    P = {k: torch.tensor(v, dtype=torch.float64) for k, v in params.items()}
+    n, d, H = model.n, model.hidden, model.heads
+    rng = np.random.default_rng(1)
+    X = torch.tensor(rng.integers(0, 2, size=(16, n)).astype(np.float64))
+    logits, phase_out = model._transformer(X)
+
+    F = torch.nn.functional
+    tok = torch.cat([torch.full((16, 1), 2), X[:, : n - 1].long()], 1)
+    h = F.embedding(tok, P["tok_emb"]) + P["pos_emb"]
+    for l in range(model.layers):
+        g = lambda s: P[f"blk{l}.{s}"]
+        a = F.layer_norm(h, (d,), g("ln1_g"), g("ln1_b"), eps=1e-5)
+        qkv = F.linear(a, g("wqkv"), g("bqkv"))
+        q, k, v = (t.reshape(16, n, H, d // H).transpose(1, 2) for t in qkv.split(d, -1))
+        o = F.scaled_dot_product_attention(q, k, v, is_causal=True).transpose(1, 2).reshape(16, n, d)
+        h = h + F.linear(o, g("wo"), g("bo"))
+        a2 = F.layer_norm(h, (d,), g("ln2_g"), g("ln2_b"), eps=1e-5)
+        h = h + F.linear(F.gelu(F.linear(a2, g("w1"), g("b1")), approximate="tanh"), g("w2"), g("b2"))
+    hf = F.layer_norm(h, (d,), P["lnf_g"], P["lnf_b"], eps=1e-5)
+    want_logits = hf @ P["head_w"] + P["head_b"]
+    want_phase = F.linear(hf[:, n - 2], P["phase_w"], P["phase_b"])
+    torch.testing.assert_close(logits, want_logits, atol=1e-12, rtol=0)
+    torch.testing.assert_close(phase_out, want_phase, atol=1e-12, rtol=0)
+
+
+def test_bf16_round_matches_torch_rne_conversion():
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.standard_normal(20000) * 10 ** rng.uniform(-6, 6, 20000),
+                        [0.0, 1.0, -1.0, 1.00390625, 1.005859375]]).astype(np.float32)
+    want = torch.tensor(v).to(torch.bfloat16).to(torch.float64)
+    got = bf16_round(torch.tensor(v.astype(np.float64)))
+    assert torch.equal(got, want)
+
+
+def test_phase_selected_by_last_two_positions():
+    model, _ = oracle_model(SMALL_MADE, beta=0.0)
+    X = torch.tensor(np.random.default_rng(4).integers(0, 2, size=(32, model.n)).astype(np.float64))
+    _, _, po = model.cond_logp(X)
+    _, ph = model.log_psi_t(X)
+    sel = (2 * X[:, -2] + X[:, -1]).long()
+    assert torch.equal(ph, po[torch.arange(32), sel])
+
+
+def test_sampling_conditionals_respect_constraint():
+    # sequentially drawing the most likely allowed bit must always end inside the sector
+    for dims in (SMALL_TF, SMALL_MADE, SMALL_PROD):
+        model, _ = oracle_model(dims, beta=0.0)
+        rng = np.random.default_rng(5)
+        for trial in range(20):
+            bits = np.zeros(1, dtype=np.uint64)
+            for k in range(model.n):
+                p = model.sampling_p(bits, k)[0]
+                b = rng.random() < p
+                if b:
+                    bits |= np.uint64(1) << np.uint64(model.order[k])
+            assert in_sector(bits, model.n, model.n_up, model.n_dn)[0]
