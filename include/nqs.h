@@ -1,0 +1,215 @@
+/*
+ * nqs.h -- C ABI of the B300 (sm_103a) library for the local-energy hot path of autoregressive
+ * neural quantum states over Jordan-Wigner qubit Hamiltonians (Zhao, Stokes, Veerapaneni,
+ * "Scalable neural quantum states architecture for quantum chemistry", arXiv 2208.05637).
+ *
+ * Conventions shared by every call
+ *  - Qubit j is bit j of a uint64 bitstring; 1 <= n_qubits <= 64.  Spin orbital j = 2p + s:
+ *    even bits are spin up (alpha), odd bits spin down (beta) (Eq. hamming_weight_constraint).
+ *  - A Pauli string is a pair of masks (x_mask, z_mask): qubit j carries I for (0,0), sigma_1
+ *    for (1,0), sigma_3 for (0,1) and sigma_2 for (1,1) (Section 3, Eq. hamiltonpauli).
+ *  - Pointers documented as "device" must point to memory of the current CUDA device; "host"
+ *    pointers to ordinary host memory.  Bulk device buffers (bits, counts, outputs, gradients,
+ *    parameters, workspace) are owned by the caller and must stay alive until the work queued
+ *    on the stream has completed.  Handles are owned by the library; *_destroy frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *    are asynchronous on it unless stated otherwise.
+ *  - Every call returns NQS_OK (0) or a negative status; no exception or abort crosses the
+ *    ABI.  nqs_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define NQS_OK               0
+#define NQS_ERR_INVALID_ARG (-1)  /* a null pointer, negative size, bad enum, bad mask bit    */
+#define NQS_ERR_NQUBITS     (-2)  /* n_qubits outside the supported range                   */
+#define NQS_ERR_CAPACITY    (-3)  /* an output buffer is too small; the needed size is set  */
+#define NQS_ERR_WORKSPACE   (-4)  /* ws_bytes smaller than nqs_workspace_size() reported      */
+#define NQS_ERR_CUDA        (-5)  /* a CUDA runtime call or kernel launch failed             */
+#define NQS_ERR_TIMEOUT     (-6)  /* a bounded device-side wait gave up                      */
+#define NQS_ERR_NAN         (-7)  /* a non-finite coefficient or parameter was supplied      */
+#define NQS_ERR_ALLOC       (-8)  /* library-owned host or device allocation failed          */
+#define NQS_ERR_UNSUPPORTED (-9)  /* valid request outside what this build implements        */
+
+typedef struct nqs_ham_s* nqs_ham_t;
+typedef struct nqs_model_s* nqs_model_t;
+
+enum nqs_arch { NQS_ARCH_PRODUCT = 0, NQS_ARCH_MADE = 1, NQS_ARCH_TRANSFORMER = 2 };
+enum nqs_precision { NQS_PREC_FP32 = 0, NQS_PREC_BF16 = 1 };
+enum nqs_op { NQS_OP_SAMPLE = 0, NQS_OP_LOGPSI = 1, NQS_OP_LOCAL_ENERGY = 2, NQS_OP_BACKWARD = 3,
+              NQS_OP_TERM_SWEEP = 4 };
+
+/* Model description (Section 4).
+ *  arch         NQS_ARCH_*: PRODUCT (pi(x_order[t]=1) = p[t], phase 0), MADE (modulus MADE with
+ *               `layers` hidden layers of width `hidden` plus the two-layer phase MLP of
+ *               Section 4), TRANSFORMER (decoder-only, d_model = hidden, `layers` blocks,
+ *               `heads` heads; not in the paper).
+ *  n_qubits     even, 4..64.  n_up / n_dn: electrons per spin, the sector of Eq.
+ *               hamming_weight_constraint.
+ *  precision    NQS_PREC_FP32 or NQS_PREC_BF16 (bf16 tensor-core contractions, fp32
+ *               accumulation; transformer only).
+ *  compensated  nonzero: TwoSum/Kahan accumulation of coefficient sums, log-probabilities
+ *               and the local-energy reduction.
+ *  order        order[t] = qubit sampled at step t; a permutation of 0..n_qubits-1.  The
+ *               paper's reverse order (Section 4) is order[t] = n_qubits-1-t. */
+typedef struct nqs_model_desc {
+    int arch;
+    int n_qubits;
+    int n_up;
+    int n_dn;
+    int hidden;
+    int layers;
+    int heads;
+    int precision;
+    int compensated;
+    int order[64];
+} nqs_model_desc;
+
+/* ---------------------------------------------------------------- Hamiltonian */
+
+/* Build a Hamiltonian H = sum_k coeff[k] P(x_mask[k], z_mask[k]) (Eq. hamiltonpauli) and run
+ * the term-grouping pass (Section 5.1: "unique flippings"): equal (x,z) strings are merged by
+ * fp64 summation in input order, exact zeros dropped, strings grouped by x_mask (the flip
+ * pattern m), and the phase (-i)^r of Eq. mtx_element (r = popcount(x & z)) folded into each
+ * coefficient.  The grouped table is copied to the current device.
+ *   n_qubits 1..64; n_terms >= 1; x_mask, z_mask, coeff: host arrays of n_terms (copied;
+ *   the caller keeps ownership).  Errors: NQS_ERR_NQUBITS, NQS_ERR_INVALID_ARG (null pointer,
+ *   mask bit >= n_qubits), NQS_ERR_NAN (non-finite coefficient), NQS_ERR_ALLOC, NQS_ERR_CUDA.
+ *   Synchronous. */
+int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const uint64_t* z_mask,
+                   const double* coeff, nqs_ham_t* out);
+
+/* Merged term count K' and group count G. */
+int nqs_ham_info(nqs_ham_t ham, int64_t* n_terms_merged, int64_t* n_groups);
+
+/* Copy the grouped table to host arrays: grp_mask[G] (ascending), grp_offset[G+1] (terms of
+ * group g are [grp_offset[g], grp_offset[g+1])), term_z[K'] (ascending within a group) and the
+ * phase-folded coefficients c'_k = c_k (-i)^{r_k} as term_c_re[K'], term_c_im[K'].  Any
+ * pointer may be NULL to skip that array.  Synchronous. */
+int nqs_ham_export(nqs_ham_t ham, uint64_t* grp_mask, int64_t* grp_offset, uint64_t* term_z,
+                   double* term_c_re, double* term_c_im);
+
+void nqs_ham_destroy(nqs_ham_t ham);
+
+/* ---------------------------------------------------------------- model */
+
+/* Validate a description and create a model handle (no parameters bound yet).
+ * Errors: NQS_ERR_NQUBITS, NQS_ERR_INVALID_ARG, NQS_ERR_UNSUPPORTED (e.g. MADE wider than
+ * 256 or a transformer head size other than 16/32), NQS_ERR_ALLOC. */
+int nqs_model_create(const nqs_model_desc* desc, nqs_model_t* out);
+
+/* Total number of fp32 parameters of the flat parameter vector. */
+int nqs_model_param_count(nqs_model_t model, int64_t* n_params);
+
+/* Number of named parameter tensors, and the name / offset / element count of tensor `index`
+ * inside the flat vector.  Weight matrices are row-major [out][in].  *name points to storage
+ * owned by the model handle. */
+int nqs_model_param_tensors(nqs_model_t model, int* n_tensors);
+int nqs_model_param_info(nqs_model_t model, int index, const char** name, int64_t* offset,
+                         int64_t* numel);
+
+/* Borrow the caller's device fp32 parameter vector (param_count floats).  Every later call
+ * reads it at execution time, so updates (e.g. nqs_adam_step) take effect without rebinding. */
+int nqs_model_bind_params(nqs_model_t model, const float* params_device);
+
+void nqs_model_destroy(nqs_model_t model);
+
+/* Workspace bytes that `op` (NQS_OP_*) needs for `batch` rows: samples for LOGPSI,
+ * LOCAL_ENERGY, BACKWARD and TERM_SWEEP; the nominal sample count N_s for SAMPLE (with
+ * max_unique = batch).  ham may be NULL except for LOCAL_ENERGY and TERM_SWEEP.  The
+ * workspace is a caller-owned device buffer, 256-byte aligned. */
+int nqs_workspace_size(nqs_model_t model, nqs_ham_t ham, int op, int64_t batch, size_t* bytes);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Unique-sample autoregressive sampling with counts (Section 4, Sampling; Eq. modifier).
+ * One buffer entry with count n_samples is doubled on qubit order[k] at step k = 0..n-1; every
+ * nominal sample draws u = word 0 of Philox4x32-10(counter (j, k, 0, 0), key (seed lo, seed
+ * hi)) and takes bit 1 iff u < floor(p * 2^32), p the fp32 constrained conditional of its
+ * parent; zero-count children are dropped and, if more than max_unique entries remain, the top
+ * max_unique by (count desc, bits asc) are kept.
+ *   bits_out[capacity] (device, uint64) and counts_out[capacity] (device, int64) receive the
+ *   U unique samples in ascending bit order; *n_unique (host) receives U.  If U > capacity,
+ *   returns NQS_ERR_CAPACITY with *n_unique = U and nothing written.
+ *   p_trace (device, may be NULL): p_trace[k * trace_stride + s] receives the fp32
+ *   probability used for parent s at step k (parents in ascending bit order);
+ *   trace_stride >= min(n_samples, 2*max_unique).
+ *   Requires 1 <= n_samples < 2^31 and max_unique >= 1.
+ *   Synchronises `stream` once at the end to read U. */
+int nqs_sample(nqs_model_t model, int64_t n_samples, int64_t max_unique, uint64_t seed,
+               uint64_t* bits_out, int64_t* counts_out, int64_t capacity, int64_t* n_unique,
+               float* p_trace, int64_t trace_stride, void* ws, size_t ws_bytes, void* stream);
+
+/* log f(x) = i phi(x) + 1/2 sum log pihat (Section 4) for B device bitstrings:
+ * log_abs[B] and phase[B] (device fp32).  Out-of-sector inputs give log_abs = -inf. */
+int nqs_logpsi(nqs_model_t model, const uint64_t* bits, int64_t B, float* log_abs, float* phase,
+               void* ws, size_t ws_bytes, void* stream);
+
+/* Term sweep alone (Eq. mtx_element on grouped strings): for each sample x_i (device,
+ * in the model's sector) and each group g whose flip x' = x_i ^ m_g stays in the sector,
+ * S_g(x_i) = sum_{k in g} c'_k (-1)^{popcount(x_i & z_k)}.  Rows are written per sample in
+ * group order: row_offset[B+1] (device int64), xprime[row], s_re[row], s_im[row] (device;
+ * fp32), capacity rows at most.  If the row count exceeds capacity, returns NQS_ERR_CAPACITY
+ * with *n_rows = the count and no rows written.  n_up, n_dn: the sector.  Synchronises
+ * `stream` once (to size the output). */
+int nqs_term_sweep(nqs_ham_t ham, int n_up, int n_dn, int compensated, const uint64_t* bits,
+                   int64_t B, int64_t* row_offset, uint64_t* xprime, float* s_re, float* s_im,
+                   int64_t capacity, int64_t* n_rows, void* ws, size_t ws_bytes, void* stream);
+
+/* Local energy (Eq. local_energy_auto; Algorithm 1) for B device bitstrings in the model's
+ * sector: eloc[2*i], eloc[2*i+1] (device fp32) = Re, Im of
+ *   l(x_i) = sum_g S_g(x_i) f(x_i ^ m_g) / f(x_i)
+ * over the in-sector flips (out-of-sector flips have f = 0 under the constraint).  The
+ * network is evaluated on every connected x' with the ratio-weighted reduction fused into its
+ * epilogue.  Synchronises `stream` once per internal sample chunk (to size the x' stream). */
+int nqs_local_energy(nqs_ham_t ham, nqs_model_t model, const uint64_t* bits, int64_t B,
+                     float* eloc, void* ws, size_t ws_bytes, void* stream);
+
+/* Vector-Jacobian product of log f (Eq. grad): grad_accum[P] (device fp32) +=
+ *   sum_i g_log_abs[i] d log|f(x_i)|/d theta + g_phase[i] d phi(x_i)/d theta
+ * with the forward recomputed inside (no saved activations).  Deterministic order. */
+int nqs_logpsi_backward(nqs_model_t model, const uint64_t* bits, int64_t B,
+                        const float* g_log_abs, const float* g_phase, float* grad_accum,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* FP64 energy statistics (Eq. total_energy_sum with sample counts as weights):
+ * stats[0..3] (device double) = Re E_bar, Im E_bar, Var = sum w|E - E_bar|^2 / W, W = sum w.
+ * If g_abs and g_phase (device fp32, may be NULL) are given they receive the upstream
+ * gradients of the VMC surrogate: g_abs[i] = 2 w_i Re(E_i - E_bar) / W and
+ * g_phase[i] = 2 w_i Im(E_i) / W (baseline b = Re E_bar of Eq. grad). */
+int nqs_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
+                     float* g_abs, float* g_phase, void* stream);
+
+/* One Adam update (Section 5.1) in place on device fp32 arrays of n elements; step is the
+ * 1-based iteration number. */
+int nqs_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int step,
+                  float lr, float beta1, float beta2, float eps, void* stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+const char* nqs_strerror(int status);
+const char* nqs_last_error(void);
+
+/* Per-kernel device timing with CUDA events recorded on the launching stream.  While enabled,
+ * each launch of a timed kernel is bracketed by two events; nqs_profile_read() synchronises
+ * the recorded events and returns the summed milliseconds and launch count of the kernel
+ * named `kernel` ("term_sweep", "eloc_rows", ...).  nqs_profile_reset() clears the records. */
+int nqs_profile_enable(int on);
+int nqs_profile_reset(void);
+int nqs_profile_read(const char* kernel, double* total_ms, int64_t* launches);
+
+/* Number of kernels this library has launched in the calling process (all streams). */
+int64_t nqs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_H */

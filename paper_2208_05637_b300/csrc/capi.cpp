@@ -1,0 +1,685 @@
+// C ABI of the library: argument validation, handle management, the host term-grouping pass,
+// workspace layout and orchestration of the device kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "nqs_internal.h"
+
+namespace nqs {
+
+// ------------------------------------------------------------------ errors and bookkeeping
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+              std::to_string(line) + ")");
+    return NQS_ERR_CUDA;
+}
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+// ------------------------------------------------------------------ profiling
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_pending;
+static std::map<std::string, std::pair<double, int64_t>> g_prof_acc;
+
+ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), stream(s) {
+    if (!g_prof_on) return;
+    if (cudaEventCreate(&e0) != cudaSuccess) { e0 = nullptr; return; }
+    cudaEventRecord(e0, stream);
+}
+
+ProfScope::~ProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+    cudaEventRecord(e1, stream);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back({name, e0, e1});
+}
+
+static void prof_drain() {
+    for (auto& r : g_prof_pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto& acc = g_prof_acc[r.name];
+        acc.first += ms;
+        acc.second += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof_pending.clear();
+}
+
+// ------------------------------------------------------------------ helpers
+static uint64_t spin_mask(int n, int spin) {
+    uint64_t m = 0;
+    for (int j = spin; j < n; j += 2) m |= (1ull << j);
+    return m;
+}
+
+static int check_device_ptr(const void* p, const char* what) {
+    if (!p) {
+        set_error(std::string(what) + " is NULL");
+        return NQS_ERR_INVALID_ARG;
+    }
+    return NQS_OK;
+}
+
+// Groups whose flip can keep some sector state inside the sector.
+static int64_t feasible_groups(const nqs_ham_s* h, int n_up, int n_dn) {
+    int n_orb = h->n / 2;
+    int64_t cnt = 0;
+    for (int64_t g = 0; g < h->G; ++g) {
+        int na = h->grp_meta[g] & 0xff, nb = (h->grp_meta[g] >> 8) & 0xff;
+        if ((na & 1) || (nb & 1)) continue;
+        if (na / 2 > std::min(n_up, n_orb - n_up)) continue;
+        if (nb / 2 > std::min(n_dn, n_orb - n_dn)) continue;
+        ++cnt;
+    }
+    return std::max<int64_t>(cnt, 1);
+}
+
+constexpr int64_t ELOC_CHUNK = 1024;   // samples per local-energy chunk
+
+struct ElocBufs {
+    float *la, *ph;
+    int32_t* cnt;
+    int64_t* off;
+    uint64_t* xprime;
+    float4* S;
+    int64_t chunk, ntiles, rows_cap;
+};
+
+static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int64_t B,
+                        ElocBufs& e) {
+    e.chunk = std::max<int64_t>(1, std::min(B, ELOC_CHUNK));
+    e.ntiles = sweep_tiles(h->dev);
+    e.rows_cap = e.chunk * feasible_groups(h, m->mc.n_up, m->mc.n_dn);
+    e.la = c.take<float>(std::max<int64_t>(B, 1));
+    e.ph = c.take<float>(std::max<int64_t>(B, 1));
+    e.cnt = c.take<int32_t>(e.chunk * e.ntiles);
+    e.off = c.take<int64_t>(e.chunk * e.ntiles + 1);
+    e.xprime = c.take<uint64_t>(e.rows_cap);
+    e.S = c.take<float4>(e.rows_cap);
+}
+
+}  // namespace nqs
+
+using namespace nqs;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* nqs_strerror(int status) {
+    switch (status) {
+        case NQS_OK: return "ok";
+        case NQS_ERR_INVALID_ARG: return "invalid argument";
+        case NQS_ERR_NQUBITS: return "unsupported number of qubits";
+        case NQS_ERR_CAPACITY: return "output capacity too small";
+        case NQS_ERR_WORKSPACE: return "workspace too small";
+        case NQS_ERR_CUDA: return "CUDA error";
+        case NQS_ERR_TIMEOUT: return "device wait timed out";
+        case NQS_ERR_NAN: return "non-finite input";
+        case NQS_ERR_ALLOC: return "allocation failed";
+        case NQS_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+const char* nqs_last_error(void) { return g_last_error.c_str(); }
+
+int64_t nqs_launch_count(void) { return g_launches.load(); }
+
+int nqs_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return NQS_OK;
+}
+
+int nqs_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    g_prof_acc.clear();
+    return NQS_OK;
+}
+
+int nqs_profile_read(const char* kernel, double* total_ms, int64_t* launches) {
+    if (!kernel || !total_ms || !launches) return NQS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    auto it = g_prof_acc.find(kernel);
+    *total_ms = it == g_prof_acc.end() ? 0.0 : it->second.first;
+    *launches = it == g_prof_acc.end() ? 0 : it->second.second;
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------ Hamiltonian
+int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const uint64_t* z_mask,
+                   const double* coeff, nqs_ham_t* out) {
+    if (!out) { set_error("out is NULL"); return NQS_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 64) { set_error("n_qubits must be in 1..64"); return NQS_ERR_NQUBITS; }
+    if (n_terms < 1 || !x_mask || !z_mask || !coeff) {
+        set_error("need n_terms >= 1 and non-NULL x_mask, z_mask, coeff");
+        return NQS_ERR_INVALID_ARG;
+    }
+    const uint64_t valid = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1);
+    for (int64_t k = 0; k < n_terms; ++k) {
+        if ((x_mask[k] | z_mask[k]) & ~valid) {
+            set_error("term " + std::to_string(k) + " has a mask bit >= n_qubits");
+            return NQS_ERR_INVALID_ARG;
+        }
+        if (!std::isfinite(coeff[k])) {
+            set_error("term " + std::to_string(k) + " has a non-finite coefficient");
+            return NQS_ERR_NAN;
+        }
+    }
+
+    // 1. merge equal (x, z) by fp64 summation in input order (stable sort keeps input order)
+    std::vector<int64_t> idx(n_terms);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+        return x_mask[a] != x_mask[b] ? x_mask[a] < x_mask[b] : z_mask[a] < z_mask[b];
+    });
+    auto* h = new (std::nothrow) nqs_ham_s();
+    if (!h) return NQS_ERR_ALLOC;
+    h->n = n_qubits;
+    h->K_in = n_terms;
+    const uint64_t A = spin_mask(n_qubits, 0), Bm = spin_mask(n_qubits, 1);
+    std::vector<double> c_signed;
+    for (int64_t i = 0; i < n_terms;) {
+        const uint64_t x = x_mask[idx[i]], z = z_mask[idx[i]];
+        double acc = 0.0;
+        int64_t j = i;
+        for (; j < n_terms && x_mask[idx[j]] == x && z_mask[idx[j]] == z; ++j) acc += coeff[idx[j]];
+        i = j;
+        if (acc == 0.0) continue;   // 2. drop exact zeros
+        // 3. group by x (the flip pattern)
+        if (h->grp_mask.empty() || h->grp_mask.back() != x) {
+            h->grp_mask.push_back(x);
+            h->grp_off.push_back((int64_t)h->term_z.size());
+            uint32_t na = (uint32_t)__builtin_popcountll(x & A);
+            uint32_t nb = (uint32_t)__builtin_popcountll(x & Bm);
+            h->grp_meta.push_back(na | (nb << 8));
+        }
+        // 4. fold (-i)^r, r = popcount(x & z), into the coefficient
+        const int r = __builtin_popcountll(x & z) & 3;
+        double re = 0.0, im = 0.0, sgn = 1.0;
+        switch (r) {
+            case 0: re = acc; sgn = 1.0; break;
+            case 1: im = -acc; sgn = -1.0; break;
+            case 2: re = -acc; sgn = -1.0; break;
+            default: im = acc; sgn = 1.0; break;
+        }
+        if (r & 1) h->grp_meta.back() |= META_HAS_IMAG;
+        h->term_z.push_back(z);
+        h->term_c_re.push_back(re);
+        h->term_c_im.push_back(im);
+        c_signed.push_back(sgn * acc);
+    }
+    h->grp_off.push_back((int64_t)h->term_z.size());
+    h->K = (int64_t)h->term_z.size();
+    h->G = (int64_t)h->grp_mask.size();
+    if (h->K == 0) {
+        // keep one zero term so the device tables are never empty
+        h->grp_mask.assign(1, 0);
+        h->grp_off.assign({0, 1});
+        h->grp_meta.assign(1, 0);
+        h->term_z.assign(1, 0);
+        h->term_c_re.assign(1, 0.0);
+        h->term_c_im.assign(1, 0.0);
+        c_signed.assign(1, 0.0);
+        h->K = 1;
+        h->G = 1;
+    }
+    if (h->K > (int64_t)0xffffffffll) { delete h; set_error("too many terms"); return NQS_ERR_UNSUPPORTED; }
+
+    // device copy: one allocation, arrays 256-byte aligned
+    Carver c(nullptr);
+    c.take<uint64_t>(h->G); c.take<uint32_t>(h->G + 1); c.take<uint32_t>(h->G);
+    c.take<uint64_t>(h->K); c.take<float2>(h->K);
+    cudaGetDevice(&h->device);
+    if (cudaMalloc(&h->d_block, c.used) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error("cudaMalloc of the Hamiltonian tables failed");
+        return NQS_ERR_ALLOC;
+    }
+    Carver d(h->d_block);
+    auto* d_mask = d.take<uint64_t>(h->G);
+    auto* d_off = d.take<uint32_t>(h->G + 1);
+    auto* d_meta = d.take<uint32_t>(h->G);
+    auto* d_z = d.take<uint64_t>(h->K);
+    auto* d_c = d.take<float2>(h->K);
+    std::vector<uint32_t> off32(h->grp_off.begin(), h->grp_off.end());
+    std::vector<float2> cc(h->K);
+    for (int64_t k = 0; k < h->K; ++k) {
+        float hi = (float)c_signed[k];
+        float lo = (float)(c_signed[k] - (double)hi);
+        cc[k] = make_float2(hi, lo);
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(d_mask, h->grp_mask.data(), h->G * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_off, off32.data(), (h->G + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_meta, h->grp_meta.data(), h->G * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_z, h->term_z.data(), h->K * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_c, cc.data(), h->K * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_block);
+        delete h;
+        return cuda_fail(e, "copy of the Hamiltonian tables", __FILE__, __LINE__);
+    }
+    h->dev = HamDev{h->n, h->K, h->G, d_mask, d_off, d_meta, d_z, d_c};
+    *out = h;
+    return NQS_OK;
+}
+
+int nqs_ham_info(nqs_ham_t ham, int64_t* n_terms_merged, int64_t* n_groups) {
+    if (!ham) return NQS_ERR_INVALID_ARG;
+    if (n_terms_merged) *n_terms_merged = ham->K;
+    if (n_groups) *n_groups = ham->G;
+    return NQS_OK;
+}
+
+int nqs_ham_export(nqs_ham_t h, uint64_t* grp_mask, int64_t* grp_offset, uint64_t* term_z,
+                   double* term_c_re, double* term_c_im) {
+    if (!h) return NQS_ERR_INVALID_ARG;
+    if (grp_mask) std::memcpy(grp_mask, h->grp_mask.data(), h->G * 8);
+    if (grp_offset) std::memcpy(grp_offset, h->grp_off.data(), (h->G + 1) * 8);
+    if (term_z) std::memcpy(term_z, h->term_z.data(), h->K * 8);
+    if (term_c_re) std::memcpy(term_c_re, h->term_c_re.data(), h->K * 8);
+    if (term_c_im) std::memcpy(term_c_im, h->term_c_im.data(), h->K * 8);
+    return NQS_OK;
+}
+
+void nqs_ham_destroy(nqs_ham_t h) {
+    if (!h) return;
+    if (h->d_block) cudaFree(h->d_block);
+    delete h;
+}
+
+// ------------------------------------------------------------------ model
+static void add_param(nqs_model_s* m, const std::string& name, int64_t numel, int64_t* slot) {
+    if (slot) *slot = m->n_params;
+    m->params.push_back({name, m->n_params, numel});
+    m->n_params += numel;
+}
+
+int nqs_model_create(const nqs_model_desc* d, nqs_model_t* out) {
+    if (!d || !out) { set_error("desc/out is NULL"); return NQS_ERR_INVALID_ARG; }
+    *out = nullptr;
+    const int n = d->n_qubits;
+    if (n < 4 || n > 64 || (n & 1)) { set_error("n_qubits must be even and in 4..64"); return NQS_ERR_NQUBITS; }
+    const int n_orb = n / 2;
+    if (d->n_up < 0 || d->n_dn < 0 || d->n_up > n_orb || d->n_dn > n_orb) {
+        set_error("n_up/n_dn outside 0..n_qubits/2");
+        return NQS_ERR_INVALID_ARG;
+    }
+    if (d->precision != NQS_PREC_FP32 && d->precision != NQS_PREC_BF16) {
+        set_error("precision must be NQS_PREC_FP32 or NQS_PREC_BF16");
+        return NQS_ERR_INVALID_ARG;
+    }
+    uint64_t seen = 0;
+    for (int t = 0; t < n; ++t) {
+        int q = d->order[t];
+        if (q < 0 || q >= n || ((seen >> q) & 1)) { set_error("order is not a permutation"); return NQS_ERR_INVALID_ARG; }
+        seen |= 1ull << q;
+    }
+    auto* m = new (std::nothrow) nqs_model_s();
+    if (!m) return NQS_ERR_ALLOC;
+    m->desc = *d;
+    ModelConst& mc = m->mc;
+    mc.arch = d->arch; mc.n = n; mc.n_up = d->n_up; mc.n_dn = d->n_dn;
+    mc.hidden = d->hidden; mc.layers = d->layers; mc.heads = d->heads;
+    mc.precision = d->precision; mc.compensated = d->compensated;
+    for (int t = 0; t < n; ++t) {
+        mc.order[t] = (uint8_t)d->order[t];
+        int cnt = 0;
+        for (int u = t + 1; u < n; ++u) cnt += ((d->order[u] & 1) == (d->order[t] & 1));
+        mc.after[t] = (uint8_t)cnt;
+    }
+    const int h = d->hidden;
+    if (d->arch == NQS_ARCH_PRODUCT) {
+        if (d->precision != NQS_PREC_FP32) { delete m; set_error("product model is fp32 only"); return NQS_ERR_UNSUPPORTED; }
+        add_param(m, "p", n, &mc.p_prob);
+    } else if (d->arch == NQS_ARCH_MADE) {
+        if (h < 1 || h > 64 || d->layers < 1 || d->layers > MADE_MAX_LAYERS) {
+            delete m;
+            set_error("MADE needs 1 <= hidden <= 64 and 1 <= layers <= 4");
+            return NQS_ERR_UNSUPPORTED;
+        }
+        if (d->precision != NQS_PREC_FP32) { delete m; set_error("MADE runs in fp32"); return NQS_ERR_UNSUPPORTED; }
+        add_param(m, "made.W0", (int64_t)h * n, &mc.made_W[0]);
+        add_param(m, "made.b0", h, &mc.made_b[0]);
+        for (int l = 1; l < d->layers; ++l) {
+            add_param(m, "made.W" + std::to_string(l), (int64_t)h * h, &mc.made_W[l]);
+            add_param(m, "made.b" + std::to_string(l), h, &mc.made_b[l]);
+        }
+        add_param(m, "made.Wout", (int64_t)n * h, &mc.made_Wout);
+        add_param(m, "made.bout", n, &mc.made_bout);
+        add_param(m, "phase.W0", (int64_t)h * (n - 2), &mc.ph_W0);
+        add_param(m, "phase.b0", h, &mc.ph_b0);
+        add_param(m, "phase.W1", 4 * (int64_t)h, &mc.ph_W1);
+        add_param(m, "phase.b1", 4, &mc.ph_b1);
+    } else if (d->arch == NQS_ARCH_TRANSFORMER) {
+        if (d->heads < 1 || h % d->heads || d->layers < 1 || d->layers > TF_MAX_LAYERS || h > 256) {
+            delete m;
+            set_error("transformer needs heads | hidden, 1 <= layers <= 8, hidden <= 256");
+            return NQS_ERR_UNSUPPORTED;
+        }
+        const int dh = h / d->heads;
+        if (dh != 16 && dh != 32) { delete m; set_error("transformer head size must be 16 or 32"); return NQS_ERR_UNSUPPORTED; }
+        add_param(m, "tok_emb", 3 * (int64_t)h, &mc.tok_emb);
+        add_param(m, "pos_emb", (int64_t)n * h, &mc.pos_emb);
+        for (int l = 0; l < d->layers; ++l) {
+            std::string p = "blk" + std::to_string(l) + ".";
+            add_param(m, p + "ln1_g", h, &mc.ln1_g[l]);
+            add_param(m, p + "ln1_b", h, &mc.ln1_b[l]);
+            add_param(m, p + "wqkv", 3 * (int64_t)h * h, &mc.wqkv[l]);
+            add_param(m, p + "bqkv", 3 * (int64_t)h, &mc.bqkv[l]);
+            add_param(m, p + "wo", (int64_t)h * h, &mc.wo[l]);
+            add_param(m, p + "bo", h, &mc.bo[l]);
+            add_param(m, p + "ln2_g", h, &mc.ln2_g[l]);
+            add_param(m, p + "ln2_b", h, &mc.ln2_b[l]);
+            add_param(m, p + "w1", 4 * (int64_t)h * h, &mc.w1[l]);
+            add_param(m, p + "b1", 4 * (int64_t)h, &mc.b1[l]);
+            add_param(m, p + "w2", 4 * (int64_t)h * h, &mc.w2[l]);
+            add_param(m, p + "b2", h, &mc.b2[l]);
+        }
+        add_param(m, "lnf_g", h, &mc.lnf_g);
+        add_param(m, "lnf_b", h, &mc.lnf_b);
+        add_param(m, "head_w", h, &mc.head_w);
+        add_param(m, "head_b", n, &mc.head_b);
+        add_param(m, "phase_w", 4 * (int64_t)h, &mc.phase_w);
+        add_param(m, "phase_b", 4, &mc.phase_b);
+    } else {
+        delete m;
+        set_error("unknown arch");
+        return NQS_ERR_INVALID_ARG;
+    }
+    *out = m;
+    return NQS_OK;
+}
+
+int nqs_model_param_count(nqs_model_t m, int64_t* n) {
+    if (!m || !n) return NQS_ERR_INVALID_ARG;
+    *n = m->n_params;
+    return NQS_OK;
+}
+
+int nqs_model_param_tensors(nqs_model_t m, int* n) {
+    if (!m || !n) return NQS_ERR_INVALID_ARG;
+    *n = (int)m->params.size();
+    return NQS_OK;
+}
+
+int nqs_model_param_info(nqs_model_t m, int index, const char** name, int64_t* offset,
+                         int64_t* numel) {
+    if (!m || index < 0 || index >= (int)m->params.size()) return NQS_ERR_INVALID_ARG;
+    if (name) *name = m->params[index].name.c_str();
+    if (offset) *offset = m->params[index].offset;
+    if (numel) *numel = m->params[index].numel;
+    return NQS_OK;
+}
+
+int nqs_model_bind_params(nqs_model_t m, const float* p) {
+    if (!m || !p) { set_error("model/params is NULL"); return NQS_ERR_INVALID_ARG; }
+    if (((uintptr_t)p) & 15) { set_error("parameter vector must be 16-byte aligned"); return NQS_ERR_INVALID_ARG; }
+    m->d_params = p;
+    return NQS_OK;
+}
+
+void nqs_model_destroy(nqs_model_t m) { delete m; }
+
+static int tf_unsupported() {
+    set_error("this operation is not implemented for the transformer in this build");
+    return NQS_ERR_UNSUPPORTED;
+}
+
+int nqs_workspace_size(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, size_t* bytes) {
+    if (!m || !bytes || batch < 0) return NQS_ERR_INVALID_ARG;
+    Carver c(nullptr);
+    switch (op) {
+        case NQS_OP_SAMPLE: {
+            SamplerBufs b;
+            NQS_TRY(sampler_layout(c, std::max<int64_t>(batch, 1), std::max<int64_t>(batch, 1), b));
+            break;
+        }
+        case NQS_OP_LOGPSI:
+            c.take<char>(256);
+            break;
+        case NQS_OP_LOCAL_ENERGY: {
+            if (!h) return NQS_ERR_INVALID_ARG;
+            ElocBufs e;
+            eloc_layout(c, m, h, batch, e);
+            break;
+        }
+        case NQS_OP_TERM_SWEEP: {
+            if (!h) return NQS_ERR_INVALID_ARG;
+            int64_t T = sweep_tiles(h->dev);
+            c.take<int32_t>(std::max<int64_t>(batch, 1) * T);
+            c.take<int64_t>(std::max<int64_t>(batch, 1) * T + 1);
+            c.take<float4>(std::max<int64_t>(batch, 1) * feasible_groups(h, m->mc.n_up, m->mc.n_dn));
+            break;
+        }
+        case NQS_OP_BACKWARD:
+            if (m->mc.arch == NQS_ARCH_MADE) c.take<float>(std::max<int64_t>(batch, 1) * made_act_stride(m->mc));
+            else c.take<char>(256);
+            break;
+        default:
+            return NQS_ERR_INVALID_ARG;
+    }
+    *bytes = c.used + 256;
+    return NQS_OK;
+}
+
+static int need_ws(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, void* ws, size_t ws_bytes) {
+    size_t need = 0;
+    NQS_TRY(nqs_workspace_size(m, h, op, batch, &need));
+    if (!ws || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return NQS_ERR_WORKSPACE;
+    }
+    if (((uintptr_t)ws) & 255) { set_error("workspace must be 256-byte aligned"); return NQS_ERR_INVALID_ARG; }
+    return NQS_OK;
+}
+
+static int need_params(nqs_model_t m) {
+    if (!m) return NQS_ERR_INVALID_ARG;
+    if (!m->d_params) { set_error("no parameters bound"); return NQS_ERR_INVALID_ARG; }
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------ hot path
+int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t seed,
+               uint64_t* bits_out, int64_t* counts_out, int64_t capacity, int64_t* n_unique,
+               float* p_trace, int64_t trace_stride, void* ws, size_t ws_bytes, void* stream) {
+    NQS_TRY(need_params(m));
+    if (n_samples < 1 || n_samples >= (1ll << 31) || max_unique < 1 || !n_unique || capacity < 0) {
+        set_error("need 1 <= n_samples < 2^31, max_unique >= 1, n_unique non-NULL");
+        return NQS_ERR_INVALID_ARG;
+    }
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
+    NQS_TRY(need_ws(m, nullptr, NQS_OP_SAMPLE, n_samples, ws, ws_bytes));
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    SamplerBufs b;
+    NQS_TRY(sampler_layout(c, n_samples, max_unique, b));
+    if (p_trace && trace_stride < b.cap) {
+        set_error("trace_stride must be >= min(n_samples, 2*max_unique)");
+        return NQS_ERR_INVALID_ARG;
+    }
+    NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride, s));
+    int64_t U = 0;
+    NQS_CK(cudaMemcpyAsync(&U, b.U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    *n_unique = U;
+    if (U > capacity) {
+        set_error("sample capacity " + std::to_string(capacity) + " < unique count " + std::to_string(U));
+        return NQS_ERR_CAPACITY;
+    }
+    if (U > 0) {
+        NQS_TRY(check_device_ptr(bits_out, "bits_out"));
+        NQS_TRY(check_device_ptr(counts_out, "counts_out"));
+        NQS_TRY(launch_copy_samples(b, bits_out, counts_out, U, s));
+    }
+    return NQS_OK;
+}
+
+int nqs_logpsi(nqs_model_t m, const uint64_t* bits, int64_t B, float* la, float* ph, void* ws,
+               size_t ws_bytes, void* stream) {
+    NQS_TRY(need_params(m));
+    if (B < 0) return NQS_ERR_INVALID_ARG;
+    if (B == 0) return NQS_OK;
+    if (!bits || !la || !ph) { set_error("bits/log_abs/phase is NULL"); return NQS_ERR_INVALID_ARG; }
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
+    (void)ws; (void)ws_bytes;
+    return launch_logpsi_rows(m->mc, m->d_params, bits, B, la, ph, (cudaStream_t)stream);
+}
+
+int nqs_term_sweep(nqs_ham_t h, int n_up, int n_dn, int compensated, const uint64_t* bits,
+                   int64_t B, int64_t* row_offset, uint64_t* xprime, float* s_re, float* s_im,
+                   int64_t capacity, int64_t* n_rows, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || !n_rows || B < 0 || capacity < 0) return NQS_ERR_INVALID_ARG;
+    int n_orb = h->n / 2;
+    if ((h->n & 1) || n_up < 0 || n_dn < 0 || n_up > n_orb || n_dn > n_orb) {
+        set_error("sector outside the Hamiltonian's qubits");
+        return NQS_ERR_INVALID_ARG;
+    }
+    if (B == 0) { *n_rows = 0; return NQS_OK; }
+    if (!bits || !row_offset) { set_error("bits/row_offset is NULL"); return NQS_ERR_INVALID_ARG; }
+    // workspace check against a throwaway model-free layout
+    int64_t T = sweep_tiles(h->dev);
+    Carver need(nullptr);
+    need.take<int32_t>(B * T); need.take<int64_t>(B * T + 1);
+    need.take<float4>(B * feasible_groups(h, n_up, n_dn));
+    if (!ws || ws_bytes < need.used) { set_error("workspace too small"); return NQS_ERR_WORKSPACE; }
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    int32_t* cnt = c.take<int32_t>(B * T);
+    int64_t* off = c.take<int64_t>(B * T + 1);
+    float4* S = c.take<float4>(B * feasible_groups(h, n_up, n_dn));
+    const uint64_t A = spin_mask(h->n, 0), Bm = spin_mask(h->n, 1);
+    {
+        ProfScope ps("sweep_count", s);
+        NQS_TRY(launch_sweep_count(h->dev, A, Bm, n_up, n_dn, bits, B, cnt, s));
+    }
+    NQS_TRY(launch_scan_i32(cnt, B * T, off, s));
+    int64_t total = 0;
+    NQS_CK(cudaMemcpyAsync(&total, off + B * T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    *n_rows = total;
+    if (total > capacity) { set_error("row capacity too small"); return NQS_ERR_CAPACITY; }
+    if (total > 0 && (!xprime || !s_re || !s_im)) { set_error("xprime/s_re/s_im is NULL"); return NQS_ERR_INVALID_ARG; }
+    {
+        ProfScope ps("term_sweep", s);
+        NQS_TRY(launch_sweep_emit(h->dev, A, Bm, n_up, n_dn, compensated, bits, B, off, xprime, S, s));
+    }
+    NQS_TRY(launch_unpack_rows(off, T, B, S, row_offset, s_re, s_im, capacity, off + B * T, s));
+    return NQS_OK;
+}
+
+int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B, float* eloc,
+                     void* ws, size_t ws_bytes, void* stream) {
+    NQS_TRY(need_params(m));
+    if (!h || B < 0) return NQS_ERR_INVALID_ARG;
+    if (h->n != m->mc.n) { set_error("Hamiltonian and model qubit counts differ"); return NQS_ERR_INVALID_ARG; }
+    if (B == 0) return NQS_OK;
+    if (!bits || !eloc) { set_error("bits/eloc is NULL"); return NQS_ERR_INVALID_ARG; }
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
+    NQS_TRY(need_ws(m, h, NQS_OP_LOCAL_ENERGY, B, ws, ws_bytes));
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    ElocBufs e;
+    eloc_layout(c, m, h, B, e);
+    const uint64_t A = spin_mask(h->n, 0), Bm = spin_mask(h->n, 1);
+    NQS_TRY(launch_logpsi_rows(m->mc, m->d_params, bits, B, e.la, e.ph, s));
+    for (int64_t lo = 0; lo < B; lo += e.chunk) {
+        const int64_t nb = std::min(e.chunk, B - lo);
+        {
+            ProfScope ps("sweep_count", s);
+            NQS_TRY(launch_sweep_count(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, bits + lo, nb, e.cnt, s));
+        }
+        NQS_TRY(launch_scan_i32(e.cnt, nb * e.ntiles, e.off, s));
+        {
+            ProfScope ps("term_sweep", s);
+            NQS_TRY(launch_sweep_emit(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, m->mc.compensated,
+                                      bits + lo, nb, e.off, e.xprime, e.S, s));
+        }
+        {
+            ProfScope ps("eloc_rows", s);
+            NQS_TRY(launch_eloc_rows(m->mc, m->d_params, bits + lo, nb, e.la + lo, e.ph + lo, e.off,
+                                     e.ntiles, e.xprime, e.S, eloc + 2 * lo, s));
+        }
+    }
+    return NQS_OK;
+}
+
+int nqs_logpsi_backward(nqs_model_t m, const uint64_t* bits, int64_t B, const float* g_abs,
+                        const float* g_phase, float* grad, void* ws, size_t ws_bytes,
+                        void* stream) {
+    NQS_TRY(need_params(m));
+    if (B < 0) return NQS_ERR_INVALID_ARG;
+    if (B == 0) return NQS_OK;
+    if (!bits || !g_abs || !g_phase || !grad) { set_error("null pointer argument"); return NQS_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->mc.arch == NQS_ARCH_PRODUCT)
+        return launch_product_backward(m->mc, m->d_params, bits, B, g_abs, grad, s);
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
+    NQS_TRY(need_ws(m, nullptr, NQS_OP_BACKWARD, B, ws, ws_bytes));
+    Carver c(ws);
+    const int64_t ld = made_act_stride(m->mc);
+    float* acts = c.take<float>(B * ld);
+    {
+        ProfScope ps("made_backward", s);
+        NQS_TRY(launch_made_backward(m->mc, m->d_params, bits, B, g_abs, g_phase, acts, ld, s));
+    }
+    {
+        ProfScope ps("grad_reduce", s);
+        NQS_TRY(made_grad_reduce(m->mc, acts, ld, B, grad, s));
+    }
+    return NQS_OK;
+}
+
+int nqs_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
+                     float* g_abs, float* g_phase, void* stream) {
+    if (B < 1 || !eloc || !counts || !stats) { set_error("need B >= 1 and eloc/counts/stats"); return NQS_ERR_INVALID_ARG; }
+    if ((g_abs == nullptr) != (g_phase == nullptr)) { set_error("g_abs and g_phase go together"); return NQS_ERR_INVALID_ARG; }
+    return launch_energy_stats(eloc, counts, B, stats, g_abs, g_phase, (cudaStream_t)stream);
+}
+
+int nqs_adam_step(float* p, const float* g, float* mm, float* v, int64_t n, int step, float lr,
+                  float b1, float b2, float eps, void* stream) {
+    if (!p || !g || !mm || !v || n < 0 || step < 1) { set_error("bad Adam arguments"); return NQS_ERR_INVALID_ARG; }
+    if (n == 0) return NQS_OK;
+    return launch_adam(p, g, mm, v, n, step, lr, b1, b2, eps, (cudaStream_t)stream);
+}
+
+}  // extern "C"

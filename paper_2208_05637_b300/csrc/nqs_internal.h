@@ -1,0 +1,212 @@
+// Internal declarations shared by the C-ABI layer and the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nqs.h"
+
+namespace nqs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define NQS_CK(call)                                                              \
+    do {                                                                          \
+        cudaError_t e__ = (call);                                                 \
+        if (e__ != cudaSuccess) return ::nqs::cuda_fail(e__, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// Check for launch errors right after a <<<>>> launch and count the launch.
+#define NQS_LAUNCHED()                                                            \
+    do {                                                                          \
+        ::nqs::count_launch();                                                    \
+        cudaError_t e__ = cudaGetLastError();                                     \
+        if (e__ != cudaSuccess) return ::nqs::cuda_fail(e__, "kernel launch", __FILE__, __LINE__); \
+    } while (0)
+
+#define NQS_TRY(x)                                                                \
+    do {                                                                          \
+        int s__ = (x);                                                            \
+        if (s__ != NQS_OK) return s__;                                            \
+    } while (0)
+
+void count_launch();
+
+// Per-kernel CUDA-event timing (enabled by nqs_profile_enable).
+struct ProfScope {
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+    const char* name;
+    cudaStream_t stream;
+    cudaEvent_t e0 = nullptr;
+};
+
+int num_sms();
+
+// ------------------------------------------------------------------ Hamiltonian
+// group meta word: bits 0-7 n_alpha, 8-15 n_beta, bit 16 "has sigma_2-odd terms"
+constexpr uint32_t META_HAS_IMAG = 1u << 16;
+
+struct HamDev {
+    int n;
+    int64_t K;      // merged terms
+    int64_t G;      // groups
+    const uint64_t* grp_mask;
+    const uint32_t* grp_off;   // G+1
+    const uint32_t* grp_meta;  // G
+    const uint64_t* term_z;    // K
+    const float2* term_c;      // K: (hi, lo) of the signed real magnitude
+};
+
+}  // namespace nqs
+
+struct nqs_ham_s {
+    int n = 0;
+    int device = 0;
+    int64_t K_in = 0, K = 0, G = 0;
+    std::vector<uint64_t> grp_mask;
+    std::vector<int64_t> grp_off;
+    std::vector<uint32_t> grp_meta;
+    std::vector<uint64_t> term_z;
+    std::vector<double> term_c_re, term_c_im;   // phase-folded c' (exactly one is nonzero)
+    void* d_block = nullptr;                    // one device allocation for all arrays
+    nqs::HamDev dev{};
+};
+
+namespace nqs {
+
+// ------------------------------------------------------------------ model
+constexpr int MAX_Q = 64;
+constexpr int MADE_MAX_LAYERS = 4;
+constexpr int TF_MAX_LAYERS = 8;
+
+// Plain-old-data model description handed to kernels by value.
+struct ModelConst {
+    int arch, n, n_up, n_dn, hidden, layers, heads, precision, compensated;
+    uint8_t order[MAX_Q];   // order[t] = qubit of position t
+    uint8_t after[MAX_Q];   // same-spin positions after t
+    // parameter tensor offsets (floats) into the flat vector
+    // PRODUCT: p
+    int64_t p_prob;
+    // MADE
+    int64_t made_W[MADE_MAX_LAYERS], made_b[MADE_MAX_LAYERS];
+    int64_t made_Wout, made_bout, ph_W0, ph_b0, ph_W1, ph_b1;
+    // TRANSFORMER
+    int64_t tok_emb, pos_emb;
+    int64_t ln1_g[TF_MAX_LAYERS], ln1_b[TF_MAX_LAYERS], wqkv[TF_MAX_LAYERS], bqkv[TF_MAX_LAYERS];
+    int64_t wo[TF_MAX_LAYERS], bo[TF_MAX_LAYERS], ln2_g[TF_MAX_LAYERS], ln2_b[TF_MAX_LAYERS];
+    int64_t w1[TF_MAX_LAYERS], b1[TF_MAX_LAYERS], w2[TF_MAX_LAYERS], b2[TF_MAX_LAYERS];
+    int64_t lnf_g, lnf_b, head_w, head_b, phase_w, phase_b;
+};
+
+struct ParamInfo {
+    std::string name;
+    int64_t offset, numel;
+};
+
+}  // namespace nqs
+
+struct nqs_model_s {
+    nqs_model_desc desc{};
+    nqs::ModelConst mc{};
+    std::vector<nqs::ParamInfo> params;
+    int64_t n_params = 0;
+    const float* d_params = nullptr;
+};
+
+namespace nqs {
+
+// ------------------------------------------------------------------ workspace carving
+// A bump allocator over the caller's workspace; in measure mode it only counts bytes.
+struct Carver {
+    char* base;
+    size_t used = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(T);
+        return base ? reinterpret_cast<T*>(base + off) : nullptr;
+    }
+};
+
+// ------------------------------------------------------------------ launchers (.cu files)
+// term sweep (sweep.cu)
+constexpr int SWEEP_GT = 256;   // groups per tile (threads per CTA)
+constexpr int SWEEP_SB = 32;    // samples per CTA batch
+int64_t sweep_tiles(const HamDev& h);
+int launch_sweep_count(const HamDev& h, uint64_t amask, uint64_t bmask, int n_up, int n_dn,
+                       const uint64_t* bits, int64_t B, int32_t* cnt, cudaStream_t s);
+int launch_sweep_emit(const HamDev& h, uint64_t amask, uint64_t bmask, int n_up, int n_dn,
+                      int compensated, const uint64_t* bits, int64_t B, const int64_t* off,
+                      uint64_t* xprime, float4* S, cudaStream_t s);
+int launch_unpack_rows(const int64_t* off, int64_t ntiles, int64_t B, const float4* S,
+                       int64_t* row_offset, float* s_re, float* s_im, int64_t rows_cap,
+                       const int64_t* total, cudaStream_t s);
+
+// scans and reductions (reduce.cu)
+// Exclusive scan of n int32 -> int64 out[n+1] (out[n] = total); one CTA.
+int launch_scan_i32(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
+// Exclusive scan of n int64 (n read from device *n_dev if non-null) -> out[n+1]; one CTA.
+int launch_scan_i64(const int64_t* in, int64_t n_host_max, const int64_t* n_dev, int64_t* out,
+                    cudaStream_t s);
+int launch_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
+                        float* g_abs, float* g_phase, cudaStream_t s);
+int launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
+                float b1, float b2, float eps, cudaStream_t s);
+// dW[o][i] += mask(o,i) * sum_b delta[b*ld_d + o] * act[b*ld_a + i]; db[o] += sum_b delta
+// mask_kind: 0 none, 1 MADE input (i < deg(o)), 2 MADE hidden (deg(i) <= deg(o)),
+//            3 MADE output (deg(i) < o+1); deg(k) = k % (n-1) + 1
+int launch_outer_grad(const float* delta, int64_t ld_d, const float* act, int64_t ld_a,
+                      int64_t B, int out_dim, int in_dim, int mask_kind, int n_mask,
+                      float* dW, float* db, cudaStream_t s);
+
+// models (made.cu): rowwise models (PRODUCT, MADE)
+int launch_logpsi_rows(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                       float* la, float* ph, cudaStream_t s);
+int launch_eloc_rows(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                     const float* la_x, const float* ph_x, const int64_t* off, int64_t ntiles,
+                     const uint64_t* xprime, const float4* S, float* eloc, cudaStream_t s);
+int launch_cond_rows(const ModelConst& mc, const float* P, int k, const uint64_t* bits,
+                     const int64_t* U, int64_t cap, float* p_out, uint64_t* thr, float* trace,
+                     cudaStream_t s);
+int launch_made_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                         const float* g_abs, const float* g_phase, float* acts, int64_t ld,
+                         cudaStream_t s);
+int64_t made_act_stride(const ModelConst& mc);
+int made_grad_reduce(const ModelConst& mc, const float* acts, int64_t ld, int64_t B,
+                     float* grad, cudaStream_t s);
+int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t* bits,
+                            int64_t B, const float* g_abs, float* grad, cudaStream_t s);
+
+// sampler (sampler.cu)
+struct SamplerBufs {
+    uint64_t *bitsA, *bitsB;
+    int64_t *cntA, *cntB;
+    int64_t* start;      // cap+1
+    int64_t* n1;         // cap
+    uint64_t* thr;       // cap
+    float* p;            // cap
+    int64_t* flags0;     // cap
+    int64_t* flags1;     // cap
+    int64_t* pos0;       // cap+1
+    int64_t* pos1;       // cap+1
+    int64_t* U;          // device scalars: U[0] current U
+    int64_t cap;
+};
+int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b);
+int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
+                uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
+                cudaStream_t s);
+int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out,
+                        int64_t n, cudaStream_t s);
+
+}  // namespace nqs

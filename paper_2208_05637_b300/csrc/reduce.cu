@@ -1,0 +1,216 @@
+// Scans, FP64 energy statistics (paper Eq. total_energy_sum), Adam (Section 5.1) and the
+// deterministic outer-product reduction used by the backward pass (Eq. grad).
+#include "nqs_internal.h"
+
+namespace nqs {
+namespace {
+
+constexpr int SCAN_T = 1024;   // threads of the single-CTA scans
+constexpr int SCAN_V = 4;      // elements per thread per tile
+
+// Block-wide exclusive scan of one int64 per thread; returns the block total in *total.
+__device__ int64_t block_excl_scan(int64_t v, int64_t* warp_sums, int64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int64_t w = lane < nw ? warp_sums[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < nw) warp_sums[lane] = wi - w;
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    const int64_t r = warp_sums[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SCAN_T)
+scan_kernel(const T* __restrict__ in, int64_t n_max, const int64_t* __restrict__ n_dev,
+            int64_t* __restrict__ out) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t tot;
+    const int64_t n = n_dev ? min(*n_dev, n_max) : n_max;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < n; base += (int64_t)SCAN_T * SCAN_V) {
+        int64_t v[SCAN_V];
+        int64_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_V; ++i) {
+            const int64_t idx = base + (int64_t)threadIdx.x * SCAN_V + i;
+            v[i] = idx < n ? (int64_t)in[idx] : 0;
+            sum += v[i];
+        }
+        int64_t ex = block_excl_scan(sum, warp_sums, &tot) + carry;
+#pragma unroll
+        for (int i = 0; i < SCAN_V; ++i) {
+            const int64_t idx = base + (int64_t)threadIdx.x * SCAN_V + i;
+            if (idx < n) out[idx] = ex;
+            ex += v[i];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// ---------------------------------------------------------------- energy statistics
+__global__ void __launch_bounds__(1024)
+stats_kernel(const float* __restrict__ eloc, const int64_t* __restrict__ counts, int64_t B,
+             double* __restrict__ stats, float* __restrict__ g_abs, float* __restrict__ g_phase) {
+    __shared__ double red[3][1024];
+    double w = 0.0, er = 0.0, ei = 0.0;
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+        const double c = (double)counts[i];
+        w += c;
+        er += c * (double)eloc[2 * i];
+        ei += c * (double)eloc[2 * i + 1];
+    }
+    red[0][threadIdx.x] = w; red[1][threadIdx.x] = er; red[2][threadIdx.x] = ei;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
+        __syncthreads();
+    }
+    const double W = red[0][0], mr = red[1][0] / W, mi = red[2][0] / W;
+    __syncthreads();
+    double var = 0.0;
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+        const double c = (double)counts[i];
+        const double dr = (double)eloc[2 * i] - mr, di = (double)eloc[2 * i + 1] - mi;
+        var += c * (dr * dr + di * di);
+        if (g_abs) {
+            g_abs[i] = (float)(2.0 * c / W * dr);
+            g_phase[i] = (float)(2.0 * c / W * (double)eloc[2 * i + 1]);
+        }
+    }
+    red[0][threadIdx.x] = var;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[0][threadIdx.x] += red[0][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        stats[0] = mr; stats[1] = mi; stats[2] = red[0][0] / W; stats[3] = W;
+    }
+}
+
+// ---------------------------------------------------------------- Adam
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi; v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------- outer-product gradients
+__device__ __forceinline__ bool made_mask(int kind, int o, int i, int n) {
+    if (kind == 0) return true;
+    const int dn = n - 1;
+    if (kind == 1) return i < (o % dn) + 1;              // input t feeds hidden o iff t < deg(o)
+    if (kind == 2) return (i % dn) <= (o % dn);           // deg(i) <= deg(o)
+    return (i % dn) + 1 < o + 1;                          // output o <- hidden i iff deg(i) < o+1
+}
+
+constexpr int OG_T = 32;   // output/input tile
+__global__ void __launch_bounds__(256)
+outer_grad_kernel(const float* __restrict__ delta, int64_t ld_d, const float* __restrict__ act,
+                  int64_t ld_a, int64_t B, int out_dim, int in_dim, int mask_kind, int n_mask,
+                  float* __restrict__ dW, float* __restrict__ db) {
+    __shared__ float sd[OG_T][OG_T + 1];
+    __shared__ float sa[OG_T][OG_T + 1];
+    const int o0 = blockIdx.y * OG_T, i0 = blockIdx.x * OG_T;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty: 0..7
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float bacc = 0.f;
+    for (int64_t b0 = 0; b0 < B; b0 += OG_T) {
+        for (int r = ty; r < OG_T; r += 8) {
+            const int64_t b = b0 + r;
+            sd[r][tx] = (b < B && o0 + tx < out_dim) ? delta[b * ld_d + o0 + tx] : 0.f;
+            sa[r][tx] = (b < B && i0 + tx < in_dim) ? act[b * ld_a + i0 + tx] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < OG_T; ++r) {
+            const float a = sa[r][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += sd[r][ty * 4 + q] * a;
+            if (ty == 0 && blockIdx.x == 0) bacc += sd[r][tx];
+        }
+        __syncthreads();
+    }
+    const int i = i0 + tx;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = o0 + ty * 4 + q;
+        if (o < out_dim && i < in_dim && made_mask(mask_kind, o, i, n_mask))
+            dW[(int64_t)o * in_dim + i] += acc[q];
+    }
+    if (db && ty == 0 && blockIdx.x == 0 && o0 + tx < out_dim) db[o0 + tx] += bacc;
+}
+
+}  // namespace
+
+int launch_scan_i32(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s) {
+    scan_kernel<int32_t><<<1, SCAN_T, 0, s>>>(in, n, nullptr, out);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int launch_scan_i64(const int64_t* in, int64_t n_max, const int64_t* n_dev, int64_t* out,
+                    cudaStream_t s) {
+    scan_kernel<int64_t><<<1, SCAN_T, 0, s>>>(in, n_max, n_dev, out);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int launch_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
+                        float* g_abs, float* g_phase, cudaStream_t s) {
+    ProfScope ps("energy_stats", s);
+    stats_kernel<<<1, 1024, 0, s>>>(eloc, counts, B, stats, g_abs, g_phase);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
+                float b1, float b2, float eps, cudaStream_t s) {
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, step)));
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+    ProfScope ps("adam", s);
+    adam_kernel<<<grid, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int launch_outer_grad(const float* delta, int64_t ld_d, const float* act, int64_t ld_a,
+                      int64_t B, int out_dim, int in_dim, int mask_kind, int n_mask, float* dW,
+                      float* db, cudaStream_t s) {
+    if (out_dim <= 0) return NQS_OK;
+    dim3 grid((unsigned)std::max(1, (in_dim + OG_T - 1) / OG_T), (unsigned)((out_dim + OG_T - 1) / OG_T));
+    outer_grad_kernel<<<grid, 256, 0, s>>>(delta, ld_d, act, ld_a, B, out_dim, in_dim, mask_kind,
+                                           n_mask, dW, db);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+}  // namespace nqs

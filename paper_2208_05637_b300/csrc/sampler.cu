@@ -1,0 +1,307 @@
+// Unique-sample autoregressive sampling with occurrence counts (paper Section 4, Sampling).
+//
+// The buffer holds distinct prefixes in ascending bit order with their counts; it starts as one
+// empty prefix with count N_s.  Step k (qubit q = order[k]):
+//   1. the model gives each parent its constrained conditional p = pihat(x_q = 1 | prefix);
+//   2. each nominal sample j -- parent s owns j in [start_s, start_s + count_s) with start the
+//      exclusive prefix sum of the counts -- draws u = word 0 of Philox4x32-10(counter
+//      (j, k, 0, 0), key (seed lo, seed hi)) and counts a one iff u < floor(p * 2^32);
+//   3. parent s splits into (bits, count - ones) and (bits | 1 << q, ones); zero counts vanish;
+//   4. if more than max_unique entries remain, the top max_unique by (count desc, bits asc)
+//      are kept (the paper evicts the lowest counts; ties are broken by bit order here).
+// Children keep the ascending order without a sort: parents are sorted and OR-ing the absent
+// bit q into every parent preserves their order, so each child list is sorted and the new
+// buffer is the merge of the two, done by binary searches.  Everything runs against the
+// device-side unique count; the host reads U once, after the last step.
+//
+// Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11 (ten rounds; multipliers 0xD2511F53, 0xCD9E8D57; Weyl key increments 0x9E3779B9,
+// 0xBB67AE85).
+#include "nqs_internal.h"
+
+namespace nqs {
+namespace {
+
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return c0;
+}
+
+__global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_samples) {
+    bits[0] = 0;
+    cnt[0] = n_samples;
+    U[0] = 1;
+}
+
+// ones per parent: warp-aggregated integer atomics (exact, order-independent)
+__global__ void draw_kernel(int64_t n_samples, const int64_t* __restrict__ start,
+                            const int64_t* __restrict__ Udev, const uint64_t* __restrict__ thr,
+                            int64_t* __restrict__ n1, int k, uint32_t key0, uint32_t key1) {
+    const int64_t U = *Udev;
+    // after an eviction the surviving counts sum to less than n_samples: the nominal indices
+    // run over [0, start[U]) only
+    const int64_t total = min(start[U], n_samples);
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < total; j0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = j0 + threadIdx.x;
+        int64_t s = -1;
+        bool one = false;
+        if (j < total) {
+            // parent = last s with start[s] <= j
+            int64_t lo = 0, hi = U - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (start[mid] <= j) lo = mid; else hi = mid - 1;
+            }
+            s = lo;
+            const uint32_t u = philox_word0((uint32_t)j, (uint32_t)k, 0u, 0u, key0, key1);
+            one = (uint64_t)u < thr[s];
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, one ? s : -1);
+        if (one) {
+            const int leader = __ffs(grp) - 1;
+            if ((int)(threadIdx.x & 31) == leader) atomicAdd((unsigned long long*)&n1[s], (unsigned long long)__popc(grp));
+        }
+    }
+}
+
+__global__ void zero_kernel(int64_t* a, const int64_t* Udev, int64_t cap) {
+    const int64_t U = min(*Udev, cap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < U; i += (int64_t)gridDim.x * blockDim.x) a[i] = 0;
+}
+
+__global__ void flags_kernel(const int64_t* __restrict__ cnt, const int64_t* __restrict__ n1,
+                             const int64_t* __restrict__ Udev, int64_t* __restrict__ f0,
+                             int64_t* __restrict__ f1) {
+    const int64_t U = *Udev;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < U; s += (int64_t)gridDim.x * blockDim.x) {
+        f0[s] = (cnt[s] - n1[s]) > 0;
+        f1[s] = n1[s] > 0;
+    }
+}
+
+// first index in [0, U) whose key exceeds v, where key(s) = bits[s] | orbit (monotone in s)
+__device__ __forceinline__ int64_t upper(const uint64_t* bits, int64_t U, uint64_t orbit, uint64_t v) {
+    int64_t lo = 0, hi = U;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((bits[mid] | orbit) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void merge_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
+                             const int64_t* __restrict__ n1, const int64_t* __restrict__ pos0,
+                             const int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
+                             uint64_t qbit, uint64_t* __restrict__ nbits, int64_t* __restrict__ ncnt) {
+    const int64_t U = *Udev;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < U; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c1 = n1[s], c0 = cnt[s] - c1;
+        if (c0 > 0) {
+            // children-1 keys below bits[s]: parents whose key (bits | q) is below bits[s]
+            const int64_t r = pos1[upper(bits, U, qbit, bits[s])];
+            nbits[pos0[s] + r] = bits[s];
+            ncnt[pos0[s] + r] = c0;
+        }
+        if (c1 > 0) {
+            const uint64_t key = bits[s] | qbit;
+            const int64_t r = pos0[upper(bits, U, 0, key)];
+            nbits[pos1[s] + r] = key;
+            ncnt[pos1[s] + r] = c1;
+        }
+    }
+}
+
+__global__ void set_u_kernel(int64_t* Udev, const int64_t* pos0, const int64_t* pos1) {
+    const int64_t U = *Udev;
+    Udev[0] = pos0[U] + pos1[U];
+}
+
+// Keep the top max_unique entries by (count desc, bits asc); one CTA, order preserved.
+__global__ void __launch_bounds__(1024)
+evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
+             int64_t* __restrict__ Udev, int64_t max_unique, uint64_t* __restrict__ obits,
+             int64_t* __restrict__ ocnt, int32_t* __restrict__ did) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t s_prefix, s_need;
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t carry_sh;
+    const int64_t U = *Udev;
+    if (U <= max_unique) { if (threadIdx.x == 0) *did = 0; return; }
+    // radix select of the max_unique-th largest count (counts < 2^31)
+    uint32_t prefix = 0, pmask = 0;
+    uint32_t need = (uint32_t)max_unique;   // how many still to take at or above prefix
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int64_t s = threadIdx.x; s < U; s += blockDim.x) {
+            const uint32_t c = (uint32_t)cnt[s];
+            if ((c & pmask) == prefix) atomicAdd(&hist[(c >> shift) & 0xffu], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            int d = 255;
+            for (; d > 0; --d) {
+                if (acc + hist[d] >= need) break;
+                acc += hist[d];
+            }
+            s_prefix = prefix | ((uint32_t)d << shift);
+            s_need = need - acc;
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        need = s_need;
+        pmask |= 0xffu << shift;
+        __syncthreads();
+    }
+    const uint32_t T = prefix;      // threshold count; keep `need` of the entries equal to T
+    // ordered compaction: keep c > T, and the first `need` entries with c == T
+    int64_t carry_keep = 0, carry_eq = 0;
+    for (int64_t base = 0; base < U; base += blockDim.x) {
+        const int64_t s = base + threadIdx.x;
+        const uint32_t c = s < U ? (uint32_t)cnt[s] : 0u;
+        const int64_t eq = (s < U && c == T) ? 1 : 0;
+        // rank among equals
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int64_t incl = eq;
+        for (int d = 1; d < 32; d <<= 1) { const int64_t y = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += y; }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0, wi = w;
+            for (int d = 1; d < 32; d <<= 1) { const int64_t y = __shfl_up_sync(0xffffffffu, wi, d); if (lane >= d) wi += y; }
+            if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = wi - w;
+            if (lane == 31) carry_sh = wi;
+        }
+        __syncthreads();
+        const int64_t eq_rank = carry_eq + warp_sums[warp] + incl - eq;
+        const int64_t tot_eq = carry_sh;
+        __syncthreads();
+        const int64_t keep = (s < U && (c > T || (c == T && eq_rank < (int64_t)need))) ? 1 : 0;
+        incl = keep;
+        for (int d = 1; d < 32; d <<= 1) { const int64_t y = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += y; }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0, wi = w;
+            for (int d = 1; d < 32; d <<= 1) { const int64_t y = __shfl_up_sync(0xffffffffu, wi, d); if (lane >= d) wi += y; }
+            if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = wi - w;
+            if (lane == 31) carry_sh = wi;
+        }
+        __syncthreads();
+        if (keep) {
+            const int64_t pos = carry_keep + warp_sums[warp] + incl - keep;
+            obits[pos] = bits[s];
+            ocnt[pos] = cnt[s];
+        }
+        carry_keep += carry_sh;
+        carry_eq += tot_eq;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { *Udev = max_unique; *did = 1; }
+}
+
+__global__ void copy_back_kernel(const int32_t* __restrict__ did, const int64_t* __restrict__ Udev,
+                                 const uint64_t* __restrict__ sb, const int64_t* __restrict__ sc,
+                                 uint64_t* __restrict__ db, int64_t* __restrict__ dc) {
+    if (!*did) return;
+    const int64_t U = *Udev;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < U; i += (int64_t)gridDim.x * blockDim.x) {
+        db[i] = sb[i];
+        dc[i] = sc[i];
+    }
+}
+
+__global__ void copy_out_kernel(const uint64_t* __restrict__ sb, const int64_t* __restrict__ sc,
+                                uint64_t* __restrict__ db, int64_t* __restrict__ dc, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        db[i] = sb[i];
+        dc[i] = sc[i];
+    }
+}
+
+inline int grid_for(int64_t work) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)num_sms() * 16));
+}
+
+}  // namespace
+
+int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b) {
+    b.cap = std::max<int64_t>(1, std::min<int64_t>(n_samples, 2 * max_unique));
+    const int64_t cap = b.cap;
+    b.bitsA = c.take<uint64_t>(cap);
+    b.bitsB = c.take<uint64_t>(cap);
+    b.cntA = c.take<int64_t>(cap);
+    b.cntB = c.take<int64_t>(cap);
+    b.start = c.take<int64_t>(cap + 1);
+    b.n1 = c.take<int64_t>(cap);
+    b.thr = c.take<uint64_t>(cap);
+    b.p = c.take<float>(cap);
+    b.flags0 = c.take<int64_t>(cap);
+    b.flags1 = c.take<int64_t>(cap);
+    b.pos0 = c.take<int64_t>(cap + 1);
+    b.pos1 = c.take<int64_t>(cap + 1);
+    b.U = c.take<int64_t>(4);
+    return NQS_OK;
+}
+
+int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
+                uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
+                cudaStream_t s) {
+    const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
+    int32_t* did = reinterpret_cast<int32_t*>(b.U + 2);
+    ProfScope ps("sample", s);
+    init_kernel<<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples);
+    NQS_LAUNCHED();
+    uint64_t* cb = b.bitsA; int64_t* cc = b.cntA;
+    uint64_t* nb = b.bitsB; int64_t* nc = b.cntB;
+    const int g = grid_for(b.cap);
+    for (int k = 0; k < mc.n; ++k) {
+        NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr,
+                                 trace ? trace + (int64_t)k * trace_stride : nullptr, s));
+        NQS_TRY(launch_scan_i64(cc, b.cap, b.U, b.start, s));
+        zero_kernel<<<g, 256, 0, s>>>(b.n1, b.U, b.cap);
+        NQS_LAUNCHED();
+        draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k, key0, key1);
+        NQS_LAUNCHED();
+        flags_kernel<<<g, 256, 0, s>>>(cc, b.n1, b.U, b.flags0, b.flags1);
+        NQS_LAUNCHED();
+        NQS_TRY(launch_scan_i64(b.flags0, b.cap, b.U, b.pos0, s));
+        NQS_TRY(launch_scan_i64(b.flags1, b.cap, b.U, b.pos1, s));
+        merge_kernel<<<g, 256, 0, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc);
+        NQS_LAUNCHED();
+        set_u_kernel<<<1, 1, 0, s>>>(b.U, b.pos0, b.pos1);
+        NQS_LAUNCHED();
+        std::swap(cb, nb);
+        std::swap(cc, nc);
+        if (max_unique < n_samples) {
+            // evict into the spare buffer, then copy back so (cb, cc) stays current
+            evict_kernel<<<1, 1024, 0, s>>>(cb, cc, b.U, max_unique, nb, nc, did);
+            NQS_LAUNCHED();
+            copy_back_kernel<<<g, 256, 0, s>>>(did, b.U, nb, nc, cb, cc);
+            NQS_LAUNCHED();
+        }
+    }
+    if (cb != b.bitsA) {
+        copy_out_kernel<<<g, 256, 0, s>>>(cb, cc, b.bitsA, b.cntA, b.cap);
+        NQS_LAUNCHED();
+    }
+    return NQS_OK;
+}
+
+int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out, int64_t n,
+                        cudaStream_t s) {
+    copy_out_kernel<<<grid_for(n), 256, 0, s>>>(b.bitsA, b.cntA, bits_out, counts_out, n);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+}  // namespace nqs

@@ -1,0 +1,85 @@
+"""The VMC step on top of the C ABI: log psi as a torch.autograd.Function with a hand-written
+backward, mini-batch gradient accumulation with forward recomputation, FP64 statistics and Adam
+(paper Eqs. total_energy, grad; Section 5.1: Adam lr 1e-3, betas (0.9, 0.99); Section 5.2
+gradient accumulation).
+"""
+import torch
+
+from . import (OP_BACKWARD, OP_LOCAL_ENERGY, OP_SAMPLE, nqs_adam_step, nqs_energy_stats,
+               nqs_local_energy, nqs_logpsi, nqs_logpsi_backward, nqs_sample)
+
+
+class LogPsi(torch.autograd.Function):
+    """(log|f(x)|, phi(x)) = LogPsi.apply(params, model, bits).
+
+    `params` must be the flat fp32 tensor bound to `model`.  Nothing is saved but the bits: the
+    backward recomputes the forward inside nqs_logpsi_backward (activation recomputation) and
+    returns sum_i g_abs_i d log|f_i|/d theta + g_phase_i d phi_i/d theta."""
+
+    @staticmethod
+    def forward(ctx, params, model, bits):
+        la, ph = nqs_logpsi(model, bits)
+        ctx.model = model
+        ctx.save_for_backward(bits)
+        return la, ph
+
+    @staticmethod
+    def backward(ctx, g_la, g_ph):
+        (bits,) = ctx.saved_tensors
+        model = ctx.model
+        g_la = torch.zeros_like(bits, dtype=torch.float32) if g_la is None else g_la.float().contiguous()
+        g_ph = torch.zeros_like(bits, dtype=torch.float32) if g_ph is None else g_ph.float().contiguous()
+        grad = torch.zeros_like(model.params)
+        nqs_logpsi_backward(model, bits, g_la, g_ph, grad)
+        return grad, None, None
+
+
+class VMC:
+    """One variational Monte Carlo step per call: sample -> local energies (mini-batched) ->
+    FP64 statistics -> surrogate backward (mini-batched, recomputed) -> Adam."""
+
+    def __init__(self, ham, model, params, n_samples, mini_batches=1, max_unique=None,
+                 lr=1e-3, betas=(0.9, 0.99), eps=1e-8):
+        self.ham, self.model = ham, model
+        self.params = params.detach().requires_grad_(True)
+        model.bind(self.params)
+        self.n_samples = int(n_samples)
+        self.max_unique = int(max_unique or n_samples)
+        self.mini_batches = int(mini_batches)
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.m = torch.zeros_like(self.params, requires_grad=False)
+        self.v = torch.zeros_like(self.params, requires_grad=False)
+        self.t = 0
+        self.ws_sample = model.workspace(OP_SAMPLE, self.n_samples)
+        self._ws = {}
+
+    def _workspace(self, op, batch):
+        key = (op, batch)
+        if key not in self._ws:
+            self._ws[key] = self.model.workspace(op, batch, self.ham if op == OP_LOCAL_ENERGY else None)
+        return self._ws[key]
+
+    def _slices(self, U):
+        per = max(1, -(-U // self.mini_batches))
+        return [slice(lo, min(U, lo + per)) for lo in range(0, U, per)]
+
+    def step(self, seed):
+        bits, counts, _ = nqs_sample(self.model, self.n_samples, self.max_unique, seed,
+                                     ws=self.ws_sample)
+        U = bits.numel()
+        eloc = torch.empty((U, 2), dtype=torch.float32, device="cuda")
+        per = max(1, -(-U // self.mini_batches))
+        for sl in self._slices(U):
+            nqs_local_energy(self.ham, self.model, bits[sl], ws=self._workspace(OP_LOCAL_ENERGY, per),
+                             out=eloc[sl])
+        stats, g_abs, g_phase = nqs_energy_stats(eloc, counts)
+        if self.params.grad is not None:
+            self.params.grad.zero_()
+        for sl in self._slices(U):
+            la, ph = LogPsi.apply(self.params, self.model, bits[sl])
+            (la * g_abs[sl]).sum().add((ph * g_phase[sl]).sum()).backward()
+        self.t += 1
+        with torch.no_grad():
+            nqs_adam_step(self.params, self.params.grad, self.m, self.v, self.t, self.lr,
+                          self.betas[0], self.betas[1], self.eps)
+        return dict(bits=bits, counts=counts, eloc=eloc, stats=stats, unique=U)
