@@ -1,0 +1,353 @@
+"""Benchmark: one VMC step of the NQS local-energy hot path per timed step.
+
+A step runs every part of the path on one batch of synthetic input: unique-sample sampling with
+counts, the grouped popcount term sweep, the network on every connected x' with the fused
+ratio-weighted reduction (mini-batched), FP64 energy statistics, the log psi backward with
+recomputation (mini-batched) and one Adam update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ID] [--impl ours|reference]
+
+metric: sample.Pauli-term local-energy evaluations per second = sum over the step's local-energy
+calls of (unique samples x Hamiltonian terms K), divided by the step time.  Under torchrun each
+rank runs an independent replica (own sampler seed); the value is the sum over ranks divided
+by the slowest rank's time (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+DEFAULT_WORKLOAD = 2
+FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", type=int, default=DEFAULT_WORKLOAD)
+    ap.add_argument("--beta", type=float, default=2.0)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    import paper_2208_05637_b300 as P
+
+    torch.cuda.set_device(local)
+    cfg = synth.get_config(args.workload)
+    n = cfg.n_qubits
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(n, xm, zm, coef)
+    K_terms, G = ham.info()
+    order = synth.default_order(n)
+    named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
+                              cfg.seed_params, beta=args.beta, order=order)
+    model = P.Model(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
+                    precision=args.precision, compensated=True, order=order)
+    params0 = model.pack(named)
+    vmc = P.VMC(ham, model, params0.clone(), cfg.n_samples, mini_batches=cfg.mini_batches)
+    seed0 = cfg.seed_sampler + 7919 * rank
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 126 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(k, first_seed, e2e=False, host=None):
+        times, evals, units = [], 0, []
+        for i in range(k):
+            flush.random_(0, 255)        # evict L2 between steps (outside the timed events)
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if e2e:
+                vmc.params.data.copy_(host["params"], non_blocking=True)
+            out = vmc.step(seed=first_seed + i)
+            if e2e:
+                host["stats"].copy_(out["stats"], non_blocking=True)
+                U = out["unique"]
+                host["eloc"][:U].copy_(out["eloc"], non_blocking=True)
+            b.record(stream)
+            if e2e:
+                torch.cuda.synchronize()
+            times.append((a, b))
+            units.append(out["unique"])
+            evals += out["unique"] * K_terms
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in times]
+        return ms, evals, units
+
+    # warmup
+    for i in range(args.warmup):
+        vmc.step(seed=seed0 + 100000 + i)
+    barrier()
+
+    # timed region (no profiling)
+    launches0 = P.launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        ms, evals, units = timed_steps(args.steps, seed0)
+        barrier()
+    launches = (P.launch_count() - launches0) / max(args.steps, 1)
+    step_ms = float(np.mean(ms))
+    tot_ms = float(np.sum(ms))
+    # max over ranks of the time; sum over ranks of the work
+    if world > 1:
+        t = torch.tensor([tot_ms, float(evals)], dtype=torch.float64, device="cuda")
+        tmax = t.clone(); dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone(); dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        tot_ms_all, evals_all = tmax[0].item(), tsum[1].item()
+    else:
+        tot_ms_all, evals_all = tot_ms, float(evals)
+    value = evals_all / (tot_ms_all / 1e3)
+
+    # second pass with per-kernel events on the launching stream
+    P.profile_reset(); P.profile_enable(True)
+    ms_p, _, units_p = timed_steps(args.steps, seed0)
+    P.profile_enable(False)
+    kern = {}
+    for name in ("sample", "logpsi_rows", "sweep_count", "term_sweep", "eloc_rows", "made_backward",
+                 "grad_reduce", "energy_stats", "adam", "product_backward"):
+        tms, cnt = P.profile_read(name)
+        if cnt:
+            kern[name] = {"ms_total": tms, "launches": cnt, "ms_per_launch": tms / cnt}
+    rows_per_step = None
+
+    # algorithmic work of the dominant kernel: the network on every connected x' (eloc_rows)
+    roofline = None
+    peaks, peak_kind = load_peaks()
+    if "eloc_rows" in kern and cfg.arch == "made":
+        # rows = connected in-sector x' other than x itself, counted on the last step's samples
+        out = vmc.step(seed=seed0 + 999)
+        bits = out["bits"]
+        ro, xp, _, _ = P.nqs_term_sweep(ham, cfg.n_up, cfg.n_dn, bits)
+        rows = int(xp.numel()) - int(bits.numel())
+        h, L = cfg.hidden, cfg.layers
+        macs = n * h + (L - 1) * h * h + n * h + (n - 2) * h + h
+        launches_per_step = kern["eloc_rows"]["launches"] / max(1, args.steps)
+        flops_launch = 2.0 * macs * rows / max(1.0, launches_per_step)
+        clk_mhz = peaks.get("sm_max_mhz", 2032.0)
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_tflops = sms * FFMA_PER_SM_PER_CLK * 2 * clk_mhz * 1e6 / 1e12
+        per_launch_s = kern["eloc_rows"]["ms_per_launch"] / 1e3
+        ach = flops_launch / per_launch_s / 1e12
+        roofline = {"kernel": "eloc_rows", "bound": "alu", "achieved": ach, "peak": peak_tflops,
+                    "unit": "TFLOP/s", "frac": ach / peak_tflops, "traffic": None,
+                    "peak_source": f"fp32 FFMA: {sms} SMs x {FFMA_PER_SM_PER_CLK} lanes x 2 x "
+                                   f"{clk_mhz:.0f} MHz (max clock)",
+                    "flops_per_row": 2 * macs, "rows_per_launch": rows / max(1.0, launches_per_step)}
+        rows_per_step = rows
+
+    # end to end through the public API with host buffers
+    import torch as _t
+    host = {"params": params0.detach().cpu().pin_memory(),
+            "stats": _t.empty(4, dtype=_t.float64).pin_memory(),
+            "eloc": _t.empty((cfg.n_samples, 2), dtype=_t.float32).pin_memory()}
+    vmc.params.data.copy_(params0)
+    ms_e, evals_e, units_e = timed_steps(args.steps, seed0, e2e=True, host=host)
+    e2e_value = evals_e / (np.sum(ms_e) / 1e3)
+    if world > 1:
+        t = _t.tensor([e2e_value], dtype=_t.float64, device="cuda")
+        dist.all_reduce(t)
+        e2e_value = t.item()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, args, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "sample.Pauli-term local-energy evals/sec (VMC step)",
+            "value": value, "unit": "sample.term/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg.name, "n_qubits": n, "electrons": [cfg.n_up, cfg.n_dn],
+                       "terms_K": K_terms, "groups_G": G, "model": f"{cfg.arch} h={cfg.hidden} L={cfg.layers}",
+                       "n_samples": cfg.n_samples, "mini_batches": cfg.mini_batches,
+                       "unique_samples_mean": float(np.mean(units)), "beta": args.beta,
+                       "precision": args.precision, "compensated": True,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "kernels": kern,
+            "connected_rows_per_step": rows_per_step,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "sample.term/s",
+                    "h2d_bytes_per_step": int(host["params"].numel() * 4),
+                    "d2h_bytes_per_step": int(32 + 8 * float(np.mean(units_e)))},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "peaks_source": peak_kind,
+        }
+        print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def cpu_baseline(cfg, args, budget_s=15.0):
+    """The FP64 oracle as it stands on this host: a bounded sample of the same VMC step
+    (sampling, per-term local energies of a subset of the unique samples, VMC gradient)."""
+    import torch
+    from oracle.eloc import local_energy
+    from oracle.models import Model
+    from oracle.sampler import model_p_fn, sample
+    from oracle.vmc import vmc_gradient
+
+    n = cfg.n_qubits
+    order = synth.default_order(n)
+    named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
+                              cfg.seed_params, beta=args.beta, order=order)
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    om = Model(cfg.arch, named, n, cfg.n_up, cfg.n_dn, order, cfg.hidden, cfg.layers, cfg.heads,
+               requires_grad=True)
+    t0 = time.perf_counter()
+    bits, counts = sample(model_p_fn(om), n, order, cfg.n_samples, cfg.n_samples, cfg.seed_sampler)
+    t_sample = time.perf_counter() - t0
+    # local energies sample by sample until the budget is used
+    done, t_el = 0, 0.0
+    e = []
+    while done < len(bits) and t_el < budget_s:
+        t1 = time.perf_counter()
+        e.append(local_energy(om, xm, zm, coef, bits[done: done + 1])[0])
+        t_el += time.perf_counter() - t1
+        done += 1
+    t2 = time.perf_counter()
+    vmc_gradient(om, bits[:done], counts[:done], np.array(e))
+    t_grad = time.perf_counter() - t2
+    frac = done / len(bits)
+    step_s = t_sample + t_el / frac + t_grad / frac
+    evals = len(bits) * len(coef)
+    return {"value": evals / step_s, "unit": "sample.term/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"full sampler ({cfg.n_samples} nominal), local energy of {done}/{len(bits)} "
+                      f"unique samples and their gradient, extrapolated to the full step "
+                      f"({step_s:.2f} s/step)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = synth.get_config(args.workload)
+    import torch
+    per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v = cpu_baseline(cfg, args, budget_s=per_step)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": "sample.Pauli-term local-energy evals/sec (VMC step)",
+            "value": value, "unit": "sample.term/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name},
+            "cpu_baseline": {"kind": "oracle", "cores": torch.get_num_threads(), "value": value,
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": "sample.term/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
