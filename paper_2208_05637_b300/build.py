@@ -1,6 +1,7 @@
 """Build the CUDA library in-tree: paper_2208_05637_b300/_nqs.so for sm_103a.
 
-    python -m paper_2208_05637_b300.build [--force]
+    python paper_2208_05637_b300/build.py [--force]   (run by path: importing the package
+                                                       needs the library this builds)
 
 One nvcc invocation compiles every .cu/.cpp under csrc/ into a shared library with the C ABI of
 include/nqs.h.  A stamp of the source hashes and flags skips rebuilds when nothing changed.

@@ -5,8 +5,8 @@ import synth
 
 
 def lib():
-    from paper_2208_05637_b300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_2208_05637_b300 as P
     return P
 

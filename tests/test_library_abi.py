@@ -14,8 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2208_05637_b300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_2208_05637_b300 as P
     return P
 
