@@ -193,6 +193,28 @@ int nqs_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double
 int nqs_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int step,
                   float lr, float beta1, float beta2, float eps, void* stream);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+
+/* Size of the library's static device scratch used by nqs_local_energy_noalloc (32 MiB). */
+#define NQS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* nqs_local_energy without any allocation, for callers that cannot call cudaMalloc (code inside
+ * an allocator's or framework's no-allocation region, plugins handed only their input and output
+ * buffers, runtimes that reserve all device memory up front).  The paper has no counterpart: it
+ * is an interface convenience of this library.
+ *   Same arguments and results as nqs_local_energy, minus the workspace: the scratch is one
+ *   static device array of NQS_NOALLOC_SCRATCH_BYTES held by every GPU that loads the library
+ *   until the process exits.  No cudaMalloc, cudaFree or allocating library routine is called.
+ *   Product and MADE models only (NQS_ERR_UNSUPPORTED otherwise).
+ *   Limit: the B per-sample log psi values plus one chunk of at least one sample's sweep rows
+ *   must fit in the scratch; larger requests return NQS_ERR_CAPACITY with a message.
+ *   The first call on a device looks up the scratch's device address (cudaGetSymbolAddress)
+ *   with that device current; make it before any stream capture.  Every call reuses the same
+ *   array: calls whose GPU work overlaps (other streams or host threads) race on it and must be
+ *   serialised by the caller.  Asynchronous on `stream`. */
+int nqs_local_energy_noalloc(nqs_ham_t ham, nqs_model_t model, const uint64_t* bits, int64_t B,
+                             float* eloc, void* stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 const char* nqs_strerror(int status);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_nqs.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"{LIB_PATH} is missing: build the CUDA library first "
-        "(python -m paper_2208_05637_b300.build); there is no CPU fallback")
+        "(python paper_2208_05637_b300/build.py); there is no CPU fallback")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -36,7 +36,7 @@ EXPORTED = [
     "nqs_model_bind_params", "nqs_model_destroy", "nqs_workspace_size", "nqs_sample",
     "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward",
     "nqs_energy_stats", "nqs_adam_step", "nqs_strerror", "nqs_last_error", "nqs_profile_enable",
-    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count",
+    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc",
 ]
 
 
@@ -78,6 +78,7 @@ _sig = {
     "nqs_profile_reset": [],
     "nqs_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
     "nqs_launch_count": [],
+    "nqs_local_energy_noalloc": [_P, _P, _P, _I64, _P, _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -306,6 +307,16 @@ def nqs_local_energy(ham, model, bits, ws=None, out=None, stream=None):
     wp, wn = _ws(ws)
     _check(_lib.nqs_local_energy(ham.handle, model.handle, _ptr(bits), B, _ptr(out), wp, wn,
                                  _stream(stream)), "nqs_local_energy")
+    return out
+
+
+def nqs_local_energy_noalloc(ham, model, bits, out=None, stream=None):
+    """nqs_local_energy without a workspace (static library scratch; see include/nqs.h)."""
+    import torch
+    B = bits.numel()
+    out = torch.empty((B, 2), dtype=torch.float32, device="cuda") if out is None else out
+    _check(_lib.nqs_local_energy_noalloc(ham.handle, model.handle, _ptr(bits), B, _ptr(out),
+                                         _stream(stream)), "nqs_local_energy_noalloc")
     return out
 
 
