@@ -114,6 +114,8 @@ struct ElocBufs {
     int64_t* off;
     uint64_t* xprime;
     float4* S;
+    float2* contrib;     // transformer: per-row ratio-weighted contributions
+    TfBufs tf;
     int64_t chunk, ntiles, rows_cap;
 };
 
@@ -128,6 +130,17 @@ static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int
     e.off = c.take<int64_t>(e.chunk * e.ntiles + 1);
     e.xprime = c.take<uint64_t>(e.rows_cap);
     e.S = c.take<float4>(e.rows_cap);
+    e.contrib = nullptr;
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+        e.contrib = c.take<float2>(e.rows_cap);
+        tf_layout(c, m->mc, std::min(std::max<int64_t>(B, e.rows_cap), tf_seq_capacity(m->mc)), e.tf);
+    }
+}
+
+// Transformer weights for one call: fp32 masters, and the bf16 copies refreshed from them.
+static int tf_weights(const nqs_model_s* m, TfWeights& w, cudaStream_t s) {
+    w.bf16 = m->d_bf16;
+    return tf_prepare_weights(m->mc, m->d_params, w, s);
 }
 
 }  // namespace nqs
@@ -453,10 +466,23 @@ int nqs_model_bind_params(nqs_model_t m, const float* p) {
     if (!m || !p) { set_error("model/params is NULL"); return NQS_ERR_INVALID_ARG; }
     if (((uintptr_t)p) & 15) { set_error("parameter vector must be 16-byte aligned"); return NQS_ERR_INVALID_ARG; }
     m->d_params = p;
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER && m->mc.precision == NQS_PREC_BF16 && !m->d_bf16) {
+        const size_t bytes = (size_t)tf_bf16_weight_elems(m->mc) * 2;
+        if (cudaMalloc((void**)&m->d_bf16, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            m->d_bf16 = nullptr;
+            set_error("cudaMalloc of the bf16 weight copies failed");
+            return NQS_ERR_ALLOC;
+        }
+    }
     return NQS_OK;
 }
 
-void nqs_model_destroy(nqs_model_t m) { delete m; }
+void nqs_model_destroy(nqs_model_t m) {
+    if (!m) return;
+    if (m->d_bf16) cudaFree(m->d_bf16);
+    delete m;
+}
 
 static int tf_unsupported() {
     set_error("this operation is not implemented for the transformer in this build");
@@ -470,10 +496,18 @@ int nqs_workspace_size(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, size_t
         case NQS_OP_SAMPLE: {
             SamplerBufs b;
             NQS_TRY(sampler_layout(c, std::max<int64_t>(batch, 1), std::max<int64_t>(batch, 1), b));
+            if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+                TfBufs tb;
+                tf_layout(c, m->mc, std::min(b.cap, tf_seq_capacity(m->mc)), tb);
+            }
             break;
         }
         case NQS_OP_LOGPSI:
             c.take<char>(256);
+            if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+                TfBufs tb;
+                tf_layout(c, m->mc, std::max<int64_t>(1, std::min(batch, tf_seq_capacity(m->mc))), tb);
+            }
             break;
         case NQS_OP_LOCAL_ENERGY: {
             if (!h) return NQS_ERR_INVALID_ARG;
@@ -526,7 +560,6 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
         set_error("need 1 <= n_samples < 2^31, max_unique >= 1, n_unique non-NULL");
         return NQS_ERR_INVALID_ARG;
     }
-    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
     NQS_TRY(need_ws(m, nullptr, NQS_OP_SAMPLE, n_samples, ws, ws_bytes));
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
@@ -536,7 +569,15 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
         set_error("trace_stride must be >= min(n_samples, 2*max_unique)");
         return NQS_ERR_INVALID_ARG;
     }
-    NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride, s));
+    TfWeights w;
+    TfBufs tb{};
+    TfCtx ctx{&w, &tb};
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+        tf_layout(c, m->mc, std::min(b.cap, tf_seq_capacity(m->mc)), tb);
+        NQS_TRY(tf_weights(m, w, s));
+    }
+    NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride,
+                        &ctx, s));
     int64_t U = 0;
     NQS_CK(cudaMemcpyAsync(&U, b.U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     NQS_CK(cudaStreamSynchronize(s));
@@ -559,7 +600,17 @@ int nqs_logpsi(nqs_model_t m, const uint64_t* bits, int64_t B, float* la, float*
     if (B < 0) return NQS_ERR_INVALID_ARG;
     if (B == 0) return NQS_OK;
     if (!bits || !la || !ph) { set_error("bits/log_abs/phase is NULL"); return NQS_ERR_INVALID_ARG; }
-    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+        NQS_TRY(need_ws(m, nullptr, NQS_OP_LOGPSI, B, ws, ws_bytes));
+        cudaStream_t s = (cudaStream_t)stream;
+        Carver c(ws);
+        c.take<char>(256);
+        TfBufs tb;
+        tf_layout(c, m->mc, std::max<int64_t>(1, std::min(B, tf_seq_capacity(m->mc))), tb);
+        TfWeights w;
+        NQS_TRY(tf_weights(m, w, s));
+        return tf_logpsi(m->mc, m->d_params, w, bits, B, la, ph, tb, s);
+    }
     (void)ws; (void)ws_bytes;
     return launch_logpsi_rows(m->mc, m->d_params, bits, B, la, ph, (cudaStream_t)stream);
 }
@@ -613,13 +664,44 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
     if (h->n != m->mc.n) { set_error("Hamiltonian and model qubit counts differ"); return NQS_ERR_INVALID_ARG; }
     if (B == 0) return NQS_OK;
     if (!bits || !eloc) { set_error("bits/eloc is NULL"); return NQS_ERR_INVALID_ARG; }
-    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
     NQS_TRY(need_ws(m, h, NQS_OP_LOCAL_ENERGY, B, ws, ws_bytes));
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     ElocBufs e;
     eloc_layout(c, m, h, B, e);
     const uint64_t A = spin_mask(h->n, 0), Bm = spin_mask(h->n, 1);
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+        TfWeights w;
+        NQS_TRY(tf_weights(m, w, s));
+        NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, e.la, e.ph, e.tf, s));
+        for (int64_t lo = 0; lo < B; lo += e.chunk) {
+            const int64_t nb = std::min(e.chunk, B - lo);
+            {
+                ProfScope ps("sweep_count", s);
+                NQS_TRY(launch_sweep_count(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, bits + lo, nb, e.cnt, s));
+            }
+            NQS_TRY(launch_scan_i32(e.cnt, nb * e.ntiles, e.off, s));
+            {
+                ProfScope ps("term_sweep", s);
+                NQS_TRY(launch_sweep_emit(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, m->mc.compensated,
+                                          bits + lo, nb, e.off, e.xprime, e.S, s));
+            }
+            int64_t rows = 0;
+            NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+            for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
+                const int64_t R = std::min(e.tf.R, rows - r0);
+                NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s));
+                HeadArgsHost ha{};
+                ha.mode = 1; ha.xsample = bits + lo; ha.la_x = e.la + lo; ha.ph_x = e.ph + lo;
+                ha.seg = e.off; ha.seg_stride = e.ntiles; ha.nseg = nb; ha.row0 = r0; ha.S = e.S;
+                ha.contrib = e.contrib;
+                NQS_TRY(tf_heads(m->mc, m->d_params, e.xprime + r0, R, m->mc.n, e.tf, ha, s));
+            }
+            NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
+        }
+        return NQS_OK;
+    }
     NQS_TRY(launch_logpsi_rows(m->mc, m->d_params, bits, B, e.la, e.ph, s));
     for (int64_t lo = 0; lo < B; lo += e.chunk) {
         const int64_t nb = std::min(e.chunk, B - lo);

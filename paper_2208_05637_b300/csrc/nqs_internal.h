@@ -120,6 +120,7 @@ struct nqs_model_s {
     std::vector<nqs::ParamInfo> params;
     int64_t n_params = 0;
     const float* d_params = nullptr;
+    uint16_t* d_bf16 = nullptr;      // bf16 copies of the transformer GEMM weights (BF16 models)
 };
 
 namespace nqs {
@@ -187,6 +188,53 @@ int made_grad_reduce(const ModelConst& mc, const float* acts, int64_t ld, int64_
 int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t* bits,
                             int64_t B, const float* g_abs, float* grad, cudaStream_t s);
 
+// transformer (transformer.cu, tc_gemm.cu)
+enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3 };
+enum { TF_WQKV = 0, TF_WO = 1, TF_W1 = 2, TF_W2 = 3 };
+struct TfBufs {
+    int64_t R;            // sequences per pass
+    float *h, *a, *qkv, *o, *mid;
+};
+struct TfWeights {
+    const float* fp32 = nullptr;
+    int64_t fp32_off[TF_MAX_LAYERS][4] = {};
+    uint16_t* bf16 = nullptr;                // bf16 working copies (model-owned)
+    int64_t bf16_off[TF_MAX_LAYERS][4] = {};
+};
+struct HeadArgsHost {
+    int mode = 0;
+    float *la = nullptr, *ph = nullptr;
+    const uint64_t* xsample = nullptr;
+    const float *la_x = nullptr, *ph_x = nullptr;
+    const int64_t* seg = nullptr;
+    int64_t seg_stride = 1, nseg = 0, row0 = 0;
+    const float4* S = nullptr;
+    float2* contrib = nullptr;
+    float* p_out = nullptr;
+    uint64_t* thr = nullptr;
+    float* trace = nullptr;
+};
+int64_t tf_seq_capacity(const ModelConst& mc);
+void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b);
+int64_t tf_bf16_weight_elems(const ModelConst& mc);
+int tf_prepare_weights(const ModelConst& mc, const float* P, TfWeights& w, cudaStream_t s);
+int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
+               int64_t R, int T, TfBufs& b, cudaStream_t s);
+int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t R, int T,
+             const TfBufs& b, const HeadArgsHost& ha, cudaStream_t s);
+int tf_segment_sum(const int64_t* seg, int64_t seg_stride, int64_t nseg, const float2* contrib,
+                   int compensated, float* eloc, cudaStream_t s);
+int tf_logpsi(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
+              int64_t B, float* la, float* ph, TfBufs& b, cudaStream_t s);
+// C[M,N] (epi) = A[M,K] (bf16) . W[N,K]^T (bf16) + bias on the tensor cores (tc_gemm.cu).
+// C is fp32 for TF_EPI_STORE / TF_EPI_RESID and bf16 for TF_EPI_GELU.
+int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, int64_t M, int N,
+                 int K, int epi, cudaStream_t s);
+struct TfCtx {
+    const TfWeights* w;
+    TfBufs* b;
+};
+
 // sampler (sampler.cu)
 struct SamplerBufs {
     uint64_t *bitsA, *bitsB;
@@ -205,7 +253,7 @@ struct SamplerBufs {
 int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b);
 int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
                 uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
-                cudaStream_t s);
+                const TfCtx* tf, cudaStream_t s);
 int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out,
                         int64_t n, cudaStream_t s);
 

@@ -253,9 +253,27 @@ int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs
     return NQS_OK;
 }
 
+// Transformer conditional at step k: the parent count is read back (one small synchronous copy
+// per step) to size the layer-wise passes over the first k+1 positions.
+static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* bits,
+                   const int64_t* Udev, SamplerBufs& b, float* trace, const TfCtx* tf,
+                   cudaStream_t s) {
+    int64_t U = 0;
+    NQS_CK(cudaMemcpyAsync(&U, Udev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    for (int64_t lo = 0; lo < U; lo += tf->b->R) {
+        const int64_t R = std::min(tf->b->R, U - lo);
+        NQS_TRY(tf_forward(mc, P, *tf->w, bits + lo, R, k + 1, *tf->b, s));
+        HeadArgsHost ha{};
+        ha.mode = 2; ha.p_out = b.p + lo; ha.thr = b.thr + lo; ha.trace = trace ? trace + lo : nullptr;
+        NQS_TRY(tf_heads(mc, P, bits + lo, R, k + 1, *tf->b, ha, s));
+    }
+    return NQS_OK;
+}
+
 int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
                 uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
-                cudaStream_t s) {
+                const TfCtx* tf, cudaStream_t s) {
     const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
     int32_t* did = reinterpret_cast<int32_t*>(b.U + 2);
     ProfScope ps("sample", s);
@@ -265,8 +283,9 @@ int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t
     uint64_t* nb = b.bitsB; int64_t* nc = b.cntB;
     const int g = grid_for(b.cap);
     for (int k = 0; k < mc.n; ++k) {
-        NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr,
-                                 trace ? trace + (int64_t)k * trace_stride : nullptr, s));
+        float* tr = trace ? trace + (int64_t)k * trace_stride : nullptr;
+        if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, s));
+        else NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr, tr, s));
         NQS_TRY(launch_scan_i64(cc, b.cap, b.U, b.start, s));
         zero_kernel<<<g, 256, 0, s>>>(b.n1, b.U, b.cap);
         NQS_LAUNCHED();
