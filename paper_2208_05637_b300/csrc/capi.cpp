@@ -484,11 +484,6 @@ void nqs_model_destroy(nqs_model_t m) {
     delete m;
 }
 
-static int tf_unsupported() {
-    set_error("this operation is not implemented for the transformer in this build");
-    return NQS_ERR_UNSUPPORTED;
-}
-
 int nqs_workspace_size(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, size_t* bytes) {
     if (!m || !bytes || batch < 0) return NQS_ERR_INVALID_ARG;
     Carver c(nullptr);
@@ -525,6 +520,7 @@ int nqs_workspace_size(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, size_t
         }
         case NQS_OP_BACKWARD:
             if (m->mc.arch == NQS_ARCH_MADE) c.take<float>(std::max<int64_t>(batch, 1) * made_act_stride(m->mc));
+            else if (m->mc.arch == NQS_ARCH_TRANSFORMER) c.take<char>(tf_bwd_workspace(m->mc, std::max<int64_t>(batch, 1)));
             else c.take<char>(256);
             break;
         default:
@@ -734,8 +730,13 @@ int nqs_logpsi_backward(nqs_model_t m, const uint64_t* bits, int64_t B, const fl
     cudaStream_t s = (cudaStream_t)stream;
     if (m->mc.arch == NQS_ARCH_PRODUCT)
         return launch_product_backward(m->mc, m->d_params, bits, B, g_abs, grad, s);
-    if (m->mc.arch == NQS_ARCH_TRANSFORMER) return tf_unsupported();
     NQS_TRY(need_ws(m, nullptr, NQS_OP_BACKWARD, B, ws, ws_bytes));
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+        ProfScope ps("tf_backward", s);
+        Carver c(ws);
+        void* base = c.take<char>(tf_bwd_workspace(m->mc, B));
+        return tf_backward(m->mc, m->d_params, bits, B, g_abs, g_phase, grad, base, s);
+    }
     Carver c(ws);
     const int64_t ld = made_act_stride(m->mc);
     float* acts = c.take<float>(B * ld);

@@ -230,6 +230,11 @@ int tf_logpsi(const ModelConst& mc, const float* P, const TfWeights& w, const ui
 // C is fp32 for TF_EPI_STORE / TF_EPI_RESID and bf16 for TF_EPI_GELU.
 int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, int64_t M, int N,
                  int K, int epi, cudaStream_t s);
+// transformer backward (tf_backward.cu)
+int64_t tf_bwd_seq_capacity(const ModelConst& mc);
+size_t tf_bwd_workspace(const ModelConst& mc, int64_t B);
+int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
 struct TfCtx {
     const TfWeights* w;
     TfBufs* b;

@@ -1,0 +1,569 @@
+// Hand-written backward of the transformer wavefunction (paper Eq. grad, via the surrogate
+// sum_i g_abs_i log|f(x_i)| + g_phase_i phi(x_i)), with the forward recomputed inside
+// (activation recomputation) in chunks of R sequences.  FP32 on CUDA cores; for BF16 models
+// the recomputed forward uses the same bf16-rounded weights and GEMM input activations as the
+// tensor-core forward, and the backward treats the rounding as identity (straight-through).
+//
+// Per chunk: forward with every block's activations saved; heads + final LayerNorm backward;
+// then for each block, last to first: MLP (W2, GELU, W1, LN2) and attention (Wo, softmax
+// attention, Wqkv, LN1) backward; finally the embeddings.  Weight gradients are reductions
+// over all rows of the chunk, done in fixed order (split-K partials reduced in order), so
+// results are bit-reproducible run to run.
+#include "tf_common.cuh"
+
+namespace nqs {
+namespace {
+
+__device__ __forceinline__ float gelu_grad(float x) {
+    const float k = 0.7978845608028654f;
+    const float u = k * (x + 0.044715f * x * x * x);
+    const float th = tanhf(u);
+    return 0.5f * (1.f + th) + 0.5f * x * (1.f - th * th) * k * (1.f + 3.f * 0.044715f * x * x);
+}
+
+template <class T>
+__device__ __forceinline__ float ldf(const T* p) { return (float)*p; }
+
+__global__ void embed_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
+                             int64_t R, int T, float* __restrict__ h) {
+    const int d = mc.hidden;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R * T * d;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / d;
+        const int j = (int)(i % d);
+        const int64_t r = row / T;
+        const int t = (int)(row % T);
+        const int tok = t == 0 ? 2 : (int)((bits[r] >> mc.order[t - 1]) & 1ull);
+        h[i] = P[mc.tok_emb + tok * d + j] + P[mc.pos_emb + t * d + j];
+    }
+}
+
+template <class T_ACT>
+__global__ void gelu_fwd_kernel(const float* __restrict__ x, T_ACT* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        store_act(y + i, gelu_tanh(x[i]));
+}
+
+__global__ void gelu_bwd_kernel(const float* __restrict__ x, float* __restrict__ g, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] *= gelu_grad(x[i]);
+}
+
+__global__ void round_bf16_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __bfloat162float(__float2bfloat16_rn(src[i]));
+}
+
+// LayerNorm backward, one warp per row: out = res + dLN/dx (x, g; dy), and gx = dy * xhat for
+// the gain gradient.
+template <int DPL>
+__global__ void __launch_bounds__(256)
+ln_bwd_kernel(const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ dy,
+              const float* __restrict__ res, float* __restrict__ out, float* __restrict__ gx,
+              int64_t M, int d) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    float v[DPL], dyv[DPL];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) { v[i] = x[row * d + lane + 32 * i]; s += v[i]; }
+    const float mu = warp_sum(s) / d;
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) { v[i] -= mu; q += v[i] * v[i]; }
+    const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
+    float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+        const int j = lane + 32 * i;
+        v[i] *= rstd;                                   // xhat
+        dyv[i] = dy[row * d + j];
+        const float dx = dyv[i] * g[j];
+        m1 += dx;
+        m2 += dx * v[i];
+    }
+    m1 = warp_sum(m1) / d;
+    m2 = warp_sum(m2) / d;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+        const int j = lane + 32 * i;
+        const float dx = dyv[i] * g[j];
+        out[row * d + j] = res[row * d + j] + rstd * (dx - m1 - v[i] * m2);
+        gx[row * d + j] = dyv[i] * v[i];
+    }
+}
+
+// Heads + final LayerNorm backward, one warp per sequence.  Writes dh (gradient wrt the final
+// residual stream), dy rows and dy*xhat rows of LNf, the LNf outputs hf, the logit deltas dl
+// and the one-hot phase deltas dph.
+template <int DPL>
+__global__ void __launch_bounds__(256)
+heads_bwd_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
+                 const float* __restrict__ h, int64_t R, const float* __restrict__ g_abs,
+                 const float* __restrict__ g_phase, float* __restrict__ dh, float* __restrict__ dyo,
+                 float* __restrict__ gx, float* __restrict__ hf, float* __restrict__ dl,
+                 float* __restrict__ dph) {
+    const int d = mc.hidden, n = mc.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= R) return;
+    const uint64_t x = bits[r];
+    const float ga = g_abs[r], gp = g_phase[r];
+    const int sel = (int)(((x >> mc.order[n - 2]) & 1ull) * 2 + ((x >> mc.order[n - 1]) & 1ull));
+    if (lane < 4) dph[r * 4 + lane] = lane == sel ? gp : 0.f;
+    int ones0 = 0, ones1 = 0;
+    for (int t = 0; t < n; ++t) {
+        const int64_t row = r * n + t;
+        const int sp = mc.order[t] & 1;
+        const int b = (int)((x >> mc.order[t]) & 1ull);
+        const int c = sp ? ones1 : ones0;
+        const int need = sp ? mc.n_dn : mc.n_up;
+        const bool free_t = !(c + mc.after[t] < need) && !(c >= need);
+        if (sp) ones1 += b; else ones0 += b;
+        float v[DPL];
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) { v[i] = h[row * d + lane + 32 * i]; s += v[i]; }
+        const float mu = warp_sum(s) / d;
+        float q = 0.f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) { v[i] -= mu; q += v[i] * v[i]; }
+        const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
+        float y[DPL];
+        float a = 0.f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) {
+            const int j = lane + 32 * i;
+            v[i] *= rstd;
+            y[i] = v[i] * P[mc.lnf_g + j] + P[mc.lnf_b + j];
+            hf[row * d + j] = y[i];
+            a = fmaf(y[i], P[mc.head_w + j], a);
+        }
+        a = warp_sum(a) + P[mc.head_b + t];
+        const float delta = free_t ? 0.5f * ga * ((float)b - 1.f / (1.f + expf(-a))) : 0.f;
+        if (lane == 0) dl[row] = delta;
+        float dyv[DPL];
+        float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) {
+            const int j = lane + 32 * i;
+            dyv[i] = delta * P[mc.head_w + j] + (t == n - 2 ? gp * P[mc.phase_w + sel * d + j] : 0.f);
+            const float dx = dyv[i] * P[mc.lnf_g + j];
+            m1 += dx;
+            m2 += dx * v[i];
+        }
+        m1 = warp_sum(m1) / d;
+        m2 = warp_sum(m2) / d;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) {
+            const int j = lane + 32 * i;
+            const float dx = dyv[i] * P[mc.lnf_g + j];
+            dh[row * d + j] = rstd * (dx - m1 - v[i] * m2);
+            dyo[row * d + j] = dyv[i];
+            gx[row * d + j] = dyv[i] * v[i];
+        }
+    }
+}
+
+// Attention backward per (sequence, head), dynamic shared memory.
+__global__ void __launch_bounds__(128)
+attention_bwd_kernel(const float* __restrict__ qkv, const float* __restrict__ dout, int T, int d,
+                     int dh, float* __restrict__ dqkv) {
+    extern __shared__ float sm[];
+    const int ld = dh + 1, lp = T + 1;
+    float* q = sm;
+    float* k = q + T * ld;
+    float* v = k + T * ld;
+    float* go = v + T * ld;
+    float* p = go + T * ld;
+    float* dp = p + T * lp;
+    const int64_t r = blockIdx.x;
+    const int hd = blockIdx.y;
+    const float scale = rsqrtf((float)dh);
+    for (int i = threadIdx.x; i < T * dh; i += blockDim.x) {
+        const int t = i / dh, j = i % dh;
+        const float* row = qkv + (r * T + t) * (int64_t)(3 * d);
+        q[t * ld + j] = row[hd * dh + j];
+        k[t * ld + j] = row[d + hd * dh + j];
+        v[t * ld + j] = row[2 * d + hd * dh + j];
+        go[t * ld + j] = dout[(r * T + t) * (int64_t)d + hd * dh + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int t = i / T, u = i % T;
+        float s = -INFINITY, g = 0.f;
+        if (u <= t) {
+            s = 0.f;
+            for (int j = 0; j < dh; ++j) { s = fmaf(q[t * ld + j], k[u * ld + j], s); g = fmaf(go[t * ld + j], v[u * ld + j], g); }
+            s *= scale;
+        }
+        p[t * lp + u] = s;
+        dp[t * lp + u] = g;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = warp; t < T; t += blockDim.x >> 5) {
+        float mx = -INFINITY;
+        for (int u = lane; u <= t; u += 32) mx = fmaxf(mx, p[t * lp + u]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        float s = 0.f;
+        for (int u = lane; u <= t; u += 32) { const float e = expf(p[t * lp + u] - mx); p[t * lp + u] = e; s += e; }
+        s = warp_sum(s);
+        const float inv = 1.f / s;
+        float pd = 0.f;
+        for (int u = lane; u <= t; u += 32) { p[t * lp + u] *= inv; pd += p[t * lp + u] * dp[t * lp + u]; }
+        pd = warp_sum(pd);
+        for (int u = lane; u <= t; u += 32) dp[t * lp + u] = p[t * lp + u] * (dp[t * lp + u] - pd);   // dS
+        for (int u = t + 1 + lane; u < T; u += 32) { p[t * lp + u] = 0.f; dp[t * lp + u] = 0.f; }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * dh; i += blockDim.x) {
+        const int t = i / dh, j = i % dh;
+        float dq = 0.f, dk = 0.f, dv = 0.f;
+        for (int u = 0; u < T; ++u) {
+            dq = fmaf(dp[t * lp + u], k[u * ld + j], dq);      // dS[t][u] k[u]
+            dk = fmaf(dp[u * lp + t], q[u * ld + j], dk);      // dS[u][t] q[u]
+            dv = fmaf(p[u * lp + t], go[u * ld + j], dv);      // P[u][t] dO[u]
+        }
+        float* row = dqkv + (r * T + t) * (int64_t)(3 * d);
+        row[hd * dh + j] = dq * scale;
+        row[d + hd * dh + j] = dk * scale;
+        row[2 * d + hd * dh + j] = dv;
+    }
+}
+
+// ---------------------------------------------------------------- deterministic reductions
+constexpr int CS_ROWS = 1024;
+__global__ void colsum_partial_kernel(const float* __restrict__ X, int64_t ld, int64_t M, int ncols,
+                                      float* __restrict__ part) {
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * CS_ROWS;
+    float s = 0.f;
+    if (c < ncols)
+        for (int64_t r = r0 + threadIdx.y; r < min(M, r0 + CS_ROWS); r += 8) s += X[r * ld + c];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < ncols) {
+        float t = 0.f;
+        for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+        part[(int64_t)blockIdx.y * ncols + c] = t;
+    }
+}
+
+__global__ void colsum_final_kernel(const float* __restrict__ part, int nchunks, int ncols, float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    float s = 0.f;
+    for (int i = 0; i < nchunks; ++i) s += part[(int64_t)i * ncols + c];
+    out[c] += s;
+}
+
+constexpr int OP_T = 32;
+template <class T_ACT>
+__global__ void __launch_bounds__(256)
+outer_partial_kernel(const float* __restrict__ delta, int64_t ld_d, const T_ACT* __restrict__ act,
+                     int64_t ld_a, int64_t M, int out_dim, int in_dim, int64_t rows_per_split,
+                     float* __restrict__ part) {
+    __shared__ float sd[OP_T][OP_T + 1];
+    __shared__ float sa[OP_T][OP_T + 1];
+    const int o0 = blockIdx.y * OP_T, i0 = blockIdx.x * OP_T;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t b_lo = (int64_t)blockIdx.z * rows_per_split;
+    const int64_t b_hi = min(M, b_lo + rows_per_split);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t b0 = b_lo; b0 < b_hi; b0 += OP_T) {
+        for (int rr = ty; rr < OP_T; rr += 8) {
+            const int64_t b = b0 + rr;
+            sd[rr][tx] = (b < b_hi && o0 + tx < out_dim) ? delta[b * ld_d + o0 + tx] : 0.f;
+            sa[rr][tx] = (b < b_hi && i0 + tx < in_dim) ? ldf(act + b * ld_a + i0 + tx) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < OP_T; ++rr) {
+            const float a = sa[rr][tx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(sd[rr][ty * 4 + q], a, acc[q]);
+        }
+        __syncthreads();
+    }
+    const int i = i0 + tx;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = o0 + ty * 4 + q;
+        if (o < out_dim && i < in_dim) part[((int64_t)blockIdx.z * out_dim + o) * in_dim + i] = acc[q];
+    }
+}
+
+__global__ void outer_final_kernel(const float* __restrict__ part, int nsplit, int64_t n, float* __restrict__ dW) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * n + i];
+        dW[i] += s;
+    }
+}
+
+// embeddings: dpos[t][j] += sum_r dh[r,t,j]; dtok[tok][j] += sum over rows with that token
+__global__ void embed_bwd_kernel(ModelConst mc, const uint64_t* __restrict__ bits, const float* __restrict__ dh,
+                                 int64_t R, float* __restrict__ grad) {
+    const int d = mc.hidden, n = mc.n;
+    const int64_t nt = (int64_t)n * d;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt + 3 * d; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nt) {
+            const int t = (int)(i / d), j = (int)(i % d);
+            float s = 0.f;
+            for (int64_t r = 0; r < R; ++r) s += dh[(r * n + t) * d + j];
+            grad[mc.pos_emb + i] += s;
+        } else {
+            const int tok = (int)((i - nt) / d), j = (int)((i - nt) % d);
+            float s = 0.f;
+            if (tok == 2) {
+                for (int64_t r = 0; r < R; ++r) s += dh[(r * n) * d + j];
+            } else {
+                for (int64_t r = 0; r < R; ++r) {
+                    const uint64_t x = bits[r];
+                    for (int t = 1; t < n; ++t)
+                        if ((int)((x >> mc.order[t - 1]) & 1ull) == tok) s += dh[(r * n + t) * d + j];
+                }
+            }
+            grad[mc.tok_emb + tok * d + j] += s;
+        }
+    }
+}
+
+inline int gs(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16)); }
+
+template <class F>
+int with_dpl_b(int d, F&& f) {
+    switch (d / 32) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        default: set_error("transformer d_model must be 32, 64, 128 or 256"); return NQS_ERR_UNSUPPORTED;
+    }
+}
+
+struct BwdBufs {
+    int64_t R, M, nsplit, part_elems;
+    float** Hin;     // L+1 x [M d]
+    float** Hmid;    // L
+    void** A1;       // L x [M d] (T_ACT)
+    float** QKV;     // L x [M 3d]
+    void** O;        // L x [M d] (T_ACT)
+    void** A2;       // L
+    float** MPRE;    // L x [M 4d]
+    void** MM;       // L x [M 4d] (T_ACT)
+    float *dH, *dHmid, *dS, *dBig, *dQKV, *GX, *HF, *DL, *DPH, *part, *Wr;
+};
+
+int64_t bwd_per_seq_floats(const ModelConst& mc) {
+    const int64_t n = mc.n, d = mc.hidden, L = mc.layers;
+    return n * (d * (L + 1) + L * (d + 3 * d + d + d + 4 * d + 4 * d + d) + 3 * d + 4 * d + 3 * d + 2 * d + 1) + 4;
+}
+
+void bwd_layout(Carver& c, const ModelConst& mc, int64_t R, BwdBufs& b, float** ptrs, void** vptrs) {
+    const int64_t n = mc.n, d = mc.hidden, L = mc.layers, M = R * n;
+    b.R = R; b.M = M;
+    b.Hin = ptrs; b.Hmid = ptrs + (L + 1); b.QKV = b.Hmid + L; b.MPRE = b.QKV + L;
+    b.A1 = vptrs; b.O = vptrs + L; b.A2 = b.O + L; b.MM = b.A2 + L;
+    for (int l = 0; l <= L; ++l) b.Hin[l] = c.take<float>(M * d);
+    for (int l = 0; l < L; ++l) {
+        b.Hmid[l] = c.take<float>(M * d);
+        b.A1[l] = c.take<float>(M * d);
+        b.QKV[l] = c.take<float>(M * 3 * d);
+        b.O[l] = c.take<float>(M * d);
+        b.A2[l] = c.take<float>(M * d);
+        b.MPRE[l] = c.take<float>(M * 4 * d);
+        b.MM[l] = c.take<float>(M * 4 * d);
+    }
+    b.dH = c.take<float>(M * d);
+    b.dHmid = c.take<float>(M * d);
+    b.dS = c.take<float>(M * d);
+    b.dBig = c.take<float>(M * 4 * d);
+    b.dQKV = c.take<float>(M * 3 * d);
+    b.GX = c.take<float>(M * d);
+    b.HF = c.take<float>(M * d);
+    b.DL = c.take<float>(M);
+    b.DPH = c.take<float>(R * 4);
+    b.nsplit = std::max<int64_t>(1, std::min<int64_t>(64, M / 512));
+    b.part_elems = std::max<int64_t>(b.nsplit * 4 * d * d, ((M + CS_ROWS - 1) / CS_ROWS) * 4 * d);
+    b.part = c.take<float>(b.part_elems);
+    b.Wr = c.take<float>(12 * d * d * L);
+}
+
+}  // namespace
+
+int64_t tf_bwd_seq_capacity(const ModelConst& mc) {
+    const int64_t per = bwd_per_seq_floats(mc) * 4;
+    int64_t R = 16;
+    while (R * 2 * per <= (512ll << 20) && R < 4096) R *= 2;
+    return R;
+}
+
+size_t tf_bwd_workspace(const ModelConst& mc, int64_t B) {
+    Carver c(nullptr);
+    float* ptrs[3 * TF_MAX_LAYERS + 2];
+    void* vptrs[4 * TF_MAX_LAYERS];
+    BwdBufs b;
+    bwd_layout(c, mc, std::max<int64_t>(1, std::min(B, tf_bwd_seq_capacity(mc))), b, ptrs, vptrs);
+    return c.used;
+}
+
+int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s) {
+    const int n = mc.n, d = mc.hidden, dh = d / mc.heads, L = mc.layers;
+    const bool bf = mc.precision == NQS_PREC_BF16;
+    float* ptrs[3 * TF_MAX_LAYERS + 2];
+    void* vptrs[4 * TF_MAX_LAYERS];
+    Carver c(ws);
+    BwdBufs b;
+    bwd_layout(c, mc, std::max<int64_t>(1, std::min(B, tf_bwd_seq_capacity(mc))), b, ptrs, vptrs);
+
+    // weights used by the GEMMs: the fp32 masters, or their bf16-rounded values (BF16 models)
+    const float* W[TF_MAX_LAYERS][4];
+    const int64_t wsz[4] = {3ll * d * d, 1ll * d * d, 4ll * d * d, 4ll * d * d};
+    {
+        int64_t off = 0;
+        for (int l = 0; l < L; ++l) {
+            const int64_t src[4] = {mc.wqkv[l], mc.wo[l], mc.w1[l], mc.w2[l]};
+            for (int q = 0; q < 4; ++q) {
+                if (bf) {
+                    round_bf16_kernel<<<gs(wsz[q]), 256, 0, s>>>(P + src[q], b.Wr + off, wsz[q]);
+                    NQS_LAUNCHED();
+                    W[l][q] = b.Wr + off;
+                    off += wsz[q];
+                } else {
+                    W[l][q] = P + src[q];
+                }
+            }
+        }
+    }
+
+    auto gemm_nt = [&](auto* A, const float* Wm, const float* bias, float* C, int64_t M, int N, int K,
+                       int epi) -> int {
+        using TA = std::remove_cv_t<std::remove_pointer_t<decltype(A)>>;
+        dim3 grid((unsigned)((N + SG_BN - 1) / SG_BN), (unsigned)((M + SG_BM - 1) / SG_BM));
+        if (epi == TF_EPI_STORE) sgemm_kernel<TA, false, TF_EPI_STORE, float><<<grid, 256, 0, s>>>(A, Wm, bias, C, M, N, K);
+        else sgemm_kernel<TA, false, TF_EPI_RESID, float><<<grid, 256, 0, s>>>(A, Wm, bias, C, M, N, K);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    };
+    auto gemm_nn = [&](const float* A, const float* Wm, float* C, int64_t M, int N, int K) -> int {
+        dim3 grid((unsigned)((N + SG_BN - 1) / SG_BN), (unsigned)((M + SG_BM - 1) / SG_BM));
+        sgemm_kernel<float, true, TF_EPI_STORE, float><<<grid, 256, 0, s>>>(A, Wm, nullptr, C, M, N, K);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    };
+    auto colsum = [&](const float* X, int64_t ld, int64_t M, int ncols, float* out) -> int {
+        const int nch = (int)((M + CS_ROWS - 1) / CS_ROWS);
+        colsum_partial_kernel<<<dim3((ncols + 31) / 32, nch), dim3(32, 8), 0, s>>>(X, ld, M, ncols, b.part);
+        NQS_LAUNCHED();
+        colsum_final_kernel<<<(ncols + 127) / 128, 128, 0, s>>>(b.part, nch, ncols, out);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    };
+    auto outer = [&](const float* delta, int64_t ld_d, const void* act, bool act_bf16, int64_t ld_a,
+                     int64_t M, int out_dim, int in_dim, float* dW) -> int {
+        const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(b.nsplit, b.part_elems / ((int64_t)out_dim * in_dim)));
+        const int64_t per = (M + ns - 1) / ns;
+        dim3 grid((unsigned)((in_dim + OP_T - 1) / OP_T), (unsigned)((out_dim + OP_T - 1) / OP_T), (unsigned)ns);
+        if (act_bf16) outer_partial_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(delta, ld_d, (const __nv_bfloat16*)act, ld_a, M, out_dim, in_dim, per, b.part);
+        else outer_partial_kernel<float><<<grid, 256, 0, s>>>(delta, ld_d, (const float*)act, ld_a, M, out_dim, in_dim, per, b.part);
+        NQS_LAUNCHED();
+        const int64_t nel = (int64_t)out_dim * in_dim;
+        outer_final_kernel<<<gs(nel), 256, 0, s>>>(b.part, (int)ns, nel, dW);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    };
+
+    return with_dpl_b(d, [&](auto dpl) -> int {
+        constexpr int DPL = decltype(dpl)::value;
+        const size_t att_smem = (size_t)(4 * n * (dh + 1) + 2 * n * (n + 1)) * sizeof(float);
+        if (att_smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(attention_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)att_smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+        }
+        for (int64_t lo = 0; lo < B; lo += b.R) {
+            const int64_t R = std::min(b.R, B - lo);
+            const int64_t M = R * n;
+            const uint64_t* xb = bits + lo;
+            // ---- forward with saved activations
+            embed_kernel<<<gs(M * d), 256, 0, s>>>(mc, P, xb, R, n, b.Hin[0]);
+            NQS_LAUNCHED();
+            auto ln_fwd = [&](const float* hsrc, const float* g, const float* bb, void* dst) -> int {
+                if (bf) layernorm_kernel<__nv_bfloat16, DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(hsrc, M, d, g, bb, (__nv_bfloat16*)dst);
+                else layernorm_kernel<float, DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(hsrc, M, d, g, bb, (float*)dst);
+                NQS_LAUNCHED();
+                return NQS_OK;
+            };
+            NQS_TRY(ln_fwd(b.Hin[0], P + mc.ln1_g[0], P + mc.ln1_b[0], b.A1[0]));
+            for (int l = 0; l < L; ++l) {
+                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.A1[l], W[l][TF_WQKV], P + mc.bqkv[l], b.QKV[l], M, 3 * d, d, TF_EPI_STORE));
+                else NQS_TRY(gemm_nt((const float*)b.A1[l], W[l][TF_WQKV], P + mc.bqkv[l], b.QKV[l], M, 3 * d, d, TF_EPI_STORE));
+                if (bf) attention_kernel<__nv_bfloat16><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.QKV[l], n, d, dh, (__nv_bfloat16*)b.O[l]);
+                else attention_kernel<float><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.QKV[l], n, d, dh, (float*)b.O[l]);
+                NQS_LAUNCHED();
+                NQS_CK(cudaMemcpyAsync(b.Hmid[l], b.Hin[l], M * d * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.O[l], W[l][TF_WO], P + mc.bo[l], b.Hmid[l], M, d, d, TF_EPI_RESID));
+                else NQS_TRY(gemm_nt((const float*)b.O[l], W[l][TF_WO], P + mc.bo[l], b.Hmid[l], M, d, d, TF_EPI_RESID));
+                NQS_TRY(ln_fwd(b.Hmid[l], P + mc.ln2_g[l], P + mc.ln2_b[l], b.A2[l]));
+                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.A2[l], W[l][TF_W1], P + mc.b1[l], b.MPRE[l], M, 4 * d, d, TF_EPI_STORE));
+                else NQS_TRY(gemm_nt((const float*)b.A2[l], W[l][TF_W1], P + mc.b1[l], b.MPRE[l], M, 4 * d, d, TF_EPI_STORE));
+                if (bf) gelu_fwd_kernel<__nv_bfloat16><<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], (__nv_bfloat16*)b.MM[l], M * 4 * d);
+                else gelu_fwd_kernel<float><<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], (float*)b.MM[l], M * 4 * d);
+                NQS_LAUNCHED();
+                NQS_CK(cudaMemcpyAsync(b.Hin[l + 1], b.Hmid[l], M * d * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.MM[l], W[l][TF_W2], P + mc.b2[l], b.Hin[l + 1], M, d, 4 * d, TF_EPI_RESID));
+                else NQS_TRY(gemm_nt((const float*)b.MM[l], W[l][TF_W2], P + mc.b2[l], b.Hin[l + 1], M, d, 4 * d, TF_EPI_RESID));
+                if (l + 1 < L) NQS_TRY(ln_fwd(b.Hin[l + 1], P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.A1[l + 1]));
+            }
+            // ---- heads and final LayerNorm
+            heads_bwd_kernel<DPL><<<(int)((R + 7) / 8), 256, 0, s>>>(mc, P, xb, b.Hin[L], R, g_abs + lo, g_phase + lo,
+                                                                      b.dH, b.dS, b.GX, b.HF, b.DL, b.DPH);
+            NQS_LAUNCHED();
+            NQS_TRY(outer(b.DL, 1, b.HF, false, d, M, 1, d, grad + mc.head_w));
+            NQS_TRY(colsum(b.DL, n, R, n, grad + mc.head_b));
+            NQS_TRY(outer(b.DPH, 4, b.HF + (int64_t)(n - 2) * d, false, (int64_t)n * d, R, 4, d, grad + mc.phase_w));
+            NQS_TRY(colsum(b.DPH, 4, R, 4, grad + mc.phase_b));
+            NQS_TRY(colsum(b.GX, d, M, d, grad + mc.lnf_g));
+            NQS_TRY(colsum(b.dS, d, M, d, grad + mc.lnf_b));
+            // ---- blocks, last to first
+            for (int l = L - 1; l >= 0; --l) {
+                // MLP: Hin[l+1] = Hmid + gelu(A2 W1^T + b1) W2^T + b2
+                NQS_TRY(colsum(b.dH, d, M, d, grad + mc.b2[l]));
+                NQS_TRY(outer(b.dH, d, b.MM[l], bf, 4 * d, M, d, 4 * d, grad + mc.w2[l]));
+                NQS_TRY(gemm_nn(b.dH, W[l][TF_W2], b.dBig, M, 4 * d, d));
+                gelu_bwd_kernel<<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], b.dBig, M * 4 * d);
+                NQS_LAUNCHED();
+                NQS_TRY(colsum(b.dBig, 4 * d, M, 4 * d, grad + mc.b1[l]));
+                NQS_TRY(outer(b.dBig, 4 * d, b.A2[l], bf, d, M, 4 * d, d, grad + mc.w1[l]));
+                NQS_TRY(gemm_nn(b.dBig, W[l][TF_W1], b.dS, M, d, 4 * d));
+                ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hmid[l], P + mc.ln2_g[l], b.dS, b.dH, b.dHmid, b.GX, M, d);
+                NQS_LAUNCHED();
+                NQS_TRY(colsum(b.GX, d, M, d, grad + mc.ln2_g[l]));
+                NQS_TRY(colsum(b.dS, d, M, d, grad + mc.ln2_b[l]));
+                // attention: Hmid = Hin + attn(A1 Wqkv^T + bqkv) Wo^T + bo
+                NQS_TRY(colsum(b.dHmid, d, M, d, grad + mc.bo[l]));
+                NQS_TRY(outer(b.dHmid, d, b.O[l], bf, d, M, d, d, grad + mc.wo[l]));
+                NQS_TRY(gemm_nn(b.dHmid, W[l][TF_WO], b.dS, M, d, d));
+                attention_bwd_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dS, n, d, dh, b.dQKV);
+                NQS_LAUNCHED();
+                NQS_TRY(colsum(b.dQKV, 3 * d, M, 3 * d, grad + mc.bqkv[l]));
+                NQS_TRY(outer(b.dQKV, 3 * d, b.A1[l], bf, d, M, 3 * d, d, grad + mc.wqkv[l]));
+                NQS_TRY(gemm_nn(b.dQKV, W[l][TF_WQKV], b.dS, M, d, 3 * d));
+                ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hin[l], P + mc.ln1_g[l], b.dS, b.dHmid, b.dH, b.GX, M, d);
+                NQS_LAUNCHED();
+                NQS_TRY(colsum(b.GX, d, M, d, grad + mc.ln1_g[l]));
+                NQS_TRY(colsum(b.dS, d, M, d, grad + mc.ln1_b[l]));
+            }
+            embed_bwd_kernel<<<gs((int64_t)(n + 3) * d), 256, 0, s>>>(mc, xb, b.dH, R, grad);
+            NQS_LAUNCHED();
+        }
+        return NQS_OK;
+    });
+}
+
+}  // namespace nqs
