@@ -22,7 +22,9 @@ Section 4 Sampling, is order[t] = n-1-t).  Conventions (readings of the paper):
 
 quant="bf16" emulates the tensor-core path: the four block GEMMs take bf16-rounded (RNE)
 weights and bf16-rounded input activations (LayerNorm outputs, attention output, GELU output);
-rounding is treated as identity by autograd (straight-through).
+quant="bf16x2" keeps the bf16 weights but represents each GEMM input activation as the sum of
+two bf16 numbers hi = bf16(a), lo = bf16(a - hi) (the compensated tensor-core form).  Rounding
+is treated as identity by autograd (straight-through).
 """
 import math
 
@@ -39,9 +41,13 @@ def bf16_round(t: torch.Tensor) -> torch.Tensor:
 
 
 def _q(t, on):
+    """Straight-through bf16 rounding of a GEMM operand (on: False, True or "x2")."""
     if not on:
         return t
-    return t + (bf16_round(t.detach()) - t.detach())
+    d = t.detach()
+    hi = bf16_round(d)
+    r = hi + bf16_round(d - hi) if on == "x2" else hi
+    return t + (r - d)
 
 
 def made_masks(n: int, hidden: int, layers: int):
@@ -59,7 +65,7 @@ class Model:
         self.arch, self.n, self.n_up, self.n_dn = arch, int(n), int(n_up), int(n_dn)
         self.order = np.asarray(order, dtype=np.int64)
         self.hidden, self.layers, self.heads = int(hidden), int(layers), int(heads)
-        self.quant = quant == "bf16"
+        self.quant = {None: False, "bf16": True, "bf16x2": "x2"}[quant]
         self.p = {k: torch.tensor(np.asarray(v, dtype=np.float64), requires_grad=requires_grad)
                   for k, v in params.items()}
         if arch == "made":
@@ -106,7 +112,8 @@ class Model:
     def _transformer(self, X):
         P, n, d, H = self.p, self.n, self.hidden, self.heads
         dh = d // H
-        qz = self.quant
+        qz = self.quant                 # activations
+        qw = bool(self.quant)           # weights: bf16 in both quantised forms
         B = X.shape[0]
         tok = torch.cat([torch.full((B, 1), 2, dtype=torch.long), X[:, : n - 1].long()], dim=1)
         h = P["tok_emb"][tok] + P["pos_emb"][None, :, :]
@@ -114,7 +121,7 @@ class Model:
         for l in range(self.layers):
             pre = f"blk{l}."
             a = _q(self._ln(h, P[pre + "ln1_g"], P[pre + "ln1_b"]), qz)
-            qkv = a @ _q(P[pre + "wqkv"], qz).T + P[pre + "bqkv"]
+            qkv = a @ _q(P[pre + "wqkv"], qw).T + P[pre + "bqkv"]
             q, k, v = qkv.split(d, dim=-1)
             q = q.reshape(B, n, H, dh).transpose(1, 2)
             k = k.reshape(B, n, H, dh).transpose(1, 2)
@@ -123,10 +130,10 @@ class Model:
             s = s.masked_fill(~causal, float("-inf"))
             att = torch.softmax(s, dim=-1)
             o = (att @ v).transpose(1, 2).reshape(B, n, d)
-            h = h + _q(o, qz) @ _q(P[pre + "wo"], qz).T + P[pre + "bo"]
+            h = h + _q(o, qz) @ _q(P[pre + "wo"], qw).T + P[pre + "bo"]
             a2 = _q(self._ln(h, P[pre + "ln2_g"], P[pre + "ln2_b"]), qz)
-            m = self._gelu(a2 @ _q(P[pre + "w1"], qz).T + P[pre + "b1"])
-            h = h + _q(m, qz) @ _q(P[pre + "w2"], qz).T + P[pre + "b2"]
+            m = self._gelu(a2 @ _q(P[pre + "w1"], qw).T + P[pre + "b1"])
+            h = h + _q(m, qz) @ _q(P[pre + "w2"], qw).T + P[pre + "b2"]
         hf = self._ln(h, P["lnf_g"], P["lnf_b"])
         logits = hf @ P["head_w"] + P["head_b"]
         phase_out = hf[:, n - 2, :] @ P["phase_w"].T + P["phase_b"]

@@ -36,7 +36,7 @@ EXPORTED = [
     "nqs_model_bind_params", "nqs_model_destroy", "nqs_workspace_size", "nqs_sample",
     "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward",
     "nqs_energy_stats", "nqs_adam_step", "nqs_strerror", "nqs_last_error", "nqs_profile_enable",
-    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc",
+    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16",
 ]
 
 
@@ -79,6 +79,7 @@ _sig = {
     "nqs_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
     "nqs_launch_count": [],
     "nqs_local_energy_noalloc": [_P, _P, _P, _I64, _P, _P],
+    "nqs_gemm_bf16": [_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -318,6 +319,15 @@ def nqs_local_energy_noalloc(ham, model, bits, out=None, stream=None):
     _check(_lib.nqs_local_energy_noalloc(ham.handle, model.handle, _ptr(bits), B, _ptr(out),
                                          _stream(stream)), "nqs_local_energy_noalloc")
     return out
+
+
+def nqs_gemm_bf16(A, W, bias, C, epilogue=0, stream=None):
+    """Diagnostic: C = A W^T + bias on the tensor cores (A [M,K], W [N,K] bf16; see nqs.h)."""
+    M, K = A.shape
+    N = W.shape[0]
+    _check(_lib.nqs_gemm_bf16(_ptr(A), _ptr(W), _ptr(bias), _ptr(C), M, N, K, int(epilogue),
+                              _stream(stream)), "nqs_gemm_bf16")
+    return C
 
 
 def nqs_logpsi_backward(model, bits, g_log_abs, g_phase, grad_accum, ws=None, stream=None):

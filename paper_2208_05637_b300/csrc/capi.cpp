@@ -577,6 +577,7 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
     int64_t U = 0;
     NQS_CK(cudaMemcpyAsync(&U, b.U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     NQS_CK(cudaStreamSynchronize(s));
+    if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
     *n_unique = U;
     if (U > capacity) {
         set_error("sample capacity " + std::to_string(capacity) + " < unique count " + std::to_string(U));
@@ -605,7 +606,12 @@ int nqs_logpsi(nqs_model_t m, const uint64_t* bits, int64_t B, float* la, float*
         tf_layout(c, m->mc, std::max<int64_t>(1, std::min(B, tf_seq_capacity(m->mc))), tb);
         TfWeights w;
         NQS_TRY(tf_weights(m, w, s));
-        return tf_logpsi(m->mc, m->d_params, w, bits, B, la, ph, tb, s);
+        NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, la, ph, tb, s));
+        if (m->mc.precision == NQS_PREC_BF16) {   // bounded-wait status of the tensor-core GEMMs
+            NQS_CK(cudaStreamSynchronize(s));
+            return tc_status_take();
+        }
+        return NQS_OK;
     }
     (void)ws; (void)ws_bytes;
     return launch_logpsi_rows(m->mc, m->d_params, bits, B, la, ph, (cudaStream_t)stream);
@@ -685,6 +691,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
             int64_t rows = 0;
             NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             NQS_CK(cudaStreamSynchronize(s));
+            if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
             for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
                 const int64_t R = std::min(e.tf.R, rows - r0);
                 NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s));

@@ -189,7 +189,7 @@ int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t
                             int64_t B, const float* g_abs, float* grad, cudaStream_t s);
 
 // transformer (transformer.cu, tc_gemm.cu)
-enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3 };
+enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3, TF_EPI_GELU2 = 4 };
 enum { TF_WQKV = 0, TF_WO = 1, TF_W1 = 2, TF_W2 = 3 };
 struct TfBufs {
     int64_t R;            // sequences per pass
@@ -235,6 +235,8 @@ int64_t tf_bwd_seq_capacity(const ModelConst& mc);
 size_t tf_bwd_workspace(const ModelConst& mc, int64_t B);
 int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
                 const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
+// status of the tensor-core kernels' bounded waits; synchronous, clears the flag
+int tc_status_take();
 struct TfCtx {
     const TfWeights* w;
     TfBufs* b;

@@ -38,10 +38,10 @@ __global__ void embed_kernel(ModelConst mc, const float* __restrict__ P, const u
     }
 }
 
-template <class T_ACT>
-__global__ void gelu_fwd_kernel(const float* __restrict__ x, T_ACT* __restrict__ y, int64_t n) {
+template <int MODE>
+__global__ void gelu_fwd_kernel(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        store_act(y + i, gelu_tanh(x[i]));
+        store_mode<MODE>(y + i, 0, 1, 0, gelu_tanh(x[i]));
 }
 
 __global__ void gelu_bwd_kernel(const float* __restrict__ x, float* __restrict__ g, int64_t n) {
@@ -412,8 +412,22 @@ size_t tf_bwd_workspace(const ModelConst& mc, int64_t B) {
     return c.used;
 }
 
+template <int MODE>
+int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                     const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
+
 int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
                 const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s) {
+    if (mc.precision != NQS_PREC_BF16) return tf_backward_mode<ACT_F32>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
+    if (mc.compensated) return tf_backward_mode<ACT_F32_Q2>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
+    return tf_backward_mode<ACT_F32_Q1>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
+}
+
+// MODE: how the recomputed forward stores GEMM input activations (fp32 values equal to the
+// ones the forward of this precision feeds its GEMMs).
+template <int MODE>
+int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
+                     const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s) {
     const int n = mc.n, d = mc.hidden, dh = d / mc.heads, L = mc.layers;
     const bool bf = mc.precision == NQS_PREC_BF16;
     float* ptrs[3 * TF_MAX_LAYERS + 2];
@@ -494,30 +508,23 @@ int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int6
             embed_kernel<<<gs(M * d), 256, 0, s>>>(mc, P, xb, R, n, b.Hin[0]);
             NQS_LAUNCHED();
             auto ln_fwd = [&](const float* hsrc, const float* g, const float* bb, void* dst) -> int {
-                if (bf) layernorm_kernel<__nv_bfloat16, DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(hsrc, M, d, g, bb, (__nv_bfloat16*)dst);
-                else layernorm_kernel<float, DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(hsrc, M, d, g, bb, (float*)dst);
+                layernorm_kernel<MODE, DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(hsrc, M, d, g, bb, dst);
                 NQS_LAUNCHED();
                 return NQS_OK;
             };
             NQS_TRY(ln_fwd(b.Hin[0], P + mc.ln1_g[0], P + mc.ln1_b[0], b.A1[0]));
             for (int l = 0; l < L; ++l) {
-                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.A1[l], W[l][TF_WQKV], P + mc.bqkv[l], b.QKV[l], M, 3 * d, d, TF_EPI_STORE));
-                else NQS_TRY(gemm_nt((const float*)b.A1[l], W[l][TF_WQKV], P + mc.bqkv[l], b.QKV[l], M, 3 * d, d, TF_EPI_STORE));
-                if (bf) attention_kernel<__nv_bfloat16><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.QKV[l], n, d, dh, (__nv_bfloat16*)b.O[l]);
-                else attention_kernel<float><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.QKV[l], n, d, dh, (float*)b.O[l]);
+                NQS_TRY(gemm_nt((const float*)b.A1[l], W[l][TF_WQKV], P + mc.bqkv[l], b.QKV[l], M, 3 * d, d, TF_EPI_STORE));
+                attention_kernel<MODE><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.QKV[l], n, d, dh, b.O[l]);
                 NQS_LAUNCHED();
                 NQS_CK(cudaMemcpyAsync(b.Hmid[l], b.Hin[l], M * d * sizeof(float), cudaMemcpyDeviceToDevice, s));
-                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.O[l], W[l][TF_WO], P + mc.bo[l], b.Hmid[l], M, d, d, TF_EPI_RESID));
-                else NQS_TRY(gemm_nt((const float*)b.O[l], W[l][TF_WO], P + mc.bo[l], b.Hmid[l], M, d, d, TF_EPI_RESID));
+                NQS_TRY(gemm_nt((const float*)b.O[l], W[l][TF_WO], P + mc.bo[l], b.Hmid[l], M, d, d, TF_EPI_RESID));
                 NQS_TRY(ln_fwd(b.Hmid[l], P + mc.ln2_g[l], P + mc.ln2_b[l], b.A2[l]));
-                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.A2[l], W[l][TF_W1], P + mc.b1[l], b.MPRE[l], M, 4 * d, d, TF_EPI_STORE));
-                else NQS_TRY(gemm_nt((const float*)b.A2[l], W[l][TF_W1], P + mc.b1[l], b.MPRE[l], M, 4 * d, d, TF_EPI_STORE));
-                if (bf) gelu_fwd_kernel<__nv_bfloat16><<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], (__nv_bfloat16*)b.MM[l], M * 4 * d);
-                else gelu_fwd_kernel<float><<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], (float*)b.MM[l], M * 4 * d);
+                NQS_TRY(gemm_nt((const float*)b.A2[l], W[l][TF_W1], P + mc.b1[l], b.MPRE[l], M, 4 * d, d, TF_EPI_STORE));
+                gelu_fwd_kernel<MODE><<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], (float*)b.MM[l], M * 4 * d);
                 NQS_LAUNCHED();
                 NQS_CK(cudaMemcpyAsync(b.Hin[l + 1], b.Hmid[l], M * d * sizeof(float), cudaMemcpyDeviceToDevice, s));
-                if (bf) NQS_TRY(gemm_nt((const __nv_bfloat16*)b.MM[l], W[l][TF_W2], P + mc.b2[l], b.Hin[l + 1], M, d, 4 * d, TF_EPI_RESID));
-                else NQS_TRY(gemm_nt((const float*)b.MM[l], W[l][TF_W2], P + mc.b2[l], b.Hin[l + 1], M, d, 4 * d, TF_EPI_RESID));
+                NQS_TRY(gemm_nt((const float*)b.MM[l], W[l][TF_W2], P + mc.b2[l], b.Hin[l + 1], M, d, 4 * d, TF_EPI_RESID));
                 if (l + 1 < L) NQS_TRY(ln_fwd(b.Hin[l + 1], P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.A1[l + 1]));
             }
             // ---- heads and final LayerNorm
@@ -534,12 +541,12 @@ int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int6
             for (int l = L - 1; l >= 0; --l) {
                 // MLP: Hin[l+1] = Hmid + gelu(A2 W1^T + b1) W2^T + b2
                 NQS_TRY(colsum(b.dH, d, M, d, grad + mc.b2[l]));
-                NQS_TRY(outer(b.dH, d, b.MM[l], bf, 4 * d, M, d, 4 * d, grad + mc.w2[l]));
+                NQS_TRY(outer(b.dH, d, b.MM[l], false, 4 * d, M, d, 4 * d, grad + mc.w2[l]));
                 NQS_TRY(gemm_nn(b.dH, W[l][TF_W2], b.dBig, M, 4 * d, d));
                 gelu_bwd_kernel<<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], b.dBig, M * 4 * d);
                 NQS_LAUNCHED();
                 NQS_TRY(colsum(b.dBig, 4 * d, M, 4 * d, grad + mc.b1[l]));
-                NQS_TRY(outer(b.dBig, 4 * d, b.A2[l], bf, d, M, 4 * d, d, grad + mc.w1[l]));
+                NQS_TRY(outer(b.dBig, 4 * d, b.A2[l], false, d, M, 4 * d, d, grad + mc.w1[l]));
                 NQS_TRY(gemm_nn(b.dBig, W[l][TF_W1], b.dS, M, d, 4 * d));
                 ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hmid[l], P + mc.ln2_g[l], b.dS, b.dH, b.dHmid, b.GX, M, d);
                 NQS_LAUNCHED();
@@ -547,12 +554,12 @@ int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int6
                 NQS_TRY(colsum(b.dS, d, M, d, grad + mc.ln2_b[l]));
                 // attention: Hmid = Hin + attn(A1 Wqkv^T + bqkv) Wo^T + bo
                 NQS_TRY(colsum(b.dHmid, d, M, d, grad + mc.bo[l]));
-                NQS_TRY(outer(b.dHmid, d, b.O[l], bf, d, M, d, d, grad + mc.wo[l]));
+                NQS_TRY(outer(b.dHmid, d, b.O[l], false, d, M, d, d, grad + mc.wo[l]));
                 NQS_TRY(gemm_nn(b.dHmid, W[l][TF_WO], b.dS, M, d, d));
                 attention_bwd_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dS, n, d, dh, b.dQKV);
                 NQS_LAUNCHED();
                 NQS_TRY(colsum(b.dQKV, 3 * d, M, 3 * d, grad + mc.bqkv[l]));
-                NQS_TRY(outer(b.dQKV, 3 * d, b.A1[l], bf, d, M, 3 * d, d, grad + mc.wqkv[l]));
+                NQS_TRY(outer(b.dQKV, 3 * d, b.A1[l], false, d, M, 3 * d, d, grad + mc.wqkv[l]));
                 NQS_TRY(gemm_nn(b.dQKV, W[l][TF_WQKV], b.dS, M, d, 3 * d));
                 ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hin[l], P + mc.ln1_g[l], b.dS, b.dHmid, b.dH, b.GX, M, d);
                 NQS_LAUNCHED();

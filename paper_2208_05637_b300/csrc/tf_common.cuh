@@ -39,12 +39,42 @@ __device__ __forceinline__ void store_act<float>(float* p, float v) { *p = v; }
 template <>
 __device__ __forceinline__ void store_act<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
+// Storage of a GEMM input activation (row `row` of a matrix of `width` columns):
+//   ACT_F32     fp32
+//   ACT_BF16    bf16 (round to nearest even)
+//   ACT_BF16X2  two bf16 numbers hi = bf16(v), lo = bf16(v - hi): row stride 2*width, hi in
+//               columns [0, width), lo in [width, 2*width) -- the compensated tensor-core form
+//   ACT_F32_Q1  fp32 holding bf16(v)            (backward recompute of ACT_BF16 models)
+//   ACT_F32_Q2  fp32 holding hi + lo            (backward recompute of ACT_BF16X2 models)
+enum { ACT_F32 = 0, ACT_BF16 = 1, ACT_BF16X2 = 2, ACT_F32_Q1 = 3, ACT_F32_Q2 = 4 };
+
+template <int MODE>
+__device__ __forceinline__ void store_mode(void* base, int64_t row, int width, int col, float v) {
+    if (MODE == ACT_F32) {
+        reinterpret_cast<float*>(base)[row * width + col] = v;
+    } else if (MODE == ACT_BF16) {
+        reinterpret_cast<__nv_bfloat16*>(base)[row * width + col] = __float2bfloat16_rn(v);
+    } else if (MODE == ACT_BF16X2) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(base) + row * 2 * width;
+        b[col] = hi;
+        b[width + col] = lo;
+    } else if (MODE == ACT_F32_Q1) {
+        reinterpret_cast<float*>(base)[row * width + col] = __bfloat162float(__float2bfloat16_rn(v));
+    } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const float h = __bfloat162float(hi);
+        reinterpret_cast<float*>(base)[row * width + col] = h + __bfloat162float(__float2bfloat16_rn(v - h));
+    }
+}
+
 // ---------------------------------------------------------------- embedding + first LayerNorm
 // One warp per row (sequence r, position t).  Writes h (fp32) and a = LN1_0(h) (T_ACT).
-template <class T_ACT, int DPL>   // DPL = d / 32 values per lane
+template <int MODE, int DPL>   // DPL = d / 32 values per lane
 __global__ void __launch_bounds__(256)
 embed_ln_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
-                int64_t R, int T, float* __restrict__ h, T_ACT* __restrict__ a) {
+                int64_t R, int T, float* __restrict__ h, void* __restrict__ a) {
     const int d = mc.hidden;
     const int lane = threadIdx.x & 31;
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -69,15 +99,15 @@ embed_ln_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __re
     for (int i = 0; i < DPL; ++i) {
         const int j = lane + 32 * i;
         h[row * d + j] = v[i];
-        store_act(a + row * d + j, (v[i] - mu) * rstd * P[mc.ln1_g[0] + j] + P[mc.ln1_b[0] + j]);
+        store_mode<MODE>(a, row, d, j, (v[i] - mu) * rstd * P[mc.ln1_g[0] + j] + P[mc.ln1_b[0] + j]);
     }
 }
 
 // LayerNorm of h rows into a (T_ACT), one warp per row.
-template <class T_ACT, int DPL>
+template <int MODE, int DPL>
 __global__ void __launch_bounds__(256)
 layernorm_kernel(const float* __restrict__ h, int64_t M, int d, const float* __restrict__ g,
-                 const float* __restrict__ b, T_ACT* __restrict__ a) {
+                 const float* __restrict__ b, void* __restrict__ a) {
     const int lane = threadIdx.x & 31;
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= M) return;
@@ -93,7 +123,7 @@ layernorm_kernel(const float* __restrict__ h, int64_t M, int d, const float* __r
 #pragma unroll
     for (int i = 0; i < DPL; ++i) {
         const int j = lane + 32 * i;
-        store_act(a + row * d + j, (v[i] - mu) * rstd * g[j] + b[j]);
+        store_mode<MODE>(a, row, d, j, (v[i] - mu) * rstd * g[j] + b[j]);
     }
 }
 
@@ -163,9 +193,9 @@ sgemm_kernel(const T_A* __restrict__ A, const float* __restrict__ W, const float
 // ---------------------------------------------------------------- causal attention
 // One CTA per (sequence, head): scores S = Q K^T / sqrt(dh) with the causal mask, row softmax,
 // O = P V.  qkv rows hold [q | k | v] (3d floats).  T <= 64, dh in {16, 32}.
-template <class T_ACT>
+template <int MODE>
 __global__ void __launch_bounds__(128)
-attention_kernel(const float* __restrict__ qkv, int T, int d, int dh, T_ACT* __restrict__ o) {
+attention_kernel(const float* __restrict__ qkv, int T, int d, int dh, void* __restrict__ o) {
     __shared__ float q[64][33], k[64][33], v[64][33];
     __shared__ float p[64][65];
     const int64_t r = blockIdx.x;
@@ -207,7 +237,7 @@ attention_kernel(const float* __restrict__ qkv, int T, int d, int dh, T_ACT* __r
         const int t = i / dh, j = i % dh;
         float acc = 0.f;
         for (int u = 0; u <= t; ++u) acc = fmaf(p[t][u], v[u][j], acc);
-        store_act(o + (r * T + t) * (int64_t)d + hd * dh + j, acc);
+        store_mode<MODE>(o, r * T + t, d, hd * dh + j, acc);
     }
 }
 

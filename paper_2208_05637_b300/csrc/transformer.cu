@@ -193,10 +193,18 @@ segment_sum_kernel(const int64_t* __restrict__ seg, int64_t seg_stride, int64_t 
     }
 }
 
-// fp32 master weights -> bf16 working copies of the four block GEMM matrices
-__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = __float2bfloat16_rn(src[i]);
+// fp32 master weights W[N][K] -> bf16 working copies; with dup the copy is [W | W] of shape
+// [N][2K], the B operand of the compensated GEMM [A_hi | A_lo] . [W | W]^T.
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t N,
+                               int K, int dup) {
+    const int KK = dup ? 2 * K : K;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N * K; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = i / K;
+        const int k = (int)(i % K);
+        const __nv_bfloat16 v = __float2bfloat16_rn(src[i]);
+        dst[n * KK + k] = v;
+        if (dup) dst[n * KK + K + k] = v;
+    }
 }
 
 inline int blocks_for(int64_t rows, int per) { return (int)((rows + per - 1) / per); }
@@ -237,9 +245,12 @@ void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b) {
 
 int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, const void* A,
             void* C, int64_t M, int N, int K, int epi, const float* bias, cudaStream_t s) {
-    if (mc.precision == NQS_PREC_BF16)
-        return tc_gemm_bf16((const __nv_bfloat16*)A, w.bf16 + w.bf16_off[layer][which], bias, C,
-                            M, N, K, epi, s);
+    if (mc.precision == NQS_PREC_BF16) {
+        // compensated form: A = [A_hi | A_lo] and B = [W | W], so K doubles
+        const bool split = mc.compensated != 0;
+        const int e = (epi == TF_EPI_GELU && split) ? TF_EPI_GELU2 : epi;
+        return tc_gemm_bf16(A, w.bf16 + w.bf16_off[layer][which], bias, C, M, N, split ? 2 * K : K, e, s);
+    }
     const float* W = w.fp32 + w.fp32_off[layer][which];
     dim3 grid((unsigned)((N + SG_BN - 1) / SG_BN), (unsigned)((M + SG_BM - 1) / SG_BM));
     const float* Af = (const float*)A;
@@ -265,16 +276,18 @@ int tf_prepare_weights(const ModelConst& mc, const float* P, TfWeights& w, cudaS
     if (mc.precision != NQS_PREC_BF16) return NQS_OK;
     if (!w.bf16) { set_error("bf16 weight buffer missing"); return NQS_ERR_INVALID_ARG; }
     const int64_t d = mc.hidden;
+    const int dup = mc.compensated ? 1 : 0;
     int64_t off = 0;
-    const int64_t sizes[4] = {3 * d * d, d * d, 4 * d * d, 4 * d * d};
+    const int64_t rows[4] = {3 * d, d, 4 * d, d}, cols[4] = {d, d, d, 4 * d};
     for (int l = 0; l < mc.layers; ++l) {
         for (int q = 0; q < 4; ++q) {
             w.bf16_off[l][q] = off;
-            const int64_t n = sizes[q];
+            const int64_t n = rows[q] * cols[q];
             const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
-            to_bf16_kernel<<<grid, 256, 0, s>>>(P + w.fp32_off[l][q], reinterpret_cast<__nv_bfloat16*>(w.bf16) + off, n);
+            to_bf16_kernel<<<grid, 256, 0, s>>>(P + w.fp32_off[l][q], reinterpret_cast<__nv_bfloat16*>(w.bf16) + off,
+                                                rows[q], (int)cols[q], dup);
             NQS_LAUNCHED();
-            off += (n + 127) & ~int64_t(127);   // 256-byte aligned matrices
+            off += ((n << dup) + 127) & ~int64_t(127);   // 256-byte aligned matrices
         }
     }
     return NQS_OK;
@@ -282,25 +295,24 @@ int tf_prepare_weights(const ModelConst& mc, const float* P, TfWeights& w, cudaS
 
 int64_t tf_bf16_weight_elems(const ModelConst& mc) {
     const int64_t d = mc.hidden;
+    const int dup = mc.compensated ? 1 : 0;
     int64_t total = 0;
     const int64_t sizes[4] = {3 * d * d, d * d, 4 * d * d, 4 * d * d};
     for (int l = 0; l < mc.layers; ++l)
-        for (int q = 0; q < 4; ++q) total += (sizes[q] + 127) & ~int64_t(127);
+        for (int q = 0; q < 4; ++q) total += ((sizes[q] << dup) + 127) & ~int64_t(127);
     return total;
 }
 
 // Forward of R sequences over their first T positions, leaving the final residual stream in
 // b.h.  `bits` are the R configurations.
-int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
-               int64_t R, int T, TfBufs& b, cudaStream_t s) {
+template <int MODE>
+static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
+                           int64_t R, int T, TfBufs& b, cudaStream_t s) {
     const int d = mc.hidden, dh = d / mc.heads;
     const int64_t M = R * T;
-    const bool bf = mc.precision == NQS_PREC_BF16;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
-        const int rows_per_cta = 8;
-        if (bf) embed_ln_kernel<__nv_bfloat16, DPL><<<blocks_for(M, rows_per_cta), 256, 0, s>>>(mc, P, bits, R, T, b.h, (__nv_bfloat16*)b.a);
-        else embed_ln_kernel<float, DPL><<<blocks_for(M, rows_per_cta), 256, 0, s>>>(mc, P, bits, R, T, b.h, b.a);
+        embed_ln_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(mc, P, bits, R, T, b.h, b.a);
         NQS_LAUNCHED();
         for (int l = 0; l < mc.layers; ++l) {
             {
@@ -309,17 +321,14 @@ int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const u
             }
             {
                 ProfScope ps("tf_attention", s);
-                dim3 g((unsigned)R, (unsigned)mc.heads);
-                if (bf) attention_kernel<__nv_bfloat16><<<g, 128, 0, s>>>(b.qkv, T, d, dh, (__nv_bfloat16*)b.o);
-                else attention_kernel<float><<<g, 128, 0, s>>>(b.qkv, T, d, dh, b.o);
+                attention_kernel<MODE><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.qkv, T, d, dh, b.o);
                 NQS_LAUNCHED();
             }
             {
                 ProfScope ps("tf_gemm", s);
                 NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
             }
-            if (bf) layernorm_kernel<__nv_bfloat16, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], (__nv_bfloat16*)b.a);
-            else layernorm_kernel<float, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
+            layernorm_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
             NQS_LAUNCHED();
             {
                 ProfScope ps("tf_gemm", s);
@@ -327,13 +336,21 @@ int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const u
                 NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
             }
             if (l + 1 < mc.layers) {
-                if (bf) layernorm_kernel<__nv_bfloat16, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], (__nv_bfloat16*)b.a);
-                else layernorm_kernel<float, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
+                layernorm_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
                 NQS_LAUNCHED();
             }
         }
         return NQS_OK;
     });
+}
+
+// Forward of R sequences over their first T positions, leaving the final residual stream in
+// b.h.  `bits` are the R configurations.
+int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
+               int64_t R, int T, TfBufs& b, cudaStream_t s) {
+    if (mc.precision != NQS_PREC_BF16) return tf_forward_mode<ACT_F32>(mc, P, w, bits, R, T, b, s);
+    if (mc.compensated) return tf_forward_mode<ACT_BF16X2>(mc, P, w, bits, R, T, b, s);
+    return tf_forward_mode<ACT_BF16>(mc, P, w, bits, R, T, b, s);
 }
 
 int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t R, int T,

@@ -114,3 +114,17 @@ def test_sampling_conditionals_respect_constraint():
                 if b:
                     bits |= np.uint64(1) << np.uint64(model.order[k])
             assert in_sector(bits, model.n, model.n_up, model.n_dn)[0]
+
+
+def test_bf16x2_split_is_a_pair_of_bf16_within_2_to_minus_16():
+    # the compensated form represents a as hi + lo with hi = bf16(a), lo = bf16(a - hi): both
+    # bf16 numbers, and |a - (hi + lo)| <= 2^-16 |a| (8 + 8 significant bits, two roundings)
+    from oracle.models import _q
+    rng = np.random.default_rng(11)
+    a = torch.tensor(rng.standard_normal(50000) * 10 ** rng.uniform(-3, 3, 50000))
+    r = _q(a, "x2")
+    hi = bf16_round(a)
+    lo = r - hi
+    assert torch.equal(bf16_round(hi), hi) and torch.equal(bf16_round(lo), lo)
+    assert torch.all((r - a).abs() <= 2.0 ** -16 * a.abs())
+    assert torch.all((bf16_round(a) - a).abs() <= 2.0 ** -8 * a.abs())
