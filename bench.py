@@ -27,18 +27,24 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-DEFAULT_WORKLOAD = 2
+DEFAULT_WORKLOAD = 3          # 20-qubit transformer: the first workload with BF16 and FP32 forms
 FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", type=int, default=DEFAULT_WORKLOAD)
-    ap.add_argument("--beta", type=float, default=2.0)
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--beta", type=float, default=0.0,
+                    help="output-head bias toward Hartree-Fock; 0 = untrained (near uniform)")
+    ap.add_argument("--max-unique", type=int, default=1024,
+                    help="unique-sample cap of the sampler; the paper fixes 1024 (Section 5.1)")
+    ap.add_argument("--precision", default=None, help="bf16 (compensated) or fp32; default: the "
+                    "workload's fastest form (bf16 for transformers)")
+    ap.add_argument("--fp32-steps", type=int, default=5, help="steps of the FP32 form timed beside "
+                    "the BF16 one for the speedup (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -127,10 +133,12 @@ def run_ours(args, rank, world, local):
     order = synth.default_order(n)
     named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
                               cfg.seed_params, beta=args.beta, order=order)
+    prec = args.precision or ("bf16" if cfg.arch == "transformer" else "fp32")
     model = P.Model(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
-                    precision=args.precision, compensated=True, order=order)
+                    precision=prec, compensated=True, order=order)
     params0 = model.pack(named)
-    vmc = P.VMC(ham, model, params0.clone(), cfg.n_samples, mini_batches=cfg.mini_batches)
+    vmc = P.VMC(ham, model, params0.clone(), cfg.n_samples, mini_batches=cfg.mini_batches,
+                max_unique=args.max_unique)
     seed0 = cfg.seed_sampler + 7919 * rank
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 126 MB L2
@@ -141,9 +149,13 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
 
     def timed_steps(k, first_seed, e2e=False, host=None):
+        # every step starts from the same parameters and optimiser state (a stationary workload:
+        # the same distribution, a new seed), reset outside the timed events except that the
+        # end-to-end form uploads the parameters from pinned host memory inside them
         times, evals, units = [], 0, []
         for i in range(k):
             flush.random_(0, 255)        # evict L2 between steps (outside the timed events)
+            vmc.reset(params0)
             a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
             if e2e:
@@ -165,6 +177,7 @@ def run_ours(args, rank, world, local):
 
     # warmup
     for i in range(args.warmup):
+        vmc.reset(params0)
         vmc.step(seed=seed0 + 100000 + i)
     barrier()
 
@@ -193,17 +206,45 @@ def run_ours(args, rank, world, local):
     P.profile_enable(False)
     kern = {}
     for name in ("sample", "logpsi_rows", "sweep_count", "term_sweep", "eloc_rows", "made_backward",
-                 "grad_reduce", "energy_stats", "adam", "product_backward"):
+                 "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_attention",
+                 "tf_heads", "tf_backward"):
         tms, cnt = P.profile_read(name)
         if cnt:
             kern[name] = {"ms_total": tms, "launches": cnt, "ms_per_launch": tms / cnt}
     rows_per_step = None
 
-    # algorithmic work of the dominant kernel: the network on every connected x' (eloc_rows)
+    # roofline of the dominant hot-path kernel
     roofline = None
     peaks, peak_kind = load_peaks()
-    if "eloc_rows" in kern and cfg.arch == "made":
-        # rows = connected in-sector x' other than x itself, counted on the last step's samples
+    clk_mhz = peaks.get("sm_max_mhz", 2032.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    ffma_peak = sms * FFMA_PER_SM_PER_CLK * 2 * clk_mhz * 1e6 / 1e12
+    if cfg.arch == "transformer" and "tf_gemm" in kern:
+        work, wbytes = P.profile_work("tf_gemm")
+        k = kern["tf_gemm"]
+        sec = k["ms_per_launch"] / 1e3
+        ach = work / k["launches"] / sec / 1e12
+        if prec == "bf16":
+            # d_model 64: 2MNK / compulsory bytes is ~20-40 FLOP/B, far below the bf16 ridge
+            # (~215 FLOP/B), so these GEMMs are bound by memory traffic, not the tensor pipe
+            peak_t = peaks.get("bf16_tflops_sustained", 1400.0)
+            peak_b = peaks.get("hbm_gbs", 6400.0)
+            ach_b = wbytes / k["launches"] / sec / 1e9
+            intensity = work / max(wbytes, 1.0)
+            roofline = {"kernel": "tc_gemm_kernel (tcgen05, bf16 hi+lo)", "bound": "hbm", "achieved": ach_b,
+                        "peak": peak_b, "unit": "GB/s", "frac": ach_b / peak_b, "traffic": None,
+                        "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                        "bytes_per_launch": wbytes / k["launches"], "flops_per_launch": work / k["launches"],
+                        "flop_per_byte": intensity, "tensor_tflops": ach, "tensor_frac": ach / peak_t,
+                        "note": "useful FLOPs 2MNK (the compensated split issues 2x on the tensor pipe); "
+                                "bytes = operands read once + results written once"}
+        else:
+            roofline = {"kernel": "sgemm_kernel (fp32 SIMT)", "bound": "alu", "achieved": ach, "peak": ffma_peak,
+                        "unit": "TFLOP/s", "frac": ach / ffma_peak, "traffic": None,
+                        "peak_source": f"fp32 FFMA: {sms} SMs x {FFMA_PER_SM_PER_CLK} lanes x 2 x {clk_mhz:.0f} MHz",
+                        "flops_per_launch": work / k["launches"], "bytes_per_launch": wbytes / k["launches"]}
+    elif "eloc_rows" in kern and cfg.arch == "made":
+        # rows = connected in-sector x' other than x itself, counted on one step's samples
         out = vmc.step(seed=seed0 + 999)
         bits = out["bits"]
         ro, xp, _, _ = P.nqs_term_sweep(ham, cfg.n_up, cfg.n_dn, bits)
@@ -212,17 +253,13 @@ def run_ours(args, rank, world, local):
         macs = n * h + (L - 1) * h * h + n * h + (n - 2) * h + h
         launches_per_step = kern["eloc_rows"]["launches"] / max(1, args.steps)
         flops_launch = 2.0 * macs * rows / max(1.0, launches_per_step)
-        clk_mhz = peaks.get("sm_max_mhz", 2032.0)
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak_tflops = sms * FFMA_PER_SM_PER_CLK * 2 * clk_mhz * 1e6 / 1e12
         per_launch_s = kern["eloc_rows"]["ms_per_launch"] / 1e3
         ach = flops_launch / per_launch_s / 1e12
-        roofline = {"kernel": "eloc_rows", "bound": "alu", "achieved": ach, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": ach / peak_tflops, "traffic": None,
+        roofline = {"kernel": "eloc_rows", "bound": "alu", "achieved": ach, "peak": ffma_peak,
+                    "unit": "TFLOP/s", "frac": ach / ffma_peak, "traffic": None,
                     "peak_source": f"fp32 FFMA: {sms} SMs x {FFMA_PER_SM_PER_CLK} lanes x 2 x "
                                    f"{clk_mhz:.0f} MHz (max clock)",
                     "flops_per_row": 2 * macs, "rows_per_launch": rows / max(1.0, launches_per_step)}
-        rows_per_step = rows
 
     # end to end through the public API with host buffers
     import torch as _t
@@ -237,6 +274,29 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t)
         e2e_value = t.item()
 
+    fp32_form = None
+    if prec == "bf16" and args.fp32_steps > 0:
+        m32 = P.Model(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
+                      precision="fp32", compensated=True, order=order)
+        v32 = P.VMC(ham, m32, params0.clone(), cfg.n_samples, mini_batches=cfg.mini_batches,
+                    max_unique=args.max_unique)
+        v32.step(seed=seed0 + 50000)
+        torch.cuda.synchronize()
+        ms32, ev32 = [], 0
+        for i in range(args.fp32_steps):
+            flush.random_(0, 255)
+            v32.reset(params0)
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            o32 = v32.step(seed=seed0 + i)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms32.append(a.elapsed_time(b))
+            ev32 += o32["unique"] * K_terms
+        fp32_form = {"ms_per_step": float(np.mean(ms32)), "value": ev32 / (np.sum(ms32) / 1e3),
+                     "steps": args.fp32_steps, "speedup_of_bf16": float(np.mean(ms32)) / step_ms}
+        del v32, m32
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, args, budget_s=args.cpu_seconds)
@@ -246,12 +306,15 @@ def run_ours(args, rank, world, local):
             "metric": "sample.Pauli-term local-energy evals/sec (VMC step)",
             "value": value, "unit": "sample.term/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (hi+lo activations, fp32 accumulate)" if prec == "bf16" else "f32",
+            "data": "synthetic",
             "config": {"workload": cfg.name, "n_qubits": n, "electrons": [cfg.n_up, cfg.n_dn],
                        "terms_K": K_terms, "groups_G": G, "model": f"{cfg.arch} h={cfg.hidden} L={cfg.layers}",
-                       "n_samples": cfg.n_samples, "mini_batches": cfg.mini_batches,
+                       "n_samples": cfg.n_samples, "max_unique": args.max_unique,
+                       "mini_batches": cfg.mini_batches,
                        "unique_samples_mean": float(np.mean(units)), "beta": args.beta,
-                       "precision": args.precision, "compensated": True,
+                       "precision": prec, "compensated": True,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "kernels": kern,
@@ -260,6 +323,7 @@ def run_ours(args, rank, world, local):
             "e2e": {"value": e2e_value, "unit": "sample.term/s",
                     "h2d_bytes_per_step": int(host["params"].numel() * 4),
                     "d2h_bytes_per_step": int(32 + 8 * float(np.mean(units_e)))},
+            "fp32_form": fp32_form,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "peaks_source": peak_kind,
@@ -269,43 +333,31 @@ def run_ours(args, rank, world, local):
 
 # ----------------------------------------------------------------------------- oracle timing
 def cpu_baseline(cfg, args, budget_s=15.0):
-    """The FP64 oracle as it stands on this host: a bounded sample of the same VMC step
-    (sampling, per-term local energies of a subset of the unique samples, VMC gradient)."""
+    """The FP64 oracle as it stands on this host, on a bounded sample of the workload: local
+    energies (per-term definition, FP64 network) of seeded in-sector configurations, one at a
+    time until the time budget is used.  Sampling and the gradient are not included, which
+    favours the CPU figure."""
     import torch
     from oracle.eloc import local_energy
     from oracle.models import Model
-    from oracle.sampler import model_p_fn, sample
-    from oracle.vmc import vmc_gradient
 
     n = cfg.n_qubits
     order = synth.default_order(n)
     named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
                               cfg.seed_params, beta=args.beta, order=order)
     xm, zm, coef = synth.hamiltonian_for(cfg)
-    om = Model(cfg.arch, named, n, cfg.n_up, cfg.n_dn, order, cfg.hidden, cfg.layers, cfg.heads,
-               requires_grad=True)
-    t0 = time.perf_counter()
-    bits, counts = sample(model_p_fn(om), n, order, cfg.n_samples, cfg.n_samples, cfg.seed_sampler)
-    t_sample = time.perf_counter() - t0
-    # local energies sample by sample until the budget is used
-    done, t_el = 0, 0.0
-    e = []
-    while done < len(bits) and t_el < budget_s:
-        t1 = time.perf_counter()
-        e.append(local_energy(om, xm, zm, coef, bits[done: done + 1])[0])
-        t_el += time.perf_counter() - t1
+    om = Model(cfg.arch, named, n, cfg.n_up, cfg.n_dn, order, cfg.hidden, cfg.layers, cfg.heads)
+    bits = synth.random_sector_bits(cfg.n_orb, cfg.n_up, cfg.n_dn, 4096, seed=cfg.seed_sampler)
+    done, t = 0, 0.0
+    while done < len(bits) and t < budget_s:
+        t0 = time.perf_counter()
+        local_energy(om, xm, zm, coef, bits[done: done + 1])
+        t += time.perf_counter() - t0
         done += 1
-    t2 = time.perf_counter()
-    vmc_gradient(om, bits[:done], counts[:done], np.array(e))
-    t_grad = time.perf_counter() - t2
-    frac = done / len(bits)
-    step_s = t_sample + t_el / frac + t_grad / frac
-    evals = len(bits) * len(coef)
-    return {"value": evals / step_s, "unit": "sample.term/s", "cores": torch.get_num_threads(),
+    return {"value": done * len(coef) / t, "unit": "sample.term/s", "cores": torch.get_num_threads(),
             "kind": "oracle",
-            "sample": f"full sampler ({cfg.n_samples} nominal), local energy of {done}/{len(bits)} "
-                      f"unique samples and their gradient, extrapolated to the full step "
-                      f"({step_s:.2f} s/step)"}
+            "sample": f"FP64 oracle local energy of {done} seeded in-sector samples of the workload "
+                      f"({t:.1f} s; K = {len(coef)} terms each); sampling and gradient excluded"}
 
 
 def run_reference(args, rank, world):

@@ -235,6 +235,11 @@ const char* nqs_last_error(void);
 int nqs_profile_enable(int on);
 int nqs_profile_reset(void);
 int nqs_profile_read(const char* kernel, double* total_ms, int64_t* launches);
+/* Summed algorithmic work recorded with the timed launches of `kernel` since the last reset:
+ * useful FLOPs and compulsory DRAM bytes (operands read once, results written once) -- for
+ * "tf_gemm" 2*M*N*K FLOPs (the compensated split's second pass not counted) and the bytes of A,
+ * W, C (and C read back for a residual add); 0 where no figure is attached. */
+int nqs_profile_work(const char* kernel, double* flops, double* bytes);
 
 /* Number of kernels this library has launched in the calling process (all streams). */
 int64_t nqs_launch_count(void);

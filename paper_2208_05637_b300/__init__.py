@@ -36,7 +36,7 @@ EXPORTED = [
     "nqs_model_bind_params", "nqs_model_destroy", "nqs_workspace_size", "nqs_sample",
     "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward",
     "nqs_energy_stats", "nqs_adam_step", "nqs_strerror", "nqs_last_error", "nqs_profile_enable",
-    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16",
+    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16", "nqs_profile_work",
 ]
 
 
@@ -80,6 +80,7 @@ _sig = {
     "nqs_launch_count": [],
     "nqs_local_energy_noalloc": [_P, _P, _P, _I64, _P, _P],
     "nqs_gemm_bf16": [_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P],
+    "nqs_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -131,6 +132,13 @@ def profile_read(kernel: str):
     ms = ctypes.c_double(); n = _I64()
     _check(_lib.nqs_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)), "nqs_profile_read")
     return ms.value, n.value
+
+
+def profile_work(kernel: str):
+    """(FLOPs, bytes) recorded with the timed launches of `kernel`."""
+    w = ctypes.c_double(); b = ctypes.c_double()
+    _check(_lib.nqs_profile_work(kernel.encode(), ctypes.byref(w), ctypes.byref(b)), "nqs_profile_work")
+    return w.value, b.value
 
 
 # ----------------------------------------------------------------- Hamiltonian

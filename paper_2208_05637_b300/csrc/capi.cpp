@@ -42,13 +42,19 @@ int num_sms() {
 struct ProfRec {
     std::string name;
     cudaEvent_t a, b;
+    double work, bytes;
+};
+struct ProfAcc {
+    double ms = 0.0;
+    int64_t launches = 0;
+    double work = 0.0, bytes = 0.0;
 };
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfRec> g_prof_pending;
-static std::map<std::string, std::pair<double, int64_t>> g_prof_acc;
+static std::map<std::string, ProfAcc> g_prof_acc;
 
-ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), stream(s) {
+ProfScope::ProfScope(const char* n, cudaStream_t s, double w, double by) : name(n), stream(s), work(w), bytes(by) {
     if (!g_prof_on) return;
     if (cudaEventCreate(&e0) != cudaSuccess) { e0 = nullptr; return; }
     cudaEventRecord(e0, stream);
@@ -60,7 +66,7 @@ ProfScope::~ProfScope() {
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
     cudaEventRecord(e1, stream);
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof_pending.push_back({name, e0, e1});
+    g_prof_pending.push_back({name, e0, e1, work, bytes});
 }
 
 static void prof_drain() {
@@ -69,8 +75,10 @@ static void prof_drain() {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         auto& acc = g_prof_acc[r.name];
-        acc.first += ms;
-        acc.second += 1;
+        acc.ms += ms;
+        acc.launches += 1;
+        acc.work += r.work;
+        acc.bytes += r.bytes;
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
@@ -188,8 +196,18 @@ int nqs_profile_read(const char* kernel, double* total_ms, int64_t* launches) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof_drain();
     auto it = g_prof_acc.find(kernel);
-    *total_ms = it == g_prof_acc.end() ? 0.0 : it->second.first;
-    *launches = it == g_prof_acc.end() ? 0 : it->second.second;
+    *total_ms = it == g_prof_acc.end() ? 0.0 : it->second.ms;
+    *launches = it == g_prof_acc.end() ? 0 : it->second.launches;
+    return NQS_OK;
+}
+
+int nqs_profile_work(const char* kernel, double* flops, double* bytes) {
+    if (!kernel || !flops || !bytes) return NQS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    auto it = g_prof_acc.find(kernel);
+    *flops = it == g_prof_acc.end() ? 0.0 : it->second.work;
+    *bytes = it == g_prof_acc.end() ? 0.0 : it->second.bytes;
     return NQS_OK;
 }
 
@@ -409,6 +427,12 @@ int nqs_model_create(const nqs_model_desc* d, nqs_model_t* out) {
         }
         const int dh = h / d->heads;
         if (dh != 16 && dh != 32) { delete m; set_error("transformer head size must be 16 or 32"); return NQS_ERR_UNSUPPORTED; }
+        if (d->heads > 8) { delete m; set_error("transformer supports at most 8 heads"); return NQS_ERR_UNSUPPORTED; }
+        if ((size_t)n * (4 * h + 2) * 4 > 200 * 1024) {
+            delete m;
+            set_error("transformer attention block (n x 4*d_model floats) exceeds shared memory");
+            return NQS_ERR_UNSUPPORTED;
+        }
         add_param(m, "tok_emb", 3 * (int64_t)h, &mc.tok_emb);
         add_param(m, "pos_emb", (int64_t)n * h, &mc.pos_emb);
         for (int l = 0; l < d->layers; ++l) {

@@ -42,10 +42,11 @@ void count_launch();
 
 // Per-kernel CUDA-event timing (enabled by nqs_profile_enable).
 struct ProfScope {
-    ProfScope(const char* name, cudaStream_t s);
+    ProfScope(const char* name, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
     ~ProfScope();
     const char* name;
     cudaStream_t stream;
+    double work, bytes;        // algorithmic FLOPs and bytes of the bracketed launch
     cudaEvent_t e0 = nullptr;
 };
 

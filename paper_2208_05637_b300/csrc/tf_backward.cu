@@ -305,32 +305,39 @@ __global__ void outer_final_kernel(const float* __restrict__ part, int nsplit, i
     }
 }
 
-// embeddings: dpos[t][j] += sum_r dh[r,t,j]; dtok[tok][j] += sum over rows with that token
-__global__ void embed_bwd_kernel(ModelConst mc, const uint64_t* __restrict__ bits, const float* __restrict__ dh,
-                                 int64_t R, float* __restrict__ grad) {
+// Embedding gradients, deterministic two-stage sums.  Stage 1: CTA (column tile, chunk of
+// EB_ROWS sequences) sums its sequences for every position and for each token id.
+constexpr int EB_ROWS = 64;
+__global__ void embed_bwd_partial_kernel(ModelConst mc, const uint64_t* __restrict__ bits,
+                                         const float* __restrict__ dh, int64_t R, float* __restrict__ part) {
     const int d = mc.hidden, n = mc.n;
-    const int64_t nt = (int64_t)n * d;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt + 3 * d; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nt) {
-            const int t = (int)(i / d), j = (int)(i % d);
-            float s = 0.f;
-            for (int64_t r = 0; r < R; ++r) s += dh[(r * n + t) * d + j];
-            grad[mc.pos_emb + i] += s;
-        } else {
-            const int tok = (int)((i - nt) / d), j = (int)((i - nt) % d);
-            float s = 0.f;
-            if (tok == 2) {
-                for (int64_t r = 0; r < R; ++r) s += dh[(r * n) * d + j];
-            } else {
-                for (int64_t r = 0; r < R; ++r) {
-                    const uint64_t x = bits[r];
-                    for (int t = 1; t < n; ++t)
-                        if ((int)((x >> mc.order[t - 1]) & 1ull) == tok) s += dh[(r * n + t) * d + j];
-                }
-            }
-            grad[mc.tok_emb + tok * d + j] += s;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * EB_ROWS, r1 = min(R, r0 + EB_ROWS);
+    if (j >= d) return;
+    float* out = part + (int64_t)blockIdx.y * (n + 3) * d;   // [n positions + 3 tokens][d]
+    float tok[3] = {0.f, 0.f, 0.f};
+    for (int t = 0; t < n; ++t) {
+        float s = 0.f;
+        for (int64_t r = r0; r < r1; ++r) {
+            const float g = dh[(r * n + t) * d + j];
+            s += g;
+            const int k = t == 0 ? 2 : (int)((bits[r] >> mc.order[t - 1]) & 1ull);
+            tok[k] += g;
         }
+        out[t * d + j] = s;
     }
+    for (int k = 0; k < 3; ++k) out[(n + k) * d + j] = tok[k];
+}
+
+__global__ void embed_bwd_final_kernel(ModelConst mc, const float* __restrict__ part, int nchunks,
+                                       float* __restrict__ grad) {
+    const int d = mc.hidden, n = mc.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (n + 3) * d) return;
+    float s = 0.f;
+    for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * (n + 3) * d + i];
+    if (i < n * d) grad[mc.pos_emb + i] += s;
+    else grad[mc.tok_emb + (i - n * d)] += s;
 }
 
 inline int gs(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16)); }
@@ -390,6 +397,7 @@ void bwd_layout(Carver& c, const ModelConst& mc, int64_t R, BwdBufs& b, float** 
     b.DPH = c.take<float>(R * 4);
     b.nsplit = std::max<int64_t>(1, std::min<int64_t>(64, M / 512));
     b.part_elems = std::max<int64_t>(b.nsplit * 4 * d * d, ((M + CS_ROWS - 1) / CS_ROWS) * 4 * d);
+    b.part_elems = std::max<int64_t>(b.part_elems, ((R + 63) / 64) * (n + 3) * d);
     b.part = c.take<float>(b.part_elems);
     b.Wr = c.take<float>(12 * d * d * L);
 }
@@ -515,8 +523,8 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
             NQS_TRY(ln_fwd(b.Hin[0], P + mc.ln1_g[0], P + mc.ln1_b[0], b.A1[0]));
             for (int l = 0; l < L; ++l) {
                 NQS_TRY(gemm_nt((const float*)b.A1[l], W[l][TF_WQKV], P + mc.bqkv[l], b.QKV[l], M, 3 * d, d, TF_EPI_STORE));
-                attention_kernel<MODE><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.QKV[l], n, d, dh, b.O[l]);
-                NQS_LAUNCHED();
+                NQS_CK(launch_attention<MODE>(b.QKV[l], R, n, d, mc.heads, b.O[l], s));
+                count_launch();
                 NQS_CK(cudaMemcpyAsync(b.Hmid[l], b.Hin[l], M * d * sizeof(float), cudaMemcpyDeviceToDevice, s));
                 NQS_TRY(gemm_nt((const float*)b.O[l], W[l][TF_WO], P + mc.bo[l], b.Hmid[l], M, d, d, TF_EPI_RESID));
                 NQS_TRY(ln_fwd(b.Hmid[l], P + mc.ln2_g[l], P + mc.ln2_b[l], b.A2[l]));
@@ -566,8 +574,13 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
                 NQS_TRY(colsum(b.GX, d, M, d, grad + mc.ln1_g[l]));
                 NQS_TRY(colsum(b.dS, d, M, d, grad + mc.ln1_b[l]));
             }
-            embed_bwd_kernel<<<gs((int64_t)(n + 3) * d), 256, 0, s>>>(mc, xb, b.dH, R, grad);
-            NQS_LAUNCHED();
+            {
+                const int nch = (int)((R + EB_ROWS - 1) / EB_ROWS);
+                embed_bwd_partial_kernel<<<dim3((d + 127) / 128, nch), 128, 0, s>>>(mc, xb, b.dH, R, b.part);
+                NQS_LAUNCHED();
+                embed_bwd_final_kernel<<<((n + 3) * d + 255) / 256, 256, 0, s>>>(mc, b.part, nch, grad);
+                NQS_LAUNCHED();
+            }
         }
         return NQS_OK;
     });

@@ -241,5 +241,69 @@ attention_kernel(const float* __restrict__ qkv, int T, int d, int dh, void* __re
     }
 }
 
+// Causal attention, one CTA per sequence (looping over sequences) with one warp per head.  The
+// sequence's whole [T x 3d] q|k|v block is read with coalesced loads into shared memory (row
+// stride 3d+1 against bank conflicts); lane l of warp h owns query rows l and l + 32 of head h
+// and runs an online (streaming) softmax over keys 0..t, accumulating P V in registers; the
+// [T x d] output is staged in shared memory and written back as whole rows.  DH = head size.
+template <int MODE, int DH>
+__global__ void __launch_bounds__(256)
+attention_seq_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int H, void* __restrict__ o) {
+    extern __shared__ float att_sm[];
+    const int ldq = 3 * d + 1, ldo = d + 1;
+    float* X = att_sm;                 // [T][3d+1]
+    float* O = att_sm + T * ldq;       // [T][d+1]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float scale = rsqrtf((float)DH);
+    for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+        const float* src = qkv + r * T * (int64_t)(3 * d);
+        for (int i = threadIdx.x; i < T * 3 * d; i += blockDim.x) X[(i / (3 * d)) * ldq + i % (3 * d)] = src[i];
+        __syncthreads();
+        const int hd = warp;
+        for (int t = lane; t < T; t += 32) {
+            float q[DH], acc[DH];
+#pragma unroll
+            for (int j = 0; j < DH; ++j) { q[j] = X[t * ldq + hd * DH + j] * scale; acc[j] = 0.f; }
+            float m = -INFINITY, ssum = 0.f;
+            for (int u = 0; u <= t; ++u) {
+                const float* kr = X + u * ldq + d + hd * DH;
+                const float* vr = X + u * ldq + 2 * d + hd * DH;
+                float sc = 0.f;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) sc = fmaf(q[j], kr[j], sc);
+                const float mn = fmaxf(m, sc);
+                const float corr = expf(m - mn);      // 0 on the first key (m = -inf)
+                const float e = expf(sc - mn);
+                ssum = ssum * corr + e;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) acc[j] = fmaf(e, vr[j], acc[j] * corr);
+                m = mn;
+            }
+            const float inv = 1.f / ssum;
+#pragma unroll
+            for (int j = 0; j < DH; ++j) O[t * ldo + hd * DH + j] = acc[j] * inv;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < T * d; i += blockDim.x)
+            store_mode<MODE>(o, r * T + i / d, d, i % d, O[(i / d) * ldo + i % d]);
+        __syncthreads();
+    }
+}
+
+template <int MODE>
+inline cudaError_t launch_attention(const float* qkv, int64_t R, int T, int d, int H, void* o, cudaStream_t s) {
+    const int dh = d / H;
+    const size_t smem = (size_t)(T * (3 * d + 1) + T * (d + 1)) * sizeof(float);
+    const unsigned grid = (unsigned)std::min<int64_t>(R, (int64_t)num_sms() * 8);
+    if (dh == 16) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(attention_seq_kernel<MODE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attention_seq_kernel<MODE, 16><<<grid, H * 32, smem, s>>>(qkv, R, T, d, H, o);
+    } else {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(attention_seq_kernel<MODE, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attention_seq_kernel<MODE, 32><<<grid, H * 32, smem, s>>>(qkv, R, T, d, H, o);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 }  // namespace nqs

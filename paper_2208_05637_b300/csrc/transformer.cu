@@ -226,7 +226,9 @@ int with_dpl(int d, F&& f) {
 
 // ====================================================================== host side
 int64_t tf_seq_capacity(const ModelConst& mc) {
-    // about 256 MB of activations: h, a, qkv, o (fp32) and the 4d MLP buffer
+    // Sequences per pass: the pass's activations (h, a, qkv, o and the 4d MLP buffer, about
+    // 10*d floats per position) are kept near 256 MB.  Smaller, L2-resident passes lose more to
+    // the extra launches than they gain in bandwidth.
     const int64_t per_seq = (int64_t)mc.n * mc.hidden * 10 * 4;
     int64_t R = 64;
     while (R * 2 * per_seq <= (256ll << 20) && R < 8192) R *= 2;
@@ -245,7 +247,15 @@ void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b) {
 
 int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, const void* A,
             void* C, int64_t M, int N, int K, int epi, const float* bias, cudaStream_t s) {
-    if (mc.precision == NQS_PREC_BF16) {
+    // compulsory bytes: A and W read once, C written once (and read once for a residual add)
+    const bool bf = mc.precision == NQS_PREC_BF16;
+    const double split = (bf && mc.compensated) ? 2.0 : 1.0;
+    const double a_el = bf ? 2.0 * split : 4.0, w_el = bf ? 2.0 * split : 4.0;
+    const double c_el = epi == TF_EPI_GELU ? (bf ? 2.0 * split : 4.0) : 4.0;
+    const double bytes = (double)M * K * a_el + (double)N * K * w_el +
+                         (double)M * N * c_el * (epi == TF_EPI_RESID ? 2.0 : 1.0);
+    ProfScope ps("tf_gemm", s, 2.0 * (double)M * N * K, bytes);
+    if (bf) {
         // compensated form: A = [A_hi | A_lo] and B = [W | W], so K doubles
         const bool split = mc.compensated != 0;
         const int e = (epi == TF_EPI_GELU && split) ? TF_EPI_GELU2 : epi;
@@ -308,33 +318,24 @@ int64_t tf_bf16_weight_elems(const ModelConst& mc) {
 template <int MODE>
 static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
                            int64_t R, int T, TfBufs& b, cudaStream_t s) {
-    const int d = mc.hidden, dh = d / mc.heads;
+    const int d = mc.hidden;
     const int64_t M = R * T;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
         embed_ln_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(mc, P, bits, R, T, b.h, b.a);
         NQS_LAUNCHED();
         for (int l = 0; l < mc.layers; ++l) {
-            {
-                ProfScope ps("tf_gemm", s);
-                NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
-            }
+            NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
             {
                 ProfScope ps("tf_attention", s);
-                attention_kernel<MODE><<<dim3((unsigned)R, (unsigned)mc.heads), 128, 0, s>>>(b.qkv, T, d, dh, b.o);
-                NQS_LAUNCHED();
+                NQS_CK(launch_attention<MODE>(b.qkv, R, T, d, mc.heads, b.o, s));
+                count_launch();
             }
-            {
-                ProfScope ps("tf_gemm", s);
-                NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
-            }
+            NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
             layernorm_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
             NQS_LAUNCHED();
-            {
-                ProfScope ps("tf_gemm", s);
-                NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, M, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
-                NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
-            }
+            NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, M, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
+            NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
             if (l + 1 < mc.layers) {
                 layernorm_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
                 NQS_LAUNCHED();

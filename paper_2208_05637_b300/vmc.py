@@ -53,6 +53,14 @@ class VMC:
         self.ws_sample = model.workspace(OP_SAMPLE, self.n_samples)
         self._ws = {}
 
+    def reset(self, params):
+        """Restore the parameters and clear the optimiser state (device copies, no sync)."""
+        with torch.no_grad():
+            self.params.data.copy_(params)
+            self.m.zero_()
+            self.v.zero_()
+        self.t = 0
+
     def _workspace(self, op, batch):
         key = (op, batch)
         if key not in self._ws:
