@@ -102,14 +102,15 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
-    v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <int EPI>
@@ -192,41 +193,45 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tc_fence_after();
         const int64_t row = m0 + warp * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < BN; c += 8) {
-            float v[8];
-            tmem_ld8(tbase + (uint32_t)c, v);
+        for (int c = 0; c < BN; c += 16) {
+            float v16[16];
+            tmem_ld16(tbase + (uint32_t)c, v16);
             if (row < M) {
-                const int col = n0 + c;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] += bias ? bias[col + j] : 0.f;
-                if (EPI == TF_EPI_GELU) {
-                    __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(Cv) + row * N + col;
-                    __align__(16) __nv_bfloat16 o[8];
+                for (int half = 0; half < 2; ++half) {
+                    const int col = n0 + c + 8 * half;
+                    float v[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(gelu_tanh(v[j]));
-                    *reinterpret_cast<uint4*>(C) = *reinterpret_cast<const uint4*>(o);
-                } else if (EPI == TF_EPI_GELU2) {
-                    // compensated output: hi in columns [0, N), lo = bf16(g - hi) in [N, 2N)
-                    __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(Cv) + row * 2 * N + col;
-                    __align__(16) __nv_bfloat16 hi[8], lo[8];
+                    for (int j = 0; j < 8; ++j) v[j] = v16[8 * half + j] + (bias ? bias[col + j] : 0.f);
+                    if (EPI == TF_EPI_GELU) {
+                        __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(Cv) + row * N + col;
+                        __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float g = gelu_tanh(v[j]);
-                        hi[j] = __float2bfloat16_rn(g);
-                        lo[j] = __float2bfloat16_rn(g - __bfloat162float(hi[j]));
+                        for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(gelu_tanh(v[j]));
+                        *reinterpret_cast<uint4*>(C) = *reinterpret_cast<const uint4*>(o);
+                    } else if (EPI == TF_EPI_GELU2) {
+                        // compensated output: hi in columns [0, N), lo = bf16(g - hi) in [N, 2N)
+                        __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(Cv) + row * 2 * N + col;
+                        __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float g = gelu_tanh(v[j]);
+                            hi[j] = __float2bfloat16_rn(g);
+                            lo[j] = __float2bfloat16_rn(g - __bfloat162float(hi[j]));
+                        }
+                        *reinterpret_cast<uint4*>(C) = *reinterpret_cast<const uint4*>(hi);
+                        *reinterpret_cast<uint4*>(C + N) = *reinterpret_cast<const uint4*>(lo);
+                    } else {
+                        float4* C = reinterpret_cast<float4*>(reinterpret_cast<float*>(Cv) + row * N + col);
+                        float4 x0 = make_float4(v[0], v[1], v[2], v[3]), x1 = make_float4(v[4], v[5], v[6], v[7]);
+                        if (EPI == TF_EPI_RESID) {
+                            const float4 y0 = C[0], y1 = C[1];
+                            x0.x += y0.x; x0.y += y0.y; x0.z += y0.z; x0.w += y0.w;
+                            x1.x += y1.x; x1.y += y1.y; x1.z += y1.z; x1.w += y1.w;
+                        }
+                        C[0] = x0;
+                        C[1] = x1;
                     }
-                    *reinterpret_cast<uint4*>(C) = *reinterpret_cast<const uint4*>(hi);
-                    *reinterpret_cast<uint4*>(C + N) = *reinterpret_cast<const uint4*>(lo);
-                } else {
-                    float4* C = reinterpret_cast<float4*>(reinterpret_cast<float*>(Cv) + row * N + col);
-                    float4 x0 = make_float4(v[0], v[1], v[2], v[3]), x1 = make_float4(v[4], v[5], v[6], v[7]);
-                    if (EPI == TF_EPI_RESID) {
-                        const float4 y0 = C[0], y1 = C[1];
-                        x0.x += y0.x; x0.y += y0.y; x0.z += y0.z; x0.w += y0.w;
-                        x1.x += y1.x; x1.y += y1.y; x1.z += y1.z; x1.w += y1.w;
-                    }
-                    C[0] = x0;
-                    C[1] = x1;
                 }
             }
         }
@@ -277,11 +282,18 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
                  cudaStream_t s) {
     if (M <= 0) return NQS_OK;
     if (N % 16 || N < 16 || K % 8 || K <= 0) { set_error("tensor-core GEMM needs N % 16 == 0 and K % 8 == 0"); return NQS_ERR_UNSUPPORTED; }
-    const int BN = N <= 256 ? N : N / 2;
-    if (BN > 256 || BN % 16 || N % BN) { set_error("tensor-core GEMM: unsupported N"); return NQS_ERR_UNSUPPORTED; }
+    // N tile: N itself up to 128 columns, else the largest multiple of 16 <= 128 dividing N, so
+    // that a 128-column TMEM accumulator lets four CTAs share an SM
+    int BN = N;
+    if (N > 128) {
+        BN = 0;
+        for (int b = 128; b >= 16; b -= 16)
+            if (N % b == 0) { BN = b; break; }
+    }
+    if (BN == 0 || BN % 16 || N % BN) { set_error("tensor-core GEMM: unsupported N"); return NQS_ERR_UNSUPPORTED; }
     if ((M + TC_BM - 1) / TC_BM > 65535) { set_error("tensor-core GEMM: M too large"); return NQS_ERR_UNSUPPORTED; }
     const int nkb = (K + TC_BK - 1) / TC_BK;
-    const int stages = std::min(nkb, 4);
+    const int stages = std::min(nkb, 2);
     int tcols = 32;
     while (tcols < BN) tcols <<= 1;
     size_t smem = 1024 + (size_t)stages * (TC_BM * 128 + (size_t)BN * 128) + (2 * stages + 1) * 8 + 16;
