@@ -19,6 +19,7 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    cudaGetLastError();   // clear a non-sticky error so later runtime calls do not report it again
     set_error(std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
               std::to_string(line) + ")");
     return NQS_ERR_CUDA;
@@ -56,6 +57,8 @@ static std::map<std::string, ProfAcc> g_prof_acc;
 
 ProfScope::ProfScope(const char* n, cudaStream_t s, double w, double by) : name(n), stream(s), work(w), bytes(by) {
     if (!g_prof_on) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
     if (cudaEventCreate(&e0) != cudaSuccess) { e0 = nullptr; return; }
     cudaEventRecord(e0, stream);
 }
@@ -502,8 +505,16 @@ int nqs_model_bind_params(nqs_model_t m, const float* p) {
     return NQS_OK;
 }
 
+static void graph_release(SamplerGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+}
+
 void nqs_model_destroy(nqs_model_t m) {
     if (!m) return;
+    graph_release(m->graph);
+    if (m->graph.ev) cudaEventDestroy(m->graph.ev);
+    if (m->graph.side) cudaStreamDestroy(m->graph.side);
     if (m->d_bf16) cudaFree(m->d_bf16);
     delete m;
 }
@@ -596,11 +607,57 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
         tf_layout(c, m->mc, std::min(b.cap, tf_seq_capacity(m->mc)), tb);
         NQS_TRY(tf_weights(m, w, s));
     }
-    NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride,
-                        &ctx, s));
     int64_t U = 0;
-    NQS_CK(cudaMemcpyAsync(&U, b.U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    NQS_CK(cudaStreamSynchronize(s));
+    const bool graphable = b.cap <= SAMPLER_GRAPH_MAX_CAP;
+    SamplerGraph& G = m->graph;
+    const bool same = G.n_samples == n_samples && G.max_unique == max_unique && G.ws == ws &&
+                      G.trace == p_trace && G.trace_stride == trace_stride && G.params == m->d_params &&
+                      G.bf16 == (const void*)m->d_bf16;
+    if (graphable && same && !G.failed && (G.exec || G.seen)) {
+        // replay (capturing first if this shape has run once eagerly): the steps run on the
+        // library's stream, ordered after the caller's stream by an event
+        if (!G.side) NQS_CK(cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking));
+        if (!G.ev) NQS_CK(cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming));
+        NQS_CK(cudaEventRecord(G.ev, s));
+        NQS_CK(cudaStreamWaitEvent(G.side, G.ev, 0));
+        if (!G.exec) {
+            cudaGraph_t graph = nullptr;
+            NQS_CK(cudaStreamBeginCapture(G.side, cudaStreamCaptureModeRelaxed));
+            const int st = sampler_steps(m->mc, m->d_params, n_samples, max_unique, b, p_trace, trace_stride,
+                                         &ctx, true, G.side);
+            const cudaError_t ce = cudaStreamEndCapture(G.side, &graph);
+            cudaError_t ie = cudaErrorUnknown;
+            if (st == NQS_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&G.exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                cudaGetLastError();
+                G.exec = nullptr;
+                G.failed = true;
+            }
+        }
+        if (G.exec) {
+            ProfScope ps("sample", G.side);
+            NQS_TRY(sampler_init(b, n_samples, seed, G.side));
+            NQS_CK(cudaGraphLaunch(G.exec, G.side));
+        } else {
+            NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride,
+                                &ctx, true, G.side));
+        }
+        NQS_CK(cudaMemcpyAsync(&U, b.U, sizeof(int64_t), cudaMemcpyDeviceToHost, G.side));
+        NQS_CK(cudaStreamSynchronize(G.side));
+    } else {
+        if (graphable && !same) {
+            graph_release(G);
+            G.n_samples = n_samples; G.max_unique = max_unique; G.ws = ws; G.trace = p_trace;
+            G.trace_stride = trace_stride; G.params = m->d_params; G.bf16 = m->d_bf16;
+            G.failed = false;
+        }
+        G.seen = graphable;
+        NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride,
+                            &ctx, graphable, s));
+        NQS_CK(cudaMemcpyAsync(&U, b.U, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+    }
     if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
     *n_unique = U;
     if (U > capacity) {

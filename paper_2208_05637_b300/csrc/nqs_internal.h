@@ -113,6 +113,20 @@ struct ParamInfo {
     int64_t offset, numel;
 };
 
+// A captured sampler (all n steps) for one call shape, replayed on a library-owned stream.
+struct SamplerGraph {
+    int64_t n_samples = -1, max_unique = -1, trace_stride = 0;
+    const void* ws = nullptr;
+    const float* trace = nullptr;
+    const float* params = nullptr;
+    const void* bf16 = nullptr;
+    bool seen = false;              // this shape ran once eagerly; capture on the next call
+    bool failed = false;            // capture not possible: stay eager for this shape
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
 }  // namespace nqs
 
 struct nqs_model_s {
@@ -122,6 +136,7 @@ struct nqs_model_s {
     int64_t n_params = 0;
     const float* d_params = nullptr;
     uint16_t* d_bf16 = nullptr;      // bf16 copies of the transformer GEMM weights (BF16 models)
+    nqs::SamplerGraph graph;         // captured sampler of the last call shape
 };
 
 namespace nqs {
@@ -261,7 +276,14 @@ struct SamplerBufs {
 int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b);
 int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
                 uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
-                const TfCtx* tf, cudaStream_t s);
+                const TfCtx* tf, bool fixed_rows, cudaStream_t s);
+int sampler_init(SamplerBufs& b, int64_t n_samples, uint64_t seed, cudaStream_t s);
+int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
+                  SamplerBufs& b, float* trace, int64_t trace_stride, const TfCtx* tf,
+                  bool fixed_rows, cudaStream_t s);
+// Parent buffers up to this size run the sampler with fixed-size passes and a CUDA graph.
+constexpr int64_t SAMPLER_GRAPH_MAX_CAP = 8192;
+
 int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out,
                         int64_t n, cudaStream_t s);
 

@@ -35,17 +35,22 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
     return c0;
 }
 
-__global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_samples) {
+// U[0] = unique count, U[2] = eviction flag, U[3] = seed (read by the draws, so that a
+// captured graph of the steps can be replayed with a new seed)
+__global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_samples, uint64_t seed) {
     bits[0] = 0;
     cnt[0] = n_samples;
     U[0] = 1;
+    U[3] = (int64_t)seed;
 }
 
 // ones per parent: warp-aggregated integer atomics (exact, order-independent)
 __global__ void draw_kernel(int64_t n_samples, const int64_t* __restrict__ start,
                             const int64_t* __restrict__ Udev, const uint64_t* __restrict__ thr,
-                            int64_t* __restrict__ n1, int k, uint32_t key0, uint32_t key1) {
-    const int64_t U = *Udev;
+                            int64_t* __restrict__ n1, int k) {
+    const int64_t U = Udev[0];
+    const uint64_t seed = (uint64_t)Udev[3];
+    const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
     // after an eviction the surviving counts sum to less than n_samples: the nominal indices
     // run over [0, start[U]) only
     const int64_t total = min(start[U], n_samples);
@@ -253,14 +258,18 @@ int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs
     return NQS_OK;
 }
 
-// Transformer conditional at step k: the parent count is read back (one small synchronous copy
-// per step) to size the layer-wise passes over the first k+1 positions.
+// Transformer conditional at step k over the first k+1 positions.  With fixed_rows the pass
+// covers the whole buffer capacity (rows past the unique count are ignored later), so no host
+// synchronisation is needed and the steps can be captured in a graph; otherwise the parent
+// count is read back (one small synchronous copy per step) to size the passes exactly.
 static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* bits,
                    const int64_t* Udev, SamplerBufs& b, float* trace, const TfCtx* tf,
-                   cudaStream_t s) {
-    int64_t U = 0;
-    NQS_CK(cudaMemcpyAsync(&U, Udev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    NQS_CK(cudaStreamSynchronize(s));
+                   bool fixed_rows, cudaStream_t s) {
+    int64_t U = b.cap;
+    if (!fixed_rows) {
+        NQS_CK(cudaMemcpyAsync(&U, Udev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+    }
     for (int64_t lo = 0; lo < U; lo += tf->b->R) {
         const int64_t R = std::min(tf->b->R, U - lo);
         NQS_TRY(tf_forward(mc, P, *tf->w, bits + lo, R, k + 1, *tf->b, s));
@@ -271,25 +280,27 @@ static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* 
     return NQS_OK;
 }
 
-int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
-                uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
-                const TfCtx* tf, cudaStream_t s) {
-    const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
-    int32_t* did = reinterpret_cast<int32_t*>(b.U + 2);
-    ProfScope ps("sample", s);
-    init_kernel<<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples);
+int sampler_init(SamplerBufs& b, int64_t n_samples, uint64_t seed, cudaStream_t s) {
+    init_kernel<<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples, seed);
     NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
+                  SamplerBufs& b, float* trace, int64_t trace_stride, const TfCtx* tf,
+                  bool fixed_rows, cudaStream_t s) {
+    int32_t* did = reinterpret_cast<int32_t*>(b.U + 2);
     uint64_t* cb = b.bitsA; int64_t* cc = b.cntA;
     uint64_t* nb = b.bitsB; int64_t* nc = b.cntB;
     const int g = grid_for(b.cap);
     for (int k = 0; k < mc.n; ++k) {
         float* tr = trace ? trace + (int64_t)k * trace_stride : nullptr;
-        if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, s));
+        if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, fixed_rows, s));
         else NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr, tr, s));
         NQS_TRY(launch_scan_i64(cc, b.cap, b.U, b.start, s));
         zero_kernel<<<g, 256, 0, s>>>(b.n1, b.U, b.cap);
         NQS_LAUNCHED();
-        draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k, key0, key1);
+        draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
         NQS_LAUNCHED();
         flags_kernel<<<g, 256, 0, s>>>(cc, b.n1, b.U, b.flags0, b.flags1);
         NQS_LAUNCHED();
@@ -314,6 +325,14 @@ int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t
         NQS_LAUNCHED();
     }
     return NQS_OK;
+}
+
+int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
+                uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
+                const TfCtx* tf, bool fixed_rows, cudaStream_t s) {
+    ProfScope ps("sample", s);
+    NQS_TRY(sampler_init(b, n_samples, seed, s));
+    return sampler_steps(mc, P, n_samples, max_unique, b, trace, trace_stride, tf, fixed_rows, s);
 }
 
 int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out, int64_t n,

@@ -302,13 +302,22 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
     const size_t sm_bytes = 228 * 1024;
     const size_t max_ctas = 512 / (size_t)tcols;
     smem = std::max(smem, sm_bytes / (max_ctas + 1) - 1024 + 1);
+    if (smem > 220 * 1024) { set_error("tensor-core GEMM: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
     CUtensorMap ma, mb;
     NQS_TRY(make_map(&ma, A, M, K, TC_BM));
     NQS_TRY(make_map(&mb, W, N, K, BN));
     dim3 grid((unsigned)(N / BN), (unsigned)((M + TC_BM - 1) / TC_BM));
     auto launch = [&](auto kernel) -> int {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm)", __FILE__, __LINE__);
+        // raise the dynamic shared-memory limit once per kernel (and device), outside any
+        // stream capture that later launches may run under
+        static int configured_device[8] = {-1, -1, -1, -1, -1, -1, -1, -1};   // per epilogue
+        int dev = 0;
+        NQS_CK(cudaGetDevice(&dev));
+        if (configured_device[epi & 7] != dev) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm)", __FILE__, __LINE__);
+            configured_device[epi & 7] = dev;
+        }
         kernel<<<grid, 128, smem, s>>>(ma, mb, bias, C, M, N, K, BN, tcols, stages);
         NQS_LAUNCHED();
         return NQS_OK;
