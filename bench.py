@@ -30,6 +30,12 @@ import synth  # noqa: E402
 DEFAULT_WORKLOAD = 3          # 20-qubit transformer: the first workload with BF16 and FP32 forms
 FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from the committed ncu capture
+# named beside it; None once the kernel has changed since that capture.
+NCU_TRAFFIC = {
+    ("n2_like_20q_tf64x2", "bf16"): (41.8e6, "profiles/tc_gemm_tf20q_bf16_ncu.md"),
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -231,8 +237,10 @@ def run_ours(args, rank, world, local):
             peak_b = peaks.get("hbm_gbs", 6400.0)
             ach_b = wbytes / k["launches"] / sec / 1e9
             intensity = work / max(wbytes, 1.0)
+            tr = NCU_TRAFFIC.get((cfg.name, prec))
             roofline = {"kernel": "tc_gemm_kernel (tcgen05, bf16 hi+lo)", "bound": "hbm", "achieved": ach_b,
-                        "peak": peak_b, "unit": "GB/s", "frac": ach_b / peak_b, "traffic": None,
+                        "peak": peak_b, "unit": "GB/s", "frac": ach_b / peak_b,
+                        "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
                         "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
                         "bytes_per_launch": wbytes / k["launches"], "flops_per_launch": work / k["launches"],
                         "flop_per_byte": intensity, "tensor_tflops": ach, "tensor_frac": ach / peak_t,
