@@ -431,7 +431,7 @@ int nqs_model_create(const nqs_model_desc* d, nqs_model_t* out) {
         const int dh = h / d->heads;
         if (dh != 16 && dh != 32) { delete m; set_error("transformer head size must be 16 or 32"); return NQS_ERR_UNSUPPORTED; }
         if (d->heads > 8) { delete m; set_error("transformer supports at most 8 heads"); return NQS_ERR_UNSUPPORTED; }
-        if ((size_t)n * (4 * h + 2) * 4 > 200 * 1024) {
+        if ((size_t)n * (4 * h + 5) * 4 > 200 * 1024) {
             delete m;
             set_error("transformer attention block (n x 4*d_model floats) exceeds shared memory");
             return NQS_ERR_UNSUPPORTED;

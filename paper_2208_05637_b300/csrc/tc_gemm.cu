@@ -113,8 +113,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+constexpr int TC_THREADS = 256;   // 8 warps: warps w and w+4 share TMEM lanes 32(w%4).., split columns
+
 template <int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const float* __restrict__ bias, void* __restrict__ Cv, int64_t M, int N, int K, int BN,
                int tmem_cols, int stages) {
@@ -191,9 +193,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (!got && threadIdx.x == 0) atomicExch(&g_tc_status, 2);
     if (got && s_ok) {
         tc_fence_after();
-        const int64_t row = m0 + warp * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < BN; c += 16) {
+        const int quad = warp & 3, half_w = warp >> 2;
+        const int64_t row = m0 + quad * 32 + lane;
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+        for (int c = half_w * 16; c < BN; c += 32) {
             float v16[16];
             tmem_ld16(tbase + (uint32_t)c, v16);
             if (row < M) {
@@ -318,7 +321,7 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm)", __FILE__, __LINE__);
             configured_device[epi & 7] = dev;
         }
-        kernel<<<grid, 128, smem, s>>>(ma, mb, bias, C, M, N, K, BN, tcols, stages);
+        kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, bias, C, M, N, K, BN, tcols, stages);
         NQS_LAUNCHED();
         return NQS_OK;
     };

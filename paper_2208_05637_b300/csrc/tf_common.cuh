@@ -242,22 +242,25 @@ attention_kernel(const float* __restrict__ qkv, int T, int d, int dh, void* __re
 }
 
 // Causal attention, one CTA per sequence (looping over sequences) with one warp per head.  The
-// sequence's whole [T x 3d] q|k|v block is read with coalesced loads into shared memory (row
-// stride 3d+1 against bank conflicts); lane l of warp h owns query rows l and l + 32 of head h
-// and runs an online (streaming) softmax over keys 0..t, accumulating P V in registers; the
-// [T x d] output is staged in shared memory and written back as whole rows.  DH = head size.
+// sequence's whole [T x 3d] q|k|v block is copied row by row with coalesced loads into shared
+// memory (row stride 3d + 4 floats: 16-byte aligned rows, so keys and values are read as
+// float4 broadcasts); lane l of warp h owns query rows l and l + 32 of head h and runs an online
+// (streaming) softmax over keys 0..t, accumulating P V in registers; the [T x d] output is staged
+// in shared memory and written back as whole rows.  DH = head size.
 template <int MODE, int DH>
 __global__ void __launch_bounds__(256)
 attention_seq_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int H, void* __restrict__ o) {
-    extern __shared__ float att_sm[];
-    const int ldq = 3 * d + 1, ldo = d + 1;
-    float* X = att_sm;                 // [T][3d+1]
+    extern __shared__ __align__(16) float att_sm[];
+    const int ldq = 3 * d + 4, ldo = d + 1;
+    float* X = att_sm;                 // [T][3d+4]
     float* O = att_sm + T * ldq;       // [T][d+1]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
     const float scale = rsqrtf((float)DH);
     for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
         const float* src = qkv + r * T * (int64_t)(3 * d);
-        for (int i = threadIdx.x; i < T * 3 * d; i += blockDim.x) X[(i / (3 * d)) * ldq + i % (3 * d)] = src[i];
+        for (int t = warp; t < T; t += nw)
+            for (int c = lane; c < 3 * d; c += 32) X[t * ldq + c] = src[(int64_t)t * 3 * d + c];
         __syncthreads();
         const int hd = warp;
         for (int t = lane; t < T; t += 32) {
@@ -266,17 +269,29 @@ attention_seq_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int
             for (int j = 0; j < DH; ++j) { q[j] = X[t * ldq + hd * DH + j] * scale; acc[j] = 0.f; }
             float m = -INFINITY, ssum = 0.f;
             for (int u = 0; u <= t; ++u) {
-                const float* kr = X + u * ldq + d + hd * DH;
-                const float* vr = X + u * ldq + 2 * d + hd * DH;
+                const float4* kr = reinterpret_cast<const float4*>(X + u * ldq + d + hd * DH);
+                const float4* vr = reinterpret_cast<const float4*>(X + u * ldq + 2 * d + hd * DH);
                 float sc = 0.f;
 #pragma unroll
-                for (int j = 0; j < DH; ++j) sc = fmaf(q[j], kr[j], sc);
+                for (int j4 = 0; j4 < DH / 4; ++j4) {
+                    const float4 k4 = kr[j4];
+                    sc = fmaf(q[4 * j4 + 0], k4.x, sc);
+                    sc = fmaf(q[4 * j4 + 1], k4.y, sc);
+                    sc = fmaf(q[4 * j4 + 2], k4.z, sc);
+                    sc = fmaf(q[4 * j4 + 3], k4.w, sc);
+                }
                 const float mn = fmaxf(m, sc);
                 const float corr = expf(m - mn);      // 0 on the first key (m = -inf)
                 const float e = expf(sc - mn);
                 ssum = ssum * corr + e;
 #pragma unroll
-                for (int j = 0; j < DH; ++j) acc[j] = fmaf(e, vr[j], acc[j] * corr);
+                for (int j4 = 0; j4 < DH / 4; ++j4) {
+                    const float4 v4 = vr[j4];
+                    acc[4 * j4 + 0] = fmaf(e, v4.x, acc[4 * j4 + 0] * corr);
+                    acc[4 * j4 + 1] = fmaf(e, v4.y, acc[4 * j4 + 1] * corr);
+                    acc[4 * j4 + 2] = fmaf(e, v4.z, acc[4 * j4 + 2] * corr);
+                    acc[4 * j4 + 3] = fmaf(e, v4.w, acc[4 * j4 + 3] * corr);
+                }
                 m = mn;
             }
             const float inv = 1.f / ssum;
@@ -284,8 +299,8 @@ attention_seq_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int
             for (int j = 0; j < DH; ++j) O[t * ldo + hd * DH + j] = acc[j] * inv;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < T * d; i += blockDim.x)
-            store_mode<MODE>(o, r * T + i / d, d, i % d, O[(i / d) * ldo + i % d]);
+        for (int t = warp; t < T; t += nw)
+            for (int c = lane; c < d; c += 32) store_mode<MODE>(o, r * T + t, d, c, O[t * ldo + c]);
         __syncthreads();
     }
 }
@@ -293,7 +308,7 @@ attention_seq_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int
 template <int MODE>
 inline cudaError_t launch_attention(const float* qkv, int64_t R, int T, int d, int H, void* o, cudaStream_t s) {
     const int dh = d / H;
-    const size_t smem = (size_t)(T * (3 * d + 1) + T * (d + 1)) * sizeof(float);
+    const size_t smem = (size_t)(T * (3 * d + 4) + T * (d + 1)) * sizeof(float);
     const unsigned grid = (unsigned)std::min<int64_t>(R, (int64_t)num_sms() * 8);
     if (dh == 16) {
         if (smem > 48 * 1024) cudaFuncSetAttribute(attention_seq_kernel<MODE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
