@@ -32,9 +32,7 @@ FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from the committed ncu capture
 # named beside it; None once the kernel has changed since that capture.
-NCU_TRAFFIC = {
-    ("n2_like_20q_tf64x2", "bf16"): (41.8e6, "profiles/tc_gemm_tf20q_bf16_ncu.md"),
-}
+NCU_TRAFFIC = {}
 
 
 def parse():

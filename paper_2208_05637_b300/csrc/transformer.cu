@@ -227,11 +227,11 @@ int with_dpl(int d, F&& f) {
 // ====================================================================== host side
 int64_t tf_seq_capacity(const ModelConst& mc) {
     // Sequences per pass: the pass's activations (h, a, qkv, o and the 4d MLP buffer, about
-    // 10*d floats per position) are kept near 256 MB.  Smaller, L2-resident passes lose more to
-    // the extra launches than they gain in bandwidth.
+    // 10*d floats per position) are kept near 1 GB.  Smaller, L2-resident passes lose more to
+    // the extra launches than they gain in bandwidth; larger ones leave fewer launch gaps.
     const int64_t per_seq = (int64_t)mc.n * mc.hidden * 10 * 4;
     int64_t R = 64;
-    while (R * 2 * per_seq <= (256ll << 20) && R < 8192) R *= 2;
+    while (R * 2 * per_seq <= (1024ll << 20) && R < 32768) R *= 2;
     return R;
 }
 
