@@ -196,7 +196,8 @@ int nqs_adam_step(float* params, const float* grad, float* m, float* v, int64_t 
 /* Diagnostic: the library's bf16 tensor-core GEMM on its own (the contraction inside the BF16
  * transformer path).  C[M,N] = A[M,K] . W[N,K]^T + bias with A, W bf16 row-major (device,
  * 16-byte aligned, K % 8 == 0), N % 16 == 0, fp32 accumulation; epilogue 0: C fp32 store,
- * 1: C bf16 = gelu_tanh(.), 2: C fp32 += (.); bias (device fp32[N]) may be NULL.  Synchronises
+ * 1: C bf16 = gelu_tanh(.), 2: C fp32 += (.), 4: C bf16[M, 2N] = (hi | lo) with hi = bf16(g),
+ * lo = bf16(g - hi), g = gelu_tanh(.); bias (device fp32[N]) may be NULL.  Synchronises
  * `stream`; returns NQS_ERR_TIMEOUT if a bounded device wait gave up. */
 int nqs_gemm_bf16(const void* A, const void* W, const float* bias, void* C, int64_t M, int N, int K,
                   int epilogue, void* stream);

@@ -13,7 +13,7 @@ SHAPES = [(128, 64, 64), (300, 192, 64), (1000, 256, 128), (517, 512, 128), (200
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
-@pytest.mark.parametrize("epi", [0, 1, 2])
+@pytest.mark.parametrize("epi", [0, 1, 2, 4])
 def test_tc_gemm_matches_fp32_reference(M, N, K, epi):
     import torch
     P = lib()
@@ -29,6 +29,16 @@ def test_tc_gemm_matches_fp32_reference(M, N, K, epi):
         want = torch.nn.functional.gelu(ref, approximate="tanh")
         err = (C.float() - want).abs()
         tol = 2e-5 * mass + 2 ** -7 * want.abs() + 1e-6
+    elif epi == 4:
+        # compensated GELU: hi in columns [0, N), lo = bf16(g - hi) in [N, 2N)
+        C = torch.empty(M, 2 * N, device="cuda", dtype=torch.bfloat16)
+        P.nqs_gemm_bf16(A, W, bias, C, epilogue=4)
+        want = torch.nn.functional.gelu(ref, approximate="tanh")
+        hi, lo = C[:, :N].float(), C[:, N:].float()
+        assert torch.equal(hi.to(torch.bfloat16).float(), hi)
+        assert bool(((lo.abs() <= 2 ** -8 * hi.abs()) | (hi == 0)).all())
+        err = (hi + lo - want).abs()
+        tol = 2e-5 * mass + 2 ** -15 * want.abs() + 1e-6
     elif epi == 2:
         C0 = torch.randn(M, N, device="cuda", generator=g)
         C = C0.clone()
