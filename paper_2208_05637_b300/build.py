@@ -30,7 +30,8 @@ def sources():
 
 def _digest(extra):
     h = hashlib.sha256()
-    for p in sources() + sorted(glob.glob(os.path.join(PKG, "csrc", "*.h"))) + \
+    for p in sources() + sorted(glob.glob(os.path.join(PKG, "csrc", "*.h")) +
+                                glob.glob(os.path.join(PKG, "csrc", "*.cuh"))) + \
             [os.path.join(ROOT, "include", "nqs.h")]:
         h.update(p.encode())
         with open(p, "rb") as f:

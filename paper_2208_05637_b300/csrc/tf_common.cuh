@@ -305,9 +305,285 @@ attention_seq_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int
     }
 }
 
+// Sixteen consecutive columns [col0, col0 + 16) of row `row` in the storage form of MODE
+// (see store_mode); col0 and width are multiples of 16.
+template <int MODE>
+__device__ __forceinline__ void store_mode16(void* base, int64_t row, int width, int col0, const float* v) {
+    if (MODE == ACT_F32 || MODE == ACT_F32_Q1 || MODE == ACT_F32_Q2) {
+        float w[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (MODE == ACT_F32) {
+                w[j] = v[j];
+            } else if (MODE == ACT_F32_Q1) {
+                w[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+            } else {
+                const float h = __bfloat162float(__float2bfloat16_rn(v[j]));
+                w[j] = h + __bfloat162float(__float2bfloat16_rn(v[j] - h));
+            }
+        }
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + row * width + col0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    } else {
+        __align__(16) __nv_bfloat16 hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            hi[j] = __float2bfloat16_rn(v[j]);
+            if (MODE == ACT_BF16X2) lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+        }
+        const int64_t stride = MODE == ACT_BF16X2 ? 2 * (int64_t)width : width;
+        uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(base) + row * stride + col0);
+        dh[0] = reinterpret_cast<const uint4*>(hi)[0];
+        dh[1] = reinterpret_cast<const uint4*>(hi)[1];
+        if (MODE == ACT_BF16X2) {
+            uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(base) + row * stride + width + col0);
+            dl[0] = reinterpret_cast<const uint4*>(lo)[0];
+            dl[1] = reinterpret_cast<const uint4*>(lo)[1];
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Dot product of a query row with a key row from shared memory, as two interleaved partial
+// sums (even and odd float4 pieces) for instruction-level parallelism.
+template <int DH>
+__device__ __forceinline__ float att_dot(const float (&q)[DH], const float4* __restrict__ k) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int j4 = 0; j4 < DH / 4; ++j4) {
+        const float4 k4 = k[j4];
+        float& sp = (j4 & 1) ? s1 : s0;
+        sp = fmaf(q[4 * j4 + 0], k4.x, sp);
+        sp = fmaf(q[4 * j4 + 1], k4.y, sp);
+        sp = fmaf(q[4 * j4 + 2], k4.z, sp);
+        sp = fmaf(q[4 * j4 + 3], k4.w, sp);
+    }
+    return s0 + s1;
+}
+
+// Online-softmax update of one row (running max m, normaliser l, unnormalised output acc) by
+// keys u and u+1 (scores s0, s1 in the log2 domain; value rows v0, v1), or by key u alone.
+template <int DH, bool PAIR>
+__device__ __forceinline__ void att_update(float s0, float s1, const float4* __restrict__ v0,
+                                           const float4* __restrict__ v1, float (&acc)[DH], float& m, float& l) {
+    const float mn = PAIR ? fmaxf(m, fmaxf(s0, s1)) : fmaxf(m, s0);
+    const float c = exp2f(m - mn);                 // 0 on the first key (m = -inf)
+    const float e0 = exp2f(s0 - mn);
+    const float e1 = PAIR ? exp2f(s1 - mn) : 0.f;
+    l = PAIR ? fmaf(l, c, e0 + e1) : fmaf(l, c, e0);
+    m = mn;
+#pragma unroll
+    for (int j4 = 0; j4 < DH / 4; ++j4) {
+        const float4 a = v0[j4];
+        float x0 = fmaf(e0, a.x, acc[4 * j4 + 0] * c), x1 = fmaf(e0, a.y, acc[4 * j4 + 1] * c);
+        float x2 = fmaf(e0, a.z, acc[4 * j4 + 2] * c), x3 = fmaf(e0, a.w, acc[4 * j4 + 3] * c);
+        if (PAIR) {
+            const float4 b = v1[j4];
+            x0 = fmaf(e1, b.x, x0); x1 = fmaf(e1, b.y, x1); x2 = fmaf(e1, b.z, x2); x3 = fmaf(e1, b.w, x3);
+        }
+        acc[4 * j4 + 0] = x0; acc[4 * j4 + 1] = x1; acc[4 * j4 + 2] = x2; acc[4 * j4 + 3] = x3;
+    }
+}
+
+// Keys [u0, u1) of the online softmax for query row qa, or for rows qa and qb sharing the key
+// and value loads.
+template <int DH, bool TWO>
+__device__ __forceinline__ void attend_keys(const float* __restrict__ kv, int LU, int VOFF, int u0, int u1,
+                                            const float (&qa)[DH], float (&aa)[DH], float& ma, float& la,
+                                            const float (&qb)[DH], float (&ab)[DH], float& mb, float& lb) {
+    int u = u0;
+    // two keys per step for a single row; the two-row form keeps one key per step (registers)
+    for (; !TWO && u + 1 < u1; u += 2) {
+        const float4* k0 = reinterpret_cast<const float4*>(kv + u * LU);
+        const float4* k1 = reinterpret_cast<const float4*>(kv + (u + 1) * LU);
+        const float4* v0 = reinterpret_cast<const float4*>(kv + u * LU + VOFF);
+        const float4* v1 = reinterpret_cast<const float4*>(kv + (u + 1) * LU + VOFF);
+        att_update<DH, true>(att_dot<DH>(qa, k0), att_dot<DH>(qa, k1), v0, v1, aa, ma, la);
+    }
+    for (; u < u1; ++u) {
+        const float4* k0 = reinterpret_cast<const float4*>(kv + u * LU);
+        const float4* v0 = reinterpret_cast<const float4*>(kv + u * LU + VOFF);
+        const float sa0 = att_dot<DH>(qa, k0);
+        if (TWO) att_update<DH, false>(att_dot<DH>(qb, k0), 0.f, v0, v0, ab, mb, lb);
+        att_update<DH, false>(sa0, 0.f, v0, v0, aa, ma, la);
+    }
+}
+
+// Query row (scaled) into q and a zeroed accumulator, for attention_grp_kernel.
+template <int DH>
+__device__ __forceinline__ void att_load_q(const float* __restrict__ src, bool act, float scale, float (&q)[DH],
+                                           float (&acc)[DH]) {
+#pragma unroll
+    for (int j4 = 0; j4 < DH / 4; ++j4) {
+        const float4 x = act ? __ldg(reinterpret_cast<const float4*>(src) + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        q[4 * j4 + 0] = x.x * scale;
+        q[4 * j4 + 1] = x.y * scale;
+        q[4 * j4 + 2] = x.z * scale;
+        q[4 * j4 + 3] = x.w * scale;
+    }
+#pragma unroll
+    for (int j = 0; j < DH; ++j) acc[j] = 0.f;
+}
+
+// Normalised output row acc / l into columns [col0, col0 + DH) of row `row`.
+template <int MODE, int DH>
+__device__ __forceinline__ void att_store_row(float (&acc)[DH], float l, void* o, int64_t row, int d, int col0) {
+    const float inv = 1.f / l;
+#pragma unroll
+    for (int j = 0; j < DH; ++j) acc[j] *= inv;
+#pragma unroll
+    for (int j0 = 0; j0 < DH; j0 += 16) store_mode16<MODE>(o, row, d, col0 + j0, acc + j0);
+}
+
+// Causal attention with lanes over (sequence, head) groups: a CTA stages the keys and values of
+// S sequences in shared memory (cp.async), lane l of every warp serves group (s = l / H,
+// h = l % H), and warp w takes the query-row pairs (p, T-1-p), p = w, w + warps, ...: the two
+// rows cost T + 1 key steps together, so every warp does the same work and every loop is
+// warp-uniform.  With DH = 16 the pair shares the key/value loads of keys 0..p.
+// Shared layout per sequence (floats): row u at u*LU, K of head h at h*LH, V at H*LH + h*LH,
+// LH = DH + 4, LU = 2*H*LH; sequence stride SS (padded by the host so that the eight lanes of a
+// quarter-warp read distinct 16-byte bank groups).
+constexpr int ATT_GRP_MAX_WARPS = 10;   // 320 threads, two CTAs per SM
+
+template <int MODE, int DH>
+__global__ void __launch_bounds__(ATT_GRP_MAX_WARPS * 32, 2)
+attention_grp_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int H, int S, int SS,
+                     void* __restrict__ o) {
+    extern __shared__ __align__(16) float att_sm[];
+    constexpr int LH = DH + 4;
+    const int LU = 2 * H * LH, VOFF = H * LH;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    // scores in the log2 domain: q is scaled by log2(e) / sqrt(DH), weights are exp2(s - max)
+    const float scale = rsqrtf((float)DH) * 1.4426950408889634f;
+    const int ld = 3 * d;
+    // staging: thread i copies float4 chunk cc = i % chunks_row of positions q = i / chunks_row,
+    // q + rows_step, ... (q = s*T + u); the chunk's offsets are fixed per thread
+    const int chunks_row = d / 2;                  // float4 chunks of K|V per position
+    const int rows_step = blockDim.x / chunks_row;
+    const int cc = threadIdx.x % chunks_row, q0 = threadIdx.x / chunks_row;
+    const int kv = cc / (d / 4), wch = cc % (d / 4);
+    const int soff = kv * VOFF + (wch / (DH / 4)) * LH + 4 * (wch % (DH / 4));
+    const bool lane_ok = lane < S * H;
+    const int ls = lane_ok ? lane / H : 0, lh = lane % H;
+    const int64_t nbatch = (R + S - 1) / S;
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        const int64_t r0 = b * S;
+        const int sv = (int)((R - r0) < S ? (R - r0) : S);
+        if (q0 < rows_step) {
+            const float* src = qkv + (r0 * T) * (int64_t)ld + d + 4 * cc;
+            int s_ = q0 / T, u = q0 % T;
+            for (int q = q0; q < sv * T; q += rows_step) {
+                cp_async16(att_sm + s_ * SS + u * LU + soff, src + (int64_t)q * ld);
+                u += rows_step;
+                while (u >= T) { u -= T; ++s_; }
+            }
+        }
+        const bool act = lane_ok && ls < sv;
+        const int64_t r = r0 + (act ? ls : 0);
+        const float* kvs = att_sm + ls * SS + lh * LH;
+        const int npairs = (T + 1) / 2;
+        const bool share = DH <= 16;               // the pair shares its key/value loads
+        float qa[DH], qb[DH], aa[DH], ab[DH];
+        // the query rows of the warp's first pair load while the keys and values are staged
+        if (warp < npairs) {
+            att_load_q<DH>(qkv + (r * T + warp) * (int64_t)ld + lh * DH, act, scale, qa, aa);
+            if (share) att_load_q<DH>(qkv + (r * T + T - 1 - warp) * (int64_t)ld + lh * DH, act, scale, qb, ab);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int p = warp; p < npairs; p += nw) {
+            const int ta = p, tb = T - 1 - p;
+            if (p != warp) {
+                att_load_q<DH>(qkv + (r * T + ta) * (int64_t)ld + lh * DH, act, scale, qa, aa);
+                if (share) att_load_q<DH>(qkv + (r * T + tb) * (int64_t)ld + lh * DH, act, scale, qb, ab);
+            }
+            float ma = -INFINITY, la = 0.f, mb = -INFINITY, lb = 0.f;
+            if (share && tb != ta) {
+                // keys 0..ta serve both rows, then row tb runs on alone
+                attend_keys<DH, true>(kvs, LU, VOFF, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
+                if (act) att_store_row<MODE, DH>(aa, la, o, r * T + ta, d, lh * DH);
+                attend_keys<DH, false>(kvs, LU, VOFF, ta + 1, tb + 1, qb, ab, mb, lb, qa, aa, ma, la);
+                if (act) att_store_row<MODE, DH>(ab, lb, o, r * T + tb, d, lh * DH);
+            } else {
+                attend_keys<DH, false>(kvs, LU, VOFF, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
+                if (act) att_store_row<MODE, DH>(aa, la, o, r * T + ta, d, lh * DH);
+                if (tb != ta) {
+                    att_load_q<DH>(qkv + (r * T + tb) * (int64_t)ld + lh * DH, act, scale, qa, aa);
+                    ma = -INFINITY; la = 0.f;
+                    attend_keys<DH, false>(kvs, LU, VOFF, 0, tb + 1, qa, aa, ma, la, qb, ab, mb, lb);
+                    if (act) att_store_row<MODE, DH>(aa, la, o, r * T + tb, d, lh * DH);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sequence stride (floats) of attention_grp_kernel's shared layout: the padding (a multiple of
+// four floats) that spreads the eight lanes of each quarter-warp over the most 16-byte bank
+// groups when they read the same key position of their (sequence, head) groups.
+inline int attention_grp_stride(int T, int H, int DH, int S) {
+    const int LH = DH + 4, LU = 2 * H * LH, base = T * LU;
+    int best = base, best_cost = 1 << 30;
+    for (int pad = 0; pad < 32; pad += 4) {
+        int cost = 0;
+        for (int q = 0; q < 4; ++q) {
+            int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int worst = 0;
+            for (int l = 8 * q; l < 8 * q + 8 && l < S * H; ++l) {
+                const int addr = (l / H) * (base + pad) + (l % H) * LH;
+                const int slot = (addr / 4) & 7;
+                worst = std::max(worst, ++used[slot]);
+            }
+            cost += worst;
+        }
+        if (cost < best_cost) { best_cost = cost; best = base + pad; }
+    }
+    return best;
+}
+
 template <int MODE>
 inline cudaError_t launch_attention(const float* qkv, int64_t R, int T, int d, int H, void* o, cudaStream_t s) {
     const int dh = d / H;
+    if (R <= 0) return cudaSuccess;
+    // grouped kernel: as many sequences per CTA as fill the 32 lanes (or ~110 KB of shared
+    // memory), when that keeps at least half of the lanes busy
+    if (32 % H == 0) {
+        const size_t seq_bytes = (size_t)T * 2 * H * (dh + 4) * sizeof(float) + 32 * sizeof(float);
+        const int S = std::min<int>(32 / H, (int)((110 * 1024) / seq_bytes));
+        if (S * H >= 16 && d / 2 <= ATT_GRP_MAX_WARPS * 32) {
+            // the dynamic shared-memory limit is raised once per kernel and device (outside any
+            // stream capture: the first launch of a shape is an eager one)
+            static int configured16 = -1, configured32 = -1;
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return e;
+            int& cfg = dh == 16 ? configured16 : configured32;
+            if (cfg != dev) {
+                e = dh == 16 ? cudaFuncSetAttribute(attention_grp_kernel<MODE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+                             : cudaFuncSetAttribute(attention_grp_kernel<MODE, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                if (e != cudaSuccess) return e;
+                cfg = dev;
+            }
+            const int SS = attention_grp_stride(T, H, dh, S);
+            const size_t smem = (size_t)S * SS * sizeof(float);
+            // one warp per query-row pair, and at least one thread per float4 of a position's K|V
+            const int warps = std::max(std::min((T + 1) / 2, ATT_GRP_MAX_WARPS), (d / 2 + 31) / 32);
+            const int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
+            const int64_t nbatch = (R + S - 1) / S;
+            const unsigned grid = (unsigned)std::min<int64_t>(nbatch, (int64_t)num_sms() * per_sm);
+            if (dh == 16) attention_grp_kernel<MODE, 16><<<grid, warps * 32, smem, s>>>(qkv, R, T, d, H, S, SS, o);
+            else attention_grp_kernel<MODE, 32><<<grid, warps * 32, smem, s>>>(qkv, R, T, d, H, S, SS, o);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = (size_t)(T * (3 * d + 4) + T * (d + 1)) * sizeof(float);
     const unsigned grid = (unsigned)std::min<int64_t>(R, (int64_t)num_sms() * 8);
     if (dh == 16) {
