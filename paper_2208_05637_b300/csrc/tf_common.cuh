@@ -27,9 +27,15 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
 
 __device__ __forceinline__ float logsig(float v) { return fminf(v, 0.f) - log1pf(expf(-fabsf(v))); }
 
+// GELU, tanh form: 0.5 x (1 + tanh(u)), u = sqrt(2/pi) (x + 0.044715 x^3).  Evaluated through
+// tanh(u) = 2 sigmoid(2u) - 1 as x / (1 + exp(-2u)), with exp(-2u) = exp2(x (c1 + c2 x^2)),
+// c1 = -2 sqrt(2/pi) log2(e), c2 = 0.044715 c1: one exp2 and one reciprocal.  For very negative
+// x the exponential overflows and the quotient is (-)0, the limit.
 __device__ __forceinline__ float gelu_tanh(float x) {
-    const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
-    return 0.5f * x * (1.f + tanhf(u));
+    constexpr float c1 = -2.f * 0.7978845608028654f * 1.4426950408889634f;
+    constexpr float c2 = c1 * 0.044715f;
+    const float e = exp2f(x * fmaf(c2, x * x, c1));
+    return __fdividef(x, 1.f + e);
 }
 
 template <class T>
