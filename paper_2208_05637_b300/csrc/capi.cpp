@@ -516,6 +516,7 @@ void nqs_model_destroy(nqs_model_t m) {
     if (m->graph.ev) cudaEventDestroy(m->graph.ev);
     if (m->graph.side) cudaStreamDestroy(m->graph.side);
     if (m->d_bf16) cudaFree(m->d_bf16);
+    if (m->d_scache) cudaFree(m->d_scache);
     delete m;
 }
 
@@ -606,13 +607,34 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
     if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
         tf_layout(c, m->mc, std::min(b.cap, tf_seq_capacity(m->mc)), tb);
         NQS_TRY(tf_weights(m, w, s));
+        // incremental forward when its cache (the keys and values of every step for every
+        // buffer slot, model-owned) stays within SAMPLER_CACHE_MAX_BYTES and the pass buffers
+        // hold one position of every slot
+        const int64_t need = tf_step_cache_bytes(m->mc, b.cap);
+        if (need <= SAMPLER_CACHE_MAX_BYTES && b.cap <= tb.R * m->mc.n) {
+            if (m->scache_bytes < (size_t)need) {
+                if (m->d_scache) NQS_CK(cudaFree(m->d_scache));
+                m->d_scache = nullptr;
+                m->scache_bytes = 0;
+                void* p = nullptr;
+                const cudaError_t e = cudaMalloc(&p, (size_t)need);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    set_error("sampler cache allocation failed");
+                    return NQS_ERR_ALLOC;
+                }
+                m->d_scache = p;
+                m->scache_bytes = (size_t)need;
+            }
+            sampler_bind_cache(b, m->mc, m->d_scache);
+        }
     }
     int64_t U = 0;
     const bool graphable = b.cap <= SAMPLER_GRAPH_MAX_CAP;
     SamplerGraph& G = m->graph;
     const bool same = G.n_samples == n_samples && G.max_unique == max_unique && G.ws == ws &&
                       G.trace == p_trace && G.trace_stride == trace_stride && G.params == m->d_params &&
-                      G.bf16 == (const void*)m->d_bf16;
+                      G.bf16 == (const void*)m->d_bf16 && G.cache == (const void*)b.kv;
     if (graphable && same && !G.failed && (G.exec || G.seen)) {
         // replay (capturing first if this shape has run once eagerly): the steps run on the
         // library's stream, ordered after the caller's stream by an event
@@ -649,7 +671,7 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
         if (graphable && !same) {
             graph_release(G);
             G.n_samples = n_samples; G.max_unique = max_unique; G.ws = ws; G.trace = p_trace;
-            G.trace_stride = trace_stride; G.params = m->d_params; G.bf16 = m->d_bf16;
+            G.trace_stride = trace_stride; G.params = m->d_params; G.bf16 = m->d_bf16; G.cache = b.kv;
             G.failed = false;
         }
         G.seen = graphable;

@@ -120,6 +120,7 @@ struct SamplerGraph {
     const float* trace = nullptr;
     const float* params = nullptr;
     const void* bf16 = nullptr;
+    const void* cache = nullptr;
     bool seen = false;              // this shape ran once eagerly; capture on the next call
     bool failed = false;            // capture not possible: stay eager for this shape
     cudaGraphExec_t exec = nullptr;
@@ -137,6 +138,8 @@ struct nqs_model_s {
     const float* d_params = nullptr;
     uint16_t* d_bf16 = nullptr;      // bf16 copies of the transformer GEMM weights (BF16 models)
     nqs::SamplerGraph graph;         // captured sampler of the last call shape
+    void* d_scache = nullptr;        // sampler cache of the incremental transformer forward
+    size_t scache_bytes = 0;
 };
 
 namespace nqs {
@@ -229,6 +232,16 @@ struct HeadArgsHost {
     float* p_out = nullptr;
     uint64_t* thr = nullptr;
     float* trace = nullptr;
+    int step_pos = -1;        // mode 2: h holds only this position (one row per prefix)
+};
+// Sampler cache of the incremental transformer forward: per layer l and step j a QKV slab of
+// cap rows x 3d floats at kv + ((l * n + j) * cap) * 3d (keys and values of the step-j
+// prefixes), and the ancestor table anc[r * n + j] = slot of prefix r's ancestor at step j.
+struct TfStepCache {
+    float* kv = nullptr;
+    int64_t cap = 0;
+    const int32_t* anc = nullptr;
+    const int64_t* Udev = nullptr;   // device count of live prefixes
 };
 int64_t tf_seq_capacity(const ModelConst& mc);
 void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b);
@@ -238,6 +251,9 @@ int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const u
                int64_t R, int T, TfBufs& b, cudaStream_t s);
 int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t R, int T,
              const TfBufs& b, const HeadArgsHost& ha, cudaStream_t s);
+int tf_step(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits, int64_t R, int k,
+            const TfStepCache& kc, TfBufs& b, cudaStream_t s);
+int64_t tf_step_cache_bytes(const ModelConst& mc, int64_t cap);
 int tf_segment_sum(const int64_t* seg, int64_t seg_stride, int64_t nseg, const float2* contrib,
                    int compensated, float* eloc, cudaStream_t s);
 int tf_logpsi(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
@@ -272,7 +288,14 @@ struct SamplerBufs {
     int64_t* pos1;       // cap+1
     int64_t* U;          // device scalars: U[0] current U
     int64_t cap;
+    // incremental transformer forward (all null when the conditionals are recomputed from
+    // scratch at every step): QKV slabs, ancestor tables (ping-pong), parent slots
+    float* kv = nullptr;
+    int32_t *ancA = nullptr, *ancB = nullptr;
+    int32_t *par = nullptr, *par2 = nullptr;
 };
+// Binds the model-owned cache memory (tf_step_cache_bytes(mc, b.cap) bytes) to b.
+void sampler_bind_cache(SamplerBufs& b, const ModelConst& mc, void* mem);
 int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b);
 int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
                 uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
@@ -283,6 +306,9 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
                   bool fixed_rows, cudaStream_t s);
 // Parent buffers up to this size run the sampler with fixed-size passes and a CUDA graph.
 constexpr int64_t SAMPLER_GRAPH_MAX_CAP = 8192;
+// Largest model-owned cache of the incremental transformer sampler; larger buffers recompute
+// the prefixes at every step.
+constexpr int64_t SAMPLER_CACHE_MAX_BYTES = 2ll << 30;
 
 int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out,
                         int64_t n, cudaStream_t s);

@@ -105,7 +105,8 @@ __device__ __forceinline__ int64_t upper(const uint64_t* bits, int64_t U, uint64
 __global__ void merge_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
                              const int64_t* __restrict__ n1, const int64_t* __restrict__ pos0,
                              const int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
-                             uint64_t qbit, uint64_t* __restrict__ nbits, int64_t* __restrict__ ncnt) {
+                             uint64_t qbit, uint64_t* __restrict__ nbits, int64_t* __restrict__ ncnt,
+                             int32_t* __restrict__ npar) {
     const int64_t U = *Udev;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < U; s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c1 = n1[s], c0 = cnt[s] - c1;
@@ -114,12 +115,14 @@ __global__ void merge_kernel(const uint64_t* __restrict__ bits, const int64_t* _
             const int64_t r = pos1[upper(bits, U, qbit, bits[s])];
             nbits[pos0[s] + r] = bits[s];
             ncnt[pos0[s] + r] = c0;
+            if (npar) npar[pos0[s] + r] = (int32_t)s;
         }
         if (c1 > 0) {
             const uint64_t key = bits[s] | qbit;
             const int64_t r = pos0[upper(bits, U, 0, key)];
             nbits[pos1[s] + r] = key;
             ncnt[pos1[s] + r] = c1;
+            if (npar) npar[pos1[s] + r] = (int32_t)s;
         }
     }
 }
@@ -133,7 +136,8 @@ __global__ void set_u_kernel(int64_t* Udev, const int64_t* pos0, const int64_t* 
 __global__ void __launch_bounds__(1024)
 evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
              int64_t* __restrict__ Udev, int64_t max_unique, uint64_t* __restrict__ obits,
-             int64_t* __restrict__ ocnt, int32_t* __restrict__ did) {
+             int64_t* __restrict__ ocnt, int32_t* __restrict__ did, const int32_t* __restrict__ par,
+             int32_t* __restrict__ opar) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t s_prefix, s_need;
     __shared__ int64_t warp_sums[32];
@@ -206,6 +210,7 @@ evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
             const int64_t pos = carry_keep + warp_sums[warp] + incl - keep;
             obits[pos] = bits[s];
             ocnt[pos] = cnt[s];
+            if (par) opar[pos] = par[s];
         }
         carry_keep += carry_sh;
         carry_eq += tot_eq;
@@ -216,12 +221,28 @@ evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
 
 __global__ void copy_back_kernel(const int32_t* __restrict__ did, const int64_t* __restrict__ Udev,
                                  const uint64_t* __restrict__ sb, const int64_t* __restrict__ sc,
-                                 uint64_t* __restrict__ db, int64_t* __restrict__ dc) {
+                                 uint64_t* __restrict__ db, int64_t* __restrict__ dc,
+                                 const int32_t* __restrict__ sp, int32_t* __restrict__ dp) {
     if (!*did) return;
     const int64_t U = *Udev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < U; i += (int64_t)gridDim.x * blockDim.x) {
         db[i] = sb[i];
         dc[i] = sc[i];
+        if (sp) dp[i] = sp[i];
+    }
+}
+
+// Ancestor table of the step-(k+1) prefixes: slot i (child of step-k slot par[i]) inherits its
+// parent's ancestors at steps 0..k-1, and its ancestor at step k is the parent itself.
+__global__ void anc_gather_kernel(const int32_t* __restrict__ par, const int32_t* __restrict__ anc_old,
+                                  int32_t* __restrict__ anc_new, const int64_t* __restrict__ Udev, int n, int k) {
+    const int64_t U = *Udev;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < U * (k + 1);
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / (k + 1);
+        const int j = (int)(e % (k + 1));
+        const int32_t p = par[i];
+        anc_new[i * n + j] = j < k ? anc_old[(int64_t)p * n + j] : p;
     }
 }
 
@@ -270,6 +291,15 @@ static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* 
         NQS_CK(cudaMemcpyAsync(&U, Udev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         NQS_CK(cudaStreamSynchronize(s));
     }
+    if (b.kv) {
+        // incremental: position k only, earlier keys and values from the cache
+        TfStepCache kc;
+        kc.kv = b.kv; kc.cap = b.cap; kc.anc = b.ancA; kc.Udev = Udev;
+        NQS_TRY(tf_step(mc, P, *tf->w, bits, U, k, kc, *tf->b, s));
+        HeadArgsHost ha{};
+        ha.mode = 2; ha.p_out = b.p; ha.thr = b.thr; ha.trace = trace; ha.step_pos = k;
+        return tf_heads(mc, P, bits, U, 1, *tf->b, ha, s);
+    }
     for (int64_t lo = 0; lo < U; lo += tf->b->R) {
         const int64_t R = std::min(tf->b->R, U - lo);
         NQS_TRY(tf_forward(mc, P, *tf->w, bits + lo, R, k + 1, *tf->b, s));
@@ -278,6 +308,15 @@ static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* 
         NQS_TRY(tf_heads(mc, P, bits + lo, R, k + 1, *tf->b, ha, s));
     }
     return NQS_OK;
+}
+
+void sampler_bind_cache(SamplerBufs& b, const ModelConst& mc, void* mem) {
+    Carver c(mem);
+    b.kv = c.take<float>((int64_t)mc.n * mc.layers * b.cap * 3 * mc.hidden);
+    b.ancA = c.take<int32_t>(b.cap * mc.n);
+    b.ancB = c.take<int32_t>(b.cap * mc.n);
+    b.par = c.take<int32_t>(b.cap);
+    b.par2 = c.take<int32_t>(b.cap);
 }
 
 int sampler_init(SamplerBufs& b, int64_t n_samples, uint64_t seed, cudaStream_t s) {
@@ -306,7 +345,7 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         NQS_LAUNCHED();
         NQS_TRY(launch_scan_i64(b.flags0, b.cap, b.U, b.pos0, s));
         NQS_TRY(launch_scan_i64(b.flags1, b.cap, b.U, b.pos1, s));
-        merge_kernel<<<g, 256, 0, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc);
+        merge_kernel<<<g, 256, 0, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc, b.par);
         NQS_LAUNCHED();
         set_u_kernel<<<1, 1, 0, s>>>(b.U, b.pos0, b.pos1);
         NQS_LAUNCHED();
@@ -314,10 +353,15 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         std::swap(cc, nc);
         if (max_unique < n_samples) {
             // evict into the spare buffer, then copy back so (cb, cc) stays current
-            evict_kernel<<<1, 1024, 0, s>>>(cb, cc, b.U, max_unique, nb, nc, did);
+            evict_kernel<<<1, 1024, 0, s>>>(cb, cc, b.U, max_unique, nb, nc, did, b.par, b.par2);
             NQS_LAUNCHED();
-            copy_back_kernel<<<g, 256, 0, s>>>(did, b.U, nb, nc, cb, cc);
+            copy_back_kernel<<<g, 256, 0, s>>>(did, b.U, nb, nc, cb, cc, b.par2, b.par);
             NQS_LAUNCHED();
+        }
+        if (b.kv && k + 1 < mc.n) {
+            anc_gather_kernel<<<grid_for(b.cap * (k + 1)), 256, 0, s>>>(b.par, b.ancA, b.ancB, b.U, mc.n, k);
+            NQS_LAUNCHED();
+            std::swap(b.ancA, b.ancB);
         }
     }
     if (cb != b.bitsA) {

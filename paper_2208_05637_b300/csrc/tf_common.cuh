@@ -76,17 +76,18 @@ __device__ __forceinline__ void store_mode(void* base, int64_t row, int width, i
 }
 
 // ---------------------------------------------------------------- embedding + first LayerNorm
-// One warp per row (sequence r, position t).  Writes h (fp32) and a = LN1_0(h) (T_ACT).
+// One warp per row (sequence r, position t = t0 + row % T).  Writes h (fp32) and
+// a = LN1_0(h) (T_ACT).
 template <int MODE, int DPL>   // DPL = d / 32 values per lane
 __global__ void __launch_bounds__(256)
 embed_ln_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
-                int64_t R, int T, float* __restrict__ h, void* __restrict__ a) {
+                int64_t R, int T, int t0, float* __restrict__ h, void* __restrict__ a) {
     const int d = mc.hidden;
     const int lane = threadIdx.x & 31;
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= R * T) return;
     const int64_t r = row / T;
-    const int t = (int)(row % T);
+    const int t = t0 + (int)(row % T);
     const int tok = t == 0 ? 2 : (int)((bits[r] >> mc.order[t - 1]) & 1ull);
     float v[DPL];
     float s = 0.f;

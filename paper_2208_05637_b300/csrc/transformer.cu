@@ -37,6 +37,7 @@ struct HeadArgs {
     float* p_out;              // mode 2
     uint64_t* thr;
     float* trace;
+    int step_pos;              // mode 2 with h holding only position step_pos (T = 1), else -1
 };
 
 template <int DPL>
@@ -68,7 +69,7 @@ heads_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restr
         for (int i = 0; i < DPL; ++i) y[i] = (y[i] - mu) * rstd * g[i] + bb[i];
     };
     if (args.mode == 2) {
-        const int k = T - 1;
+        const int k = args.step_pos >= 0 ? args.step_pos : T - 1;
         int ones0 = 0, ones1 = 0;
         for (int t = 0; t < k; ++t) {
             const int b = (int)((x >> mc.order[t]) & 1ull);
@@ -82,7 +83,7 @@ heads_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restr
         else if (c >= need) p = 0.f;
         else {
             float y[DPL];
-            lnf_row(k, y);
+            lnf_row(args.step_pos >= 0 ? 0 : k, y);
             float a = 0.f;
 #pragma unroll
             for (int i = 0; i < DPL; ++i) a = fmaf(y[i], hw[i], a);
@@ -156,6 +157,46 @@ heads_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restr
         ci = sre * ri + sim * rr;
     }
     args.contrib[grow] = make_float2(cr, ci);
+}
+
+// Attention of position k for R prefixes whose keys and values of positions j < k sit in the
+// per-step QKV slabs of the sampler cache (slab j holds [cap][3d] for the prefixes of step j;
+// anc[r * n + j] is the slot of prefix r's ancestor at step j; position k is row r of slab k).
+// One thread per (prefix, head), keys in order j = 0..k (the loop is uniform across threads).
+template <int MODE, int DH>
+__global__ void __launch_bounds__(256)
+attention_step_kernel(const float* __restrict__ slab0, int64_t slab_stride, int64_t cap,
+                      const int32_t* __restrict__ anc, int n, int k, const int64_t* __restrict__ Udev,
+                      int64_t R, int d, int H, void* __restrict__ o) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t U = min(*Udev, R);
+    if (i >= U * H) return;
+    const int64_t r = i / H;
+    const int h = (int)(i % H);
+    const int ld = 3 * d;
+    const float scale = rsqrtf((float)DH) * 1.4426950408889634f;   // log2 domain
+    const float* own = slab0 + (int64_t)k * slab_stride + r * ld;
+    float q[DH], acc[DH];
+#pragma unroll
+    for (int j4 = 0; j4 < DH / 4; ++j4) {
+        const float4 x = reinterpret_cast<const float4*>(own + h * DH)[j4];
+        q[4 * j4] = x.x * scale; q[4 * j4 + 1] = x.y * scale; q[4 * j4 + 2] = x.z * scale; q[4 * j4 + 3] = x.w * scale;
+    }
+#pragma unroll
+    for (int j = 0; j < DH; ++j) acc[j] = 0.f;
+    float m = -INFINITY, l = 0.f;
+    for (int j = 0; j <= k; ++j) {
+        int64_t slot = r;
+        if (j < k) {
+            slot = anc[r * n + j];
+            slot = slot < 0 ? 0 : (slot >= cap ? cap - 1 : slot);
+        }
+        const float* row = slab0 + (int64_t)j * slab_stride + slot * ld;
+        const float4* kr = reinterpret_cast<const float4*>(row + d + h * DH);
+        const float4* vr = reinterpret_cast<const float4*>(row + 2 * d + h * DH);
+        att_update<DH, false>(att_dot<DH>(q, kr), 0.f, vr, vr, acc, m, l);
+    }
+    att_store_row<MODE, DH>(acc, l, o, r, d, h * DH);
 }
 
 // Per-sample sum of the row contributions (TwoSum), one CTA per sample.
@@ -322,7 +363,7 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
     const int64_t M = R * T;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
-        embed_ln_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(mc, P, bits, R, T, b.h, b.a);
+        embed_ln_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(mc, P, bits, R, T, 0, b.h, b.a);
         NQS_LAUNCHED();
         for (int l = 0; l < mc.layers; ++l) {
             NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
@@ -354,6 +395,64 @@ int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const u
     return tf_forward_mode<ACT_BF16>(mc, P, w, bits, R, T, b, s);
 }
 
+// Position k of R prefixes (bits) for the sampler, with the keys and values of positions < k
+// read from the cache (kc) and those of position k written into slab k: the forward of one
+// position per prefix, leaving its final residual stream in b.h (R rows).
+template <int MODE>
+static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
+                        int64_t R, int k, const TfStepCache& kc, TfBufs& b, cudaStream_t s) {
+    const int d = mc.hidden, H = mc.heads, dh = d / H;
+    const int64_t layer_stride = (int64_t)mc.n * kc.cap * 3 * d;   // slabs of one layer
+    const int64_t slab_stride = kc.cap * 3 * d;
+    return with_dpl(d, [&](auto dpl) -> int {
+        constexpr int DPL = decltype(dpl)::value;
+        embed_ln_kernel<MODE, DPL><<<blocks_for(R, 8), 256, 0, s>>>(mc, P, bits, R, 1, k, b.h, b.a);
+        NQS_LAUNCHED();
+        for (int l = 0; l < mc.layers; ++l) {
+            float* slab0 = kc.kv + l * layer_stride;
+            NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, slab0 + k * slab_stride, R, 3 * d, d, TF_EPI_STORE,
+                            P + mc.bqkv[l], s));
+            {
+                ProfScope ps("tf_attention", s);
+                const int64_t threads = R * H;
+                const unsigned grid = (unsigned)((threads + 255) / 256);
+                if (dh == 16)
+                    attention_step_kernel<MODE, 16><<<grid, 256, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
+                                                                         kc.Udev, R, d, H, b.o);
+                else
+                    attention_step_kernel<MODE, 32><<<grid, 256, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
+                                                                         kc.Udev, R, d, H, b.o);
+                NQS_LAUNCHED();
+            }
+            NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, R, d, d, TF_EPI_RESID, P + mc.bo[l], s));
+            layernorm_kernel<MODE, DPL><<<blocks_for(R, 8), 256, 0, s>>>(b.h, R, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
+            NQS_LAUNCHED();
+            NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, R, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
+            NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, R, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
+            if (l + 1 < mc.layers) {
+                layernorm_kernel<MODE, DPL><<<blocks_for(R, 8), 256, 0, s>>>(b.h, R, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
+                NQS_LAUNCHED();
+            }
+        }
+        return NQS_OK;
+    });
+}
+
+int tf_step(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits, int64_t R, int k,
+            const TfStepCache& kc, TfBufs& b, cudaStream_t s) {
+    if (R > kc.cap) { set_error("sampler step: more prefixes than the cache holds"); return NQS_ERR_CAPACITY; }
+    if (mc.precision != NQS_PREC_BF16) return tf_step_mode<ACT_F32>(mc, P, w, bits, R, k, kc, b, s);
+    if (mc.compensated) return tf_step_mode<ACT_BF16X2>(mc, P, w, bits, R, k, kc, b, s);
+    return tf_step_mode<ACT_BF16>(mc, P, w, bits, R, k, kc, b, s);
+}
+
+int64_t tf_step_cache_bytes(const ModelConst& mc, int64_t cap) {
+    const int64_t slabs = (int64_t)mc.n * mc.layers * cap * 3 * mc.hidden * (int64_t)sizeof(float);
+    const int64_t anc = 2 * cap * (int64_t)mc.n * (int64_t)sizeof(int32_t);
+    const int64_t par = 2 * cap * (int64_t)sizeof(int32_t);
+    return slabs + anc + par + 5 * 256;   // five 256-byte aligned pieces
+}
+
 int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t R, int T,
              const TfBufs& b, const HeadArgsHost& ha, cudaStream_t s) {
     HeadArgs a{};
@@ -361,6 +460,7 @@ int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t
     a.ph_x = ha.ph_x; a.seg = ha.seg; a.seg_stride = ha.seg_stride; a.nseg = ha.nseg;
     a.row0 = ha.row0; a.S = ha.S; a.contrib = ha.contrib; a.p_out = ha.p_out; a.thr = ha.thr;
     a.trace = ha.trace;
+    a.step_pos = ha.step_pos;
     return with_dpl(mc.hidden, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
         ProfScope ps("tf_heads", s);
