@@ -211,7 +211,8 @@ def run_ours(args, rank, world, local):
     kern = {}
     for name in ("sample", "logpsi_rows", "sweep_count", "term_sweep", "eloc_rows", "made_backward",
                  "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_attention",
-                 "tf_heads", "tf_backward"):
+                 "tf_heads", "tf_backward", "bwd_recompute", "bwd_heads", "bwd_mlp", "bwd_attention",
+                 "bwd_embed"):
         tms, cnt = P.profile_read(name)
         if cnt:
             kern[name] = {"ms_total": tms, "launches": cnt, "ms_per_launch": tms / cnt}

@@ -9,6 +9,8 @@
 // attention, Wqkv, LN1) backward; finally the embeddings.  Weight gradients are reductions
 // over all rows of the chunk, done in fixed order (split-K partials reduced in order), so
 // results are bit-reproducible run to run.
+#include <memory>
+
 #include "tf_common.cuh"
 
 namespace nqs {
@@ -21,8 +23,6 @@ __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.f + th) + 0.5f * x * (1.f - th * th) * k * (1.f + 3.f * 0.044715f * x * x);
 }
 
-template <class T>
-__device__ __forceinline__ float ldf(const T* p) { return (float)*p; }
 
 __global__ void embed_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
                              int64_t R, int T, float* __restrict__ h) {
@@ -235,10 +235,13 @@ attention_bwd_kernel(const float* __restrict__ qkv, const float* __restrict__ do
 }
 
 // ---------------------------------------------------------------- deterministic reductions
-constexpr int CS_ROWS = 1024;
-__global__ void colsum_partial_kernel(const float* __restrict__ X, int64_t ld, int64_t M, int ncols,
-                                      float* __restrict__ part) {
+// Column sums of one or two matrices X0, X1 (same shape; blockIdx.z picks one): stage 1 sums
+// chunks of CS_ROWS rows per column, stage 2 adds the chunk sums in chunk order.
+constexpr int CS_ROWS = 128;
+__global__ void colsum_partial_kernel(const float* __restrict__ X0, const float* __restrict__ X1, int64_t ld,
+                                      int64_t M, int ncols, float* __restrict__ part) {
     __shared__ float red[8][33];
+    const float* X = blockIdx.z ? X1 : X0;
     const int c = blockIdx.x * 32 + threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * CS_ROWS;
     float s = 0.f;
@@ -249,95 +252,160 @@ __global__ void colsum_partial_kernel(const float* __restrict__ X, int64_t ld, i
     if (threadIdx.y == 0 && c < ncols) {
         float t = 0.f;
         for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-        part[(int64_t)blockIdx.y * ncols + c] = t;
+        part[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * ncols + c] = t;
     }
 }
 
-__global__ void colsum_final_kernel(const float* __restrict__ part, int nchunks, int ncols, float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
+// Stage 2: one warp per (matrix, column); lane l adds chunks l, l + 32, ... in order, then a
+// fixed shuffle tree (deterministic).
+__global__ void colsum_final_kernel(const float* __restrict__ part, int nchunks, int ncols, int nmat,
+                                    float* __restrict__ out0, float* __restrict__ out1) {
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= nmat * ncols) return;
+    const int z = e / ncols, c = e % ncols;
     float s = 0.f;
-    for (int i = 0; i < nchunks; ++i) s += part[(int64_t)i * ncols + c];
-    out[c] += s;
+    for (int i = lane; i < nchunks; i += 32) s += part[((int64_t)z * nchunks + i) * ncols + c];
+    s = warp_sum(s);
+    if (lane == 0) (z ? out1 : out0)[c] += s;
 }
 
-constexpr int OP_T = 32;
-template <class T_ACT>
+// Weight (and bias) gradients of a dense layer, split over row ranges: partial z holds
+//   dW[o][i] = sum_b delta[b][o] act[b][i]   and   db[o] = sum_b delta[b][o]
+// over rows b of its range, at part + z * (out_dim * in_dim + out_dim) (weights, then bias).
+// 64 x 64 output tiles, 16 rows per shared-memory stage (the next stage is fetched into
+// registers while the current one is used), 4 x 4 outputs per thread.
+constexpr int OP_B = 64, OP_K = 16;
 __global__ void __launch_bounds__(256)
-outer_partial_kernel(const float* __restrict__ delta, int64_t ld_d, const T_ACT* __restrict__ act,
+outer_partial_kernel(const float* __restrict__ delta, int64_t ld_d, const float* __restrict__ act,
                      int64_t ld_a, int64_t M, int out_dim, int in_dim, int64_t rows_per_split,
                      float* __restrict__ part) {
-    __shared__ float sd[OP_T][OP_T + 1];
-    __shared__ float sa[OP_T][OP_T + 1];
-    const int o0 = blockIdx.y * OP_T, i0 = blockIdx.x * OP_T;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    __shared__ __align__(16) float sd[2][OP_K][OP_B + 4];
+    __shared__ __align__(16) float sa[2][OP_K][OP_B + 4];
+    const int o0 = blockIdx.y * OP_B, i0 = blockIdx.x * OP_B;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
     const int64_t b_lo = (int64_t)blockIdx.z * rows_per_split;
     const int64_t b_hi = min(M, b_lo + rows_per_split);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t b0 = b_lo; b0 < b_hi; b0 += OP_T) {
-        for (int rr = ty; rr < OP_T; rr += 8) {
-            const int64_t b = b0 + rr;
-            sd[rr][tx] = (b < b_hi && o0 + tx < out_dim) ? delta[b * ld_d + o0 + tx] : 0.f;
-            sa[rr][tx] = (b < b_hi && i0 + tx < in_dim) ? ldf(act + b * ld_a + i0 + tx) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int rr = 0; rr < OP_T; ++rr) {
-            const float a = sa[rr][tx];
+    // fetch roles: rows (tid >> 6) + 4 q, column tid & 63
+    const int fr = tid >> 6, fc = tid & 63;
+    float rd[4], ra[4];
+    auto fetch = [&](int64_t b0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(sd[rr][ty * 4 + q], a, acc[q]);
+        for (int q = 0; q < 4; ++q) {
+            const int64_t b = b0 + fr + 4 * q;
+            rd[q] = (b < b_hi && o0 + fc < out_dim) ? delta[b * ld_d + o0 + fc] : 0.f;
+            ra[q] = (b < b_hi && i0 + fc < in_dim) ? act[b * ld_a + i0 + fc] : 0.f;
         }
-        __syncthreads();
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            sd[buf][fr + 4 * q][fc] = rd[q];
+            sa[buf][fr + 4 * q][fc] = ra[q];
+        }
+    };
+    float acc[4][4] = {};
+    float accb[4] = {0.f, 0.f, 0.f, 0.f};
+    fetch(b_lo);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t b0 = b_lo; b0 < b_hi; b0 += OP_K) {
+        const bool more = b0 + OP_K < b_hi;
+        if (more) fetch(b0 + OP_K);
+#pragma unroll
+        for (int kk = 0; kk < OP_K; ++kk) {
+            const float4 dv = *reinterpret_cast<const float4*>(&sd[buf][kk][ty * 4]);
+            const float4 av = *reinterpret_cast<const float4*>(&sa[buf][kk][tx * 4]);
+            const float dq[4] = {dv.x, dv.y, dv.z, dv.w}, aq[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                accb[q] += dq[q];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[q][j] = fmaf(dq[q], aq[j], acc[q][j]);
+            }
+        }
+        if (more) {
+            stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
     }
-    const int i = i0 + tx;
+    const int64_t stride = (int64_t)out_dim * in_dim + out_dim;
+    float* pz = part + (int64_t)blockIdx.z * stride;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int o = o0 + ty * 4 + q;
-        if (o < out_dim && i < in_dim) part[((int64_t)blockIdx.z * out_dim + o) * in_dim + i] = acc[q];
+        if (o >= out_dim) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = i0 + tx * 4 + j;
+            if (i < in_dim) pz[(int64_t)o * in_dim + i] = acc[q][j];
+        }
+        if (blockIdx.x == 0 && tx == 0) pz[(int64_t)out_dim * in_dim + o] = accb[q];
     }
 }
 
-__global__ void outer_final_kernel(const float* __restrict__ part, int nsplit, int64_t n, float* __restrict__ dW) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// Stage 2: dW += sum of the partials (in split order); db += its sums when db is given.
+__global__ void outer_final_kernel(const float* __restrict__ part, int nsplit, int out_dim, int in_dim,
+                                   float* __restrict__ dW, float* __restrict__ db) {
+    const int64_t nw = (int64_t)out_dim * in_dim, stride = nw + out_dim;
+    const int64_t n = db ? stride : nw;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.f;
-        for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * n + i];
-        dW[i] += s;
+#pragma unroll 8
+        for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * stride + e];
+        if (e < nw) dW[e] += s;
+        else db[e - nw] += s;
     }
 }
 
-// Embedding gradients, deterministic two-stage sums.  Stage 1: CTA (column tile, chunk of
-// EB_ROWS sequences) sums its sequences for every position and for each token id.
+// Embedding gradients, deterministic two-stage sums.  Stage 1: CTA (position t, chunk of
+// EB_ROWS sequences), thread j = column: the chunk's sums of dh[., t, j] over the sequences
+// whose token at t is 0 (or the start token, t = 0) and over those whose token is 1.
 constexpr int EB_ROWS = 64;
 __global__ void embed_bwd_partial_kernel(ModelConst mc, const uint64_t* __restrict__ bits,
                                          const float* __restrict__ dh, int64_t R, float* __restrict__ part) {
     const int d = mc.hidden, n = mc.n;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x, j = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * EB_ROWS, r1 = min(R, r0 + EB_ROWS);
     if (j >= d) return;
-    float* out = part + (int64_t)blockIdx.y * (n + 3) * d;   // [n positions + 3 tokens][d]
-    float tok[3] = {0.f, 0.f, 0.f};
-    for (int t = 0; t < n; ++t) {
-        float s = 0.f;
-        for (int64_t r = r0; r < r1; ++r) {
-            const float g = dh[(r * n + t) * d + j];
-            s += g;
-            const int k = t == 0 ? 2 : (int)((bits[r] >> mc.order[t - 1]) & 1ull);
-            tok[k] += g;
-        }
-        out[t * d + j] = s;
+    float s0 = 0.f, s1 = 0.f;
+    for (int64_t r = r0; r < r1; ++r) {
+        const float g = dh[(r * n + t) * d + j];
+        const bool one = t > 0 && ((bits[r] >> mc.order[t - 1]) & 1ull);
+        if (one) s1 += g; else s0 += g;
     }
-    for (int k = 0; k < 3; ++k) out[(n + k) * d + j] = tok[k];
+    float* out = part + (((int64_t)blockIdx.y * n + t) * 2) * d;   // [chunk][t][token 0/1][d]
+    out[j] = s0;
+    out[d + j] = s1;
 }
 
+// Stage 2: pos_emb[t] += sum over chunks of both sums; tok_emb[0/1] += sums over chunks and
+// positions t >= 1; tok_emb[2] (start token) += the position-0 sums.
 __global__ void embed_bwd_final_kernel(ModelConst mc, const float* __restrict__ part, int nchunks,
                                        float* __restrict__ grad) {
     const int d = mc.hidden, n = mc.n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (n + 3) * d) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (n + 3) * d) return;
+    const int j = e % d;
+    auto at = [&](int c, int t, int k) { return part[(((int64_t)c * n + t) * 2 + k) * d + j]; };
     float s = 0.f;
-    for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * (n + 3) * d + i];
-    if (i < n * d) grad[mc.pos_emb + i] += s;
-    else grad[mc.tok_emb + (i - n * d)] += s;
+    if (e < n * d) {
+        const int t = e / d;
+        for (int c = 0; c < nchunks; ++c) s += at(c, t, 0) + at(c, t, 1);
+        grad[mc.pos_emb + e] += s;
+        return;
+    }
+    const int k = e / d - n;   // token id
+    if (k == 2) {
+        for (int c = 0; c < nchunks; ++c) s += at(c, 0, 0);
+    } else {
+        for (int c = 0; c < nchunks; ++c)
+            for (int t = 1; t < n; ++t) s += at(c, t, k);
+    }
+    grad[mc.tok_emb + k * d + j] += s;
 }
 
 inline int gs(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16)); }
@@ -395,9 +463,10 @@ void bwd_layout(Carver& c, const ModelConst& mc, int64_t R, BwdBufs& b, float** 
     b.HF = c.take<float>(M * d);
     b.DL = c.take<float>(M);
     b.DPH = c.take<float>(R * 4);
-    b.nsplit = std::max<int64_t>(1, std::min<int64_t>(64, M / 512));
-    b.part_elems = std::max<int64_t>(b.nsplit * 4 * d * d, ((M + CS_ROWS - 1) / CS_ROWS) * 4 * d);
-    b.part_elems = std::max<int64_t>(b.part_elems, ((R + 63) / 64) * (n + 3) * d);
+    b.nsplit = std::max<int64_t>(1, std::min<int64_t>(256, (M + 255) / 256));   // ~256 rows per split
+    b.part_elems = std::max<int64_t>(b.nsplit * (4 * d * d + 4 * d), ((M + CS_ROWS - 1) / CS_ROWS) * 4 * d);
+    b.part_elems = std::max<int64_t>(b.part_elems, 2 * ((M + CS_ROWS - 1) / CS_ROWS) * d);
+    b.part_elems = std::max<int64_t>(b.part_elems, ((R + EB_ROWS - 1) / EB_ROWS) * n * 2 * d);
     b.part = c.take<float>(b.part_elems);
     b.Wr = c.take<float>(12 * d * d * L);
 }
@@ -479,24 +548,27 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         NQS_LAUNCHED();
         return NQS_OK;
     };
-    auto colsum = [&](const float* X, int64_t ld, int64_t M, int ncols, float* out) -> int {
+    // column sums of X0 (and X1) into out0 (and out1)
+    auto colsum = [&](const float* X0, const float* X1, int64_t ld, int64_t M, int ncols, float* out0,
+                      float* out1) -> int {
         const int nch = (int)((M + CS_ROWS - 1) / CS_ROWS);
-        colsum_partial_kernel<<<dim3((ncols + 31) / 32, nch), dim3(32, 8), 0, s>>>(X, ld, M, ncols, b.part);
+        const int nmat = X1 ? 2 : 1;
+        colsum_partial_kernel<<<dim3((ncols + 31) / 32, nch, nmat), dim3(32, 8), 0, s>>>(X0, X1, ld, M, ncols, b.part);
         NQS_LAUNCHED();
-        colsum_final_kernel<<<(ncols + 127) / 128, 128, 0, s>>>(b.part, nch, ncols, out);
+        colsum_final_kernel<<<(nmat * ncols + 7) / 8, 256, 0, s>>>(b.part, nch, ncols, nmat, out0, out1);
         NQS_LAUNCHED();
         return NQS_OK;
     };
-    auto outer = [&](const float* delta, int64_t ld_d, const void* act, bool act_bf16, int64_t ld_a,
-                     int64_t M, int out_dim, int in_dim, float* dW) -> int {
-        const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(b.nsplit, b.part_elems / ((int64_t)out_dim * in_dim)));
+    // dW += delta^T act and (if db) db += column sums of delta
+    auto outer = [&](const float* delta, int64_t ld_d, const float* act, int64_t ld_a, int64_t M, int out_dim,
+                     int in_dim, float* dW, float* db) -> int {
+        const int64_t stride = (int64_t)out_dim * in_dim + out_dim;
+        const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(b.nsplit, b.part_elems / stride));
         const int64_t per = (M + ns - 1) / ns;
-        dim3 grid((unsigned)((in_dim + OP_T - 1) / OP_T), (unsigned)((out_dim + OP_T - 1) / OP_T), (unsigned)ns);
-        if (act_bf16) outer_partial_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(delta, ld_d, (const __nv_bfloat16*)act, ld_a, M, out_dim, in_dim, per, b.part);
-        else outer_partial_kernel<float><<<grid, 256, 0, s>>>(delta, ld_d, (const float*)act, ld_a, M, out_dim, in_dim, per, b.part);
+        dim3 grid((unsigned)((in_dim + OP_B - 1) / OP_B), (unsigned)((out_dim + OP_B - 1) / OP_B), (unsigned)ns);
+        outer_partial_kernel<<<grid, 256, 0, s>>>(delta, ld_d, act, ld_a, M, out_dim, in_dim, per, b.part);
         NQS_LAUNCHED();
-        const int64_t nel = (int64_t)out_dim * in_dim;
-        outer_final_kernel<<<gs(nel), 256, 0, s>>>(b.part, (int)ns, nel, dW);
+        outer_final_kernel<<<gs(stride), 256, 0, s>>>(b.part, (int)ns, out_dim, in_dim, dW, db);
         NQS_LAUNCHED();
         return NQS_OK;
     };
@@ -513,6 +585,7 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
             const int64_t M = R * n;
             const uint64_t* xb = bits + lo;
             // ---- forward with saved activations
+            auto ps_fwd = std::make_unique<ProfScope>("bwd_recompute", s);
             embed_kernel<<<gs(M * d), 256, 0, s>>>(mc, P, xb, R, n, b.Hin[0]);
             NQS_LAUNCHED();
             auto ln_fwd = [&](const float* hsrc, const float* g, const float* bb, void* dst) -> int {
@@ -535,48 +608,48 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
                 NQS_TRY(gemm_nt((const float*)b.MM[l], W[l][TF_W2], P + mc.b2[l], b.Hin[l + 1], M, d, 4 * d, TF_EPI_RESID));
                 if (l + 1 < L) NQS_TRY(ln_fwd(b.Hin[l + 1], P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.A1[l + 1]));
             }
+            ps_fwd.reset();
             // ---- heads and final LayerNorm
+            auto ps_heads = std::make_unique<ProfScope>("bwd_heads", s);
             heads_bwd_kernel<DPL><<<(int)((R + 7) / 8), 256, 0, s>>>(mc, P, xb, b.Hin[L], R, g_abs + lo, g_phase + lo,
                                                                       b.dH, b.dS, b.GX, b.HF, b.DL, b.DPH);
             NQS_LAUNCHED();
-            NQS_TRY(outer(b.DL, 1, b.HF, false, d, M, 1, d, grad + mc.head_w));
-            NQS_TRY(colsum(b.DL, n, R, n, grad + mc.head_b));
-            NQS_TRY(outer(b.DPH, 4, b.HF + (int64_t)(n - 2) * d, false, (int64_t)n * d, R, 4, d, grad + mc.phase_w));
-            NQS_TRY(colsum(b.DPH, 4, R, 4, grad + mc.phase_b));
-            NQS_TRY(colsum(b.GX, d, M, d, grad + mc.lnf_g));
-            NQS_TRY(colsum(b.dS, d, M, d, grad + mc.lnf_b));
+            NQS_TRY(outer(b.DL, 1, b.HF, d, M, 1, d, grad + mc.head_w, nullptr));
+            NQS_TRY(colsum(b.DL, nullptr, n, R, n, grad + mc.head_b, nullptr));
+            NQS_TRY(outer(b.DPH, 4, b.HF + (int64_t)(n - 2) * d, (int64_t)n * d, R, 4, d, grad + mc.phase_w,
+                          grad + mc.phase_b));
+            NQS_TRY(colsum(b.GX, b.dS, d, M, d, grad + mc.lnf_g, grad + mc.lnf_b));
+            ps_heads.reset();
             // ---- blocks, last to first
             for (int l = L - 1; l >= 0; --l) {
                 // MLP: Hin[l+1] = Hmid + gelu(A2 W1^T + b1) W2^T + b2
-                NQS_TRY(colsum(b.dH, d, M, d, grad + mc.b2[l]));
-                NQS_TRY(outer(b.dH, d, b.MM[l], false, 4 * d, M, d, 4 * d, grad + mc.w2[l]));
+                auto ps_mlp = std::make_unique<ProfScope>("bwd_mlp", s);
+                NQS_TRY(outer(b.dH, d, (const float*)b.MM[l], 4 * d, M, d, 4 * d, grad + mc.w2[l], grad + mc.b2[l]));
                 NQS_TRY(gemm_nn(b.dH, W[l][TF_W2], b.dBig, M, 4 * d, d));
                 gelu_bwd_kernel<<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], b.dBig, M * 4 * d);
                 NQS_LAUNCHED();
-                NQS_TRY(colsum(b.dBig, 4 * d, M, 4 * d, grad + mc.b1[l]));
-                NQS_TRY(outer(b.dBig, 4 * d, b.A2[l], false, d, M, 4 * d, d, grad + mc.w1[l]));
+                NQS_TRY(outer(b.dBig, 4 * d, (const float*)b.A2[l], d, M, 4 * d, d, grad + mc.w1[l], grad + mc.b1[l]));
                 NQS_TRY(gemm_nn(b.dBig, W[l][TF_W1], b.dS, M, d, 4 * d));
                 ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hmid[l], P + mc.ln2_g[l], b.dS, b.dH, b.dHmid, b.GX, M, d);
                 NQS_LAUNCHED();
-                NQS_TRY(colsum(b.GX, d, M, d, grad + mc.ln2_g[l]));
-                NQS_TRY(colsum(b.dS, d, M, d, grad + mc.ln2_b[l]));
+                NQS_TRY(colsum(b.GX, b.dS, d, M, d, grad + mc.ln2_g[l], grad + mc.ln2_b[l]));
+                ps_mlp.reset();
                 // attention: Hmid = Hin + attn(A1 Wqkv^T + bqkv) Wo^T + bo
-                NQS_TRY(colsum(b.dHmid, d, M, d, grad + mc.bo[l]));
-                NQS_TRY(outer(b.dHmid, d, b.O[l], false, d, M, d, d, grad + mc.wo[l]));
+                ProfScope ps_att("bwd_attention", s);
+                NQS_TRY(outer(b.dHmid, d, (const float*)b.O[l], d, M, d, d, grad + mc.wo[l], grad + mc.bo[l]));
                 NQS_TRY(gemm_nn(b.dHmid, W[l][TF_WO], b.dS, M, d, d));
                 attention_bwd_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dS, n, d, dh, b.dQKV);
                 NQS_LAUNCHED();
-                NQS_TRY(colsum(b.dQKV, 3 * d, M, 3 * d, grad + mc.bqkv[l]));
-                NQS_TRY(outer(b.dQKV, 3 * d, b.A1[l], false, d, M, 3 * d, d, grad + mc.wqkv[l]));
+                NQS_TRY(outer(b.dQKV, 3 * d, (const float*)b.A1[l], d, M, 3 * d, d, grad + mc.wqkv[l], grad + mc.bqkv[l]));
                 NQS_TRY(gemm_nn(b.dQKV, W[l][TF_WQKV], b.dS, M, d, 3 * d));
                 ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hin[l], P + mc.ln1_g[l], b.dS, b.dHmid, b.dH, b.GX, M, d);
                 NQS_LAUNCHED();
-                NQS_TRY(colsum(b.GX, d, M, d, grad + mc.ln1_g[l]));
-                NQS_TRY(colsum(b.dS, d, M, d, grad + mc.ln1_b[l]));
+                NQS_TRY(colsum(b.GX, b.dS, d, M, d, grad + mc.ln1_g[l], grad + mc.ln1_b[l]));
             }
             {
+                ProfScope ps_emb("bwd_embed", s);
                 const int nch = (int)((R + EB_ROWS - 1) / EB_ROWS);
-                embed_bwd_partial_kernel<<<dim3((d + 127) / 128, nch), 128, 0, s>>>(mc, xb, b.dH, R, b.part);
+                embed_bwd_partial_kernel<<<dim3(n, nch), d, 0, s>>>(mc, xb, b.dH, R, b.part);
                 NQS_LAUNCHED();
                 embed_bwd_final_kernel<<<((n + 3) * d + 255) / 256, 256, 0, s>>>(mc, b.part, nch, grad);
                 NQS_LAUNCHED();

@@ -5,6 +5,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "nqs_internal.h"
 
 namespace nqs {
@@ -137,62 +139,126 @@ layernorm_kernel(const float* __restrict__ h, int64_t M, int d, const float* __r
 // ---------------------------------------------------------------- FP32 SIMT GEMM
 // C[M,N] (epilogue) A[M,K] . B^T with B = W[N][K] (NT) or B = W[K][N] (NN, for dX = dY . W).
 // 64x64 tile, K step 16, 256 threads with 4x4 outputs each.
-constexpr int SG_BM = 64, SG_BN = 64, SG_BK = 16;
+// FP32 SIMT GEMM  C[M, N] (epilogue) = A[M, K] . W^T + bias  (W [N, K]; NN: A . W with W [K, N]).
+// 128 x 64 output tile per CTA, 16-deep k-slices double-buffered in shared memory (the next
+// slice is fetched into registers while the current one is multiplied); 256 threads, each with
+// an 8 x 4 block of outputs fed by float4 shared-memory loads.
+constexpr int SG_BM = 128, SG_BN = 64, SG_BK = 16;
 
 template <class T_A, bool NN, int EPI, class T_C>
 __global__ void __launch_bounds__(256)
 sgemm_kernel(const T_A* __restrict__ A, const float* __restrict__ W, const float* __restrict__ bias,
              T_C* __restrict__ C, int64_t M, int N, int K) {
-    __shared__ float As[SG_BK][SG_BM + 4];
-    __shared__ float Bs[SG_BK][SG_BN + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ __align__(16) float As[2][SG_BK][SG_BM + 4];
+    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;          // outputs: rows ty*8.., columns tx*4..
     const int64_t m0 = (int64_t)blockIdx.y * SG_BM;
     const int n0 = blockIdx.x * SG_BN;
-    float acc[4][4] = {};
+    // global fetch roles: A rows (tid >> 2) and (tid >> 2) + 64, k quad (tid & 3);
+    // W (NT) row tid >> 2, k quad tid & 3;  W (NN) k row tid >> 4, n quad tid & 15
+    const int ar = tid >> 2, aq = tid & 3;
+    float ra[2][4], rb[4];
+    // four consecutive elements, as one float4 when in range and aligned (vec)
+    auto load4 = [&](const auto* p, bool in0, bool all_in, bool vec_ok, float (&r)[4], int64_t stride_in) {
+        if (all_in && vec_ok) {
+            const float4 v = *reinterpret_cast<const float4*>(p);
+            r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) r[j] = 0.f;
+            if (in0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) r[j] = (j < stride_in) ? (float)p[j] : 0.f;
+            }
+        }
+    };
+    const bool avec = std::is_same<T_A, float>::value && (K & 3) == 0 && ((uintptr_t)A & 15) == 0;
+    const bool wvec = NN ? ((N & 3) == 0 && ((uintptr_t)W & 15) == 0) : ((K & 3) == 0 && ((uintptr_t)W & 15) == 0);
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t gm = m0 + ar + 64 * h;
+            const int gk = k0 + 4 * aq;
+            load4(A + gm * K + gk, gm < M && gk < K, gm < M && gk + 3 < K, avec, ra[h], (int64_t)K - gk);
+        }
+        if (NN) {
+            const int gk = k0 + (tid >> 4), gn = n0 + 4 * (tid & 15);
+            load4(W + (int64_t)gk * N + gn, gk < K && gn < N, gk < K && gn + 3 < N, wvec, rb, (int64_t)N - gn);
+        } else {
+            const int gn = n0 + ar, gk = k0 + 4 * aq;
+            load4(W + (int64_t)gn * K + gk, gn < N && gk < K, gn < N && gk + 3 < K, wvec, rb, (int64_t)K - gk);
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) As[buf][4 * aq + j][ar + 64 * h] = ra[h][j];
+        if (NN) {
+            *reinterpret_cast<float4*>(&Bs[buf][tid >> 4][4 * (tid & 15)]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Bs[buf][4 * aq + j][ar] = rb[j];
+        }
+    };
+    float acc[8][4] = {};
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
     for (int k0 = 0; k0 < K; k0 += SG_BK) {
-        // A tile: 64 rows x 16 k
-        for (int i = threadIdx.x; i < SG_BM * SG_BK; i += 256) {
-            const int mm = i / SG_BK, kk = i % SG_BK;
-            const int64_t gm = m0 + mm;
-            const int gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? (float)A[gm * K + gk] : 0.f;
-        }
-        for (int i = threadIdx.x; i < SG_BN * SG_BK; i += 256) {
-            int nn, kk;
-            if (NN) { kk = i / SG_BN; nn = i % SG_BN; }
-            else    { nn = i / SG_BK; kk = i % SG_BK; }
-            const int gn = n0 + nn, gk = k0 + kk;
-            float w = 0.f;
-            if (gn < N && gk < K) w = NN ? W[(int64_t)gk * N + gn] : W[(int64_t)gn * K + gk];
-            Bs[kk][nn] = w;
-        }
-        __syncthreads();
+        const bool more = k0 + SG_BK < K;
+        if (more) fetch(k0 + SG_BK);
 #pragma unroll
         for (int kk = 0; kk < SG_BK; ++kk) {
-            float av[4], bv[4];
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { av[i] = As[kk][ty * 4 + i]; bv[i] = Bs[kk][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
-        __syncthreads();
+        if (more) {
+            stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
     }
+    const bool cvec = std::is_same<T_C, float>::value && (N & 3) == 0 && ((uintptr_t)C & 15) == 0;
+    const int gn0 = n0 + tx * 4;
+    float bj[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t gm = m0 + ty * 4 + i;
+    for (int j = 0; j < 4; ++j) bj[j] = (bias && gn0 + j < N) ? bias[gn0 + j] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t gm = m0 + ty * 8 + i;
         if (gm >= M) continue;
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (EPI == TF_EPI_ACCUM) ? acc[i][j] : acc[i][j] + bj[j];
+        T_C* dst = C + gm * N + gn0;
+        if (cvec && gn0 + 3 < N) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+            float4 o = make_float4(v[0], v[1], v[2], v[3]);
+            if (EPI == TF_EPI_RESID || EPI == TF_EPI_ACCUM) {
+                const float4 y = *d4;
+                o.x += y.x; o.y += y.y; o.z += y.z; o.w += y.w;
+            } else if (EPI == TF_EPI_GELU) {
+                o = make_float4(gelu_tanh(v[0]), gelu_tanh(v[1]), gelu_tanh(v[2]), gelu_tanh(v[3]));
+            }
+            *d4 = o;
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + tx * 4 + j;
-            if (gn >= N) continue;
-            float v = acc[i][j] + (bias ? bias[gn] : 0.f);
-            T_C* dst = C + gm * N + gn;
-            if (EPI == TF_EPI_GELU) store_act(dst, gelu_tanh(v));
-            else if (EPI == TF_EPI_RESID) store_act(dst, (float)*dst + v);
-            else if (EPI == TF_EPI_ACCUM) store_act(dst, (float)*dst + acc[i][j]);
-            else store_act(dst, v);
+            if (gn0 + j >= N) continue;
+            if (EPI == TF_EPI_GELU) store_act(dst + j, gelu_tanh(v[j]));
+            else if (EPI == TF_EPI_RESID || EPI == TF_EPI_ACCUM) store_act(dst + j, (float)dst[j] + v[j]);
+            else store_act(dst + j, v[j]);
         }
     }
 }
