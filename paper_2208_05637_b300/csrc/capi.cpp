@@ -776,6 +776,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
     eloc_layout(c, m, h, B, e);
     const uint64_t A = spin_mask(h->n, 0), Bm = spin_mask(h->n, 1);
     if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
+        ProfScope ps_all("local_energy", s);
         TfWeights w;
         NQS_TRY(tf_weights(m, w, s));
         NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, e.la, e.ph, e.tf, s));

@@ -589,7 +589,7 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
             embed_kernel<<<gs(M * d), 256, 0, s>>>(mc, P, xb, R, n, b.Hin[0]);
             NQS_LAUNCHED();
             auto ln_fwd = [&](const float* hsrc, const float* g, const float* bb, void* dst) -> int {
-                layernorm_kernel<MODE, DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(hsrc, M, d, g, bb, dst);
+                layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(hsrc, M, d, g, bb, dst);
                 NQS_LAUNCHED();
                 return NQS_OK;
             };

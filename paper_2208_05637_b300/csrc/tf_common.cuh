@@ -77,68 +77,182 @@ __device__ __forceinline__ void store_mode(void* base, int64_t row, int width, i
     }
 }
 
-// ---------------------------------------------------------------- embedding + first LayerNorm
-// One warp per row (sequence r, position t = t0 + row % T).  Writes h (fp32) and
-// a = LN1_0(h) (T_ACT).
+// ---------------------------------------------------------------- LayerNorm kernels
+// One warp per LN_ROWS rows (their loads issued together), lane l holding the DPL = d / 32
+// contiguous columns [l * DPL, (l + 1) * DPL); eight warps per CTA.
+constexpr int LN_ROWS = 4;
+constexpr int LN_ROWS_PER_CTA = 8 * LN_ROWS;
+inline int ln_grid(int64_t rows) { return (int)((rows + LN_ROWS_PER_CTA - 1) / LN_ROWS_PER_CTA); }
+
+template <int DPL>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[DPL]) {
+    if (DPL == 1) {
+        v[0] = p[0];
+    } else if (DPL == 2) {
+        const float2 x = *reinterpret_cast<const float2*>(p);
+        v[0] = x.x; v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < DPL; i += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(p + i);
+            v[i] = x.x; v[i + 1] = x.y; v[i + 2] = x.z; v[i + 3] = x.w;
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_floats(float* p, const float* v) {
+    if (N == 1) {
+        p[0] = v[0];
+    } else if (N == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_bf16s(__nv_bfloat16* p, const __nv_bfloat16* v) {
+    if (N == 1) {
+        p[0] = v[0];
+    } else if (N == 2) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            uint2 u;
+            u.x = (uint32_t)__bfloat16_as_ushort(v[i]) | ((uint32_t)__bfloat16_as_ushort(v[i + 1]) << 16);
+            u.y = (uint32_t)__bfloat16_as_ushort(v[i + 2]) | ((uint32_t)__bfloat16_as_ushort(v[i + 3]) << 16);
+            *reinterpret_cast<uint2*>(p + i) = u;
+        }
+    }
+}
+
+// N consecutive columns [col0, col0 + N) of row `row` in the storage form of MODE (store_mode).
+template <int MODE, int N>
+__device__ __forceinline__ void store_mode_vec(void* base, int64_t row, int width, int col0, const float* v) {
+    if (MODE == ACT_F32 || MODE == ACT_F32_Q1 || MODE == ACT_F32_Q2) {
+        float w[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (MODE == ACT_F32) {
+                w[j] = v[j];
+            } else if (MODE == ACT_F32_Q1) {
+                w[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+            } else {
+                const float hv = __bfloat162float(__float2bfloat16_rn(v[j]));
+                w[j] = hv + __bfloat162float(__float2bfloat16_rn(v[j] - hv));
+            }
+        }
+        store_floats<N>(reinterpret_cast<float*>(base) + row * width + col0, w);
+    } else {
+        __nv_bfloat16 hi[N], lo[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            hi[j] = __float2bfloat16_rn(v[j]);
+            if (MODE == ACT_BF16X2) lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+        }
+        const int64_t stride = MODE == ACT_BF16X2 ? 2 * (int64_t)width : width;
+        __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(base) + row * stride + col0;
+        store_bf16s<N>(b, hi);
+        if (MODE == ACT_BF16X2) store_bf16s<N>(b + width, lo);
+    }
+}
+
+// LayerNorm of LN_ROWS rows held by one warp (v[r] = row r's DPL values of this lane):
+// two-pass mean and variance, then a = (v - mean) * rstd * g + b stored in MODE's form.
+template <int MODE, int DPL>
+__device__ __forceinline__ void ln_rows_store(float (&v)[LN_ROWS][DPL], const int64_t (&rows)[LN_ROWS], int64_t M,
+                                              int d, int col0, const float* __restrict__ g,
+                                              const float* __restrict__ b, void* __restrict__ a) {
+    float gg[DPL], bb[DPL];
+    load_row<DPL>(g + col0, gg);
+    load_row<DPL>(b + col0, bb);
+    float mu[LN_ROWS], q[LN_ROWS];
+#pragma unroll
+    for (int r = 0; r < LN_ROWS; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) s += v[r][i];
+        mu[r] = s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < LN_ROWS; ++r) mu[r] += __shfl_xor_sync(0xffffffffu, mu[r], o);
+#pragma unroll
+    for (int r = 0; r < LN_ROWS; ++r) {
+        mu[r] /= d;
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) { const float c = v[r][i] - mu[r]; t += c * c; }
+        q[r] = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < LN_ROWS; ++r) q[r] += __shfl_xor_sync(0xffffffffu, q[r], o);
+#pragma unroll
+    for (int r = 0; r < LN_ROWS; ++r) {
+        if (rows[r] >= M) continue;
+        const float rstd = rsqrtf(q[r] / d + LN_EPS);
+        float y[DPL];
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) y[i] = (v[r][i] - mu[r]) * rstd * gg[i] + bb[i];
+        store_mode_vec<MODE, DPL>(a, rows[r], d, col0, y);
+    }
+}
+
+// Embedding + first LayerNorm: rows (sequence r, position t = t0 + row % T) get
+// h = tok_emb[token] + pos_emb[t] (fp32) and a = LN1_0(h) (MODE).
 template <int MODE, int DPL>   // DPL = d / 32 values per lane
 __global__ void __launch_bounds__(256)
 embed_ln_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
                 int64_t R, int T, int t0, float* __restrict__ h, void* __restrict__ a) {
     const int d = mc.hidden;
-    const int lane = threadIdx.x & 31;
-    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= R * T) return;
-    const int64_t r = row / T;
-    const int t = t0 + (int)(row % T);
-    const int tok = t == 0 ? 2 : (int)((bits[r] >> mc.order[t - 1]) & 1ull);
-    float v[DPL];
-    float s = 0.f;
+    const int lane = threadIdx.x & 31, col0 = lane * DPL;
+    const int64_t M = R * T;
+    const int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * LN_ROWS;
+    if (base >= M) return;
+    float v[LN_ROWS][DPL];
+    int64_t rows[LN_ROWS];
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) {
-        const int j = lane + 32 * i;
-        v[i] = P[mc.tok_emb + tok * d + j] + P[mc.pos_emb + t * d + j];
-        s += v[i];
+    for (int r = 0; r < LN_ROWS; ++r) {
+        rows[r] = base + r;
+        const int64_t row = rows[r] < M ? rows[r] : M - 1;
+        const int64_t sq = row / T;
+        const int t = t0 + (int)(row % T);
+        const int tok = t == 0 ? 2 : (int)((bits[sq] >> mc.order[t - 1]) & 1ull);
+        float e[DPL], p[DPL];
+        load_row<DPL>(P + mc.tok_emb + tok * d + col0, e);
+        load_row<DPL>(P + mc.pos_emb + t * d + col0, p);
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) v[r][i] = e[i] + p[i];
+        if (rows[r] < M) store_floats<DPL>(h + rows[r] * d + col0, v[r]);
     }
-    const float mu = warp_sum(s) / d;
-    float q = 0.f;
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) { const float c = v[i] - mu; q += c * c; }
-    const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) {
-        const int j = lane + 32 * i;
-        h[row * d + j] = v[i];
-        store_mode<MODE>(a, row, d, j, (v[i] - mu) * rstd * P[mc.ln1_g[0] + j] + P[mc.ln1_b[0] + j]);
-    }
+    ln_rows_store<MODE, DPL>(v, rows, M, d, col0, P + mc.ln1_g[0], P + mc.ln1_b[0], a);
 }
 
-// LayerNorm of h rows into a (T_ACT), one warp per row.
+// LayerNorm of h rows into a (MODE).
 template <int MODE, int DPL>
 __global__ void __launch_bounds__(256)
 layernorm_kernel(const float* __restrict__ h, int64_t M, int d, const float* __restrict__ g,
                  const float* __restrict__ b, void* __restrict__ a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= M) return;
-    float v[DPL];
-    float s = 0.f;
+    const int lane = threadIdx.x & 31, col0 = lane * DPL;
+    const int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * LN_ROWS;
+    if (base >= M) return;
+    float v[LN_ROWS][DPL];
+    int64_t rows[LN_ROWS];
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) { v[i] = h[row * d + lane + 32 * i]; s += v[i]; }
-    const float mu = warp_sum(s) / d;
-    float q = 0.f;
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) { const float c = v[i] - mu; q += c * c; }
-    const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) {
-        const int j = lane + 32 * i;
-        store_mode<MODE>(a, row, d, j, (v[i] - mu) * rstd * g[j] + b[j]);
+    for (int r = 0; r < LN_ROWS; ++r) {
+        rows[r] = base + r;
+        load_row<DPL>(h + (rows[r] < M ? rows[r] : M - 1) * d + col0, v[r]);
     }
+    ln_rows_store<MODE, DPL>(v, rows, M, d, col0, g, b, a);
 }
 
 // ---------------------------------------------------------------- FP32 SIMT GEMM
-// C[M,N] (epilogue) A[M,K] . B^T with B = W[N][K] (NT) or B = W[K][N] (NN, for dX = dY . W).
-// 64x64 tile, K step 16, 256 threads with 4x4 outputs each.
 // FP32 SIMT GEMM  C[M, N] (epilogue) = A[M, K] . W^T + bias  (W [N, K]; NN: A . W with W [K, N]).
 // 128 x 64 output tile per CTA, 16-deep k-slices double-buffered in shared memory (the next
 // slice is fetched into registers while the current one is multiplied); 256 threads, each with

@@ -363,8 +363,11 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
     const int64_t M = R * T;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
-        embed_ln_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(mc, P, bits, R, T, 0, b.h, b.a);
-        NQS_LAUNCHED();
+        {
+            ProfScope ps("tf_layernorm", s);
+            embed_ln_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(mc, P, bits, R, T, 0, b.h, b.a);
+            NQS_LAUNCHED();
+        }
         for (int l = 0; l < mc.layers; ++l) {
             NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
             {
@@ -373,12 +376,16 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
                 count_launch();
             }
             NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
-            layernorm_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
-            NQS_LAUNCHED();
+            {
+                ProfScope ps("tf_layernorm", s);
+                layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
+                NQS_LAUNCHED();
+            }
             NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, M, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
             NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
             if (l + 1 < mc.layers) {
-                layernorm_kernel<MODE, DPL><<<blocks_for(M, 8), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
+                ProfScope ps("tf_layernorm", s);
+                layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
                 NQS_LAUNCHED();
             }
         }
@@ -406,7 +413,7 @@ static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w
     const int64_t slab_stride = kc.cap * 3 * d;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
-        embed_ln_kernel<MODE, DPL><<<blocks_for(R, 8), 256, 0, s>>>(mc, P, bits, R, 1, k, b.h, b.a);
+        embed_ln_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(mc, P, bits, R, 1, k, b.h, b.a);
         NQS_LAUNCHED();
         for (int l = 0; l < mc.layers; ++l) {
             float* slab0 = kc.kv + l * layer_stride;
@@ -425,12 +432,12 @@ static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w
                 NQS_LAUNCHED();
             }
             NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, R, d, d, TF_EPI_RESID, P + mc.bo[l], s));
-            layernorm_kernel<MODE, DPL><<<blocks_for(R, 8), 256, 0, s>>>(b.h, R, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
+            layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
             NQS_LAUNCHED();
             NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, R, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
             NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, R, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
             if (l + 1 < mc.layers) {
-                layernorm_kernel<MODE, DPL><<<blocks_for(R, 8), 256, 0, s>>>(b.h, R, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
+                layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
                 NQS_LAUNCHED();
             }
         }
