@@ -210,7 +210,7 @@ def run_ours(args, rank, world, local):
     P.profile_enable(False)
     kern = {}
     for name in ("sample", "local_energy", "logpsi_rows", "sweep_count", "term_sweep", "eloc_rows", "made_backward",
-                 "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_attention",
+                 "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_mlp", "tf_attention",
                  "tf_heads", "tf_layernorm", "tf_backward", "bwd_recompute", "bwd_heads", "bwd_mlp", "bwd_attention",
                  "bwd_embed"):
         tms, cnt = P.profile_read(name)

@@ -268,6 +268,9 @@ size_t tf_bwd_workspace(const ModelConst& mc, int64_t B);
 int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
                 const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
 // status of the tensor-core kernels' bounded waits; synchronous, clears the flag
+// h += GELU(A . W1d^T + b1) . W2d^T + b2 (compensated bf16 forms), the hidden layer kept on chip
+int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint16_t* W2d, const float* b2,
+                float* h, int64_t M, int D, cudaStream_t s);
 int tc_status_take();
 struct TfCtx {
     const TfWeights* w;

@@ -384,6 +384,259 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// ---------------------------------------------------------------- fused MLP block
+// h[M, D] += GELU(A . W1d^T + b1) . W2d^T + b2 in the compensated bf16 forms: A = [a_hi | a_lo]
+// (M x 2D), W1d = [W1 | W1] (4D x 2D), W2d = [W2 | W2] (D x 8D).  The 4D-wide hidden
+// activation never leaves the SM: per 128-row tile and 128-column chunk j of the hidden layer,
+//   GEMM1_j  acc1 = A . W1d[128 j .. +128]^T                     (TMEM, two buffers)
+//   GELU_j   G = [hi | lo] of GELU(acc1 + b1) in shared memory   (epilogue warps, UMMA layout)
+//   GEMM2_j  acc2 += G . [W2 | W2](chunk j's hi and lo columns)^T (TMEM, two buffers)
+// and after the last chunk the epilogue adds acc2 + b2 into h with TMA reduce-adds.  Roles: warp 0
+// TMA producer (A per tile, W1/W2 k-blocks through a ring in the MMA's order), warp 1 MMA issuer
+// (order G1_0, G1_1, then G2_j followed by G1_{j+2}), warps 2..9 epilogue (two per TMEM lane
+// quadrant, splitting the columns).  One CTA per SM (all 512 TMEM columns).
+template <int D>
+struct MlpPlan {
+    static constexpr int KB1 = 2 * D / 64;                // 64-wide k-blocks of GEMM1
+    static constexpr int NCH = 4 * D / 128;               // 128-column chunks of the hidden layer
+    static constexpr int A_BYTES = KB1 * 16384;           // 128 rows x 2D bf16
+    static constexpr int STAGES = 4;                      // ring slots of 16 KB
+    static constexpr int RING_BYTES = STAGES * 16384;
+    static constexpr int G_BYTES = 4 * 16384;             // 128 rows x (128 hi + 128 lo) bf16
+    static constexpr int STG_BYTES = 8 * 4096;            // per epilogue warp: 32 rows x 32 fp32
+    static constexpr int BAR_OFF = A_BYTES + RING_BYTES + G_BYTES + STG_BYTES;
+    static constexpr int NBAR = 2 + 2 * STAGES + 4 + 2 + 4;
+    static constexpr int SMEM = 1024 + BAR_OFF + NBAR * 8 + 16;
+};
+constexpr int MLP_THREADS = 320;
+
+template <int D>
+__global__ void __launch_bounds__(MLP_THREADS, 1)
+tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
+              const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH,
+              const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles) {
+    using PL = MlpPlan<D>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* ring = smem + PL::A_BYTES;
+    uint8_t* sG = ring + PL::RING_BYTES;
+    uint8_t* sStg = sG + PL::G_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + PL::BAR_OFF);
+    uint64_t* a_full = bars;
+    uint64_t* a_empty = bars + 1;
+    uint64_t* full = bars + 2;
+    uint64_t* empty = full + PL::STAGES;
+    uint64_t* acc1_full = empty + PL::STAGES;      // [2]
+    uint64_t* acc1_empty = acc1_full + 2;          // [2]
+    uint64_t* g_full = acc1_empty + 2;
+    uint64_t* g_empty = g_full + 1;
+    uint64_t* acc2_full = g_empty + 1;             // [2]
+    uint64_t* acc2_empty = acc2_full + 2;          // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + PL::NBAR);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        for (int i = 0; i < PL::STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc1_full[i], 1); mbar_init(&acc1_empty[i], 8);
+            mbar_init(&acc2_full[i], 1); mbar_init(&acc2_empty[i], 8);
+        }
+        mbar_init(g_full, 8);
+        mbar_init(g_empty, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: A per tile, then the W1 / W2 k-blocks in the MMA's order
+            int64_t it = 0, tt = 0;
+            bool ok = true;
+            auto ring_load = [&](const CUtensorMap* map, int x, int y, uint32_t bytes) -> bool {
+                const int sl = (int)(it % PL::STAGES);
+                if (!mbar_wait_or_abort(&empty[sl], (uint32_t)(((it / PL::STAGES) & 1) ^ 1), abort)) return false;
+                mbar_expect_tx(&full[sl], bytes);
+                tma_load_2d(ring + (size_t)sl * 16384, map, &full[sl], x, y);
+                ++it;
+                return true;
+            };
+            auto w1 = [&](int j) -> bool {
+                for (int kb = 0; kb < PL::KB1; ++kb)
+                    if (!ring_load(&tmW1, kb * 64, j * 128, 16384)) return false;
+                return true;
+            };
+            auto w2 = [&](int j) -> bool {
+                for (int kb = 0; kb < 4; ++kb) {
+                    const int x = (kb < 2 ? 0 : 4 * D) + j * 128 + (kb & 1) * 64;
+                    if (!ring_load(&tmW2, x, 0, (uint32_t)D * 128)) return false;
+                }
+                return true;
+            };
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                const int m0 = (int)(t * 128);
+                if (!mbar_wait_or_abort(a_empty, (uint32_t)((tt & 1) ^ 1), abort)) break;
+                mbar_expect_tx(a_full, PL::A_BYTES);
+                for (int kb = 0; kb < PL::KB1; ++kb) tma_load_2d(sA + kb * 16384, &tmA, a_full, kb * 64, m0);
+                ok = w1(0) && (PL::NCH < 2 || w1(1));
+                for (int j = 0; ok && j < PL::NCH; ++j) ok = w2(j) && (j + 2 >= PL::NCH || w1(j + 2));
+            }
+            // copies still in flight complete before the CTA exits (bounded waits)
+            if (tt > 0) mbar_wait(a_full, (uint32_t)((tt - 1) & 1));
+            for (int64_t j = it - PL::STAGES < 0 ? 0 : it - PL::STAGES; j < it; ++j)
+                mbar_wait(&full[j % PL::STAGES], (uint32_t)((j / PL::STAGES) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t id1 = idesc_bf16(128, 128), id2 = idesc_bf16(128, D);
+            int64_t it = 0, tt = 0, c1 = 0, cg = 0;
+            bool ok = true;
+            auto g1 = [&](int j) -> bool {
+                const int b = (int)(c1 & 1);
+                if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) return false;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
+                for (int kb = 0; kb < PL::KB1; ++kb, ++it) {
+                    const int sl = (int)(it % PL::STAGES);
+                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / PL::STAGES) & 1), abort)) return false;
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sA + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
+                    umma_commit(&empty[sl]);
+                }
+                umma_commit(&acc1_full[b]);
+                if (j == PL::NCH - 1) umma_commit(a_empty);
+                ++c1;
+                return true;
+            };
+            auto g2 = [&](int j) -> bool {
+                const int ab = (int)(tt & 1);
+                if (j == 0 && !mbar_wait_or_abort(&acc2_empty[ab], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) return false;
+                if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) return false;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab * D);
+                for (int kb = 0; kb < 4; ++kb, ++it) {
+                    const int sl = (int)(it % PL::STAGES);
+                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / PL::STAGES) & 1), abort)) return false;
+                    tc_fence_after();
+                    const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
+                    umma_commit(&empty[sl]);
+                }
+                umma_commit(g_empty);
+                if (j == PL::NCH - 1) umma_commit(&acc2_full[ab]);
+                ++cg;
+                return true;
+            };
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                if (!mbar_wait_or_abort(a_full, (uint32_t)(tt & 1), abort)) break;
+                tc_fence_after();
+                ok = g1(0) && (PL::NCH < 2 || g1(1));
+                for (int j = 0; ok && j < PL::NCH; ++j) ok = g2(j) && (j + 2 >= PL::NCH || g1(j + 2));
+            }
+        }
+    } else {
+        // ---- epilogue warps: quadrant q of the TMEM lanes (rows), column half hc
+        const int q = warp & 3, hc = (warp - 2) >> 2;
+        const int r = q * 32 + lane;                       // row within the tile
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        uint8_t* stg = sStg + (size_t)(warp - 2) * 4096;
+        int64_t tt = 0, c1 = 0, cg = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tt) {
+            for (int j = 0; j < PL::NCH; ++j) {
+                const int b = (int)(c1 & 1);
+                if (!mbar_wait_or_abort(&acc1_full[b], (uint32_t)((c1 >> 1) & 1), abort)) { ok = false; break; }
+                tc_fence_after();
+                // GELU of this warp's 64 columns of the chunk, split into hi and lo (packed bf16 pairs)
+                uint32_t hp[32], lp[32];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    float v16[16];
+                    tmem_ld16(lane_base + (uint32_t)(b * 128 + hc * 64 + 16 * p), v16);
+                    const float* bb = b1 + j * 128 + hc * 64 + 16 * p;
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const float g0 = gelu_tanh(v16[i] + bb[i]), g1v = gelu_tanh(v16[i + 1] + bb[i + 1]);
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(g0), h1 = __float2bfloat16_rn(g1v);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(g0 - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(g1v - __bfloat162float(h1));
+                        hp[8 * p + i / 2] = pack_bf16(h0, h1);
+                        lp[8 * p + i / 2] = pack_bf16(l0, l1);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc1_empty[b]);
+                ++c1;
+                // write G once the previous chunk's GEMM2 has read it
+                if (!mbar_wait_or_abort(g_empty, (uint32_t)((cg & 1) ^ 1), abort)) { ok = false; break; }
+                const uint32_t ghi = su32(sG + hc * 16384) + (uint32_t)r * 128;
+                const uint32_t glo = su32(sG + (2 + hc) * 16384) + (uint32_t)r * 128;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t off = (uint32_t)((u ^ (r & 7)) << 4);
+                    st_shared_v4(ghi + off, hp[4 * u], hp[4 * u + 1], hp[4 * u + 2], hp[4 * u + 3]);
+                    st_shared_v4(glo + off, lp[4 * u], lp[4 * u + 1], lp[4 * u + 2], lp[4 * u + 3]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(g_full);
+                ++cg;
+            }
+            if (!ok) break;
+            // residual: h += acc2 + b2, this warp's D/2 columns in 32-column TMA reduce-adds
+            const int ab = (int)(tt & 1);
+            if (!mbar_wait_or_abort(&acc2_full[ab], (uint32_t)((tt >> 1) & 1), abort)) break;
+            tc_fence_after();
+            const int64_t row0 = t * 128 + q * 32;
+#pragma unroll
+            for (int c = 0; c < D / 2; c += 32) {
+                const int col = hc * (D / 2) + c;
+                if (lane == 0) bulk_wait_read<0>();
+                __syncwarp();
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    float v16[16];
+                    tmem_ld16(lane_base + 256u + (uint32_t)(ab * D + col + 16 * p), v16);
+                    stage16<TF_EPI_RESID>(v16, b2, col + 16 * p, p, su32(stg), lane);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (row0 < M) tma_reduce_add_2d(&tmH, stg, col, (int)row0);
+                    bulk_commit();
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc2_empty[ab]);
+        }
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // ---------------------------------------------------------------- host: tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -485,6 +738,36 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
         case TF_EPI_GELU2 * 2 + 1: return launch(tc_gemm_kernel<TF_EPI_GELU2, true>);
         default: set_error("bad GEMM epilogue"); return NQS_ERR_INVALID_ARG;
     }
+}
+
+// Fused MLP block of the compensated transformer (see tc_mlp_kernel); D = 64 or 128.
+int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint16_t* W2d, const float* b2,
+                float* h, int64_t M, int D, cudaStream_t s) {
+    if (M <= 0) return NQS_OK;
+    if (D != 64 && D != 128) { set_error("fused MLP needs d_model 64 or 128"); return NQS_ERR_UNSUPPORTED; }
+    if (((uintptr_t)h & 15) || !b1 || !b2) { set_error("fused MLP: bad operand"); return NQS_ERR_INVALID_ARG; }
+    CUtensorMap ma, m1, m2, mh;
+    NQS_TRY(make_map(&ma, A, M, 2 * D, 128));
+    NQS_TRY(make_map(&m1, W1d, 4 * D, 2 * D, 128));
+    NQS_TRY(make_map(&m2, W2d, D, 8 * D, D));
+    NQS_TRY(make_map(&mh, h, M, D, 32, true));
+    const int64_t ntiles = (M + 127) / 128;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
+    auto launch = [&](auto kernel, int smem, int slot) -> int {
+        static int configured_device[2] = {-1, -1};
+        int dev = 0;
+        NQS_CK(cudaGetDevice(&dev));
+        if (configured_device[slot] != dev) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_mlp)", __FILE__, __LINE__);
+            configured_device[slot] = dev;
+        }
+        kernel<<<grid, MLP_THREADS, smem, s>>>(ma, m1, m2, mh, b1, b2, M, ntiles);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    };
+    if (D == 64) return launch(tc_mlp_kernel<64>, MlpPlan<64>::SMEM, 0);
+    return launch(tc_mlp_kernel<128>, MlpPlan<128>::SMEM, 1);
 }
 
 // Read and clear the device status of the tensor-core kernels (synchronous).

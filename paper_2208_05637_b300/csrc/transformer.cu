@@ -316,6 +316,23 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
     return NQS_OK;
 }
 
+// MLP half of block l: h += W2 . gelu(W1 . a + b1) + b2.  Compensated BF16 models with d_model
+// 64 or 128 run it as one fused tensor-core kernel (the 4d hidden layer stays on chip); the
+// others as two GEMMs through the mid buffer.
+static int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* a, void* mid,
+                  float* h, int64_t M, cudaStream_t s) {
+    const int d = mc.hidden;
+    if (mc.precision == NQS_PREC_BF16 && mc.compensated && (d == 64 || d == 128)) {
+        const double flops = 2.0 * 2.0 * (double)M * 4 * d * d;
+        const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * 2 + 2.0 * 8.0 * d * d * 2;
+        ProfScope ps("tf_mlp", s, flops, bytes);
+        return tc_mlp_bf16(a, w.bf16 + w.bf16_off[layer][TF_W1], P + mc.b1[layer], w.bf16 + w.bf16_off[layer][TF_W2],
+                           P + mc.b2[layer], h, M, d, s);
+    }
+    NQS_TRY(tf_gemm(mc, w, TF_W1, layer, a, mid, M, 4 * d, d, TF_EPI_GELU, P + mc.b1[layer], s));
+    return tf_gemm(mc, w, TF_W2, layer, mid, h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[layer], s);
+}
+
 int tf_prepare_weights(const ModelConst& mc, const float* P, TfWeights& w, cudaStream_t s) {
     w.fp32 = P;
     for (int l = 0; l < mc.layers; ++l) {
@@ -381,8 +398,7 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
                 NQS_LAUNCHED();
             }
-            NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, M, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
-            NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
+            NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, M, s));
             if (l + 1 < mc.layers) {
                 ProfScope ps("tf_layernorm", s);
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
@@ -434,8 +450,7 @@ static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w
             NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, R, d, d, TF_EPI_RESID, P + mc.bo[l], s));
             layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
             NQS_LAUNCHED();
-            NQS_TRY(tf_gemm(mc, w, TF_W1, l, b.a, b.mid, R, 4 * d, d, TF_EPI_GELU, P + mc.b1[l], s));
-            NQS_TRY(tf_gemm(mc, w, TF_W2, l, b.mid, b.h, R, d, 4 * d, TF_EPI_RESID, P + mc.b2[l], s));
+            NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, R, s));
             if (l + 1 < mc.layers) {
                 layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
                 NQS_LAUNCHED();
