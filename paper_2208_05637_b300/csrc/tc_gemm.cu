@@ -139,6 +139,16 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+// 16 columns of the warp's 32 TMEM lanes without waiting (tmem_wait_ld() before use).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
+    uint32_t* r = reinterpret_cast<uint32_t*>(v);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }
@@ -393,25 +403,31 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 //   GEMM2_j  acc2 += G . [W2 | W2](chunk j's hi and lo columns)^T (TMEM, two buffers)
 // and after the last chunk the epilogue adds acc2 + b2 into h with TMA reduce-adds.  Roles: warp 0
 // TMA producer (A per tile, W1/W2 k-blocks through a ring in the MMA's order), warp 1 MMA issuer
-// (order G1_0, G1_1, then G2_j followed by G1_{j+2}), warps 2..9 epilogue (two per TMEM lane
-// quadrant, splitting the columns).  One CTA per SM (all 512 TMEM columns).
+// (order G1_0, G1_1, then G2_j followed by G1_{j+2}), warps 2.. epilogue (EW / 4 per TMEM lane
+// quadrant, each taking a column slice).  One CTA per SM (all 512 TMEM columns).
 template <int D>
 struct MlpPlan {
+    static constexpr int EW = D == 64 ? 16 : 8;           // epilogue warps
+    static constexpr int SLICES = EW / 4;                 // column slices per lane quadrant
+    static constexpr int SL = 128 / SLICES;               // hidden columns per warp and chunk
+    static constexpr int RES_SLICES = SLICES < D / 32 ? SLICES : D / 32;   // warps per quadrant on the residual
+    static constexpr int RC = D / RES_SLICES;             // residual columns per such warp
+    static constexpr int THREADS = 64 + 32 * EW;
     static constexpr int KB1 = 2 * D / 64;                // 64-wide k-blocks of GEMM1
     static constexpr int NCH = 4 * D / 128;               // 128-column chunks of the hidden layer
     static constexpr int A_BYTES = KB1 * 16384;           // 128 rows x 2D bf16
-    static constexpr int STAGES = 4;                      // ring slots of 16 KB
+    static constexpr int STAGES = D == 64 ? 4 : 3;        // ring slots of 16 KB
     static constexpr int RING_BYTES = STAGES * 16384;
     static constexpr int G_BYTES = 4 * 16384;             // 128 rows x (128 hi + 128 lo) bf16
-    static constexpr int STG_BYTES = 8 * 4096;            // per epilogue warp: 32 rows x 32 fp32
-    static constexpr int BAR_OFF = A_BYTES + RING_BYTES + G_BYTES + STG_BYTES;
+    static constexpr int STG_BYTES = 4 * RES_SLICES * 4096;   // residual staging: 32 rows x 32 fp32 per warp
+    static constexpr int BIAS_OFF = A_BYTES + RING_BYTES + G_BYTES + STG_BYTES;
+    static constexpr int BAR_OFF = BIAS_OFF + 5 * D * 4;  // b1 (4D) and b2 (D)
     static constexpr int NBAR = 2 + 2 * STAGES + 4 + 2 + 4;
     static constexpr int SMEM = 1024 + BAR_OFF + NBAR * 8 + 16;
 };
-constexpr int MLP_THREADS = 320;
 
 template <int D>
-__global__ void __launch_bounds__(MLP_THREADS, 1)
+__global__ void __launch_bounds__(MlpPlan<D>::THREADS, 1)
 tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
               const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH,
               const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles) {
@@ -422,6 +438,8 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint8_t* ring = smem + PL::A_BYTES;
     uint8_t* sG = ring + PL::RING_BYTES;
     uint8_t* sStg = sG + PL::G_BYTES;
+    float* sb1 = reinterpret_cast<float*>(smem + PL::BIAS_OFF);
+    float* sb2 = sb1 + 4 * D;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + PL::BAR_OFF);
     uint64_t* a_full = bars;
     uint64_t* a_empty = bars + 1;
@@ -437,15 +455,17 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    for (int i = threadIdx.x; i < 4 * D; i += blockDim.x) sb1[i] = b1[i];
+    for (int i = threadIdx.x; i < D; i += blockDim.x) sb2[i] = b2[i];
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
         for (int i = 0; i < PL::STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&acc1_full[i], 1); mbar_init(&acc1_empty[i], 8);
-            mbar_init(&acc2_full[i], 1); mbar_init(&acc2_empty[i], 8);
+            mbar_init(&acc1_full[i], 1); mbar_init(&acc1_empty[i], PL::EW);
+            mbar_init(&acc2_full[i], 1); mbar_init(&acc2_empty[i], PL::EW);
         }
-        mbar_init(g_full, 8);
+        mbar_init(g_full, PL::EW);
         mbar_init(g_empty, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -552,11 +572,12 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
         }
     } else {
-        // ---- epilogue warps: quadrant q of the TMEM lanes (rows), column half hc
-        const int q = warp & 3, hc = (warp - 2) >> 2;
+        // ---- epilogue warps: quadrant q of the TMEM lanes (rows), column slice sl
+        const int q = warp & 3, sl = (warp - 2) >> 2;
         const int r = q * 32 + lane;                       // row within the tile
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        uint8_t* stg = sStg + (size_t)(warp - 2) * 4096;
+        const bool res_warp = sl < PL::RES_SLICES;
+        uint8_t* stg = sStg + (size_t)(q + 4 * (res_warp ? sl : 0)) * 4096;
         int64_t tt = 0, c1 = 0, cg = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tt) {
@@ -564,21 +585,24 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const int b = (int)(c1 & 1);
                 if (!mbar_wait_or_abort(&acc1_full[b], (uint32_t)((c1 >> 1) & 1), abort)) { ok = false; break; }
                 tc_fence_after();
-                // GELU of this warp's 64 columns of the chunk, split into hi and lo (packed bf16 pairs)
-                uint32_t hp[32], lp[32];
+                // GELU of this warp's SL columns of the chunk, split into hi and lo (packed bf16 pairs)
+                uint32_t hp[PL::SL / 2], lp[PL::SL / 2];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float v16[16];
-                    tmem_ld16(lane_base + (uint32_t)(b * 128 + hc * 64 + 16 * p), v16);
-                    const float* bb = b1 + j * 128 + hc * 64 + 16 * p;
+                for (int p = 0; p < PL::SL / 32; ++p) {
+                    const int c0 = sl * PL::SL + 32 * p;           // column within the chunk
+                    float v[32];
+                    tmem_ld16_nowait(lane_base + (uint32_t)(b * 128 + c0), v);
+                    tmem_ld16_nowait(lane_base + (uint32_t)(b * 128 + c0 + 16), v + 16);
+                    tmem_wait_ld();
+                    const float* bb = sb1 + j * 128 + c0;
 #pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const float g0 = gelu_tanh(v16[i] + bb[i]), g1v = gelu_tanh(v16[i + 1] + bb[i + 1]);
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(g0), h1 = __float2bfloat16_rn(g1v);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(g0 - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(g1v - __bfloat162float(h1));
-                        hp[8 * p + i / 2] = pack_bf16(h0, h1);
-                        lp[8 * p + i / 2] = pack_bf16(l0, l1);
+                    for (int i = 0; i < 32; i += 2) {
+                        const float g0 = gelu_tanh(v[i] + bb[i]), g1v = gelu_tanh(v[i + 1] + bb[i + 1]);
+                        const __nv_bfloat162 hh = __floats2bfloat162_rn(g0, g1v);
+                        const float2 hf = __bfloat1622float2(hh);
+                        const __nv_bfloat162 ll = __floats2bfloat162_rn(g0 - hf.x, g1v - hf.y);
+                        hp[16 * p + i / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+                        lp[16 * p + i / 2] = *reinterpret_cast<const uint32_t*>(&ll);
                     }
                 }
                 tc_fence_before();
@@ -587,11 +611,12 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 ++c1;
                 // write G once the previous chunk's GEMM2 has read it
                 if (!mbar_wait_or_abort(g_empty, (uint32_t)((cg & 1) ^ 1), abort)) { ok = false; break; }
-                const uint32_t ghi = su32(sG + hc * 16384) + (uint32_t)r * 128;
-                const uint32_t glo = su32(sG + (2 + hc) * 16384) + (uint32_t)r * 128;
+                const int kb_hi = (sl * PL::SL) >> 6, u0 = ((sl * PL::SL) & 63) >> 3;
+                const uint32_t ghi = su32(sG + kb_hi * 16384) + (uint32_t)r * 128;
+                const uint32_t glo = su32(sG + (2 + kb_hi) * 16384) + (uint32_t)r * 128;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t off = (uint32_t)((u ^ (r & 7)) << 4);
+                for (int u = 0; u < PL::SL / 8; ++u) {
+                    const uint32_t off = (uint32_t)(((u0 + u) ^ (r & 7)) << 4);
                     st_shared_v4(ghi + off, hp[4 * u], hp[4 * u + 1], hp[4 * u + 2], hp[4 * u + 3]);
                     st_shared_v4(glo + off, lp[4 * u], lp[4 * u + 1], lp[4 * u + 2], lp[4 * u + 3]);
                 }
@@ -601,27 +626,29 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 ++cg;
             }
             if (!ok) break;
-            // residual: h += acc2 + b2, this warp's D/2 columns in 32-column TMA reduce-adds
+            // residual: h += acc2 + b2, RC columns per warp in 32-column TMA reduce-adds
             const int ab = (int)(tt & 1);
             if (!mbar_wait_or_abort(&acc2_full[ab], (uint32_t)((tt >> 1) & 1), abort)) break;
             tc_fence_after();
-            const int64_t row0 = t * 128 + q * 32;
+            if (res_warp) {
+                const int64_t row0 = t * 128 + q * 32;
 #pragma unroll
-            for (int c = 0; c < D / 2; c += 32) {
-                const int col = hc * (D / 2) + c;
-                if (lane == 0) bulk_wait_read<0>();
-                __syncwarp();
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    float v16[16];
-                    tmem_ld16(lane_base + 256u + (uint32_t)(ab * D + col + 16 * p), v16);
-                    stage16<TF_EPI_RESID>(v16, b2, col + 16 * p, p, su32(stg), lane);
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    if (row0 < M) tma_reduce_add_2d(&tmH, stg, col, (int)row0);
-                    bulk_commit();
+                for (int c = 0; c < PL::RC; c += 32) {
+                    const int col = sl * PL::RC + c;
+                    if (lane == 0) bulk_wait_read<0>();
+                    __syncwarp();
+                    float v[32];
+                    tmem_ld16_nowait(lane_base + 256u + (uint32_t)(ab * D + col), v);
+                    tmem_ld16_nowait(lane_base + 256u + (uint32_t)(ab * D + col + 16), v + 16);
+                    tmem_wait_ld();
+                    stage16<TF_EPI_RESID>(*reinterpret_cast<const float(*)[16]>(v), sb2, col, 0, su32(stg), lane);
+                    stage16<TF_EPI_RESID>(*reinterpret_cast<const float(*)[16]>(v + 16), sb2, col + 16, 1, su32(stg), lane);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (row0 < M) tma_reduce_add_2d(&tmH, stg, col, (int)row0);
+                        bulk_commit();
+                    }
                 }
             }
             tc_fence_before();
@@ -753,7 +780,7 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
     NQS_TRY(make_map(&mh, h, M, D, 32, true));
     const int64_t ntiles = (M + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
-    auto launch = [&](auto kernel, int smem, int slot) -> int {
+    auto launch = [&](auto kernel, int smem, int threads, int slot) -> int {
         static int configured_device[2] = {-1, -1};
         int dev = 0;
         NQS_CK(cudaGetDevice(&dev));
@@ -762,12 +789,12 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_mlp)", __FILE__, __LINE__);
             configured_device[slot] = dev;
         }
-        kernel<<<grid, MLP_THREADS, smem, s>>>(ma, m1, m2, mh, b1, b2, M, ntiles);
+        kernel<<<grid, threads, smem, s>>>(ma, m1, m2, mh, b1, b2, M, ntiles);
         NQS_LAUNCHED();
         return NQS_OK;
     };
-    if (D == 64) return launch(tc_mlp_kernel<64>, MlpPlan<64>::SMEM, 0);
-    return launch(tc_mlp_kernel<128>, MlpPlan<128>::SMEM, 1);
+    if (D == 64) return launch(tc_mlp_kernel<64>, MlpPlan<64>::SMEM, MlpPlan<64>::THREADS, 0);
+    return launch(tc_mlp_kernel<128>, MlpPlan<128>::SMEM, MlpPlan<128>::THREADS, 1);
 }
 
 // Read and clear the device status of the tensor-core kernels (synchronous).
