@@ -406,173 +406,57 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // (order G1_0, G1_1, then G2_j followed by G1_{j+2}), warps 2.. epilogue (EW / 4 per TMEM lane
 // quadrant, each taking a column slice).  One CTA per SM (all 512 TMEM columns).
 template <int D>
-struct MlpPlan {
+struct MlpPlan {                                          // epilogue layout (both variants)
     static constexpr int EW = D == 64 ? 16 : 8;           // epilogue warps
     static constexpr int SLICES = EW / 4;                 // column slices per lane quadrant
     static constexpr int SL = 128 / SLICES;               // hidden columns per warp and chunk
     static constexpr int RES_SLICES = SLICES < D / 32 ? SLICES : D / 32;   // warps per quadrant on the residual
     static constexpr int RC = D / RES_SLICES;             // residual columns per such warp
     static constexpr int THREADS = 64 + 32 * EW;
-    static constexpr int KB1 = 2 * D / 64;                // 64-wide k-blocks of GEMM1
     static constexpr int NCH = 4 * D / 128;               // 128-column chunks of the hidden layer
+    static constexpr int STG_BYTES = 4 * RES_SLICES * 4096;   // residual staging: 32 rows x 32 fp32 per warp
+};
+
+template <int D>
+struct MlpRingPlan {                                      // weights streamed through a ring
+    static constexpr int KB1 = 2 * D / 64;                // 64-wide k-blocks of GEMM1
     static constexpr int A_BYTES = KB1 * 16384;           // 128 rows x 2D bf16
-    static constexpr int STAGES = D == 64 ? 4 : 3;        // ring slots of 16 KB
+    static constexpr int STAGES = 3;                      // ring slots of 16 KB
     static constexpr int RING_BYTES = STAGES * 16384;
     static constexpr int G_BYTES = 4 * 16384;             // 128 rows x (128 hi + 128 lo) bf16
-    static constexpr int STG_BYTES = 4 * RES_SLICES * 4096;   // residual staging: 32 rows x 32 fp32 per warp
-    static constexpr int BIAS_OFF = A_BYTES + RING_BYTES + G_BYTES + STG_BYTES;
+    static constexpr int BIAS_OFF = A_BYTES + RING_BYTES + G_BYTES + MlpPlan<D>::STG_BYTES;
     static constexpr int BAR_OFF = BIAS_OFF + 5 * D * 4;  // b1 (4D) and b2 (D)
     static constexpr int NBAR = 2 + 2 * STAGES + 4 + 2 + 4;
     static constexpr int SMEM = 1024 + BAR_OFF + NBAR * 8 + 16;
 };
 
+// Epilogue warps of the fused MLP (both variants): per hidden chunk, GELU of the warp's column
+// slice of acc1 split into hi | lo and written into G; per tile, h += acc2 + b2 by TMA reduce-adds.
 template <int D>
-__global__ void __launch_bounds__(MlpPlan<D>::THREADS, 1)
-tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
-              const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH,
-              const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles) {
+struct MlpEpiArgs {
+    uint32_t tmem;
+    uint8_t *sG, *sStg;
+    const float *sb1, *sb2;
+    uint64_t *acc1_full, *acc1_empty, *g_full, *g_empty, *acc2_full, *acc2_empty;
+    volatile int* abort;
+    const CUtensorMap* tmH;
+    int64_t M, ntiles;
+};
+
+template <int D>
+__device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, int lane) {
     using PL = MlpPlan<D>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;
-    uint8_t* ring = smem + PL::A_BYTES;
-    uint8_t* sG = ring + PL::RING_BYTES;
-    uint8_t* sStg = sG + PL::G_BYTES;
-    float* sb1 = reinterpret_cast<float*>(smem + PL::BIAS_OFF);
-    float* sb2 = sb1 + 4 * D;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + PL::BAR_OFF);
-    uint64_t* a_full = bars;
-    uint64_t* a_empty = bars + 1;
-    uint64_t* full = bars + 2;
-    uint64_t* empty = full + PL::STAGES;
-    uint64_t* acc1_full = empty + PL::STAGES;      // [2]
-    uint64_t* acc1_empty = acc1_full + 2;          // [2]
-    uint64_t* g_full = acc1_empty + 2;
-    uint64_t* g_empty = g_full + 1;
-    uint64_t* acc2_full = g_empty + 1;             // [2]
-    uint64_t* acc2_empty = acc2_full + 2;          // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + PL::NBAR);
-    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    for (int i = threadIdx.x; i < 4 * D; i += blockDim.x) sb1[i] = b1[i];
-    for (int i = threadIdx.x; i < D; i += blockDim.x) sb2[i] = b2[i];
-    if (threadIdx.x == 0) {
-        mbar_init(a_full, 1);
-        mbar_init(a_empty, 1);
-        for (int i = 0; i < PL::STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&acc1_full[i], 1); mbar_init(&acc1_empty[i], PL::EW);
-            mbar_init(&acc2_full[i], 1); mbar_init(&acc2_empty[i], PL::EW);
-        }
-        mbar_init(g_full, PL::EW);
-        mbar_init(g_empty, 1);
-        *abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // ---- producer: A per tile, then the W1 / W2 k-blocks in the MMA's order
-            int64_t it = 0, tt = 0;
-            bool ok = true;
-            auto ring_load = [&](const CUtensorMap* map, int x, int y, uint32_t bytes) -> bool {
-                const int sl = (int)(it % PL::STAGES);
-                if (!mbar_wait_or_abort(&empty[sl], (uint32_t)(((it / PL::STAGES) & 1) ^ 1), abort)) return false;
-                mbar_expect_tx(&full[sl], bytes);
-                tma_load_2d(ring + (size_t)sl * 16384, map, &full[sl], x, y);
-                ++it;
-                return true;
-            };
-            auto w1 = [&](int j) -> bool {
-                for (int kb = 0; kb < PL::KB1; ++kb)
-                    if (!ring_load(&tmW1, kb * 64, j * 128, 16384)) return false;
-                return true;
-            };
-            auto w2 = [&](int j) -> bool {
-                for (int kb = 0; kb < 4; ++kb) {
-                    const int x = (kb < 2 ? 0 : 4 * D) + j * 128 + (kb & 1) * 64;
-                    if (!ring_load(&tmW2, x, 0, (uint32_t)D * 128)) return false;
-                }
-                return true;
-            };
-            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
-                const int m0 = (int)(t * 128);
-                if (!mbar_wait_or_abort(a_empty, (uint32_t)((tt & 1) ^ 1), abort)) break;
-                mbar_expect_tx(a_full, PL::A_BYTES);
-                for (int kb = 0; kb < PL::KB1; ++kb) tma_load_2d(sA + kb * 16384, &tmA, a_full, kb * 64, m0);
-                ok = w1(0) && (PL::NCH < 2 || w1(1));
-                for (int j = 0; ok && j < PL::NCH; ++j) ok = w2(j) && (j + 2 >= PL::NCH || w1(j + 2));
-            }
-            // copies still in flight complete before the CTA exits (bounded waits)
-            if (tt > 0) mbar_wait(a_full, (uint32_t)((tt - 1) & 1));
-            for (int64_t j = it - PL::STAGES < 0 ? 0 : it - PL::STAGES; j < it; ++j)
-                mbar_wait(&full[j % PL::STAGES], (uint32_t)((j / PL::STAGES) & 1));
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            // ---- MMA issuer
-            const uint32_t id1 = idesc_bf16(128, 128), id2 = idesc_bf16(128, D);
-            int64_t it = 0, tt = 0, c1 = 0, cg = 0;
-            bool ok = true;
-            auto g1 = [&](int j) -> bool {
-                const int b = (int)(c1 & 1);
-                if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) return false;
-                tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
-                for (int kb = 0; kb < PL::KB1; ++kb, ++it) {
-                    const int sl = (int)(it % PL::STAGES);
-                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / PL::STAGES) & 1), abort)) return false;
-                    tc_fence_after();
-                    const uint32_t a0 = su32(sA + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
-                    umma_commit(&empty[sl]);
-                }
-                umma_commit(&acc1_full[b]);
-                if (j == PL::NCH - 1) umma_commit(a_empty);
-                ++c1;
-                return true;
-            };
-            auto g2 = [&](int j) -> bool {
-                const int ab = (int)(tt & 1);
-                if (j == 0 && !mbar_wait_or_abort(&acc2_empty[ab], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) return false;
-                if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) return false;
-                tc_fence_after();
-                const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab * D);
-                for (int kb = 0; kb < 4; ++kb, ++it) {
-                    const int sl = (int)(it % PL::STAGES);
-                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / PL::STAGES) & 1), abort)) return false;
-                    tc_fence_after();
-                    const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
-                    umma_commit(&empty[sl]);
-                }
-                umma_commit(g_empty);
-                if (j == PL::NCH - 1) umma_commit(&acc2_full[ab]);
-                ++cg;
-                return true;
-            };
-            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
-                if (!mbar_wait_or_abort(a_full, (uint32_t)(tt & 1), abort)) break;
-                tc_fence_after();
-                ok = g1(0) && (PL::NCH < 2 || g1(1));
-                for (int j = 0; ok && j < PL::NCH; ++j) ok = g2(j) && (j + 2 >= PL::NCH || g1(j + 2));
-            }
-        }
-    } else {
-        // ---- epilogue warps: quadrant q of the TMEM lanes (rows), column slice sl
+    const uint32_t tmem = E.tmem;
+    uint8_t* sG = E.sG;
+    uint8_t* sStg = E.sStg;
+    const float* sb1 = E.sb1;
+    const float* sb2 = E.sb2;
+    uint64_t *acc1_full = E.acc1_full, *acc1_empty = E.acc1_empty, *g_full = E.g_full, *g_empty = E.g_empty;
+    uint64_t *acc2_full = E.acc2_full, *acc2_empty = E.acc2_empty;
+    volatile int* abort = E.abort;
+    const CUtensorMap& tmH = *E.tmH;
+    const int64_t M = E.M, ntiles = E.ntiles;
+    {   // ---- epilogue warps: quadrant q of the TMEM lanes (rows), column slice sl
         const int q = warp & 3, sl = (warp - 2) >> 2;
         const int r = q * 32 + lane;                       // row within the tile
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
@@ -657,6 +541,307 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         if (lane == 0) bulk_wait_all();
         __syncwarp();
+        }
+}
+
+template <int D>
+__global__ void __launch_bounds__(MlpPlan<D>::THREADS, 1)
+tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
+              const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH,
+              const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles) {
+    using PL = MlpPlan<D>;
+    using RPL = MlpRingPlan<D>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* ring = smem + RPL::A_BYTES;
+    uint8_t* sG = ring + RPL::RING_BYTES;
+    uint8_t* sStg = sG + RPL::G_BYTES;
+    float* sb1 = reinterpret_cast<float*>(smem + RPL::BIAS_OFF);
+    float* sb2 = sb1 + 4 * D;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RPL::BAR_OFF);
+    uint64_t* a_full = bars;
+    uint64_t* a_empty = bars + 1;
+    uint64_t* full = bars + 2;
+    uint64_t* empty = full + RPL::STAGES;
+    uint64_t* acc1_full = empty + RPL::STAGES;      // [2]
+    uint64_t* acc1_empty = acc1_full + 2;          // [2]
+    uint64_t* g_full = acc1_empty + 2;
+    uint64_t* g_empty = g_full + 1;
+    uint64_t* acc2_full = g_empty + 1;             // [2]
+    uint64_t* acc2_empty = acc2_full + 2;          // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + RPL::NBAR);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int i = threadIdx.x; i < 4 * D; i += blockDim.x) sb1[i] = b1[i];
+    for (int i = threadIdx.x; i < D; i += blockDim.x) sb2[i] = b2[i];
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        for (int i = 0; i < RPL::STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc1_full[i], 1); mbar_init(&acc1_empty[i], PL::EW);
+            mbar_init(&acc2_full[i], 1); mbar_init(&acc2_empty[i], PL::EW);
+        }
+        mbar_init(g_full, PL::EW);
+        mbar_init(g_empty, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: A per tile, then the W1 / W2 k-blocks in the MMA's order
+            int64_t it = 0, tt = 0;
+            bool ok = true;
+            auto ring_load = [&](const CUtensorMap* map, int x, int y, uint32_t bytes) -> bool {
+                const int sl = (int)(it % RPL::STAGES);
+                if (!mbar_wait_or_abort(&empty[sl], (uint32_t)(((it / RPL::STAGES) & 1) ^ 1), abort)) return false;
+                mbar_expect_tx(&full[sl], bytes);
+                tma_load_2d(ring + (size_t)sl * 16384, map, &full[sl], x, y);
+                ++it;
+                return true;
+            };
+            auto w1 = [&](int j) -> bool {
+                for (int kb = 0; kb < RPL::KB1; ++kb)
+                    if (!ring_load(&tmW1, kb * 64, j * 128, 16384)) return false;
+                return true;
+            };
+            auto w2 = [&](int j) -> bool {
+                for (int kb = 0; kb < 4; ++kb) {
+                    const int x = (kb < 2 ? 0 : 4 * D) + j * 128 + (kb & 1) * 64;
+                    if (!ring_load(&tmW2, x, 0, (uint32_t)D * 128)) return false;
+                }
+                return true;
+            };
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                const int m0 = (int)(t * 128);
+                if (!mbar_wait_or_abort(a_empty, (uint32_t)((tt & 1) ^ 1), abort)) break;
+                mbar_expect_tx(a_full, RPL::A_BYTES);
+                for (int kb = 0; kb < RPL::KB1; ++kb) tma_load_2d(sA + kb * 16384, &tmA, a_full, kb * 64, m0);
+                ok = w1(0) && (PL::NCH < 2 || w1(1));
+                for (int j = 0; ok && j < PL::NCH; ++j) ok = w2(j) && (j + 2 >= PL::NCH || w1(j + 2));
+            }
+            // copies still in flight complete before the CTA exits (bounded waits)
+            if (tt > 0) mbar_wait(a_full, (uint32_t)((tt - 1) & 1));
+            for (int64_t j = it - RPL::STAGES < 0 ? 0 : it - RPL::STAGES; j < it; ++j)
+                mbar_wait(&full[j % RPL::STAGES], (uint32_t)((j / RPL::STAGES) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t id1 = idesc_bf16(128, 128), id2 = idesc_bf16(128, D);
+            int64_t it = 0, tt = 0, c1 = 0, cg = 0;
+            bool ok = true;
+            auto g1 = [&](int j) -> bool {
+                const int b = (int)(c1 & 1);
+                if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) return false;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
+                for (int kb = 0; kb < RPL::KB1; ++kb, ++it) {
+                    const int sl = (int)(it % RPL::STAGES);
+                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / RPL::STAGES) & 1), abort)) return false;
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sA + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
+                    umma_commit(&empty[sl]);
+                }
+                umma_commit(&acc1_full[b]);
+                if (j == PL::NCH - 1) umma_commit(a_empty);
+                ++c1;
+                return true;
+            };
+            auto g2 = [&](int j) -> bool {
+                const int ab = (int)(tt & 1);
+                if (j == 0 && !mbar_wait_or_abort(&acc2_empty[ab], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) return false;
+                if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) return false;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab * D);
+                for (int kb = 0; kb < 4; ++kb, ++it) {
+                    const int sl = (int)(it % RPL::STAGES);
+                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / RPL::STAGES) & 1), abort)) return false;
+                    tc_fence_after();
+                    const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
+                    umma_commit(&empty[sl]);
+                }
+                umma_commit(g_empty);
+                if (j == PL::NCH - 1) umma_commit(&acc2_full[ab]);
+                ++cg;
+                return true;
+            };
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                if (!mbar_wait_or_abort(a_full, (uint32_t)(tt & 1), abort)) break;
+                tc_fence_after();
+                ok = g1(0) && (PL::NCH < 2 || g1(1));
+                for (int j = 0; ok && j < PL::NCH; ++j) ok = g2(j) && (j + 2 >= PL::NCH || g1(j + 2));
+            }
+        }
+    } else {
+        MlpEpiArgs<D> E{tmem, sG, sStg, sb1, sb2, acc1_full, acc1_empty, g_full, g_empty, acc2_full, acc2_empty,
+                        abort, &tmH, M, ntiles};
+        mlp_epilogue<D>(E, warp, lane);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// d = 64 variant with the weights resident in shared memory: W1 (256 x 64) and W2 (64 x 256),
+// the first halves of the duplicated forms, are loaded once per CTA; each 128-row tile's A
+// (hi and lo k-blocks, double-buffered) meets them twice, as A_hi . W^T + A_lo . W^T, and G's
+// hi and lo k-blocks likewise meet the same W2 k-blocks.  No weight traffic per tile.
+struct MlpResPlan {
+    static constexpr int D = 64;
+    static constexpr int W1_BYTES = 4 * D * 128;          // 256 rows x 64 bf16
+    static constexpr int W2_BYTES = 4 * D * 128;          // 4 k-blocks x 64 rows x 64 bf16
+    static constexpr int A_BYTES = 2 * 16384;             // hi and lo k-blocks of 128 rows
+    static constexpr int G_BYTES = 4 * 16384;
+    static constexpr int STG_BYTES = MlpPlan<64>::STG_BYTES;
+    static constexpr int OFF_W2 = W1_BYTES;
+    static constexpr int OFF_A = OFF_W2 + W2_BYTES;
+    static constexpr int OFF_G = OFF_A + 2 * A_BYTES;
+    static constexpr int OFF_STG = OFF_G + G_BYTES;
+    static constexpr int OFF_BIAS = OFF_STG + STG_BYTES;
+    static constexpr int OFF_BAR = OFF_BIAS + 5 * D * 4;
+    static constexpr int NBAR = 1 + 4 + 4 + 2 + 4;
+    static constexpr int SMEM = 1024 + OFF_BAR + NBAR * 8 + 16;
+};
+
+__global__ void __launch_bounds__(MlpPlan<64>::THREADS, 1)
+tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
+                  const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH,
+                  const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles) {
+    using RP = MlpResPlan;
+    constexpr int D = 64, NCH = 2;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sW1 = smem;
+    uint8_t* sW2 = smem + RP::OFF_W2;
+    uint8_t* sA = smem + RP::OFF_A;
+    uint8_t* sG = smem + RP::OFF_G;
+    uint8_t* sStg = smem + RP::OFF_STG;
+    float* sb1 = reinterpret_cast<float*>(smem + RP::OFF_BIAS);
+    float* sb2 = sb1 + 4 * D;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RP::OFF_BAR);
+    uint64_t* w_full = bars;
+    uint64_t* a_full = bars + 1;           // [2]
+    uint64_t* a_empty = a_full + 2;        // [2]
+    uint64_t* acc1_full = a_empty + 2;     // [2]
+    uint64_t* acc1_empty = acc1_full + 2;  // [2]
+    uint64_t* g_full = acc1_empty + 2;
+    uint64_t* g_empty = g_full + 1;
+    uint64_t* acc2_full = g_empty + 1;     // [2]
+    uint64_t* acc2_empty = acc2_full + 2;  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + RP::NBAR);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int EW = MlpPlan<64>::EW;
+
+    for (int i = threadIdx.x; i < 4 * D; i += blockDim.x) sb1[i] = b1[i];
+    for (int i = threadIdx.x; i < D; i += blockDim.x) sb2[i] = b2[i];
+    if (threadIdx.x == 0) {
+        mbar_init(w_full, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a_full[i], 1); mbar_init(&a_empty[i], 1);
+            mbar_init(&acc1_full[i], 1); mbar_init(&acc1_empty[i], EW);
+            mbar_init(&acc2_full[i], 1); mbar_init(&acc2_empty[i], EW);
+        }
+        mbar_init(g_full, EW);
+        mbar_init(g_empty, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: the weights once, then A per tile (two buffers)
+            mbar_expect_tx(w_full, RP::W1_BYTES + RP::W2_BYTES);
+            tma_load_2d(sW1, &tmW1, w_full, 0, 0);
+            for (int kb = 0; kb < 4; ++kb) tma_load_2d(sW2 + kb * 8192, &tmW2, w_full, kb * 64, 0);
+            int64_t tt = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tt) {
+                const int ab = (int)(tt & 1);
+                if (!mbar_wait_or_abort(&a_empty[ab], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) break;
+                mbar_expect_tx(&a_full[ab], RP::A_BYTES);
+                for (int kb = 0; kb < 2; ++kb)
+                    tma_load_2d(sA + ab * RP::A_BYTES + kb * 16384, &tmA, &a_full[ab], kb * 64, (int)(t * 128));
+            }
+            // copies still in flight complete before the CTA exits (bounded waits)
+            mbar_wait(w_full, 0);
+            for (int64_t j = tt - 2 < 0 ? 0 : tt - 2; j < tt; ++j) mbar_wait(&a_full[j & 1], (uint32_t)((j >> 1) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: G1_0, G1_1, G2_0, G2_1 per tile
+            const uint32_t id1 = idesc_bf16(128, 128), id2 = idesc_bf16(128, D);
+            int64_t tt = 0, c1 = 0, cg = 0;
+            bool ok = mbar_wait_or_abort(w_full, 0, abort);
+            tc_fence_after();
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                const int ab = (int)(tt & 1);
+                if (!mbar_wait_or_abort(&a_full[ab], (uint32_t)((tt >> 1) & 1), abort)) break;
+                tc_fence_after();
+                for (int j = 0; ok && j < NCH; ++j) {
+                    const int b = (int)(c1 & 1);
+                    if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
+#pragma unroll
+                    for (int kb = 0; kb < 2; ++kb) {
+                        const uint32_t a0 = su32(sA + ab * RP::A_BYTES + kb * 16384), w0 = su32(sW1 + j * 16384);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
+                    }
+                    umma_commit(&acc1_full[b]);
+                    if (j == NCH - 1) umma_commit(&a_empty[ab]);
+                    ++c1;
+                }
+                for (int j = 0; ok && j < NCH; ++j) {
+                    if (j == 0 && !mbar_wait_or_abort(&acc2_empty[ab], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) { ok = false; break; }
+                    if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab * D);
+#pragma unroll
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(sW2 + (2 * j + (kb & 1)) * 8192);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
+                    }
+                    umma_commit(g_empty);
+                    if (j == NCH - 1) umma_commit(&acc2_full[ab]);
+                    ++cg;
+                }
+            }
+        }
+    } else {
+        MlpEpiArgs<64> E{tmem, sG, sStg, sb1, sb2, acc1_full, acc1_empty, g_full, g_empty, acc2_full, acc2_empty,
+                         abort, &tmH, M, ntiles};
+        mlp_epilogue<64>(E, warp, lane);
     }
     tc_fence_before();
     __syncthreads();
@@ -793,8 +978,22 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
         NQS_LAUNCHED();
         return NQS_OK;
     };
-    if (D == 64) return launch(tc_mlp_kernel<64>, MlpPlan<64>::SMEM, MlpPlan<64>::THREADS, 0);
-    return launch(tc_mlp_kernel<128>, MlpPlan<128>::SMEM, MlpPlan<128>::THREADS, 1);
+    if (D == 64) {
+        CUtensorMap m1r;   // the whole W1 (first K half of W1d) as one 256-row box
+        NQS_TRY(make_map(&m1r, W1d, 4 * D, 2 * D, 256));
+        static int configured_res = -1;
+        int dev = 0;
+        NQS_CK(cudaGetDevice(&dev));
+        if (configured_res != dev) {
+            cudaError_t e = cudaFuncSetAttribute(tc_mlp_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpResPlan::SMEM);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_mlp_res)", __FILE__, __LINE__);
+            configured_res = dev;
+        }
+        tc_mlp_res_kernel<<<grid, MlpPlan<64>::THREADS, MlpResPlan::SMEM, s>>>(ma, m1r, m2, mh, b1, b2, M, ntiles);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    }
+    return launch(tc_mlp_kernel<128>, MlpRingPlan<128>::SMEM, MlpPlan<128>::THREADS, 1);
 }
 
 // Read and clear the device status of the tensor-core kernels (synchronous).
