@@ -31,13 +31,24 @@ __device__ __forceinline__ float logsig(float v) { return fminf(v, 0.f) - log1pf
 
 // GELU, tanh form: 0.5 x (1 + tanh(u)), u = sqrt(2/pi) (x + 0.044715 x^3).  Evaluated through
 // tanh(u) = 2 sigmoid(2u) - 1 as x / (1 + exp(-2u)), with exp(-2u) = exp2(x (c1 + c2 x^2)),
-// c1 = -2 sqrt(2/pi) log2(e), c2 = 0.044715 c1: one exp2 and one reciprocal.  For very negative
-// x the exponential overflows and the quotient is (-)0, the limit.
+// c1 = -2 sqrt(2/pi) log2(e), c2 = 0.044715 c1, on the hardware approximations ex2.approx and
+// rcp.approx (PTX ISA: ~2 ulp each).  Limits: for large x the exponential flushes to 0 and the
+// result is x; for very negative x it is +inf and the result is (-)0.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float gelu_tanh(float x) {
     constexpr float c1 = -2.f * 0.7978845608028654f * 1.4426950408889634f;
     constexpr float c2 = c1 * 0.044715f;
-    const float e = exp2f(x * fmaf(c2, x * x, c1));
-    return __fdividef(x, 1.f + e);
+    const float e = ex2_approx(x * fmaf(c2, x * x, c1));
+    return x * rcp_approx(1.f + e);
 }
 
 template <class T>
