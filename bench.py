@@ -30,8 +30,9 @@ import synth  # noqa: E402
 DEFAULT_WORKLOAD = 3          # 20-qubit transformer: the first workload with BF16 and FP32 forms
 FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from the committed ncu capture
-# named beside it; None once the kernel has changed since that capture.
+# DRAM bytes (read + write) per algorithmic byte of each transformer scope's big-pass launch, from
+# the committed ncu capture named beside it (traffic = ratio x the scope's bytes per launch); an
+# entry is removed once its kernel changes.
 NCU_TRAFFIC = {}
 
 
@@ -218,38 +219,60 @@ def run_ours(args, rank, world, local):
             kern[name] = {"ms_total": tms, "launches": cnt, "ms_per_launch": tms / cnt}
     rows_per_step = None
 
-    # roofline of the dominant hot-path kernel
+    # roofline of the dominant hot-path kernel: the transformer scope with the largest time
+    # among those whose algorithmic bytes are recorded, and the same figures for the others
     roofline = None
+    rooflines = {}
     peaks, peak_kind = load_peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2032.0)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     ffma_peak = sms * FFMA_PER_SM_PER_CLK * 2 * clk_mhz * 1e6 / 1e12
-    if cfg.arch == "transformer" and "tf_gemm" in kern:
+    tf_scopes = {"tf_gemm": "tc_gemm_kernel (tcgen05 GEMM: QKV, attention output + residual)",
+                 "tf_mlp": "tc_mlp_res_kernel (fused tcgen05 MLP block)",
+                 "tf_attention": "attention_grp_kernel (causal attention)",
+                 "tf_layernorm": "layernorm / embedding kernels",
+                 "tf_heads": "heads_kernel (LNf, heads, ratio-weighted contribution)"}
+    if cfg.arch == "transformer" and prec == "bf16":
+        peak_b = peaks.get("hbm_gbs", 6400.0)
+        peak_t = peaks.get("bf16_tflops_sustained", 1400.0)
+        for name, desc in tf_scopes.items():
+            if name not in kern:
+                continue
+            work, wbytes = P.profile_work(name)
+            if wbytes <= 0:
+                continue
+            k = kern[name]
+            sec = k["ms_per_launch"] / 1e3
+            ach_b = wbytes / k["launches"] / sec / 1e9
+            tr = NCU_TRAFFIC.get((cfg.name, name))
+            r = {"kernel": desc, "bound": "hbm", "achieved": ach_b, "peak": peak_b, "unit": "GB/s",
+                 "frac": ach_b / peak_b, "ms_per_step": k["ms_total"] / max(1, args.steps),
+                 "bytes_per_launch": wbytes / k["launches"],
+                 "traffic": tr[0] * wbytes / k["launches"] if tr else None,
+                 "traffic_source": tr[1] if tr else None,
+                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+            if work > 0:
+                # useful FLOPs (2MNK); the compensated split issues twice that on the tensor pipe
+                r["flops_per_launch"] = work / k["launches"]
+                r["flop_per_byte"] = work / wbytes
+                r["tensor_tflops"] = work / k["launches"] / sec / 1e12
+                r["tensor_frac"] = r["tensor_tflops"] / peak_t
+            rooflines[name] = r
+        if rooflines:
+            top = max(rooflines, key=lambda nm: kern[nm]["ms_total"])
+            roofline = dict(rooflines[top])
+            roofline["note"] = ("dominant kernel of the step by time; bytes = compulsory operand reads + "
+                                "result writes per launch; traffic = ncu DRAM bytes of the same launch "
+                                "shape scaled to the mean launch")
+    elif cfg.arch == "transformer" and "tf_gemm" in kern:
         work, wbytes = P.profile_work("tf_gemm")
         k = kern["tf_gemm"]
         sec = k["ms_per_launch"] / 1e3
         ach = work / k["launches"] / sec / 1e12
-        if prec == "bf16":
-            # d_model 64: 2MNK / compulsory bytes is ~20-40 FLOP/B, far below the bf16 ridge
-            # (~215 FLOP/B), so these GEMMs are bound by memory traffic, not the tensor pipe
-            peak_t = peaks.get("bf16_tflops_sustained", 1400.0)
-            peak_b = peaks.get("hbm_gbs", 6400.0)
-            ach_b = wbytes / k["launches"] / sec / 1e9
-            intensity = work / max(wbytes, 1.0)
-            tr = NCU_TRAFFIC.get((cfg.name, prec))
-            roofline = {"kernel": "tc_gemm_kernel (tcgen05, bf16 hi+lo)", "bound": "hbm", "achieved": ach_b,
-                        "peak": peak_b, "unit": "GB/s", "frac": ach_b / peak_b,
-                        "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
-                        "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
-                        "bytes_per_launch": wbytes / k["launches"], "flops_per_launch": work / k["launches"],
-                        "flop_per_byte": intensity, "tensor_tflops": ach, "tensor_frac": ach / peak_t,
-                        "note": "useful FLOPs 2MNK (the compensated split issues 2x on the tensor pipe); "
-                                "bytes = operands read once + results written once"}
-        else:
-            roofline = {"kernel": "sgemm_kernel (fp32 SIMT)", "bound": "alu", "achieved": ach, "peak": ffma_peak,
-                        "unit": "TFLOP/s", "frac": ach / ffma_peak, "traffic": None,
-                        "peak_source": f"fp32 FFMA: {sms} SMs x {FFMA_PER_SM_PER_CLK} lanes x 2 x {clk_mhz:.0f} MHz",
-                        "flops_per_launch": work / k["launches"], "bytes_per_launch": wbytes / k["launches"]}
+        roofline = {"kernel": "sgemm_kernel (fp32 SIMT)", "bound": "alu", "achieved": ach, "peak": ffma_peak,
+                    "unit": "TFLOP/s", "frac": ach / ffma_peak, "traffic": None,
+                    "peak_source": f"fp32 FFMA: {sms} SMs x {FFMA_PER_SM_PER_CLK} lanes x 2 x {clk_mhz:.0f} MHz",
+                    "flops_per_launch": work / k["launches"], "bytes_per_launch": wbytes / k["launches"]}
     elif "eloc_rows" in kern and cfg.arch == "made":
         # rows = connected in-sector x' other than x itself, counted on one step's samples
         out = vmc.step(seed=seed0 + 999)
@@ -324,6 +347,7 @@ def run_ours(args, rank, world, local):
                        "precision": prec, "compensated": True,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "roofline": roofline,
+            "rooflines": rooflines or None,
             "kernels": kern,
             "connected_rows_per_step": rows_per_step,
             "gpu_launches": launches,

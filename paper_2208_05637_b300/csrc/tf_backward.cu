@@ -68,11 +68,11 @@ ln_bwd_kernel(const float* __restrict__ x, const float* __restrict__ g, const fl
     float s = 0.f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) { v[i] = x[row * d + lane + 32 * i]; s += v[i]; }
-    const float mu = warp_sum(s) / d;
+    const float mu = warp_sum(s) * (1.f / (float)d);
     float q = 0.f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) { v[i] -= mu; q += v[i] * v[i]; }
-    const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
+    const float rstd = rsqrtf(fmaf(warp_sum(q), 1.f / (float)d, LN_EPS));
     float m1 = 0.f, m2 = 0.f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) {
@@ -83,8 +83,8 @@ ln_bwd_kernel(const float* __restrict__ x, const float* __restrict__ g, const fl
         m1 += dx;
         m2 += dx * v[i];
     }
-    m1 = warp_sum(m1) / d;
-    m2 = warp_sum(m2) / d;
+    m1 = warp_sum(m1) * (1.f / (float)d);
+    m2 = warp_sum(m2) * (1.f / (float)d);
 #pragma unroll
     for (int i = 0; i < DPL; ++i) {
         const int j = lane + 32 * i;
@@ -125,11 +125,11 @@ heads_bwd_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __r
         float s = 0.f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) { v[i] = h[row * d + lane + 32 * i]; s += v[i]; }
-        const float mu = warp_sum(s) / d;
+        const float mu = warp_sum(s) * (1.f / (float)d);
         float q = 0.f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) { v[i] -= mu; q += v[i] * v[i]; }
-        const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
+        const float rstd = rsqrtf(fmaf(warp_sum(q), 1.f / (float)d, LN_EPS));
         float y[DPL];
         float a = 0.f;
 #pragma unroll
@@ -153,8 +153,8 @@ heads_bwd_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __r
             m1 += dx;
             m2 += dx * v[i];
         }
-        m1 = warp_sum(m1) / d;
-        m2 = warp_sum(m2) / d;
+        m1 = warp_sum(m1) * (1.f / (float)d);
+        m2 = warp_sum(m2) * (1.f / (float)d);
 #pragma unroll
         for (int i = 0; i < DPL; ++i) {
             const int j = lane + 32 * i;

@@ -159,10 +159,20 @@ __device__ __forceinline__ void store_mode_vec(void* base, int64_t row, int widt
         store_floats<N>(reinterpret_cast<float*>(base) + row * width + col0, w);
     } else {
         __nv_bfloat16 hi[N], lo[N];
+        if (N >= 2) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            hi[j] = __float2bfloat16_rn(v[j]);
-            if (MODE == ACT_BF16X2) lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+            for (int j = 0; j < N; j += 2) {   // packed conversions, two columns at a time
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(v[j], v[j + 1]);
+                hi[j] = hh.x; hi[j + 1] = hh.y;
+                if (MODE == ACT_BF16X2) {
+                    const float2 hf = __bfloat1622float2(hh);
+                    const __nv_bfloat162 ll = __floats2bfloat162_rn(v[j] - hf.x, v[j + 1] - hf.y);
+                    lo[j] = ll.x; lo[j + 1] = ll.y;
+                }
+            }
+        } else {
+            hi[0] = __float2bfloat16_rn(v[0]);
+            if (MODE == ACT_BF16X2) lo[0] = __float2bfloat16_rn(v[0] - __bfloat162float(hi[0]));
         }
         const int64_t stride = MODE == ACT_BF16X2 ? 2 * (int64_t)width : width;
         __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(base) + row * stride + col0;
@@ -192,9 +202,10 @@ __device__ __forceinline__ void ln_rows_store(float (&v)[LN_ROWS][DPL], const in
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int r = 0; r < LN_ROWS; ++r) mu[r] += __shfl_xor_sync(0xffffffffu, mu[r], o);
+    const float inv_d = 1.f / (float)d;   // d is a power of two: exact
 #pragma unroll
     for (int r = 0; r < LN_ROWS; ++r) {
-        mu[r] /= d;
+        mu[r] *= inv_d;
         float t = 0.f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) { const float c = v[r][i] - mu[r]; t += c * c; }
@@ -207,7 +218,7 @@ __device__ __forceinline__ void ln_rows_store(float (&v)[LN_ROWS][DPL], const in
 #pragma unroll
     for (int r = 0; r < LN_ROWS; ++r) {
         if (rows[r] >= M) continue;
-        const float rstd = rsqrtf(q[r] / d + LN_EPS);
+        const float rstd = rsqrtf(fmaf(q[r], inv_d, LN_EPS));
         float y[DPL];
 #pragma unroll
         for (int i = 0; i < DPL; ++i) y[i] = (v[r][i] - mu[r]) * rstd * gg[i] + bb[i];
@@ -228,13 +239,15 @@ embed_ln_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __re
     if (base >= M) return;
     float v[LN_ROWS][DPL];
     int64_t rows[LN_ROWS];
+    // (sequence, position) of the first row, then advanced row by row (rows < 2^31)
+    int sq = (int)(base / T), tp = (int)(base - (int64_t)sq * T);
 #pragma unroll
     for (int r = 0; r < LN_ROWS; ++r) {
         rows[r] = base + r;
-        const int64_t row = rows[r] < M ? rows[r] : M - 1;
-        const int64_t sq = row / T;
-        const int t = t0 + (int)(row % T);
-        const int tok = t == 0 ? 2 : (int)((bits[sq] >> mc.order[t - 1]) & 1ull);
+        if (r > 0 && ++tp == T) { tp = 0; ++sq; }
+        const int sqc = rows[r] < M ? sq : (int)((M - 1) / T);
+        const int t = t0 + (rows[r] < M ? tp : (int)((M - 1) % T));
+        const int tok = t == 0 ? 2 : (int)((bits[sqc] >> mc.order[t - 1]) & 1ull);
         float e[DPL], p[DPL];
         load_row<DPL>(P + mc.tok_emb + tok * d + col0, e);
         load_row<DPL>(P + mc.pos_emb + t * d + col0, p);

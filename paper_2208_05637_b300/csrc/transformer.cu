@@ -55,16 +55,17 @@ heads_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restr
         const int j = lane + 32 * i;
         hw[i] = P[mc.head_w + j]; g[i] = P[mc.lnf_g + j]; bb[i] = P[mc.lnf_b + j];
     }
+    const float inv_d = 1.f / (float)d;   // d is a power of two: exact
     auto lnf_row = [&](int t, float (&y)[DPL]) {
         const float* row = h + (r * T + t) * (int64_t)d;
         float s = 0.f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) { y[i] = row[lane + 32 * i]; s += y[i]; }
-        const float mu = warp_sum(s) / d;
+        const float mu = warp_sum(s) * inv_d;
         float q = 0.f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) { const float c = y[i] - mu; q += c * c; }
-        const float rstd = rsqrtf(warp_sum(q) / d + LN_EPS);
+        const float rstd = rsqrtf(fmaf(warp_sum(q), inv_d, LN_EPS));
 #pragma unroll
         for (int i = 0; i < DPL; ++i) y[i] = (y[i] - mu) * rstd * g[i] + bb[i];
     };
@@ -411,27 +412,31 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
     const int64_t M = R * T;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
+        // algorithmic bytes: an activation element is 4 bytes in every storage form (fp32, or
+        // bf16 hi + lo); a plain bf16 form would be 2
+        const double act_b = MODE == ACT_BF16 ? 2.0 : 4.0;
+        const double ln_bytes = (double)M * d * (4.0 + act_b);       // h read (or written) + a written
         {
-            ProfScope ps("tf_layernorm", s);
+            ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
             embed_ln_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(mc, P, bits, R, T, 0, b.h, b.a);
             NQS_LAUNCHED();
         }
         for (int l = 0; l < mc.layers; ++l) {
             NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
             {
-                ProfScope ps("tf_attention", s);
+                ProfScope ps("tf_attention", s, 0.0, (double)M * 3 * d * 4 + (double)M * d * act_b);
                 NQS_CK(launch_attention<MODE>(b.qkv, R, T, d, mc.heads, b.o, s));
                 count_launch();
             }
             NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
             {
-                ProfScope ps("tf_layernorm", s);
+                ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
                 NQS_LAUNCHED();
             }
             NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, M, s));
             if (l + 1 < mc.layers) {
-                ProfScope ps("tf_layernorm", s);
+                ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
                 NQS_LAUNCHED();
             }
@@ -467,7 +472,7 @@ static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w
             NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, slab0 + k * slab_stride, R, 3 * d, d, TF_EPI_STORE,
                             P + mc.bqkv[l], s));
             {
-                ProfScope ps("tf_attention", s);
+                ProfScope ps("tf_step_attention", s);
                 const unsigned grid = (unsigned)((R + 7) / 8);   // one warp per prefix
                 if (dh == 16)
                     attention_step_kernel<MODE, 16><<<grid, 256, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
@@ -515,7 +520,7 @@ int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t
     a.step_pos = ha.step_pos;
     return with_dpl(mc.hidden, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
-        ProfScope ps("tf_heads", s);
+        ProfScope ps("tf_heads", s, 0.0, (double)R * T * mc.hidden * 4);
         heads_kernel<DPL><<<blocks_for(R, 8), 256, 0, s>>>(mc, P, bits, b.h, R, T, a);
         NQS_LAUNCHED();
         return NQS_OK;
