@@ -132,18 +132,15 @@ __global__ void set_u_kernel(int64_t* Udev, const int64_t* pos0, const int64_t* 
     Udev[0] = pos0[U] + pos1[U];
 }
 
-// Keep the top max_unique entries by (count desc, bits asc); one CTA, order preserved.
-__global__ void __launch_bounds__(1024)
-evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
-             int64_t* __restrict__ Udev, int64_t max_unique, uint64_t* __restrict__ obits,
-             int64_t* __restrict__ ocnt, int32_t* __restrict__ did, const int32_t* __restrict__ par,
-             int32_t* __restrict__ opar) {
+// Keep the top max_unique of the U entries (bits, cnt[, par]) by (count desc, bits asc) into
+// (obits, ocnt[, opar]) with their order preserved; one CTA of 1024 threads, U > max_unique.
+__device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
+                            const int32_t* __restrict__ par, int64_t U, int64_t max_unique,
+                            uint64_t* __restrict__ obits, int64_t* __restrict__ ocnt, int32_t* __restrict__ opar) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t s_prefix, s_need;
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t carry_sh;
-    const int64_t U = *Udev;
-    if (U <= max_unique) { if (threadIdx.x == 0) *did = 0; return; }
     // radix select of the max_unique-th largest count (counts < 2^31)
     uint32_t prefix = 0, pmask = 0;
     uint32_t need = (uint32_t)max_unique;   // how many still to take at or above prefix
@@ -216,7 +213,135 @@ evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
         carry_eq += tot_eq;
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(1024)
+evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
+             int64_t* __restrict__ Udev, int64_t max_unique, uint64_t* __restrict__ obits,
+             int64_t* __restrict__ ocnt, int32_t* __restrict__ did, const int32_t* __restrict__ par,
+             int32_t* __restrict__ opar) {
+    const int64_t U = *Udev;
+    if (U <= max_unique) { if (threadIdx.x == 0) *did = 0; return; }
+    evict_block(bits, cnt, par, U, max_unique, obits, ocnt, opar);
     if (threadIdx.x == 0) { *Udev = max_unique; *did = 1; }
+}
+
+// ---------------------------------------------------------------- one-CTA step bookkeeping
+// For buffers of at most SAMPLER_GRAPH_MAX_CAP entries the per-step bookkeeping runs in two
+// one-CTA kernels around the draws (same results as the multi-kernel sequence above).
+constexpr int BK_T = 1024;
+
+// Exclusive scan of one value per thread across the CTA; *total receives the block sum.
+__device__ int64_t bk_block_scan(int64_t v, int64_t* warp_sums, int64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t w = warp_sums[lane];
+        int64_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        warp_sums[lane] = wi - w;
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    const int64_t r = warp_sums[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// start = exclusive scan of the counts (start[U] = their sum); n1 = 0.
+__global__ void __launch_bounds__(BK_T)
+bk_prep_kernel(const int64_t* __restrict__ cnt, const int64_t* __restrict__ Udev, int64_t* __restrict__ start,
+               int64_t* __restrict__ n1) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t tot;
+    const int64_t U = *Udev;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < U; base += BK_T) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < U ? cnt[i] : 0;
+        const int64_t ex = bk_block_scan(v, warp_sums, &tot) + carry;
+        if (i < U) { start[i] = ex; n1[i] = 0; }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) start[U] = carry;
+}
+
+// After the draws: children positions (scans of the two flag arrays), merge into the spare
+// buffers (nb, nc, npar), eviction or copy back into (cb, cc, par), the unique count, and the
+// ancestor table of the next step (when the transformer cache is bound).
+__global__ void __launch_bounds__(BK_T)
+bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int64_t* __restrict__ n1,
+                 int64_t* __restrict__ pos0, int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
+                 uint64_t qbit, uint64_t* __restrict__ nb, int64_t* __restrict__ nc,
+                 int32_t* __restrict__ par, int32_t* __restrict__ npar, int64_t max_unique,
+                 const int32_t* __restrict__ anc_old, int32_t* __restrict__ anc_new, int n, int k) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t tot0, tot1;
+    const int64_t U = *Udev;
+    // flags and their scans
+    int64_t c0 = 0, c1 = 0;
+    for (int64_t base = 0; base < U; base += BK_T) {
+        const int64_t s = base + threadIdx.x;
+        const int64_t f1 = s < U ? (n1[s] > 0) : 0;
+        const int64_t f0 = s < U ? ((cc[s] - n1[s]) > 0) : 0;
+        const int64_t e0 = bk_block_scan(f0, warp_sums, &tot0) + c0;
+        const int64_t e1 = bk_block_scan(f1, warp_sums, &tot1) + c1;
+        if (s < U) { pos0[s] = e0; pos1[s] = e1; }
+        c0 += tot0;
+        c1 += tot1;
+    }
+    if (threadIdx.x == 0) { pos0[U] = c0; pos1[U] = c1; }
+    __syncthreads();
+    // merge (as merge_kernel)
+    for (int64_t s = threadIdx.x; s < U; s += BK_T) {
+        const int64_t m1 = n1[s], m0 = cc[s] - m1;
+        if (m0 > 0) {
+            const int64_t r = pos1[upper(cb, U, qbit, cb[s])];
+            nb[pos0[s] + r] = cb[s];
+            nc[pos0[s] + r] = m0;
+            if (npar) npar[pos0[s] + r] = (int32_t)s;
+        }
+        if (m1 > 0) {
+            const uint64_t key = cb[s] | qbit;
+            const int64_t r = pos0[upper(cb, U, 0, key)];
+            nb[pos1[s] + r] = key;
+            nc[pos1[s] + r] = m1;
+            if (npar) npar[pos1[s] + r] = (int32_t)s;
+        }
+    }
+    __syncthreads();
+    int64_t Un = c0 + c1;
+    if (Un > max_unique) {
+        evict_block(nb, nc, npar, Un, max_unique, cb, cc, par);
+        Un = max_unique;
+    } else {
+        for (int64_t i = threadIdx.x; i < Un; i += BK_T) {
+            cb[i] = nb[i];
+            cc[i] = nc[i];
+            if (npar) par[i] = npar[i];
+        }
+    }
+    __syncthreads();
+    if (anc_new) {
+        // one warp per prefix, lanes over the steps 0..k
+        const int lane = threadIdx.x & 31;
+        for (int64_t i = threadIdx.x >> 5; i < Un; i += BK_T / 32) {
+            const int32_t p = par[i];
+            for (int j = lane; j <= k; j += 32) anc_new[i * n + j] = j < k ? anc_old[(int64_t)p * n + j] : p;
+        }
+    }
+    if (threadIdx.x == 0) *Udev = Un;
 }
 
 __global__ void copy_back_kernel(const int32_t* __restrict__ did, const int64_t* __restrict__ Udev,
@@ -332,10 +457,25 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
     uint64_t* cb = b.bitsA; int64_t* cc = b.cntA;
     uint64_t* nb = b.bitsB; int64_t* nc = b.cntB;
     const int g = grid_for(b.cap);
+    const bool one_cta = b.cap <= SAMPLER_GRAPH_MAX_CAP;
     for (int k = 0; k < mc.n; ++k) {
         float* tr = trace ? trace + (int64_t)k * trace_stride : nullptr;
         if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, fixed_rows, s));
         else NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr, tr, s));
+        if (one_cta) {
+            // three launches: scan + zero, draws, then flags / merge / eviction / ancestors
+            bk_prep_kernel<<<1, BK_T, 0, s>>>(cc, b.U, b.start, b.n1);
+            NQS_LAUNCHED();
+            draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
+            NQS_LAUNCHED();
+            const bool anc = b.kv && k + 1 < mc.n;
+            bk_finish_kernel<<<1, BK_T, 0, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
+                                                b.kv ? b.par : nullptr, b.kv ? b.par2 : nullptr, max_unique,
+                                                anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k);
+            NQS_LAUNCHED();
+            if (anc) std::swap(b.ancA, b.ancB);
+            continue;
+        }
         NQS_TRY(launch_scan_i64(cc, b.cap, b.U, b.start, s));
         zero_kernel<<<g, 256, 0, s>>>(b.n1, b.U, b.cap);
         NQS_LAUNCHED();
