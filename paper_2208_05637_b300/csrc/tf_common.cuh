@@ -578,22 +578,31 @@ __device__ __forceinline__ float att_dot(const float (&q)[DH], const float4* __r
     return s0 + s1;
 }
 
-// Online-softmax update of one row (running max m, normaliser l, unnormalised output acc) by
-// keys u and u+1 (scores s0, s1 in the log2 domain; value rows v0, v1), or by key u alone.
+// Online-softmax update of one row (reference max m, normaliser l, unnormalised output acc) by
+// keys u and u+1 (scores s0, s1 in the log2 domain; value rows v0, v1), or by key u alone.  The
+// reference moves only when some lane of the warp sees a score more than 2^8 above it (the
+// weights exp2(s - m) then stay below 256 and the quotient acc / l is unchanged), so the
+// rescaling of acc is skipped on most keys; all lanes of the warp call this together.
 template <int DH, bool PAIR>
 __device__ __forceinline__ void att_update(float s0, float s1, const float4* __restrict__ v0,
                                            const float4* __restrict__ v1, float (&acc)[DH], float& m, float& l) {
-    const float mn = PAIR ? fmaxf(m, fmaxf(s0, s1)) : fmaxf(m, s0);
-    const float c = exp2f(m - mn);                 // 0 on the first key (m = -inf)
-    const float e0 = exp2f(s0 - mn);
-    const float e1 = PAIR ? exp2f(s1 - mn) : 0.f;
-    l = PAIR ? fmaf(l, c, e0 + e1) : fmaf(l, c, e0);
-    m = mn;
+    const float smax = PAIR ? fmaxf(s0, s1) : s0;
+    if (__any_sync(0xffffffffu, smax > m + 8.f)) {
+        const float mn = fmaxf(m, smax);
+        const float c = ex2_approx(m - mn);        // 0 on the first key (m = -inf)
+        l *= c;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) acc[j] *= c;
+        m = mn;
+    }
+    const float e0 = ex2_approx(s0 - m);
+    const float e1 = PAIR ? ex2_approx(s1 - m) : 0.f;
+    l += PAIR ? e0 + e1 : e0;
 #pragma unroll
     for (int j4 = 0; j4 < DH / 4; ++j4) {
         const float4 a = v0[j4];
-        float x0 = fmaf(e0, a.x, acc[4 * j4 + 0] * c), x1 = fmaf(e0, a.y, acc[4 * j4 + 1] * c);
-        float x2 = fmaf(e0, a.z, acc[4 * j4 + 2] * c), x3 = fmaf(e0, a.w, acc[4 * j4 + 3] * c);
+        float x0 = fmaf(e0, a.x, acc[4 * j4 + 0]), x1 = fmaf(e0, a.y, acc[4 * j4 + 1]);
+        float x2 = fmaf(e0, a.z, acc[4 * j4 + 2]), x3 = fmaf(e0, a.w, acc[4 * j4 + 3]);
         if (PAIR) {
             const float4 b = v1[j4];
             x0 = fmaf(e1, b.x, x0); x1 = fmaf(e1, b.y, x1); x2 = fmaf(e1, b.z, x2); x3 = fmaf(e1, b.w, x3);
