@@ -2,6 +2,12 @@
 backward, mini-batch gradient accumulation with forward recomputation, FP64 statistics and Adam
 (paper Eqs. total_energy, grad; Section 5.1: Adam lr 1e-3, betas (0.9, 0.99); Section 5.2
 gradient accumulation).
+
+The gradient of the VMC surrogate sum_i g_abs_i log|f(x_i)| + g_phase_i phi(x_i) is exactly the
+vector-Jacobian product with upstream gradients (g_abs, g_phase).  VMC.step hands those to the
+backward entry point directly (the backward recomputes the forward itself); with
+``autograd=True`` it goes through LogPsi and torch autograd instead, which also evaluates the
+surrogate's forward.  Both give the same gradient.
 """
 import torch
 
@@ -39,7 +45,7 @@ class VMC:
     FP64 statistics -> surrogate backward (mini-batched, recomputed) -> Adam."""
 
     def __init__(self, ham, model, params, n_samples, mini_batches=1, max_unique=None,
-                 lr=1e-3, betas=(0.9, 0.99), eps=1e-8):
+                 lr=1e-3, betas=(0.9, 0.99), eps=1e-8, autograd=False):
         self.ham, self.model = ham, model
         self.params = params.detach().requires_grad_(True)
         model.bind(self.params)
@@ -47,6 +53,7 @@ class VMC:
         self.max_unique = int(max_unique or n_samples)
         self.mini_batches = int(mini_batches)
         self.lr, self.betas, self.eps = lr, betas, eps
+        self.autograd = bool(autograd)
         self.m = torch.zeros_like(self.params, requires_grad=False)
         self.v = torch.zeros_like(self.params, requires_grad=False)
         self.t = 0
@@ -81,11 +88,17 @@ class VMC:
             nqs_local_energy(self.ham, self.model, bits[sl], ws=self._workspace(OP_LOCAL_ENERGY, per),
                              out=eloc[sl])
         stats, g_abs, g_phase = nqs_energy_stats(eloc, counts)
-        if self.params.grad is not None:
+        if self.params.grad is None:
+            self.params.grad = torch.zeros_like(self.params)
+        else:
             self.params.grad.zero_()
         for sl in self._slices(U):
-            la, ph = LogPsi.apply(self.params, self.model, bits[sl])
-            (la * g_abs[sl]).sum().add((ph * g_phase[sl]).sum()).backward()
+            if self.autograd:
+                la, ph = LogPsi.apply(self.params, self.model, bits[sl])
+                (la * g_abs[sl]).sum().add((ph * g_phase[sl]).sum()).backward()
+            else:
+                nqs_logpsi_backward(self.model, bits[sl], g_abs[sl], g_phase[sl], self.params.grad,
+                                    ws=self._workspace(OP_BACKWARD, per))
         self.t += 1
         with torch.no_grad():
             nqs_adam_step(self.params, self.params.grad, self.m, self.v, self.t, self.lr,

@@ -122,3 +122,26 @@ def test_vmc_steps_run_and_respect_variational_bound(cid):
     psi = np.exp(la.cpu().numpy().astype(np.float64) + 1j * ph.cpu().numpy())
     e_var = np.real(np.vdot(psi, sector_hamiltonian(xm, zm, coef, cfg.n_qubits, st) @ psi))
     assert e_var >= lam - 1e-5 * abs(lam)
+
+
+@pytest.mark.parametrize("cid", [2, 3])
+def test_vmc_direct_backward_equals_autograd(cid):
+    # the step's default (backward entry called with the surrogate's upstream gradients) and the
+    # torch-autograd route through LogPsi produce the same gradient and the same update, bitwise
+    import torch
+    P = lib()
+    cfg = synth.get_config(cid)
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(cfg.n_qubits, xm, zm, coef)
+    m, _ = gpu_model(cfg, beta=1.0)
+    p0 = m.params.detach().clone()
+    res = []
+    for autograd in (True, False):
+        vmc = P.VMC(ham, m, p0.clone(), cfg.n_samples, mini_batches=2, max_unique=512, autograd=autograd)
+        out = vmc.step(seed=cfg.seed_sampler + 5)
+        torch.cuda.synchronize()
+        res.append((out["stats"].cpu(), vmc.params.grad.detach().cpu().clone(), vmc.params.detach().cpu().clone()))
+    (sa, ga, pa), (sb, gb, pb) = res
+    assert torch.equal(sa, sb)
+    assert torch.equal(ga, gb)
+    assert torch.equal(pa, pb)
