@@ -208,7 +208,8 @@ int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t
                             int64_t B, const float* g_abs, float* grad, cudaStream_t s);
 
 // transformer (transformer.cu, tc_gemm.cu)
-enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3, TF_EPI_GELU2 = 4 };
+enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3, TF_EPI_GELU2 = 4,
+       TF_EPI_RESID_LN = 5 };   // h += acc + bias, then a = LayerNorm(h) as hi|lo bf16 (d = 64)
 enum { TF_WQKV = 0, TF_WO = 1, TF_W1 = 2, TF_W2 = 3 };
 struct TfBufs {
     int64_t R;            // sequences per pass
@@ -271,6 +272,10 @@ int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int6
 // h += GELU(A . W1d^T + b1) . W2d^T + b2 (compensated bf16 forms), the hidden layer kept on chip
 int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint16_t* W2d, const float* b2,
                 float* h, int64_t M, int D, cudaStream_t s);
+// h[M, 64] += A . W^T + bias, then a[M, 2*64] = hi|lo of LayerNorm(h; ln_g, ln_b) (compensated
+// BF16 transformer, d_model 64): the attention-output GEMM with the next LayerNorm fused in.
+int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
+                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s);
 int tc_status_take();
 struct TfCtx {
     const TfWeights* w;

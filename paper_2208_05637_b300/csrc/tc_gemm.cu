@@ -256,10 +256,12 @@ constexpr int TC_THREADS = 192;
 constexpr int TC_STAGE_BYTES_PER_WARP = 8192;   // two 4 KB chunk buffers, or hi + lo of one
 
 template <int EPI, bool TMA_EPI>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const __grid_constant__ CUtensorMap tmC, const float* __restrict__ bias, void* __restrict__ Cv,
-               int64_t M, int N, int K, int BN, int tmem_cols, int stages, int n_tiles_n, int64_t total_tiles) {
+               const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmD,
+               const float* __restrict__ bias, void* __restrict__ Cv, const float* __restrict__ ln_g,
+               const float* __restrict__ ln_b, int64_t M, int N, int K, int BN, int tmem_cols, int stages,
+               int n_tiles_n, int64_t total_tiles) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nkb = (K + TC_BK - 1) / TC_BK;
@@ -272,13 +274,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint64_t* empty = full + stages;
     uint64_t* tfull = empty + stages;       // [2] accumulator ready for the epilogue
     uint64_t* tempty = tfull + 2;           // [2] accumulator drained by the epilogue
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* hbar = tempty + 2;            // [4] per epilogue warp: residual rows loaded (RESID_LN)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(hbar + 4);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+        for (int b = 0; b < 4; ++b) mbar_init(&hbar[b], 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -339,6 +343,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         uint8_t* stg = sC + (size_t)(warp - 2) * TC_STAGE_BYTES_PER_WARP;
         int64_t acc = 0;
         int chunk = 0;
+        if (EPI == TF_EPI_RESID_LN && lane == 0 && (int64_t)blockIdx.x < total_tiles) {
+            // residual rows of the first tile
+            const int nrow = (int)((blockIdx.x / n_tiles_n) * TC_BM + quad * 32);
+            mbar_expect_tx(&hbar[quad], 8192);
+            tma_load_2d(stg, &tmC, &hbar[quad], 0, nrow);
+            tma_load_2d(stg + 4096, &tmC, &hbar[quad], 32, nrow);
+        }
+        __syncwarp();
         for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x, ++acc) {
             const int buf = (int)(acc & 1);
             if (!mbar_wait_or_abort(&tfull[buf], (uint32_t)((acc >> 1) & 1), abort)) break;
@@ -346,7 +358,107 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const int64_t row0 = (t / n_tiles_n) * TC_BM + quad * 32;
             const int n0 = (int)(t % n_tiles_n) * BN;
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * (tmem_cols >> 1));
-            if constexpr (TMA_EPI) {
+            if constexpr (EPI == TF_EPI_RESID_LN) {
+                // the tile spans whole rows of d = 64: lane = row.  h_new = h + acc + bias,
+                // stored back; then a = LayerNorm(h_new) as hi | lo bf16.
+                const int64_t hrow0 = (t / n_tiles_n) * TC_BM + quad * 32;
+                if (!mbar_wait_or_abort(&hbar[quad], (uint32_t)(acc & 1), abort)) break;
+                const uint32_t st = su32(stg);
+                const int sw = lane & 7;
+                // address of columns c .. c+3 of this lane's row in the staging (two 32-column halves)
+                auto saddr = [&](int c) -> uint32_t {
+                    return st + (uint32_t)((c >> 5) * 4096 + lane * 128 + ((((c & 31) >> 2) ^ sw) << 4));
+                };
+                // pass 1: h_new = h + acc + bias, in place in the staging; row sum
+                float sum = 0.f;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    float v16[16];
+                    tmem_ld16(tbase + (uint32_t)(16 * p), v16);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 16 * p + 4 * u;
+                        const uint32_t addr = saddr(c);
+                        float4 o;
+                        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(addr));
+                        o.x += v16[4 * u] + bias[c];
+                        o.y += v16[4 * u + 1] + bias[c + 1];
+                        o.z += v16[4 * u + 2] + bias[c + 2];
+                        o.w += v16[4 * u + 3] + bias[c + 3];
+                        sum += (o.x + o.y) + (o.z + o.w);
+                        st_shared_v4(addr, __float_as_uint(o.x), __float_as_uint(o.y), __float_as_uint(o.z), __float_as_uint(o.w));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+                // h_new back to global (the TMA reads the staging while the passes below read it too)
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (hrow0 < M) {
+                        tma_store_2d(&tmC, stg, 0, (int)hrow0);
+                        tma_store_2d(&tmC, stg + 4096, 32, (int)hrow0);
+                    }
+                    bulk_commit();
+                }
+                // pass 2: variance about the mean; pass 3: normalised hi | lo bf16 pairs
+                const float mu = sum * (1.f / 64.f);
+                float var = 0.f;
+#pragma unroll
+                for (int c = 0; c < 64; c += 4) {
+                    float4 o;
+                    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(saddr(c)));
+                    const float d0 = o.x - mu, d1 = o.y - mu, d2 = o.z - mu, d3 = o.w - mu;
+                    var = fmaf(d0, d0, var); var = fmaf(d1, d1, var); var = fmaf(d2, d2, var); var = fmaf(d3, d3, var);
+                }
+                const float rstd = rsqrtf(fmaf(var, 1.f / 64.f, LN_EPS));
+                uint32_t hp[32], lp[32];
+#pragma unroll
+                for (int c = 0; c < 64; c += 4) {
+                    float4 o;
+                    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(saddr(c)));
+                    const float y[4] = {(o.x - mu) * rstd * ln_g[c] + ln_b[c], (o.y - mu) * rstd * ln_g[c + 1] + ln_b[c + 1],
+                                        (o.z - mu) * rstd * ln_g[c + 2] + ln_b[c + 2], (o.w - mu) * rstd * ln_g[c + 3] + ln_b[c + 3]};
+#pragma unroll
+                    for (int q2 = 0; q2 < 4; q2 += 2) {
+                        const __nv_bfloat162 hh = __floats2bfloat162_rn(y[q2], y[q2 + 1]);
+                        const float2 hf = __bfloat1622float2(hh);
+                        const __nv_bfloat162 ll = __floats2bfloat162_rn(y[q2] - hf.x, y[q2 + 1] - hf.y);
+                        hp[(c + q2) / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+                        lp[(c + q2) / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+                    }
+                }
+                // the staging again, once the h store has read it: hi rows, then lo rows
+                if (lane == 0) bulk_wait_read<0>();
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t off = (uint32_t)(lane * 128 + ((u ^ sw) << 4));
+                    st_shared_v4(st + off, hp[4 * u], hp[4 * u + 1], hp[4 * u + 2], hp[4 * u + 3]);
+                    st_shared_v4(st + 4096 + off, lp[4 * u], lp[4 * u + 1], lp[4 * u + 2], lp[4 * u + 3]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (hrow0 < M) {
+                        tma_store_2d(&tmD, stg, 0, (int)hrow0);
+                        tma_store_2d(&tmD, stg + 4096, 64, (int)hrow0);
+                    }
+                    bulk_commit();
+                    // the next tile's residual rows into the staging once these stores have read it
+                    const int64_t tn = t + gridDim.x;
+                    if (tn < total_tiles) {
+                        bulk_wait_read<0>();
+                        mbar_expect_tx(&hbar[quad], 8192);
+                        const int nrow = (int)((tn / n_tiles_n) * TC_BM + quad * 32);
+                        tma_load_2d(stg, &tmC, &hbar[quad], 0, nrow);
+                        tma_load_2d(stg + 4096, &tmC, &hbar[quad], 32, nrow);
+                    }
+                }
+                __syncwarp();
+                continue;
+            } else if constexpr (TMA_EPI) {
                 // 128-byte chunks: 32 fp32 or 64 bf16 columns
                 constexpr int CW = (EPI == TF_EPI_STORE || EPI == TF_EPI_RESID) ? 32 : 64;
                 for (int c = 0; c < BN; c += CW, ++chunk) {
@@ -385,7 +497,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         // the staging buffers (and the results) must be complete before the CTA exits
-        if (TMA_EPI && lane == 0) bulk_wait_all();
+        if ((TMA_EPI || EPI == TF_EPI_RESID_LN) && lane == 0) bulk_wait_all();
         __syncwarp();
     }
     tc_fence_before();
@@ -911,7 +1023,7 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
     const size_t staging = tma_epi ? 4 * TC_STAGE_BYTES_PER_WARP : 0;
     // fill ~104 KB per CTA with ring stages (at least two) so that two CTAs share an SM
     const int stages = (int)std::max<size_t>(2, std::min<size_t>(6, (104 * 1024 - staging) / stage_bytes));
-    const size_t smem = 1024 + (size_t)stages * stage_bytes + staging + (2 * stages + 4) * 8 + 16;
+    const size_t smem = 1024 + (size_t)stages * stage_bytes + staging + (2 * stages + 8) * 8 + 16;
     if (smem > 220 * 1024) { set_error("tensor-core GEMM: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
     CUtensorMap ma, mb, mc;
     NQS_TRY(make_map(&ma, A, M, K, TC_BM));
@@ -935,7 +1047,8 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm)", __FILE__, __LINE__);
             configured_device[slot] = dev;
         }
-        kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, bias, C, M, N, K, BN, tcols, stages, n_tiles_n, total_tiles);
+        kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, mc, bias, C, nullptr, nullptr, M, N, K, BN, tcols, stages,
+                                              n_tiles_n, total_tiles);
         NQS_LAUNCHED();
         return NQS_OK;
     };
@@ -950,6 +1063,43 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
         case TF_EPI_GELU2 * 2 + 1: return launch(tc_gemm_kernel<TF_EPI_GELU2, true>);
         default: set_error("bad GEMM epilogue"); return NQS_ERR_INVALID_ARG;
     }
+}
+
+// Attention-output GEMM with the next LayerNorm fused into its epilogue (compensated BF16,
+// d_model 64): h += A . W^T + bias; a = hi | lo of LayerNorm(h; ln_g, ln_b).
+int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
+                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s) {
+    if (M <= 0) return NQS_OK;
+    constexpr int N = 64, BN = 64, tcols = 128;
+    if (K % 64 || K <= 0 || ((uintptr_t)h & 15) || ((uintptr_t)a_out & 15) || !bias || !ln_g || !ln_b) {
+        set_error("fused residual + LayerNorm GEMM: bad operand");
+        return NQS_ERR_INVALID_ARG;
+    }
+    const size_t stage_bytes = TC_BM * 128 + (size_t)BN * 128;
+    const size_t staging = 4 * TC_STAGE_BYTES_PER_WARP;
+    const int stages = (int)std::max<size_t>(2, std::min<size_t>(6, (104 * 1024 - staging) / stage_bytes));
+    const size_t smem = 1024 + (size_t)stages * stage_bytes + staging + (2 * stages + 8) * 8 + 16;
+    CUtensorMap ma, mb, mc, md;
+    NQS_TRY(make_map(&ma, A, M, K, TC_BM));
+    NQS_TRY(make_map(&mb, W, N, K, BN));
+    NQS_TRY(make_map(&mc, h, M, N, 32, true));
+    NQS_TRY(make_map(&md, a_out, M, 2 * N, 32));
+    const int64_t total_tiles = (M + TC_BM - 1) / TC_BM;
+    const int ctas_per_sm = (int)std::max<int64_t>(1, std::min<int64_t>(512 / tcols, (228 * 1024) / (smem + 1024)));
+    const int grid = (int)std::min<int64_t>(total_tiles, (int64_t)num_sms() * ctas_per_sm);
+    static int configured_device = -1;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<TF_EPI_RESID_LN, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm resid_ln)", __FILE__, __LINE__);
+        configured_device = dev;
+    }
+    tc_gemm_kernel<TF_EPI_RESID_LN, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N, K,
+                                                                          BN, tcols, stages, 1, total_tiles);
+    NQS_LAUNCHED();
+    return NQS_OK;
 }
 
 // Fused MLP block of the compensated transformer (see tc_mlp_kernel); D = 64 or 128.

@@ -348,6 +348,18 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
     return NQS_OK;
 }
 
+// Attention-output projection of block l with the residual add and LayerNorm 2 fused
+// (compensated BF16, d_model 64): h += Wo . o + bo; a = LN2(h).
+static int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* o, float* h,
+                       void* a, int64_t M, cudaStream_t s) {
+    const int d = mc.hidden;
+    // A (hi+lo) read, h read and written, a (hi+lo) written, weights
+    const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * 2 + (double)M * 2 * d * 2 + 2.0 * d * d * 2;
+    ProfScope ps("tf_resid_ln", s, 2.0 * (double)M * d * d, bytes);
+    return tc_gemm_bf16_resid_ln(o, w.bf16 + w.bf16_off[layer][TF_WO], P + mc.bo[layer], h, a, P + mc.ln2_g[layer],
+                                 P + mc.ln2_b[layer], M, 2 * d, s);
+}
+
 // MLP half of block l: h += W2 . gelu(W1 . a + b1) + b2.  Compensated BF16 models with d_model
 // 64 or 128 run it as one fused tensor-core kernel (the 4d hidden layer stays on chip); the
 // others as two GEMMs through the mid buffer.
@@ -428,8 +440,10 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
                 NQS_CK(launch_attention<MODE>(b.qkv, R, T, d, mc.heads, b.o, s));
                 count_launch();
             }
-            NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
-            {
+            if (MODE == ACT_BF16X2 && d == 64) {
+                NQS_TRY(tf_resid_ln(mc, P, w, l, b.o, b.h, b.a, M, s));
+            } else {
+                NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
                 ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
                 NQS_LAUNCHED();
@@ -482,9 +496,13 @@ static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w
                                                                          kc.Udev, R, d, H, b.o);
                 NQS_LAUNCHED();
             }
-            NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, R, d, d, TF_EPI_RESID, P + mc.bo[l], s));
-            layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
-            NQS_LAUNCHED();
+            if (MODE == ACT_BF16X2 && d == 64) {
+                NQS_TRY(tf_resid_ln(mc, P, w, l, b.o, b.h, b.a, R, s));
+            } else {
+                NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, R, d, d, TF_EPI_RESID, P + mc.bo[l], s));
+                layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
+                NQS_LAUNCHED();
+            }
             NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, R, s));
             if (l + 1 < mc.layers) {
                 layernorm_kernel<MODE, DPL><<<ln_grid(R), 256, 0, s>>>(b.h, R, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
