@@ -217,7 +217,7 @@ def run_ours(args, rank, world, local):
     P.profile_enable(False)
     kern = {}
     for name in ("sample", "local_energy", "logpsi_rows", "sweep_count", "term_sweep", "eloc_rows", "made_backward",
-                 "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_resid_ln", "tf_mlp", "tf_attention",
+                 "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_qkv_attention", "tf_resid_ln", "tf_mlp", "tf_attention",
                  "tf_heads", "tf_layernorm", "tf_backward", "bwd_recompute", "bwd_heads", "bwd_mlp", "bwd_attention",
                  "bwd_embed"):
         tms, cnt = P.profile_read(name)
@@ -234,6 +234,7 @@ def run_ours(args, rank, world, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     ffma_peak = sms * FFMA_PER_SM_PER_CLK * 2 * clk_mhz * 1e6 / 1e12
     tf_scopes = {"tf_gemm": "tc_gemm_kernel (tcgen05 GEMM: QKV projection)",
+                 "tf_qkv_attention": "tc_qkv_attn_kernel (fused QKV projection + causal attention)",
                  "tf_resid_ln": "tc_gemm_kernel<RESID_LN> (attention output + residual + LayerNorm 2)",
                  "tf_mlp": "tc_mlp_res_kernel (fused tcgen05 MLP block)",
                  "tf_attention": "attention_grp_kernel (causal attention)",

@@ -276,6 +276,10 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
 // BF16 transformer, d_model 64): the attention-output GEMM with the next LayerNorm fused in.
 int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
                           const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s);
+// o = causal attention of (A . Wqkv^T + bqkv) for the compensated d_model-64 transformer with
+// head size 16, without writing qkv (R sequences of T <= 64 positions; o hi|lo bf16).
+int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, void* o, int64_t R, int T,
+                          cudaStream_t s);
 int tc_status_take();
 struct TfCtx {
     const TfWeights* w;

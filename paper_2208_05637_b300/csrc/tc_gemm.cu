@@ -961,6 +961,180 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
+// ---------------------------------------------------------------- fused QKV projection + attention
+// For the compensated d_model-64 transformer with head size 16: per tile of S whole sequences
+// (S = min(8, 128 / T), S*T <= 128 rows), the MMA warp computes qkv = [a_hi | a_lo] . W^T with
+// Wqkv (192 x 64 bf16) resident in shared memory into one of two TMEM accumulators; twelve
+// attention warps move Q, K, V (+ bias) from TMEM into padded shared layouts (warp = lane
+// quadrant x {Q, K, V}), release the accumulator, and run the grouped causal attention of
+// attention_grp_kernel on them (lanes = (sequence, head), warps = query-row pairs), writing o
+// as hi | lo bf16.  qkv never goes through HBM.
+constexpr int QA_WARPS = 12;
+constexpr int QA_THREADS = 64 + 32 * QA_WARPS;
+constexpr int QA_LH = 20;                       // head stride (16 + 4 floats)
+constexpr int QA_LU = 2 * 4 * QA_LH + 4;        // K|V row stride (164 floats: rows land on distinct bank groups)
+constexpr int QA_QL = 4 * QA_LH + 4;            // Q row stride (84 floats)
+
+__device__ __forceinline__ void bar_sync_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__global__ void __launch_bounds__(QA_THREADS, 1)
+tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+                   const float* __restrict__ bqkv, void* __restrict__ o, int64_t R, int T, int S, int SS, int SQ,
+                   int64_t ntiles) {
+    constexpr int D = 64, H = 4, DH = 16;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sW = smem;                              // 192 rows x 64 bf16 (24 KB)
+    uint8_t* sA = smem + 24576;                      // hi and lo k-blocks (32 KB)
+    float* sKV = reinterpret_cast<float*>(smem + 24576 + 32768);
+    float* sQ = sKV + (size_t)S * SS;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + (size_t)S * SQ);
+    uint64_t* w_full = bars;
+    uint64_t* a_full = bars + 1;
+    uint64_t* a_empty = bars + 2;
+    uint64_t* acc_full = bars + 3;                   // [2]
+    uint64_t* acc_empty = bars + 5;                  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows_tile = S * T;
+
+    if (threadIdx.x == 0) {
+        mbar_init(w_full, 1);
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], QA_WARPS); }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: Wqkv once, then each tile's A rows
+            mbar_expect_tx(w_full, 24576);
+            tma_load_2d(sW, &tmW, w_full, 0, 0);
+            int64_t tt = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tt) {
+                if (!mbar_wait_or_abort(a_empty, (uint32_t)((tt & 1) ^ 1), abort)) break;
+                mbar_expect_tx(a_full, 32768);
+                const int y = (int)(t * rows_tile);
+                tma_load_2d(sA, &tmA, a_full, 0, y);
+                tma_load_2d(sA + 16384, &tmA, a_full, 64, y);
+            }
+            mbar_wait(w_full, 0);
+            if (tt > 0) mbar_wait(a_full, (uint32_t)((tt - 1) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: qkv = A_hi . W^T + A_lo . W^T into accumulator tt % 2
+            const uint32_t id = idesc_bf16(128, 192);
+            bool ok = mbar_wait_or_abort(w_full, 0, abort);
+            tc_fence_after();
+            int64_t tt = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                const int b = (int)(tt & 1);
+                if (!mbar_wait_or_abort(&acc_empty[b], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) break;
+                if (!mbar_wait_or_abort(a_full, (uint32_t)(tt & 1), abort)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
+#pragma unroll
+                for (int kb = 0; kb < 2; ++kb) {
+                    const uint32_t a0 = su32(sA + kb * 16384), w0 = su32(sW);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id, (kb | kk) != 0);
+                }
+                umma_commit(a_empty);
+                umma_commit(&acc_full[b]);
+            }
+        }
+    } else {
+        // ---- attention warps
+        const int e = warp - 2, q = warp & 3, part = e >> 2;     // part 0 Q, 1 K, 2 V
+        const int r = q * 32 + lane;                             // row of the tile (TMEM lane)
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        const float scale = 0.25f * 1.4426950408889634f;          // rsqrt(16) log2(e)
+        const int npairs = (T + 1) / 2;
+        const int g = lane;                                      // attention group of this lane
+        const bool g_ok = g < S * H;
+        const int gs = g_ok ? g / H : 0, gh = g & (H - 1);
+        int64_t tt = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tt) {
+            const int b = (int)(tt & 1);
+            // every attention warp reaches the named barriers below, even after a timed-out
+            // wait, and all of them leave together when the abort flag is up
+            const bool got = mbar_wait_or_abort(&acc_full[b], (uint32_t)((tt >> 1) & 1), abort);
+            tc_fence_after();
+            // stage this warp's part (64 columns) of its 32 rows
+            if (got) {
+                float v[64];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) tmem_ld16_nowait(lane_base + (uint32_t)(b * 256 + part * 64 + 16 * p), v + 16 * p);
+                tmem_wait_ld();
+                if (r < rows_tile) {
+                    const int sq = r / T, tp = r - sq * T;
+                    float* dst = part == 0 ? sQ + (size_t)sq * SQ + tp * QA_QL
+                                           : sKV + (size_t)sq * SS + tp * QA_LU + (part - 1) * (H * QA_LH);
+                    const float* bb = bqkv + part * 64;
+#pragma unroll
+                    for (int hh = 0; hh < H; ++hh)
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            const int c = hh * 16 + 4 * j4;
+                            *reinterpret_cast<float4*>(dst + hh * QA_LH + 4 * j4) =
+                                make_float4(v[c] + bb[c], v[c + 1] + bb[c + 1], v[c + 2] + bb[c + 2], v[c + 3] + bb[c + 3]);
+                        }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0 && got) mbar_arrive(&acc_empty[b]);
+            bar_sync_named(1, 32 * QA_WARPS);                    // staging complete
+            if (*abort) break;
+            const int64_t seq0 = t * S;
+            const int sv = (int)((R - seq0) < S ? (R - seq0) : S);
+            const bool act = g_ok && gs < sv;
+            const float* kvs = sKV + (size_t)gs * SS + gh * QA_LH;
+            const float* qs = sQ + (size_t)gs * SQ + gh * QA_LH;
+            const int64_t rowbase = (seq0 + gs) * T;
+            for (int p = e; p < npairs; p += QA_WARPS) {
+                const int ta = p, tb = T - 1 - p;
+                float qa[DH], qb[DH], aa[DH], ab[DH];
+#pragma unroll
+                for (int j = 0; j < DH; ++j) {
+                    qa[j] = qs[ta * QA_QL + j] * scale;
+                    qb[j] = qs[tb * QA_QL + j] * scale;
+                    aa[j] = 0.f;
+                    ab[j] = 0.f;
+                }
+                float ma = -INFINITY, la = 0.f, mb = -INFINITY, lb = 0.f;
+                if (tb != ta) {
+                    attend_keys<DH, true>(kvs, QA_LU, H * QA_LH, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
+                    if (act) att_store_row<ACT_BF16X2, DH>(aa, la, o, rowbase + ta, D, gh * DH);
+                    attend_keys<DH, false>(kvs, QA_LU, H * QA_LH, ta + 1, tb + 1, qb, ab, mb, lb, qa, aa, ma, la);
+                    if (act) att_store_row<ACT_BF16X2, DH>(ab, lb, o, rowbase + tb, D, gh * DH);
+                } else {
+                    attend_keys<DH, false>(kvs, QA_LU, H * QA_LH, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
+                    if (act) att_store_row<ACT_BF16X2, DH>(aa, la, o, rowbase + ta, D, gh * DH);
+                }
+            }
+            bar_sync_named(1, 32 * QA_WARPS);                    // shared layouts free for the next tile
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // ---------------------------------------------------------------- host: tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1098,6 +1272,35 @@ int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, f
     }
     tc_gemm_kernel<TF_EPI_RESID_LN, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N, K,
                                                                           BN, tcols, stages, 1, total_tiles);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+// Fused QKV projection + causal attention (compensated BF16, d_model 64, head size 16, T <= 64):
+// o (hi | lo bf16 [R*T, 128]) = attention of qkv = A . Wqkv^T + bqkv, A = [a_hi | a_lo] [R*T, 128].
+int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, void* o, int64_t R, int T,
+                          cudaStream_t s) {
+    if (R <= 0) return NQS_OK;
+    if (T < 1 || T > 64 || ((uintptr_t)o & 15) || !bqkv) { set_error("fused QKV attention: bad operand"); return NQS_ERR_INVALID_ARG; }
+    const int S = std::min(8, 128 / T);
+    const int SS = grp_seq_stride(T * QA_LU, 4, QA_LH, S);
+    const int SQ = grp_seq_stride(T * QA_QL, 4, QA_LH, S);
+    const size_t smem = 1024 + 24576 + 32768 + (size_t)(S * SS + S * SQ) * 4 + 7 * 8 + 16;
+    if (smem > 227 * 1024) { set_error("fused QKV attention: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
+    CUtensorMap ma, mw;
+    NQS_TRY(make_map(&ma, A, R * T, 128, 128));
+    NQS_TRY(make_map(&mw, Wd, 192, 128, 192));       // first K half of [W | W]: W itself
+    const int64_t ntiles = (R + S - 1) / S;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
+    static int configured_device = -1;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(tc_qkv_attn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_qkv_attn)", __FILE__, __LINE__);
+        configured_device = dev;
+    }
+    tc_qkv_attn_kernel<<<grid, QA_THREADS, smem, s>>>(ma, mw, bqkv, o, R, T, S, SS, SQ, ntiles);
     NQS_LAUNCHED();
     return NQS_OK;
 }

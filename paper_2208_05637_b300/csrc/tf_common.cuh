@@ -746,11 +746,11 @@ attention_grp_kernel(const float* __restrict__ qkv, int64_t R, int T, int d, int
     }
 }
 
-// Sequence stride (floats) of attention_grp_kernel's shared layout: the padding (a multiple of
-// four floats) that spreads the eight lanes of each quarter-warp over the most 16-byte bank
-// groups when they read the same key position of their (sequence, head) groups.
-inline int attention_grp_stride(int T, int H, int DH, int S) {
-    const int LH = DH + 4, LU = 2 * H * LH, base = T * LU;
+// Sequence stride (floats) of a grouped-attention shared layout whose sequences hold `base`
+// floats: the padding (a multiple of four floats) that spreads the eight lanes of each
+// quarter-warp over the most 16-byte bank groups when lanes l = (sequence l / H, head l % H)
+// read the same position (head stride LH floats).
+inline int grp_seq_stride(int base, int H, int LH, int S) {
     int best = base, best_cost = 1 << 30;
     for (int pad = 0; pad < 32; pad += 4) {
         int cost = 0;
@@ -768,6 +768,7 @@ inline int attention_grp_stride(int T, int H, int DH, int S) {
     }
     return best;
 }
+inline int attention_grp_stride(int T, int H, int DH, int S) { return grp_seq_stride(T * 2 * H * (DH + 4), H, DH + 4, S); }
 
 template <int MODE>
 inline cudaError_t launch_attention(const float* qkv, int64_t R, int T, int d, int H, void* o, cudaStream_t s) {

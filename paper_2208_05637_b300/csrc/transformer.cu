@@ -433,9 +433,15 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
             embed_ln_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(mc, P, bits, R, T, 0, b.h, b.a);
             NQS_LAUNCHED();
         }
+        const bool fused_qkv_attention = MODE == ACT_BF16X2 && d == 64 && mc.heads == 4 && T <= 64;
         for (int l = 0; l < mc.layers; ++l) {
-            NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
-            {
+            if (fused_qkv_attention) {
+                // A (hi+lo) read, o (hi+lo) written, Wqkv
+                ProfScope ps("tf_qkv_attention", s, 2.0 * (double)M * 3 * d * d,
+                             (double)M * 2 * d * 2 + (double)M * d * act_b + 3.0 * d * d * 2);
+                NQS_TRY(tc_qkv_attention_bf16(b.a, w.bf16 + w.bf16_off[l][TF_WQKV], P + mc.bqkv[l], b.o, R, T, s));
+            } else {
+                NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
                 ProfScope ps("tf_attention", s, 0.0, (double)M * 3 * d * 4 + (double)M * d * act_b);
                 NQS_CK(launch_attention<MODE>(b.qkv, R, T, d, mc.heads, b.o, s));
                 count_launch();
