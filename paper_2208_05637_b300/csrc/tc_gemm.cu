@@ -964,29 +964,61 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // ---------------------------------------------------------------- fused QKV projection + attention
 // For the compensated d_model-64 transformer with head size 16: per tile of S whole sequences
 // (S = min(8, 128 / T), S*T <= 128 rows), the MMA warp computes qkv = [a_hi | a_lo] . W^T with
-// Wqkv (192 x 64 bf16) resident in shared memory into one of two TMEM accumulators; twelve
-// attention warps move Q, K, V (+ bias) from TMEM into padded shared layouts (warp = lane
-// quadrant x {Q, K, V}), release the accumulator, and run the grouped causal attention of
-// attention_grp_kernel on them (lanes = (sequence, head), warps = query-row pairs), writing o
-// as hi | lo bf16.  qkv never goes through HBM.
-constexpr int QA_WARPS = 12;
-constexpr int QA_THREADS = 64 + 32 * QA_WARPS;
+// Wqkv (192 x 64 bf16) resident in shared memory into one of two TMEM accumulators; AW
+// attention warps (one per query-row pair, 4..14) move Q, K, V (+ bias) from TMEM into padded
+// shared layouts (each (lane quadrant, part) job taken by a warp of that quadrant), release the
+// accumulator, run the grouped causal attention of attention_grp_kernel on them (lanes =
+// (sequence, head), warps = query-row pairs) and leave o as hi | lo bf16 in a swizzled staging
+// tile that one thread writes with two TMA stores.  qkv never goes through HBM.
+constexpr int QA_MAX_WARPS = 14;
 constexpr int QA_LH = 20;                       // head stride (16 + 4 floats)
 constexpr int QA_LU = 2 * 4 * QA_LH + 4;        // K|V row stride (164 floats: rows land on distinct bank groups)
 constexpr int QA_QL = 4 * QA_LH + 4;            // Q row stride (84 floats)
+constexpr int QA_O_BYTES = 2 * 128 * 128;       // o staging: hi and lo, up to 128 rows x 128 bytes
 
 __device__ __forceinline__ void bar_sync_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
-__global__ void __launch_bounds__(QA_THREADS, 1)
+__device__ __forceinline__ float4 lds4(const float* p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(su32(p)));
+    return v;
+}
+
+// Normalised output row (acc / l) of one (row, head) into the swizzled o staging: hi at
+// sO, lo at sO + 16 KB; row r is 128 bytes (64 bf16 = 4 heads x 16) with 16-byte unit u at
+// position u ^ (r & 7), the layout of a 128B-swizzle TMA box.
+__device__ __forceinline__ void qa_stage_row(const float (&acc)[16], float l, uint8_t* sO, int r, int h) {
+    const float inv = 1.f / l;
+    uint32_t hp[8], lp[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+        const float y0 = acc[j] * inv, y1 = acc[j + 1] * inv;
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(y0, y1);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+        hp[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+        lp[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+    }
+    const uint32_t base = su32(sO) + (uint32_t)r * 128;
+#pragma unroll
+    for (int u2 = 0; u2 < 2; ++u2) {
+        const uint32_t off = (uint32_t)(((2 * h + u2) ^ (r & 7)) << 4);
+        st_shared_v4(base + off, hp[4 * u2], hp[4 * u2 + 1], hp[4 * u2 + 2], hp[4 * u2 + 3]);
+        st_shared_v4(base + 16384 + off, lp[4 * u2], lp[4 * u2 + 1], lp[4 * u2 + 2], lp[4 * u2 + 3]);
+    }
+}
+
+__global__ void __launch_bounds__(64 + 32 * QA_MAX_WARPS, 1)
 tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
-                   const float* __restrict__ bqkv, void* __restrict__ o, int64_t R, int T, int S, int SS, int SQ,
-                   int64_t ntiles) {
-    constexpr int D = 64, H = 4, DH = 16;
+                   const __grid_constant__ CUtensorMap tmO, const float* __restrict__ bqkv, int64_t R, int T, int S,
+                   int SS, int SQ, int64_t ntiles) {
+    constexpr int H = 4, DH = 16;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sW = smem;                              // 192 rows x 64 bf16 (24 KB)
     uint8_t* sA = smem + 24576;                      // hi and lo k-blocks (32 KB)
-    float* sKV = reinterpret_cast<float*>(smem + 24576 + 32768);
+    uint8_t* sO = sA + 32768;                        // o staging (32 KB)
+    float* sKV = reinterpret_cast<float*>(sO + QA_O_BYTES);
     float* sQ = sKV + (size_t)S * SS;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + (size_t)S * SQ);
     uint64_t* w_full = bars;
@@ -997,13 +1029,14 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int AW = (int)(blockDim.x >> 5) - 2;       // attention warps
     const int rows_tile = S * T;
 
     if (threadIdx.x == 0) {
         mbar_init(w_full, 1);
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
-        for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], QA_WARPS); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], AW); }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1058,14 +1091,15 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     } else {
         // ---- attention warps
-        const int e = warp - 2, q = warp & 3, part = e >> 2;     // part 0 Q, 1 K, 2 V
+        const int e = warp - 2, q = warp & 3;
+        const int qidx = e >> 2;                                 // this warp's index among its quadrant's warps
+        const int qcount = (AW - (q >= 2 ? q - 2 : q + 2) + 3) >> 2;   // warps of this quadrant
         const int r = q * 32 + lane;                             // row of the tile (TMEM lane)
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
         const float scale = 0.25f * 1.4426950408889634f;          // rsqrt(16) log2(e)
         const int npairs = (T + 1) / 2;
-        const int g = lane;                                      // attention group of this lane
-        const bool g_ok = g < S * H;
-        const int gs = g_ok ? g / H : 0, gh = g & (H - 1);
+        const bool g_ok = lane < S * H;
+        const int gs = g_ok ? lane / H : 0, gh = lane & (H - 1);
         int64_t tt = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tt) {
             const int b = (int)(tt & 1);
@@ -1073,61 +1107,71 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             // wait, and all of them leave together when the abort flag is up
             const bool got = mbar_wait_or_abort(&acc_full[b], (uint32_t)((tt >> 1) & 1), abort);
             tc_fence_after();
-            // stage this warp's part (64 columns) of its 32 rows
+            // stage Q, K, V (+ bias) of this quadrant's 32 rows: parts qidx, qidx + qcount, ...
             if (got) {
-                float v[64];
+                for (int part = qidx; part < 3; part += qcount) {
+                    float v[64];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) tmem_ld16_nowait(lane_base + (uint32_t)(b * 256 + part * 64 + 16 * p), v + 16 * p);
-                tmem_wait_ld();
-                if (r < rows_tile) {
-                    const int sq = r / T, tp = r - sq * T;
-                    float* dst = part == 0 ? sQ + (size_t)sq * SQ + tp * QA_QL
-                                           : sKV + (size_t)sq * SS + tp * QA_LU + (part - 1) * (H * QA_LH);
-                    const float* bb = bqkv + part * 64;
+                    for (int p = 0; p < 4; ++p) tmem_ld16_nowait(lane_base + (uint32_t)(b * 256 + part * 64 + 16 * p), v + 16 * p);
+                    tmem_wait_ld();
+                    if (r < rows_tile) {
+                        const int sq = r / T, tp = r - sq * T;
+                        float* dst = part == 0 ? sQ + (size_t)sq * SQ + tp * QA_QL
+                                               : sKV + (size_t)sq * SS + tp * QA_LU + (part - 1) * (H * QA_LH);
+                        const float* bb = bqkv + part * 64;
 #pragma unroll
-                    for (int hh = 0; hh < H; ++hh)
+                        for (int hh = 0; hh < H; ++hh)
 #pragma unroll
-                        for (int j4 = 0; j4 < 4; ++j4) {
-                            const int c = hh * 16 + 4 * j4;
-                            *reinterpret_cast<float4*>(dst + hh * QA_LH + 4 * j4) =
-                                make_float4(v[c] + bb[c], v[c + 1] + bb[c + 1], v[c + 2] + bb[c + 2], v[c + 3] + bb[c + 3]);
-                        }
+                            for (int j4 = 0; j4 < 4; ++j4) {
+                                const int c = hh * 16 + 4 * j4;
+                                *reinterpret_cast<float4*>(dst + hh * QA_LH + 4 * j4) =
+                                    make_float4(v[c] + bb[c], v[c + 1] + bb[c + 1], v[c + 2] + bb[c + 2], v[c + 3] + bb[c + 3]);
+                            }
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0 && got) mbar_arrive(&acc_empty[b]);
-            bar_sync_named(1, 32 * QA_WARPS);                    // staging complete
+            // the previous tile's o stores must have read the staging before it is rewritten
+            if (threadIdx.x == 64) bulk_wait_read<0>();
+            bar_sync_named(1, 32 * AW);                          // staging complete
             if (*abort) break;
-            const int64_t seq0 = t * S;
-            const int sv = (int)((R - seq0) < S ? (R - seq0) : S);
-            const bool act = g_ok && gs < sv;
             const float* kvs = sKV + (size_t)gs * SS + gh * QA_LH;
             const float* qs = sQ + (size_t)gs * SQ + gh * QA_LH;
-            const int64_t rowbase = (seq0 + gs) * T;
-            for (int p = e; p < npairs; p += QA_WARPS) {
+            for (int p = e; p < npairs; p += AW) {
                 const int ta = p, tb = T - 1 - p;
                 float qa[DH], qb[DH], aa[DH], ab[DH];
 #pragma unroll
-                for (int j = 0; j < DH; ++j) {
-                    qa[j] = qs[ta * QA_QL + j] * scale;
-                    qb[j] = qs[tb * QA_QL + j] * scale;
-                    aa[j] = 0.f;
-                    ab[j] = 0.f;
+                for (int j4 = 0; j4 < 4; ++j4) {
+                    const float4 x = lds4(qs + ta * QA_QL + 4 * j4), y = lds4(qs + tb * QA_QL + 4 * j4);
+                    qa[4 * j4] = x.x * scale; qa[4 * j4 + 1] = x.y * scale; qa[4 * j4 + 2] = x.z * scale; qa[4 * j4 + 3] = x.w * scale;
+                    qb[4 * j4] = y.x * scale; qb[4 * j4 + 1] = y.y * scale; qb[4 * j4 + 2] = y.z * scale; qb[4 * j4 + 3] = y.w * scale;
                 }
+#pragma unroll
+                for (int j = 0; j < DH; ++j) { aa[j] = 0.f; ab[j] = 0.f; }
                 float ma = -INFINITY, la = 0.f, mb = -INFINITY, lb = 0.f;
                 if (tb != ta) {
                     attend_keys<DH, true>(kvs, QA_LU, H * QA_LH, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
-                    if (act) att_store_row<ACT_BF16X2, DH>(aa, la, o, rowbase + ta, D, gh * DH);
+                    if (g_ok) qa_stage_row(aa, la, sO, gs * T + ta, gh);
                     attend_keys<DH, false>(kvs, QA_LU, H * QA_LH, ta + 1, tb + 1, qb, ab, mb, lb, qa, aa, ma, la);
-                    if (act) att_store_row<ACT_BF16X2, DH>(ab, lb, o, rowbase + tb, D, gh * DH);
+                    if (g_ok) qa_stage_row(ab, lb, sO, gs * T + tb, gh);
                 } else {
                     attend_keys<DH, false>(kvs, QA_LU, H * QA_LH, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
-                    if (act) att_store_row<ACT_BF16X2, DH>(aa, la, o, rowbase + ta, D, gh * DH);
+                    if (g_ok) qa_stage_row(aa, la, sO, gs * T + ta, gh);
                 }
             }
-            bar_sync_named(1, 32 * QA_WARPS);                    // shared layouts free for the next tile
+            fence_proxy_async_smem();
+            bar_sync_named(1, 32 * AW);                          // o staged; shared layouts free
+            if (threadIdx.x == 64) {
+                // rows of sequences past R lie beyond the tensor and are clipped by the TMA
+                const int y = (int)(t * rows_tile);
+                tma_store_2d(&tmO, sO, 0, y);
+                tma_store_2d(&tmO, sO + 16384, 64, y);
+                bulk_commit();
+            }
         }
+        if (threadIdx.x == 64) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -1285,11 +1329,13 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
     const int S = std::min(8, 128 / T);
     const int SS = grp_seq_stride(T * QA_LU, 4, QA_LH, S);
     const int SQ = grp_seq_stride(T * QA_QL, 4, QA_LH, S);
-    const size_t smem = 1024 + 24576 + 32768 + (size_t)(S * SS + S * SQ) * 4 + 7 * 8 + 16;
+    const int AW = std::max(4, std::min(QA_MAX_WARPS, (T + 1) / 2));   // one warp per query-row pair
+    const size_t smem = 1024 + 24576 + 32768 + QA_O_BYTES + (size_t)(S * SS + S * SQ) * 4 + 7 * 8 + 16;
     if (smem > 227 * 1024) { set_error("fused QKV attention: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
-    CUtensorMap ma, mw;
+    CUtensorMap ma, mw, mo;
     NQS_TRY(make_map(&ma, A, R * T, 128, 128));
     NQS_TRY(make_map(&mw, Wd, 192, 128, 192));       // first K half of [W | W]: W itself
+    NQS_TRY(make_map(&mo, o, R * T, 128, S * T));     // o: hi | lo, boxes of 64 bf16 x (S*T) rows
     const int64_t ntiles = (R + S - 1) / S;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
     static int configured_device = -1;
@@ -1300,7 +1346,7 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_qkv_attn)", __FILE__, __LINE__);
         configured_device = dev;
     }
-    tc_qkv_attn_kernel<<<grid, QA_THREADS, smem, s>>>(ma, mw, bqkv, o, R, T, S, SS, SQ, ntiles);
+    tc_qkv_attn_kernel<<<grid, 64 + 32 * AW, smem, s>>>(ma, mw, mo, bqkv, R, T, S, SS, SQ, ntiles);
     NQS_LAUNCHED();
     return NQS_OK;
 }
