@@ -1008,6 +1008,165 @@ __device__ __forceinline__ void qa_stage_row(const float (&acc)[16], float l, ui
     }
 }
 
+// ---- attention of one (sequence, head) on the mma.sync tensor path (m16n8k16, bf16 in, fp32
+// accumulate).  Every product takes the compensated form x y ~ x_hi y_hi + x_hi y_lo + x_lo y_hi
+// (hi = bf16(x), lo = bf16(x - hi): ~2^-16 relative, like the block GEMMs).  Fragment layouts
+// (PTX ISA, m16n8k16 .bf16; g = lane / 4, c = lane % 4): A regs {(g, 2c..2c+1), (g+8, 2c..),
+// (g, 2c+8..), (g+8, 2c+8..)}; B regs {(k 2c..2c+1, n g), (k 2c+8.., n g)}; C {(g, 2c), (g, 2c+1),
+// (g+8, 2c), (g+8, 2c+1)}.  MT m-tiles of 16 queries, NT n-tiles of 8 keys (T <= 16 MT, 8 NT).
+__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(hh);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&hh);
+    lo = *reinterpret_cast<const uint32_t*>(&ll);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                 "{%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+    mma16816(d, al, bh);     // small terms first
+    mma16816(d, ah, bl);
+    mma16816(d, ah, bh);
+}
+
+__device__ __forceinline__ float2 lds2(const float* p) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(su32(p)));
+    return v;
+}
+__device__ __forceinline__ float lds1(const float* p) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(su32(p)));
+    return v;
+}
+
+// qs: Q of the unit (row stride QA_QL), kv: K of the unit (row stride QA_LU; V at + 4*QA_LH);
+// the normalised output rows go to the o staging rows row0 .. row0 + T - 1, columns of head h.
+template <int MT, int NT>
+__device__ __forceinline__ void qa_unit_mma(const float* qs, const float* kv, int T, uint8_t* sO, int row0, int h,
+                                            int lane) {
+    constexpr int KK = (NT + 1) / 2;          // 16-key steps of P . V
+    const int g = lane >> 2, c = lane & 3;
+    const float scale = 0.25f * 1.4426950408889634f;   // rsqrt(16) log2(e): scores in the log2 domain
+    const float* vs = kv + 4 * QA_LH;
+    // K^T fragments: key 8 nt + g, dims 2c.. and 2c+8..
+    uint32_t kh[NT][2], kl[NT][2];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int key = min(8 * nt + g, T - 1);
+        const float2 x0 = lds2(kv + key * QA_LU + 2 * c), x1 = lds2(kv + key * QA_LU + 2 * c + 8);
+        split2(x0.x, x0.y, kh[nt][0], kl[nt][0]);
+        split2(x1.x, x1.y, kh[nt][1], kl[nt][1]);
+    }
+    float S[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        const int ra = min(16 * mt + g, T - 1), rb = min(16 * mt + g + 8, T - 1);
+        const float2 q0 = lds2(qs + ra * QA_QL + 2 * c), q1 = lds2(qs + rb * QA_QL + 2 * c);
+        const float2 q2 = lds2(qs + ra * QA_QL + 2 * c + 8), q3 = lds2(qs + rb * QA_QL + 2 * c + 8);
+        uint32_t qh[4], ql[4];
+        split2(q0.x * scale, q0.y * scale, qh[0], ql[0]);
+        split2(q1.x * scale, q1.y * scale, qh[1], ql[1]);
+        split2(q2.x * scale, q2.y * scale, qh[2], ql[2]);
+        split2(q3.x * scale, q3.y * scale, qh[3], ql[3]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            S[mt][nt][0] = S[mt][nt][1] = S[mt][nt][2] = S[mt][nt][3] = 0.f;
+            mma3(S[mt][nt], qh, ql, kh[nt], kl[nt]);
+        }
+    }
+    // causal softmax per query row (quads of four lanes share a row)
+    float inv[MT][2];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int row = 16 * mt + g + 8 * hf;
+            float m = -INFINITY;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int key = 8 * nt + 2 * c + e;
+                    const float v = key <= row ? S[mt][nt][2 * hf + e] : -INFINITY;
+                    S[mt][nt][2 * hf + e] = v;
+                    m = fmaxf(m, v);
+                }
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+            float l = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float p = ex2_approx(S[mt][nt][2 * hf + e] - m);
+                    S[mt][nt][2 * hf + e] = p;
+                    l += p;
+                }
+            l += __shfl_xor_sync(0xffffffffu, l, 1);
+            l += __shfl_xor_sync(0xffffffffu, l, 2);
+            inv[mt][hf] = 1.f / l;
+        }
+    // O = P . V
+    float O[MT][2][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) O[mt][n2][0] = O[mt][n2][1] = O[mt][n2][2] = O[mt][n2][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < KK; ++kk) {
+        uint32_t vh[2][2], vl[2][2];
+        const int k0 = min(16 * kk + 2 * c, T - 1), k1 = min(16 * kk + 2 * c + 1, T - 1);
+        const int k2 = min(16 * kk + 2 * c + 8, T - 1), k3 = min(16 * kk + 2 * c + 9, T - 1);
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) {
+            const int dcol = 8 * n2 + g;
+            split2(lds1(vs + k0 * QA_LU + dcol), lds1(vs + k1 * QA_LU + dcol), vh[n2][0], vl[n2][0]);
+            split2(lds1(vs + k2 * QA_LU + dcol), lds1(vs + k3 * QA_LU + dcol), vh[n2][1], vl[n2][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            uint32_t ph[4], pl[4];
+            split2(S[mt][2 * kk][0], S[mt][2 * kk][1], ph[0], pl[0]);
+            split2(S[mt][2 * kk][2], S[mt][2 * kk][3], ph[1], pl[1]);
+            if (2 * kk + 1 < NT) {
+                split2(S[mt][2 * kk + 1][0], S[mt][2 * kk + 1][1], ph[2], pl[2]);
+                split2(S[mt][2 * kk + 1][2], S[mt][2 * kk + 1][3], ph[3], pl[3]);
+            } else {
+                ph[2] = ph[3] = pl[2] = pl[3] = 0u;
+            }
+#pragma unroll
+            for (int n2 = 0; n2 < 2; ++n2) mma3(O[mt][n2], ph, pl, vh[n2], vl[n2]);
+        }
+    }
+    // normalised rows into the o staging (hi at sO, lo at sO + 16 KB; 128B-swizzled rows)
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            const int row = 16 * mt + g + 8 * hf;
+            if (row >= T) continue;
+            const int r = row0 + row;
+#pragma unroll
+            for (int n2 = 0; n2 < 2; ++n2) {
+                const int col = h * 16 + 8 * n2 + 2 * c;             // bf16 column of the 64-wide row
+                uint32_t hi, lo;
+                split2(O[mt][n2][2 * hf] * inv[mt][hf], O[mt][n2][2 * hf + 1] * inv[mt][hf], hi, lo);
+                const uint32_t off = (uint32_t)r * 128 + ((((col >> 3) ^ (r & 7)) << 4) | ((col & 7) << 1));
+                asm volatile("st.shared.b32 [%0], %1;" ::"r"(su32(sO) + off), "r"(hi) : "memory");
+                asm volatile("st.shared.b32 [%0], %1;" ::"r"(su32(sO) + 16384 + off), "r"(lo) : "memory");
+            }
+        }
+}
+
+template <int MT, int NT>   // MT = 0: CUDA-core row-pair attention (any T <= 64)
 __global__ void __launch_bounds__(64 + 32 * QA_MAX_WARPS, 1)
 tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
                    const __grid_constant__ CUtensorMap tmO, const float* __restrict__ bqkv, int64_t R, int T, int S,
@@ -1137,6 +1296,14 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             if (threadIdx.x == 64) bulk_wait_read<0>();
             bar_sync_named(1, 32 * AW);                          // staging complete
             if (*abort) break;
+            if constexpr (MT > 0) {
+                // tensor-core attention: one (sequence, head) unit per warp at a time
+                for (int u = e; u < S * H; u += AW) {
+                    const int us = u >> 2, uh = u & 3;
+                    qa_unit_mma<MT, NT>(sQ + (size_t)us * SQ + uh * QA_LH, sKV + (size_t)us * SS + uh * QA_LH, T, sO,
+                                        us * T, uh, lane);
+                }
+            } else {
             const float* kvs = sKV + (size_t)gs * SS + gh * QA_LH;
             const float* qs = sQ + (size_t)gs * SQ + gh * QA_LH;
             for (int p = e; p < npairs; p += AW) {
@@ -1160,6 +1327,7 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     attend_keys<DH, false>(kvs, QA_LU, H * QA_LH, 0, ta + 1, qa, aa, ma, la, qb, ab, mb, lb);
                     if (g_ok) qa_stage_row(aa, la, sO, gs * T + ta, gh);
                 }
+            }
             }
             fence_proxy_async_smem();
             bar_sync_named(1, 32 * AW);                          // o staged; shared layouts free
@@ -1329,7 +1497,12 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
     const int S = std::min(8, 128 / T);
     const int SS = grp_seq_stride(T * QA_LU, 4, QA_LH, S);
     const int SQ = grp_seq_stride(T * QA_QL, 4, QA_LH, S);
-    const int AW = std::max(4, std::min(QA_MAX_WARPS, (T + 1) / 2));   // one warp per query-row pair
+    // tensor-core attention for T <= 32 (one (sequence, head) unit per warp at a time); longer
+    // sequences use the CUDA-core row-pair form (one warp per query-row pair)
+    const int mt = T <= 16 ? 1 : (T <= 32 ? 2 : 0);
+    const int nt = T <= 16 ? 2 : (T <= 24 ? 3 : 4);
+    const int AW = mt ? std::max(4, std::min(QA_MAX_WARPS, (S * 4 + 1) / 2))
+                      : std::max(4, std::min(QA_MAX_WARPS, (T + 1) / 2));
     const size_t smem = 1024 + 24576 + 32768 + QA_O_BYTES + (size_t)(S * SS + S * SQ) * 4 + 7 * 8 + 16;
     if (smem > 227 * 1024) { set_error("fused QKV attention: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
     CUtensorMap ma, mw, mo;
@@ -1338,17 +1511,23 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
     NQS_TRY(make_map(&mo, o, R * T, 128, S * T));     // o: hi | lo, boxes of 64 bf16 x (S*T) rows
     const int64_t ntiles = (R + S - 1) / S;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
-    static int configured_device = -1;
-    int dev = 0;
-    NQS_CK(cudaGetDevice(&dev));
-    if (configured_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(tc_qkv_attn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_qkv_attn)", __FILE__, __LINE__);
-        configured_device = dev;
-    }
-    tc_qkv_attn_kernel<<<grid, 64 + 32 * AW, smem, s>>>(ma, mw, mo, bqkv, R, T, S, SS, SQ, ntiles);
-    NQS_LAUNCHED();
-    return NQS_OK;
+    auto launch = [&](auto kernel, int slot) -> int {
+        static int configured_device[4] = {-1, -1, -1, -1};
+        int dev = 0;
+        NQS_CK(cudaGetDevice(&dev));
+        if (configured_device[slot] != dev) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_qkv_attn)", __FILE__, __LINE__);
+            configured_device[slot] = dev;
+        }
+        kernel<<<grid, 64 + 32 * AW, smem, s>>>(ma, mw, mo, bqkv, R, T, S, SS, SQ, ntiles);
+        NQS_LAUNCHED();
+        return NQS_OK;
+    };
+    if (mt == 1) return launch(tc_qkv_attn_kernel<1, 2>, 0);
+    if (mt == 2 && nt == 3) return launch(tc_qkv_attn_kernel<2, 3>, 1);
+    if (mt == 2) return launch(tc_qkv_attn_kernel<2, 4>, 2);
+    return launch(tc_qkv_attn_kernel<0, 0>, 3);
 }
 
 // Fused MLP block of the compensated transformer (see tc_mlp_kernel); D = 64 or 128.
