@@ -152,15 +152,37 @@ __device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __
             if ((c & pmask) == prefix) atomicAdd(&hist[(c >> shift) & 0xffu], 1u);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            int d = 255;
-            for (; d > 0; --d) {
-                if (acc + hist[d] >= need) break;
-                acc += hist[d];
+        if (threadIdx.x < 32) {
+            // highest bin d whose count from the top reaches `need` (else 0), and the count of
+            // the bins above it: lane l scans bins 255 - 8l .. 248 - 8l, a warp scan joins them
+            const int lane = threadIdx.x;
+            uint32_t loc[8], sum = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { loc[i] = hist[255 - 8 * lane - i]; sum += loc[i]; }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            s_prefix = prefix | ((uint32_t)d << shift);
-            s_need = need - acc;
+            uint32_t acc = incl - sum;
+            int found = -1;
+            uint32_t above = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (found < 0) {
+                    if (acc + loc[i] >= need) { found = 255 - 8 * lane - i; above = acc; }
+                    else acc += loc[i];
+                }
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, found >= 0 && found > 0);
+            if (hit) {
+                if (lane == __ffs(hit) - 1) { s_prefix = prefix | ((uint32_t)found << shift); s_need = need - above; }
+            } else if (lane == 31) {
+                // no bin above 0 reaches `need`: bin 0, below all the others
+                s_prefix = prefix;
+                s_need = need - (incl - loc[7]);
+            }
         }
         __syncthreads();
         prefix = s_prefix;
@@ -280,6 +302,16 @@ bk_prep_kernel(const int64_t* __restrict__ cnt, const int64_t* __restrict__ Udev
 // After the draws: children positions (scans of the two flag arrays), merge into the spare
 // buffers (nb, nc, npar), eviction or copy back into (cb, cc, par), the unique count, and the
 // ancestor table of the next step (when the transformer cache is bound).
+// first index in [0, U) whose key exceeds v, over bits staged in shared memory
+__device__ __forceinline__ int upper_s(const uint64_t* sbits, int U, uint64_t orbit, uint64_t v) {
+    int lo = 0, hi = U;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((sbits[mid] | orbit) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(BK_T)
 bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int64_t* __restrict__ n1,
                  int64_t* __restrict__ pos0, int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
@@ -288,7 +320,9 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
                  const int32_t* __restrict__ anc_old, int32_t* __restrict__ anc_new, int n, int k) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t tot0, tot1;
+    extern __shared__ uint64_t sbits[];              // the U parent bit strings
     const int64_t U = *Udev;
+    for (int64_t i = threadIdx.x; i < U; i += BK_T) sbits[i] = cb[i];
     // flags and their scans
     int64_t c0 = 0, c1 = 0;
     for (int64_t base = 0; base < U; base += BK_T) {
@@ -303,18 +337,19 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
     }
     if (threadIdx.x == 0) { pos0[U] = c0; pos1[U] = c1; }
     __syncthreads();
-    // merge (as merge_kernel)
+    // merge (as merge_kernel), searching the staged bits
     for (int64_t s = threadIdx.x; s < U; s += BK_T) {
         const int64_t m1 = n1[s], m0 = cc[s] - m1;
+        const uint64_t bs = sbits[s];
         if (m0 > 0) {
-            const int64_t r = pos1[upper(cb, U, qbit, cb[s])];
-            nb[pos0[s] + r] = cb[s];
+            const int64_t r = pos1[upper_s(sbits, (int)U, qbit, bs)];
+            nb[pos0[s] + r] = bs;
             nc[pos0[s] + r] = m0;
             if (npar) npar[pos0[s] + r] = (int32_t)s;
         }
         if (m1 > 0) {
-            const uint64_t key = cb[s] | qbit;
-            const int64_t r = pos0[upper(cb, U, 0, key)];
+            const uint64_t key = bs | qbit;
+            const int64_t r = pos0[upper_s(sbits, (int)U, 0, key)];
             nb[pos1[s] + r] = key;
             nc[pos1[s] + r] = m1;
             if (npar) npar[pos1[s] + r] = (int32_t)s;
@@ -458,6 +493,18 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
     uint64_t* nb = b.bitsB; int64_t* nc = b.cntB;
     const int g = grid_for(b.cap);
     const bool one_cta = b.cap <= SAMPLER_GRAPH_MAX_CAP;
+    if (one_cta) {
+        // the parent bits staged by bk_finish_kernel take up to 64 KB of shared memory; the limit
+        // is raised once per device (before any captured launch: the first call is an eager one)
+        static int configured_device = -1;
+        int dev = 0;
+        NQS_CK(cudaGetDevice(&dev));
+        if (configured_device != dev) {
+            NQS_CK(cudaFuncSetAttribute(bk_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(SAMPLER_GRAPH_MAX_CAP * sizeof(uint64_t))));
+            configured_device = dev;
+        }
+    }
     for (int k = 0; k < mc.n; ++k) {
         float* tr = trace ? trace + (int64_t)k * trace_stride : nullptr;
         if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, fixed_rows, s));
@@ -469,7 +516,7 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
             draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
             NQS_LAUNCHED();
             const bool anc = b.kv && k + 1 < mc.n;
-            bk_finish_kernel<<<1, BK_T, 0, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
+            bk_finish_kernel<<<1, BK_T, b.cap * sizeof(uint64_t), s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
                                                 b.kv ? b.par : nullptr, b.kv ? b.par2 : nullptr, max_unique,
                                                 anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k);
             NQS_LAUNCHED();
