@@ -34,10 +34,10 @@ FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
 # the committed ncu capture named beside it (traffic = ratio x the scope's bytes per launch); an
 # entry is removed once its kernel changes.
 NCU_TRAFFIC = {
-    ("n2_like_20q_tf64x2", "tf_gemm"): (0.802, "profiles/tc_gemm_tf20q_bf16_ncu.md"),
-    ("n2_like_20q_tf64x2", "tf_mlp"): (0.780, "profiles/tc_mlp_tf20q_bf16_ncu.md"),
-    ("n2_like_20q_tf64x2", "tf_attention"): (0.926, "profiles/attention_tf20q_bf16_ncu.md"),
-    ("n2_like_20q_tf64x2", "tf_layernorm"): (0.714, "profiles/layernorm_tf20q_bf16_ncu.md"),
+    ("n2_like_20q_tf64x2", "tf_qkv_attention"): (0.706, "profiles/qkv_attention_tf20q_bf16_ncu.md"),
+    ("n2_like_20q_tf64x2", "tf_resid_ln"): (0.823, "profiles/resid_ln_tf20q_bf16_ncu.md"),
+    ("n2_like_20q_tf64x2", "tf_mlp"): (0.782, "profiles/tc_mlp_tf20q_bf16_ncu.md"),
+    ("n2_like_20q_tf64x2", "tf_layernorm"): (0.689, "profiles/layernorm_tf20q_bf16_ncu.md"),
     ("n2_like_20q_tf64x2", "tf_heads"): (0.769, "profiles/heads_tf20q_bf16_ncu.md"),
 }
 
