@@ -907,47 +907,61 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer: G1_0, G1_1, G2_0, G2_1 per tile
+            // ---- MMA issuer.  Order G1_0(t0), G1_1(t0), then per tile G2_0(t), G1_0(t+1), G2_1(t),
+            // G1_1(t+1): the next tile's W1 products run while the epilogue works on this tile's
+            // GELU, so the epilogue never waits for them.
             const uint32_t id1 = idesc_bf16(128, 128), id2 = idesc_bf16(128, D);
             int64_t tt = 0, c1 = 0, cg = 0;
             bool ok = mbar_wait_or_abort(w_full, 0, abort);
             tc_fence_after();
-            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
-                const int ab = (int)(tt & 1);
-                if (!mbar_wait_or_abort(&a_full[ab], (uint32_t)((tt >> 1) & 1), abort)) break;
+            auto g1 = [&](int j, int ab) -> bool {
+                const int b = (int)(c1 & 1);
+                if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) return false;
                 tc_fence_after();
-                for (int j = 0; ok && j < NCH; ++j) {
-                    const int b = (int)(c1 & 1);
-                    if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
+                const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
 #pragma unroll
-                    for (int kb = 0; kb < 2; ++kb) {
-                        const uint32_t a0 = su32(sA + ab * RP::A_BYTES + kb * 16384), w0 = su32(sW1 + j * 16384);
+                for (int kb = 0; kb < 2; ++kb) {
+                    const uint32_t a0 = su32(sA + ab * RP::A_BYTES + kb * 16384), w0 = su32(sW1 + j * 16384);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
-                    }
-                    umma_commit(&acc1_full[b]);
-                    if (j == NCH - 1) umma_commit(&a_empty[ab]);
-                    ++c1;
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
                 }
-                for (int j = 0; ok && j < NCH; ++j) {
-                    if (j == 0 && !mbar_wait_or_abort(&acc2_empty[ab], (uint32_t)(((tt >> 1) & 1) ^ 1), abort)) { ok = false; break; }
-                    if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab * D);
+                umma_commit(&acc1_full[b]);
+                if (j == NCH - 1) umma_commit(&a_empty[ab]);
+                ++c1;
+                return true;
+            };
+            auto g2 = [&](int j, int64_t ttile) -> bool {
+                const int ab2 = (int)(ttile & 1);
+                if (j == 0 && !mbar_wait_or_abort(&acc2_empty[ab2], (uint32_t)(((ttile >> 1) & 1) ^ 1), abort)) return false;
+                if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) return false;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab2 * D);
 #pragma unroll
-                    for (int kb = 0; kb < 4; ++kb) {
-                        const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(sW2 + (2 * j + (kb & 1)) * 8192);
+                for (int kb = 0; kb < 4; ++kb) {
+                    const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(sW2 + (2 * j + (kb & 1)) * 8192);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
-                    }
-                    umma_commit(g_empty);
-                    if (j == NCH - 1) umma_commit(&acc2_full[ab]);
-                    ++cg;
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
                 }
+                umma_commit(g_empty);
+                if (j == NCH - 1) umma_commit(&acc2_full[ab2]);
+                ++cg;
+                return true;
+            };
+            auto a_ready = [&](int64_t ttile) -> bool {
+                if (!mbar_wait_or_abort(&a_full[ttile & 1], (uint32_t)((ttile >> 1) & 1), abort)) return false;
+                tc_fence_after();
+                return true;
+            };
+            if (ok && (int64_t)blockIdx.x < ntiles) ok = a_ready(0) && g1(0, 0) && g1(1, 0);
+            for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
+                const bool has_next = t + gridDim.x < ntiles;
+                const int abn = (int)((tt + 1) & 1);
+                ok = g2(0, tt);
+                if (ok && has_next) ok = a_ready(tt + 1) && g1(0, abn);
+                ok = ok && g2(1, tt);
+                if (ok && has_next) ok = g1(1, abn);
             }
         }
     } else {
