@@ -163,18 +163,18 @@ heads_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restr
 // Attention of position k for R prefixes whose keys and values of positions j < k sit in the
 // per-step QKV slabs of the sampler cache (slab j holds [cap][3d] for the prefixes of step j;
 // anc[r * n + j] is the slot of prefix r's ancestor at step j; position k is row r of slab k).
-// One warp per prefix, lanes over the key positions j = lane, lane + 32 (k < 64): every lane
-// resolves its ancestor slot once, then per head: scores, warp max / sum in the log2 domain,
-// and the weighted value rows summed across the lanes.
+// One CTA per prefix, one warp per head, lanes over the key positions j = lane, lane + 32
+// (k < 64): every lane resolves its ancestor slot, then scores, warp max / sum in the log2
+// domain and the weighted value rows summed across the lanes.
 template <int MODE, int DH>
 __global__ void __launch_bounds__(256)
 attention_step_kernel(const float* __restrict__ slab0, int64_t slab_stride, int64_t cap,
                       const int32_t* __restrict__ anc, int n, int k, const int64_t* __restrict__ Udev,
                       int64_t R, int d, int H, void* __restrict__ o) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+    const int64_t r = blockIdx.x;
     const int64_t U = min(*Udev, R);
-    if (r >= U) return;
+    if (r >= U || h >= H) return;
     const int ld = 3 * d;
     const float scale = rsqrtf((float)DH) * 1.4426950408889634f;   // log2 domain
     const float* own = slab0 + (int64_t)k * slab_stride + r * ld;
@@ -191,44 +191,42 @@ attention_step_kernel(const float* __restrict__ slab0, int64_t slab_stride, int6
         }
         kr[h2] = slab0 + (int64_t)j * slab_stride + slot * ld;
     }
-    for (int h = 0; h < H; ++h) {
-        float q[DH];
+    float q[DH];
+#pragma unroll
+    for (int j4 = 0; j4 < DH / 4; ++j4) {
+        const float4 x = reinterpret_cast<const float4*>(own + h * DH)[j4];
+        q[4 * j4] = x.x * scale; q[4 * j4 + 1] = x.y * scale; q[4 * j4 + 2] = x.z * scale; q[4 * j4 + 3] = x.w * scale;
+    }
+    float sc[2] = {-INFINITY, -INFINITY};
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2)
+        if (kr[h2]) sc[h2] = att_dot<DH>(q, reinterpret_cast<const float4*>(kr[h2] + d + h * DH));
+    float m = fmaxf(sc[0], sc[1]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    float e[2], l = 0.f;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) { e[h2] = kr[h2] ? exp2f(sc[h2] - m) : 0.f; l += e[h2]; }
+    l = warp_sum(l);
+    float acc[DH];
+#pragma unroll
+    for (int c = 0; c < DH; ++c) acc[c] = 0.f;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        if (!kr[h2]) continue;
+        const float4* vr = reinterpret_cast<const float4*>(kr[h2] + 2 * d + h * DH);
 #pragma unroll
         for (int j4 = 0; j4 < DH / 4; ++j4) {
-            const float4 x = reinterpret_cast<const float4*>(own + h * DH)[j4];
-            q[4 * j4] = x.x * scale; q[4 * j4 + 1] = x.y * scale; q[4 * j4 + 2] = x.z * scale; q[4 * j4 + 3] = x.w * scale;
+            const float4 v4 = vr[j4];
+            acc[4 * j4] = fmaf(e[h2], v4.x, acc[4 * j4]);
+            acc[4 * j4 + 1] = fmaf(e[h2], v4.y, acc[4 * j4 + 1]);
+            acc[4 * j4 + 2] = fmaf(e[h2], v4.z, acc[4 * j4 + 2]);
+            acc[4 * j4 + 3] = fmaf(e[h2], v4.w, acc[4 * j4 + 3]);
         }
-        float sc[2] = {-INFINITY, -INFINITY};
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2)
-            if (kr[h2]) sc[h2] = att_dot<DH>(q, reinterpret_cast<const float4*>(kr[h2] + d + h * DH));
-        float m = fmaxf(sc[0], sc[1]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-        float e[2], l = 0.f;
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) { e[h2] = kr[h2] ? exp2f(sc[h2] - m) : 0.f; l += e[h2]; }
-        l = warp_sum(l);
-        float acc[DH];
-#pragma unroll
-        for (int c = 0; c < DH; ++c) acc[c] = 0.f;
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            if (!kr[h2]) continue;
-            const float4* vr = reinterpret_cast<const float4*>(kr[h2] + 2 * d + h * DH);
-#pragma unroll
-            for (int j4 = 0; j4 < DH / 4; ++j4) {
-                const float4 v4 = vr[j4];
-                acc[4 * j4] = fmaf(e[h2], v4.x, acc[4 * j4]);
-                acc[4 * j4 + 1] = fmaf(e[h2], v4.y, acc[4 * j4 + 1]);
-                acc[4 * j4 + 2] = fmaf(e[h2], v4.z, acc[4 * j4 + 2]);
-                acc[4 * j4 + 3] = fmaf(e[h2], v4.w, acc[4 * j4 + 3]);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < DH; ++c) acc[c] = warp_sum(acc[c]);
-        if (lane == 0) att_store_row<MODE, DH>(acc, l, o, r, d, h * DH);
     }
+#pragma unroll
+    for (int c = 0; c < DH; ++c) acc[c] = warp_sum(acc[c]);
+    if (lane == 0) att_store_row<MODE, DH>(acc, l, o, r, d, h * DH);
 }
 
 // Per-sample sum of the row contributions (TwoSum), one CTA per sample.
@@ -493,13 +491,13 @@ static int tf_step_mode(const ModelConst& mc, const float* P, const TfWeights& w
                             P + mc.bqkv[l], s));
             {
                 ProfScope ps("tf_step_attention", s);
-                const unsigned grid = (unsigned)((R + 7) / 8);   // one warp per prefix
+                const unsigned grid = (unsigned)R;                // one CTA per prefix, one warp per head
                 if (dh == 16)
-                    attention_step_kernel<MODE, 16><<<grid, 256, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
-                                                                         kc.Udev, R, d, H, b.o);
+                    attention_step_kernel<MODE, 16><<<grid, 32 * H, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
+                                                                            kc.Udev, R, d, H, b.o);
                 else
-                    attention_step_kernel<MODE, 32><<<grid, 256, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
-                                                                         kc.Udev, R, d, H, b.o);
+                    attention_step_kernel<MODE, 32><<<grid, 32 * H, 0, s>>>(slab0, slab_stride, kc.cap, kc.anc, mc.n, k,
+                                                                            kc.Udev, R, d, H, b.o);
                 NQS_LAUNCHED();
             }
             if (MODE == ACT_BF16X2 && d == 64) {
