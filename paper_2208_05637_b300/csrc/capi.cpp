@@ -798,7 +798,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
             if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
             for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
                 const int64_t R = std::min(e.tf.R, rows - r0);
-                NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s));
+                NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s, true));
                 HeadArgsHost ha{};
                 ha.mode = 1; ha.xsample = bits + lo; ha.la_x = e.la + lo; ha.ph_x = e.ph + lo;
                 ha.seg = e.off; ha.seg_stride = e.ntiles; ha.nseg = nb; ha.row0 = r0; ha.S = e.S;

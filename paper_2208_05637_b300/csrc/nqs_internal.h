@@ -214,6 +214,8 @@ enum { TF_WQKV = 0, TF_WO = 1, TF_W1 = 2, TF_W2 = 3 };
 struct TfBufs {
     int64_t R;            // sequences per pass
     float *h, *a, *qkv, *o, *mid;
+    float *logit, *hph;      // per-row head logits and per-sequence h of position n - 2 (fused heads)
+    bool fused_heads;        // the last forward left logit / hph instead of the final h
 };
 struct TfWeights {
     const float* fp32 = nullptr;
@@ -248,8 +250,10 @@ int64_t tf_seq_capacity(const ModelConst& mc);
 void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b);
 int64_t tf_bf16_weight_elems(const ModelConst& mc);
 int tf_prepare_weights(const ModelConst& mc, const float* P, TfWeights& w, cudaStream_t s);
+// head_logits: whole sequences whose heads follow (modes 0 and 1) may have the last block leave
+// per-row head logits instead of the final h (compensated d_model 64)
 int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
-               int64_t R, int T, TfBufs& b, cudaStream_t s);
+               int64_t R, int T, TfBufs& b, cudaStream_t s, bool head_logits = false);
 int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t R, int T,
              const TfBufs& b, const HeadArgsHost& ha, cudaStream_t s);
 int tf_step(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits, int64_t R, int k,
@@ -269,9 +273,18 @@ size_t tf_bwd_workspace(const ModelConst& mc, int64_t B);
 int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
                 const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
 // status of the tensor-core kernels' bounded waits; synchronous, clears the flag
-// h += GELU(A . W1d^T + b1) . W2d^T + b2 (compensated bf16 forms), the hidden layer kept on chip
+// Head form of the last block's fused MLP (d_model 64): per row the output-head logit of
+// LNf(h) and, on rows at position n - 2, the four phase-head dot products (h is not stored).
+struct TcMlpHead {
+    const float *lnf_g, *lnf_b, *head_w, *head_b;
+    int n;
+    float* logit;   // [M]
+    float* hph;     // [M / n][64]: h of position n - 2
+};
+// h += GELU(A . W1d^T + b1) . W2d^T + b2 (compensated bf16 forms), the hidden layer kept on chip;
+// with hd, the head form instead.
 int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint16_t* W2d, const float* b2,
-                float* h, int64_t M, int D, cudaStream_t s);
+                float* h, int64_t M, int D, cudaStream_t s, const TcMlpHead* hd = nullptr);
 // h[M, 64] += A . W^T + bias, then a[M, 2*64] = hi|lo of LayerNorm(h; ln_g, ln_b) (compensated
 // BF16 transformer, d_model 64): the attention-output GEMM with the next LayerNorm fused in.
 int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,

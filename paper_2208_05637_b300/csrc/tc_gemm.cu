@@ -542,6 +542,22 @@ struct MlpRingPlan {                                      // weights streamed th
     static constexpr int SMEM = 1024 + BAR_OFF + NBAR * 8 + 16;
 };
 
+// Head form of the last block's MLP: instead of h, the epilogue leaves per row the output-head
+// logit LNf(h) . head_w + head_b[t] (t = row mod n) and, on rows with t = n - 2, the four
+// phase-head dot products LNf(h) . phase_w[k] + phase_b[k] (k = 0..3, per sequence).
+struct MlpHeadArgs {
+    const float *lnf_g, *lnf_b, *head_w, *head_b;
+    int n;
+    float* logit;               // [M]
+    float* hph;                 // [M / n][64]: h of position n - 2 (the phase head's input)
+};
+
+__device__ __forceinline__ float4 lds4f(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
 // Epilogue warps of the fused MLP (both variants): per hidden chunk, GELU of the warp's column
 // slice of acc1 split into hi | lo and written into G; per tile, h += acc2 + b2 by TMA reduce-adds.
 template <int D>
@@ -553,9 +569,12 @@ struct MlpEpiArgs {
     volatile int* abort;
     const CUtensorMap* tmH;
     int64_t M, ntiles;
+    uint64_t* hbar;             // [4] head form: residual rows loaded, per lane quadrant
+    MlpHeadArgs head;
+    const float* sgw;           // head form: lnf_g * head_w [D], sum of it, sum(lnf_b * head_w)
 };
 
-template <int D>
+template <int D, bool HEAD = false>
 __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, int lane) {
     using PL = MlpPlan<D>;
     const uint32_t tmem = E.tmem;
@@ -572,11 +591,31 @@ __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, i
         const int q = warp & 3, sl = (warp - 2) >> 2;
         const int r = q * 32 + lane;                       // row within the tile
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const bool res_warp = sl < PL::RES_SLICES;
-        uint8_t* stg = sStg + (size_t)(q + 4 * (res_warp ? sl : 0)) * 4096;
+        const bool res_warp = HEAD ? sl == 0 : sl < PL::RES_SLICES;
+        // head form: one warp per quadrant owns whole rows (64 fp32 = 8 KB of staging)
+        uint8_t* stg = HEAD ? sStg + (size_t)q * 8192 : sStg + (size_t)(q + 4 * (res_warp ? sl : 0)) * 4096;
         int64_t tt = 0, c1 = 0, cg = 0;
         bool ok = true;
+        if (HEAD && res_warp && lane == 0 && (int64_t)blockIdx.x < ntiles) {
+            // residual rows of the first tile
+            const int y = (int)(blockIdx.x * 128 + q * 32);
+            mbar_expect_tx(&E.hbar[q], 8192);
+            tma_load_2d(stg, &tmH, &E.hbar[q], 0, y);
+            tma_load_2d(stg + 4096, &tmH, &E.hbar[q], 32, y);
+        }
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tt) {
+            // head form: this lane's row, its sequence and position, the head bias (loaded early)
+            int64_t hd_row = 0, hd_seq = 0;
+            int hd_pos = 0;
+            float hd_b = 0.f;
+            if (HEAD && res_warp) {
+                hd_row = t * 128 + r;
+                const int64_t seq0 = (t * 128) / E.head.n;
+                const int pq = (int)(t * 128 - seq0 * E.head.n) + r;   // < n + 128
+                hd_seq = seq0 + pq / E.head.n;
+                hd_pos = pq - (int)(hd_seq - seq0) * E.head.n;
+                hd_b = __ldg(E.head.head_b + hd_pos);
+            }
             for (int j = 0; j < PL::NCH; ++j) {
                 const int b = (int)(c1 & 1);
                 if (!mbar_wait_or_abort(&acc1_full[b], (uint32_t)((c1 >> 1) & 1), abort)) { ok = false; break; }
@@ -626,7 +665,61 @@ __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, i
             const int ab = (int)(tt & 1);
             if (!mbar_wait_or_abort(&acc2_full[ab], (uint32_t)((tt >> 1) & 1), abort)) break;
             tc_fence_after();
-            if (res_warp) {
+            if (HEAD && res_warp) {
+                // h_new = h + acc2 + b2, never stored.  With LNf folded into the output head,
+                // logit = rstd (h . gw - mean sum(gw)) + lnf_b . head_w + head_b[t] (gw = lnf_g * head_w),
+                // so one pass over the row gives the dot product and, from the 16-column chunks'
+                // means and squared deviations, the row's mean and variance; the rows of position
+                // n - 2 also leave h for the phase head.
+                if (!mbar_wait_or_abort(&E.hbar[q], (uint32_t)(tt & 1), abort)) break;
+                const uint32_t st = su32(stg);
+                const int sw = lane & 7;
+                auto saddr = [&](int c) -> uint32_t {
+                    return st + (uint32_t)((c >> 5) * 4096 + lane * 128 + ((((c & 31) >> 2) ^ sw) << 4));
+                };
+                const float* gw = E.sgw;
+                const bool ph_row = hd_pos == E.head.n - 2 && hd_row < M;
+                float4* ph_dst = reinterpret_cast<float4*>(E.head.hph + hd_seq * 64);
+                float dot = 0.f, m2 = 0.f, cm[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    float x[16];
+                    tmem_ld16(lane_base + 256u + (uint32_t)(ab * D + 16 * p), x);
+                    float cs = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 16 * p + 4 * u;
+                        const float4 o = lds4f(saddr(c));
+                        const float4 b4 = lds4f(su32(sb2 + c));
+                        const float4 g4 = lds4f(su32(gw + c));
+                        x[4 * u] += o.x + b4.x;
+                        x[4 * u + 1] += o.y + b4.y;
+                        x[4 * u + 2] += o.z + b4.z;
+                        x[4 * u + 3] += o.w + b4.w;
+                        cs += (x[4 * u] + x[4 * u + 1]) + (x[4 * u + 2] + x[4 * u + 3]);
+                        dot = fmaf(x[4 * u], g4.x, dot); dot = fmaf(x[4 * u + 1], g4.y, dot);
+                        dot = fmaf(x[4 * u + 2], g4.z, dot); dot = fmaf(x[4 * u + 3], g4.w, dot);
+                        if (ph_row) ph_dst[c >> 2] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+                    }
+                    cm[p] = cs * (1.f / 16.f);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) { const float dv = x[i] - cm[p]; m2 = fmaf(dv, dv, m2); }
+                }
+                const float mu = ((cm[0] + cm[1]) + (cm[2] + cm[3])) * 0.25f;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) { const float dv = cm[p] - mu; m2 = fmaf(16.f * dv, dv, m2); }
+                const float rstd = rsqrtf(fmaf(m2, 1.f / 64.f, LN_EPS));
+                if (hd_row < M) E.head.logit[hd_row] = rstd * (dot - mu * gw[64]) + gw[65] + hd_b;
+                // the next tile's residual rows into the staging (this warp has read it)
+                __syncwarp();
+                const int64_t tn = t + gridDim.x;
+                if (lane == 0 && tn < ntiles) {
+                    const int y = (int)(tn * 128 + q * 32);
+                    mbar_expect_tx(&E.hbar[q], 8192);
+                    tma_load_2d(stg, &tmH, &E.hbar[q], 0, y);
+                    tma_load_2d(stg + 4096, &tmH, &E.hbar[q], 32, y);
+                }
+            } else if (!HEAD && res_warp) {
                 const int64_t row0 = t * 128 + q * 32;
 #pragma unroll
                 for (int c = 0; c < PL::RC; c += 32) {
@@ -829,15 +922,17 @@ struct MlpResPlan {
     static constexpr int OFF_G = OFF_A + 2 * A_BYTES;
     static constexpr int OFF_STG = OFF_G + G_BYTES;
     static constexpr int OFF_BIAS = OFF_STG + STG_BYTES;
-    static constexpr int OFF_BAR = OFF_BIAS + 5 * D * 4;
-    static constexpr int NBAR = 1 + 4 + 4 + 2 + 4;
+    static constexpr int OFF_BAR = OFF_BIAS + (5 * D + 68) * 4;   // b1, b2, head form: lnf_g * head_w, two sums
+    static constexpr int NBAR = 1 + 4 + 4 + 2 + 4 + 4;   // ..., head form: residual rows per quadrant
     static constexpr int SMEM = 1024 + OFF_BAR + NBAR * 8 + 16;
 };
 
+template <bool HEAD>
 __global__ void __launch_bounds__(MlpPlan<64>::THREADS, 1)
 tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
                   const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH,
-                  const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles) {
+                  const float* __restrict__ b1, const float* __restrict__ b2, int64_t M, int64_t ntiles,
+                  MlpHeadArgs head) {
     using RP = MlpResPlan;
     constexpr int D = 64, NCH = 2;
     extern __shared__ uint8_t smem_raw[];
@@ -859,6 +954,7 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     uint64_t* g_empty = g_full + 1;
     uint64_t* acc2_full = g_empty + 1;     // [2]
     uint64_t* acc2_empty = acc2_full + 2;  // [2]
+    uint64_t* hbar = acc2_empty + 2;       // [4]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + RP::NBAR);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -866,6 +962,16 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
     for (int i = threadIdx.x; i < 4 * D; i += blockDim.x) sb1[i] = b1[i];
     for (int i = threadIdx.x; i < D; i += blockDim.x) sb2[i] = b2[i];
+    float* sgw = sb2 + D;            // head form: lnf_g * head_w [D], then sum(lnf_g * head_w), sum(lnf_b * head_w)
+    if (HEAD) {
+        for (int i = threadIdx.x; i < D; i += blockDim.x) sgw[i] = head.lnf_g[i] * head.head_w[i];
+        if (threadIdx.x == 0) {
+            float a = 0.f, c = 0.f;
+            for (int i = 0; i < D; ++i) { a = fmaf(head.lnf_g[i], head.head_w[i], a); c = fmaf(head.lnf_b[i], head.head_w[i], c); }
+            sgw[D] = a;
+            sgw[D + 1] = c;
+        }
+    }
     if (threadIdx.x == 0) {
         mbar_init(w_full, 1);
         for (int i = 0; i < 2; ++i) {
@@ -875,6 +981,7 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
         mbar_init(g_full, EW);
         mbar_init(g_empty, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&hbar[i], 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -966,8 +1073,8 @@ tc_mlp_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
     } else {
         MlpEpiArgs<64> E{tmem, sG, sStg, sb1, sb2, acc1_full, acc1_empty, g_full, g_empty, acc2_full, acc2_empty,
-                         abort, &tmH, M, ntiles};
-        mlp_epilogue<64>(E, warp, lane);
+                         abort, &tmH, M, ntiles, hbar, head, sgw};
+        mlp_epilogue<64, HEAD>(E, warp, lane);
     }
     tc_fence_before();
     __syncthreads();
@@ -1546,9 +1653,10 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
 
 // Fused MLP block of the compensated transformer (see tc_mlp_kernel); D = 64 or 128.
 int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint16_t* W2d, const float* b2,
-                float* h, int64_t M, int D, cudaStream_t s) {
+                float* h, int64_t M, int D, cudaStream_t s, const TcMlpHead* hd) {
     if (M <= 0) return NQS_OK;
     if (D != 64 && D != 128) { set_error("fused MLP needs d_model 64 or 128"); return NQS_ERR_UNSUPPORTED; }
+    if (hd && D != 64) { set_error("fused MLP head form needs d_model 64"); return NQS_ERR_UNSUPPORTED; }
     if (((uintptr_t)h & 15) || !b1 || !b2) { set_error("fused MLP: bad operand"); return NQS_ERR_INVALID_ARG; }
     CUtensorMap ma, m1, m2, mh;
     NQS_TRY(make_map(&ma, A, M, 2 * D, 128));
@@ -1573,15 +1681,24 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
     if (D == 64) {
         CUtensorMap m1r;   // the whole W1 (first K half of W1d) as one 256-row box
         NQS_TRY(make_map(&m1r, W1d, 4 * D, 2 * D, 256));
-        static int configured_res = -1;
+        static int configured_res[2] = {-1, -1};
         int dev = 0;
         NQS_CK(cudaGetDevice(&dev));
-        if (configured_res != dev) {
-            cudaError_t e = cudaFuncSetAttribute(tc_mlp_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpResPlan::SMEM);
+        const int slot = hd ? 1 : 0;
+        if (configured_res[slot] != dev) {
+            cudaError_t e = hd ? cudaFuncSetAttribute(tc_mlp_res_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpResPlan::SMEM)
+                               : cudaFuncSetAttribute(tc_mlp_res_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MlpResPlan::SMEM);
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_mlp_res)", __FILE__, __LINE__);
-            configured_res = dev;
+            configured_res[slot] = dev;
         }
-        tc_mlp_res_kernel<<<grid, MlpPlan<64>::THREADS, MlpResPlan::SMEM, s>>>(ma, m1r, m2, mh, b1, b2, M, ntiles);
+        MlpHeadArgs ha{};
+        if (hd) {
+            ha.lnf_g = hd->lnf_g; ha.lnf_b = hd->lnf_b; ha.head_w = hd->head_w; ha.head_b = hd->head_b;
+            ha.n = hd->n; ha.logit = hd->logit; ha.hph = hd->hph;
+            tc_mlp_res_kernel<true><<<grid, MlpPlan<64>::THREADS, MlpResPlan::SMEM, s>>>(ma, m1r, m2, mh, b1, b2, M, ntiles, ha);
+        } else {
+            tc_mlp_res_kernel<false><<<grid, MlpPlan<64>::THREADS, MlpResPlan::SMEM, s>>>(ma, m1r, m2, mh, b1, b2, M, ntiles, ha);
+        }
         NQS_LAUNCHED();
         return NQS_OK;
     }

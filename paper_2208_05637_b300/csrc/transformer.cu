@@ -229,6 +229,88 @@ attention_step_kernel(const float* __restrict__ slab0, int64_t slab_stride, int6
     if (lane == 0) att_store_row<MODE, DH>(acc, l, o, r, d, h * DH);
 }
 
+// Heads of whole sequences from the per-row logits and phase dots left by the fused last MLP
+// (modes 0 and 1 of HeadArgs): one warp per sequence, lane l taking positions t = l, l + 32.  A
+// lane applies the Hamming-weight constraint at its positions (forced conditionals and
+// violations from the same-spin ones before t) and the log-sigmoid of the free ones; the lanes'
+// sums are joined with TwoSum (compensated models) or plainly.
+__global__ void __launch_bounds__(256)
+heads_reduce_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
+                    const float* __restrict__ logit, const float* __restrict__ hph, int64_t R, HeadArgs args) {
+    const int n = mc.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= R) return;
+    const uint64_t x = bits[r];
+    float s = 0.f, e = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int t = lane + 32 * half;
+        if (t >= n) continue;
+        const int q = mc.order[t], sp = q & 1;
+        const int b = (int)((x >> q) & 1ull);
+        int c = 0;
+        for (int u = 0; u < t; ++u) {
+            const int qu = mc.order[u];
+            if ((qu & 1) == sp) c += (int)((x >> qu) & 1ull);
+        }
+        const int need = sp ? mc.n_dn : mc.n_up;
+        const bool f1 = c + mc.after[t] < need, f0 = c >= need;
+        if (f1) bad |= (b == 0);
+        else if (f0) bad |= (b == 1);
+        if (!(f1 || f0)) {
+            const float a = logit[r * n + t];
+            const float lp = logsig(b ? a : -a);
+            if (mc.compensated) two_sum_acc(s, e, lp); else s += lp;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, off), e2 = __shfl_xor_sync(0xffffffffu, e, off);
+        if (mc.compensated) { e += e2; two_sum_acc(s, e, s2); }
+        else s += s2;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    // phase head: LNf of h at position n - 2 (d = 64, two features a lane), the selected row
+    const int sel = (int)(((x >> mc.order[n - 2]) & 1ull) * 2 + ((x >> mc.order[n - 1]) & 1ull));
+    const float2 hv = reinterpret_cast<const float2*>(hph + r * 64)[lane];
+    const float mu = warp_sum(hv.x + hv.y) * (1.f / 64.f);
+    const float c0 = hv.x - mu, c1 = hv.y - mu;
+    const float rstd = rsqrtf(fmaf(warp_sum(fmaf(c0, c0, c1 * c1)), 1.f / 64.f, LN_EPS));
+    const int j = 2 * lane;
+    const float y0 = c0 * rstd * P[mc.lnf_g + j] + P[mc.lnf_b + j];
+    const float y1 = c1 * rstd * P[mc.lnf_g + j + 1] + P[mc.lnf_b + j + 1];
+    const float* pw = P + mc.phase_w + sel * 64 + j;
+    const float phase = warp_sum(fmaf(y0, pw[0], y1 * pw[1])) + P[mc.phase_b + sel];
+    if (lane != 0) return;
+    const float la = bad ? -INFINITY : 0.5f * (s + e);
+    if (args.mode == 0) {
+        args.la[r] = la;
+        args.ph[r] = phase;
+        return;
+    }
+    // mode 1: row r of the chunk belongs to the sample whose segment contains row0 + r
+    const int64_t grow = args.row0 + r;
+    int64_t lo = 0, hi = args.nseg - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (args.seg[mid * args.seg_stride] <= grow) lo = mid; else hi = mid - 1;
+    }
+    const float4 s4 = args.S[grow];
+    const float sre = s4.x + s4.y, sim = s4.z + s4.w;
+    float cr = sre, ci = sim;
+    if (x != args.xsample[lo]) {
+        const float mag = expf(la - args.la_x[lo]);
+        float sn, cs;
+        sincosf(phase - args.ph_x[lo], &sn, &cs);
+        const float rr = mag * cs, ri = mag * sn;
+        cr = sre * rr - sim * ri;
+        ci = sre * ri + sim * rr;
+    }
+    args.contrib[grow] = make_float2(cr, ci);
+}
+
 // Per-sample sum of the row contributions (TwoSum), one CTA per sample.
 __global__ void __launch_bounds__(128)
 segment_sum_kernel(const int64_t* __restrict__ seg, int64_t seg_stride, int64_t nseg,
@@ -314,6 +396,9 @@ void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b) {
     b.qkv = c.take<float>(M * 3 * d);
     b.o = c.take<float>(M * d);          // fp32 or bf16 view
     b.mid = c.take<float>(M * 4 * d);    // fp32 or bf16 view
+    b.logit = c.take<float>(M);
+    b.hph = c.take<float>(R * 64);
+    b.fused_heads = false;
 }
 
 int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, const void* A,
@@ -362,14 +447,16 @@ static int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w,
 // 64 or 128 run it as one fused tensor-core kernel (the 4d hidden layer stays on chip); the
 // others as two GEMMs through the mid buffer.
 static int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* a, void* mid,
-                  float* h, int64_t M, cudaStream_t s) {
+                  float* h, int64_t M, cudaStream_t s, const TcMlpHead* head = nullptr) {
     const int d = mc.hidden;
     if (mc.precision == NQS_PREC_BF16 && mc.compensated && (d == 64 || d == 128)) {
         const double flops = 2.0 * 2.0 * (double)M * 4 * d * d;
-        const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * 2 + 2.0 * 8.0 * d * d * 2;
+        // A (hi+lo) read, h read (and written unless the heads are fused), weights
+        const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * (head ? 1 : 2) + 2.0 * 8.0 * d * d * 2 +
+                             (head ? (double)M * 4 : 0.0);
         ProfScope ps("tf_mlp", s, flops, bytes);
         return tc_mlp_bf16(a, w.bf16 + w.bf16_off[layer][TF_W1], P + mc.b1[layer], w.bf16 + w.bf16_off[layer][TF_W2],
-                           P + mc.b2[layer], h, M, d, s);
+                           P + mc.b2[layer], h, M, d, s, head);
     }
     NQS_TRY(tf_gemm(mc, w, TF_W1, layer, a, mid, M, 4 * d, d, TF_EPI_GELU, P + mc.b1[layer], s));
     return tf_gemm(mc, w, TF_W2, layer, mid, h, M, d, 4 * d, TF_EPI_RESID, P + mc.b2[layer], s);
@@ -417,9 +504,10 @@ int64_t tf_bf16_weight_elems(const ModelConst& mc) {
 // b.h.  `bits` are the R configurations.
 template <int MODE>
 static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
-                           int64_t R, int T, TfBufs& b, cudaStream_t s) {
+                           int64_t R, int T, TfBufs& b, cudaStream_t s, bool head_logits) {
     const int d = mc.hidden;
     const int64_t M = R * T;
+    b.fused_heads = false;
     return with_dpl(d, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
         // algorithmic bytes: an activation element is 4 bytes in every storage form (fp32, or
@@ -452,7 +540,16 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], b.a);
                 NQS_LAUNCHED();
             }
-            NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, M, s));
+            // whole sequences of the compensated d = 64 model: the last MLP also applies LNf and
+            // the output / phase heads and leaves per-row logits instead of the final h
+            const bool fuse_heads = head_logits && l + 1 == mc.layers && T == mc.n && MODE == ACT_BF16X2 && d == 64;
+            if (fuse_heads) {
+                TcMlpHead hd{P + mc.lnf_g, P + mc.lnf_b, P + mc.head_w, P + mc.head_b, mc.n, b.logit, b.hph};
+                NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, M, s, &hd));
+                b.fused_heads = true;
+            } else {
+                NQS_TRY(tf_mlp(mc, P, w, l, b.a, b.mid, b.h, M, s));
+            }
             if (l + 1 < mc.layers) {
                 ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
                 layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(b.h, M, d, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.a);
@@ -466,10 +563,10 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
 // Forward of R sequences over their first T positions, leaving the final residual stream in
 // b.h.  `bits` are the R configurations.
 int tf_forward(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
-               int64_t R, int T, TfBufs& b, cudaStream_t s) {
-    if (mc.precision != NQS_PREC_BF16) return tf_forward_mode<ACT_F32>(mc, P, w, bits, R, T, b, s);
-    if (mc.compensated) return tf_forward_mode<ACT_BF16X2>(mc, P, w, bits, R, T, b, s);
-    return tf_forward_mode<ACT_BF16>(mc, P, w, bits, R, T, b, s);
+               int64_t R, int T, TfBufs& b, cudaStream_t s, bool head_logits) {
+    if (mc.precision != NQS_PREC_BF16) return tf_forward_mode<ACT_F32>(mc, P, w, bits, R, T, b, s, head_logits);
+    if (mc.compensated) return tf_forward_mode<ACT_BF16X2>(mc, P, w, bits, R, T, b, s, head_logits);
+    return tf_forward_mode<ACT_BF16>(mc, P, w, bits, R, T, b, s, head_logits);
 }
 
 // Position k of R prefixes (bits) for the sampler, with the keys and values of positions < k
@@ -542,6 +639,13 @@ int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t
     a.step_pos = ha.step_pos;
     return with_dpl(mc.hidden, [&](auto dpl) -> int {
         constexpr int DPL = decltype(dpl)::value;
+        if (b.fused_heads && a.mode != 2 && T == mc.n) {
+            // the last MLP left the per-row logits and phase dots: constraint, log-sigmoid and ratio
+            ProfScope ps("tf_heads", s, 0.0, (double)R * T * 4 + (double)R * 64 * 4);
+            heads_reduce_kernel<<<blocks_for(R, 8), 256, 0, s>>>(mc, P, bits, b.logit, b.hph, R, a);
+            NQS_LAUNCHED();
+            return NQS_OK;
+        }
         ProfScope ps("tf_heads", s, 0.0, (double)R * T * mc.hidden * 4);
         heads_kernel<DPL><<<blocks_for(R, 8), 256, 0, s>>>(mc, P, bits, b.h, R, T, a);
         NQS_LAUNCHED();
@@ -561,7 +665,7 @@ int tf_logpsi(const ModelConst& mc, const float* P, const TfWeights& w, const ui
               int64_t B, float* la, float* ph, TfBufs& b, cudaStream_t s) {
     for (int64_t lo = 0; lo < B; lo += b.R) {
         const int64_t R = std::min(b.R, B - lo);
-        NQS_TRY(tf_forward(mc, P, w, bits + lo, R, mc.n, b, s));
+        NQS_TRY(tf_forward(mc, P, w, bits + lo, R, mc.n, b, s, true));
         HeadArgsHost ha{};
         ha.mode = 0; ha.la = la + lo; ha.ph = ph + lo;
         NQS_TRY(tf_heads(mc, P, bits + lo, R, mc.n, b, ha, s));
