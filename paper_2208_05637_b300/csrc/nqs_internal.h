@@ -258,6 +258,11 @@ int tf_heads(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t
              const TfBufs& b, const HeadArgsHost& ha, cudaStream_t s);
 int tf_step(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits, int64_t R, int k,
             const TfStepCache& kc, TfBufs& b, cudaStream_t s);
+// The whole step in one kernel (d_model 64, four heads, bf16 forms): p, the draw thresholds and
+// the trace of position k for the R prefixes, as tf_step followed by the mode-2 heads.
+bool tf_step_fused_supported(const ModelConst& mc);
+int tf_step_fused(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits, int64_t R,
+                  int k, const TfStepCache& kc, float* p_out, uint64_t* thr, float* trace, cudaStream_t s);
 int64_t tf_step_cache_bytes(const ModelConst& mc, int64_t cap);
 int tf_segment_sum(const int64_t* seg, int64_t seg_stride, int64_t nseg, const float2* contrib,
                    int compensated, float* eloc, cudaStream_t s);

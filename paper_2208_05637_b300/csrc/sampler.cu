@@ -134,28 +134,50 @@ __global__ void set_u_kernel(int64_t* Udev, const int64_t* pos0, const int64_t* 
 
 // Keep the top max_unique of the U entries (bits, cnt[, par]) by (count desc, bits asc) into
 // (obits, ocnt[, opar]) with their order preserved; one CTA of 1024 threads, U > max_unique.
+// scnt, when given, holds the U counts (as uint32) in shared memory and replaces the reads of cnt.
 __device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
                             const int32_t* __restrict__ par, int64_t U, int64_t max_unique,
-                            uint64_t* __restrict__ obits, int64_t* __restrict__ ocnt, int32_t* __restrict__ opar) {
+                            uint64_t* __restrict__ obits, int64_t* __restrict__ ocnt, int32_t* __restrict__ opar,
+                            const uint32_t* scnt = nullptr) {
     __shared__ uint32_t hist[256];
-    __shared__ uint32_t s_prefix, s_need;
+    __shared__ uint32_t s_prefix, s_need, s_max;
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t carry_sh;
-    // radix select of the max_unique-th largest count (counts < 2^31)
-    uint32_t prefix = 0, pmask = 0;
+    auto count_at = [&](int64_t i) -> uint32_t { return scnt ? scnt[i] : (uint32_t)cnt[i]; };
+    const int lane = threadIdx.x & 31;
+    // the largest count fixes the first radix digit that is not zero for every entry
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    {
+        uint32_t m = 0;
+        for (int64_t s = threadIdx.x; s < U; s += blockDim.x) m = max(m, count_at(s));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) atomicMax(&s_max, m);
+    }
+    __syncthreads();
+    const uint32_t cmax = s_max;
+    const int top = cmax >= (1u << 24) ? 24 : cmax >= (1u << 16) ? 16 : cmax >= (1u << 8) ? 8 : 0;
+    // radix select of the max_unique-th largest count (counts < 2^31); the digits above `top`
+    // are zero for every entry and need no pass
+    uint32_t prefix = 0, pmask = top < 24 ? ~0u << (top + 8) : 0u;
     uint32_t need = (uint32_t)max_unique;   // how many still to take at or above prefix
-    for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int shift = top; shift >= 0; shift -= 8) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int64_t s = threadIdx.x; s < U; s += blockDim.x) {
-            const uint32_t c = (uint32_t)cnt[s];
-            if ((c & pmask) == prefix) atomicAdd(&hist[(c >> shift) & 0xffu], 1u);
+        // one shared atomic per distinct digit and warp (the low digits repeat heavily)
+        for (int64_t base = 0; base < U; base += blockDim.x) {
+            const int64_t s = base + threadIdx.x;
+            const uint32_t c = s < U ? count_at(s) : 0u;
+            const bool in = s < U && (c & pmask) == prefix;
+            const uint32_t key = in ? (c >> shift) & 0xffu : 0x100u;
+            const unsigned grp = __match_any_sync(0xffffffffu, key);
+            if (in && lane == __ffs(grp) - 1) atomicAdd(&hist[key], (uint32_t)__popc(grp));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
             // highest bin d whose count from the top reaches `need` (else 0), and the count of
             // the bins above it: lane l scans bins 255 - 8l .. 248 - 8l, a warp scan joins them
-            const int lane = threadIdx.x;
             uint32_t loc[8], sum = 0;
 #pragma unroll
             for (int i = 0; i < 8; ++i) { loc[i] = hist[255 - 8 * lane - i]; sum += loc[i]; }
@@ -195,10 +217,10 @@ __device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __
     int64_t carry_keep = 0, carry_eq = 0;
     for (int64_t base = 0; base < U; base += blockDim.x) {
         const int64_t s = base + threadIdx.x;
-        const uint32_t c = s < U ? (uint32_t)cnt[s] : 0u;
+        const uint32_t c = s < U ? count_at(s) : 0u;
         const int64_t eq = (s < U && c == T) ? 1 : 0;
         // rank among equals
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int warp = threadIdx.x >> 5;
         int64_t incl = eq;
         for (int d = 1; d < 32; d <<= 1) { const int64_t y = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += y; }
         if (lane == 31) warp_sums[warp] = incl;
@@ -228,7 +250,7 @@ __device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __
         if (keep) {
             const int64_t pos = carry_keep + warp_sums[warp] + incl - keep;
             obits[pos] = bits[s];
-            ocnt[pos] = cnt[s];
+            ocnt[pos] = c;
             if (par) opar[pos] = par[s];
         }
         carry_keep += carry_sh;
@@ -252,6 +274,7 @@ evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
 // For buffers of at most SAMPLER_GRAPH_MAX_CAP entries the per-step bookkeeping runs in two
 // one-CTA kernels around the draws (same results as the multi-kernel sequence above).
 constexpr int BK_T = 1024;
+constexpr int64_t BK_SMEM_PER_ENTRY = sizeof(uint64_t) + sizeof(uint32_t);   // parent bits + merged count
 
 // Exclusive scan of one value per thread across the CTA; *total receives the block sum.
 __device__ int64_t bk_block_scan(int64_t v, int64_t* warp_sums, int64_t* total) {
@@ -317,11 +340,13 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
                  int64_t* __restrict__ pos0, int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
                  uint64_t qbit, uint64_t* __restrict__ nb, int64_t* __restrict__ nc,
                  int32_t* __restrict__ par, int32_t* __restrict__ npar, int64_t max_unique,
-                 const int32_t* __restrict__ anc_old, int32_t* __restrict__ anc_new, int n, int k) {
+                 const int32_t* __restrict__ anc_old, int32_t* __restrict__ anc_new, int n, int k,
+                 int64_t cap) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t tot0, tot1;
-    extern __shared__ uint64_t sbits[];              // the U parent bit strings
+    extern __shared__ uint64_t sbits[];              // the U parent bit strings, then cap merged counts
     const int64_t U = *Udev;
+    uint32_t* scnt = reinterpret_cast<uint32_t*>(sbits + cap);
     for (int64_t i = threadIdx.x; i < U; i += BK_T) sbits[i] = cb[i];
     // flags and their scans
     int64_t c0 = 0, c1 = 0;
@@ -345,6 +370,7 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
             const int64_t r = pos1[upper_s(sbits, (int)U, qbit, bs)];
             nb[pos0[s] + r] = bs;
             nc[pos0[s] + r] = m0;
+            scnt[pos0[s] + r] = (uint32_t)m0;
             if (npar) npar[pos0[s] + r] = (int32_t)s;
         }
         if (m1 > 0) {
@@ -352,13 +378,14 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
             const int64_t r = pos0[upper_s(sbits, (int)U, 0, key)];
             nb[pos1[s] + r] = key;
             nc[pos1[s] + r] = m1;
+            scnt[pos1[s] + r] = (uint32_t)m1;
             if (npar) npar[pos1[s] + r] = (int32_t)s;
         }
     }
     __syncthreads();
     int64_t Un = c0 + c1;
     if (Un > max_unique) {
-        evict_block(nb, nc, npar, Un, max_unique, cb, cc, par);
+        evict_block(nb, nc, npar, Un, max_unique, cb, cc, par, scnt);
         Un = max_unique;
     } else {
         for (int64_t i = threadIdx.x; i < Un; i += BK_T) {
@@ -455,6 +482,7 @@ static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* 
         // incremental: position k only, earlier keys and values from the cache
         TfStepCache kc;
         kc.kv = b.kv; kc.cap = b.cap; kc.anc = b.ancA; kc.Udev = Udev;
+        if (tf_step_fused_supported(mc)) return tf_step_fused(mc, P, *tf->w, bits, U, k, kc, b.p, b.thr, trace, s);
         NQS_TRY(tf_step(mc, P, *tf->w, bits, U, k, kc, *tf->b, s));
         HeadArgsHost ha{};
         ha.mode = 2; ha.p_out = b.p; ha.thr = b.thr; ha.trace = trace; ha.step_pos = k;
@@ -494,14 +522,15 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
     const int g = grid_for(b.cap);
     const bool one_cta = b.cap <= SAMPLER_GRAPH_MAX_CAP;
     if (one_cta) {
-        // the parent bits staged by bk_finish_kernel take up to 64 KB of shared memory; the limit
-        // is raised once per device (before any captured launch: the first call is an eager one)
+        // the parent bits and merged counts staged by bk_finish_kernel take up to 96 KB of shared
+        // memory; the limit is raised once per device (before any captured launch: the first call
+        // is an eager one)
         static int configured_device = -1;
         int dev = 0;
         NQS_CK(cudaGetDevice(&dev));
         if (configured_device != dev) {
             NQS_CK(cudaFuncSetAttribute(bk_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(SAMPLER_GRAPH_MAX_CAP * sizeof(uint64_t))));
+                                        (int)(SAMPLER_GRAPH_MAX_CAP * BK_SMEM_PER_ENTRY)));
             configured_device = dev;
         }
     }
@@ -516,9 +545,9 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
             draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
             NQS_LAUNCHED();
             const bool anc = b.kv && k + 1 < mc.n;
-            bk_finish_kernel<<<1, BK_T, b.cap * sizeof(uint64_t), s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
+            bk_finish_kernel<<<1, BK_T, b.cap * BK_SMEM_PER_ENTRY, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
                                                 b.kv ? b.par : nullptr, b.kv ? b.par2 : nullptr, max_unique,
-                                                anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k);
+                                                anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k, b.cap);
             NQS_LAUNCHED();
             if (anc) std::swap(b.ancA, b.ancB);
             continue;

@@ -81,26 +81,33 @@ def test_bf16_local_energy_against_quantised_oracle(c, B):
     assert eq <= 1e-4, eq
 
 
-def test_bf16_sampler_trace_replay():
+# d_model 64 / four heads runs the one-kernel sampler step: compensated and plain bf16 forms,
+# with and without eviction (max_unique below the unique count), and the 20-qubit workload with
+# its 1024-sample buffer; called twice, so the second call replays the captured graph.
+@pytest.mark.parametrize("c,comp,n_samples,max_unique", [(TF_D64, True, 20_000, 10**6), (TF_D64, False, 20_000, 10**6),
+                                                         (TF_D64, True, 20_000, 40), (3, True, 100_000, 1024)])
+def test_bf16_sampler_trace_replay(c, comp, n_samples, max_unique):
     P = lib()
-    cfg = TF_D64
-    m, _ = gpu_model(cfg, beta=1.0, precision="bf16")
-    oq, _ = oracle_model(cfg, beta=1.0, quant="bf16x2")
+    cfg = _cfg(c)
+    m, _ = gpu_model(cfg, beta=1.0, precision="bf16", compensated=comp)
+    oq, _ = oracle_model(cfg, beta=1.0, quant="bf16x2" if comp else "bf16")
     seed = 99
-    bits, counts, trace = P.nqs_sample(m, 20_000, 10**6, seed, trace=True)
-    trace = trace.cpu().numpy()
-    diffs = []
+    for call in range(2):
+        bits, counts, trace = P.nqs_sample(m, n_samples, max_unique, seed + call, trace=True)
+        trace = trace.cpu().numpy()
+        diffs = []
 
-    def replay(parent_bits, k):
-        p = trace[k, : len(parent_bits)]
-        diffs.append(np.max(np.abs(p.astype(np.float64) - oq.sampling_p(parent_bits, k))))
-        return p
+        def replay(parent_bits, k):
+            p = trace[k, : len(parent_bits)]
+            diffs.append(np.max(np.abs(p.astype(np.float64) - oq.sampling_p(parent_bits, k))))
+            return p
 
-    wb, wc = sample(replay, oq.n, oq.order, 20_000, 10**6, seed)
-    assert np.array_equal(from_dev_bits(bits), wb)
-    assert np.array_equal(counts.cpu().numpy(), wc)
-    assert max(diffs) <= 1e-5
-    assert np.all(in_sector(wb, oq.n, oq.n_up, oq.n_dn))
+        wb, wc = sample(replay, oq.n, oq.order, n_samples, max_unique, seed + call)
+        assert np.array_equal(from_dev_bits(bits), wb)
+        assert np.array_equal(counts.cpu().numpy(), wc)
+        # the plain form's activation rounding flips move p by up to ~1e-4 (log|psi| bounds above)
+        assert max(diffs) <= (1e-5 if comp else 1e-3)
+        assert np.all(in_sector(wb, oq.n, oq.n_up, oq.n_dn))
 
 
 @pytest.mark.parametrize("c,comp", [(TF_D64, True), (3, True), (TF_D64, False)])
