@@ -9,7 +9,8 @@
 // The four GEMMs run on mma.sync m16n8k16 (bf16 in, fp32 accumulate) with the operand forms of
 // the batched forward: activations as bf16 (ACT_BF16) or as hi | lo bf16 pairs against the
 // duplicated [W | W] weights (ACT_BF16X2), so the arithmetic is that of the multi-kernel step
-// up to the fp32 summation order.  The weights stream from L2 straight into B fragments.
+// up to the fp32 summation order.  Each block's weights are staged in shared memory one group
+// (Wqkv | Wo, W1 | W2) ahead of their use by asynchronous copies.
 #include "tf_common.cuh"
 
 namespace nqs {
@@ -25,17 +26,35 @@ constexpr int FS_LDQ = 3 * FS_D + 8;            // fp32: q | k | v of position k
 constexpr int FS_LDA = 2 * FS_D + 8;            // bf16: GEMM operand of width d (hi | lo)
 constexpr int FS_LDG = 2 * FS_F + 8;            // bf16: MLP hidden operand (hi | lo)
 constexpr int FS_MAXK = 64;                     // positions (n <= 64)
-constexpr int FS_OFF_H = 0;
+constexpr int FS_VB = 6;                        // value rows in flight per lane
+constexpr int FS_LDW = FS_D + 8;                // bf16: staged Wqkv, Wo, W1 rows (K = d)
+constexpr int FS_LDW2 = FS_F + 8;               // bf16: staged W2 rows (K = 4d)
+constexpr int FS_OFF_WQKV = 0;                  // block weights staged in shared memory: Wqkv | Wo
+constexpr int FS_OFF_WO = FS_OFF_WQKV + 3 * FS_D * FS_LDW * 2;            // (group A), W1 | W2
+constexpr int FS_OFF_W1 = FS_OFF_WO + FS_D * FS_LDW * 2;                  // (group B)
+constexpr int FS_OFF_W2 = FS_OFF_W1 + FS_F * FS_LDW * 2;
+constexpr int FS_OFF_H = FS_OFF_W2 + FS_D * FS_LDW2 * 2;
 constexpr int FS_OFF_RED = FS_OFF_H + FS_RB * FS_LDH * 4;
 constexpr int FS_OFF_Q = FS_OFF_RED + FS_RB * FS_LDH * 4;
 constexpr int FS_OFF_A = FS_OFF_Q + FS_RB * FS_LDQ * 4;
 constexpr int FS_OFF_G = FS_OFF_A + FS_RB * FS_LDA * 2;
 constexpr int FS_OFF_E = FS_OFF_G + FS_RB * FS_LDG * 2;          // per warp: e[head][key]
 constexpr int FS_OFF_S = FS_OFF_E + FS_WARPS * FS_H * FS_MAXK * 4;   // per warp: key slots
-constexpr int FS_SMEM = FS_OFF_S + FS_WARPS * FS_MAXK * 4;
+constexpr int FS_OFF_PV = FS_OFF_S + FS_WARPS * FS_MAXK * 4;     // small parameter vectors
+// per block: bqkv | bo | ln2_g | ln2_b | b1 | b2 | ln1_g | ln1_b, then lnf_g | lnf_b | head_w | head_b[k]
+constexpr int FS_PV_NF = 8;
+__host__ __device__ constexpr int fs_pv_start(int f) {
+    return f == 0 ? 0 : f == 1 ? 3 * FS_D : f == 2 ? 4 * FS_D : f == 3 ? 5 * FS_D : f == 4 ? 6 * FS_D
+         : f == 5 ? 6 * FS_D + FS_F : f == 6 ? 7 * FS_D + FS_F : f == 7 ? 8 * FS_D + FS_F : 9 * FS_D + FS_F;
+}
+constexpr int FS_PV = fs_pv_start(FS_PV_NF);   // floats per block
+constexpr int FS_PG = 3 * FS_D + 4;            // the head's vectors (padded)
+inline int fs_smem_bytes(int layers) { return FS_OFF_PV + (layers * FS_PV + FS_PG) * 4; }
 
 struct FsArgs {
     const float* P;
+    int64_t pv[TF_MAX_LAYERS][FS_PV_NF];        // offsets in P of each block's small vectors
+    int64_t pg[4];                              // offsets of lnf_g, lnf_b, head_w, head_b
     const __nv_bfloat16* wb;                    // bf16 weights (duplicated rows when compensated)
     int64_t woff[TF_MAX_LAYERS][4];             // element offsets of Wqkv, Wo, W1, W2 in wb
     const uint64_t* bits;
@@ -62,25 +81,65 @@ __device__ __forceinline__ uint32_t fs_lds32(const __nv_bfloat16* p) {
     return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// C (16 x 8) += A[:, k0:k1] . W[n0:n0+8, k0:k1]^T: A in shared memory (bf16, row stride lda), W
-// row-major in global memory (bf16, row stride ldw).  Fragment layouts of m16n8k16: A rows g and
-// g + 8, columns 2q, 2q + 1 and 2q + 8, 2q + 9 of the k-step; B column g, the same k; C rows g,
-// g + 8, columns 2q, 2q + 1 (g = lane / 4, q = lane % 4).
-template <int KSTEPS>
-__device__ __forceinline__ void fs_tile(const __nv_bfloat16* sA, int lda, const __nv_bfloat16* W, int64_t ldw,
-                                        int n0, int k0, float (&c)[4], int lane) {
-    const int g = lane >> 2, q = lane & 3;
-    const uint32_t* wr = reinterpret_cast<const uint32_t*>(W + (int64_t)(n0 + g) * ldw + k0 + 2 * q);
-    const __nv_bfloat16* a0 = sA + g * lda + k0 + 2 * q;
-    const __nv_bfloat16* a1 = a0 + 8 * lda;
-    uint32_t b[KSTEPS][2];
+__device__ __forceinline__ void fs_ldm4(uint32_t (&r)[4], const __nv_bfloat16* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+}
+__device__ __forceinline__ void fs_ldm2(uint32_t& r0, uint32_t& r1, const __nv_bfloat16* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+}
+
+// C (16 x 8) += A . W[n0 : n0 + 8]^T over the logical columns kb .. kb + 16 KS of W (width K):
+// A and W in shared memory (bf16, row strides lda and ldw); a compensated A holds its lo halves
+// K columns after the hi ones and both meet the same W fragment, on two accumulators (the plain
+// form alternates its k-steps between them), joined at the end.  Fragments by ldmatrix: A as four
+// 8 x 8 pieces (rows 0-7 / 8-15, columns 0-7 / 8-15 of the k-step), W as two (its 8 rows,
+// columns 0-7 / 8-15), which are the m16n8k16 operand layouts.
+template <int MODE, int KS>
+__device__ __forceinline__ void fs_tile(const __nv_bfloat16* sA, int lda, int K, const __nv_bfloat16* W, int ldw,
+                                        int n0, int kb, float (&c)[4], int lane) {
+    const __nv_bfloat16* pa = sA + (lane & 15) * lda + kb + 8 * (lane >> 4);
+    const __nv_bfloat16* pb = W + (n0 + (lane & 7)) * ldw + kb + 8 * ((lane >> 3) & 1);
+    float c2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int s = 0; s < KSTEPS; ++s) { b[s][0] = __ldg(wr + 8 * s); b[s][1] = __ldg(wr + 8 * s + 4); }
+    for (int s = 0; s < KS; ++s) {
+        uint32_t b0, b1, a[4];
+        fs_ldm2(b0, b1, pb + 16 * s);
+        fs_ldm4(a, pa + 16 * s);
+        if (MODE == ACT_BF16X2) {
+            uint32_t al[4];
+            fs_ldm4(al, pa + K + 16 * s);
+            fs_mma(c, a, b0, b1);
+            fs_mma(c2, al, b0, b1);
+        } else if (s & 1) {
+            fs_mma(c2, a, b0, b1);
+        } else {
+            fs_mma(c, a, b0, b1);
+        }
+    }
 #pragma unroll
-    for (int s = 0; s < KSTEPS; ++s) {
-        const uint32_t a[4] = {fs_lds32(a0 + 16 * s), fs_lds32(a1 + 16 * s), fs_lds32(a0 + 16 * s + 8),
-                               fs_lds32(a1 + 16 * s + 8)};
-        fs_mma(c, a, b[s][0], b[s][1]);
+    for (int i = 0; i < 4; ++i) c[i] += c2[i];
+}
+
+__device__ __forceinline__ void fs_cp16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void fs_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void fs_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Rows [0, N) of a weight matrix (the first K columns of each global row, row stride ldw) into
+// shared memory with row stride lds, by 16-byte asynchronous copies spread over the CTA.
+template <int N, int K>
+__device__ __forceinline__ void fs_stage(__nv_bfloat16* dst, int lds, const __nv_bfloat16* src, int64_t ldw) {
+    constexpr int CPR = K / 8;                         // 16-byte pieces per row
+    for (int i = threadIdx.x; i < N * CPR; i += FS_THREADS) {
+        const int r = i / CPR, c = i - r * CPR;
+        fs_cp16(dst + r * lds + 8 * c, src + r * ldw + 8 * c);
     }
 }
 
@@ -111,10 +170,34 @@ __device__ __forceinline__ float2 fs_ln(const float* sH, int r, const float* __r
     return make_float2(d0 * rstd * gg.x + bb.x, d1 * rstd * gg.y + bb.y);
 }
 
+// split-K pair of a 64-column GEMM: warps 8..15 leave their partial sums in sRed, warps 0..7 add
+// them, the bias and the residual into h
+__device__ __forceinline__ void fs_resid_join(float* sH, float* sRed, const float* __restrict__ bias,
+                                              const float (&c)[4], int kh, int col, int g) {
+    if (kh) {
+        *reinterpret_cast<float2*>(sRed + g * FS_LDH + col) = make_float2(c[0], c[1]);
+        *reinterpret_cast<float2*>(sRed + (g + 8) * FS_LDH + col) = make_float2(c[2], c[3]);
+    }
+    __syncthreads();
+    if (!kh) {
+        const float2 bb = *reinterpret_cast<const float2*>(bias + col);
+        const float2 p0 = *reinterpret_cast<const float2*>(sRed + g * FS_LDH + col);
+        const float2 p1 = *reinterpret_cast<const float2*>(sRed + (g + 8) * FS_LDH + col);
+        float2* h0 = reinterpret_cast<float2*>(sH + g * FS_LDH + col);
+        float2* h1 = reinterpret_cast<float2*>(sH + (g + 8) * FS_LDH + col);
+        h0->x += (c[0] + p0.x) + bb.x; h0->y += (c[1] + p0.y) + bb.y;
+        h1->x += (c[2] + p1.x) + bb.x; h1->y += (c[3] + p1.y) + bb.y;
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(FS_THREADS, 1)
-tf_step_fused_kernel(ModelConst mc, FsArgs A) {
+tf_step_fused_kernel(const __grid_constant__ ModelConst mc, const __grid_constant__ FsArgs A) {
     extern __shared__ __align__(16) uint8_t fs_smem[];
+    __nv_bfloat16* sWqkv = reinterpret_cast<__nv_bfloat16*>(fs_smem + FS_OFF_WQKV);
+    __nv_bfloat16* sWo = reinterpret_cast<__nv_bfloat16*>(fs_smem + FS_OFF_WO);
+    __nv_bfloat16* sW1 = reinterpret_cast<__nv_bfloat16*>(fs_smem + FS_OFF_W1);
+    __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(fs_smem + FS_OFF_W2);
     float* sH = reinterpret_cast<float*>(fs_smem + FS_OFF_H);
     float* sRed = reinterpret_cast<float*>(fs_smem + FS_OFF_RED);
     float* sQ = reinterpret_cast<float*>(fs_smem + FS_OFF_Q);
@@ -135,6 +218,55 @@ tf_step_fused_kernel(ModelConst mc, FsArgs A) {
     const int64_t grow = row0 + r;
     const bool live = grow < U;
     const uint64_t x = A.bits[live ? grow : U - 1];
+    // block weights: Wqkv | Wo of block l in group A, W1 | W2 in group B, staged one group ahead
+    auto stage_a = [&](int l) {
+        fs_stage<3 * FS_D, FS_D>(sWqkv, FS_LDW, A.wb + A.woff[l][TF_WQKV], KX * FS_D);
+        fs_stage<FS_D, FS_D>(sWo, FS_LDW, A.wb + A.woff[l][TF_WO], KX * FS_D);
+        fs_cp_commit();
+    };
+    auto stage_b = [&](int l) {
+        fs_stage<FS_F, FS_D>(sW1, FS_LDW, A.wb + A.woff[l][TF_W1], KX * FS_D);
+        fs_stage<FS_D, FS_F>(sW2, FS_LDW2, A.wb + A.woff[l][TF_W2], KX * FS_F);
+        fs_cp_commit();
+    };
+    stage_a(0);
+    stage_b(0);
+    // the blocks' biases and LayerNorm vectors and the head's vectors into shared memory
+    float* sPv = reinterpret_cast<float*>(fs_smem + FS_OFF_PV);
+    const int L = mc.layers;
+    const int npv = L * FS_PV + FS_PG;
+    for (int base = 0; base < npv; base += 4 * FS_THREADS) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * FS_THREADS + threadIdx.x;
+            int64_t src = -1;
+            if (i < L * FS_PV) {
+                const int l = i / FS_PV, o = i - l * FS_PV;
+                int f = 0;
+                while (o >= fs_pv_start(f + 1)) ++f;
+                src = A.pv[l][f] + (o - fs_pv_start(f));
+            } else if (i < npv) {
+                const int o = i - L * FS_PV;
+                if (o < 3 * FS_D) src = A.pg[o / FS_D] + (o % FS_D);
+                else if (o == 3 * FS_D) src = A.pg[3] + k;
+            }
+            v[u] = src >= 0 ? __ldg(P + src) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + u * FS_THREADS + threadIdx.x;
+            if (i < npv) sPv[i] = v[u];
+        }
+    }
+    const float* sHead = sPv + L * FS_PV;                // lnf_g | lnf_b | head_w | head_b[k]
+    // this row's ancestor slots (the same for every block)
+    int32_t* s_s = sS + warp * FS_MAXK;
+    for (int j = lane; j < k; j += 32) {
+        int64_t slot = live ? A.anc[grow * n + j] : 0;
+        slot = slot < 0 ? 0 : (slot >= A.cap ? A.cap - 1 : slot);
+        s_s[j] = (int32_t)slot;
+    }
 
     // ---- embedding and LayerNorm 1 of block 0
     {
@@ -143,21 +275,23 @@ tf_step_fused_kernel(ModelConst mc, FsArgs A) {
         const float2 e = *reinterpret_cast<const float2*>(P + mc.tok_emb + tok * FS_D + c0);
         const float2 p = *reinterpret_cast<const float2*>(P + mc.pos_emb + k * FS_D + c0);
         *reinterpret_cast<float2*>(sH + r * FS_LDH + c0) = make_float2(e.x + p.x, e.y + p.y);
-        __syncwarp();
-        const float2 y = fs_ln(sH, r, P + mc.ln1_g[0], P + mc.ln1_b[0], lane);
+        __syncthreads();
+        const float2 y = fs_ln(sH, r, sPv + fs_pv_start(6), sPv + fs_pv_start(7), lane);
         fs_put2<MODE>(sA, FS_LDA, FS_D, r, c0, y.x, y.y);
     }
-    __syncthreads();
 
     for (int l = 0; l < mc.layers; ++l) {
+        const bool next = l + 1 < mc.layers;
         float* slab0 = A.kv + (int64_t)l * n * slab_stride;   // step-0 slab of this layer
+        const float* pv = sPv + l * FS_PV;
+        fs_cp_wait<1>();                                     // group A of this block has landed
+        __syncthreads();
         // ---- qkv = a . Wqkv^T + bqkv: 24 n-tiles over the 16 warps
         {
-            const __nv_bfloat16* W = A.wb + A.woff[l][TF_WQKV];
-            const float* bq = P + mc.bqkv[l];
+            const float* bq = pv + fs_pv_start(0);
             for (int t = warp; t < 3 * FS_D / 8; t += FS_WARPS) {
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
-                fs_tile<KX * FS_D / 16>(sA, FS_LDA, W, KX * FS_D, 8 * t, 0, c, lane);
+                fs_tile<MODE, FS_D / 16>(sA, FS_LDA, FS_D, sWqkv, FS_LDW, 8 * t, 0, c, lane);
                 const int col = 8 * t + 2 * q4;
                 const float2 bb = *reinterpret_cast<const float2*>(bq + col);
                 *reinterpret_cast<float2*>(sQ + g * FS_LDQ + col) = make_float2(c[0] + bb.x, c[1] + bb.y);
@@ -177,41 +311,38 @@ tf_step_fused_kernel(ModelConst mc, FsArgs A) {
         // ---- attention of row r over keys j = 0..k (ancestor slots for j < k, own row at k)
         {
             float* e_s = sE + warp * FS_H * FS_MAXK;
-            int32_t* s_s = sS + warp * FS_MAXK;
             const float scale = rsqrtf((float)FS_DH) * 1.4426950408889634f;   // log2 domain
+            const float4* qrow = reinterpret_cast<const float4*>(sQ + r * FS_LDQ);   // the query row
+            // scores: lane takes keys j = lane and j = lane + 32 (the second only when k >= 32)
             float sc[2][FS_H];
-            const float* kr[2] = {nullptr, nullptr};
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
                 const int j = lane + 32 * h2;
-                if (j > k) continue;
-                if (j < k) {
-                    int64_t slot = live ? A.anc[grow * n + j] : 0;
-                    slot = slot < 0 ? 0 : (slot >= A.cap ? A.cap - 1 : slot);
-                    s_s[j] = (int32_t)slot;
-                    kr[h2] = slab0 + (int64_t)j * slab_stride + slot * (3 * FS_D) + FS_D;
-                } else {
-                    kr[h2] = sQ + r * FS_LDQ + FS_D;
-                }
-            }
+                if (h2 == 1 && k < 32) {
 #pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
+                    for (int hd = 0; hd < FS_H; ++hd) sc[1][hd] = -INFINITY;
+                    break;
+                }
+                const float* kr = j < k ? slab0 + (int64_t)j * slab_stride + (int64_t)s_s[j] * (3 * FS_D) + FS_D
+                                        : sQ + r * FS_LDQ + FS_D;
 #pragma unroll
                 for (int hd = 0; hd < FS_H; ++hd) {
-                    if (!kr[h2]) { sc[h2][hd] = -INFINITY; continue; }
-                    const float4* k4 = reinterpret_cast<const float4*>(kr[h2] + hd * FS_DH);
-                    const float4* q4p = reinterpret_cast<const float4*>(sQ + r * FS_LDQ + hd * FS_DH);
+                    float4 kk[FS_DH / 4];
+#pragma unroll
+                    for (int j4 = 0; j4 < FS_DH / 4; ++j4)
+                        kk[j4] = j <= k ? reinterpret_cast<const float4*>(kr)[hd * (FS_DH / 4) + j4] : make_float4(0.f, 0.f, 0.f, 0.f);
                     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                     for (int j4 = 0; j4 < FS_DH / 4; ++j4) {
-                        const float4 kk = k4[j4], qq = q4p[j4];
+                        const float4 k4 = kk[j4];
+                        const float4 qh = qrow[hd * (FS_DH / 4) + j4];
                         float& sp = (j4 & 1) ? s1 : s0;
-                        sp = fmaf(qq.x * scale, kk.x, sp);
-                        sp = fmaf(qq.y * scale, kk.y, sp);
-                        sp = fmaf(qq.z * scale, kk.z, sp);
-                        sp = fmaf(qq.w * scale, kk.w, sp);
+                        sp = fmaf(qh.x * scale, k4.x, sp);
+                        sp = fmaf(qh.y * scale, k4.y, sp);
+                        sp = fmaf(qh.z * scale, k4.z, sp);
+                        sp = fmaf(qh.w * scale, k4.w, sp);
                     }
-                    sc[h2][hd] = s0 + s1;
+                    sc[h2][hd] = j <= k ? s0 + s1 : -INFINITY;
                 }
             }
             float inv_l[FS_H];
@@ -220,82 +351,77 @@ tf_step_fused_kernel(ModelConst mc, FsArgs A) {
                 float m = fmaxf(sc[0][hd], sc[1][hd]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                const float e0 = kr[0] ? exp2f(sc[0][hd] - m) : 0.f;
-                const float e1 = kr[1] ? exp2f(sc[1][hd] - m) : 0.f;
-                if (kr[0]) e_s[hd * FS_MAXK + lane] = e0;
-                if (kr[1]) e_s[hd * FS_MAXK + lane + 32] = e1;
+                const float e0 = lane <= k ? exp2f(sc[0][hd] - m) : 0.f;
+                const float e1 = lane + 32 <= k ? exp2f(sc[1][hd] - m) : 0.f;
+                if (lane <= k) e_s[hd * FS_MAXK + lane] = e0;
+                if (lane + 32 <= k) e_s[hd * FS_MAXK + lane + 32] = e1;
                 inv_l[hd] = 1.f / warp_sum(e0 + e1);
             }
             __syncwarp();
-            // weighted values: lane takes output columns 2 lane, 2 lane + 1 (head lane / 8)
-            const int c0 = 2 * lane, hd = lane >> 3;
+            // weighted values: lane (half, dq) takes columns 4 dq .. 4 dq + 3 (head dq / 4) over the
+            // keys j = half, half + 2, ...; the two halves are joined by one shuffle
+            const int half = lane >> 4, dq = lane & 15, hd = dq >> 2;
             const float* ev = e_s + hd * FS_MAXK;
-            float ox = 0.f, oy = 0.f;
-            int j = 0;
-            for (; j + 4 <= k; j += 4) {
-                float2 v[4];
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int jb = half; jb < k; jb += 2 * FS_VB) {
+                float4 v[FS_VB];
+                float e[FS_VB];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    v[u] = *reinterpret_cast<const float2*>(slab0 + (int64_t)(j + u) * slab_stride +
-                                                            (int64_t)s_s[j + u] * (3 * FS_D) + 2 * FS_D + c0);
+                for (int u = 0; u < FS_VB; ++u) {
+                    const int j = jb + 2 * u;
+                    e[u] = j < k ? ev[j] : 0.f;
+                    v[u] = j < k ? *reinterpret_cast<const float4*>(slab0 + (int64_t)j * slab_stride +
+                                                                     (int64_t)s_s[j] * (3 * FS_D) + 2 * FS_D + 4 * dq)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) { ox = fmaf(ev[j + u], v[u].x, ox); oy = fmaf(ev[j + u], v[u].y, oy); }
+                for (int u = 0; u < FS_VB; ++u) {
+                    o.x = fmaf(e[u], v[u].x, o.x); o.y = fmaf(e[u], v[u].y, o.y);
+                    o.z = fmaf(e[u], v[u].z, o.z); o.w = fmaf(e[u], v[u].w, o.w);
+                }
             }
-            for (; j < k; ++j) {
-                const float2 v = *reinterpret_cast<const float2*>(slab0 + (int64_t)j * slab_stride +
-                                                                  (int64_t)s_s[j] * (3 * FS_D) + 2 * FS_D + c0);
-                ox = fmaf(ev[j], v.x, ox);
-                oy = fmaf(ev[j], v.y, oy);
+            if (half == (k & 1)) {                           // the own value row, once
+                const float4 v = *reinterpret_cast<const float4*>(sQ + r * FS_LDQ + 2 * FS_D + 4 * dq);
+                o.x = fmaf(ev[k], v.x, o.x); o.y = fmaf(ev[k], v.y, o.y);
+                o.z = fmaf(ev[k], v.z, o.z); o.w = fmaf(ev[k], v.w, o.w);
             }
-            {
-                const float2 v = *reinterpret_cast<const float2*>(sQ + r * FS_LDQ + 2 * FS_D + c0);
-                ox = fmaf(ev[k], v.x, ox);
-                oy = fmaf(ev[k], v.y, oy);
-            }
+            o.x += __shfl_xor_sync(0xffffffffu, o.x, 16);
+            o.y += __shfl_xor_sync(0xffffffffu, o.y, 16);
+            o.z += __shfl_xor_sync(0xffffffffu, o.z, 16);
+            o.w += __shfl_xor_sync(0xffffffffu, o.w, 16);
             float il = inv_l[0];
 #pragma unroll
             for (int h2 = 1; h2 < FS_H; ++h2) il = hd == h2 ? inv_l[h2] : il;
-            fs_put2<MODE>(sA, FS_LDA, FS_D, r, c0, ox * il, oy * il);
+            if (half == 0) {
+                fs_put2<MODE>(sA, FS_LDA, FS_D, r, 4 * dq, o.x * il, o.y * il);
+                fs_put2<MODE>(sA, FS_LDA, FS_D, r, 4 * dq + 2, o.z * il, o.w * il);
+            }
         }
         __syncthreads();
         // ---- h += o . Wo^T + bo: 8 n-tiles, K split over two warp halves
         {
-            const __nv_bfloat16* W = A.wb + A.woff[l][TF_WO];
             const int t = warp & 7, kh = warp >> 3;
             float c[4] = {0.f, 0.f, 0.f, 0.f};
-            fs_tile<KX * FS_D / 32>(sA, FS_LDA, W, KX * FS_D, 8 * t, kh * (KX * FS_D / 2), c, lane);
-            const int col = 8 * t + 2 * q4;
-            if (kh) {
-                *reinterpret_cast<float2*>(sRed + g * FS_LDH + col) = make_float2(c[0], c[1]);
-                *reinterpret_cast<float2*>(sRed + (g + 8) * FS_LDH + col) = make_float2(c[2], c[3]);
-            }
-            __syncthreads();
-            if (!kh) {
-                const float2 bb = *reinterpret_cast<const float2*>(P + mc.bo[l] + col);
-                const float2 p0 = *reinterpret_cast<const float2*>(sRed + g * FS_LDH + col);
-                const float2 p1 = *reinterpret_cast<const float2*>(sRed + (g + 8) * FS_LDH + col);
-                float2* h0 = reinterpret_cast<float2*>(sH + g * FS_LDH + col);
-                float2* h1 = reinterpret_cast<float2*>(sH + (g + 8) * FS_LDH + col);
-                h0->x += (c[0] + p0.x) + bb.x; h0->y += (c[1] + p0.y) + bb.y;
-                h1->x += (c[2] + p1.x) + bb.x; h1->y += (c[3] + p1.y) + bb.y;
-            }
+            fs_tile<MODE, FS_D / 32>(sA, FS_LDA, FS_D, sWo, FS_LDW, 8 * t, kh * (FS_D / 2), c, lane);
+            fs_resid_join(sH, sRed, pv + fs_pv_start(1), c, kh, 8 * t + 2 * q4, g);
         }
         __syncthreads();
+        if (next) stage_a(l + 1);                            // Wqkv and Wo are free
         // ---- LayerNorm 2
         {
-            const float2 y = fs_ln(sH, r, P + mc.ln2_g[l], P + mc.ln2_b[l], lane);
+            const float2 y = fs_ln(sH, r, pv + fs_pv_start(2), pv + fs_pv_start(3), lane);
             fs_put2<MODE>(sA, FS_LDA, FS_D, r, 2 * lane, y.x, y.y);
         }
+        if (next) fs_cp_wait<1>(); else fs_cp_wait<0>();     // group B of this block has landed
         __syncthreads();
         // ---- hidden = GELU(a . W1^T + b1): 32 n-tiles, two per warp
         {
-            const __nv_bfloat16* W = A.wb + A.woff[l][TF_W1];
-            const float* b1 = P + mc.b1[l];
+            const float* b1 = pv + fs_pv_start(4);
 #pragma unroll
             for (int tt = 0; tt < 2; ++tt) {
                 const int t = warp + FS_WARPS * tt;
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
-                fs_tile<KX * FS_D / 16>(sA, FS_LDA, W, KX * FS_D, 8 * t, 0, c, lane);
+                fs_tile<MODE, FS_D / 16>(sA, FS_LDA, FS_D, sW1, FS_LDW, 8 * t, 0, c, lane);
                 const int col = 8 * t + 2 * q4;
                 const float2 bb = *reinterpret_cast<const float2*>(b1 + col);
                 fs_put2<MODE>(sG, FS_LDG, FS_F, g, col, gelu_tanh(c[0] + bb.x), gelu_tanh(c[1] + bb.y));
@@ -305,31 +431,16 @@ tf_step_fused_kernel(ModelConst mc, FsArgs A) {
         __syncthreads();
         // ---- h += hidden . W2^T + b2: 8 n-tiles, K split over two warp halves
         {
-            const __nv_bfloat16* W = A.wb + A.woff[l][TF_W2];
             const int t = warp & 7, kh = warp >> 3;
             float c[4] = {0.f, 0.f, 0.f, 0.f};
-            fs_tile<KX * FS_F / 32>(sG, FS_LDG, W, KX * FS_F, 8 * t, kh * (KX * FS_F / 2), c, lane);
-            const int col = 8 * t + 2 * q4;
-            if (kh) {
-                *reinterpret_cast<float2*>(sRed + g * FS_LDH + col) = make_float2(c[0], c[1]);
-                *reinterpret_cast<float2*>(sRed + (g + 8) * FS_LDH + col) = make_float2(c[2], c[3]);
-            }
-            __syncthreads();
-            if (!kh) {
-                const float2 bb = *reinterpret_cast<const float2*>(P + mc.b2[l] + col);
-                const float2 p0 = *reinterpret_cast<const float2*>(sRed + g * FS_LDH + col);
-                const float2 p1 = *reinterpret_cast<const float2*>(sRed + (g + 8) * FS_LDH + col);
-                float2* h0 = reinterpret_cast<float2*>(sH + g * FS_LDH + col);
-                float2* h1 = reinterpret_cast<float2*>(sH + (g + 8) * FS_LDH + col);
-                h0->x += (c[0] + p0.x) + bb.x; h0->y += (c[1] + p0.y) + bb.y;
-                h1->x += (c[2] + p1.x) + bb.x; h1->y += (c[3] + p1.y) + bb.y;
-            }
+            fs_tile<MODE, FS_F / 32>(sG, FS_LDG, FS_F, sW2, FS_LDW2, 8 * t, kh * (FS_F / 2), c, lane);
+            fs_resid_join(sH, sRed, pv + fs_pv_start(5), c, kh, 8 * t + 2 * q4, g);
         }
         __syncthreads();
-        if (l + 1 < mc.layers) {
-            const float2 y = fs_ln(sH, r, P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], lane);
+        if (next) {
+            stage_b(l + 1);                                  // W1 and W2 are free
+            const float2 y = fs_ln(sH, r, pv + FS_PV + fs_pv_start(6), pv + FS_PV + fs_pv_start(7), lane);
             fs_put2<MODE>(sA, FS_LDA, FS_D, r, 2 * lane, y.x, y.y);
-            __syncthreads();
         }
     }
 
@@ -348,9 +459,9 @@ tf_step_fused_kernel(ModelConst mc, FsArgs A) {
     } else if (cnt >= need) {
         p = 0.f;
     } else {
-        const float2 y = fs_ln(sH, r, P + mc.lnf_g, P + mc.lnf_b, lane);
-        const float2 hw = *reinterpret_cast<const float2*>(P + mc.head_w + 2 * lane);
-        const float a = warp_sum(fmaf(y.x, hw.x, y.y * hw.y)) + P[mc.head_b + k];
+        const float2 y = fs_ln(sH, r, sHead, sHead + FS_D, lane);
+        const float2 hw = *reinterpret_cast<const float2*>(sHead + 2 * FS_D + 2 * lane);
+        const float a = warp_sum(fmaf(y.x, hw.x, y.y * hw.y)) + sHead[3 * FS_D];
         p = 1.f / (1.f + expf(-a));
     }
     if (lane == 0 && live) {
@@ -378,12 +489,18 @@ int tf_step_fused(const ModelConst& mc, const float* P, const TfWeights& w, cons
     int dev = 0;
     NQS_CK(cudaGetDevice(&dev));
     if (configured_device != dev) {
-        NQS_CK(cudaFuncSetAttribute(tf_step_fused_kernel<ACT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_SMEM));
-        NQS_CK(cudaFuncSetAttribute(tf_step_fused_kernel<ACT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_SMEM));
+        const int most = fs_smem_bytes(TF_MAX_LAYERS);
+        NQS_CK(cudaFuncSetAttribute(tf_step_fused_kernel<ACT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+        NQS_CK(cudaFuncSetAttribute(tf_step_fused_kernel<ACT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
         configured_device = dev;
     }
     FsArgs a{};
     a.P = P;
+    for (int l = 0; l < mc.layers; ++l) {
+        const int64_t f[FS_PV_NF] = {mc.bqkv[l], mc.bo[l], mc.ln2_g[l], mc.ln2_b[l], mc.b1[l], mc.b2[l], mc.ln1_g[l], mc.ln1_b[l]};
+        for (int i = 0; i < FS_PV_NF; ++i) a.pv[l][i] = f[i];
+    }
+    a.pg[0] = mc.lnf_g; a.pg[1] = mc.lnf_b; a.pg[2] = mc.head_w; a.pg[3] = mc.head_b;
     a.wb = reinterpret_cast<const __nv_bfloat16*>(w.bf16);
     for (int l = 0; l < mc.layers; ++l)
         for (int m = 0; m < 4; ++m) a.woff[l][m] = w.bf16_off[l][m];
@@ -394,8 +511,9 @@ int tf_step_fused(const ModelConst& mc, const float* P, const TfWeights& w, cons
     const int64_t M = R;
     const double flops = 2.0 * M * mc.layers * (double)FS_D * (3 * FS_D + FS_D + 2 * FS_F) * (mc.compensated ? 2 : 1);
     ProfScope ps("tf_step_fused", s, flops, 0.0);
-    if (mc.compensated) tf_step_fused_kernel<ACT_BF16X2><<<grid, FS_THREADS, FS_SMEM, s>>>(mc, a);
-    else tf_step_fused_kernel<ACT_BF16><<<grid, FS_THREADS, FS_SMEM, s>>>(mc, a);
+    const int smem = fs_smem_bytes(mc.layers);
+    if (mc.compensated) tf_step_fused_kernel<ACT_BF16X2><<<grid, FS_THREADS, smem, s>>>(mc, a);
+    else tf_step_fused_kernel<ACT_BF16><<<grid, FS_THREADS, smem, s>>>(mc, a);
     NQS_LAUNCHED();
     return NQS_OK;
 }
