@@ -209,12 +209,24 @@ int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t
 
 // transformer (transformer.cu, tc_gemm.cu)
 enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3, TF_EPI_GELU2 = 4,
-       TF_EPI_RESID_LN = 5 };   // h += acc + bias, then a = LayerNorm(h) as hi|lo bf16 (d = 64)
+       TF_EPI_RESID_LN = 5,     // h += acc + bias, then a = LayerNorm(h) as hi|lo bf16 (d = 64)
+       TF_EPI_RESID_LN_TAB = 6  // the same with the old h taken from a token-position table
+};
+// First-block rows that depend on the (token, position) pair only: the token of position t is 2
+// at t = 0 and bit order[t - 1] of the sequence's configuration after it; row (token, t) of a
+// table sits at tab + (token * T + t) * width.
+struct TcTokTable {
+    const float* tab = nullptr;
+    const uint64_t* bits = nullptr;   // one configuration per sequence
+    int T = 0;
+    uint8_t order[MAX_Q] = {};
+};
 enum { TF_WQKV = 0, TF_WO = 1, TF_W1 = 2, TF_W2 = 3 };
 struct TfBufs {
     int64_t R;            // sequences per pass
     float *h, *a, *qkv, *o, *mid;
     float *logit, *hph;      // per-row head logits and per-sequence h of position n - 2 (fused heads)
+    float *tab_h, *tab_qkv;  // first-block tables over (token, position): h [3T][d], q|k|v [3T][3d]
     bool fused_heads;        // the last forward left logit / hph instead of the final h
 };
 struct TfWeights {
@@ -293,11 +305,13 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
 // h[M, 64] += A . W^T + bias, then a[M, 2*64] = hi|lo of LayerNorm(h; ln_g, ln_b) (compensated
 // BF16 transformer, d_model 64): the attention-output GEMM with the next LayerNorm fused in.
 int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
-                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s);
+                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s,
+                          const TcTokTable* h_old = nullptr);
 // o = causal attention of (A . Wqkv^T + bqkv) for the compensated d_model-64 transformer with
 // head size 16, without writing qkv (R sequences of T <= 64 positions; o hi|lo bf16).
 int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, void* o, int64_t R, int T,
-                          cudaStream_t s);
+                          cudaStream_t s, const TcTokTable* qkv = nullptr);
+bool tc_qkv_gather_fits(int T);   // the gather form's table fits its shared memory
 int tc_status_take();
 struct TfCtx {
     const TfWeights* w;

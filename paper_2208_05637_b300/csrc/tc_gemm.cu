@@ -261,7 +261,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmD,
                const float* __restrict__ bias, void* __restrict__ Cv, const float* __restrict__ ln_g,
                const float* __restrict__ ln_b, int64_t M, int N, int K, int BN, int tmem_cols, int stages,
-               int n_tiles_n, int64_t total_tiles) {
+               int n_tiles_n, int64_t total_tiles, const __grid_constant__ TcTokTable tok) {
+    constexpr bool RLN = EPI == TF_EPI_RESID_LN || EPI == TF_EPI_RESID_LN_TAB;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nkb = (K + TC_BK - 1) / TC_BK;
@@ -351,18 +352,38 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             tma_load_2d(stg + 4096, &tmC, &hbar[quad], 32, nrow);
         }
         __syncwarp();
+        // TAB: the configuration of this lane's row, loaded one tile ahead
+        auto tab_bits = [&](int64_t tile) -> uint64_t {
+            if (EPI != TF_EPI_RESID_LN_TAB || tile >= total_tiles) return 0ull;
+            const int64_t row = min((tile / n_tiles_n) * TC_BM + quad * 32 + lane, M - 1);
+            return __ldg(tok.bits + row / tok.T);
+        };
+        uint64_t xb_next = tab_bits(blockIdx.x);
         for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x, ++acc) {
             const int buf = (int)(acc & 1);
+            const uint64_t xb = xb_next;
+            if constexpr (EPI == TF_EPI_RESID_LN_TAB) xb_next = tab_bits(t + gridDim.x);
             if (!mbar_wait_or_abort(&tfull[buf], (uint32_t)((acc >> 1) & 1), abort)) break;
             tc_fence_after();
             const int64_t row0 = (t / n_tiles_n) * TC_BM + quad * 32;
             const int n0 = (int)(t % n_tiles_n) * BN;
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * (tmem_cols >> 1));
-            if constexpr (EPI == TF_EPI_RESID_LN) {
+            if constexpr (RLN) {
                 // the tile spans whole rows of d = 64: lane = row.  h_new = h + acc + bias,
-                // stored back; then a = LayerNorm(h_new) as hi | lo bf16.
+                // stored back; then a = LayerNorm(h_new) as hi | lo bf16.  The old h comes through
+                // the staging (TMA), or from the token-position table (TAB: first block)
                 const int64_t hrow0 = (t / n_tiles_n) * TC_BM + quad * 32;
-                if (!mbar_wait_or_abort(&hbar[quad], (uint32_t)(acc & 1), abort)) break;
+                const float* hrow = nullptr;
+                if constexpr (EPI == TF_EPI_RESID_LN_TAB) {
+                    const int64_t row = min(hrow0 + lane, M - 1);
+                    const int tp = (int)(row % tok.T);
+                    const int tk = tp == 0 ? 2 : (int)((xb >> tok.order[tp - 1]) & 1ull);
+                    hrow = tok.tab + (int64_t)(tk * tok.T + tp) * 64;
+                    if (lane == 0) bulk_wait_read<0>();      // the previous tile's stores have read the staging
+                    __syncwarp();
+                } else {
+                    if (!mbar_wait_or_abort(&hbar[quad], (uint32_t)(acc & 1), abort)) break;
+                }
                 const uint32_t st = su32(stg);
                 const int sw = lane & 7;
                 // address of columns c .. c+3 of this lane's row in the staging (two 32-column halves)
@@ -380,7 +401,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         const int c = 16 * p + 4 * u;
                         const uint32_t addr = saddr(c);
                         float4 o;
-                        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(addr));
+                        if constexpr (EPI == TF_EPI_RESID_LN_TAB) o = __ldg(reinterpret_cast<const float4*>(hrow + c));
+                        else asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(addr));
                         o.x += v16[4 * u] + bias[c];
                         o.y += v16[4 * u + 1] + bias[c + 1];
                         o.z += v16[4 * u + 2] + bias[c + 2];
@@ -448,7 +470,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     bulk_commit();
                     // the next tile's residual rows into the staging once these stores have read it
                     const int64_t tn = t + gridDim.x;
-                    if (tn < total_tiles) {
+                    if (EPI == TF_EPI_RESID_LN && tn < total_tiles) {
                         bulk_wait_read<0>();
                         mbar_expect_tx(&hbar[quad], 8192);
                         const int nrow = (int)((tn / n_tiles_n) * TC_BM + quad * 32);
@@ -497,7 +519,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         // the staging buffers (and the results) must be complete before the CTA exits
-        if ((TMA_EPI || EPI == TF_EPI_RESID_LN) && lane == 0) bulk_wait_all();
+        if ((TMA_EPI || RLN) && lane == 0) bulk_wait_all();
         __syncwarp();
     }
     tc_fence_before();
@@ -1095,6 +1117,7 @@ constexpr int QA_MAX_WARPS = 14;
 constexpr int QA_LH = 20;                       // head stride (16 + 4 floats)
 constexpr int QA_LU = 2 * 4 * QA_LH + 4;        // K|V row stride (164 floats: rows land on distinct bank groups)
 constexpr int QA_QL = 4 * QA_LH + 4;            // Q row stride (84 floats)
+constexpr int QA_TAB_LD = 196;          // gather form: padded table row (floats) in shared memory
 constexpr int QA_O_BYTES = 2 * 128 * 128;       // o staging: hi and lo, up to 128 rows x 128 bytes
 
 __device__ __forceinline__ void bar_sync_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
@@ -1287,11 +1310,13 @@ __device__ __forceinline__ void qa_unit_mma(const float* qs, const float* kv, in
         }
 }
 
-template <int MT, int NT>   // MT = 0: CUDA-core row-pair attention (any T <= 64)
+// GATHER: the first block, whose q, k and v rows depend on (token, position) only, gathers them
+// from a table (without the bias) instead of running the projection.
+template <int MT, int NT, bool GATHER>   // MT = 0: CUDA-core row-pair attention (any T <= 64)
 __global__ void __launch_bounds__(64 + 32 * QA_MAX_WARPS, 1)
 tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
                    const __grid_constant__ CUtensorMap tmO, const float* __restrict__ bqkv, int64_t R, int T, int S,
-                   int SS, int SQ, int64_t ntiles) {
+                   int SS, int SQ, int64_t ntiles, const __grid_constant__ TcTokTable tok) {
     constexpr int H = 4, DH = 16;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1311,6 +1336,15 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int AW = (int)(blockDim.x >> 5) - 2;       // attention warps
     const int rows_tile = S * T;
+    // gather form: the 3T table rows (q | k | v, QA_TAB_LD floats apart) in place of Wqkv and A
+    float* sTab = reinterpret_cast<float*>(sW);
+    if constexpr (GATHER) {
+        const int n4 = 3 * T * 48;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+            const int row = i / 48, c4 = i - row * 48;
+            reinterpret_cast<float4*>(sTab + row * QA_TAB_LD)[c4] = __ldg(reinterpret_cast<const float4*>(tok.tab + row * 192) + c4);
+        }
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(w_full, 1);
@@ -1320,17 +1354,17 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (!GATHER && warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = GATHER ? 0u : *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
+        if (!GATHER && lane == 0) {
             // ---- producer: Wqkv once, then each tile's A rows
             mbar_expect_tx(w_full, 24576);
             tma_load_2d(sW, &tmW, w_full, 0, 0);
@@ -1346,7 +1380,7 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             if (tt > 0) mbar_wait(a_full, (uint32_t)((tt - 1) & 1));
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (!GATHER && lane == 0) {
             // ---- MMA issuer: qkv = A_hi . W^T + A_lo . W^T into accumulator tt % 2
             const uint32_t id = idesc_bf16(128, 192);
             bool ok = mbar_wait_or_abort(w_full, 0, abort);
@@ -1380,20 +1414,43 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         const int npairs = (T + 1) / 2;
         const bool g_ok = lane < S * H;
         const int gs = g_ok ? lane / H : 0, gh = lane & (H - 1);
+        // gather form: this row's configuration, loaded one tile ahead
+        auto row_bits = [&](int64_t tile) -> uint64_t {
+            return (GATHER && r < rows_tile && tile < ntiles) ? __ldg(tok.bits + min(tile * S + r / T, R - 1)) : 0ull;
+        };
+        uint64_t xb_next = row_bits(blockIdx.x);
         int64_t tt = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tt) {
             const int b = (int)(tt & 1);
+            const uint64_t xb = xb_next;
+            if constexpr (GATHER) xb_next = row_bits(t + gridDim.x);
             // every attention warp reaches the named barriers below, even after a timed-out
             // wait, and all of them leave together when the abort flag is up
-            const bool got = mbar_wait_or_abort(&acc_full[b], (uint32_t)((tt >> 1) & 1), abort);
-            tc_fence_after();
+            bool got = true;
+            if constexpr (!GATHER) {
+                got = mbar_wait_or_abort(&acc_full[b], (uint32_t)((tt >> 1) & 1), abort);
+                tc_fence_after();
+            }
             // stage Q, K, V (+ bias) of this quadrant's 32 rows: parts qidx, qidx + qcount, ...
             if (got) {
                 for (int part = qidx; part < 3; part += qcount) {
                     float v[64];
+                    if constexpr (GATHER) {
+                        if (r < rows_tile) {
+                            const int tp = r % T;
+                            const int tk = tp == 0 ? 2 : (int)((xb >> tok.order[tp - 1]) & 1ull);
+                            const float4* src = reinterpret_cast<const float4*>(sTab + (tk * T + tp) * QA_TAB_LD + part * 64);
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) tmem_ld16_nowait(lane_base + (uint32_t)(b * 256 + part * 64 + 16 * p), v + 16 * p);
-                    tmem_wait_ld();
+                            for (int j4 = 0; j4 < 16; ++j4) {
+                                const float4 x = src[j4];
+                                v[4 * j4] = x.x; v[4 * j4 + 1] = x.y; v[4 * j4 + 2] = x.z; v[4 * j4 + 3] = x.w;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) tmem_ld16_nowait(lane_base + (uint32_t)(b * 256 + part * 64 + 16 * p), v + 16 * p);
+                        tmem_wait_ld();
+                    }
                     if (r < rows_tile) {
                         const int sq = r / T, tp = r - sq * T;
                         float* dst = part == 0 ? sQ + (size_t)sq * SQ + tp * QA_QL
@@ -1410,9 +1467,11 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0 && got) mbar_arrive(&acc_empty[b]);
+            if constexpr (!GATHER) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0 && got) mbar_arrive(&acc_empty[b]);
+            }
             // the previous tile's o stores must have read the staging before it is rewritten
             if (threadIdx.x == 64) bulk_wait_read<0>();
             bar_sync_named(1, 32 * AW);                          // staging complete
@@ -1464,7 +1523,7 @@ tc_qkv_attn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (!GATHER && warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
@@ -1555,7 +1614,7 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
             configured_device[slot] = dev;
         }
         kernel<<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, mc, bias, C, nullptr, nullptr, M, N, K, BN, tcols, stages,
-                                              n_tiles_n, total_tiles);
+                                              n_tiles_n, total_tiles, TcTokTable{});
         NQS_LAUNCHED();
         return NQS_OK;
     };
@@ -1575,10 +1634,12 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
 // Attention-output GEMM with the next LayerNorm fused into its epilogue (compensated BF16,
 // d_model 64): h += A . W^T + bias; a = hi | lo of LayerNorm(h; ln_g, ln_b).
 int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
-                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s) {
+                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s,
+                          const TcTokTable* h_old) {
     if (M <= 0) return NQS_OK;
     constexpr int N = 64, BN = 64, tcols = 128;
-    if (K % 64 || K <= 0 || ((uintptr_t)h & 15) || ((uintptr_t)a_out & 15) || !bias || !ln_g || !ln_b) {
+    if (K % 64 || K <= 0 || ((uintptr_t)h & 15) || ((uintptr_t)a_out & 15) || !bias || !ln_g || !ln_b ||
+        (h_old && (!h_old->tab || !h_old->bits || h_old->T < 1 || ((uintptr_t)h_old->tab & 15)))) {
         set_error("fused residual + LayerNorm GEMM: bad operand");
         return NQS_ERR_INVALID_ARG;
     }
@@ -1600,21 +1661,35 @@ int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, f
     if (configured_device != dev) {
         cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<TF_EPI_RESID_LN, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tc_gemm_kernel<TF_EPI_RESID_LN_TAB, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm resid_ln)", __FILE__, __LINE__);
         configured_device = dev;
     }
-    tc_gemm_kernel<TF_EPI_RESID_LN, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N, K,
-                                                                          BN, tcols, stages, 1, total_tiles);
+    if (h_old)
+        tc_gemm_kernel<TF_EPI_RESID_LN_TAB, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N,
+                                                                                  K, BN, tcols, stages, 1, total_tiles, *h_old);
+    else
+        tc_gemm_kernel<TF_EPI_RESID_LN, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N, K,
+                                                                              BN, tcols, stages, 1, total_tiles, TcTokTable{});
     NQS_LAUNCHED();
     return NQS_OK;
 }
 
+bool tc_qkv_gather_fits(int T) { return 3 * T * QA_TAB_LD * 4 <= 24576 + 32768; }
+
 // Fused QKV projection + causal attention (compensated BF16, d_model 64, head size 16, T <= 64):
 // o (hi | lo bf16 [R*T, 128]) = attention of qkv = A . Wqkv^T + bqkv, A = [a_hi | a_lo] [R*T, 128].
 int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, void* o, int64_t R, int T,
-                          cudaStream_t s) {
+                          cudaStream_t s, const TcTokTable* qkv) {
     if (R <= 0) return NQS_OK;
-    if (T < 1 || T > 64 || ((uintptr_t)o & 15) || !bqkv) { set_error("fused QKV attention: bad operand"); return NQS_ERR_INVALID_ARG; }
+    if (T < 1 || T > 64 || ((uintptr_t)o & 15) || !bqkv ||
+        (qkv && (!qkv->tab || !qkv->bits || qkv->T != T || ((uintptr_t)qkv->tab & 15) ||
+                 !tc_qkv_gather_fits(T)))) {
+        set_error("fused QKV attention: bad operand");
+        return NQS_ERR_INVALID_ARG;
+    }
     const int S = std::min(8, 128 / T);
     const int SS = grp_seq_stride(T * QA_LU, 4, QA_LH, S);
     const int SQ = grp_seq_stride(T * QA_QL, 4, QA_LH, S);
@@ -1626,14 +1701,17 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
                       : std::max(4, std::min(QA_MAX_WARPS, (T + 1) / 2));
     const size_t smem = 1024 + 24576 + 32768 + QA_O_BYTES + (size_t)(S * SS + S * SQ) * 4 + 7 * 8 + 16;
     if (smem > 227 * 1024) { set_error("fused QKV attention: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
-    CUtensorMap ma, mw, mo;
-    NQS_TRY(make_map(&ma, A, R * T, 128, 128));
-    NQS_TRY(make_map(&mw, Wd, 192, 128, 192));       // first K half of [W | W]: W itself
+    CUtensorMap ma{}, mw{}, mo;
+    if (!qkv) {                                       // the gather form reads neither A nor Wqkv
+        NQS_TRY(make_map(&ma, A, R * T, 128, 128));
+        NQS_TRY(make_map(&mw, Wd, 192, 128, 192));   // first K half of [W | W]: W itself
+    }
     NQS_TRY(make_map(&mo, o, R * T, 128, S * T));     // o: hi | lo, boxes of 64 bf16 x (S*T) rows
     const int64_t ntiles = (R + S - 1) / S;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
+    const TcTokTable tok = qkv ? *qkv : TcTokTable{};
     auto launch = [&](auto kernel, int slot) -> int {
-        static int configured_device[4] = {-1, -1, -1, -1};
+        static int configured_device[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
         int dev = 0;
         NQS_CK(cudaGetDevice(&dev));
         if (configured_device[slot] != dev) {
@@ -1641,14 +1719,20 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_qkv_attn)", __FILE__, __LINE__);
             configured_device[slot] = dev;
         }
-        kernel<<<grid, 64 + 32 * AW, smem, s>>>(ma, mw, mo, bqkv, R, T, S, SS, SQ, ntiles);
+        kernel<<<grid, 64 + 32 * AW, smem, s>>>(ma, mw, mo, bqkv, R, T, S, SS, SQ, ntiles, tok);
         NQS_LAUNCHED();
         return NQS_OK;
     };
-    if (mt == 1) return launch(tc_qkv_attn_kernel<1, 2>, 0);
-    if (mt == 2 && nt == 3) return launch(tc_qkv_attn_kernel<2, 3>, 1);
-    if (mt == 2) return launch(tc_qkv_attn_kernel<2, 4>, 2);
-    return launch(tc_qkv_attn_kernel<0, 0>, 3);
+    if (qkv) {
+        if (mt == 1) return launch(tc_qkv_attn_kernel<1, 2, true>, 4);
+        if (mt == 2 && nt == 3) return launch(tc_qkv_attn_kernel<2, 3, true>, 5);
+        if (mt == 2) return launch(tc_qkv_attn_kernel<2, 4, true>, 6);
+        return launch(tc_qkv_attn_kernel<0, 0, true>, 7);
+    }
+    if (mt == 1) return launch(tc_qkv_attn_kernel<1, 2, false>, 0);
+    if (mt == 2 && nt == 3) return launch(tc_qkv_attn_kernel<2, 3, false>, 1);
+    if (mt == 2) return launch(tc_qkv_attn_kernel<2, 4, false>, 2);
+    return launch(tc_qkv_attn_kernel<0, 0, false>, 3);
 }
 
 // Fused MLP block of the compensated transformer (see tc_mlp_kernel); D = 64 or 128.

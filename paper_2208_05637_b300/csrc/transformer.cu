@@ -397,6 +397,8 @@ void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b) {
     b.o = c.take<float>(M * d);          // fp32 or bf16 view
     b.mid = c.take<float>(M * 4 * d);    // fp32 or bf16 view
     b.logit = c.take<float>(M);
+    b.tab_h = c.take<float>(3 * (int64_t)mc.n * d);
+    b.tab_qkv = c.take<float>(3 * (int64_t)mc.n * 3 * d);
     b.hph = c.take<float>(R * 64);
     b.fused_heads = false;
 }
@@ -434,13 +436,63 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
 // Attention-output projection of block l with the residual add and LayerNorm 2 fused
 // (compensated BF16, d_model 64): h += Wo . o + bo; a = LN2(h).
 static int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* o, float* h,
-                       void* a, int64_t M, cudaStream_t s) {
+                       void* a, int64_t M, cudaStream_t s, const TcTokTable* h_old = nullptr) {
     const int d = mc.hidden;
-    // A (hi+lo) read, h read and written, a (hi+lo) written, weights
-    const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * 2 + (double)M * 2 * d * 2 + 2.0 * d * d * 2;
+    // A (hi+lo) read, h read (unless it comes from the token-position table) and written,
+    // a (hi+lo) written, weights
+    const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * (h_old ? 1 : 2) + (double)M * 2 * d * 2 +
+                         2.0 * d * d * 2;
     ProfScope ps("tf_resid_ln", s, 2.0 * (double)M * d * d, bytes);
     return tc_gemm_bf16_resid_ln(o, w.bf16 + w.bf16_off[layer][TF_WO], P + mc.bo[layer], h, a, P + mc.ln2_g[layer],
-                                 P + mc.ln2_b[layer], M, 2 * d, s);
+                                 P + mc.ln2_b[layer], M, 2 * d, s, h_old);
+}
+
+// The first block's rows as functions of the (token, position) pair, for positions 0..T-1 of the
+// compensated d_model-64 model: h0 = tok_emb[token] + pos_emb[t] and the projection
+// LN1_0(h0) . Wqkv^T with the tensor-core operands (hi + lo activations against the bf16
+// weights, products summed in fp32; the bias is added where the rows are used).  One CTA of 192
+// threads per (token, position); rows that never occur (token 2 past t = 0, tokens 0 and 1 at
+// t = 0) are computed too and left unused.
+__global__ void __launch_bounds__(192)
+tok_table_kernel(ModelConst mc, const float* __restrict__ P, const __nv_bfloat16* __restrict__ Wqkv, int ldw, int T,
+                 float* __restrict__ tab_h, float* __restrict__ tab_qkv) {
+    constexpr int D = 64;
+    __shared__ float s_hi[D], s_lo[D];
+    const int row = blockIdx.x;                    // token * T + t
+    const int tok = row / T, t = row - tok * T;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, c0 = 2 * lane;
+        float v[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            v[i] = P[mc.tok_emb + tok * D + c0 + i] + P[mc.pos_emb + t * D + c0 + i];
+            tab_h[row * D + c0 + i] = v[i];
+        }
+        const float inv_d = 1.f / (float)D;
+        const float mu = warp_sum(v[0] + v[1]) * inv_d;
+        float q = 0.f;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) { const float c = v[i] - mu; q += c * c; }
+        const float rstd = rsqrtf(fmaf(warp_sum(q), inv_d, LN_EPS));
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float y = (v[i] - mu) * rstd * P[mc.ln1_g[0] + c0 + i] + P[mc.ln1_b[0] + c0 + i];
+            const float hi = __bfloat162float(__float2bfloat16_rn(y));
+            s_hi[c0 + i] = hi;
+            s_lo[c0 + i] = __bfloat162float(__float2bfloat16_rn(y - hi));
+        }
+    }
+    __syncthreads();
+    const int j = threadIdx.x;                     // output column
+    const __nv_bfloat16* wr = Wqkv + (int64_t)j * ldw;
+    float acc = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < D; ++k) {
+        const float wk = __bfloat162float(wr[k]);
+        acc = fmaf(s_hi[k], wk, acc);
+        acc = fmaf(s_lo[k], wk, acc);
+    }
+    tab_qkv[row * 3 * D + j] = acc;
 }
 
 // MLP half of block l: h += W2 . gelu(W1 . a + b1) + b2.  Compensated BF16 models with d_model
@@ -514,18 +566,33 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
         // bf16 hi + lo); a plain bf16 form would be 2
         const double act_b = MODE == ACT_BF16 ? 2.0 : 4.0;
         const double ln_bytes = (double)M * d * (4.0 + act_b);       // h read (or written) + a written
-        {
+        const bool fused_qkv_attention = MODE == ACT_BF16X2 && d == 64 && mc.heads == 4 && T <= 64;
+        // the compensated d = 64 forward takes the first block's h and q | k | v rows from tables
+        // over the 3T (token, position) pairs; the others embed every row
+        const bool tables = fused_qkv_attention && tc_qkv_gather_fits(T);
+        TcTokTable tab_qkv, tab_h;
+        if (tables) {
+            tab_qkv.tab = b.tab_qkv; tab_qkv.bits = bits; tab_qkv.T = T;
+            for (int t = 0; t < mc.n; ++t) tab_qkv.order[t] = mc.order[t];
+            tab_h = tab_qkv;
+            tab_h.tab = b.tab_h;
+            ProfScope ps("tf_tok_table", s, 2.0 * 3 * T * 2 * d * 3 * d, 3.0 * T * 4 * d * 4);
+            tok_table_kernel<<<3 * T, 192, 0, s>>>(mc, P, reinterpret_cast<const __nv_bfloat16*>(w.bf16 + w.bf16_off[0][TF_WQKV]),
+                                                   2 * d, T, b.tab_h, b.tab_qkv);
+            NQS_LAUNCHED();
+        } else {
             ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
             embed_ln_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(mc, P, bits, R, T, 0, b.h, b.a);
             NQS_LAUNCHED();
         }
-        const bool fused_qkv_attention = MODE == ACT_BF16X2 && d == 64 && mc.heads == 4 && T <= 64;
         for (int l = 0; l < mc.layers; ++l) {
             if (fused_qkv_attention) {
-                // A (hi+lo) read, o (hi+lo) written, Wqkv
-                ProfScope ps("tf_qkv_attention", s, 2.0 * (double)M * 3 * d * d,
-                             (double)M * 2 * d * 2 + (double)M * d * act_b + 3.0 * d * d * 2);
-                NQS_TRY(tc_qkv_attention_bf16(b.a, w.bf16 + w.bf16_off[l][TF_WQKV], P + mc.bqkv[l], b.o, R, T, s));
+                // A (hi+lo) read unless gathered, o (hi+lo) written, Wqkv
+                const bool gather = tables && l == 0;
+                ProfScope ps("tf_qkv_attention", s, gather ? 0.0 : 2.0 * (double)M * 3 * d * d,
+                             (gather ? (double)R * 8 : (double)M * 2 * d * 2 + 3.0 * d * d * 2) + (double)M * d * act_b);
+                NQS_TRY(tc_qkv_attention_bf16(b.a, w.bf16 + w.bf16_off[l][TF_WQKV], P + mc.bqkv[l], b.o, R, T, s,
+                                              gather ? &tab_qkv : nullptr));
             } else {
                 NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, b.a, b.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
                 ProfScope ps("tf_attention", s, 0.0, (double)M * 3 * d * 4 + (double)M * d * act_b);
@@ -533,7 +600,7 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
                 count_launch();
             }
             if (MODE == ACT_BF16X2 && d == 64) {
-                NQS_TRY(tf_resid_ln(mc, P, w, l, b.o, b.h, b.a, M, s));
+                NQS_TRY(tf_resid_ln(mc, P, w, l, b.o, b.h, b.a, M, s, tables && l == 0 ? &tab_h : nullptr));
             } else {
                 NQS_TRY(tf_gemm(mc, w, TF_WO, l, b.o, b.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
                 ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
