@@ -127,6 +127,8 @@ struct ElocBufs {
     float4* S;
     float2* contrib;     // transformer: per-row ratio-weighted contributions
     TfBufs tf;
+    DedupBufs dd;        // transformer: the chunk's distinct x'
+    bool dedup;          // x' dedup applies (the all-ones word is then no configuration)
     int64_t chunk, ntiles, rows_cap;
 };
 
@@ -142,9 +144,12 @@ static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int
     e.xprime = c.take<uint64_t>(e.rows_cap);
     e.S = c.take<float4>(e.rows_cap);
     e.contrib = nullptr;
+    e.dedup = false;
     if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
         e.contrib = c.take<float2>(e.rows_cap);
         tf_layout(c, m->mc, std::min(std::max<int64_t>(B, e.rows_cap), tf_seq_capacity(m->mc)), e.tf);
+        e.dedup = m->mc.n_up + m->mc.n_dn < m->mc.n;
+        if (e.dedup) dedup_layout(c, e.rows_cap, e.dd);
     }
 }
 
@@ -796,6 +801,22 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
             NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             NQS_CK(cudaStreamSynchronize(s));
             if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
+            if (e.dedup) {
+                // log psi once per distinct x' of the chunk, then the rows' contributions
+                int64_t nu = 0;
+                NQS_TRY(dedup_rows(e.xprime, rows, e.dd, &nu, s));
+                for (int64_t r0 = 0; r0 < nu; r0 += e.tf.R) {
+                    const int64_t R = std::min(e.tf.R, nu - r0);
+                    NQS_TRY(tf_forward(m->mc, m->d_params, w, e.dd.uniq + r0, R, m->mc.n, e.tf, s, true));
+                    HeadArgsHost ha{};
+                    ha.mode = 0; ha.la = e.dd.la_u + r0; ha.ph = e.dd.ph_u + r0;
+                    NQS_TRY(tf_heads(m->mc, m->d_params, e.dd.uniq + r0, R, m->mc.n, e.tf, ha, s));
+                }
+                NQS_TRY(dedup_contrib(e.xprime, rows, e.dd, bits + lo, e.la + lo, e.ph + lo, e.off, e.ntiles, nb, e.S,
+                                      e.contrib, s));
+                NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
+                continue;
+            }
             for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
                 const int64_t R = std::min(e.tf.R, rows - r0);
                 NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s, true));

@@ -1,0 +1,131 @@
+// Unique flipped configurations of a local-energy chunk.  The connected x' = x ^ m of the
+// chunk's samples repeat across samples (every x' lies in the same particle-number sector), so
+// log psi is evaluated once per distinct x' and the per-row contributions of Eq. local_energy_auto,
+// <x|P|x'> psi(x')/psi(x), gather it back (the cross-sample counterpart of the per-sample
+// unique flippings of the tensorized local energy).  Each row of the network forward depends on its own
+// configuration only, so the values are those of the row-by-row evaluation bit for bit.
+//
+// The distinct keys are found with an open-addressing hash table (linear probing, 64-bit
+// atomicCAS, load factor at most 1/2) and numbered in table-slot order by a scan of the
+// occupied flags.
+#include "nqs_internal.h"
+
+namespace nqs {
+namespace {
+
+constexpr uint64_t DD_EMPTY = ~0ull;   // not a configuration of any sector with N_up + N_dn < n
+
+__device__ __forceinline__ uint64_t dd_mix(uint64_t z) {   // SplitMix64 finaliser
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void dd_insert_kernel(const uint64_t* __restrict__ xp, int64_t rows, unsigned long long* table,
+                                 int64_t mask, int32_t* __restrict__ slot) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = xp[i];
+        int64_t h = (int64_t)(dd_mix(key) & (uint64_t)mask);
+        // at most mask + 1 probes: the table is never full
+        for (int64_t probe = 0; probe <= mask; ++probe) {
+            const unsigned long long prev = atomicCAS(table + h, (unsigned long long)DD_EMPTY, (unsigned long long)key);
+            if (prev == DD_EMPTY || prev == key) { slot[i] = (int32_t)h; break; }
+            h = (h + 1) & mask;
+        }
+    }
+}
+
+__global__ void dd_flag_kernel(const unsigned long long* __restrict__ table, int64_t n, int32_t* __restrict__ flags) {
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x)
+        flags[h] = table[h] != DD_EMPTY ? 1 : 0;
+}
+
+__global__ void dd_compact_kernel(const unsigned long long* __restrict__ table, int64_t n, const int64_t* __restrict__ pos,
+                                  uint64_t* __restrict__ uniq) {
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x)
+        if (table[h] != DD_EMPTY) uniq[pos[h]] = table[h];
+}
+
+// Row i of the chunk (sample lo = the segment holding i): S(x, x') times psi(x')/psi(x), with
+// log psi(x') from the unique list; the diagonal row x' = x keeps S alone.
+__global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows, const int32_t* __restrict__ slot,
+                                  const int64_t* __restrict__ pos, const float* __restrict__ la_u,
+                                  const float* __restrict__ ph_u, const uint64_t* __restrict__ xsample,
+                                  const float* __restrict__ la_x, const float* __restrict__ ph_x,
+                                  const int64_t* __restrict__ seg, int64_t seg_stride, int64_t nseg,
+                                  const float4* __restrict__ S, float2* __restrict__ contrib) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (seg[mid * seg_stride] <= i) lo = mid; else hi = mid - 1;
+        }
+        const float4 s4 = S[i];
+        const float sre = s4.x + s4.y, sim = s4.z + s4.w;
+        float cr = sre, ci = sim;
+        if (xp[i] != xsample[lo]) {
+            const int64_t u = pos[slot[i]];
+            const float mag = expf(la_u[u] - la_x[lo]);
+            float sn, cs;
+            sincosf(ph_u[u] - ph_x[lo], &sn, &cs);
+            const float rr = mag * cs, ri = mag * sn;
+            cr = sre * rr - sim * ri;
+            ci = sre * ri + sim * rr;
+        }
+        contrib[i] = make_float2(cr, ci);
+    }
+}
+
+inline int dd_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16)); }
+
+}  // namespace
+
+int64_t dedup_table_slots(int64_t rows_cap) {
+    int64_t h = 1024;
+    while (h < 2 * rows_cap) h <<= 1;
+    return h;
+}
+
+void dedup_layout(Carver& c, int64_t rows_cap, DedupBufs& d) {
+    d.hcap = dedup_table_slots(rows_cap);
+    d.table = c.take<uint64_t>(d.hcap);
+    d.flags = c.take<int32_t>(d.hcap);
+    d.pos = c.take<int64_t>(d.hcap + 1);
+    d.slot = c.take<int32_t>(rows_cap);
+    d.uniq = c.take<uint64_t>(rows_cap);
+    d.la_u = c.take<float>(rows_cap);
+    d.ph_u = c.take<float>(rows_cap);
+}
+
+int dedup_rows(const uint64_t* xp, int64_t rows, const DedupBufs& d, int64_t* n_unique, cudaStream_t s) {
+    *n_unique = 0;
+    if (rows <= 0) return NQS_OK;
+    if (2 * rows > d.hcap || d.hcap > (1ll << 31)) { set_error("x' dedup: table too small"); return NQS_ERR_CAPACITY; }
+    ProfScope ps("dedup", s, 0.0, (double)rows * (8 + 4) + (double)d.hcap * (8 * 3 + 4 * 2 + 8));
+    NQS_CK(cudaMemsetAsync(d.table, 0xff, (size_t)d.hcap * sizeof(uint64_t), s));
+    dd_insert_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, reinterpret_cast<unsigned long long*>(d.table), d.hcap - 1,
+                                                   d.slot);
+    NQS_LAUNCHED();
+    dd_flag_kernel<<<dd_grid(d.hcap), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), d.hcap, d.flags);
+    NQS_LAUNCHED();
+    NQS_TRY(launch_scan_i32(d.flags, d.hcap, d.pos, s));
+    dd_compact_kernel<<<dd_grid(d.hcap), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), d.hcap, d.pos,
+                                                      d.uniq);
+    NQS_LAUNCHED();
+    NQS_CK(cudaMemcpyAsync(n_unique, d.pos + d.hcap, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    return NQS_OK;
+}
+
+int dedup_contrib(const uint64_t* xp, int64_t rows, const DedupBufs& d, const uint64_t* xsample, const float* la_x,
+                  const float* ph_x, const int64_t* seg, int64_t seg_stride, int64_t nseg, const float4* S,
+                  float2* contrib, cudaStream_t s) {
+    if (rows <= 0) return NQS_OK;
+    ProfScope ps("dedup_contrib", s, 0.0, (double)rows * (8 + 4 + 8 + 8 + 16 + 8));
+    dd_contrib_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, d.slot, d.pos, d.la_u, d.ph_u, xsample, la_x, ph_x, seg,
+                                                    seg_stride, nseg, S, contrib);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+}  // namespace nqs

@@ -338,6 +338,25 @@ struct SamplerBufs {
     int32_t *ancA = nullptr, *ancB = nullptr;
     int32_t *par = nullptr, *par2 = nullptr;
 };
+// Unique flipped configurations of a local-energy chunk (dedup.cu): a hash table of hcap slots,
+// each row's slot, the slots' positions in the unique list, and log psi of the unique rows.
+struct DedupBufs {
+    uint64_t* table = nullptr;
+    int64_t hcap = 0;
+    int32_t* flags = nullptr;
+    int64_t* pos = nullptr;      // hcap + 1
+    int32_t* slot = nullptr;     // per row
+    uint64_t* uniq = nullptr;    // per unique row
+    float *la_u = nullptr, *ph_u = nullptr;
+};
+void dedup_layout(Carver& c, int64_t rows_cap, DedupBufs& d);
+// The distinct values of xp[0, rows) into d.uniq (their number into *n_unique; synchronizes s).
+int dedup_rows(const uint64_t* xp, int64_t rows, const DedupBufs& d, int64_t* n_unique, cudaStream_t s);
+// Per-row contributions <x|P|x'> psi(x')/psi(x) of the chunk from d.la_u / d.ph_u.
+int dedup_contrib(const uint64_t* xp, int64_t rows, const DedupBufs& d, const uint64_t* xsample, const float* la_x,
+                  const float* ph_x, const int64_t* seg, int64_t seg_stride, int64_t nseg, const float4* S,
+                  float2* contrib, cudaStream_t s);
+
 // Binds the model-owned cache memory (tf_step_cache_bytes(mc, b.cap) bytes) to b.
 void sampler_bind_cache(SamplerBufs& b, const ModelConst& mc, void* mem);
 int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b);

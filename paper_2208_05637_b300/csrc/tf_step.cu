@@ -1,5 +1,5 @@
-// Fused incremental step of the transformer sampler (Sec. 3.2: the conditional of position k
-// given the prefix x_<k, with the keys and values of earlier positions cached) for the d_model-64,
+// Fused incremental step of the transformer sampler (Section 4, Sampling: the conditional of
+// position k given the prefix x_<k, with the keys and values of earlier positions cached) for the d_model-64,
 // four-head models in the bf16 tensor-core forms.  One CTA takes 16 prefixes through the whole
 // step: embedding and LayerNorm, per block the QKV projection (stored into the cache slab of
 // step k), causal attention over the cached keys of the prefix's ancestors, output projection
