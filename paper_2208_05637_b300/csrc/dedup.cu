@@ -6,8 +6,8 @@
 // configuration only, so the values are those of the row-by-row evaluation bit for bit.
 //
 // The distinct keys are found with an open-addressing hash table (linear probing, 64-bit
-// atomicCAS, load factor at most 1/2) and numbered in table-slot order by a scan of the
-// occupied flags.
+// atomicCAS, load factor at most 1/2, sized for the chunk's rows) and numbered by a warp-
+// aggregated atomic counter over the occupied slots.
 #include "nqs_internal.h"
 
 namespace nqs {
@@ -35,21 +35,32 @@ __global__ void dd_insert_kernel(const uint64_t* __restrict__ xp, int64_t rows, 
     }
 }
 
-__global__ void dd_flag_kernel(const unsigned long long* __restrict__ table, int64_t n, int32_t* __restrict__ flags) {
-    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x)
-        flags[h] = table[h] != DD_EMPTY ? 1 : 0;
-}
-
-__global__ void dd_compact_kernel(const unsigned long long* __restrict__ table, int64_t n, const int64_t* __restrict__ pos,
-                                  uint64_t* __restrict__ uniq) {
-    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x)
-        if (table[h] != DD_EMPTY) uniq[pos[h]] = table[h];
+// Number the occupied slots (one atomic per warp) and list their keys.  The numbering order
+// depends on the schedule; every row's value does not.
+__global__ void dd_compact_kernel(const unsigned long long* __restrict__ table, int64_t n, int32_t* __restrict__ id,
+                                  uint64_t* __restrict__ uniq, unsigned long long* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
+        const int64_t h = base + threadIdx.x;
+        const unsigned long long key = h < n ? table[h] : DD_EMPTY;
+        const bool occ = key != DD_EMPTY;
+        const unsigned m = __ballot_sync(0xffffffffu, occ);
+        unsigned long long first = 0;
+        if (lane == 0 && m) first = atomicAdd(count, (unsigned long long)__popc(m));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (occ) {
+            const int64_t u = (int64_t)first + __popc(m & ((1u << lane) - 1u));
+            uniq[u] = key;
+            id[h] = (int32_t)u;
+        }
+    }
 }
 
 // Row i of the chunk (sample lo = the segment holding i): S(x, x') times psi(x')/psi(x), with
 // log psi(x') from the unique list; the diagonal row x' = x keeps S alone.
 __global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows, const int32_t* __restrict__ slot,
-                                  const int64_t* __restrict__ pos, const float* __restrict__ la_u,
+                                  const int32_t* __restrict__ id, const float* __restrict__ la_u,
                                   const float* __restrict__ ph_u, const uint64_t* __restrict__ xsample,
                                   const float* __restrict__ la_x, const float* __restrict__ ph_x,
                                   const int64_t* __restrict__ seg, int64_t seg_stride, int64_t nseg,
@@ -64,7 +75,7 @@ __global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows,
         const float sre = s4.x + s4.y, sim = s4.z + s4.w;
         float cr = sre, ci = sim;
         if (xp[i] != xsample[lo]) {
-            const int64_t u = pos[slot[i]];
+            const int32_t u = id[slot[i]];
             const float mag = expf(la_u[u] - la_x[lo]);
             float sn, cs;
             sincosf(ph_u[u] - ph_x[lo], &sn, &cs);
@@ -89,8 +100,8 @@ int64_t dedup_table_slots(int64_t rows_cap) {
 void dedup_layout(Carver& c, int64_t rows_cap, DedupBufs& d) {
     d.hcap = dedup_table_slots(rows_cap);
     d.table = c.take<uint64_t>(d.hcap);
-    d.flags = c.take<int32_t>(d.hcap);
-    d.pos = c.take<int64_t>(d.hcap + 1);
+    d.id = c.take<int32_t>(d.hcap);
+    d.count = c.take<unsigned long long>(1);
     d.slot = c.take<int32_t>(rows_cap);
     d.uniq = c.take<uint64_t>(rows_cap);
     d.la_u = c.take<float>(rows_cap);
@@ -100,20 +111,20 @@ void dedup_layout(Carver& c, int64_t rows_cap, DedupBufs& d) {
 int dedup_rows(const uint64_t* xp, int64_t rows, const DedupBufs& d, int64_t* n_unique, cudaStream_t s) {
     *n_unique = 0;
     if (rows <= 0) return NQS_OK;
-    if (2 * rows > d.hcap || d.hcap > (1ll << 31)) { set_error("x' dedup: table too small"); return NQS_ERR_CAPACITY; }
-    ProfScope ps("dedup", s, 0.0, (double)rows * (8 + 4) + (double)d.hcap * (8 * 3 + 4 * 2 + 8));
-    NQS_CK(cudaMemsetAsync(d.table, 0xff, (size_t)d.hcap * sizeof(uint64_t), s));
-    dd_insert_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, reinterpret_cast<unsigned long long*>(d.table), d.hcap - 1,
-                                                   d.slot);
+    const int64_t hc = dedup_table_slots(rows);          // at least twice the rows, within the layout's table
+    if (hc > d.hcap || hc > (1ll << 31)) { set_error("x' dedup: table too small"); return NQS_ERR_CAPACITY; }
+    ProfScope ps("dedup", s, 0.0, (double)rows * (8 + 4) + (double)hc * (8 * 2 + 4));
+    NQS_CK(cudaMemsetAsync(d.table, 0xff, (size_t)hc * sizeof(uint64_t), s));
+    NQS_CK(cudaMemsetAsync(d.count, 0, sizeof(unsigned long long), s));
+    dd_insert_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, reinterpret_cast<unsigned long long*>(d.table), hc - 1, d.slot);
     NQS_LAUNCHED();
-    dd_flag_kernel<<<dd_grid(d.hcap), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), d.hcap, d.flags);
+    dd_compact_kernel<<<dd_grid(hc), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), hc, d.id, d.uniq,
+                                                  d.count);
     NQS_LAUNCHED();
-    NQS_TRY(launch_scan_i32(d.flags, d.hcap, d.pos, s));
-    dd_compact_kernel<<<dd_grid(d.hcap), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), d.hcap, d.pos,
-                                                      d.uniq);
-    NQS_LAUNCHED();
-    NQS_CK(cudaMemcpyAsync(n_unique, d.pos + d.hcap, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    unsigned long long nu = 0;
+    NQS_CK(cudaMemcpyAsync(&nu, d.count, sizeof(nu), cudaMemcpyDeviceToHost, s));
     NQS_CK(cudaStreamSynchronize(s));
+    *n_unique = (int64_t)nu;
     return NQS_OK;
 }
 
@@ -122,7 +133,7 @@ int dedup_contrib(const uint64_t* xp, int64_t rows, const DedupBufs& d, const ui
                   float2* contrib, cudaStream_t s) {
     if (rows <= 0) return NQS_OK;
     ProfScope ps("dedup_contrib", s, 0.0, (double)rows * (8 + 4 + 8 + 8 + 16 + 8));
-    dd_contrib_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, d.slot, d.pos, d.la_u, d.ph_u, xsample, la_x, ph_x, seg,
+    dd_contrib_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, d.slot, d.id, d.la_u, d.ph_u, xsample, la_x, ph_x, seg,
                                                     seg_stride, nseg, S, contrib);
     NQS_LAUNCHED();
     return NQS_OK;

@@ -338,13 +338,13 @@ struct SamplerBufs {
     int32_t *ancA = nullptr, *ancB = nullptr;
     int32_t *par = nullptr, *par2 = nullptr;
 };
-// Unique flipped configurations of a local-energy chunk (dedup.cu): a hash table of hcap slots,
-// each row's slot, the slots' positions in the unique list, and log psi of the unique rows.
+// Unique flipped configurations of a local-energy chunk (dedup.cu): a hash table of up to hcap
+// slots, each row's slot, the slots' positions in the unique list, and log psi of the unique rows.
 struct DedupBufs {
     uint64_t* table = nullptr;
     int64_t hcap = 0;
-    int32_t* flags = nullptr;
-    int64_t* pos = nullptr;      // hcap + 1
+    int32_t* id = nullptr;       // per slot: position in the unique list
+    unsigned long long* count = nullptr;
     int32_t* slot = nullptr;     // per row
     uint64_t* uniq = nullptr;    // per unique row
     float *la_u = nullptr, *ph_u = nullptr;
