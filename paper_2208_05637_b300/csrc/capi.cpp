@@ -149,7 +149,7 @@ static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int
         e.contrib = c.take<float2>(e.rows_cap);
         tf_layout(c, m->mc, std::min(std::max<int64_t>(B, e.rows_cap), tf_seq_capacity(m->mc)), e.tf);
         e.dedup = m->mc.n_up + m->mc.n_dn < m->mc.n;
-        if (e.dedup) dedup_layout(c, e.rows_cap, e.dd);
+        if (e.dedup) dedup_layout(c, e.rows_cap, e.chunk, e.dd);
     }
 }
 
@@ -784,7 +784,8 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
         ProfScope ps_all("local_energy", s);
         TfWeights w;
         NQS_TRY(tf_weights(m, w, s));
-        NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, e.la, e.ph, e.tf, s));
+        // log psi of the samples: with the x' dedup from the chunk's unique list, else here
+        if (!e.dedup) NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, e.la, e.ph, e.tf, s));
         for (int64_t lo = 0; lo < B; lo += e.chunk) {
             const int64_t nb = std::min(e.chunk, B - lo);
             {
@@ -804,7 +805,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
             if (e.dedup) {
                 // log psi once per distinct x' of the chunk, then the rows' contributions
                 int64_t nu = 0;
-                NQS_TRY(dedup_rows(e.xprime, rows, e.dd, &nu, s));
+                NQS_TRY(dedup_rows(e.xprime, rows, bits + lo, nb, e.dd, &nu, s));
                 for (int64_t r0 = 0; r0 < nu; r0 += e.tf.R) {
                     const int64_t R = std::min(e.tf.R, nu - r0);
                     NQS_TRY(tf_forward(m->mc, m->d_params, w, e.dd.uniq + r0, R, m->mc.n, e.tf, s, true));
@@ -812,8 +813,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
                     ha.mode = 0; ha.la = e.dd.la_u + r0; ha.ph = e.dd.ph_u + r0;
                     NQS_TRY(tf_heads(m->mc, m->d_params, e.dd.uniq + r0, R, m->mc.n, e.tf, ha, s));
                 }
-                NQS_TRY(dedup_contrib(e.xprime, rows, e.dd, bits + lo, e.la + lo, e.ph + lo, e.off, e.ntiles, nb, e.S,
-                                      e.contrib, s));
+                NQS_TRY(dedup_contrib(e.xprime, rows, e.dd, bits + lo, e.off, e.ntiles, nb, e.S, e.contrib, s));
                 NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
                 continue;
             }

@@ -58,11 +58,11 @@ __global__ void dd_compact_kernel(const unsigned long long* __restrict__ table, 
 }
 
 // Row i of the chunk (sample lo = the segment holding i): S(x, x') times psi(x')/psi(x), with
-// log psi(x') from the unique list; the diagonal row x' = x keeps S alone.
+// log psi of x' and of the sample x from the unique list; the diagonal row x' = x keeps S alone.
 __global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows, const int32_t* __restrict__ slot,
                                   const int32_t* __restrict__ id, const float* __restrict__ la_u,
                                   const float* __restrict__ ph_u, const uint64_t* __restrict__ xsample,
-                                  const float* __restrict__ la_x, const float* __restrict__ ph_x,
+                                  const int32_t* __restrict__ sslot,
                                   const int64_t* __restrict__ seg, int64_t seg_stride, int64_t nseg,
                                   const float4* __restrict__ S, float2* __restrict__ contrib) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
@@ -75,10 +75,10 @@ __global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows,
         const float sre = s4.x + s4.y, sim = s4.z + s4.w;
         float cr = sre, ci = sim;
         if (xp[i] != xsample[lo]) {
-            const int32_t u = id[slot[i]];
-            const float mag = expf(la_u[u] - la_x[lo]);
+            const int32_t u = id[slot[i]], ux = id[sslot[lo]];
+            const float mag = expf(la_u[u] - la_u[ux]);
             float sn, cs;
-            sincosf(ph_u[u] - ph_x[lo], &sn, &cs);
+            sincosf(ph_u[u] - ph_u[ux], &sn, &cs);
             const float rr = mag * cs, ri = mag * sn;
             cr = sre * rr - sim * ri;
             ci = sre * ri + sim * rr;
@@ -97,8 +97,9 @@ int64_t dedup_table_slots(int64_t rows_cap) {
     return h;
 }
 
-void dedup_layout(Carver& c, int64_t rows_cap, DedupBufs& d) {
-    d.hcap = dedup_table_slots(rows_cap);
+void dedup_layout(Carver& c, int64_t rows_cap, int64_t chunk, DedupBufs& d) {
+    d.hcap = dedup_table_slots(rows_cap + chunk);
+    d.sslot = c.take<int32_t>(chunk);
     d.table = c.take<uint64_t>(d.hcap);
     d.id = c.take<int32_t>(d.hcap);
     d.count = c.take<unsigned long long>(1);
@@ -108,16 +109,24 @@ void dedup_layout(Carver& c, int64_t rows_cap, DedupBufs& d) {
     d.ph_u = c.take<float>(rows_cap);
 }
 
-int dedup_rows(const uint64_t* xp, int64_t rows, const DedupBufs& d, int64_t* n_unique, cudaStream_t s) {
+int dedup_rows(const uint64_t* xp, int64_t rows, const uint64_t* xs, int64_t nb, const DedupBufs& d,
+               int64_t* n_unique, cudaStream_t s) {
     *n_unique = 0;
-    if (rows <= 0) return NQS_OK;
-    const int64_t hc = dedup_table_slots(rows);          // at least twice the rows, within the layout's table
+    if (rows + nb <= 0) return NQS_OK;
+    const int64_t hc = dedup_table_slots(rows + nb);     // at least twice the keys, within the layout's table
     if (hc > d.hcap || hc > (1ll << 31)) { set_error("x' dedup: table too small"); return NQS_ERR_CAPACITY; }
-    ProfScope ps("dedup", s, 0.0, (double)rows * (8 + 4) + (double)hc * (8 * 2 + 4));
+    ProfScope ps("dedup", s, 0.0, (double)(rows + nb) * (8 + 4) + (double)hc * (8 * 2 + 4));
     NQS_CK(cudaMemsetAsync(d.table, 0xff, (size_t)hc * sizeof(uint64_t), s));
     NQS_CK(cudaMemsetAsync(d.count, 0, sizeof(unsigned long long), s));
-    dd_insert_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, reinterpret_cast<unsigned long long*>(d.table), hc - 1, d.slot);
-    NQS_LAUNCHED();
+    unsigned long long* tab = reinterpret_cast<unsigned long long*>(d.table);
+    if (rows > 0) {
+        dd_insert_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, tab, hc - 1, d.slot);
+        NQS_LAUNCHED();
+    }
+    if (nb > 0) {   // the samples themselves: their log psi comes from the same list
+        dd_insert_kernel<<<dd_grid(nb), 256, 0, s>>>(xs, nb, tab, hc - 1, d.sslot);
+        NQS_LAUNCHED();
+    }
     dd_compact_kernel<<<dd_grid(hc), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), hc, d.id, d.uniq,
                                                   d.count);
     NQS_LAUNCHED();
@@ -128,12 +137,11 @@ int dedup_rows(const uint64_t* xp, int64_t rows, const DedupBufs& d, int64_t* n_
     return NQS_OK;
 }
 
-int dedup_contrib(const uint64_t* xp, int64_t rows, const DedupBufs& d, const uint64_t* xsample, const float* la_x,
-                  const float* ph_x, const int64_t* seg, int64_t seg_stride, int64_t nseg, const float4* S,
-                  float2* contrib, cudaStream_t s) {
+int dedup_contrib(const uint64_t* xp, int64_t rows, const DedupBufs& d, const uint64_t* xsample, const int64_t* seg,
+                  int64_t seg_stride, int64_t nseg, const float4* S, float2* contrib, cudaStream_t s) {
     if (rows <= 0) return NQS_OK;
     ProfScope ps("dedup_contrib", s, 0.0, (double)rows * (8 + 4 + 8 + 8 + 16 + 8));
-    dd_contrib_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, d.slot, d.id, d.la_u, d.ph_u, xsample, la_x, ph_x, seg,
+    dd_contrib_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, d.slot, d.id, d.la_u, d.ph_u, xsample, d.sslot, seg,
                                                     seg_stride, nseg, S, contrib);
     NQS_LAUNCHED();
     return NQS_OK;

@@ -49,11 +49,6 @@ __global__ void gelu_bwd_kernel(const float* __restrict__ x, float* __restrict__
         g[i] *= gelu_grad(x[i]);
 }
 
-__global__ void round_bf16_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = __bfloat162float(__float2bfloat16_rn(src[i]));
-}
-
 // LayerNorm backward, one warp per row: out = res + dLN/dx (x, g; dy), and gx = dy * xhat for
 // the gain gradient.
 template <int DPL>
@@ -518,18 +513,29 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
     const int64_t wsz[4] = {3ll * d * d, 1ll * d * d, 4ll * d * d, 4ll * d * d};
     {
         int64_t off = 0;
+        WconvList wl{};
+        wl.f32_out = 1;
         for (int l = 0; l < L; ++l) {
             const int64_t src[4] = {mc.wqkv[l], mc.wo[l], mc.w1[l], mc.w2[l]};
+            const int cols[4] = {d, d, d, 4 * d};
             for (int q = 0; q < 4; ++q) {
                 if (bf) {
-                    round_bf16_kernel<<<gs(wsz[q]), 256, 0, s>>>(P + src[q], b.Wr + off, wsz[q]);
-                    NQS_LAUNCHED();
+                    WconvJob& J = wl.job[wl.njobs++];
+                    J.src = P + src[q];
+                    J.dst = b.Wr + off;
+                    J.start = wl.total;
+                    J.cols = cols[q];
+                    wl.total += wsz[q];
                     W[l][q] = b.Wr + off;
                     off += wsz[q];
                 } else {
                     W[l][q] = P + src[q];
                 }
             }
+        }
+        if (bf) {   // all blocks' bf16-rounded copies in one launch
+            wconv_kernel<<<gs(wl.total), 256, 0, s>>>(wl);
+            NQS_LAUNCHED();
         }
     }
 

@@ -817,5 +817,41 @@ inline cudaError_t launch_attention(const float* qkv, int64_t R, int T, int d, i
     return cudaGetLastError();
 }
 
+// Weight conversions of every block in one launch: job j takes the rows x cols fp32 matrix at
+// src and writes its bf16 values (dup: the [W | W] rows of the compensated GEMM) or, with
+// f32_out, their bf16-rounded fp32 values; jobs are laid end to end in the element index.
+struct WconvJob {
+    const float* src;
+    void* dst;
+    int64_t start;      // first element index of the job
+    int cols;
+};
+struct WconvList {
+    WconvJob job[4 * TF_MAX_LAYERS];
+    int njobs;
+    int dup, f32_out;
+    int64_t total;
+};
+
+__global__ void wconv_kernel(const __grid_constant__ WconvList L) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.total; i += (int64_t)gridDim.x * blockDim.x) {
+        int j = 0;
+        while (j + 1 < L.njobs && L.job[j + 1].start <= i) ++j;
+        const WconvJob& J = L.job[j];
+        const int64_t e = i - J.start;
+        const int64_t r = e / J.cols;
+        const int k = (int)(e - r * J.cols);
+        const __nv_bfloat16 v = __float2bfloat16_rn(J.src[e]);
+        if (L.f32_out) {
+            reinterpret_cast<float*>(J.dst)[e] = __bfloat162float(v);
+        } else {
+            __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(J.dst);
+            const int64_t kk = L.dup ? 2 * (int64_t)J.cols : J.cols;
+            dst[r * kk + k] = v;
+            if (L.dup) dst[r * kk + J.cols + k] = v;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace nqs

@@ -346,20 +346,6 @@ segment_sum_kernel(const int64_t* __restrict__ seg, int64_t seg_stride, int64_t 
     }
 }
 
-// fp32 master weights W[N][K] -> bf16 working copies; with dup the copy is [W | W] of shape
-// [N][2K], the B operand of the compensated GEMM [A_hi | A_lo] . [W | W]^T.
-__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t N,
-                               int K, int dup) {
-    const int KK = dup ? 2 * K : K;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N * K; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = i / K;
-        const int k = (int)(i % K);
-        const __nv_bfloat16 v = __float2bfloat16_rn(src[i]);
-        dst[n * KK + k] = v;
-        if (dup) dst[n * KK + K + k] = v;
-    }
-}
-
 inline int blocks_for(int64_t rows, int per) { return (int)((rows + per - 1) / per); }
 
 template <class F>
@@ -528,17 +514,26 @@ int tf_prepare_weights(const ModelConst& mc, const float* P, TfWeights& w, cudaS
     const int dup = mc.compensated ? 1 : 0;
     int64_t off = 0;
     const int64_t rows[4] = {3 * d, d, 4 * d, d}, cols[4] = {d, d, d, 4 * d};
+    WconvList wl{};
+    wl.dup = dup;
+    wl.f32_out = 0;
     for (int l = 0; l < mc.layers; ++l) {
         for (int q = 0; q < 4; ++q) {
             w.bf16_off[l][q] = off;
             const int64_t n = rows[q] * cols[q];
-            const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
-            to_bf16_kernel<<<grid, 256, 0, s>>>(P + w.fp32_off[l][q], reinterpret_cast<__nv_bfloat16*>(w.bf16) + off,
-                                                rows[q], (int)cols[q], dup);
-            NQS_LAUNCHED();
+            WconvJob& J = wl.job[wl.njobs++];
+            J.src = P + w.fp32_off[l][q];
+            J.dst = reinterpret_cast<__nv_bfloat16*>(w.bf16) + off;
+            J.start = wl.total;
+            J.cols = (int)cols[q];
+            wl.total += n;
             off += ((n << dup) + 127) & ~int64_t(127);   // 256-byte aligned matrices
         }
     }
+    // all blocks' matrices in one launch
+    const int grid = (int)std::min<int64_t>((wl.total + 255) / 256, (int64_t)num_sms() * 8);
+    wconv_kernel<<<grid, 256, 0, s>>>(wl);
+    NQS_LAUNCHED();
     return NQS_OK;
 }
 
