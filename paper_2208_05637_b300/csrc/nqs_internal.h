@@ -338,6 +338,17 @@ struct SamplerBufs {
     int32_t *ancA = nullptr, *ancB = nullptr;
     int32_t *par = nullptr, *par2 = nullptr;
 };
+// Tensor-core GEMMs of the bf16 models' backward (tc_bwd.cu): NT recompute (W [N][K], bias,
+// residual), NN input gradients (W [K][N]), TN weight-gradient split-K partials in the layout of
+// outer_final_kernel ([z][out][in] then [z][out] column sums when with_bias).
+bool tc_bwd_ok(const void* A, int64_t lda, const void* B, int64_t ldb);
+int tc_bwd_gemm_nt(const float* A, int64_t lda, const float* W, int64_t ldw, const float* bias, float* C, int64_t ldc,
+                   int64_t M, int N, int K, bool resid, cudaStream_t s);
+int tc_bwd_gemm_nn(const float* A, int64_t lda, const float* W, int64_t ldw, float* C, int64_t ldc, int64_t M, int N,
+                   int K, cudaStream_t s);
+int tc_bwd_outer_partial(const float* delta, int64_t ld_d, const float* act, int64_t ld_a, int64_t rows, int out_dim,
+                         int in_dim, int64_t nsplit, int64_t per, bool with_bias, float* part, cudaStream_t s);
+
 // Unique flipped configurations of a local-energy chunk (dedup.cu): a hash table of up to hcap
 // slots, each row's slot, the slots' positions in the unique list, and log psi of the unique rows.
 struct DedupBufs {

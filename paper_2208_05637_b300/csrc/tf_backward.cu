@@ -539,9 +539,15 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         }
     }
 
+    // bf16 models: the GEMMs on the tensor cores (split fp32 operands); fp32 models: SIMT
+    const bool tc = bf;
     auto gemm_nt = [&](auto* A, const float* Wm, const float* bias, float* C, int64_t M, int N, int K,
                        int epi) -> int {
         using TA = std::remove_cv_t<std::remove_pointer_t<decltype(A)>>;
+        if constexpr (std::is_same<TA, float>::value) {
+            if (tc && tc_bwd_ok(A, K, Wm, K))
+                return tc_bwd_gemm_nt(A, K, Wm, K, bias, C, N, M, N, K, epi == TF_EPI_RESID, s);
+        }
         dim3 grid((unsigned)((N + SG_BN - 1) / SG_BN), (unsigned)((M + SG_BM - 1) / SG_BM));
         if (epi == TF_EPI_STORE) sgemm_kernel<TA, false, TF_EPI_STORE, float><<<grid, 256, 0, s>>>(A, Wm, bias, C, M, N, K);
         else sgemm_kernel<TA, false, TF_EPI_RESID, float><<<grid, 256, 0, s>>>(A, Wm, bias, C, M, N, K);
@@ -549,6 +555,7 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         return NQS_OK;
     };
     auto gemm_nn = [&](const float* A, const float* Wm, float* C, int64_t M, int N, int K) -> int {
+        if (tc && N % 4 == 0 && tc_bwd_ok(A, K, Wm, N)) return tc_bwd_gemm_nn(A, K, Wm, N, C, N, M, N, K, s);
         dim3 grid((unsigned)((N + SG_BN - 1) / SG_BN), (unsigned)((M + SG_BM - 1) / SG_BM));
         sgemm_kernel<float, true, TF_EPI_STORE, float><<<grid, 256, 0, s>>>(A, Wm, nullptr, C, M, N, K);
         NQS_LAUNCHED();
@@ -571,9 +578,13 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         const int64_t stride = (int64_t)out_dim * in_dim + out_dim;
         const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(b.nsplit, b.part_elems / stride));
         const int64_t per = (M + ns - 1) / ns;
-        dim3 grid((unsigned)((in_dim + OP_B - 1) / OP_B), (unsigned)((out_dim + OP_B - 1) / OP_B), (unsigned)ns);
-        outer_partial_kernel<<<grid, 256, 0, s>>>(delta, ld_d, act, ld_a, M, out_dim, in_dim, per, b.part);
-        NQS_LAUNCHED();
+        if (tc && out_dim >= 64 && out_dim % 4 == 0 && in_dim % 4 == 0 && tc_bwd_ok(delta, ld_d, act, ld_a)) {
+            NQS_TRY(tc_bwd_outer_partial(delta, ld_d, act, ld_a, M, out_dim, in_dim, ns, per, db != nullptr, b.part, s));
+        } else {
+            dim3 grid((unsigned)((in_dim + OP_B - 1) / OP_B), (unsigned)((out_dim + OP_B - 1) / OP_B), (unsigned)ns);
+            outer_partial_kernel<<<grid, 256, 0, s>>>(delta, ld_d, act, ld_a, M, out_dim, in_dim, per, b.part);
+            NQS_LAUNCHED();
+        }
         outer_final_kernel<<<gs(stride), 256, 0, s>>>(b.part, (int)ns, out_dim, in_dim, dW, db);
         NQS_LAUNCHED();
         return NQS_OK;
