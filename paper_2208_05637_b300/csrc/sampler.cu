@@ -396,11 +396,14 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
     }
     __syncthreads();
     if (anc_new) {
-        // one warp per prefix, lanes over the steps 0..k
-        const int lane = threadIdx.x & 31;
-        for (int64_t i = threadIdx.x >> 5; i < Un; i += BK_T / 32) {
+        // every (prefix, step 0..k) entry by its own thread iteration: independent loads in flight
+        const int kk = k + 1;
+        const int tot = (int)Un * kk;                // Un <= SAMPLER_GRAPH_MAX_CAP, k < 64
+#pragma unroll 4
+        for (int e = threadIdx.x; e < tot; e += BK_T) {
+            const int i = e / kk, j = e - i * kk;
             const int32_t p = par[i];
-            for (int j = lane; j <= k; j += 32) anc_new[i * n + j] = j < k ? anc_old[(int64_t)p * n + j] : p;
+            anc_new[(int64_t)i * n + j] = j < k ? anc_old[(int64_t)p * n + j] : p;
         }
     }
     if (threadIdx.x == 0) *Udev = Un;
