@@ -34,6 +34,9 @@ FFMA_PER_SM_PER_CLK = 128      # fp32 lanes per SM (sm_100 family)
 # the committed ncu capture named beside it (traffic = ratio x the scope's bytes per launch); an
 # entry is removed once its kernel changes.
 NCU_TRAFFIC = {
+    ("n2_like_20q_tf64x2", "tf_qkv_attention"): (0.46, "profiles/qkv_attention_tf20q_bf16_ncu.md"),
+    ("n2_like_20q_tf64x2", "tf_resid_ln"): (0.74, "profiles/resid_ln_tf20q_bf16_ncu.md"),
+    ("n2_like_20q_tf64x2", "tf_mlp"): (0.85, "profiles/tc_mlp_tf20q_bf16_ncu.md"),
     ("n2_like_20q_tf64x2", "tf_layernorm"): (0.74, "profiles/layernorm_tf20q_bf16_ncu.md"),
 }
 
