@@ -14,7 +14,9 @@ namespace nqs {
 namespace {
 
 constexpr int TB_M = 64, TB_N = 64, TB_K = 32;   // CTA tile, k-stage
-constexpr int TB_LD = TB_M + 4;                  // fp32 smem row stride ([k][m] and [k][n] tiles)
+constexpr int TB_LD = TB_M + 4;                  // fp32 smem row stride of [k][m] / [k][n] tiles
+constexpr int TB_LDK = TB_K + 8;                 // fp32 smem row stride of [m][k] / [n][k] tiles (float2 reads conflict-free)
+constexpr int TB_TILE = TB_K * TB_LD > TB_M * TB_LDK ? TB_K * TB_LD : TB_M * TB_LDK;
 constexpr int TB_THREADS = 128;                  // 2 x 2 warps of 32 x 32 outputs
 
 __device__ __forceinline__ void tb_mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
@@ -35,8 +37,9 @@ __device__ __forceinline__ void tb_split(float x, float y, uint32_t& hi, uint32_
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// One k-stage's fp32 tile into shared memory as [k][m]: from global [M][K] (transposed on the
-// way, lanes on consecutive m) or from global [K][M] (float4 rows).  Out-of-range elements are 0.
+// One k-stage's fp32 tile into shared memory in the layout of global memory: [k][m] rows (stride
+// TB_LD) from global [K][M], or [m][k] rows (stride TB_LDK) from global [M][K]; float4 loads with
+// consecutive lanes on consecutive 16-byte pieces of a row.  Out-of-range elements are 0.
 template <bool KM>
 struct TbLoader {
     float4 r[4];
@@ -51,7 +54,7 @@ struct TbLoader {
                 r[i] = (gk < klim && gm < mlim) ? __ldg(reinterpret_cast<const float4*>(g + gk * ld + gm))
                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
             } else {    // rows m (64) x 8 float4 of k
-                const int m = f & 63, kq = f >> 6;
+                const int m = f >> 3, kq = f & 7;
                 const int64_t gm = m0 + m, gk = k0 + 4 * kq;
                 r[i] = (gm < mlim && gk < klim) ? __ldg(reinterpret_cast<const float4*>(g + gm * ld + gk))
                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -66,15 +69,27 @@ struct TbLoader {
                 const int k = f >> 4, mq = f & 15;
                 *reinterpret_cast<float4*>(s + k * TB_LD + 4 * mq) = r[i];
             } else {
-                const int m = f & 63, kq = f >> 6;
-                s[(4 * kq + 0) * TB_LD + m] = r[i].x;
-                s[(4 * kq + 1) * TB_LD + m] = r[i].y;
-                s[(4 * kq + 2) * TB_LD + m] = r[i].z;
-                s[(4 * kq + 3) * TB_LD + m] = r[i].w;
+                const int m = f >> 3, kq = f & 7;
+                *reinterpret_cast<float4*>(s + m * TB_LDK + 4 * kq) = r[i];
             }
         }
     }
 };
+
+// Element (m, k) of a staged tile and the bf16 hi | lo pair of elements (m, k), (m, k + 1).
+template <bool KM>
+__device__ __forceinline__ float tb_at(const float* s, int m, int k) {
+    return KM ? s[k * TB_LD + m] : s[m * TB_LDK + k];
+}
+template <bool KM>
+__device__ __forceinline__ void tb_pair(const float* s, int m, int k, uint32_t& hi, uint32_t& lo) {
+    if (KM) {
+        tb_split(s[k * TB_LD + m], s[(k + 1) * TB_LD + m], hi, lo);
+    } else {
+        const float2 v = *reinterpret_cast<const float2*>(s + m * TB_LDK + k);
+        tb_split(v.x, v.y, hi, lo);
+    }
+}
 
 // EPI: 0 store (C = acc + bias), 1 residual (C += acc + bias), 2 split-K partial (TN)
 template <bool A_KM, bool B_KN, bool B_EXACT, int EPI>
@@ -82,8 +97,8 @@ __global__ void __launch_bounds__(TB_THREADS)
 tb_gemm_kernel(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
                const float* __restrict__ bias, float* __restrict__ C, int64_t ldc, int64_t M, int N, int64_t K,
                int64_t k_split, float* __restrict__ part, int with_colsum) {
-    __shared__ __align__(16) float sA[TB_K * TB_LD];
-    __shared__ __align__(16) float sB[TB_K * TB_LD];
+    __shared__ __align__(16) float sA[TB_TILE];
+    __shared__ __align__(16) float sB[TB_TILE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, q = lane & 3;
     const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
@@ -112,25 +127,25 @@ tb_gemm_kernel(const float* __restrict__ A, int64_t lda, const float* __restrict
         }
         if (EPI == 2 && with_colsum && blockIdx.x == 0 && threadIdx.x < TB_M) {
 #pragma unroll 8
-            for (int k = 0; k < TB_K; ++k) csum += sA[k * TB_LD + threadIdx.x];
+            for (int k = 0; k < TB_K; ++k) csum += tb_at<A_KM>(sA, threadIdx.x, k);
         }
 #pragma unroll
         for (int ks = 0; ks < TB_K; ks += 16) {
             uint32_t bh[4][2], bl[4][2];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float* bp = sB + (ks + 2 * q) * TB_LD + wn + 8 * j + g;
-                tb_split(bp[0], bp[TB_LD], bh[j][0], bl[j][0]);
-                tb_split(bp[8 * TB_LD], bp[9 * TB_LD], bh[j][1], bl[j][1]);
+                const int nn = wn + 8 * j + g;
+                tb_pair<B_KN>(sB, nn, ks + 2 * q, bh[j][0], bl[j][0]);
+                tb_pair<B_KN>(sB, nn, ks + 2 * q + 8, bh[j][1], bl[j][1]);
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const float* ap = sA + (ks + 2 * q) * TB_LD + wm + 16 * i + g;
+                const int mm = wm + 16 * i + g;
                 uint32_t ah[4], al[4];
-                tb_split(ap[0], ap[TB_LD], ah[0], al[0]);                       // row g, k 2q..
-                tb_split(ap[8], ap[TB_LD + 8], ah[1], al[1]);                   // row g + 8
-                tb_split(ap[8 * TB_LD], ap[9 * TB_LD], ah[2], al[2]);           // row g, k 2q + 8..
-                tb_split(ap[8 * TB_LD + 8], ap[9 * TB_LD + 8], ah[3], al[3]);   // row g + 8
+                tb_pair<A_KM>(sA, mm, ks + 2 * q, ah[0], al[0]);            // row g, k 2q..
+                tb_pair<A_KM>(sA, mm + 8, ks + 2 * q, ah[1], al[1]);        // row g + 8
+                tb_pair<A_KM>(sA, mm, ks + 2 * q + 8, ah[2], al[2]);        // row g, k 2q + 8..
+                tb_pair<A_KM>(sA, mm + 8, ks + 2 * q + 8, ah[3], al[3]);    // row g + 8
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     tb_mma(acc[i][j], ah[0], ah[1], ah[2], ah[3], bh[j][0], bh[j][1]);
