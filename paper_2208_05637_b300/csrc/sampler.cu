@@ -37,11 +37,15 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
 
 // U[0] = unique count, U[2] = eviction flag, U[3] = seed (read by the draws, so that a
 // captured graph of the steps can be replayed with a new seed)
-__global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_samples, uint64_t seed) {
+__global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_samples, uint64_t seed,
+                            int64_t* start, int64_t* n1) {
     bits[0] = 0;
     cnt[0] = n_samples;
     U[0] = 1;
     U[3] = (int64_t)seed;
+    start[0] = 0;          // the first step's draw ranges and ones counters (one-CTA bookkeeping)
+    start[1] = n_samples;
+    n1[0] = 0;
 }
 
 // ones per parent: warp-aggregated integer atomics (exact, order-independent)
@@ -304,24 +308,6 @@ __device__ int64_t bk_block_scan(int64_t v, int64_t* warp_sums, int64_t* total) 
     return r;
 }
 
-// start = exclusive scan of the counts (start[U] = their sum); n1 = 0.
-__global__ void __launch_bounds__(BK_T)
-bk_prep_kernel(const int64_t* __restrict__ cnt, const int64_t* __restrict__ Udev, int64_t* __restrict__ start,
-               int64_t* __restrict__ n1) {
-    __shared__ int64_t warp_sums[32];
-    __shared__ int64_t tot;
-    const int64_t U = *Udev;
-    int64_t carry = 0;
-    for (int64_t base = 0; base < U; base += BK_T) {
-        const int64_t i = base + threadIdx.x;
-        const int64_t v = i < U ? cnt[i] : 0;
-        const int64_t ex = bk_block_scan(v, warp_sums, &tot) + carry;
-        if (i < U) { start[i] = ex; n1[i] = 0; }
-        carry += tot;
-    }
-    if (threadIdx.x == 0) start[U] = carry;
-}
-
 // After the draws: children positions (scans of the two flag arrays), merge into the spare
 // buffers (nb, nc, npar), eviction or copy back into (cb, cc, par), the unique count, and the
 // ancestor table of the next step (when the transformer cache is bound).
@@ -336,12 +322,12 @@ __device__ __forceinline__ int upper_s(const uint64_t* sbits, int U, uint64_t or
 }
 
 __global__ void __launch_bounds__(BK_T)
-bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int64_t* __restrict__ n1,
+bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, int64_t* __restrict__ n1,
                  int64_t* __restrict__ pos0, int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
                  uint64_t qbit, uint64_t* __restrict__ nb, int64_t* __restrict__ nc,
                  int32_t* __restrict__ par, int32_t* __restrict__ npar, int64_t max_unique,
                  const int32_t* __restrict__ anc_old, int32_t* __restrict__ anc_new, int n, int k,
-                 int64_t cap) {
+                 int64_t cap, int64_t* __restrict__ start_next) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t tot0, tot1;
     extern __shared__ uint64_t sbits[];              // the U parent bit strings, then cap merged counts
@@ -405,6 +391,20 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, const int6
             const int32_t p = par[i];
             anc_new[(int64_t)i * n + j] = j < k ? anc_old[(int64_t)p * n + j] : p;
         }
+    }
+    if (start_next) {
+        // the next step's draw ranges (exclusive scan of the surviving counts, start[U] = their
+        // sum) and zeroed ones counters
+        __syncthreads();
+        int64_t carry = 0;
+        for (int64_t base = 0; base < Un; base += BK_T) {
+            const int64_t i = base + threadIdx.x;
+            const int64_t v = i < Un ? cc[i] : 0;
+            const int64_t ex = bk_block_scan(v, warp_sums, &tot0) + carry;
+            if (i < Un) { start_next[i] = ex; n1[i] = 0; }
+            carry += tot0;
+        }
+        if (threadIdx.x == 0) start_next[Un] = carry;
     }
     if (threadIdx.x == 0) *Udev = Un;
 }
@@ -511,7 +511,7 @@ void sampler_bind_cache(SamplerBufs& b, const ModelConst& mc, void* mem) {
 }
 
 int sampler_init(SamplerBufs& b, int64_t n_samples, uint64_t seed, cudaStream_t s) {
-    init_kernel<<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples, seed);
+    init_kernel<<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples, seed, b.start, b.n1);
     NQS_LAUNCHED();
     return NQS_OK;
 }
@@ -542,15 +542,15 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, fixed_rows, s));
         else NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr, tr, s));
         if (one_cta) {
-            // three launches: scan + zero, draws, then flags / merge / eviction / ancestors
-            bk_prep_kernel<<<1, BK_T, 0, s>>>(cc, b.U, b.start, b.n1);
-            NQS_LAUNCHED();
+            // two launches: draws, then flags / merge / eviction / ancestors and the next step's
+            // draw ranges (the first step's come from init_kernel)
             draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
             NQS_LAUNCHED();
             const bool anc = b.kv && k + 1 < mc.n;
             bk_finish_kernel<<<1, BK_T, b.cap * BK_SMEM_PER_ENTRY, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
                                                 b.kv ? b.par : nullptr, b.kv ? b.par2 : nullptr, max_unique,
-                                                anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k, b.cap);
+                                                anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k, b.cap,
+                                                b.start);
             NQS_LAUNCHED();
             if (anc) std::swap(b.ancA, b.ancB);
             continue;
