@@ -798,14 +798,14 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
                 NQS_TRY(launch_sweep_emit(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, m->mc.compensated,
                                           bits + lo, nb, e.off, e.xprime, e.S, s));
             }
-            int64_t rows = 0;
-            NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            NQS_CK(cudaStreamSynchronize(s));
-            if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
             if (e.dedup) {
-                // log psi once per distinct x' of the chunk, then the rows' contributions
+                // log psi once per distinct x' of the chunk, then the rows' contributions; the row
+                // count stays on the device (bounded by the chunk's feasible groups)
+                const int64_t* rows_dev = e.off + nb * e.ntiles;
+                const int64_t rows_max = nb * (e.rows_cap / e.chunk);
                 int64_t nu = 0;
-                NQS_TRY(dedup_rows(e.xprime, rows, bits + lo, nb, e.dd, &nu, s));
+                NQS_TRY(dedup_rows(e.xprime, rows_dev, rows_max, bits + lo, nb, e.dd, &nu, s));
+                if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
                 for (int64_t r0 = 0; r0 < nu; r0 += e.tf.R) {
                     const int64_t R = std::min(e.tf.R, nu - r0);
                     NQS_TRY(tf_forward(m->mc, m->d_params, w, e.dd.uniq + r0, R, m->mc.n, e.tf, s, true));
@@ -813,10 +813,15 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
                     ha.mode = 0; ha.la = e.dd.la_u + r0; ha.ph = e.dd.ph_u + r0;
                     NQS_TRY(tf_heads(m->mc, m->d_params, e.dd.uniq + r0, R, m->mc.n, e.tf, ha, s));
                 }
-                NQS_TRY(dedup_contrib(e.xprime, rows, e.dd, bits + lo, e.off, e.ntiles, nb, e.S, e.contrib, s));
+                NQS_TRY(dedup_contrib(e.xprime, rows_dev, rows_max, e.dd, bits + lo, e.off, e.ntiles, nb, e.S, e.contrib,
+                                      s));
                 NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
                 continue;
             }
+            int64_t rows = 0;
+            NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+            if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
             for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
                 const int64_t R = std::min(e.tf.R, rows - r0);
                 NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s, true));

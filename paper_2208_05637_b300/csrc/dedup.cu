@@ -21,8 +21,9 @@ __device__ __forceinline__ uint64_t dd_mix(uint64_t z) {   // SplitMix64 finalis
     return z ^ (z >> 31);
 }
 
-__global__ void dd_insert_kernel(const uint64_t* __restrict__ xp, int64_t rows, unsigned long long* table,
-                                 int64_t mask, int32_t* __restrict__ slot) {
+__global__ void dd_insert_kernel(const uint64_t* __restrict__ xp, int64_t rows_max, const int64_t* __restrict__ rows_dev,
+                                 unsigned long long* table, int64_t mask, int32_t* __restrict__ slot) {
+    const int64_t rows = rows_dev ? min(*rows_dev, rows_max) : rows_max;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = xp[i];
         int64_t h = (int64_t)(dd_mix(key) & (uint64_t)mask);
@@ -59,12 +60,14 @@ __global__ void dd_compact_kernel(const unsigned long long* __restrict__ table, 
 
 // Row i of the chunk (sample lo = the segment holding i): S(x, x') times psi(x')/psi(x), with
 // log psi of x' and of the sample x from the unique list; the diagonal row x' = x keeps S alone.
-__global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows, const int32_t* __restrict__ slot,
+__global__ void dd_contrib_kernel(const uint64_t* __restrict__ xp, int64_t rows_max, const int64_t* __restrict__ rows_dev,
+                                  const int32_t* __restrict__ slot,
                                   const int32_t* __restrict__ id, const float* __restrict__ la_u,
                                   const float* __restrict__ ph_u, const uint64_t* __restrict__ xsample,
                                   const int32_t* __restrict__ sslot,
                                   const int64_t* __restrict__ seg, int64_t seg_stride, int64_t nseg,
                                   const float4* __restrict__ S, float2* __restrict__ contrib) {
+    const int64_t rows = min(*rows_dev, rows_max);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = nseg - 1;
         while (lo < hi) {
@@ -109,22 +112,22 @@ void dedup_layout(Carver& c, int64_t rows_cap, int64_t chunk, DedupBufs& d) {
     d.ph_u = c.take<float>(rows_cap);
 }
 
-int dedup_rows(const uint64_t* xp, int64_t rows, const uint64_t* xs, int64_t nb, const DedupBufs& d,
-               int64_t* n_unique, cudaStream_t s) {
+int dedup_rows(const uint64_t* xp, const int64_t* rows_dev, int64_t rows_max, const uint64_t* xs, int64_t nb,
+               const DedupBufs& d, int64_t* n_unique, cudaStream_t s) {
     *n_unique = 0;
-    if (rows + nb <= 0) return NQS_OK;
-    const int64_t hc = dedup_table_slots(rows + nb);     // at least twice the keys, within the layout's table
+    if (rows_max + nb <= 0) return NQS_OK;
+    const int64_t hc = dedup_table_slots(rows_max + nb);  // at least twice the keys, within the layout's table
     if (hc > d.hcap || hc > (1ll << 31)) { set_error("x' dedup: table too small"); return NQS_ERR_CAPACITY; }
-    ProfScope ps("dedup", s, 0.0, (double)(rows + nb) * (8 + 4) + (double)hc * (8 * 2 + 4));
+    ProfScope ps("dedup", s, 0.0, (double)(rows_max + nb) * (8 + 4) + (double)hc * (8 * 2 + 4));
     NQS_CK(cudaMemsetAsync(d.table, 0xff, (size_t)hc * sizeof(uint64_t), s));
     NQS_CK(cudaMemsetAsync(d.count, 0, sizeof(unsigned long long), s));
     unsigned long long* tab = reinterpret_cast<unsigned long long*>(d.table);
-    if (rows > 0) {
-        dd_insert_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, tab, hc - 1, d.slot);
+    if (rows_max > 0) {   // the row count stays on the device (no host round trip before the table)
+        dd_insert_kernel<<<dd_grid(rows_max), 256, 0, s>>>(xp, rows_max, rows_dev, tab, hc - 1, d.slot);
         NQS_LAUNCHED();
     }
     if (nb > 0) {   // the samples themselves: their log psi comes from the same list
-        dd_insert_kernel<<<dd_grid(nb), 256, 0, s>>>(xs, nb, tab, hc - 1, d.sslot);
+        dd_insert_kernel<<<dd_grid(nb), 256, 0, s>>>(xs, nb, nullptr, tab, hc - 1, d.sslot);
         NQS_LAUNCHED();
     }
     dd_compact_kernel<<<dd_grid(hc), 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d.table), hc, d.id, d.uniq,
@@ -137,12 +140,13 @@ int dedup_rows(const uint64_t* xp, int64_t rows, const uint64_t* xs, int64_t nb,
     return NQS_OK;
 }
 
-int dedup_contrib(const uint64_t* xp, int64_t rows, const DedupBufs& d, const uint64_t* xsample, const int64_t* seg,
-                  int64_t seg_stride, int64_t nseg, const float4* S, float2* contrib, cudaStream_t s) {
-    if (rows <= 0) return NQS_OK;
-    ProfScope ps("dedup_contrib", s, 0.0, (double)rows * (8 + 4 + 8 + 8 + 16 + 8));
-    dd_contrib_kernel<<<dd_grid(rows), 256, 0, s>>>(xp, rows, d.slot, d.id, d.la_u, d.ph_u, xsample, d.sslot, seg,
-                                                    seg_stride, nseg, S, contrib);
+int dedup_contrib(const uint64_t* xp, const int64_t* rows_dev, int64_t rows_max, const DedupBufs& d,
+                  const uint64_t* xsample, const int64_t* seg, int64_t seg_stride, int64_t nseg, const float4* S,
+                  float2* contrib, cudaStream_t s) {
+    if (rows_max <= 0) return NQS_OK;
+    ProfScope ps("dedup_contrib", s, 0.0, (double)rows_max * (8 + 4 + 8 + 8 + 16 + 8));
+    dd_contrib_kernel<<<dd_grid(rows_max), 256, 0, s>>>(xp, rows_max, rows_dev, d.slot, d.id, d.la_u, d.ph_u, xsample,
+                                                        d.sslot, seg, seg_stride, nseg, S, contrib);
     NQS_LAUNCHED();
     return NQS_OK;
 }
