@@ -13,6 +13,8 @@
 
 #include "tf_common.cuh"
 
+#include <mutex>
+
 namespace nqs {
 namespace {
 
@@ -426,12 +428,18 @@ struct BwdBufs {
     void** A2;       // L
     float** MPRE;    // L x [M 4d]
     void** MM;       // L x [M 4d] (T_ACT)
-    float *dH, *dHmid, *dS, *dBig, *dQKV, *GX, *HF, *DL, *DPH, *part, *Wr;
+    // gradients, one buffer per block and use, so that the weight-gradient reductions (a side
+    // stream) only read buffers that the main chain never writes again within a chunk
+    float* dH[TF_MAX_LAYERS + 1];                  // w.r.t. Hin[l]
+    float *dHmid[TF_MAX_LAYERS], *dBig[TF_MAX_LAYERS], *dQKV[TF_MAX_LAYERS];
+    float *dSa[TF_MAX_LAYERS], *dSb[TF_MAX_LAYERS], *dSc[TF_MAX_LAYERS];   // into LN2, attention, LN1
+    float *GXa[TF_MAX_LAYERS], *GXc[TF_MAX_LAYERS];                        // LN2, LN1 gain terms
+    float *dSh, *GXh, *HF, *DL, *DPH, *part, *part_e, *Wr;
 };
 
 int64_t bwd_per_seq_floats(const ModelConst& mc) {
     const int64_t n = mc.n, d = mc.hidden, L = mc.layers;
-    return n * (d * (L + 1) + L * (d + 3 * d + d + d + 4 * d + 4 * d + d) + 3 * d + 4 * d + 3 * d + 2 * d + 1) + 4;
+    return n * (d * (L + 1) + L * (d + 3 * d + d + d + 4 * d + 4 * d + d) + d * (L + 1) + L * 13 * d + 3 * d + 1) + 4;
 }
 
 void bwd_layout(Carver& c, const ModelConst& mc, int64_t R, BwdBufs& b, float** ptrs, void** vptrs) {
@@ -449,12 +457,19 @@ void bwd_layout(Carver& c, const ModelConst& mc, int64_t R, BwdBufs& b, float** 
         b.MPRE[l] = c.take<float>(M * 4 * d);
         b.MM[l] = c.take<float>(M * 4 * d);
     }
-    b.dH = c.take<float>(M * d);
-    b.dHmid = c.take<float>(M * d);
-    b.dS = c.take<float>(M * d);
-    b.dBig = c.take<float>(M * 4 * d);
-    b.dQKV = c.take<float>(M * 3 * d);
-    b.GX = c.take<float>(M * d);
+    for (int l = 0; l <= L; ++l) b.dH[l] = c.take<float>(M * d);
+    for (int l = 0; l < L; ++l) {
+        b.dHmid[l] = c.take<float>(M * d);
+        b.dBig[l] = c.take<float>(M * 4 * d);
+        b.dQKV[l] = c.take<float>(M * 3 * d);
+        b.dSa[l] = c.take<float>(M * d);
+        b.dSb[l] = c.take<float>(M * d);
+        b.dSc[l] = c.take<float>(M * d);
+        b.GXa[l] = c.take<float>(M * d);
+        b.GXc[l] = c.take<float>(M * d);
+    }
+    b.dSh = c.take<float>(M * d);
+    b.GXh = c.take<float>(M * d);
     b.HF = c.take<float>(M * d);
     b.DL = c.take<float>(M);
     b.DPH = c.take<float>(R * 4);
@@ -463,6 +478,7 @@ void bwd_layout(Carver& c, const ModelConst& mc, int64_t R, BwdBufs& b, float** 
     b.part_elems = std::max<int64_t>(b.part_elems, 2 * ((M + CS_ROWS - 1) / CS_ROWS) * d);
     b.part_elems = std::max<int64_t>(b.part_elems, ((R + EB_ROWS - 1) / EB_ROWS) * n * 2 * d);
     b.part = c.take<float>(b.part_elems);
+    b.part_e = c.take<float>(((R + EB_ROWS - 1) / EB_ROWS) * n * 2 * d);
     b.Wr = c.take<float>(12 * d * d * L);
 }
 
@@ -493,6 +509,29 @@ int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int6
     if (mc.precision != NQS_PREC_BF16) return tf_backward_mode<ACT_F32>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
     if (mc.compensated) return tf_backward_mode<ACT_F32_Q2>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
     return tf_backward_mode<ACT_F32_Q1>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
+}
+
+// The weight-gradient reductions run on a library-owned side stream, ordered after the main
+// chain's producers by events (one stream and two events per device, created on first use).
+struct BwdSide {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+static int bwd_side(BwdSide*& out) {
+    static BwdSide sides[16];
+    static std::mutex mu;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 16) { set_error("backward side stream: device index out of range"); return NQS_ERR_UNSUPPORTED; }
+    std::lock_guard<std::mutex> lk(mu);
+    BwdSide& b = sides[dev];
+    if (!b.st) {
+        NQS_CK(cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
+        NQS_CK(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+        NQS_CK(cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming));
+    }
+    out = &b;
+    return NQS_OK;
 }
 
 // MODE: how the recomputed forward stores GEMM input activations (fp32 values equal to the
@@ -561,14 +600,29 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         NQS_LAUNCHED();
         return NQS_OK;
     };
+    // the gradient reductions below run on the side stream ss, each after a fork() that orders it
+    // behind everything the main stream has issued so far; b.part is theirs alone
+    BwdSide* side = nullptr;
+    NQS_TRY(bwd_side(side));
+    cudaStream_t ss = side->st;
+    auto fork = [&]() -> int {
+        NQS_CK(cudaEventRecord(side->fork, s));
+        NQS_CK(cudaStreamWaitEvent(ss, side->fork, 0));
+        return NQS_OK;
+    };
+    auto join = [&]() -> int {
+        NQS_CK(cudaEventRecord(side->join, ss));
+        NQS_CK(cudaStreamWaitEvent(s, side->join, 0));
+        return NQS_OK;
+    };
     // column sums of X0 (and X1) into out0 (and out1)
     auto colsum = [&](const float* X0, const float* X1, int64_t ld, int64_t M, int ncols, float* out0,
                       float* out1) -> int {
         const int nch = (int)((M + CS_ROWS - 1) / CS_ROWS);
         const int nmat = X1 ? 2 : 1;
-        colsum_partial_kernel<<<dim3((ncols + 31) / 32, nch, nmat), dim3(32, 8), 0, s>>>(X0, X1, ld, M, ncols, b.part);
+        colsum_partial_kernel<<<dim3((ncols + 31) / 32, nch, nmat), dim3(32, 8), 0, ss>>>(X0, X1, ld, M, ncols, b.part);
         NQS_LAUNCHED();
-        colsum_final_kernel<<<(nmat * ncols + 7) / 8, 256, 0, s>>>(b.part, nch, ncols, nmat, out0, out1);
+        colsum_final_kernel<<<(nmat * ncols + 7) / 8, 256, 0, ss>>>(b.part, nch, ncols, nmat, out0, out1);
         NQS_LAUNCHED();
         return NQS_OK;
     };
@@ -579,13 +633,13 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(b.nsplit, b.part_elems / stride));
         const int64_t per = (M + ns - 1) / ns;
         if (tc && out_dim >= 64 && out_dim % 4 == 0 && in_dim % 4 == 0 && tc_bwd_ok(delta, ld_d, act, ld_a)) {
-            NQS_TRY(tc_bwd_outer_partial(delta, ld_d, act, ld_a, M, out_dim, in_dim, ns, per, db != nullptr, b.part, s));
+            NQS_TRY(tc_bwd_outer_partial(delta, ld_d, act, ld_a, M, out_dim, in_dim, ns, per, db != nullptr, b.part, ss));
         } else {
             dim3 grid((unsigned)((in_dim + OP_B - 1) / OP_B), (unsigned)((out_dim + OP_B - 1) / OP_B), (unsigned)ns);
-            outer_partial_kernel<<<grid, 256, 0, s>>>(delta, ld_d, act, ld_a, M, out_dim, in_dim, per, b.part);
+            outer_partial_kernel<<<grid, 256, 0, ss>>>(delta, ld_d, act, ld_a, M, out_dim, in_dim, per, b.part);
             NQS_LAUNCHED();
         }
-        outer_final_kernel<<<gs(stride), 256, 0, s>>>(b.part, (int)ns, out_dim, in_dim, dW, db);
+        outer_final_kernel<<<gs(stride), 256, 0, ss>>>(b.part, (int)ns, out_dim, in_dim, dW, db);
         NQS_LAUNCHED();
         return NQS_OK;
     };
@@ -629,48 +683,59 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
             // ---- heads and final LayerNorm
             auto ps_heads = std::make_unique<ProfScope>("bwd_heads", s);
             heads_bwd_kernel<DPL><<<(int)((R + 7) / 8), 256, 0, s>>>(mc, P, xb, b.Hin[L], R, g_abs + lo, g_phase + lo,
-                                                                      b.dH, b.dS, b.GX, b.HF, b.DL, b.DPH);
+                                                                      b.dH[L], b.dSh, b.GXh, b.HF, b.DL, b.DPH);
             NQS_LAUNCHED();
+            NQS_TRY(fork());
             NQS_TRY(outer(b.DL, 1, b.HF, d, M, 1, d, grad + mc.head_w, nullptr));
             NQS_TRY(colsum(b.DL, nullptr, n, R, n, grad + mc.head_b, nullptr));
             NQS_TRY(outer(b.DPH, 4, b.HF + (int64_t)(n - 2) * d, (int64_t)n * d, R, 4, d, grad + mc.phase_w,
                           grad + mc.phase_b));
-            NQS_TRY(colsum(b.GX, b.dS, d, M, d, grad + mc.lnf_g, grad + mc.lnf_b));
+            NQS_TRY(colsum(b.GXh, b.dSh, d, M, d, grad + mc.lnf_g, grad + mc.lnf_b));
             ps_heads.reset();
-            // ---- blocks, last to first
+            // ---- blocks, last to first (weight gradients on the side stream)
             for (int l = L - 1; l >= 0; --l) {
                 // MLP: Hin[l+1] = Hmid + gelu(A2 W1^T + b1) W2^T + b2
                 auto ps_mlp = std::make_unique<ProfScope>("bwd_mlp", s);
-                NQS_TRY(outer(b.dH, d, (const float*)b.MM[l], 4 * d, M, d, 4 * d, grad + mc.w2[l], grad + mc.b2[l]));
-                NQS_TRY(gemm_nn(b.dH, W[l][TF_W2], b.dBig, M, 4 * d, d));
-                gelu_bwd_kernel<<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], b.dBig, M * 4 * d);
+                NQS_TRY(outer(b.dH[l + 1], d, (const float*)b.MM[l], 4 * d, M, d, 4 * d, grad + mc.w2[l], grad + mc.b2[l]));
+                NQS_TRY(gemm_nn(b.dH[l + 1], W[l][TF_W2], b.dBig[l], M, 4 * d, d));
+                gelu_bwd_kernel<<<gs(M * 4 * d), 256, 0, s>>>(b.MPRE[l], b.dBig[l], M * 4 * d);
                 NQS_LAUNCHED();
-                NQS_TRY(outer(b.dBig, 4 * d, (const float*)b.A2[l], d, M, 4 * d, d, grad + mc.w1[l], grad + mc.b1[l]));
-                NQS_TRY(gemm_nn(b.dBig, W[l][TF_W1], b.dS, M, d, 4 * d));
-                ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hmid[l], P + mc.ln2_g[l], b.dS, b.dH, b.dHmid, b.GX, M, d);
+                NQS_TRY(fork());
+                NQS_TRY(outer(b.dBig[l], 4 * d, (const float*)b.A2[l], d, M, 4 * d, d, grad + mc.w1[l], grad + mc.b1[l]));
+                NQS_TRY(gemm_nn(b.dBig[l], W[l][TF_W1], b.dSa[l], M, d, 4 * d));
+                ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hmid[l], P + mc.ln2_g[l], b.dSa[l], b.dH[l + 1],
+                                                                       b.dHmid[l], b.GXa[l], M, d);
                 NQS_LAUNCHED();
-                NQS_TRY(colsum(b.GX, b.dS, d, M, d, grad + mc.ln2_g[l], grad + mc.ln2_b[l]));
+                NQS_TRY(fork());
+                NQS_TRY(colsum(b.GXa[l], b.dSa[l], d, M, d, grad + mc.ln2_g[l], grad + mc.ln2_b[l]));
                 ps_mlp.reset();
                 // attention: Hmid = Hin + attn(A1 Wqkv^T + bqkv) Wo^T + bo
                 ProfScope ps_att("bwd_attention", s);
-                NQS_TRY(outer(b.dHmid, d, (const float*)b.O[l], d, M, d, d, grad + mc.wo[l], grad + mc.bo[l]));
-                NQS_TRY(gemm_nn(b.dHmid, W[l][TF_WO], b.dS, M, d, d));
-                attention_bwd_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dS, n, d, dh, b.dQKV);
+                NQS_TRY(outer(b.dHmid[l], d, (const float*)b.O[l], d, M, d, d, grad + mc.wo[l], grad + mc.bo[l]));
+                NQS_TRY(gemm_nn(b.dHmid[l], W[l][TF_WO], b.dSb[l], M, d, d));
+                attention_bwd_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dSb[l], n, d, dh,
+                                                                                                b.dQKV[l]);
                 NQS_LAUNCHED();
-                NQS_TRY(outer(b.dQKV, 3 * d, (const float*)b.A1[l], d, M, 3 * d, d, grad + mc.wqkv[l], grad + mc.bqkv[l]));
-                NQS_TRY(gemm_nn(b.dQKV, W[l][TF_WQKV], b.dS, M, d, 3 * d));
-                ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hin[l], P + mc.ln1_g[l], b.dS, b.dHmid, b.dH, b.GX, M, d);
+                NQS_TRY(fork());
+                NQS_TRY(outer(b.dQKV[l], 3 * d, (const float*)b.A1[l], d, M, 3 * d, d, grad + mc.wqkv[l], grad + mc.bqkv[l]));
+                NQS_TRY(gemm_nn(b.dQKV[l], W[l][TF_WQKV], b.dSc[l], M, d, 3 * d));
+                ln_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(b.Hin[l], P + mc.ln1_g[l], b.dSc[l], b.dHmid[l], b.dH[l],
+                                                                       b.GXc[l], M, d);
                 NQS_LAUNCHED();
-                NQS_TRY(colsum(b.GX, b.dS, d, M, d, grad + mc.ln1_g[l], grad + mc.ln1_b[l]));
+                NQS_TRY(fork());
+                NQS_TRY(colsum(b.GXc[l], b.dSc[l], d, M, d, grad + mc.ln1_g[l], grad + mc.ln1_b[l]));
             }
             {
                 ProfScope ps_emb("bwd_embed", s);
                 const int nch = (int)((R + EB_ROWS - 1) / EB_ROWS);
-                embed_bwd_partial_kernel<<<dim3(n, nch), d, 0, s>>>(mc, xb, b.dH, R, b.part);
+                embed_bwd_partial_kernel<<<dim3(n, nch), d, 0, s>>>(mc, xb, b.dH[0], R, b.part_e);
                 NQS_LAUNCHED();
-                embed_bwd_final_kernel<<<((n + 3) * d + 255) / 256, 256, 0, s>>>(mc, b.part, nch, grad);
+                embed_bwd_final_kernel<<<((n + 3) * d + 255) / 256, 256, 0, s>>>(mc, b.part_e, nch, grad);
                 NQS_LAUNCHED();
             }
+            // the side stream's reductions are done before the next chunk reuses the buffers and
+            // before the caller reads the gradient
+            NQS_TRY(join());
         }
         return NQS_OK;
     });
