@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <utility>
 #include <stdint.h>
 
 #include <algorithm>
@@ -348,6 +349,30 @@ int tc_bwd_gemm_nn(const float* A, int64_t lda, const float* W, int64_t ldw, flo
                    int K, cudaStream_t s);
 int tc_bwd_outer_partial(const float* delta, int64_t ld_d, const float* act, int64_t ld_a, int64_t rows, int out_dim,
                          int in_dim, int64_t nsplit, int64_t per, bool with_bias, float* part, cudaStream_t s);
+
+// Programmatic dependent launch for chains of small kernels on one stream: the kernel may be
+// resident before its predecessor finishes and waits in pdl_wait() for the predecessor's
+// completion (and memory) before it reads anything the predecessor wrote; pdl_trigger() lets the
+// next kernel of the chain launch.  Without the launch attribute both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
 
 // Unique flipped configurations of a local-energy chunk (dedup.cu): a hash table of up to hcap
 // slots, each row's slot, the slots' positions in the unique list, and log psi of the unique rows.

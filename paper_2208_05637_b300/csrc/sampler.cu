@@ -52,6 +52,8 @@ __global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_
 __global__ void draw_kernel(int64_t n_samples, const int64_t* __restrict__ start,
                             const int64_t* __restrict__ Udev, const uint64_t* __restrict__ thr,
                             int64_t* __restrict__ n1, int k) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t U = Udev[0];
     const uint64_t seed = (uint64_t)Udev[3];
     const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
@@ -331,6 +333,8 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, int64_t* _
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t tot0, tot1;
     extern __shared__ uint64_t sbits[];              // the U parent bit strings, then cap merged counts
+    pdl_wait();
+    pdl_trigger();
     const int64_t U = *Udev;
     uint32_t* scnt = reinterpret_cast<uint32_t*>(sbits + cap);
     for (int64_t i = threadIdx.x; i < U; i += BK_T) sbits[i] = cb[i];
@@ -544,14 +548,16 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         if (one_cta) {
             // two launches: draws, then flags / merge / eviction / ancestors and the next step's
             // draw ranges (the first step's come from init_kernel)
-            draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
-            NQS_LAUNCHED();
+            // programmatic dependent launches: each kernel is resident before its predecessor ends
+            NQS_CK(launch_pdl(draw_kernel, dim3(grid_for(n_samples)), dim3(256), 0, s, n_samples,
+                              (const int64_t*)b.start, (const int64_t*)b.U, (const uint64_t*)b.thr, b.n1, k));
+            count_launch();
             const bool anc = b.kv && k + 1 < mc.n;
-            bk_finish_kernel<<<1, BK_T, b.cap * BK_SMEM_PER_ENTRY, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc,
-                                                b.kv ? b.par : nullptr, b.kv ? b.par2 : nullptr, max_unique,
-                                                anc ? b.ancA : nullptr, anc ? b.ancB : nullptr, mc.n, k, b.cap,
-                                                b.start);
-            NQS_LAUNCHED();
+            NQS_CK(launch_pdl(bk_finish_kernel, dim3(1), dim3(BK_T), (size_t)(b.cap * BK_SMEM_PER_ENTRY), s, cb, cc, b.n1,
+                              b.pos0, b.pos1, b.U, (uint64_t)(1ull << mc.order[k]), nb, nc, b.kv ? b.par : nullptr,
+                              b.kv ? b.par2 : nullptr, max_unique, (const int32_t*)(anc ? b.ancA : nullptr),
+                              anc ? b.ancB : nullptr, (int)mc.n, k, b.cap, b.start));
+            count_launch();
             if (anc) std::swap(b.ancA, b.ancB);
             continue;
         }

@@ -208,6 +208,8 @@ tf_step_fused_kernel(const __grid_constant__ ModelConst mc, const __grid_constan
     constexpr int KX = MODE == ACT_BF16X2 ? 2 : 1;       // operand width factor (hi | lo)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, q4 = lane & 3;
+    pdl_wait();                                          // the previous step's bookkeeping is complete
+    pdl_trigger();
     const int64_t U = min(*A.Udev, A.R);
     const int64_t row0 = (int64_t)blockIdx.x * FS_RB;
     if (row0 >= U) return;
@@ -512,9 +514,10 @@ int tf_step_fused(const ModelConst& mc, const float* P, const TfWeights& w, cons
     const double flops = 2.0 * M * mc.layers * (double)FS_D * (3 * FS_D + FS_D + 2 * FS_F) * (mc.compensated ? 2 : 1);
     ProfScope ps("tf_step_fused", s, flops, 0.0);
     const int smem = fs_smem_bytes(mc.layers);
-    if (mc.compensated) tf_step_fused_kernel<ACT_BF16X2><<<grid, FS_THREADS, smem, s>>>(mc, a);
-    else tf_step_fused_kernel<ACT_BF16><<<grid, FS_THREADS, smem, s>>>(mc, a);
-    NQS_LAUNCHED();
+    // a programmatic dependent launch: resident before the previous step's bookkeeping ends
+    if (mc.compensated) NQS_CK(launch_pdl(tf_step_fused_kernel<ACT_BF16X2>, dim3(grid), dim3(FS_THREADS), (size_t)smem, s, mc, a));
+    else NQS_CK(launch_pdl(tf_step_fused_kernel<ACT_BF16>, dim3(grid), dim3(FS_THREADS), (size_t)smem, s, mc, a));
+    count_launch();
     return NQS_OK;
 }
 
