@@ -162,7 +162,7 @@ struct Carver {
 // ------------------------------------------------------------------ launchers (.cu files)
 // term sweep (sweep.cu)
 constexpr int SWEEP_GT = 256;   // groups per tile (threads per CTA)
-constexpr int SWEEP_SB = 8;     // samples per CTA batch
+constexpr int SWEEP_SB = 4;     // samples per CTA batch
 int64_t sweep_tiles(const HamDev& h);
 int launch_sweep_count(const HamDev& h, uint64_t amask, uint64_t bmask, int n_up, int n_dn,
                        const uint64_t* bits, int64_t B, int32_t* cnt, cudaStream_t s);
