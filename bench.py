@@ -217,7 +217,8 @@ def run_ours(args, rank, world, local):
     kern = {}
     for name in ("sample", "local_energy", "logpsi_rows", "sweep_count", "term_sweep", "eloc_rows", "made_backward",
                  "grad_reduce", "energy_stats", "adam", "product_backward", "tf_gemm", "tf_qkv_attention", "tf_resid_ln", "tf_mlp", "tf_attention",
-                 "tf_heads", "tf_layernorm", "tf_tok_table", "tf_step_fused", "dedup", "dedup_contrib", "tf_backward", "bwd_recompute",
+                 "tf_heads", "tf_layernorm", "tf_tok_table", "tf_step_fused", "dedup", "dedup_contrib", "tf_backward",
+                 "tf_backward_recompute", "bwd_recompute",
                  "bwd_heads", "bwd_mlp", "bwd_attention", "bwd_embed"):
         tms, cnt = P.profile_read(name)
         if cnt:

@@ -180,6 +180,18 @@ int nqs_logpsi_backward(nqs_model_t model, const uint64_t* bits, int64_t B,
                         const float* g_log_abs, const float* g_phase, float* grad_accum,
                         void* ws, size_t ws_bytes, void* stream);
 
+/* nqs_logpsi_backward in two calls, so that the forward recompute (phase 1: needs only the
+ * parameters and bits) can run on another stream while the local energy and its statistics
+ * produce g_log_abs and g_phase; phase 2 then runs the backward from the recomputed activations.
+ * Phase 2 must follow phase 1 with the same model, bits, B and workspace, the parameters
+ * unchanged, and ordered after it on the device.  Transformer models need B within one recompute
+ * pass (else NQS_ERR_UNSUPPORTED: use nqs_logpsi_backward); for the other models phase 1 does
+ * nothing and phase 2 is nqs_logpsi_backward.  g_log_abs, g_phase and grad_accum may be NULL in
+ * phase 1.  Same results as nqs_logpsi_backward, bit for bit. */
+int nqs_logpsi_backward_phase(nqs_model_t model, int phase, const uint64_t* bits, int64_t B,
+                              const float* g_log_abs, const float* g_phase, float* grad_accum,
+                              void* ws, size_t ws_bytes, void* stream);
+
 /* FP64 energy statistics (Eq. total_energy_sum with sample counts as weights):
  * stats[0..3] (device double) = Re E_bar, Im E_bar, Var = sum w|E - E_bar|^2 / W, W = sum w.
  * If g_abs and g_phase (device fp32, may be NULL) are given they receive the upstream

@@ -34,7 +34,7 @@ EXPORTED = [
     "nqs_ham_create", "nqs_ham_info", "nqs_ham_export", "nqs_ham_destroy", "nqs_model_create",
     "nqs_model_param_count", "nqs_model_param_tensors", "nqs_model_param_info",
     "nqs_model_bind_params", "nqs_model_destroy", "nqs_workspace_size", "nqs_sample",
-    "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward",
+    "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward", "nqs_logpsi_backward_phase",
     "nqs_energy_stats", "nqs_adam_step", "nqs_strerror", "nqs_last_error", "nqs_profile_enable",
     "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16", "nqs_profile_work",
 ]
@@ -69,6 +69,7 @@ _sig = {
                        ctypes.POINTER(_I64), _P, ctypes.c_size_t, _P],
     "nqs_local_energy": [_P, _P, _P, _I64, _P, _P, ctypes.c_size_t, _P],
     "nqs_logpsi_backward": [_P, _P, _I64, _P, _P, _P, _P, ctypes.c_size_t, _P],
+    "nqs_logpsi_backward_phase": [_P, ctypes.c_int, _P, _I64, _P, _P, _P, _P, ctypes.c_size_t, _P],
     "nqs_energy_stats": [_P, _P, _I64, _P, _P, _P, _P],
     "nqs_adam_step": [_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                       ctypes.c_float, ctypes.c_float, _P],
@@ -344,6 +345,18 @@ def nqs_logpsi_backward(model, bits, g_log_abs, g_phase, grad_accum, ws=None, st
     wp, wn = _ws(ws)
     _check(_lib.nqs_logpsi_backward(model.handle, _ptr(bits), B, _ptr(g_log_abs), _ptr(g_phase),
                                     _ptr(grad_accum), wp, wn, _stream(stream)), "nqs_logpsi_backward")
+    return grad_accum
+
+
+def nqs_logpsi_backward_phase(model, phase, bits, g_log_abs=None, g_phase=None, grad_accum=None, ws=None,
+                              stream=None):
+    """nqs_logpsi_backward in two calls: phase 1 recomputes the forward (bits only), phase 2 runs
+    the backward from it with the same bits and workspace."""
+    B = bits.numel()
+    ws = model.workspace(OP_BACKWARD, B) if ws is None else ws
+    wp, wn = _ws(ws)
+    _check(_lib.nqs_logpsi_backward_phase(model.handle, int(phase), _ptr(bits), B, _ptr(g_log_abs), _ptr(g_phase),
+                                          _ptr(grad_accum), wp, wn, _stream(stream)), "nqs_logpsi_backward_phase")
     return grad_accum
 
 

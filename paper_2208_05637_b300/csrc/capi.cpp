@@ -888,6 +888,24 @@ int nqs_logpsi_backward(nqs_model_t m, const uint64_t* bits, int64_t B, const fl
     return NQS_OK;
 }
 
+int nqs_logpsi_backward_phase(nqs_model_t m, int phase, const uint64_t* bits, int64_t B, const float* g_abs,
+                              const float* g_phase, float* grad, void* ws, size_t ws_bytes, void* stream) {
+    NQS_TRY(need_params(m));
+    if (B < 0 || (phase != 1 && phase != 2)) { set_error("need B >= 0 and phase 1 or 2"); return NQS_ERR_INVALID_ARG; }
+    if (B == 0) return NQS_OK;
+    if (!bits || (phase == 2 && (!g_abs || !g_phase || !grad))) { set_error("null pointer argument"); return NQS_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->mc.arch != NQS_ARCH_TRANSFORMER) {
+        // nothing to recompute ahead: phase 2 is the whole backward
+        return phase == 1 ? NQS_OK : nqs_logpsi_backward(m, bits, B, g_abs, g_phase, grad, ws, ws_bytes, stream);
+    }
+    NQS_TRY(need_ws(m, nullptr, NQS_OP_BACKWARD, B, ws, ws_bytes));
+    ProfScope ps(phase == 1 ? "tf_backward_recompute" : "tf_backward", s);
+    Carver c(ws);
+    void* base = c.take<char>(tf_bwd_workspace(m->mc, B));
+    return tf_backward(m->mc, m->d_params, bits, B, g_abs, g_phase, grad, base, s, phase);
+}
+
 int nqs_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
                      float* g_abs, float* g_phase, void* stream) {
     if (B < 1 || !eloc || !counts || !stats) { set_error("need B >= 1 and eloc/counts/stats"); return NQS_ERR_INVALID_ARG; }

@@ -288,11 +288,13 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
 // transformer backward (tf_backward.cu)
 int64_t tf_bwd_seq_capacity(const ModelConst& mc);
 size_t tf_bwd_workspace(const ModelConst& mc, int64_t B);
+// phases: 1 recomputes the forward activations into ws, 2 runs the backward from them (same
+// bits, B, ws and parameters; B within one recompute pass), 3 both.
 int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
-                const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
+                const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s, int phases = 3);
 // status of the tensor-core kernels' bounded waits; synchronous, clears the flag
 // Head form of the last block's fused MLP (d_model 64): per row the output-head logit of
-// LNf(h) and, on rows at position n - 2, the four phase-head dot products (h is not stored).
+// LNf(h) and, on rows at position n - 2, h itself for the phase head (the final h is not stored).
 struct TcMlpHead {
     const float *lnf_g, *lnf_b, *head_w, *head_b;
     int n;

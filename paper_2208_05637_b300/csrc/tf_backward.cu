@@ -502,13 +502,17 @@ size_t tf_bwd_workspace(const ModelConst& mc, int64_t B) {
 
 template <int MODE>
 int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
-                     const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s);
+                     const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s, int phases);
 
 int tf_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
-                const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s) {
-    if (mc.precision != NQS_PREC_BF16) return tf_backward_mode<ACT_F32>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
-    if (mc.compensated) return tf_backward_mode<ACT_F32_Q2>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
-    return tf_backward_mode<ACT_F32_Q1>(mc, P, bits, B, g_abs, g_phase, grad, ws, s);
+                const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s, int phases) {
+    if (phases != 3 && B > tf_bwd_seq_capacity(mc)) {
+        set_error("two-phase backward: the batch exceeds one recompute pass");
+        return NQS_ERR_UNSUPPORTED;
+    }
+    if (mc.precision != NQS_PREC_BF16) return tf_backward_mode<ACT_F32>(mc, P, bits, B, g_abs, g_phase, grad, ws, s, phases);
+    if (mc.compensated) return tf_backward_mode<ACT_F32_Q2>(mc, P, bits, B, g_abs, g_phase, grad, ws, s, phases);
+    return tf_backward_mode<ACT_F32_Q1>(mc, P, bits, B, g_abs, g_phase, grad, ws, s, phases);
 }
 
 // The weight-gradient reductions run on a library-owned side stream, ordered after the main
@@ -536,9 +540,10 @@ static int bwd_side(BwdSide*& out) {
 
 // MODE: how the recomputed forward stores GEMM input activations (fp32 values equal to the
 // ones the forward of this precision feeds its GEMMs).
+// phases: 1 recompute the forward into the workspace, 2 the backward from it, 3 both.
 template <int MODE>
 int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
-                     const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s) {
+                     const float* g_abs, const float* g_phase, float* grad, void* ws, cudaStream_t s, int phases) {
     const int n = mc.n, d = mc.hidden, dh = d / mc.heads, L = mc.layers;
     const bool bf = mc.precision == NQS_PREC_BF16;
     float* ptrs[3 * TF_MAX_LAYERS + 2];
@@ -572,7 +577,7 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
                 }
             }
         }
-        if (bf) {   // all blocks' bf16-rounded copies in one launch
+        if (bf && (phases & 1)) {   // all blocks' bf16-rounded copies in one launch
             wconv_kernel<<<gs(wl.total), 256, 0, s>>>(wl);
             NQS_LAUNCHED();
         }
@@ -655,6 +660,7 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
             const int64_t R = std::min(b.R, B - lo);
             const int64_t M = R * n;
             const uint64_t* xb = bits + lo;
+            if (phases & 1) {
             // ---- forward with saved activations
             auto ps_fwd = std::make_unique<ProfScope>("bwd_recompute", s);
             embed_kernel<<<gs(M * d), 256, 0, s>>>(mc, P, xb, R, n, b.Hin[0]);
@@ -680,6 +686,8 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
                 if (l + 1 < L) NQS_TRY(ln_fwd(b.Hin[l + 1], P + mc.ln1_g[l + 1], P + mc.ln1_b[l + 1], b.A1[l + 1]));
             }
             ps_fwd.reset();
+            }
+            if (!(phases & 2)) continue;
             // ---- heads and final LayerNorm
             auto ps_heads = std::make_unique<ProfScope>("bwd_heads", s);
             heads_bwd_kernel<DPL><<<(int)((R + 7) / 8), 256, 0, s>>>(mc, P, xb, b.Hin[L], R, g_abs + lo, g_phase + lo,

@@ -7,12 +7,15 @@ The gradient of the VMC surrogate sum_i g_abs_i log|f(x_i)| + g_phase_i phi(x_i)
 vector-Jacobian product with upstream gradients (g_abs, g_phase).  VMC.step hands those to the
 backward entry point directly (the backward recomputes the forward itself); with
 ``autograd=True`` it goes through LogPsi and torch autograd instead, which also evaluates the
-surrogate's forward.  Both give the same gradient.
+surrogate's forward.  Both give the same gradient.  With one mini-batch the backward's forward
+recompute (which needs only the samples) runs on a second stream while the local energy is
+computed (nqs_logpsi_backward_phase); the gradient is the same bit for bit.
 """
 import torch
 
-from . import (OP_BACKWARD, OP_LOCAL_ENERGY, OP_SAMPLE, nqs_adam_step, nqs_energy_stats,
-               nqs_local_energy, nqs_logpsi, nqs_logpsi_backward, nqs_sample)
+from . import (NQS_ERR_UNSUPPORTED, NQSError, OP_BACKWARD, OP_LOCAL_ENERGY, OP_SAMPLE, nqs_adam_step,
+               nqs_energy_stats, nqs_local_energy, nqs_logpsi, nqs_logpsi_backward, nqs_logpsi_backward_phase,
+               nqs_sample)
 
 
 class LogPsi(torch.autograd.Function):
@@ -59,6 +62,8 @@ class VMC:
         self.t = 0
         self.ws_sample = model.workspace(OP_SAMPLE, self.n_samples)
         self._ws = {}
+        self._side = None            # stream of the overlapped backward recompute
+        self.overlap_backward = True
 
     def reset(self, params):
         """Restore the parameters and clear the optimiser state (device copies, no sync)."""
@@ -78,12 +83,29 @@ class VMC:
         per = max(1, -(-U // self.mini_batches))
         return [slice(lo, min(U, lo + per)) for lo in range(0, U, per)]
 
+    def _recompute_ahead(self, bits, ws):
+        """Phase 1 of the backward on the side stream (True), or False where it does not apply."""
+        if self.autograd or not self.overlap_backward or self.mini_batches != 1:
+            return False
+        main = torch.cuda.current_stream()
+        if self._side is None:
+            self._side = torch.cuda.Stream()
+        self._side.wait_stream(main)
+        try:
+            nqs_logpsi_backward_phase(self.model, 1, bits, ws=ws, stream=self._side)
+        except NQSError as e:
+            if e.status != NQS_ERR_UNSUPPORTED:
+                raise
+            return False
+        return True
+
     def step(self, seed):
         bits, counts, _ = nqs_sample(self.model, self.n_samples, self.max_unique, seed,
                                      ws=self.ws_sample)
         U = bits.numel()
         eloc = torch.empty((U, 2), dtype=torch.float32, device="cuda")
         per = max(1, -(-U // self.mini_batches))
+        ahead = self._recompute_ahead(bits, self._workspace(OP_BACKWARD, per))
         for sl in self._slices(U):
             nqs_local_energy(self.ham, self.model, bits[sl], ws=self._workspace(OP_LOCAL_ENERGY, per),
                              out=eloc[sl])
@@ -92,7 +114,11 @@ class VMC:
             self.params.grad = torch.zeros_like(self.params)
         else:
             self.params.grad.zero_()
-        for sl in self._slices(U):
+        if ahead:
+            torch.cuda.current_stream().wait_stream(self._side)
+            nqs_logpsi_backward_phase(self.model, 2, bits, g_abs, g_phase, self.params.grad,
+                                      ws=self._workspace(OP_BACKWARD, per))
+        for sl in ([] if ahead else self._slices(U)):
             if self.autograd:
                 la, ph = LogPsi.apply(self.params, self.model, bits[sl])
                 (la * g_abs[sl]).sum().add((ph * g_phase[sl]).sum()).backward()

@@ -145,3 +145,40 @@ def test_vmc_direct_backward_equals_autograd(cid):
     assert torch.equal(sa, sb)
     assert torch.equal(ga, gb)
     assert torch.equal(pa, pb)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_two_phase_backward_equals_one_call(precision):
+    # nqs_logpsi_backward_phase 1 (recompute) then 2 (backward) == nqs_logpsi_backward, bitwise;
+    # and the VMC step that runs phase 1 on a second stream gives the same step as the one-call path
+    import torch
+    P = lib()
+    cfg = synth.get_config(3)
+    m, _ = gpu_model(cfg, beta=1.0, precision=precision)
+    bits = to_dev_bits(synth.random_sector_bits(cfg.n_qubits // 2, cfg.n_up, cfg.n_dn, 700, seed=8))
+    g = torch.Generator(device="cpu").manual_seed(9)
+    ga = torch.randn(bits.numel(), generator=g).cuda()
+    gp = torch.randn(bits.numel(), generator=g).cuda()
+    one = torch.zeros(m.param_count, dtype=torch.float32, device="cuda")
+    P.nqs_logpsi_backward(m, bits, ga, gp, one)
+    two = torch.zeros_like(one)
+    ws = m.workspace(P.OP_BACKWARD, bits.numel())
+    P.nqs_logpsi_backward_phase(m, 1, bits, ws=ws)
+    P.nqs_logpsi_backward_phase(m, 2, bits, ga, gp, two, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(one, two)
+
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(cfg.n_qubits, xm, zm, coef)
+    p0 = m.params.detach().clone()
+    res = []
+    for overlap in (True, False):
+        vmc = P.VMC(ham, m, p0.clone(), cfg.n_samples, mini_batches=1, max_unique=1024)
+        vmc.overlap_backward = overlap
+        out = vmc.step(seed=cfg.seed_sampler + 6)
+        torch.cuda.synchronize()
+        res.append((out["stats"].cpu(), vmc.params.grad.detach().cpu().clone(), vmc.params.detach().cpu().clone()))
+    (sa, ga_, pa), (sb, gb, pb) = res
+    assert torch.equal(sa, sb)
+    assert torch.equal(ga_, gb)
+    assert torch.equal(pa, pb)
