@@ -104,6 +104,18 @@ static int check_device_ptr(const void* p, const char* what) {
 }
 
 // Groups whose flip can keep some sector state inside the sector.
+// Number of configurations with n_up and n_dn electrons in n / 2 orbitals per spin (saturating
+// at 2^62): the most distinct x' a local-energy chunk can have.
+static int64_t sector_dim(int n, int n_up, int n_dn) {
+    auto binom = [](int a, int b) -> double {
+        double r = 1.0;
+        for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+        return r;
+    };
+    const double v = binom(n / 2, n_up) * binom(n / 2, n_dn);
+    return v >= 4.6e18 ? (int64_t)1 << 62 : (int64_t)(v + 0.5);
+}
+
 static int64_t feasible_groups(const nqs_ham_s* h, int n_up, int n_dn) {
     int n_orb = h->n / 2;
     int64_t cnt = 0;
@@ -803,8 +815,11 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
                 // count stays on the device (bounded by the chunk's feasible groups)
                 const int64_t* rows_dev = e.off + nb * e.ntiles;
                 const int64_t rows_max = nb * (e.rows_cap / e.chunk);
+                // the table holds the distinct keys: at most the rows plus samples, and at most
+                // the sector's configurations
+                const int64_t keys = std::min(rows_max + nb, sector_dim(m->mc.n, m->mc.n_up, m->mc.n_dn));
                 int64_t nu = 0;
-                NQS_TRY(dedup_rows(e.xprime, rows_dev, rows_max, bits + lo, nb, e.dd, &nu, s));
+                NQS_TRY(dedup_rows(e.xprime, rows_dev, rows_max, bits + lo, nb, keys, e.dd, &nu, s));
                 if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
                 for (int64_t r0 = 0; r0 < nu; r0 += e.tf.R) {
                     const int64_t R = std::min(e.tf.R, nu - r0);

@@ -113,10 +113,11 @@ void dedup_layout(Carver& c, int64_t rows_cap, int64_t chunk, DedupBufs& d) {
 }
 
 int dedup_rows(const uint64_t* xp, const int64_t* rows_dev, int64_t rows_max, const uint64_t* xs, int64_t nb,
-               const DedupBufs& d, int64_t* n_unique, cudaStream_t s) {
+               int64_t max_keys, const DedupBufs& d, int64_t* n_unique, cudaStream_t s) {
     *n_unique = 0;
     if (rows_max + nb <= 0) return NQS_OK;
-    const int64_t hc = dedup_table_slots(rows_max + nb);  // at least twice the keys, within the layout's table
+    // at least twice the distinct keys, within the layout's table
+    const int64_t hc = dedup_table_slots(std::max<int64_t>(1, std::min(max_keys, rows_max + nb)));
     if (hc > d.hcap || hc > (1ll << 31)) { set_error("x' dedup: table too small"); return NQS_ERR_CAPACITY; }
     ProfScope ps("dedup", s, 0.0, (double)(rows_max + nb) * (8 + 4) + (double)hc * (8 * 2 + 4));
     NQS_CK(cudaMemsetAsync(d.table, 0xff, (size_t)hc * sizeof(uint64_t), s));

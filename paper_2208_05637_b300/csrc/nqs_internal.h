@@ -390,9 +390,10 @@ struct DedupBufs {
 };
 void dedup_layout(Carver& c, int64_t rows_cap, int64_t chunk, DedupBufs& d);
 // The distinct values of the rows xp[0, *rows_dev) (rows_dev on the device, at most rows_max) and
-// the samples xs[0, nb) into d.uniq (their number into *n_unique; synchronizes s).
+// the samples xs[0, nb) into d.uniq (their number into *n_unique; synchronizes s).  max_keys
+// bounds the number of distinct values (it sizes the hash table).
 int dedup_rows(const uint64_t* xp, const int64_t* rows_dev, int64_t rows_max, const uint64_t* xs, int64_t nb,
-               const DedupBufs& d, int64_t* n_unique, cudaStream_t s);
+               int64_t max_keys, const DedupBufs& d, int64_t* n_unique, cudaStream_t s);
 // Per-row contributions <x|P|x'> psi(x')/psi(x) of the chunk, log psi of x' and x from d.la_u / d.ph_u.
 int dedup_contrib(const uint64_t* xp, const int64_t* rows_dev, int64_t rows_max, const DedupBufs& d,
                   const uint64_t* xsample, const int64_t* seg, int64_t seg_stride, int64_t nseg, const float4* S,
