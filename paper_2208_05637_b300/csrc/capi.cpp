@@ -661,9 +661,12 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
         NQS_CK(cudaStreamWaitEvent(G.side, G.ev, 0));
         if (!G.exec) {
             cudaGraph_t graph = nullptr;
+            const int64_t before = g_launches.load();
             NQS_CK(cudaStreamBeginCapture(G.side, cudaStreamCaptureModeRelaxed));
             const int st = sampler_steps(m->mc, m->d_params, n_samples, max_unique, b, p_trace, trace_stride,
                                          &ctx, true, G.side);
+            G.kernels = g_launches.load() - before;   // kernel nodes of the graph (counted at capture)
+            g_launches.fetch_sub(G.kernels);          // counted again at every replay instead
             const cudaError_t ce = cudaStreamEndCapture(G.side, &graph);
             cudaError_t ie = cudaErrorUnknown;
             if (st == NQS_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&G.exec, graph, 0);
@@ -678,6 +681,7 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
             ProfScope ps("sample", G.side);
             NQS_TRY(sampler_init(b, n_samples, seed, G.side));
             NQS_CK(cudaGraphLaunch(G.exec, G.side));
+            g_launches.fetch_add(G.kernels, std::memory_order_relaxed);
         } else {
             NQS_TRY(run_sampler(m->mc, m->d_params, n_samples, max_unique, seed, b, p_trace, trace_stride,
                                 &ctx, true, G.side));

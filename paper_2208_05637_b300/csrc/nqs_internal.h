@@ -125,6 +125,7 @@ struct SamplerGraph {
     bool seen = false;              // this shape ran once eagerly; capture on the next call
     bool failed = false;            // capture not possible: stay eager for this shape
     cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;            // kernel launches inside the graph
     cudaStream_t side = nullptr;
     cudaEvent_t ev = nullptr;
 };

@@ -49,17 +49,26 @@ __global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_
 }
 
 // ones per parent: warp-aggregated integer atomics (exact, order-independent)
+// sstart_cap > 0: the U + 1 range starts are staged in shared memory (dynamic, sstart_cap
+// entries) when they fit, so the parent searches run there instead of in global memory.
 __global__ void draw_kernel(int64_t n_samples, const int64_t* __restrict__ start,
                             const int64_t* __restrict__ Udev, const uint64_t* __restrict__ thr,
-                            int64_t* __restrict__ n1, int k) {
+                            int64_t* __restrict__ n1, int k, int64_t sstart_cap) {
+    extern __shared__ int64_t sstart[];
     pdl_wait();
     pdl_trigger();
     const int64_t U = Udev[0];
     const uint64_t seed = (uint64_t)Udev[3];
     const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
+    const bool staged = U + 1 <= sstart_cap;
+    if (staged) {
+        for (int64_t i = threadIdx.x; i <= U; i += blockDim.x) sstart[i] = start[i];
+        __syncthreads();
+    }
+    const int64_t* st = staged ? sstart : start;
     // after an eviction the surviving counts sum to less than n_samples: the nominal indices
     // run over [0, start[U]) only
-    const int64_t total = min(start[U], n_samples);
+    const int64_t total = min(st[U], n_samples);
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < total; j0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = j0 + threadIdx.x;
         int64_t s = -1;
@@ -69,7 +78,7 @@ __global__ void draw_kernel(int64_t n_samples, const int64_t* __restrict__ start
             int64_t lo = 0, hi = U - 1;
             while (lo < hi) {
                 const int64_t mid = (lo + hi + 1) >> 1;
-                if (start[mid] <= j) lo = mid; else hi = mid - 1;
+                if (st[mid] <= j) lo = mid; else hi = mid - 1;
             }
             s = lo;
             const uint32_t u = philox_word0((uint32_t)j, (uint32_t)k, 0u, 0u, key0, key1);
@@ -538,6 +547,8 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         if (configured_device != dev) {
             NQS_CK(cudaFuncSetAttribute(bk_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(SAMPLER_GRAPH_MAX_CAP * BK_SMEM_PER_ENTRY)));
+            NQS_CK(cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((SAMPLER_GRAPH_MAX_CAP + 1) * sizeof(int64_t))));
             configured_device = dev;
         }
     }
@@ -549,8 +560,9 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
             // two launches: draws, then flags / merge / eviction / ancestors and the next step's
             // draw ranges (the first step's come from init_kernel)
             // programmatic dependent launches: each kernel is resident before its predecessor ends
-            NQS_CK(launch_pdl(draw_kernel, dim3(grid_for(n_samples)), dim3(256), 0, s, n_samples,
-                              (const int64_t*)b.start, (const int64_t*)b.U, (const uint64_t*)b.thr, b.n1, k));
+            NQS_CK(launch_pdl(draw_kernel, dim3(grid_for(n_samples)), dim3(256), (size_t)((b.cap + 1) * sizeof(int64_t)), s,
+                              n_samples, (const int64_t*)b.start, (const int64_t*)b.U, (const uint64_t*)b.thr, b.n1, k,
+                              (int64_t)(b.cap + 1)));
             count_launch();
             const bool anc = b.kv && k + 1 < mc.n;
             NQS_CK(launch_pdl(bk_finish_kernel, dim3(1), dim3(BK_T), (size_t)(b.cap * BK_SMEM_PER_ENTRY), s, cb, cc, b.n1,
@@ -564,7 +576,7 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         NQS_TRY(launch_scan_i64(cc, b.cap, b.U, b.start, s));
         zero_kernel<<<g, 256, 0, s>>>(b.n1, b.U, b.cap);
         NQS_LAUNCHED();
-        draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k);
+        draw_kernel<<<grid_for(n_samples), 256, 0, s>>>(n_samples, b.start, b.U, b.thr, b.n1, k, 0);
         NQS_LAUNCHED();
         flags_kernel<<<g, 256, 0, s>>>(cc, b.n1, b.U, b.flags0, b.flags1);
         NQS_LAUNCHED();

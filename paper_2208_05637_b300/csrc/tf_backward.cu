@@ -163,10 +163,87 @@ heads_bwd_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __r
     }
 }
 
-// Attention backward per (sequence, head), dynamic shared memory.
+// Attention backward per (sequence, head), dynamic shared memory; DH = head size.  Threads map
+// to (row, column) pairs by shifts and strided loops (no divisions in the loops).
+template <int DH>
 __global__ void __launch_bounds__(128)
 attention_bwd_kernel(const float* __restrict__ qkv, const float* __restrict__ dout, int T, int d,
-                     int dh, float* __restrict__ dqkv) {
+                     float* __restrict__ dqkv) {
+    extern __shared__ float sm[];
+    constexpr int LD = DH + 1;
+    const int lp = T + 1;
+    float* q = sm;
+    float* k = q + T * LD;
+    float* v = k + T * LD;
+    float* go = v + T * LD;
+    float* p = go + T * LD;
+    float* dp = p + T * lp;
+    const int64_t r = blockIdx.x;
+    const int hd = blockIdx.y;
+    const float scale = rsqrtf((float)DH);
+    for (int i = threadIdx.x; i < T * DH; i += blockDim.x) {
+        const int t = i / DH, j = i % DH;              // DH is a power of two: shifts
+        const float* row = qkv + (r * T + t) * (int64_t)(3 * d);
+        q[t * LD + j] = row[hd * DH + j];
+        k[t * LD + j] = row[d + hd * DH + j];
+        v[t * LD + j] = row[2 * d + hd * DH + j];
+        go[t * LD + j] = dout[(r * T + t) * (int64_t)d + hd * DH + j];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // scores and dP: warp w takes rows t = w, w + nw, ...; lane the keys u = lane, lane + 32, ...
+    for (int t = warp; t < T; t += nw) {
+        float qt[DH], gt[DH];
+#pragma unroll
+        for (int j = 0; j < DH; ++j) { qt[j] = q[t * LD + j]; gt[j] = go[t * LD + j]; }
+        for (int u = lane; u < T; u += 32) {
+            float sc = -INFINITY, g = 0.f;
+            if (u <= t) {
+                sc = 0.f;
+#pragma unroll
+                for (int j = 0; j < DH; ++j) { sc = fmaf(qt[j], k[u * LD + j], sc); g = fmaf(gt[j], v[u * LD + j], g); }
+                sc *= scale;
+            }
+            p[t * lp + u] = sc;
+            dp[t * lp + u] = g;
+        }
+    }
+    __syncwarp();
+    for (int t = warp; t < T; t += nw) {
+        float mx = -INFINITY;
+        for (int u = lane; u <= t; u += 32) mx = fmaxf(mx, p[t * lp + u]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        float s = 0.f;
+        for (int u = lane; u <= t; u += 32) { const float e = expf(p[t * lp + u] - mx); p[t * lp + u] = e; s += e; }
+        s = warp_sum(s);
+        const float inv = 1.f / s;
+        float pd = 0.f;
+        for (int u = lane; u <= t; u += 32) { p[t * lp + u] *= inv; pd += p[t * lp + u] * dp[t * lp + u]; }
+        pd = warp_sum(pd);
+        for (int u = lane; u <= t; u += 32) dp[t * lp + u] = p[t * lp + u] * (dp[t * lp + u] - pd);   // dS
+        for (int u = t + 1 + lane; u < T; u += 32) { p[t * lp + u] = 0.f; dp[t * lp + u] = 0.f; }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * DH; i += blockDim.x) {
+        const int t = i / DH, j = i % DH;
+        float dq = 0.f, dk = 0.f, dv = 0.f;
+        for (int u = 0; u < T; ++u) {
+            dq = fmaf(dp[t * lp + u], k[u * LD + j], dq);      // dS[t][u] k[u]
+            dk = fmaf(dp[u * lp + t], q[u * LD + j], dk);      // dS[u][t] q[u]
+            dv = fmaf(p[u * lp + t], go[u * LD + j], dv);      // P[u][t] dO[u]
+        }
+        float* row = dqkv + (r * T + t) * (int64_t)(3 * d);
+        row[hd * DH + j] = dq * scale;
+        row[d + hd * DH + j] = dk * scale;
+        row[2 * d + hd * DH + j] = dv;
+    }
+}
+
+// Head sizes other than the template's.
+__global__ void __launch_bounds__(128)
+attention_bwd_any_kernel(const float* __restrict__ qkv, const float* __restrict__ dout, int T, int d,
+                         int dh, float* __restrict__ dqkv) {
     extern __shared__ float sm[];
     const int ld = dh + 1, lp = T + 1;
     float* q = sm;
@@ -220,9 +297,9 @@ attention_bwd_kernel(const float* __restrict__ qkv, const float* __restrict__ do
         const int t = i / dh, j = i % dh;
         float dq = 0.f, dk = 0.f, dv = 0.f;
         for (int u = 0; u < T; ++u) {
-            dq = fmaf(dp[t * lp + u], k[u * ld + j], dq);      // dS[t][u] k[u]
-            dk = fmaf(dp[u * lp + t], q[u * ld + j], dk);      // dS[u][t] q[u]
-            dv = fmaf(p[u * lp + t], go[u * ld + j], dv);      // P[u][t] dO[u]
+            dq = fmaf(dp[t * lp + u], k[u * ld + j], dq);
+            dk = fmaf(dp[u * lp + t], q[u * ld + j], dk);
+            dv = fmaf(p[u * lp + t], go[u * ld + j], dv);
         }
         float* row = dqkv + (r * T + t) * (int64_t)(3 * d);
         row[hd * dh + j] = dq * scale;
@@ -653,7 +730,9 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
         constexpr int DPL = decltype(dpl)::value;
         const size_t att_smem = (size_t)(4 * n * (dh + 1) + 2 * n * (n + 1)) * sizeof(float);
         if (att_smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(attention_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)att_smem);
+            cudaError_t e = cudaFuncSetAttribute(attention_bwd_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)att_smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(attention_bwd_any_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)att_smem);
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
         }
         for (int64_t lo = 0; lo < B; lo += b.R) {
@@ -721,8 +800,12 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
                 ProfScope ps_att("bwd_attention", s);
                 NQS_TRY(outer(b.dHmid[l], d, (const float*)b.O[l], d, M, d, d, grad + mc.wo[l], grad + mc.bo[l]));
                 NQS_TRY(gemm_nn(b.dHmid[l], W[l][TF_WO], b.dSb[l], M, d, d));
-                attention_bwd_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dSb[l], n, d, dh,
-                                                                                                b.dQKV[l]);
+                if (dh == 16)
+                    attention_bwd_kernel<16><<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dSb[l], n, d,
+                                                                                                        b.dQKV[l]);
+                else
+                    attention_bwd_any_kernel<<<dim3((unsigned)R, (unsigned)mc.heads), 128, att_smem, s>>>(b.QKV[l], b.dSb[l], n, d, dh,
+                                                                                                        b.dQKV[l]);
                 NQS_LAUNCHED();
                 NQS_TRY(fork());
                 NQS_TRY(outer(b.dQKV[l], 3 * d, (const float*)b.A1[l], d, M, 3 * d, d, grad + mc.wqkv[l], grad + mc.bqkv[l]));
