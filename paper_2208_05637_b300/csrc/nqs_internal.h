@@ -259,6 +259,10 @@ struct TfStepCache {
     int64_t cap = 0;
     const int32_t* anc = nullptr;
     const int64_t* Udev = nullptr;   // device count of live prefixes
+    // one-kernel step only: with par set, anc is the previous step's table and the kernel composes
+    // this step's slots (anc[par[r]][j] for j < k - 1, par[r] at j = k - 1) and writes them to anc_new
+    const int32_t* par = nullptr;
+    int32_t* anc_new = nullptr;
 };
 int64_t tf_seq_capacity(const ModelConst& mc);
 void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b);

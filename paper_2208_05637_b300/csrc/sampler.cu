@@ -488,7 +488,7 @@ int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs
 // count is read back (one small synchronous copy per step) to size the passes exactly.
 static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* bits,
                    const int64_t* Udev, SamplerBufs& b, float* trace, const TfCtx* tf,
-                   bool fixed_rows, cudaStream_t s) {
+                   bool fixed_rows, bool compose, cudaStream_t s) {
     int64_t U = b.cap;
     if (!fixed_rows) {
         NQS_CK(cudaMemcpyAsync(&U, Udev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -498,7 +498,10 @@ static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* 
         // incremental: position k only, earlier keys and values from the cache
         TfStepCache kc;
         kc.kv = b.kv; kc.cap = b.cap; kc.anc = b.ancA; kc.Udev = Udev;
-        if (tf_step_fused_supported(mc)) return tf_step_fused(mc, P, *tf->w, bits, U, k, kc, b.p, b.thr, trace, s);
+        if (tf_step_fused_supported(mc)) {
+            if (compose) { kc.par = b.par; kc.anc_new = b.ancB; }
+            return tf_step_fused(mc, P, *tf->w, bits, U, k, kc, b.p, b.thr, trace, s);
+        }
         NQS_TRY(tf_step(mc, P, *tf->w, bits, U, k, kc, *tf->b, s));
         HeadArgsHost ha{};
         ha.mode = 2; ha.p_out = b.p; ha.thr = b.thr; ha.trace = trace; ha.step_pos = k;
@@ -552,10 +555,14 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
             configured_device = dev;
         }
     }
+    // the one-kernel transformer step composes each step's ancestor table itself (from the
+    // parents the bookkeeping leaves), so the bookkeeping does not write it
+    const bool compose = one_cta && mc.arch == NQS_ARCH_TRANSFORMER && b.kv && tf_step_fused_supported(mc);
     for (int k = 0; k < mc.n; ++k) {
         float* tr = trace ? trace + (int64_t)k * trace_stride : nullptr;
-        if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, fixed_rows, s));
+        if (mc.arch == NQS_ARCH_TRANSFORMER) NQS_TRY(tf_cond(mc, P, k, cb, b.U, b, tr, tf, fixed_rows, compose, s));
         else NQS_TRY(launch_cond_rows(mc, P, k, cb, b.U, b.cap, b.p, b.thr, tr, s));
+        if (compose) std::swap(b.ancA, b.ancB);
         if (one_cta) {
             // two launches: draws, then flags / merge / eviction / ancestors and the next step's
             // draw ranges (the first step's come from init_kernel)
@@ -564,7 +571,7 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
                               n_samples, (const int64_t*)b.start, (const int64_t*)b.U, (const uint64_t*)b.thr, b.n1, k,
                               (int64_t)(b.cap + 1)));
             count_launch();
-            const bool anc = b.kv && k + 1 < mc.n;
+            const bool anc = b.kv && k + 1 < mc.n && !compose;
             NQS_CK(launch_pdl(bk_finish_kernel, dim3(1), dim3(BK_T), (size_t)(b.cap * BK_SMEM_PER_ENTRY), s, cb, cc, b.n1,
                               b.pos0, b.pos1, b.U, (uint64_t)(1ull << mc.order[k]), nb, nc, b.kv ? b.par : nullptr,
                               b.kv ? b.par2 : nullptr, max_unique, (const int32_t*)(anc ? b.ancA : nullptr),

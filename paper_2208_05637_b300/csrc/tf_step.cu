@@ -63,6 +63,8 @@ struct FsArgs {
     float* kv;                                  // QKV slabs of every layer and step
     int64_t cap;
     const int32_t* anc;                         // anc[r * n + j]: slot of r's ancestor at step j
+    const int32_t* par;                         // set: anc is the previous step's table (compose)
+    int32_t* anc_new;                           //   and this step's table is written here
     const int64_t* Udev;
     float* p_out;
     uint64_t* thr;
@@ -264,10 +266,22 @@ tf_step_fused_kernel(const __grid_constant__ ModelConst mc, const __grid_constan
     const float* sHead = sPv + L * FS_PV;                // lnf_g | lnf_b | head_w | head_b[k]
     // this row's ancestor slots (the same for every block)
     int32_t* s_s = sS + warp * FS_MAXK;
-    for (int j = lane; j < k; j += 32) {
-        int64_t slot = live ? A.anc[grow * n + j] : 0;
-        slot = slot < 0 ? 0 : (slot >= A.cap ? A.cap - 1 : slot);
-        s_s[j] = (int32_t)slot;
+    if (A.par) {
+        // compose this step's table from the parent's row of the previous one and keep it
+        int64_t p = live ? A.par[grow] : 0;
+        p = p < 0 ? 0 : (p >= A.cap ? A.cap - 1 : p);
+        for (int j = lane; j < k; j += 32) {
+            int64_t slot = j + 1 < k ? (int64_t)A.anc[p * n + j] : p;
+            slot = slot < 0 ? 0 : (slot >= A.cap ? A.cap - 1 : slot);
+            s_s[j] = (int32_t)slot;
+            if (live) A.anc_new[grow * n + j] = (int32_t)slot;
+        }
+    } else {
+        for (int j = lane; j < k; j += 32) {
+            int64_t slot = live ? A.anc[grow * n + j] : 0;
+            slot = slot < 0 ? 0 : (slot >= A.cap ? A.cap - 1 : slot);
+            s_s[j] = (int32_t)slot;
+        }
     }
 
     // ---- embedding and LayerNorm 1 of block 0
@@ -508,6 +522,7 @@ int tf_step_fused(const ModelConst& mc, const float* P, const TfWeights& w, cons
         for (int m = 0; m < 4; ++m) a.woff[l][m] = w.bf16_off[l][m];
     a.bits = bits; a.R = R; a.k = k;
     a.kv = kc.kv; a.cap = kc.cap; a.anc = kc.anc; a.Udev = kc.Udev;
+    a.par = kc.par; a.anc_new = kc.anc_new;
     a.p_out = p_out; a.thr = thr; a.trace = trace;
     const unsigned grid = (unsigned)((R + FS_RB - 1) / FS_RB);
     const int64_t M = R;
