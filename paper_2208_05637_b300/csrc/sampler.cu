@@ -289,7 +289,7 @@ evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
 // For buffers of at most SAMPLER_GRAPH_MAX_CAP entries the per-step bookkeeping runs in two
 // one-CTA kernels around the draws (same results as the multi-kernel sequence above).
 constexpr int BK_T = 1024;
-constexpr int64_t BK_SMEM_PER_ENTRY = sizeof(uint64_t) + sizeof(uint32_t);   // parent bits + merged count
+constexpr int64_t BK_SMEM_PER_ENTRY = sizeof(uint64_t) + 3 * sizeof(uint32_t);   // bits, merged count, ones, zeros
 
 // Exclusive scan of one value per thread across the CTA; *total receives the block sum.
 __device__ int64_t bk_block_scan(int64_t v, int64_t* warp_sums, int64_t* total) {
@@ -341,57 +341,65 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, int64_t* _
                  int64_t cap, int64_t* __restrict__ start_next) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t tot0, tot1;
-    extern __shared__ uint64_t sbits[];              // the U parent bit strings, then cap merged counts
+    // dynamic shared memory: the U parent bit strings, cap merged counts, the parents' ones and
+    // zeros counts (BK_SMEM_PER_ENTRY bytes per buffer entry)
+    extern __shared__ uint64_t sbits[];
     pdl_wait();
     pdl_trigger();
     const int64_t U = *Udev;
     uint32_t* scnt = reinterpret_cast<uint32_t*>(sbits + cap);
-    for (int64_t i = threadIdx.x; i < U; i += BK_T) sbits[i] = cb[i];
-    // flags and their scans
+    uint32_t* s1 = scnt + cap;
+    uint32_t* s0 = s1 + cap;
+    // flags and their scans; the parents' bits and child counts staged (counts < 2^31)
     int64_t c0 = 0, c1 = 0;
     for (int64_t base = 0; base < U; base += BK_T) {
         const int64_t s = base + threadIdx.x;
-        const int64_t f1 = s < U ? (n1[s] > 0) : 0;
-        const int64_t f0 = s < U ? ((cc[s] - n1[s]) > 0) : 0;
-        const int64_t e0 = bk_block_scan(f0, warp_sums, &tot0) + c0;
-        const int64_t e1 = bk_block_scan(f1, warp_sums, &tot1) + c1;
+        int64_t m1 = 0, m0 = 0;
+        if (s < U) {
+            sbits[s] = cb[s];
+            m1 = n1[s];
+            m0 = cc[s] - m1;
+            s1[s] = (uint32_t)m1;
+            s0[s] = (uint32_t)m0;
+        }
+        const int64_t e0 = bk_block_scan(m0 > 0 ? 1 : 0, warp_sums, &tot0) + c0;
+        const int64_t e1 = bk_block_scan(m1 > 0 ? 1 : 0, warp_sums, &tot1) + c1;
         if (s < U) { pos0[s] = e0; pos1[s] = e1; }
         c0 += tot0;
         c1 += tot1;
     }
     if (threadIdx.x == 0) { pos0[U] = c0; pos1[U] = c1; }
     __syncthreads();
-    // merge (as merge_kernel), searching the staged bits
+    int64_t Un = c0 + c1;
+    // merge (as merge_kernel), searching the staged bits: straight into the current buffers when
+    // nothing is evicted (the parents' data is all staged), else into the spare ones
+    const bool direct = Un <= max_unique;
+    uint64_t* ob = direct ? cb : nb;
+    int64_t* oc = direct ? cc : nc;
+    int32_t* op = direct ? par : npar;
     for (int64_t s = threadIdx.x; s < U; s += BK_T) {
-        const int64_t m1 = n1[s], m0 = cc[s] - m1;
+        const int64_t m1 = s1[s], m0 = s0[s];
         const uint64_t bs = sbits[s];
         if (m0 > 0) {
             const int64_t r = pos1[upper_s(sbits, (int)U, qbit, bs)];
-            nb[pos0[s] + r] = bs;
-            nc[pos0[s] + r] = m0;
+            ob[pos0[s] + r] = bs;
+            oc[pos0[s] + r] = m0;
             scnt[pos0[s] + r] = (uint32_t)m0;
-            if (npar) npar[pos0[s] + r] = (int32_t)s;
+            if (npar) op[pos0[s] + r] = (int32_t)s;
         }
         if (m1 > 0) {
             const uint64_t key = bs | qbit;
             const int64_t r = pos0[upper_s(sbits, (int)U, 0, key)];
-            nb[pos1[s] + r] = key;
-            nc[pos1[s] + r] = m1;
+            ob[pos1[s] + r] = key;
+            oc[pos1[s] + r] = m1;
             scnt[pos1[s] + r] = (uint32_t)m1;
-            if (npar) npar[pos1[s] + r] = (int32_t)s;
+            if (npar) op[pos1[s] + r] = (int32_t)s;
         }
     }
     __syncthreads();
-    int64_t Un = c0 + c1;
-    if (Un > max_unique) {
+    if (!direct) {
         evict_block(nb, nc, npar, Un, max_unique, cb, cc, par, scnt);
         Un = max_unique;
-    } else {
-        for (int64_t i = threadIdx.x; i < Un; i += BK_T) {
-            cb[i] = nb[i];
-            cc[i] = nc[i];
-            if (npar) par[i] = npar[i];
-        }
     }
     __syncthreads();
     if (anc_new) {
@@ -412,7 +420,7 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, int64_t* _
         int64_t carry = 0;
         for (int64_t base = 0; base < Un; base += BK_T) {
             const int64_t i = base + threadIdx.x;
-            const int64_t v = i < Un ? cc[i] : 0;
+            const int64_t v = i < Un ? (direct ? (int64_t)scnt[i] : cc[i]) : 0;
             const int64_t ex = bk_block_scan(v, warp_sums, &tot0) + carry;
             if (i < Un) { start_next[i] = ex; n1[i] = 0; }
             carry += tot0;
@@ -541,7 +549,7 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
     const int g = grid_for(b.cap);
     const bool one_cta = b.cap <= SAMPLER_GRAPH_MAX_CAP;
     if (one_cta) {
-        // the parent bits and merged counts staged by bk_finish_kernel take up to 96 KB of shared
+        // the parent bits and counts staged by bk_finish_kernel take up to 160 KB of shared
         // memory; the limit is raised once per device (before any captured launch: the first call
         // is an eager one)
         static int configured_device = -1;
