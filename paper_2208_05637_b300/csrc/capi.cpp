@@ -644,6 +644,11 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
                 m->scache_bytes = (size_t)need;
             }
             sampler_bind_cache(b, m->mc, m->d_scache);
+            // the one-kernel step takes block 0 from the (token, position) tables of this call
+            if (tf_step_fused_supported(m->mc)) {
+                NQS_TRY(tf_tok_tables(m->mc, m->d_params, w, m->mc.n, tb.tab_h, tb.tab_qkv, s));
+                ctx.tok_tables = true;
+            }
         }
     }
     int64_t U = 0;

@@ -263,7 +263,14 @@ struct TfStepCache {
     // this step's slots (anc[par[r]][j] for j < k - 1, par[r] at j = k - 1) and writes them to anc_new
     const int32_t* par = nullptr;
     int32_t* anc_new = nullptr;
+    // optional first-block tables over (token, position) (tf_tok_tables with T = n)
+    const float* tab_h = nullptr;
+    const float* tab_qkv = nullptr;
 };
+// First-block tables of the d_model-64 bf16 models for positions 0..T-1: h0 [3T][64] and the
+// QKV projection of LN1_0(h0) without its bias [3T][192] (rows token * T + t).
+int tf_tok_tables(const ModelConst& mc, const float* P, const TfWeights& w, int T, float* tab_h, float* tab_qkv,
+                  cudaStream_t s);
 int64_t tf_seq_capacity(const ModelConst& mc);
 void tf_layout(Carver& c, const ModelConst& mc, int64_t R, TfBufs& b);
 int64_t tf_bf16_weight_elems(const ModelConst& mc);
@@ -324,6 +331,7 @@ int tc_status_take();
 struct TfCtx {
     const TfWeights* w;
     TfBufs* b;
+    bool tok_tables = false;   // b holds this call's first-block tables for T = n (tf_tok_tables)
 };
 
 // sampler (sampler.cu)

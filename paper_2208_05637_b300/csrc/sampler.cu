@@ -508,6 +508,7 @@ static int tf_cond(const ModelConst& mc, const float* P, int k, const uint64_t* 
         kc.kv = b.kv; kc.cap = b.cap; kc.anc = b.ancA; kc.Udev = Udev;
         if (tf_step_fused_supported(mc)) {
             if (compose) { kc.par = b.par; kc.anc_new = b.ancB; }
+            if (tf->tok_tables) { kc.tab_h = tf->b->tab_h; kc.tab_qkv = tf->b->tab_qkv; }
             return tf_step_fused(mc, P, *tf->w, bits, U, k, kc, b.p, b.thr, trace, s);
         }
         NQS_TRY(tf_step(mc, P, *tf->w, bits, U, k, kc, *tf->b, s));

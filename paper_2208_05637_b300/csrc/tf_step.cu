@@ -65,6 +65,8 @@ struct FsArgs {
     const int32_t* anc;                         // anc[r * n + j]: slot of r's ancestor at step j
     const int32_t* par;                         // set: anc is the previous step's table (compose)
     int32_t* anc_new;                           //   and this step's table is written here
+    const float* tab_h;                         // optional first-block tables over (token, position):
+    const float* tab_qkv;                       //   h0 [3n][64] and q|k|v without bias [3n][192]
     const int64_t* Udev;
     float* p_out;
     uint64_t* thr;
@@ -223,8 +225,9 @@ tf_step_fused_kernel(const __grid_constant__ ModelConst mc, const __grid_constan
     const bool live = grow < U;
     const uint64_t x = A.bits[live ? grow : U - 1];
     // block weights: Wqkv | Wo of block l in group A, W1 | W2 in group B, staged one group ahead
+    const bool tables = A.tab_qkv != nullptr;             // block 0's h and q|k|v from the tables
     auto stage_a = [&](int l) {
-        fs_stage<3 * FS_D, FS_D>(sWqkv, FS_LDW, A.wb + A.woff[l][TF_WQKV], KX * FS_D);
+        if (l > 0 || !tables) fs_stage<3 * FS_D, FS_D>(sWqkv, FS_LDW, A.wb + A.woff[l][TF_WQKV], KX * FS_D);
         fs_stage<FS_D, FS_D>(sWo, FS_LDW, A.wb + A.woff[l][TF_WO], KX * FS_D);
         fs_cp_commit();
     };
@@ -284,8 +287,21 @@ tf_step_fused_kernel(const __grid_constant__ ModelConst mc, const __grid_constan
         }
     }
 
-    // ---- embedding and LayerNorm 1 of block 0
-    {
+    // ---- embedding and LayerNorm 1 of block 0, or block 0's h and q|k|v from the tables
+    if (tables) {
+        const int tok = k == 0 ? 2 : (int)((x >> mc.order[k - 1]) & 1ull);
+        const int64_t trow = (int64_t)tok * n + k;
+        const int c0 = 2 * lane;
+        *reinterpret_cast<float2*>(sH + r * FS_LDH + c0) = *reinterpret_cast<const float2*>(A.tab_h + trow * FS_D + c0);
+        __syncthreads();                                 // the staged bias of block 0
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int c = FS_D * i + c0;
+            const float2 v = *reinterpret_cast<const float2*>(A.tab_qkv + trow * 3 * FS_D + c);
+            const float2 bb = *reinterpret_cast<const float2*>(sPv + fs_pv_start(0) + c);
+            *reinterpret_cast<float2*>(sQ + r * FS_LDQ + c) = make_float2(v.x + bb.x, v.y + bb.y);
+        }
+    } else {
         const int tok = k == 0 ? 2 : (int)((x >> mc.order[k - 1]) & 1ull);
         const int c0 = 2 * lane;
         const float2 e = *reinterpret_cast<const float2*>(P + mc.tok_emb + tok * FS_D + c0);
@@ -302,8 +318,8 @@ tf_step_fused_kernel(const __grid_constant__ ModelConst mc, const __grid_constan
         const float* pv = sPv + l * FS_PV;
         fs_cp_wait<1>();                                     // group A of this block has landed
         __syncthreads();
-        // ---- qkv = a . Wqkv^T + bqkv: 24 n-tiles over the 16 warps
-        {
+        // ---- qkv = a . Wqkv^T + bqkv: 24 n-tiles over the 16 warps (block 0 with tables: done)
+        if (l > 0 || !tables) {
             const float* bq = pv + fs_pv_start(0);
             for (int t = warp; t < 3 * FS_D / 8; t += FS_WARPS) {
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -523,6 +539,7 @@ int tf_step_fused(const ModelConst& mc, const float* P, const TfWeights& w, cons
     a.bits = bits; a.R = R; a.k = k;
     a.kv = kc.kv; a.cap = kc.cap; a.anc = kc.anc; a.Udev = kc.Udev;
     a.par = kc.par; a.anc_new = kc.anc_new;
+    a.tab_h = kc.tab_h; a.tab_qkv = kc.tab_qkv;
     a.p_out = p_out; a.thr = thr; a.trace = trace;
     const unsigned grid = (unsigned)((R + FS_RB - 1) / FS_RB);
     const int64_t M = R;

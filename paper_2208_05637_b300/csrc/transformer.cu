@@ -441,7 +441,7 @@ static int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w,
 // t = 0) are computed too and left unused.
 __global__ void __launch_bounds__(192)
 tok_table_kernel(ModelConst mc, const float* __restrict__ P, const __nv_bfloat16* __restrict__ Wqkv, int ldw, int T,
-                 float* __restrict__ tab_h, float* __restrict__ tab_qkv) {
+                 float* __restrict__ tab_h, float* __restrict__ tab_qkv, int compensated) {
     constexpr int D = 64;
     __shared__ float s_hi[D], s_lo[D];
     const int row = blockIdx.x;                    // token * T + t
@@ -465,7 +465,7 @@ tok_table_kernel(ModelConst mc, const float* __restrict__ P, const __nv_bfloat16
             const float y = (v[i] - mu) * rstd * P[mc.ln1_g[0] + c0 + i] + P[mc.ln1_b[0] + c0 + i];
             const float hi = __bfloat162float(__float2bfloat16_rn(y));
             s_hi[c0 + i] = hi;
-            s_lo[c0 + i] = __bfloat162float(__float2bfloat16_rn(y - hi));
+            s_lo[c0 + i] = compensated ? __bfloat162float(__float2bfloat16_rn(y - hi)) : 0.f;
         }
     }
     __syncthreads();
@@ -573,7 +573,7 @@ static int tf_forward_mode(const ModelConst& mc, const float* P, const TfWeights
             tab_h.tab = b.tab_h;
             ProfScope ps("tf_tok_table", s, 2.0 * 3 * T * 2 * d * 3 * d, 3.0 * T * 4 * d * 4);
             tok_table_kernel<<<3 * T, 192, 0, s>>>(mc, P, reinterpret_cast<const __nv_bfloat16*>(w.bf16 + w.bf16_off[0][TF_WQKV]),
-                                                   2 * d, T, b.tab_h, b.tab_qkv);
+                                                   2 * d, T, b.tab_h, b.tab_qkv, 1);
             NQS_LAUNCHED();
         } else {
             ProfScope ps("tf_layernorm", s, 0.0, ln_bytes);
@@ -719,6 +719,20 @@ int tf_segment_sum(const int64_t* seg, int64_t seg_stride, int64_t nseg, const f
                    int compensated, float* eloc, cudaStream_t s) {
     const int grid = (int)std::min<int64_t>(nseg, (int64_t)num_sms() * 8);
     segment_sum_kernel<<<grid, 128, 0, s>>>(seg, seg_stride, nseg, contrib, compensated, eloc);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int tf_tok_tables(const ModelConst& mc, const float* P, const TfWeights& w, int T, float* tab_h, float* tab_qkv,
+                  cudaStream_t s) {
+    if (mc.hidden != 64 || mc.precision != NQS_PREC_BF16 || T < 1 || T > mc.n) {
+        set_error("token-position tables: d_model 64 bf16 models only");
+        return NQS_ERR_UNSUPPORTED;
+    }
+    const int ldw = mc.compensated ? 2 * mc.hidden : mc.hidden;
+    ProfScope ps("tf_tok_table", s);
+    tok_table_kernel<<<3 * T, 192, 0, s>>>(mc, P, reinterpret_cast<const __nv_bfloat16*>(w.bf16 + w.bf16_off[0][TF_WQKV]),
+                                           ldw, T, tab_h, tab_qkv, mc.compensated ? 1 : 0);
     NQS_LAUNCHED();
     return NQS_OK;
 }
