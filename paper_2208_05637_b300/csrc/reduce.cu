@@ -67,44 +67,58 @@ scan_kernel(const T* __restrict__ in, int64_t n_max, const int64_t* __restrict__
 }
 
 // ---------------------------------------------------------------- energy statistics
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 block sums of up to three values per thread: warp shuffles, then warp 0 over the warp sums.
+__device__ __forceinline__ void block_sum3_f64(double (&v)[3], int nv, double (*red)[32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = 0; q < nv; ++q) v[q] = warp_sum_f64(v[q]);
+    if (lane == 0)
+        for (int q = 0; q < nv; ++q) red[q][warp] = v[q];
+    __syncthreads();
+    if (warp == 0) {
+        for (int q = 0; q < nv; ++q) {
+            const double t = lane < nw ? red[q][lane] : 0.0;
+            red[q][lane] = warp_sum_f64(t);
+        }
+    }
+    __syncthreads();
+    for (int q = 0; q < nv; ++q) v[q] = red[q][0];
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(1024)
 stats_kernel(const float* __restrict__ eloc, const int64_t* __restrict__ counts, int64_t B,
              double* __restrict__ stats, float* __restrict__ g_abs, float* __restrict__ g_phase) {
-    __shared__ double red[3][1024];
-    double w = 0.0, er = 0.0, ei = 0.0;
+    __shared__ double red[3][32];
+    double a[3] = {0.0, 0.0, 0.0};          // W, sum w Re E, sum w Im E
     for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
         const double c = (double)counts[i];
-        w += c;
-        er += c * (double)eloc[2 * i];
-        ei += c * (double)eloc[2 * i + 1];
+        a[0] += c;
+        a[1] += c * (double)eloc[2 * i];
+        a[2] += c * (double)eloc[2 * i + 1];
     }
-    red[0][threadIdx.x] = w; red[1][threadIdx.x] = er; red[2][threadIdx.x] = ei;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st)
-            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
-        __syncthreads();
-    }
-    const double W = red[0][0], mr = red[1][0] / W, mi = red[2][0] / W;
-    __syncthreads();
-    double var = 0.0;
+    block_sum3_f64(a, 3, red);
+    // one FP64 division (the reciprocal of W), products elsewhere
+    const double W = a[0], invW = 1.0 / W, mr = a[1] * invW, mi = a[2] * invW;
+    double v[3] = {0.0, 0.0, 0.0};
     for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
         const double c = (double)counts[i];
         const double dr = (double)eloc[2 * i] - mr, di = (double)eloc[2 * i + 1] - mi;
-        var += c * (dr * dr + di * di);
+        v[0] += c * (dr * dr + di * di);
         if (g_abs) {
-            g_abs[i] = (float)(2.0 * c / W * dr);
-            g_phase[i] = (float)(2.0 * c / W * (double)eloc[2 * i + 1]);
+            const double cw = 2.0 * c * invW;
+            g_abs[i] = (float)(cw * dr);
+            g_phase[i] = (float)(cw * (double)eloc[2 * i + 1]);
         }
     }
-    red[0][threadIdx.x] = var;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[0][threadIdx.x] += red[0][threadIdx.x + st];
-        __syncthreads();
-    }
+    block_sum3_f64(v, 1, red);
     if (threadIdx.x == 0) {
-        stats[0] = mr; stats[1] = mi; stats[2] = red[0][0] / W; stats[3] = W;
+        stats[0] = mr; stats[1] = mi; stats[2] = v[0] * invW; stats[3] = W;
     }
 }
 
