@@ -91,7 +91,7 @@ ln_bwd_kernel(const float* __restrict__ x, const float* __restrict__ g, const fl
     }
 }
 
-// Heads + final LayerNorm backward, one warp per sequence.  Writes dh (gradient wrt the final
+// Heads + final LayerNorm backward, one warp per (sequence, position).  Writes dh (gradient wrt the final
 // residual stream), dy rows and dy*xhat rows of LNf, the LNf outputs hf, the logit deltas dl
 // and the one-hot phase deltas dph.
 template <int DPL>
@@ -103,21 +103,24 @@ heads_bwd_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __r
                  float* __restrict__ dph) {
     const int d = mc.hidden, n = mc.n;
     const int lane = threadIdx.x & 31;
-    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= R) return;
+    // one warp per (sequence, position) row: the rows run in parallel, the constraint's counts of
+    // earlier same-spin ones come from the configuration directly
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= R * n) return;
+    const int64_t r = row / n;
+    const int t = (int)(row - r * n);
     const uint64_t x = bits[r];
     const float ga = g_abs[r], gp = g_phase[r];
     const int sel = (int)(((x >> mc.order[n - 2]) & 1ull) * 2 + ((x >> mc.order[n - 1]) & 1ull));
-    if (lane < 4) dph[r * 4 + lane] = lane == sel ? gp : 0.f;
-    int ones0 = 0, ones1 = 0;
-    for (int t = 0; t < n; ++t) {
-        const int64_t row = r * n + t;
+    if (t == 0 && lane < 4) dph[r * 4 + lane] = lane == sel ? gp : 0.f;
+    {
         const int sp = mc.order[t] & 1;
         const int b = (int)((x >> mc.order[t]) & 1ull);
-        const int c = sp ? ones1 : ones0;
+        int c = 0;
+        for (int u = 0; u < t; ++u)
+            if ((mc.order[u] & 1) == sp) c += (int)((x >> mc.order[u]) & 1ull);
         const int need = sp ? mc.n_dn : mc.n_up;
         const bool free_t = !(c + mc.after[t] < need) && !(c >= need);
-        if (sp) ones1 += b; else ones0 += b;
         float v[DPL];
         float s = 0.f;
 #pragma unroll
@@ -769,7 +772,7 @@ int tf_backward_mode(const ModelConst& mc, const float* P, const uint64_t* bits,
             if (!(phases & 2)) continue;
             // ---- heads and final LayerNorm
             auto ps_heads = std::make_unique<ProfScope>("bwd_heads", s);
-            heads_bwd_kernel<DPL><<<(int)((R + 7) / 8), 256, 0, s>>>(mc, P, xb, b.Hin[L], R, g_abs + lo, g_phase + lo,
+            heads_bwd_kernel<DPL><<<(int)((M + 7) / 8), 256, 0, s>>>(mc, P, xb, b.Hin[L], R, g_abs + lo, g_phase + lo,
                                                                       b.dH[L], b.dSh, b.GXh, b.HF, b.DL, b.DPH);
             NQS_LAUNCHED();
             NQS_TRY(fork());
