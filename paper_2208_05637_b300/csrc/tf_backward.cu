@@ -449,7 +449,8 @@ __global__ void embed_bwd_partial_kernel(ModelConst mc, const uint64_t* __restri
     const int64_t r0 = (int64_t)blockIdx.y * EB_ROWS, r1 = min(R, r0 + EB_ROWS);
     if (j >= d) return;
     float s0 = 0.f, s1 = 0.f;
-    for (int64_t r = r0; r < r1; ++r) {
+#pragma unroll 8
+    for (int64_t r = r0; r < r1; ++r) {            // unrolled: the loads fly together, the sums keep their order
         const float g = dh[(r * n + t) * d + j];
         const bool one = t > 0 && ((bits[r] >> mc.order[t - 1]) & 1ull);
         if (one) s1 += g; else s0 += g;
@@ -471,15 +472,18 @@ __global__ void embed_bwd_final_kernel(ModelConst mc, const float* __restrict__ 
     float s = 0.f;
     if (e < n * d) {
         const int t = e / d;
+#pragma unroll 8
         for (int c = 0; c < nchunks; ++c) s += at(c, t, 0) + at(c, t, 1);
         grad[mc.pos_emb + e] += s;
         return;
     }
     const int k = e / d - n;   // token id
     if (k == 2) {
+#pragma unroll 8
         for (int c = 0; c < nchunks; ++c) s += at(c, 0, 0);
     } else {
         for (int c = 0; c < nchunks; ++c)
+#pragma unroll 8
             for (int t = 1; t < n; ++t) s += at(c, t, k);
     }
     grad[mc.tok_emb + k * d + j] += s;
