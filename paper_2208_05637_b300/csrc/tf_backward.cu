@@ -231,8 +231,9 @@ attention_bwd_kernel(const float* __restrict__ qkv, const float* __restrict__ do
     for (int i = threadIdx.x; i < T * DH; i += blockDim.x) {
         const int t = i / DH, j = i % DH;
         float dq = 0.f, dk = 0.f, dv = 0.f;
-        for (int u = 0; u < T; ++u) {
-            dq = fmaf(dp[t * lp + u], k[u * LD + j], dq);      // dS[t][u] k[u]
+        // causal: dS[t][u] and P[t][u] vanish for u > t
+        for (int u = 0; u <= t; ++u) dq = fmaf(dp[t * lp + u], k[u * LD + j], dq);   // dS[t][u] k[u]
+        for (int u = t; u < T; ++u) {
             dk = fmaf(dp[u * lp + t], q[u * LD + j], dk);      // dS[u][t] q[u]
             dv = fmaf(p[u * lp + t], go[u * LD + j], dv);      // P[u][t] dO[u]
         }
