@@ -12,8 +12,12 @@ from .pauli import matrix_element
 from .models import in_sector
 
 
-def local_energy(model, xm, zm, c, bits, term_chunk: int = 1 << 16) -> np.ndarray:
-    """Complex E_loc for each sample in bits (uint64[B]) in FP64."""
+def local_energy(model, xm, zm, c, bits, term_chunk: int = 1 << 16, return_abs: bool = False):
+    """Complex E_loc for each sample in bits (uint64[B]) in FP64.
+
+    With return_abs, also returns A[B] = sum_k |c_k <x|P_k|x^k> f(x^k)/f(x)|, the sum of the
+    magnitudes of the terms (the conditioning of the sum: an FP32 evaluation of the same terms
+    carries rounding errors of order A times the unit roundoff)."""
     xm = np.asarray(xm, dtype=np.uint64)
     zm = np.asarray(zm, dtype=np.uint64)
     c = np.asarray(c, dtype=np.float64)
@@ -21,6 +25,7 @@ def local_energy(model, xm, zm, c, bits, term_chunk: int = 1 << 16) -> np.ndarra
     n = model.n
     la_x, ph_x = model.log_psi(bits)
     out = np.zeros(len(bits), dtype=np.complex128)
+    mag = np.zeros(len(bits), dtype=np.float64)
     for i, x in enumerate(bits):
         xp = x ^ xm
         ok = in_sector(xp, n, model.n_up, model.n_dn)
@@ -29,12 +34,16 @@ def local_energy(model, xm, zm, c, bits, term_chunk: int = 1 << 16) -> np.ndarra
         ratio = np.zeros(len(xm), dtype=np.complex128)
         ratio[ok] = np.exp((la[inv] - la_x[i]) + 1j * (ph[inv] - ph_x[i]))
         total = 0.0 + 0.0j
+        absum = 0.0
         for lo in range(0, len(xm), term_chunk):
             sl = slice(lo, lo + term_chunk)
             elem = matrix_element(x, xm[sl], zm[sl], n)
-            total += np.sum(c[sl] * elem * ratio[sl])
+            terms = c[sl] * elem * ratio[sl]
+            total += np.sum(terms)
+            absum += np.sum(np.abs(terms))
         out[i] = total
-    return out
+        mag[i] = absum
+    return (out, mag) if return_abs else out
 
 
 def connected_count(model, xm, bits) -> np.ndarray:

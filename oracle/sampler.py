@@ -76,13 +76,22 @@ def sample(p_fn, n: int, order, n_samples: int, max_unique: int, seed: int, trac
         keep = cc > 0
         cb, cc = cb[keep], cc[keep]
         idx = np.argsort(cb, kind="stable")
-        cb, cc = cb[idx], cc[idx]
-        if len(cb) > max_unique:
-            top = np.lexsort((cb, -cc))[:max_unique]
-            top = top[np.argsort(cb[top], kind="stable")]
-            cb, cc = cb[top], cc[top]
-        bits, counts = cb, cc
+        bits, counts = evict(cb[idx], cc[idx], max_unique)
     return bits, counts
+
+
+def evict(bits, counts, max_unique: int):
+    """Eviction of the buffer (Section 4, Sampling: the entries with the lowest numbers of
+    occurrences are dropped): if more than max_unique entries remain, keep the max_unique with
+    the highest counts, ties broken by bits ascending (a reading: the paper names no
+    tie-break).  Input and output are in bits-ascending order."""
+    bits = np.asarray(bits, dtype=np.uint64)
+    counts = np.asarray(counts, dtype=np.int64)
+    if len(bits) <= max_unique:
+        return bits, counts
+    top = np.lexsort((bits, -counts))[:max_unique]
+    top = top[np.argsort(bits[top], kind="stable")]
+    return bits[top], counts[top]
 
 
 def model_p_fn(model):

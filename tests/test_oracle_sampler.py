@@ -8,7 +8,7 @@ from scipy import stats
 import synth
 from oracle.lanczos import sector_states
 from oracle.models import in_sector
-from oracle.sampler import philox4x32_10, sample, model_p_fn, threshold
+from oracle.sampler import bernoulli_ones, evict, philox4x32_10, sample, model_p_fn, threshold
 from tests.common import oracle_model
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -95,3 +95,65 @@ def test_sampler_single_nominal_sample_follows_draws():
         if int(u) < int(threshold(p)[0]):
             x |= np.uint64(1) << np.uint64(model.order[k])
     assert counts.tolist() == [1] and bits.tolist() == x.tolist()
+
+
+def test_eviction_rule_on_a_hand_built_buffer():
+    # Section 4, Sampling: the entries with the lowest numbers of occurrences are evicted; the
+    # tie-break (bits ascending) is this build's reading.  The survivors below are written by
+    # hand from that rule: counts 7 (bits 3) and 4 (bits 5) first, then the count-2 tie among
+    # bits 1, 7, 9 in ascending bit order, then the count-1 tie among bits 2 and 12.
+    bits = np.array([1, 2, 3, 5, 7, 9, 12], dtype=np.uint64)
+    counts = np.array([2, 1, 7, 4, 2, 2, 1], dtype=np.int64)
+    want = {
+        1: ([3], [7]),
+        2: ([3, 5], [7, 4]),
+        3: ([1, 3, 5], [2, 7, 4]),
+        4: ([1, 3, 5, 7], [2, 7, 4, 2]),
+        5: ([1, 3, 5, 7, 9], [2, 7, 4, 2, 2]),
+        6: ([1, 2, 3, 5, 7, 9], [2, 1, 7, 4, 2, 2]),
+        7: ([1, 2, 3, 5, 7, 9, 12], [2, 1, 7, 4, 2, 2, 1]),
+        9: ([1, 2, 3, 5, 7, 9, 12], [2, 1, 7, 4, 2, 2, 1]),
+    }
+    for mu, (wb, wc) in want.items():
+        b, c = evict(bits, counts, mu)
+        assert b.tolist() == wb and c.tolist() == wc, mu
+
+
+def test_sampler_applies_the_eviction_rule_at_the_step_that_overflows():
+    # A step-dependent p makes the buffer overflow only at the last step: p = 1/2 at steps 0
+    # and n-1, p = 0 in between (no split).  The sampler with max_unique = 2 must then equal
+    # the unevicted run cut by the hand-pinned rule above, and the seed is chosen so that the
+    # cut falls inside a tie of counts (so the bits-ascending tie-break decides).
+    n, N = 6, 40
+    order = np.arange(n)[::-1]
+
+    def p_fn(parent_bits, k):
+        return np.full(len(parent_bits), 0.5 if k in (0, n - 1) else 0.0, dtype=np.float32)
+
+    seed = None
+    for s in range(1, 400):
+        b_all, c_all = sample(p_fn, n, order, N, 1 << 30, s)
+        srt = np.sort(c_all)[::-1]
+        if len(c_all) == 4 and srt[1] == srt[2]:
+            seed = s
+            break
+    assert seed is not None
+    b_all, c_all = sample(p_fn, n, order, N, 1 << 30, seed)
+    b2, c2 = sample(p_fn, n, order, N, 2, seed)
+    wb, wc = evict(b_all, c_all, 2)
+    assert b2.tolist() == wb.tolist() and c2.tolist() == wc.tolist()
+    # the tie at the cut is broken toward the smaller bitstring
+    tied = np.sort(c_all)[::-1][1]
+    cand = b_all[c_all == tied]
+    assert cand.min() in b2 and cand.max() not in b2
+
+
+def test_nominal_indices_after_eviction_run_over_the_survivors():
+    # after an eviction the surviving parents own consecutive nominal indices from 0 in
+    # bits-ascending order (the dropped entries' draws are not consumed)
+    counts = np.array([3, 5, 2], dtype=np.int64)
+    thr = threshold(np.array([0.5, 0.25, 0.75], dtype=np.float32))
+    seed, k = 99, 4
+    u = philox4x32_10(np.arange(10), k, 0, 0, seed & 0xFFFFFFFF, seed >> 32)[0]
+    want = [int(np.sum(u[0:3] < thr[0])), int(np.sum(u[3:8] < thr[1])), int(np.sum(u[8:10] < thr[2]))]
+    assert bernoulli_ones(counts, thr, k, seed).tolist() == want
