@@ -120,6 +120,18 @@ int nqs_model_param_info(nqs_model_t model, int index, const char** name, int64_
  * reads it at execution time, so updates (e.g. nqs_adam_step) take effect without rebinding. */
 int nqs_model_bind_params(nqs_model_t model, const float* params_device);
 
+/* Prefix reuse of the transformer local energy (Section 5.1's unique flippings carried over to
+ * prefixes: the network's row at sampling position t depends on the bits before t only, so a
+ * connected x' shares its rows before its first flip with the sample x, and x' with the same
+ * first flips share more).  depth 0: every x' evaluated from position 0; 1: x's keys and values
+ * reused up to the first flip; 2: also strings carrying each sample's first flip; 3: also its
+ * first two flips; -1 (default): automatic -- depth 3, or, when the particle-number sector holds
+ * fewer configurations than one 1024-sample chunk has connected rows, the per-chunk hash
+ * deduplication of x' instead.  The local energies do not depend on the depth, bit for bit;
+ * the workspace does (query nqs_workspace_size after setting it).  Transformer models only
+ * (NQS_ERR_UNSUPPORTED otherwise); NQS_ERR_INVALID_ARG outside -1..3. */
+int nqs_model_set_prefix_reuse(nqs_model_t model, int depth);
+
 void nqs_model_destroy(nqs_model_t model);
 
 /* Workspace bytes that `op` (NQS_OP_*) needs for `batch` rows: samples for LOGPSI,
@@ -155,8 +167,8 @@ int nqs_logpsi(nqs_model_t model, const uint64_t* bits, int64_t B, float* log_ab
 
 /* Term sweep alone (Eq. mtx_element on grouped strings): for each sample x_i (device,
  * in the model's sector) and each group g whose flip x' = x_i ^ m_g stays in the sector,
- * S_g(x_i) = sum_{k in g} c'_k (-1)^{popcount(x_i & z_k)}.  Rows are written per sample in
- * group order: row_offset[B+1] (device int64), xprime[row], s_re[row], s_im[row] (device;
+ * S_g(x_i) = sum_{k in g} c'_k (-1)^{popcount(x_i & z_k)}.  A sample outside the sector gets
+ * one row, x' = x_i with S = NaN + i NaN.  Rows are written per sample in group order: row_offset[B+1] (device int64), xprime[row], s_re[row], s_im[row] (device;
  * fp32), capacity rows at most.  If the row count exceeds capacity, returns NQS_ERR_CAPACITY
  * with *n_rows = the count and no rows written.  n_up, n_dn: the sector.  Synchronises
  * `stream` once (to size the output). */
@@ -167,7 +179,8 @@ int nqs_term_sweep(nqs_ham_t ham, int n_up, int n_dn, int compensated, const uin
 /* Local energy (Eq. local_energy_auto; Algorithm 1) for B device bitstrings in the model's
  * sector: eloc[2*i], eloc[2*i+1] (device fp32) = Re, Im of
  *   l(x_i) = sum_g S_g(x_i) f(x_i ^ m_g) / f(x_i)
- * over the in-sector flips (out-of-sector flips have f = 0 under the constraint).  The
+ * over the in-sector flips (out-of-sector flips have f = 0 under the constraint).  A sample
+ * outside the sector gets NaN (it has f(x_i) = 0, so l(x_i) is undefined).  The
  * network is evaluated on every connected x' with the ratio-weighted reduction fused into its
  * epilogue.  Synchronises `stream` once per internal sample chunk (to size the x' stream). */
 int nqs_local_energy(nqs_ham_t ham, nqs_model_t model, const uint64_t* bits, int64_t B,
@@ -200,6 +213,17 @@ int nqs_logpsi_backward_phase(nqs_model_t model, int phase, const uint64_t* bits
 int nqs_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
                      float* g_abs, float* g_phase, void* stream);
 
+/* Per-rank pieces of the data-parallel VMC gradient (Section 5: the B*K summands are split over
+ * L GPUs and the gradients averaged).  sums[0..3] (device double) = sum_i w_i Re E_i,
+ * sum_i w_i Im E_i, sum_i w_i |E_i|^2 and W = sum_i w_i over this rank's B samples (weights =
+ * counts).  If the three device fp32 arrays are given they receive the upstream gradients
+ * g_abs_e[i] = 2 w_i Re E_i, g_phase_e[i] = 2 w_i Im E_i and g_abs_w[i] = w_i: the backward
+ * (nqs_logpsi_backward) with (g_abs_e, g_phase_e) gives the sum `first`, with (g_abs_w, 0) the
+ * sum `second`, and after one all-reduce of [sums, first, second] over the ranks the gradient of
+ * Eq. grad is (first - 2 Re(E_bar) second) / W with E_bar = (sums[0] + i sums[1]) / W. */
+int nqs_energy_sums(const float* eloc, const int64_t* counts, int64_t B, double* sums, float* g_abs_e,
+                    float* g_phase_e, float* g_abs_w, void* stream);
+
 /* One Adam update (Section 5.1) in place on device fp32 arrays of n elements; step is the
  * 1-based iteration number. */
 int nqs_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int step,
@@ -230,7 +254,10 @@ int nqs_gemm_bf16(const void* A, const void* W, const float* bias, void* C, int6
  *   Limit: the B per-sample log psi values plus one chunk of at least one sample's sweep rows
  *   must fit in the scratch; larger requests return NQS_ERR_CAPACITY with a message.
  *   The first call on a device looks up the scratch's device address (cudaGetSymbolAddress)
- *   with that device current; make it before any stream capture.  Every call reuses the same
+ *   with that device current.  Under lazy module loading (CUDA's default since 12.2) that
+ *   lookup loads the library's device module, which is when the array is allocated: make the
+ *   first call on each device outside any no-allocation region and before any stream capture.
+ *   Every call reuses the same
  *   array: calls whose GPU work overlaps (other streams or host threads) race on it and must be
  *   serialised by the caller.  Asynchronous on `stream`. */
 int nqs_local_energy_noalloc(nqs_ham_t ham, nqs_model_t model, const uint64_t* bits, int64_t B,
@@ -253,6 +280,17 @@ int nqs_profile_read(const char* kernel, double* total_ms, int64_t* launches);
  * "tf_gemm" 2*M*N*K FLOPs (the compensated split's second pass not counted) and the bytes of A,
  * W, C (and C read back for a residual add); 0 where no figure is attached. */
 int nqs_profile_work(const char* kernel, double* flops, double* bytes);
+
+/* Diagnostic: measured issue rates of the SM pipes that bound the term sweep and the fp32
+ * network, in instructions per SM per clock cycle: out[0] 32-bit population count (each probe
+ * instruction is paired with one logic op), out[1] three-input logic (LOP3), out[2] 32-bit
+ * integer add, out[3] fp32 fused multiply-add.  One CTA of 1024 threads per SM runs eight
+ * independent chains of the instruction; the rate is the CTA's instruction count over its own
+ * elapsed SM cycles (median over the SMs), so it does not depend on the clock frequency.  The
+ * paper has no counterpart: these are the denominators of the rooflines of Section 5.1's
+ * operator-matrix evaluation on this GPU.  Synchronous; allocates and frees two small device
+ * buffers.  per_sm_per_clock: host double[4]. */
+int nqs_probe_pipes(double* per_sm_per_clock);
 
 /* Number of kernels this library has launched in the calling process (all streams). */
 int64_t nqs_launch_count(void);

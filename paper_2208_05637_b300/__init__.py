@@ -36,7 +36,8 @@ EXPORTED = [
     "nqs_model_bind_params", "nqs_model_destroy", "nqs_workspace_size", "nqs_sample",
     "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward", "nqs_logpsi_backward_phase",
     "nqs_energy_stats", "nqs_adam_step", "nqs_strerror", "nqs_last_error", "nqs_profile_enable",
-    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16", "nqs_profile_work",
+    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16", "nqs_profile_work", "nqs_probe_pipes", "nqs_model_set_prefix_reuse",
+    "nqs_energy_sums",
 ]
 
 
@@ -82,6 +83,9 @@ _sig = {
     "nqs_local_energy_noalloc": [_P, _P, _P, _I64, _P, _P],
     "nqs_gemm_bf16": [_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P],
     "nqs_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "nqs_probe_pipes": [_P],
+    "nqs_model_set_prefix_reuse": [_P, ctypes.c_int],
+    "nqs_energy_sums": [_P, _P, _I64, _P, _P, _P, _P, _P],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -140,6 +144,13 @@ def profile_work(kernel: str):
     w = ctypes.c_double(); b = ctypes.c_double()
     _check(_lib.nqs_profile_work(kernel.encode(), ctypes.byref(w), ctypes.byref(b)), "nqs_profile_work")
     return w.value, b.value
+
+
+def probe_pipes():
+    """Measured SM pipe rates (instructions per SM per clock): dict with popc, lop3, iadd, ffma."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.nqs_probe_pipes(ctypes.cast(out, _P)), "nqs_probe_pipes")
+    return dict(popc=out[0], lop3=out[1], iadd=out[2], ffma=out[3])
 
 
 # ----------------------------------------------------------------- Hamiltonian
@@ -237,6 +248,10 @@ class Model:
         _check(_lib.nqs_model_bind_params(self.handle, _ptr(params)), "nqs_model_bind_params")
         self.params = params
 
+    def set_prefix_reuse(self, depth: int):
+        """Prefix reuse depth of the transformer local energy (-1 automatic, 0..3; include/nqs.h)."""
+        _check(_lib.nqs_model_set_prefix_reuse(self.handle, int(depth)), "nqs_model_set_prefix_reuse")
+
     def workspace(self, op, batch, ham=None):
         import torch
         n = ctypes.c_size_t()
@@ -291,9 +306,10 @@ def nqs_term_sweep(ham, n_up, n_dn, bits, compensated=True, capacity=None, strea
     K, G = ham.info()
     cap = B * G if capacity is None else int(capacity)
     size = ctypes.c_size_t()
-    # workspace: counts, offsets and the compensated sums of every feasible row
+    # workspace: counts, offsets, the count pass's validity words (one per group and 32-sample
+    # batch) and the compensated sums of every feasible row
     T = (G + 255) // 256
-    wsz = 4 * B * T + 8 * (B * T + 1) + 16 * B * G + 3 * 256
+    wsz = 4 * B * T + 8 * (B * T + 1) + 4 * max(1, -(-B // 32)) * T * 256 + 16 * B * G + 4 * 256
     ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
     row_offset = torch.empty(B + 1, dtype=torch.int64, device="cuda")
     xp = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
@@ -370,6 +386,18 @@ def nqs_energy_stats(eloc, counts, with_weights=True, stream=None):
     _check(_lib.nqs_energy_stats(_ptr(eloc), _ptr(counts), B, _ptr(stats), _ptr(ga), _ptr(gp),
                                  _stream(stream)), "nqs_energy_stats")
     return stats, ga, gp
+
+
+def nqs_energy_sums(eloc, counts, with_weights=True, stream=None):
+    """(sums fp64[4] = sum w Re E, sum w Im E, sum w |E|^2, W; g_abs_e, g_phase_e, g_abs_w) on the
+    device: the per-rank pieces of the data-parallel gradient (include/nqs.h)."""
+    import torch
+    B = counts.numel()
+    sums = torch.empty(4, dtype=torch.float64, device="cuda")
+    ws = [torch.empty(B, dtype=torch.float32, device="cuda") for _ in range(3)] if with_weights else [None] * 3
+    _check(_lib.nqs_energy_sums(_ptr(eloc), _ptr(counts), B, _ptr(sums), *(_ptr(w) for w in ws), _stream(stream)),
+           "nqs_energy_sums")
+    return (sums, *ws)
 
 
 def nqs_adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.99, eps=1e-8, stream=None):

@@ -72,6 +72,8 @@ ProfScope::~ProfScope() {
     g_prof_pending.push_back({name, e0, e1, work, bytes});
 }
 
+bool prof_enabled() { return g_prof_on; }
+
 static void prof_drain() {
     for (auto& r : g_prof_pending) {
         cudaEventSynchronize(r.b);
@@ -89,12 +91,6 @@ static void prof_drain() {
 }
 
 // ------------------------------------------------------------------ helpers
-static uint64_t spin_mask(int n, int spin) {
-    uint64_t m = 0;
-    for (int j = spin; j < n; j += 2) m |= (1ull << j);
-    return m;
-}
-
 static int check_device_ptr(const void* p, const char* what) {
     if (!p) {
         set_error(std::string(what) + " is NULL");
@@ -103,7 +99,6 @@ static int check_device_ptr(const void* p, const char* what) {
     return NQS_OK;
 }
 
-// Groups whose flip can keep some sector state inside the sector.
 // Number of configurations with n_up and n_dn electrons in n / 2 orbitals per spin (saturating
 // at 2^62): the most distinct x' a local-energy chunk can have.
 static int64_t sector_dim(int n, int n_up, int n_dn) {
@@ -116,49 +111,70 @@ static int64_t sector_dim(int n, int n_up, int n_dn) {
     return v >= 4.6e18 ? (int64_t)1 << 62 : (int64_t)(v + 0.5);
 }
 
-static int64_t feasible_groups(const nqs_ham_s* h, int n_up, int n_dn) {
-    int n_orb = h->n / 2;
-    int64_t cnt = 0;
-    for (int64_t g = 0; g < h->G; ++g) {
-        int na = h->grp_meta[g] & 0xff, nb = (h->grp_meta[g] >> 8) & 0xff;
-        if ((na & 1) || (nb & 1)) continue;
-        if (na / 2 > std::min(n_up, n_orb - n_up)) continue;
-        if (nb / 2 > std::min(n_dn, n_orb - n_dn)) continue;
-        ++cnt;
-    }
-    return std::max<int64_t>(cnt, 1);
-}
 
 constexpr int64_t ELOC_CHUNK = 1024;   // samples per local-energy chunk
+
+// The term sweep of nb samples: count pass, row offsets, emit pass (rows sample-major).
+static int sweep_chunk(const nqs_ham_s* h, int n_up, int n_dn, int compensated, const uint64_t* bits, int64_t nb,
+                       int32_t* cnt, int64_t* off, uint32_t* valid, uint64_t* xprime, float4* S, cudaStream_t s) {
+    {
+        ProfScope ps("sweep_count", s);
+        NQS_TRY(launch_sweep_count(h->dev, n_up, n_dn, bits, nb, cnt, valid, s));
+    }
+    NQS_TRY(launch_scan_i32(cnt, nb * sweep_tiles(h->dev), off, s));
+    ProfScope ps("term_sweep", s);
+    return launch_sweep_emit(h->dev, n_up, n_dn, compensated, bits, nb, off, valid, xprime, S, s);
+}
 
 struct ElocBufs {
     float *la, *ph;
     int32_t* cnt;
     int64_t* off;
+    uint32_t* valid;     // the count pass's validity words
     uint64_t* xprime;
     float4* S;
     float2* contrib;     // transformer: per-row ratio-weighted contributions
     TfBufs tf;
     DedupBufs dd;        // transformer: the chunk's distinct x'
+    ChainBufs ch;        // transformer: prefix sharing
     bool dedup;          // x' dedup applies (the all-ones word is then no configuration)
+    int chain_depth;     // prefix sharing at this depth (0..3), or -1
     int64_t chunk, ntiles, rows_cap;
 };
 
+// Prefix-sharing depth of the transformer local energy (-1: the hash dedup path).  Automatic:
+// the dedup when the sector holds fewer configurations than a chunk has connected rows (they
+// then repeat a lot), prefix sharing at depth 3 otherwise.
+static int chain_depth_for(const nqs_model_s* m, const nqs_ham_s* h) {
+    if (m->mc.arch != NQS_ARCH_TRANSFORMER) return -1;
+    if (m->prefix_depth >= 0) return m->prefix_depth;
+    if (m->mc.n_up + m->mc.n_dn >= m->mc.n) return 3;     // the dedup's empty key is a configuration
+    const int64_t rows = ELOC_CHUNK * feasible_groups(h, m->mc.n_up, m->mc.n_dn);
+    return sector_dim(m->mc.n, m->mc.n_up, m->mc.n_dn) > rows ? 3 : -1;
+}
+
 static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int64_t B,
                         ElocBufs& e) {
-    e.chunk = std::max<int64_t>(1, std::min(B, ELOC_CHUNK));
+    e.chain_depth = chain_depth_for(m, h);
+    const int64_t chunk_max = e.chain_depth >= 0 ? chain_chunk(m->mc, e.chain_depth) : ELOC_CHUNK;
+    e.chunk = std::max<int64_t>(1, std::min(B, chunk_max));
     e.ntiles = sweep_tiles(h->dev);
     e.rows_cap = e.chunk * feasible_groups(h, m->mc.n_up, m->mc.n_dn);
     e.la = c.take<float>(std::max<int64_t>(B, 1));
     e.ph = c.take<float>(std::max<int64_t>(B, 1));
     e.cnt = c.take<int32_t>(e.chunk * e.ntiles);
     e.off = c.take<int64_t>(e.chunk * e.ntiles + 1);
+    e.valid = c.take<uint32_t>(sweep_valid_words(h->dev, e.chunk));
     e.xprime = c.take<uint64_t>(e.rows_cap);
     e.S = c.take<float4>(e.rows_cap);
     e.contrib = nullptr;
     e.dedup = false;
     if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
         e.contrib = c.take<float2>(e.rows_cap);
+        if (e.chain_depth >= 0) {
+            chain_layout(c, m->mc, e.chain_depth, e.chunk, e.rows_cap, e.ch);
+            return;
+        }
         tf_layout(c, m->mc, std::min(std::max<int64_t>(B, e.rows_cap), tf_seq_capacity(m->mc)), e.tf);
         e.dedup = m->mc.n_up + m->mc.n_dn < m->mc.n;
         if (e.dedup) dedup_layout(c, e.rows_cap, e.chunk, e.dd);
@@ -313,9 +329,10 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     if (h->K > (int64_t)0xffffffffll) { delete h; set_error("too many terms"); return NQS_ERR_UNSUPPORTED; }
 
     // device copy: one allocation, arrays 256-byte aligned
+    // the term arrays carry one zero padding term (the sweep stages even-aligned ranges)
     Carver c(nullptr);
     c.take<uint64_t>(h->G); c.take<uint32_t>(h->G + 1); c.take<uint32_t>(h->G);
-    c.take<uint64_t>(h->K); c.take<float2>(h->K);
+    c.take<uint64_t>(h->K + 1); c.take<float2>(h->K + 1);
     cudaGetDevice(&h->device);
     if (cudaMalloc(&h->d_block, c.used) != cudaSuccess) {
         cudaGetLastError();
@@ -327,10 +344,12 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     auto* d_mask = d.take<uint64_t>(h->G);
     auto* d_off = d.take<uint32_t>(h->G + 1);
     auto* d_meta = d.take<uint32_t>(h->G);
-    auto* d_z = d.take<uint64_t>(h->K);
-    auto* d_c = d.take<float2>(h->K);
+    auto* d_z = d.take<uint64_t>(h->K + 1);
+    auto* d_c = d.take<float2>(h->K + 1);
     std::vector<uint32_t> off32(h->grp_off.begin(), h->grp_off.end());
-    std::vector<float2> cc(h->K);
+    std::vector<float2> cc(h->K + 1, make_float2(0.f, 0.f));
+    std::vector<uint64_t> zz(h->term_z);
+    zz.push_back(0);
     for (int64_t k = 0; k < h->K; ++k) {
         float hi = (float)c_signed[k];
         float lo = (float)(c_signed[k] - (double)hi);
@@ -340,8 +359,8 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     if (e == cudaSuccess) e = cudaMemcpy(d_mask, h->grp_mask.data(), h->G * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_off, off32.data(), (h->G + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_meta, h->grp_meta.data(), h->G * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_z, h->term_z.data(), h->K * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_c, cc.data(), h->K * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_z, zz.data(), (h->K + 1) * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_c, cc.data(), (h->K + 1) * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(h->d_block);
         delete h;
@@ -412,6 +431,7 @@ int nqs_model_create(const nqs_model_desc* d, nqs_model_t* out) {
     mc.precision = d->precision; mc.compensated = d->compensated;
     for (int t = 0; t < n; ++t) {
         mc.order[t] = (uint8_t)d->order[t];
+        mc.pos[d->order[t]] = (uint8_t)t;
         int cnt = 0;
         for (int u = t + 1; u < n; ++u) cnt += ((d->order[u] & 1) == (d->order[t] & 1));
         mc.after[t] = (uint8_t)cnt;
@@ -527,6 +547,13 @@ static void graph_release(SamplerGraph& g) {
     g.exec = nullptr;
 }
 
+int nqs_model_set_prefix_reuse(nqs_model_t m, int depth) {
+    if (!m || depth < -1 || depth > 3) { set_error("need a model and depth in -1..3"); return NQS_ERR_INVALID_ARG; }
+    if (m->mc.arch != NQS_ARCH_TRANSFORMER) { set_error("prefix reuse applies to the transformer"); return NQS_ERR_UNSUPPORTED; }
+    m->prefix_depth = depth;
+    return NQS_OK;
+}
+
 void nqs_model_destroy(nqs_model_t m) {
     if (!m) return;
     graph_release(m->graph);
@@ -568,6 +595,7 @@ int nqs_workspace_size(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, size_t
             int64_t T = sweep_tiles(h->dev);
             c.take<int32_t>(std::max<int64_t>(batch, 1) * T);
             c.take<int64_t>(std::max<int64_t>(batch, 1) * T + 1);
+            c.take<uint32_t>(sweep_valid_words(h->dev, std::max<int64_t>(batch, 1)));
             c.take<float4>(std::max<int64_t>(batch, 1) * feasible_groups(h, m->mc.n_up, m->mc.n_dn));
             break;
         }
@@ -761,17 +789,18 @@ int nqs_term_sweep(nqs_ham_t h, int n_up, int n_dn, int compensated, const uint6
     int64_t T = sweep_tiles(h->dev);
     Carver need(nullptr);
     need.take<int32_t>(B * T); need.take<int64_t>(B * T + 1);
+    need.take<uint32_t>(sweep_valid_words(h->dev, B));
     need.take<float4>(B * feasible_groups(h, n_up, n_dn));
     if (!ws || ws_bytes < need.used) { set_error("workspace too small"); return NQS_ERR_WORKSPACE; }
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     int32_t* cnt = c.take<int32_t>(B * T);
     int64_t* off = c.take<int64_t>(B * T + 1);
+    uint32_t* valid = c.take<uint32_t>(sweep_valid_words(h->dev, B));
     float4* S = c.take<float4>(B * feasible_groups(h, n_up, n_dn));
-    const uint64_t A = spin_mask(h->n, 0), Bm = spin_mask(h->n, 1);
     {
         ProfScope ps("sweep_count", s);
-        NQS_TRY(launch_sweep_count(h->dev, A, Bm, n_up, n_dn, bits, B, cnt, s));
+        NQS_TRY(launch_sweep_count(h->dev, n_up, n_dn, bits, B, cnt, valid, s));
     }
     NQS_TRY(launch_scan_i32(cnt, B * T, off, s));
     int64_t total = 0;
@@ -782,10 +811,11 @@ int nqs_term_sweep(nqs_ham_t h, int n_up, int n_dn, int compensated, const uint6
     if (total > 0 && (!xprime || !s_re || !s_im)) { set_error("xprime/s_re/s_im is NULL"); return NQS_ERR_INVALID_ARG; }
     {
         ProfScope ps("term_sweep", s);
-        NQS_TRY(launch_sweep_emit(h->dev, A, Bm, n_up, n_dn, compensated, bits, B, off, xprime, S, s));
+        NQS_TRY(launch_sweep_emit(h->dev, n_up, n_dn, compensated, bits, B, off, valid, xprime, S, s));
     }
     NQS_TRY(launch_unpack_rows(off, T, B, S, row_offset, s_re, s_im, capacity, off + B * T, s));
-    return NQS_OK;
+    NQS_CK(cudaStreamSynchronize(s));
+    return tc_status_take();
 }
 
 int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B, float* eloc,
@@ -800,7 +830,24 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
     Carver c(ws);
     ElocBufs e;
     eloc_layout(c, m, h, B, e);
-    const uint64_t A = spin_mask(h->n, 0), Bm = spin_mask(h->n, 1);
+    if (m->mc.arch == NQS_ARCH_TRANSFORMER && e.chain_depth >= 0) {
+        // prefix sharing: the samples' log psi come from level 0 of each chunk's jobs
+        ProfScope ps_all("local_energy", s);
+        TfWeights w;
+        NQS_TRY(tf_weights(m, w, s));
+        for (int64_t lo = 0; lo < B; lo += e.chunk) {
+            const int64_t nb = std::min(e.chunk, B - lo);
+            NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo, nb, e.cnt, e.off, e.valid,
+                                    e.xprime, e.S, s));
+            const int64_t rows_max = nb * (e.rows_cap / e.chunk);
+            NQS_TRY(chain_local_energy(m->mc, m->d_params, w, e.ch, e.chain_depth, bits + lo, nb, e.off, e.ntiles,
+                                       e.xprime, e.S, e.off + nb * e.ntiles, rows_max, e.la + lo, e.ph + lo,
+                                       e.contrib, s));
+            NQS_TRY(tc_status_take());
+            NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
+        }
+        return NQS_OK;
+    }
     if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
         ProfScope ps_all("local_energy", s);
         TfWeights w;
@@ -809,16 +856,8 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
         if (!e.dedup) NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, e.la, e.ph, e.tf, s));
         for (int64_t lo = 0; lo < B; lo += e.chunk) {
             const int64_t nb = std::min(e.chunk, B - lo);
-            {
-                ProfScope ps("sweep_count", s);
-                NQS_TRY(launch_sweep_count(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, bits + lo, nb, e.cnt, s));
-            }
-            NQS_TRY(launch_scan_i32(e.cnt, nb * e.ntiles, e.off, s));
-            {
-                ProfScope ps("term_sweep", s);
-                NQS_TRY(launch_sweep_emit(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, m->mc.compensated,
-                                          bits + lo, nb, e.off, e.xprime, e.S, s));
-            }
+            NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo, nb, e.cnt, e.off, e.valid,
+                                    e.xprime, e.S, s));
             if (e.dedup) {
                 // log psi once per distinct x' of the chunk, then the rows' contributions; the row
                 // count stays on the device (bounded by the chunk's feasible groups)
@@ -829,7 +868,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
                 const int64_t keys = std::min(rows_max + nb, sector_dim(m->mc.n, m->mc.n_up, m->mc.n_dn));
                 int64_t nu = 0;
                 NQS_TRY(dedup_rows(e.xprime, rows_dev, rows_max, bits + lo, nb, keys, e.dd, &nu, s));
-                if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
+                NQS_TRY(tc_status_take());     // bounded waits of the sweep (and the GEMMs so far)
                 for (int64_t r0 = 0; r0 < nu; r0 += e.tf.R) {
                     const int64_t R = std::min(e.tf.R, nu - r0);
                     NQS_TRY(tf_forward(m->mc, m->d_params, w, e.dd.uniq + r0, R, m->mc.n, e.tf, s, true));
@@ -845,7 +884,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
             int64_t rows = 0;
             NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             NQS_CK(cudaStreamSynchronize(s));
-            if (m->mc.precision == NQS_PREC_BF16) NQS_TRY(tc_status_take());
+            NQS_TRY(tc_status_take());
             for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
                 const int64_t R = std::min(e.tf.R, rows - r0);
                 NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s, true));
@@ -862,16 +901,8 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
     NQS_TRY(launch_logpsi_rows(m->mc, m->d_params, bits, B, e.la, e.ph, s));
     for (int64_t lo = 0; lo < B; lo += e.chunk) {
         const int64_t nb = std::min(e.chunk, B - lo);
-        {
-            ProfScope ps("sweep_count", s);
-            NQS_TRY(launch_sweep_count(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, bits + lo, nb, e.cnt, s));
-        }
-        NQS_TRY(launch_scan_i32(e.cnt, nb * e.ntiles, e.off, s));
-        {
-            ProfScope ps("term_sweep", s);
-            NQS_TRY(launch_sweep_emit(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, m->mc.compensated,
-                                      bits + lo, nb, e.off, e.xprime, e.S, s));
-        }
+        NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo, nb, e.cnt, e.off, e.valid,
+                                e.xprime, e.S, s));
         {
             ProfScope ps("eloc_rows", s);
             NQS_TRY(launch_eloc_rows(m->mc, m->d_params, bits + lo, nb, e.la + lo, e.ph + lo, e.off,
@@ -935,6 +966,16 @@ int nqs_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double
     if (B < 1 || !eloc || !counts || !stats) { set_error("need B >= 1 and eloc/counts/stats"); return NQS_ERR_INVALID_ARG; }
     if ((g_abs == nullptr) != (g_phase == nullptr)) { set_error("g_abs and g_phase go together"); return NQS_ERR_INVALID_ARG; }
     return launch_energy_stats(eloc, counts, B, stats, g_abs, g_phase, (cudaStream_t)stream);
+}
+
+int nqs_energy_sums(const float* eloc, const int64_t* counts, int64_t B, double* sums, float* g_abs_e,
+                    float* g_phase_e, float* g_abs_w, void* stream) {
+    if (B < 1 || !eloc || !counts || !sums) { set_error("need B >= 1 and eloc/counts/sums"); return NQS_ERR_INVALID_ARG; }
+    if (!((g_abs_e && g_phase_e && g_abs_w) || (!g_abs_e && !g_phase_e && !g_abs_w))) {
+        set_error("g_abs_e, g_phase_e and g_abs_w go together");
+        return NQS_ERR_INVALID_ARG;
+    }
+    return launch_energy_sums(eloc, counts, B, sums, g_abs_e, g_phase_e, g_abs_w, (cudaStream_t)stream);
 }
 
 int nqs_adam_step(float* p, const float* g, float* mm, float* v, int64_t n, int step, float lr,

@@ -11,8 +11,10 @@
 // allocating library routine.
 //
 // Set-up: the first call on each device looks up the array's device address with
-// cudaGetSymbolAddress while that device is current and caches it; make that first call before
-// any stream capture.  All calls share the one array and it keeps whatever the previous call
+// cudaGetSymbolAddress while that device is current and caches it.  When CUDA loads modules
+// lazily (the default since CUDA 12.2), that lookup is also what loads this file's module and
+// so allocates the array: make the first call on each device outside any no-allocation region
+// and before any stream capture.  All calls share the one array and it keeps whatever the previous call
 // left in it: every word a call reads is written earlier in the same call, so nothing needs
 // clearing, but two calls whose work overlaps on the GPU (different streams, or different host
 // threads) race on the array and must be serialised by the caller.
@@ -49,43 +51,25 @@ int scratch_address(void** out) {
     return NQS_OK;
 }
 
-uint64_t spin_bits(int n, int spin) {
-    uint64_t m = 0;
-    for (int j = spin; j < n; j += 2) m |= 1ull << j;
-    return m;
-}
-
-// Groups whose flip can keep some sector state in the sector (an upper bound on the rows one
-// sample can produce).
-int64_t sector_feasible_groups(const nqs_ham_s* h, int n_up, int n_dn) {
-    const int n_orb = h->n / 2;
-    int64_t cnt = 0;
-    for (int64_t g = 0; g < h->G; ++g) {
-        const int na = h->grp_meta[g] & 0xff, nb = (h->grp_meta[g] >> 8) & 0xff;
-        if ((na & 1) || (nb & 1)) continue;
-        if (na / 2 > std::min(n_up, n_orb - n_up) || nb / 2 > std::min(n_dn, n_orb - n_dn)) continue;
-        ++cnt;
-    }
-    return std::max<int64_t>(cnt, 1);
-}
-
 struct Plan {
     float *la, *ph;
     int32_t* cnt;
     int64_t* off;
+    uint32_t* valid;
     uint64_t* xprime;
     float4* S;
     int64_t chunk, ntiles;
 };
 
 // Carve the scratch for B samples processed `chunk` at a time; returns the bytes used.
-size_t carve(Carver& c, int64_t B, int64_t chunk, int64_t ntiles, int64_t feas, Plan& p) {
+size_t carve(Carver& c, const HamDev& h, int64_t B, int64_t chunk, int64_t ntiles, int64_t feas, Plan& p) {
     p.chunk = chunk;
     p.ntiles = ntiles;
     p.la = c.take<float>(B);
     p.ph = c.take<float>(B);
     p.cnt = c.take<int32_t>(chunk * ntiles);
     p.off = c.take<int64_t>(chunk * ntiles + 1);
+    p.valid = c.take<uint32_t>(sweep_valid_words(h, chunk));
     p.xprime = c.take<uint64_t>(chunk * feas);
     p.S = c.take<float4>(chunk * feas);
     return c.used;
@@ -109,13 +93,13 @@ extern "C" int nqs_local_energy_noalloc(nqs_ham_t h, nqs_model_t m, const uint64
     if (!bits || !eloc) { set_error("bits/eloc is NULL"); return NQS_ERR_INVALID_ARG; }
 
     const int64_t ntiles = sweep_tiles(h->dev);
-    const int64_t feas = sector_feasible_groups(h, m->mc.n_up, m->mc.n_dn);
+    const int64_t feas = feasible_groups(h, m->mc.n_up, m->mc.n_dn);
     // largest chunk (<= 1024 samples) whose buffers fit next to the per-sample log psi
     Plan plan{};
     int64_t chunk = std::min<int64_t>(B, 1024);
     for (;; chunk = chunk / 2) {
         Carver probe(nullptr);
-        if (carve(probe, B, chunk, ntiles, feas, plan) <= kScratchBytes) break;
+        if (carve(probe, h->dev, B, chunk, ntiles, feas, plan) <= kScratchBytes) break;
         if (chunk == 1) {
             set_error("nqs_local_energy_noalloc: " + std::to_string(B) + " samples with up to " +
                       std::to_string(feas) + " connected rows each need more than the " +
@@ -127,17 +111,16 @@ extern "C" int nqs_local_energy_noalloc(nqs_ham_t h, nqs_model_t m, const uint64
     void* base = nullptr;
     NQS_TRY(scratch_address(&base));
     Carver c(base);
-    carve(c, B, chunk, ntiles, feas, plan);
+    carve(c, h->dev, B, chunk, ntiles, feas, plan);
 
     cudaStream_t s = (cudaStream_t)stream;
-    const uint64_t A = spin_bits(h->n, 0), Bm = spin_bits(h->n, 1);
     NQS_TRY(launch_logpsi_rows(m->mc, m->d_params, bits, B, plan.la, plan.ph, s));
     for (int64_t lo = 0; lo < B; lo += plan.chunk) {
         const int64_t nb = std::min(plan.chunk, B - lo);
-        NQS_TRY(launch_sweep_count(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, bits + lo, nb, plan.cnt, s));
+        NQS_TRY(launch_sweep_count(h->dev, m->mc.n_up, m->mc.n_dn, bits + lo, nb, plan.cnt, plan.valid, s));
         NQS_TRY(launch_scan_i32(plan.cnt, nb * ntiles, plan.off, s));
-        NQS_TRY(launch_sweep_emit(h->dev, A, Bm, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo,
-                                  nb, plan.off, plan.xprime, plan.S, s));
+        NQS_TRY(launch_sweep_emit(h->dev, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo,
+                                  nb, plan.off, plan.valid, plan.xprime, plan.S, s));
         NQS_TRY(launch_eloc_rows(m->mc, m->d_params, bits + lo, nb, plan.la + lo, plan.ph + lo,
                                  plan.off, ntiles, plan.xprime, plan.S, eloc + 2 * lo, s));
     }

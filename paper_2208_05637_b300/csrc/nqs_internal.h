@@ -52,6 +52,7 @@ struct ProfScope {
 };
 
 int num_sms();
+bool prof_enabled();   // per-kernel profiling is on (nqs_profile_enable)
 
 // ------------------------------------------------------------------ Hamiltonian
 // group meta word: bits 0-7 n_alpha, 8-15 n_beta, bit 16 "has sigma_2-odd terms"
@@ -85,6 +86,28 @@ struct nqs_ham_s {
 
 namespace nqs {
 
+// Spin masks: bits of one spin species (0: even bits, spin up; 1: odd bits, spin down).
+inline uint64_t spin_mask(int n, int spin) {
+    uint64_t m = 0;
+    for (int j = spin; j < n; j += 2) m |= (1ull << j);
+    return m;
+}
+
+// Groups whose flip can keep some sector state inside the (n_up, n_dn) sector: an upper bound
+// (at least 1) on the rows the term sweep writes for one sample.
+inline int64_t feasible_groups(const nqs_ham_s* h, int n_up, int n_dn) {
+    const int n_orb = h->n / 2;
+    int64_t cnt = 0;
+    for (int64_t g = 0; g < h->G; ++g) {
+        const int na = h->grp_meta[g] & 0xff, nb = (h->grp_meta[g] >> 8) & 0xff;
+        if ((na & 1) || (nb & 1)) continue;
+        if (na / 2 > std::min(n_up, n_orb - n_up)) continue;
+        if (nb / 2 > std::min(n_dn, n_orb - n_dn)) continue;
+        ++cnt;
+    }
+    return std::max<int64_t>(cnt, 1);
+}
+
 // ------------------------------------------------------------------ model
 constexpr int MAX_Q = 64;
 constexpr int MADE_MAX_LAYERS = 4;
@@ -94,6 +117,7 @@ constexpr int TF_MAX_LAYERS = 8;
 struct ModelConst {
     int arch, n, n_up, n_dn, hidden, layers, heads, precision, compensated;
     uint8_t order[MAX_Q];   // order[t] = qubit of position t
+    uint8_t pos[MAX_Q];     // pos[q] = position of qubit q (the inverse of order)
     uint8_t after[MAX_Q];   // same-spin positions after t
     // parameter tensor offsets (floats) into the flat vector
     // PRODUCT: p
@@ -142,6 +166,7 @@ struct nqs_model_s {
     nqs::SamplerGraph graph;         // captured sampler of the last call shape
     void* d_scache = nullptr;        // sampler cache of the incremental transformer forward
     size_t scache_bytes = 0;
+    int prefix_depth = -1;           // transformer local energy: -1 automatic, 0..3 prefix sharing
 };
 
 namespace nqs {
@@ -163,13 +188,16 @@ struct Carver {
 // ------------------------------------------------------------------ launchers (.cu files)
 // term sweep (sweep.cu)
 constexpr int SWEEP_GT = 256;   // groups per tile (threads per CTA)
-constexpr int SWEEP_SB = 4;     // samples per CTA batch
+constexpr int SWEEP_SB = 32;    // samples per CTA batch (count and emit passes)
+constexpr int SWEEP_STAGE = 2048;   // terms of a tile staged in shared memory by the emit pass
+constexpr int SWEEP_SMALL = 16;     // groups with more terms are summed by a whole warp
 int64_t sweep_tiles(const HamDev& h);
-int launch_sweep_count(const HamDev& h, uint64_t amask, uint64_t bmask, int n_up, int n_dn,
-                       const uint64_t* bits, int64_t B, int32_t* cnt, cudaStream_t s);
-int launch_sweep_emit(const HamDev& h, uint64_t amask, uint64_t bmask, int n_up, int n_dn,
-                      int compensated, const uint64_t* bits, int64_t B, const int64_t* off,
-                      uint64_t* xprime, float4* S, cudaStream_t s);
+// Validity words (one uint32 per group and 32-sample batch) the count pass hands to the emit pass.
+int64_t sweep_valid_words(const HamDev& h, int64_t B);
+int launch_sweep_count(const HamDev& h, int n_up, int n_dn, const uint64_t* bits, int64_t B, int32_t* cnt,
+                       uint32_t* valid, cudaStream_t s);
+int launch_sweep_emit(const HamDev& h, int n_up, int n_dn, int compensated, const uint64_t* bits, int64_t B,
+                      const int64_t* off, const uint32_t* valid, uint64_t* xprime, float4* S, cudaStream_t s);
 int launch_unpack_rows(const int64_t* off, int64_t ntiles, int64_t B, const float4* S,
                        int64_t* row_offset, float* s_re, float* s_im, int64_t rows_cap,
                        const int64_t* total, cudaStream_t s);
@@ -182,6 +210,8 @@ int launch_scan_i64(const int64_t* in, int64_t n_host_max, const int64_t* n_dev,
                     cudaStream_t s);
 int launch_energy_stats(const float* eloc, const int64_t* counts, int64_t B, double* stats,
                         float* g_abs, float* g_phase, cudaStream_t s);
+int launch_energy_sums(const float* eloc, const int64_t* counts, int64_t B, double* sums, float* ga_e,
+                       float* gp_e, float* ga_w, cudaStream_t s);
 int launch_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
                 float b1, float b2, float eps, cudaStream_t s);
 // dW[o][i] += mask(o,i) * sum_b delta[b*ld_d + o] * act[b*ld_a + i]; db[o] += sum_b delta
@@ -328,6 +358,57 @@ int tc_qkv_attention_bf16(const void* A, const uint16_t* Wd, const float* bqkv, 
                           cudaStream_t s, const TcTokTable* qkv = nullptr);
 bool tc_qkv_gather_fits(int T);   // the gather form's table fits its shared memory
 int tc_status_take();
+// Device address of the status word that bounded device waits set on timeout (read and cleared
+// by tc_status_take).
+int device_status_ptr(int** out);
+// Row-generic pieces of the transformer forward (transformer.cu): C = A . W^T (+ epilogue) of
+// block `layer`'s matrix `which`, and the MLP half h += W2 . gelu(W1 . a + b1) + b2.
+int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, const void* A, void* C, int64_t M, int N,
+            int K, int epi, const float* bias, cudaStream_t s);
+int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* a, void* mid, float* h,
+           int64_t M, cudaStream_t s, const TcMlpHead* head = nullptr);
+
+// Prefix-sharing local energy of the transformer (chains.cu).  Jobs of levels 0 (the samples),
+// 1 (one flip) and 2 (two flips) with their per-layer key/value caches, and the leaves (the
+// sweep's rows); see chains.cu.
+constexpr int64_t CHAIN_MAX_CHUNK = 64;                     // samples per chunk
+constexpr int64_t CHAIN_CACHE_BYTES = 24ll << 30;           // key/value caches of one chunk
+constexpr int64_t CHAIN_PASS_BYTES = 16ll << 30;            // activations of one pass-B sub-pass
+constexpr int CHAIN_MAX_SPLIT = 4096;                       // pass-B sub-passes of one chunk
+struct ChainBufs {
+    int64_t chunk = 0, rows_cap = 0, jobs_cap = 0, pass_rows = 0;
+    unsigned long long *l1 = nullptr, *l2 = nullptr;         // per sample: level-1 flips, level-2 (f1, f2) bits
+    int64_t *cnt1 = nullptr, *cnt2 = nullptr, *base1 = nullptr, *base2 = nullptr;
+    int32_t* cum2 = nullptr;                                 // per (sample, f1): level-2 jobs before f1
+    uint64_t* jbits = nullptr;                               // pass-A jobs
+    int32_t *jstart = nullptr, *jpar = nullptr;
+    int64_t *jrows = nullptr, *joff = nullptr, *jseg = nullptr;   // jseg: end of the parent's job range
+    int32_t *lpar = nullptr, *lstart = nullptr;              // leaves (sweep rows)
+    int64_t* lrows = nullptr;
+    int32_t* lorder = nullptr;                               // slot -> leaf, leaves with rows grouped by parent
+    int64_t *srows = nullptr, *soff = nullptr, *sseg = nullptr;  // per slot: rows, row offset, parent's end
+    unsigned long long* hist = nullptr;                      // per parent: leaves (then cursors)
+    int64_t* hoff = nullptr;                                 // per parent: first slot; [jobs + 1] = slots
+    float* kv = nullptr;                                     // [jobs][layers][n][2d]
+    float2* cum = nullptr;                                   // [jobs][n + 1]
+    float* logit = nullptr;                                  // [jobs][n]
+    float* ph4 = nullptr;                                    // [jobs][4]
+    int32_t* rjob = nullptr;                                 // per pass row
+    uint8_t* rpos = nullptr;
+    int64_t *split = nullptr, *split_off = nullptr;
+    TfBufs tf{};
+};
+int64_t chain_jobs_per_sample(const ModelConst& mc, int depth);
+int64_t chain_chunk(const ModelConst& mc, int depth);
+int64_t chain_pass_rows(const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap);
+void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, ChainBufs& b);
+// Ratio-weighted contributions of the chunk's sweep rows (contrib) and the samples' log psi
+// (la_x, ph_x) by prefix sharing at the given depth (0..3).
+int chain_local_energy(const ModelConst& mc, const float* P, const TfWeights& w, ChainBufs& b, int depth,
+                       const uint64_t* xs, int64_t nb, const int64_t* seg, int64_t seg_stride, const uint64_t* xprime,
+                       const float4* S, const int64_t* rows_dev, int64_t rows_max, float* la_x, float* ph_x,
+                       float2* contrib, cudaStream_t s);
+
 struct TfCtx {
     const TfWeights* w;
     TfBufs* b;

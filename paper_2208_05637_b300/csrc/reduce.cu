@@ -122,6 +122,33 @@ stats_kernel(const float* __restrict__ eloc, const int64_t* __restrict__ counts,
     }
 }
 
+// Per-rank pieces of the data-parallel VMC gradient: FP64 sums [sum w Re E, sum w Im E,
+// sum w |E|^2, W] and the two sets of upstream gradients whose backward passes give the
+// unnormalised gradient sums (2 w Re E, 2 w Im E) and (w, 0).
+__global__ void __launch_bounds__(1024)
+sums_kernel(const float* __restrict__ eloc, const int64_t* __restrict__ counts, int64_t B, double* __restrict__ sums,
+            float* __restrict__ ga_e, float* __restrict__ gp_e, float* __restrict__ ga_w) {
+    __shared__ double red[3][32];
+    double a[3] = {0.0, 0.0, 0.0};
+    double q[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+        const double c = (double)counts[i];
+        const double er = (double)eloc[2 * i], ei = (double)eloc[2 * i + 1];
+        a[0] += c * er;
+        a[1] += c * ei;
+        a[2] += c * (er * er + ei * ei);
+        q[0] += c;
+        if (ga_e) {
+            ga_e[i] = (float)(2.0 * c * er);
+            gp_e[i] = (float)(2.0 * c * ei);
+            ga_w[i] = (float)c;
+        }
+    }
+    block_sum3_f64(a, 3, red);
+    block_sum3_f64(q, 1, red);
+    if (threadIdx.x == 0) { sums[0] = a[0]; sums[1] = a[1]; sums[2] = a[2]; sums[3] = q[0]; }
+}
+
 // ---------------------------------------------------------------- Adam
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
@@ -201,6 +228,13 @@ int launch_energy_stats(const float* eloc, const int64_t* counts, int64_t B, dou
                         float* g_abs, float* g_phase, cudaStream_t s) {
     ProfScope ps("energy_stats", s);
     stats_kernel<<<1, 1024, 0, s>>>(eloc, counts, B, stats, g_abs, g_phase);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+int launch_energy_sums(const float* eloc, const int64_t* counts, int64_t B, double* sums, float* ga_e,
+                       float* gp_e, float* ga_w, cudaStream_t s) {
+    sums_kernel<<<1, 1024, 0, s>>>(eloc, counts, B, sums, ga_e, gp_e, ga_w);
     NQS_LAUNCHED();
     return NQS_OK;
 }

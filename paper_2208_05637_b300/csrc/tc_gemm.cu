@@ -1789,13 +1789,25 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
     return launch(tc_mlp_kernel<128>, MlpRingPlan<128>::SMEM, MlpPlan<128>::THREADS, 1);
 }
 
-// Read and clear the device status of the tensor-core kernels (synchronous).
+int device_status_ptr(int** out) {
+    static int* addr[256] = {};
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) { set_error("device ordinal out of range"); return NQS_ERR_UNSUPPORTED; }
+    if (!addr[dev]) NQS_CK(cudaGetSymbolAddress((void**)&addr[dev], g_tc_status));
+    *out = addr[dev];
+    return NQS_OK;
+}
+
+// Read and clear the device status of the bounded waits (tensor-core kernels, term-sweep
+// staging) (synchronous).
 int tc_status_take() {
     int v = 0, z = 0;
     NQS_CK(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)));
     if (v) {
         NQS_CK(cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)));
-        set_error("a tensor-core GEMM wait timed out (status " + std::to_string(v) + ")");
+        set_error(std::string(v == 2 ? "a term-sweep staging copy" : "a tensor-core GEMM wait") +
+                  " timed out (status " + std::to_string(v) + ")");
         return NQS_ERR_TIMEOUT;
     }
     return NQS_OK;

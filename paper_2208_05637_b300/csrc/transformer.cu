@@ -484,8 +484,8 @@ tok_table_kernel(ModelConst mc, const float* __restrict__ P, const __nv_bfloat16
 // MLP half of block l: h += W2 . gelu(W1 . a + b1) + b2.  Compensated BF16 models with d_model
 // 64 or 128 run it as one fused tensor-core kernel (the 4d hidden layer stays on chip); the
 // others as two GEMMs through the mid buffer.
-static int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* a, void* mid,
-                  float* h, int64_t M, cudaStream_t s, const TcMlpHead* head = nullptr) {
+int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* a, void* mid,
+           float* h, int64_t M, cudaStream_t s, const TcMlpHead* head) {
     const int d = mc.hidden;
     if (mc.precision == NQS_PREC_BF16 && mc.compensated && (d == 64 || d == 128)) {
         const double flops = 2.0 * 2.0 * (double)M * 4 * d * d;

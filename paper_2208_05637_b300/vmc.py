@@ -14,8 +14,9 @@ computed (nqs_logpsi_backward_phase); the gradient is the same bit for bit.
 import torch
 
 from . import (NQS_ERR_UNSUPPORTED, NQSError, OP_BACKWARD, OP_LOCAL_ENERGY, OP_SAMPLE, nqs_adam_step,
-               nqs_energy_stats, nqs_local_energy, nqs_logpsi, nqs_logpsi_backward, nqs_logpsi_backward_phase,
-               nqs_sample)
+               nqs_energy_stats, nqs_energy_sums, nqs_local_energy, nqs_logpsi, nqs_logpsi_backward,
+               nqs_logpsi_backward_phase, nqs_sample)
+from . import parallel
 
 
 class LogPsi(torch.autograd.Function):
@@ -48,7 +49,7 @@ class VMC:
     FP64 statistics -> surrogate backward (mini-batched, recomputed) -> Adam."""
 
     def __init__(self, ham, model, params, n_samples, mini_batches=1, max_unique=None,
-                 lr=1e-3, betas=(0.9, 0.99), eps=1e-8, autograd=False):
+                 lr=1e-3, betas=(0.9, 0.99), eps=1e-8, autograd=False, group=None):
         self.ham, self.model = ham, model
         self.params = params.detach().requires_grad_(True)
         model.bind(self.params)
@@ -64,6 +65,10 @@ class VMC:
         self._ws = {}
         self._side = None            # stream of the overlapped backward recompute
         self.overlap_backward = True
+        # data parallel over the ranks of `group` (NCCL): own samples per rank, one all-reduce of
+        # the gradient pieces per step (paper Section 5); None or one rank: a single replica
+        self.group = group
+        self.rank, self.world = parallel.world(group) if group is not None else (0, 1)
 
     def reset(self, params):
         """Restore the parameters and clear the optimiser state (device copies, no sync)."""
@@ -100,8 +105,21 @@ class VMC:
         return True
 
     def step(self, seed):
+        # ranks draw from disjoint seed streams (each keeps its own unique samples)
+        seed = seed + 0x9E3779B97F4A7C15 * self.rank if self.world > 1 else seed
         bits, counts, _ = nqs_sample(self.model, self.n_samples, self.max_unique, seed,
                                      ws=self.ws_sample)
+        out = self.gradient(bits, counts)
+        self.t += 1
+        with torch.no_grad():
+            nqs_adam_step(self.params, self.params.grad, self.m, self.v, self.t, self.lr,
+                          self.betas[0], self.betas[1], self.eps)
+        return out
+
+    def gradient(self, bits, counts):
+        """Local energies (mini-batched), FP64 statistics and the VMC gradient (Eq. grad) of
+        the given unique samples and counts, accumulated into params.grad over the mini-batches
+        with the forward recomputed in each; no parameter update."""
         U = bits.numel()
         eloc = torch.empty((U, 2), dtype=torch.float32, device="cuda")
         per = max(1, -(-U // self.mini_batches))
@@ -109,6 +127,8 @@ class VMC:
         for sl in self._slices(U):
             nqs_local_energy(self.ham, self.model, bits[sl], ws=self._workspace(OP_LOCAL_ENERGY, per),
                              out=eloc[sl])
+        if self.world > 1:
+            return self._gradient_parallel(bits, counts, eloc, per, ahead)
         stats, g_abs, g_phase = nqs_energy_stats(eloc, counts)
         if self.params.grad is None:
             self.params.grad = torch.zeros_like(self.params)
@@ -125,8 +145,26 @@ class VMC:
             else:
                 nqs_logpsi_backward(self.model, bits[sl], g_abs[sl], g_phase[sl], self.params.grad,
                                     ws=self._workspace(OP_BACKWARD, per))
-        self.t += 1
-        with torch.no_grad():
-            nqs_adam_step(self.params, self.params.grad, self.m, self.v, self.t, self.lr,
-                          self.betas[0], self.betas[1], self.eps)
         return dict(bits=bits, counts=counts, eloc=eloc, stats=stats, unique=U)
+
+    def _gradient_parallel(self, bits, counts, eloc, per, ahead):
+        """Data-parallel gradient: this rank's two backward sums, one all-reduce (parallel.combine)."""
+        sums, ga_e, gp_e, ga_w = nqs_energy_sums(eloc, counts)
+        first = torch.zeros_like(self.params)
+        second = torch.zeros_like(self.params)
+        zero = torch.zeros_like(ga_w)
+        if ahead:   # the overlapped recompute served one backward; the second recomputes itself
+            torch.cuda.current_stream().wait_stream(self._side)
+            nqs_logpsi_backward_phase(self.model, 2, bits, ga_e, gp_e, first, ws=self._workspace(OP_BACKWARD, per))
+            nqs_logpsi_backward(self.model, bits, ga_w, zero, second, ws=self._workspace(OP_BACKWARD, per))
+        else:
+            for sl in self._slices(bits.numel()):
+                ws = self._workspace(OP_BACKWARD, per)
+                nqs_logpsi_backward(self.model, bits[sl], ga_e[sl], gp_e[sl], first, ws=ws)
+                nqs_logpsi_backward(self.model, bits[sl], ga_w[sl], zero[sl], second, ws=ws)
+        grad, stats = parallel.combine(sums, first, second, self.group)
+        if self.params.grad is None:
+            self.params.grad = grad
+        else:
+            self.params.grad.copy_(grad)
+        return dict(bits=bits, counts=counts, eloc=eloc, stats=stats, unique=bits.numel())

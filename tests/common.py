@@ -32,3 +32,28 @@ def rel_norm(a, b, w=None):
     a = np.asarray(a); b = np.asarray(b)
     w = np.ones(len(b)) if w is None else np.asarray(w, dtype=np.float64)
     return float(np.sqrt(np.sum(w * np.abs(a - b) ** 2)) / max(np.sqrt(np.sum(w * np.abs(b) ** 2)), 1e-300))
+
+
+def elem_metric(got, want, absum):
+    """max_i |got_i - want_i| / (|want_i| + A_i 2^-24): the element-wise relative error of the
+    local energies, with A_i (the sum of the magnitudes of sample i's terms) times the fp32 unit
+    roundoff as the floor where the terms cancel."""
+    got = np.asarray(got); want = np.asarray(want)
+    return float(np.max(np.abs(got - want) / (np.abs(want) + np.asarray(absum) * 2.0 ** -24)))
+
+
+# Local-energy gates (north star: relative error 1e-5 in the FP32 path, 1e-4 in the compensated
+# BF16 path against the quantisation-aware oracle).  The norm over the batch takes the stated
+# tolerance; the element-wise maximum takes ten times it.
+TOL_NORM = {"fp32": 1e-5, "bf16": 1e-4}
+TOL_ELEM = {"fp32": 1e-4, "bf16": 1e-3}
+
+
+def check_eloc(got, want, absum, form="fp32", w=None, label=""):
+    """Assert both local-energy gates; returns (rel_norm, elem_metric)."""
+    rn = rel_norm(got, want, w)
+    em = elem_metric(got, want, absum)
+    print(f"{label} E_loc rel_norm {rn:.2e} elementwise {em:.2e} ({form})")
+    assert rn <= TOL_NORM[form], (label, rn)
+    assert em <= TOL_ELEM[form], (label, em)
+    return rn, em

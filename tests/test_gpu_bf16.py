@@ -13,7 +13,7 @@ import synth
 from oracle.eloc import local_energy
 from oracle.models import in_sector
 from oracle.sampler import sample
-from tests.common import oracle_model, rel_norm
+from tests.common import check_eloc, oracle_model, rel_norm
 from tests.gpu_common import from_dev_bits, gpu_model, lib, to_dev_bits
 
 pytestmark = pytest.mark.gpu
@@ -74,11 +74,11 @@ def test_bf16_local_energy_against_quantised_oracle(c, B):
     o64, _ = oracle_model(cfg, beta=1.0)
     got = P.nqs_local_energy(ham, m, to_dev_bits(bits)).cpu().numpy().astype(np.float64)
     got = got[:, 0] + 1j * got[:, 1]
-    wq = local_energy(oq, xm, zm, coef, bits)
+    wq, absum = local_energy(oq, xm, zm, coef, bits, return_abs=True)
     w64 = local_energy(o64, xm, zm, coef, bits)
-    eq, e64 = rel_norm(got, wq), rel_norm(got, w64)
-    print(f"bf16 E_loc rel_norm vs quantised oracle {eq:.2e}; vs fp64 oracle {e64:.2e}")
-    assert eq <= 1e-4, eq
+    e64 = rel_norm(got, w64)
+    print(f"bf16 E_loc rel_norm vs fp64 oracle {e64:.2e} (reported, not gated)")
+    check_eloc(got, wq, absum, "bf16", label="bf16 vs quantised oracle")
 
 
 # d_model 64 / four heads runs the one-kernel sampler step: compensated and plain bf16 forms,

@@ -9,7 +9,7 @@ from oracle.eloc import local_energy
 from oracle.lanczos import sector_states
 from oracle.models import in_sector
 from oracle.sampler import sample
-from tests.common import oracle_model, rel_norm
+from tests.common import check_eloc, oracle_model, rel_norm
 from tests.gpu_common import from_dev_bits, gpu_model, lib, to_dev_bits
 
 pytestmark = pytest.mark.gpu
@@ -50,7 +50,7 @@ def test_transformer_logpsi(c, beta):
     assert np.max(np.abs(ph - wph) / (1 + np.abs(wph))) <= 1e-5
 
 
-@pytest.mark.parametrize("c,B", [(TF_SMALL, None), (TF_D64, 150), (3, 40)])
+@pytest.mark.parametrize("c,B", [(TF_SMALL, None), (TF_D64, 150), (TF_D128, 60), (3, 40)])
 @pytest.mark.parametrize("beta", [0.0, 2.0])
 def test_transformer_local_energy(c, B, beta):
     P = lib()
@@ -67,9 +67,8 @@ def test_transformer_local_energy(c, B, beta):
     om, _ = oracle_model(cfg, beta=beta)
     got = P.nqs_local_energy(ham, m, to_dev_bits(bits)).cpu().numpy().astype(np.float64)
     got = got[:, 0] + 1j * got[:, 1]
-    want = local_energy(om, xm, zm, coef, bits)
-    err = rel_norm(got, want)
-    assert err <= 1e-5, err
+    want, absum = local_energy(om, xm, zm, coef, bits, return_abs=True)
+    check_eloc(got, want, absum, "fp32", label=f"{c if isinstance(c, int) else n} beta={beta}")
 
 
 @pytest.mark.parametrize("c,n_samples,max_unique", [(TF_SMALL, 5000, 10**6), (3, 100_000, 10**6),

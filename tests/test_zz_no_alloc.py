@@ -65,3 +65,27 @@ def test_noalloc_rejects_requests_beyond_the_static_scratch():
     out_big = torch.empty((5_000_000, 2), dtype=torch.float32, device="cuda")
     assert _call_noalloc(P, ham, model, big, out_big) == P.NQS_ERR_CAPACITY
     assert b"static scratch" in P._lib.nqs_last_error()
+
+
+def test_noalloc_halves_its_chunk_when_the_log_psi_fill_the_scratch():
+    # 4.1e6 samples of the 12-qubit workload: their log psi take 32.8 MB of the 32 MiB scratch,
+    # so the sweep chunk drops from 1024 to 256 samples; results as with the workspace version
+    import torch
+    P = lib()
+    cfg = synth.get_config(2)
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(cfg.n_qubits, xm, zm, coef)
+    model, _ = gpu_model(cfg, beta=1.0)
+    st = sector_states(cfg.n_orb, cfg.n_up, cfg.n_dn)
+    B = 4_100_000
+    bits = st[np.random.default_rng(7).integers(0, len(st), B)]
+    bt = to_dev_bits(bits)
+    out = torch.full((B, 2), float("nan"), dtype=torch.float32, device="cuda")
+    assert _call_noalloc(P, ham, model, bt, out) == P.NQS_OK, P._lib.nqs_last_error()
+    want = P.nqs_local_energy(ham, model, bt)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    w = want.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    err = rel_norm(got[:, 0] + 1j * got[:, 1], w[:, 0] + 1j * w[:, 1])
+    assert err <= 1e-5, err
