@@ -147,8 +147,10 @@ struct ElocBufs {
 // then repeat a lot), prefix sharing at depth 3 otherwise.
 static int chain_depth_for(const nqs_model_s* m, const nqs_ham_s* h) {
     if (m->mc.arch != NQS_ARCH_TRANSFORMER) return -1;
+    const bool full = m->mc.n_up + m->mc.n_dn >= m->mc.n;   // the dedup's empty key is then a configuration
+    if (!chain_supported(m->mc)) return full ? -2 : -1;     // -2: neither form applies
     if (m->prefix_depth >= 0) return m->prefix_depth;
-    if (m->mc.n_up + m->mc.n_dn >= m->mc.n) return 3;     // the dedup's empty key is a configuration
+    if (full) return 3;
     const int64_t rows = ELOC_CHUNK * feasible_groups(h, m->mc.n_up, m->mc.n_dn);
     return sector_dim(m->mc.n, m->mc.n_up, m->mc.n_dn) > rows ? 3 : -1;
 }
@@ -550,6 +552,11 @@ static void graph_release(SamplerGraph& g) {
 int nqs_model_set_prefix_reuse(nqs_model_t m, int depth) {
     if (!m || depth < -1 || depth > 3) { set_error("need a model and depth in -1..3"); return NQS_ERR_INVALID_ARG; }
     if (m->mc.arch != NQS_ARCH_TRANSFORMER) { set_error("prefix reuse applies to the transformer"); return NQS_ERR_UNSUPPORTED; }
+    if (depth >= 0 && !chain_supported(m->mc)) {
+        set_error("prefix reuse needs head size 16 or 32, 1/2/4/8 heads and d_model <= 128 (d_model 256: head size 32 "
+                  "with at most 4 heads)");
+        return NQS_ERR_UNSUPPORTED;
+    }
     m->prefix_depth = depth;
     return NQS_OK;
 }
@@ -830,6 +837,11 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
     Carver c(ws);
     ElocBufs e;
     eloc_layout(c, m, h, B, e);
+    if (e.chain_depth == -2) {
+        set_error("transformer local energy: a completely filled sector needs the prefix-sharing form, which this "
+                  "head shape does not support");
+        return NQS_ERR_UNSUPPORTED;
+    }
     if (m->mc.arch == NQS_ARCH_TRANSFORMER && e.chain_depth >= 0) {
         // prefix sharing: the samples' log psi come from level 0 of each chunk's jobs
         ProfScope ps_all("local_energy", s);
@@ -852,13 +864,12 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
         ProfScope ps_all("local_energy", s);
         TfWeights w;
         NQS_TRY(tf_weights(m, w, s));
-        // log psi of the samples: with the x' dedup from the chunk's unique list, else here
-        if (!e.dedup) NQS_TRY(tf_logpsi(m->mc, m->d_params, w, bits, B, e.la, e.ph, e.tf, s));
+        // the samples' log psi come from the chunk's unique list
         for (int64_t lo = 0; lo < B; lo += e.chunk) {
             const int64_t nb = std::min(e.chunk, B - lo);
             NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo, nb, e.cnt, e.off, e.valid,
                                     e.xprime, e.S, s));
-            if (e.dedup) {
+            {
                 // log psi once per distinct x' of the chunk, then the rows' contributions; the row
                 // count stays on the device (bounded by the chunk's feasible groups)
                 const int64_t* rows_dev = e.off + nb * e.ntiles;
@@ -879,22 +890,7 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
                 NQS_TRY(dedup_contrib(e.xprime, rows_dev, rows_max, e.dd, bits + lo, e.off, e.ntiles, nb, e.S, e.contrib,
                                       s));
                 NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
-                continue;
             }
-            int64_t rows = 0;
-            NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            NQS_CK(cudaStreamSynchronize(s));
-            NQS_TRY(tc_status_take());
-            for (int64_t r0 = 0; r0 < rows; r0 += e.tf.R) {
-                const int64_t R = std::min(e.tf.R, rows - r0);
-                NQS_TRY(tf_forward(m->mc, m->d_params, w, e.xprime + r0, R, m->mc.n, e.tf, s, true));
-                HeadArgsHost ha{};
-                ha.mode = 1; ha.xsample = bits + lo; ha.la_x = e.la + lo; ha.ph_x = e.ph + lo;
-                ha.seg = e.off; ha.seg_stride = e.ntiles; ha.nseg = nb; ha.row0 = r0; ha.S = e.S;
-                ha.contrib = e.contrib;
-                NQS_TRY(tf_heads(m->mc, m->d_params, e.xprime + r0, R, m->mc.n, e.tf, ha, s));
-            }
-            NQS_TRY(tf_segment_sum(e.off, e.ntiles, nb, e.contrib, m->mc.compensated, eloc + 2 * lo, s));
         }
         return NQS_OK;
     }

@@ -178,7 +178,7 @@ __global__ void ch_leaf_kernel(ModelConst mc, const uint64_t* __restrict__ xs, i
 // whose rows [off[i] - base, ...) are its positions start[id] .. n-1.
 __global__ void ch_rows_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ order,
                                const int32_t* __restrict__ start, int64_t i0, int64_t i1, int64_t base, int n,
-                               int32_t* __restrict__ rjob, uint8_t* __restrict__ rpos) {
+                               int32_t* __restrict__ rjob, uint8_t* __restrict__ rpos, uint8_t* __restrict__ rstart) {
     for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t id = order ? order[i] : i;
         const int64_t q0 = off[i] - base;
@@ -186,6 +186,7 @@ __global__ void ch_rows_kernel(const int64_t* __restrict__ off, const int32_t* _
         for (int t = s0; t < n; ++t) {
             rjob[q0 + t - s0] = (int32_t)id;
             rpos[q0 + t - s0] = (uint8_t)t;
+            rstart[q0 + t - s0] = (uint8_t)s0;
         }
     }
 }
@@ -235,6 +236,53 @@ __global__ void ch_split_kernel(const int64_t* __restrict__ off, const int64_t* 
     }
     split[k] = lo;
     split_off[k] = off[lo];
+}
+
+// Chunks of a pass for the attention: consecutive slots of one parent whose rows fit `cap`
+// rows, packed greedily from each parent segment's first slot.  Pass 1 counts a segment's
+// chunks at its first slot, pass 2 writes [first slot, end slot) of each chunk at the scanned
+// offset; the chunk count lands in *n_chunks (device).
+__device__ __forceinline__ bool ch_seg_first(const int64_t* __restrict__ segend, int64_t i, int64_t i0) {
+    return i == i0 || segend[i] != segend[i - 1];
+}
+
+__global__ void ch_chunk_count_kernel(const int64_t* __restrict__ off, const int64_t* __restrict__ segend,
+                                      const int64_t* __restrict__ n_dev, int64_t i0, int64_t i1, int cap,
+                                      int64_t* __restrict__ cnt) {
+    const int64_t e1 = n_dev ? min(i1, *n_dev) : i1;
+    for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e1; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        if (ch_seg_first(segend, i, i0)) {
+            const int64_t se = min(segend[i], e1);
+            int64_t a = i;
+            while (a < se) {
+                int64_t e = a + 1;
+                while (e < se && off[e + 1] - off[a] <= cap) ++e;
+                ++c;
+                a = e;
+            }
+        }
+        cnt[i - i0] = c;
+    }
+}
+
+__global__ void ch_chunk_write_kernel(const int64_t* __restrict__ off, const int64_t* __restrict__ segend,
+                                      const int64_t* __restrict__ n_dev, int64_t i0, int64_t i1, int cap,
+                                      const int64_t* __restrict__ coff, int64_t* __restrict__ chunks) {
+    const int64_t e1 = n_dev ? min(i1, *n_dev) : i1;
+    for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e1; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!ch_seg_first(segend, i, i0)) continue;
+        const int64_t se = min(segend[i], e1);
+        int64_t a = i, k = coff[i - i0];
+        while (a < se) {
+            int64_t e = a + 1;
+            while (e < se && off[e + 1] - off[a] <= cap) ++e;
+            chunks[2 * k] = a;
+            chunks[2 * k + 1] = e;
+            ++k;
+            a = e;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- forward pieces
@@ -287,76 +335,77 @@ ch_cache_fill_kernel(float* __restrict__ kv, int L, int l, int n, int d, int64_t
     }
 }
 
-// Causal attention of the pass's rows.  A CTA takes a contiguous range of slots (jobs or
-// leaves, grouped by parent) and walks it in segments of equal parent: the parent's keys and
-// values of all n positions are staged once per segment in shared memory (cp.async, padded per
-// head so the lanes of a quarter-warp reading different heads hit distinct bank groups), then
-// every (row, head) item of the segment's rows runs the online softmax over keys 0..t in the
-// log2 domain -- keys before the row's job start from the staged parent, the job's own keys
-// from its rows of this pass (global memory, served from L1 to the job's later rows) -- and
-// writes its head's slice of o.
+// Causal attention of the pass's rows over a list of chunks (consecutive slots of one parent
+// whose rows fit the staging buffer).  CTAs take chunks interleaved, so the CTAs running at any
+// moment work on neighbouring chunks and share their parents' caches in L2.  For each chunk and
+// group of HG heads a CTA stages in shared memory (cp.async) the group's keys and values of the
+// parent at all n positions and of the chunk's own rows; then each warp takes a (block of 32
+// rows, head) item -- lane = row -- and runs the online softmax over keys 0..t in the log2
+// domain, in blocks of KB keys: keys before the row's job start from the staged parent, the
+// job's own keys from its staged rows.  Lanes of a block share most keys, so a key load is a
+// broadcast; rows are padded so neighbouring rows sit on other banks.
+constexpr int CH_ATT_THREADS = 128;
+constexpr int CH_ATT_HG = 2;                            // heads per staging group
+
 template <int MODE, int DH, int H>
-__global__ void __launch_bounds__(256)
-ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, int64_t i0, int64_t i1,
-                    const int32_t* __restrict__ order, const int32_t* __restrict__ start,
-                    const int32_t* __restrict__ par, const int64_t* __restrict__ off, const int64_t* __restrict__ segend,
-                    int64_t row_base, const int32_t* __restrict__ rjob, const uint8_t* __restrict__ rpos,
-                    const float* __restrict__ kv, int L, int l) {
+__global__ void __launch_bounds__(CH_ATT_THREADS, 6)
+ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, const int64_t* __restrict__ chunks,
+                    const int64_t* __restrict__ n_chunks, const int32_t* __restrict__ order,
+                    const int32_t* __restrict__ par, const int64_t* __restrict__ off, int64_t row_base,
+                    const uint8_t* __restrict__ rpos, const uint8_t* __restrict__ rstart, const float* __restrict__ kv,
+                    int L, int l) {
     extern __shared__ __align__(16) float ch_att_sm[];
     constexpr int D = H * DH;
-    constexpr int LH = DH + 4;
-    constexpr int LU = 2 * H * LH, VOFF = H * LH;
-    constexpr int PER_POS = D / 2;                      // float4 chunks of K|V per position
+    constexpr int HG = H < CH_ATT_HG ? H : CH_ATT_HG;   // heads per staging group
+    constexpr int KVP = 2 * DH + 4;                     // a head's (key, value) slice, padded
+    constexpr int RS = HG * KVP + 4;                    // one position / row of the group (rows on other banks)
     constexpr int ld = 3 * D;
-    __shared__ int64_t seg_end;
-    __shared__ int32_t seg_par;
+    constexpr int C4 = HG * DH / 2;                     // float4 chunks of the group's K|V of one position
+    float* sp = ch_att_sm;                              // parent: [n][RS]
+    float* so = ch_att_sm + n * RS;                     // chunk rows: [rows][RS]
     const float scale = rsqrtf((float)DH) * 1.4426950408889634f;
-    const int64_t total = i1 - i0;
-    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    int64_t a = i0 + (int64_t)blockIdx.x * per;
-    const int64_t b = min(i1, a + per);
-    int32_t staged = -2;
-    while (a < b) {
-        if (threadIdx.x == 0) {
-            seg_par = par[order ? order[a] : a];
-            seg_end = max(min(segend[a], b), a + 1);     // always advances
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = CH_ATT_THREADS / 32;
+    const int64_t nck = *n_chunks;
+    for (int64_t wi = blockIdx.x; wi < nck * (H / HG); wi += gridDim.x) {
+        const int64_t ck = wi / (H / HG);
+        const int h0 = (int)(wi % (H / HG)) * HG;
+        const int64_t a = chunks[2 * ck], e = chunks[2 * ck + 1];
+        const int32_t p0 = par[order ? order[a] : a];
+        const int64_t r_lo = off[a] - row_base;
+        const int nrows = (int)(off[e] - off[a]);
+        for (int c = threadIdx.x; c < nrows * C4; c += blockDim.x) {
+            const int r = c / C4, w = c % C4;
+            const int kvsel = w / (C4 / 2), col = 4 * (w % (C4 / 2));      // col within the group's heads
+            cp_async16(so + r * RS + (col / DH) * KVP + kvsel * DH + (col % DH),
+                       qkv + (r_lo + r) * ld + D + kvsel * D + h0 * DH + col);
         }
-        __syncthreads();
-        const int64_t e = seg_end;
-        const int32_t p0 = seg_par;
-        if (p0 >= 0 && p0 != staged) {
+        if (p0 >= 0) {
             const float* pre = kv + (((int64_t)p0 * L + l) * (int64_t)n) * 2 * D;
-            for (int c = threadIdx.x; c < n * PER_POS; c += blockDim.x) {
-                const int p = c / PER_POS, w4 = c % PER_POS;
-                const int col = 4 * w4, kvsel = col / D, w = col % D;
-                cp_async16(ch_att_sm + p * LU + kvsel * VOFF + (w / DH) * LH + (w % DH), pre + (int64_t)p * 2 * D + col);
+            for (int c = threadIdx.x; c < n * C4; c += blockDim.x) {
+                const int p = c / C4, w = c % C4;
+                const int kvsel = w / (C4 / 2), col = 4 * (w % (C4 / 2));
+                cp_async16(sp + p * RS + (col / DH) * KVP + kvsel * DH + (col % DH),
+                           pre + (int64_t)p * 2 * D + kvsel * D + h0 * DH + col);
             }
-            cp_async_wait_all();
         }
+        cp_async_wait_all();
         __syncthreads();
-        staged = p0;
-        const int64_t r_lo = off[a] - row_base, r_hi = off[e] - row_base;
-        // warp items: (block of 32 rows, head); lane = row, so every shared-memory key load is one
-        // broadcast wavefront
-        const int64_t nblk = (r_hi - r_lo + 31) / 32;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int64_t it = warp; it < nblk * H; it += (blockDim.x >> 5)) {
-            const int64_t blk = it / H;
-            const int hh = (int)(it - blk * H);
-            const int64_t q = r_lo + blk * 32 + lane;
-            const bool act = q < r_hi;
-            const int64_t qc = act ? q : r_hi - 1;
-            const int t = rpos[qc];
-            const int s0 = start[rjob[qc]];
-            const int64_t row0 = qc - (t - s0);
-            int tmax = act ? t : -1, smin = act ? s0 : 1 << 20;
+        const int nblk = (nrows + 31) / 32;
+        for (int it = warp; it < nblk * HG; it += NW) {
+            const int blk = it / HG, hl = it % HG, hh = h0 + hl;
+            const int rr = blk * 32 + lane;
+            const bool act = rr < nrows;
+            const int rc = act ? rr : nrows - 1;
+            const int64_t q = r_lo + rc;
+            const int t = rpos[q];
+            const int s0 = rstart[q];
+            const int own0 = rc - (t - s0);             // chunk row of the job's position s0
+            int tmax = act ? t : -1;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-                smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
-            }
+            for (int o2 = 16; o2 > 0; o2 >>= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o2));
             float qv[DH], acc[DH];
-            const float4* qs = reinterpret_cast<const float4*>(qkv + qc * ld + hh * DH);
+            const float4* qs = reinterpret_cast<const float4*>(qkv + q * ld + hh * DH);
 #pragma unroll
             for (int j4 = 0; j4 < DH / 4; ++j4) {
                 const float4 x = __ldg(qs + j4);
@@ -366,44 +415,51 @@ ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, 
 #pragma unroll
             for (int c = 0; c < DH; ++c) acc[c] = 0.f;
             float m = -INFINITY, lsum = 0.f;
-            auto key = [&](const float4* kr, const float4* vr) {
-                const float sc = att_dot<DH>(qv, kr);
-                if (sc > m) {
-                    const float c = ex2_approx(m - sc);    // 0 on the first key
+            constexpr int KB = 8;
+            const float* sph = sp + hl * KVP;
+            const float* soh = so + hl * KVP;
+            for (int pk = 0; pk <= tmax; pk += KB) {
+                const float* kp[KB];
+                bool ok[KB];
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    const int p = pk + j;
+                    ok[j] = act && p <= t;
+                    // masked keys read the chunk's first row, the same address in every lane
+                    kp[j] = !ok[j] ? soh : (p < s0 ? sph + p * RS : soh + (own0 + p - s0) * RS);
+                }
+                float sc[KB];
+                float bm = -INFINITY;
+#pragma unroll
+                for (int j = 0; j < KB; ++j) {
+                    sc[j] = ok[j] ? att_dot<DH>(qv, reinterpret_cast<const float4*>(kp[j])) : -INFINITY;
+                    bm = fmaxf(bm, sc[j]);
+                }
+                if (bm > m) {
+                    const float c = ex2_approx(m - bm);    // 0 on the first block
                     lsum *= c;
 #pragma unroll
                     for (int c2 = 0; c2 < DH; ++c2) acc[c2] *= c;
-                    m = sc;
+                    m = bm;
                 }
-                const float ev = ex2_approx(sc - m);
-                lsum += ev;
 #pragma unroll
-                for (int j4 = 0; j4 < DH / 4; ++j4) {
-                    const float4 v4 = vr[j4];
-                    acc[4 * j4] = fmaf(ev, v4.x, acc[4 * j4]);
-                    acc[4 * j4 + 1] = fmaf(ev, v4.y, acc[4 * j4 + 1]);
-                    acc[4 * j4 + 2] = fmaf(ev, v4.z, acc[4 * j4 + 2]);
-                    acc[4 * j4 + 3] = fmaf(ev, v4.w, acc[4 * j4 + 3]);
-                }
-            };
-            // keys every row of the block takes from the staged parent (p < every row's start)
-            const float* sk = ch_att_sm + hh * LH;
-            for (int p = 0; p < smin; ++p)
-                key(reinterpret_cast<const float4*>(sk + p * LU), reinterpret_cast<const float4*>(sk + p * LU + VOFF));
-            // the rest: the row's parent below its start, its own rows from there to t
-            for (int p = smin; p <= tmax; ++p) {
-                if (!act || p > t) continue;
-                if (p < s0) {
-                    key(reinterpret_cast<const float4*>(sk + p * LU), reinterpret_cast<const float4*>(sk + p * LU + VOFF));
-                } else {
-                    const float* row = qkv + (row0 + p - s0) * ld + D + hh * DH;
-                    key(reinterpret_cast<const float4*>(row), reinterpret_cast<const float4*>(row + D));
+                for (int j = 0; j < KB; ++j) {
+                    const float ev = ok[j] ? ex2_approx(sc[j] - m) : 0.f;
+                    lsum += ev;
+                    const float4* vr = reinterpret_cast<const float4*>(kp[j] + DH);
+#pragma unroll
+                    for (int j4 = 0; j4 < DH / 4; ++j4) {
+                        const float4 v4 = vr[j4];
+                        acc[4 * j4] = fmaf(ev, v4.x, acc[4 * j4]);
+                        acc[4 * j4 + 1] = fmaf(ev, v4.y, acc[4 * j4 + 1]);
+                        acc[4 * j4 + 2] = fmaf(ev, v4.z, acc[4 * j4 + 2]);
+                        acc[4 * j4 + 3] = fmaf(ev, v4.w, acc[4 * j4 + 3]);
+                    }
                 }
             }
             if (act) att_store_row<MODE, DH>(acc, lsum, o, q, D, hh * DH);
         }
         __syncthreads();
-        a = e;
     }
 }
 
@@ -615,38 +671,46 @@ inline int grid_for(int64_t n, int per, int cap_per_sm = 16) {
 }
 
 template <int MODE, int DH, int H>
-int ch_attention_launch(const ModelConst& mc, const float* qkv, void* o, int64_t i0, int64_t i1, const int32_t* order,
-                        const int32_t* start, const int32_t* par, const int64_t* off, const int64_t* segend,
-                        int64_t row_base, const int32_t* rjob, const uint8_t* rpos, const float* kv, int l,
+size_t ch_attention_smem(int n) {
+    constexpr int HG = H < CH_ATT_HG ? H : CH_ATT_HG;
+    return (size_t)(n + std::max(n, 48)) * (HG * (2 * DH + 4) + 4) * sizeof(float);
+}
+
+template <int MODE, int DH, int H>
+int ch_attention_launch(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks, const int64_t* n_chunks,
+                        int64_t max_chunks, const int32_t* order, const int32_t* par, const int64_t* off,
+                        int64_t row_base, const uint8_t* rpos, const uint8_t* rstart, const float* kv, int l,
                         cudaStream_t s) {
     const int n = mc.n;
-    const size_t smem = (size_t)n * 2 * H * (DH + 4) * sizeof(float);
+    const size_t smem = ch_attention_smem<MODE, DH, H>(n);
     static int configured = -1;
     int dev = 0;
     NQS_CK(cudaGetDevice(&dev));
     if (configured != dev) {
         NQS_CK(cudaFuncSetAttribute(ch_attention_kernel<MODE, DH, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    200 * 1024));
+                                    220 * 1024));
         configured = dev;
     }
-    const int per_sm = std::max(1, (int)((220 * 1024) / (smem + 2048)));
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(i1 - i0, (int64_t)num_sms() * std::min(per_sm, 4)));
-    ch_attention_kernel<MODE, DH, H><<<grid, 256, smem, s>>>(qkv, o, n, i0, i1, order, start, par, off, segend,
-                                                             row_base, rjob, rpos, kv, mc.layers, l);
+    if (smem > 220 * 1024) { set_error("prefix-sharing attention: staging exceeds shared memory"); return NQS_ERR_UNSUPPORTED; }
+    const int per_sm = std::max(1, std::min(6, (int)((227 * 1024) / (smem + 1024))));
+    constexpr int GROUPS = H < CH_ATT_HG ? 1 : H / CH_ATT_HG;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks * GROUPS, (int64_t)num_sms() * per_sm));
+    ch_attention_kernel<MODE, DH, H><<<grid, CH_ATT_THREADS, smem, s>>>(qkv, o, n, chunks, n_chunks, order, par, off,
+                                                                       row_base, rpos, rstart, kv, mc.layers, l);
     NQS_LAUNCHED();
     return NQS_OK;
 }
 
 template <int MODE>
-int ch_attention(const ModelConst& mc, const float* qkv, void* o, int64_t i0, int64_t i1, const int32_t* order,
-                 const int32_t* start, const int32_t* par, const int64_t* off, const int64_t* segend, int64_t row_base,
-                 const int32_t* rjob, const uint8_t* rpos, const float* kv, int l, cudaStream_t s) {
-    if (i1 <= i0) return NQS_OK;
+int ch_attention(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks, const int64_t* n_chunks,
+                 int64_t max_chunks, const int32_t* order, const int32_t* par, const int64_t* off, int64_t row_base,
+                 const uint8_t* rpos, const uint8_t* rstart, const float* kv, int l, cudaStream_t s) {
+    if (max_chunks <= 0) return NQS_OK;
     const int H = mc.heads, dh = mc.hidden / mc.heads;
 #define CH_ATT(DH_, H_)                                                                                           \
     if (dh == DH_ && H == H_)                                                                                     \
-        return ch_attention_launch<MODE, DH_, H_>(mc, qkv, o, i0, i1, order, start, par, off, segend, row_base, rjob, \
-                                                  rpos, kv, l, s);
+        return ch_attention_launch<MODE, DH_, H_>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off,      \
+                                                  row_base, rpos, rstart, kv, l, s);
     CH_ATT(16, 1) CH_ATT(16, 2) CH_ATT(16, 4) CH_ATT(16, 8) CH_ATT(32, 1) CH_ATT(32, 2) CH_ATT(32, 4) CH_ATT(32, 8)
 #undef CH_ATT
     set_error("prefix-sharing attention: head size 16 or 32 with 1, 2, 4 or 8 heads");
@@ -656,6 +720,14 @@ int ch_attention(const ModelConst& mc, const float* qkv, void* o, int64_t i0, in
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+bool chain_supported(const ModelConst& mc) {
+    const int H = mc.heads, dh = mc.hidden / std::max(1, mc.heads);
+    const int HG = H < CH_ATT_HG ? H : CH_ATT_HG;
+    const size_t smem = (size_t)(mc.n + std::max(mc.n, 48)) * (HG * (2 * dh + 4) + 4) * sizeof(float);
+    return mc.arch == NQS_ARCH_TRANSFORMER && (dh == 16 || dh == 32) && (H == 1 || H == 2 || H == 4 || H == 8) &&
+           smem <= 220 * 1024;
+}
+
 int64_t chain_jobs_per_sample(const ModelConst& mc, int depth) {
     const int64_t n = mc.n;
     return 1 + (depth >= 2 ? n : 0) + (depth >= 3 ? n * (n - 1) / 2 : 0);
@@ -720,6 +792,11 @@ void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int
     b.ph4 = c.take<float>(b.jobs_cap * 4);
     b.rjob = c.take<int32_t>(b.pass_rows);
     b.rpos = c.take<uint8_t>(b.pass_rows);
+    b.rstart = c.take<uint8_t>(b.pass_rows);
+    const int64_t max_slots = std::max(b.jobs_cap, rows_cap);
+    b.ccnt = c.take<int64_t>(max_slots);
+    b.coff = c.take<int64_t>(max_slots + 1);
+    b.chunks = c.take<int64_t>(2 * max_slots);
     b.split = c.take<int64_t>(CHAIN_MAX_SPLIT + 1);
     b.split_off = c.take<int64_t>(CHAIN_MAX_SPLIT + 1);
     tf_layout(c, mc, (b.pass_rows + n - 1) / n, b.tf);
@@ -754,6 +831,17 @@ static int ch_forward(const ModelConst& mc, const float* P, const TfWeights& w, 
             ch_embed_ln_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(mc, P, jbits, b.rjob, b.rpos, M, t.h, t.a);
             NQS_LAUNCHED();
         }
+        // the attention's chunk list (shared by every layer)
+        const int64_t nsl = j1 - j0;
+        if (M > 0) {
+            ProfScope ps("ch_build", s);
+            const int cap = std::max(n, 48);
+            ch_chunk_count_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.ccnt);
+            NQS_LAUNCHED();
+            NQS_TRY(launch_scan_i64(b.ccnt, nsl, nullptr, b.coff, s));
+            ch_chunk_write_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.coff, b.chunks);
+            NQS_LAUNCHED();
+        }
         for (int l = 0; l < mc.layers; ++l) {
             if (M > 0) NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, t.a, t.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
             if (pass_a) {
@@ -766,9 +854,11 @@ static int ch_forward(const ModelConst& mc, const float* P, const TfWeights& w, 
                 }
             }
             if (M > 0) {
-                ProfScope ps("ch_attention", s, att_flops, (double)M * 3 * d * 4 + (double)M * d * act_b);
-                NQS_TRY(ch_attention<MODE>(mc, t.qkv, t.o, j0, j1, order, jstart, jpar, joff, segend, row_base, b.rjob,
-                                           b.rpos, b.kv, l, s));
+                {
+                    ProfScope ps("ch_attention", s, att_flops, (double)M * 3 * d * 4 + (double)M * d * act_b);
+                    NQS_TRY(ch_attention<MODE>(mc, t.qkv, t.o, b.chunks, b.coff + nsl, nsl, order, jpar, joff, row_base,
+                                               b.rpos, b.rstart, b.kv, l, s));
+                }
                 NQS_TRY(tf_gemm(mc, w, TF_WO, l, t.o, t.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
                 {
                     ProfScope ps2("tf_layernorm", s, 0.0, ln_bytes);
@@ -832,7 +922,7 @@ static int ch_local_energy_mode(const ModelConst& mc, const float* P, const TfWe
 
     ChainView V{b.cum, b.logit, b.ph4};
     // pass A
-    ch_rows_kernel<<<grid_for(jobs, 256), 256, 0, s>>>(b.joff, nullptr, b.jstart, 0, jobs, 0, n, b.rjob, b.rpos);
+    ch_rows_kernel<<<grid_for(jobs, 256), 256, 0, s>>>(b.joff, nullptr, b.jstart, 0, jobs, 0, n, b.rjob, b.rpos, b.rstart);
     NQS_LAUNCHED();
     NQS_TRY(ch_forward<MODE>(mc, P, w, b, b.jbits, rows_a, true, lev, 0, jobs, nullptr, b.jstart, b.jpar, b.joff,
                              b.jseg, 0, s));
@@ -882,7 +972,7 @@ static int ch_local_energy_mode(const ModelConst& mc, const float* P, const TfWe
         const int64_t M = so[k + 1] - so[k];
         if (M > b.pass_rows) { set_error("prefix-sharing sub-pass exceeds the workspace"); return NQS_ERR_CAPACITY; }
         ch_rows_kernel<<<grid_for(i1 - i0, 256), 256, 0, s>>>(b.soff, b.lorder, b.lstart, i0, i1, so[k], n, b.rjob,
-                                                             b.rpos);
+                                                             b.rpos, b.rstart);
         NQS_LAUNCHED();
         NQS_TRY(ch_forward<MODE>(mc, P, w, b, xprime, M, false, lev, i0, i1, b.lorder, b.lstart, b.lpar, b.soff,
                                  b.sseg, so[k], s));

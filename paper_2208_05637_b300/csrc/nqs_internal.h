@@ -395,9 +395,12 @@ struct ChainBufs {
     float* ph4 = nullptr;                                    // [jobs][4]
     int32_t* rjob = nullptr;                                 // per pass row
     uint8_t* rpos = nullptr;
+    uint8_t* rstart = nullptr;                               // per pass row: its job's first own position
+    int64_t *ccnt = nullptr, *coff = nullptr, *chunks = nullptr;   // attention chunks of a pass: [first, end) slots
     int64_t *split = nullptr, *split_off = nullptr;
     TfBufs tf{};
 };
+bool chain_supported(const ModelConst& mc);   // head shape and staging fit the prefix-sharing kernels
 int64_t chain_jobs_per_sample(const ModelConst& mc, int depth);
 int64_t chain_chunk(const ModelConst& mc, int depth);
 int64_t chain_pass_rows(const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap);

@@ -166,6 +166,8 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     __shared__ uint32_t plist[SWEEP_SB * SWEEP_GT];    // small pairs from the front, large from the back
     __shared__ int32_t n_small, n_large, next_small;
     __shared__ __align__(8) uint64_t bar;
+    __shared__ uint64_t g_mask[SWEEP_GT];                  // the tile's groups: flip mask, meta, term range
+    __shared__ uint32_t g_meta[SWEEP_GT], g_k0[SWEEP_GT], g_k1[SWEEP_GT];
 
     const int tile = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * SWEEP_SB;
@@ -197,6 +199,10 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     }
     const uint32_t k0 = live ? h.grp_off[g] : 0, k1 = live ? h.grp_off[g + 1] : 0;
     const bool large = k1 - k0 > (uint32_t)SWEEP_SMALL;
+    g_mask[threadIdx.x] = live ? h.grp_mask[g] : 0;
+    g_meta[threadIdx.x] = live ? h.grp_meta[g] : 0;
+    g_k0[threadIdx.x] = k0;
+    g_k1[threadIdx.x] = k1;
     if (threadIdx.x < nb) {
         xs[threadIdx.x] = bits[s0 + threadIdx.x];
         obase[threadIdx.x] = off[(s0 + threadIdx.x) * ntiles + tile];
@@ -295,11 +301,10 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     for (int i = warp; i < nl; i += SWEEP_NW) {
         const uint32_t e = plist[SWEEP_SB * SWEEP_GT - 1 - i];
         const int p = e & 0x1fff, s = (e >> 13) & 0x1f, gl = e >> 18;
-        const int64_t gg = g0 + gl;
         const uint64_t x = xs[s];
-        const uint64_t mg = h.grp_mask[gg];
-        const bool has_imag = (h.grp_meta[gg] & META_HAS_IMAG) != 0;
-        const uint32_t a0 = h.grp_off[gg], a1 = h.grp_off[gg + 1];
+        const uint64_t mg = g_mask[gl];
+        const bool has_imag = (g_meta[gl] & META_HAS_IMAG) != 0;
+        const uint32_t a0 = g_k0[gl], a1 = g_k1[gl];
         float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
         for (uint32_t k = a0 + lane; k < a1; k += 32) {
             const uint64_t z = staged ? zs[k - t0] : __ldg(h.term_z + k);
@@ -344,11 +349,10 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
         if (i < ns) {
             const uint32_t e = plist[i];
             const int p = e & 0x1fff, s = (e >> 13) & 0x1f, gl = e >> 18;
-            const int64_t gg = g0 + gl;
             const uint64_t x = xs[s];
-            const uint64_t mg = h.grp_mask[gg];
-            const bool has_imag = (h.grp_meta[gg] & META_HAS_IMAG) != 0;
-            const uint32_t a0 = h.grp_off[gg], a1 = h.grp_off[gg + 1];
+            const uint64_t mg = g_mask[gl];
+            const bool has_imag = (g_meta[gl] & META_HAS_IMAG) != 0;
+            const uint32_t a0 = g_k0[gl], a1 = g_k1[gl];
             float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
             for (uint32_t k = a0; k < a1; ++k) {
                 const uint64_t z = staged ? zs[k - t0] : __ldg(h.term_z + k);
