@@ -68,6 +68,9 @@ def parse():
                     "the BF16 one for the speedup (0: skip)")
     ap.add_argument("--sweep-samples", type=int, default=1 << 16,
                     help="samples of the term-sweep microbenchmark (0: skip)")
+    ap.add_argument("--mode", default="step", choices=["step", "sweep"],
+                    help="step: the VMC-step benchmark (the JSON line); sweep: the term-sweep "
+                         "microbenchmark alone on --sweep-samples samples (its own JSON line)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -457,6 +460,27 @@ def sweep_microbench(P, torch, cfg, ham, B, popc_peak, pipes, sms, clk_mhz):
                          "work": "2 POPC per (sample, group) + 1 per performed (sample, term)"}}
 
 
+def run_sweep(args, local):
+    """The term-sweep microbenchmark alone (one JSON line)."""
+    import torch
+    import paper_2208_05637_b300 as P
+    torch.cuda.set_device(local)
+    cfg = synth.get_config(args.workload)
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(cfg.n_qubits, xm, zm, coef)
+    peaks, _ = load_peaks()
+    clk_mhz = peaks.get("sm_max_mhz", 2032.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    pipes = P.probe_pipes()
+    popc_peak = sms * pipes["popc"] * clk_mhz * 1e6 / 1e9
+    with ClockSampler(local) as clk:
+        res = sweep_microbench(P, torch, cfg, ham, max(1024, args.sweep_samples), popc_peak, pipes, sms, clk_mhz)
+    K, G = ham.info()
+    print(json.dumps({"metric": "term-sweep (sample, Pauli term) pairs/s", "workload": cfg.name, "terms_K": K,
+                      "groups_G": G, "pipes_per_sm_per_clk": pipes, "term_sweep_microbench": res,
+                      "clocks": clk.summary()}))
+
+
 # ----------------------------------------------------------------------------- oracle timing
 def cpu_baseline(cfg, args, budget_s=15.0):
     """The FP64 oracle as it stands on this host, on a bounded sample of the workload: local
@@ -532,6 +556,8 @@ def main():
             dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "sweep":
+        run_sweep(args, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and args.impl == "ours":

@@ -463,6 +463,271 @@ ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, 
     }
 }
 
+// ---------------------------------------------------------------- attention on the mma.sync path
+// The same causal attention for the bf16 forms with head size 16, on the tensor path (mma.sync
+// m16n8k16, bf16 operands, fp32 accumulate) with every product in the compensated form
+// x y ~ x_hi y_hi + x_hi y_lo + x_lo y_hi (hi = bf16(x), lo = bf16(x - hi)).  A warp takes a
+// tile of up to 16 consecutive rows of ONE job and one head, and runs the online softmax over
+// key positions in steps of 16 (positions 16 k .. 16 k + 15 for every row, whatever its job):
+// the keys of a step are gathered by ldmatrix from per-lane row addresses, position p from the
+// staged parent when p < start and from the job's own staged row otherwise, so the arithmetic
+// of a row is the same whichever job (and prefix depth) it is computed in -- the local
+// energies stay independent of the prefix depth bit for bit.  Positions after a row's own are
+// masked (their weights are exactly 0).
+// Fragment layouts (PTX ISA, m16n8k16 .bf16; g = lane / 4, c = lane % 4): A {(g, 2c..2c+1),
+// (g+8, 2c..), (g, 2c+8..), (g+8, 2c+8..)}; B {(k 2c..2c+1, n g), (k 2c+8.., n g)}; C {(g, 2c),
+// (g, 2c+1), (g+8, 2c), (g+8, 2c+1)}.
+// Shared staging: per key slot and head a 128-byte record of eight 16-byte segments (K hi
+// dims 0-7, 8-15, K lo 0-7, 8-15, V hi 0-7, 8-15, V lo 0-7, 8-15), segment s of slot k stored
+// at position s ^ (k & 7) so that eight consecutive slots read by one ldmatrix sit on
+// distinct banks.  Slots [0, n): the parent's positions; slots n + r: the chunk's row r (plus
+// 15 zeroed slots past the last row, read only under the mask).
+constexpr int CHM_THREADS = 128;
+constexpr int CHM_HG = 4;                // heads per staging group
+constexpr int CHM_MAX_TILES = 64;        // 16-row tiles of one chunk (chunk rows <= 64)
+
+__device__ __forceinline__ void chm_split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(hh);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&hh);
+    lo = *reinterpret_cast<const uint32_t*>(&ll);
+}
+
+__device__ __forceinline__ void chm_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                 "{%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += a b in the compensated form (small terms first)
+__device__ __forceinline__ void chm_mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
+                                         uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    chm_mma(d, al, bh0, bh1);
+    chm_mma(d, ah, bl0, bl1);
+    chm_mma(d, ah, bh0, bh1);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+
+// Byte offset of segment `seg` of key slot `slot`, head `hl` (HG heads per slot).
+template <int HG>
+__device__ __forceinline__ uint32_t chm_seg(int slot, int hl, int seg) {
+    return (uint32_t)((((slot * HG + hl) << 3) + (seg ^ (slot & 7))) << 4);
+}
+
+// 16 floats -> their hi and lo bf16 halves as two 16-byte segment pairs at slot/head.
+template <int HG>
+__device__ __forceinline__ void chm_stage16(uint32_t keys, int slot, int hl, int seg0, const float4 (&v)[4]) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        chm_split2(v[i].x, v[i].y, hi[2 * i], lo[2 * i]);
+        chm_split2(v[i].z, v[i].w, hi[2 * i + 1], lo[2 * i + 1]);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(keys + chm_seg<HG>(slot, hl, seg0 + s)),
+                     "r"(hi[4 * s]), "r"(hi[4 * s + 1]), "r"(hi[4 * s + 2]), "r"(hi[4 * s + 3]) : "memory");
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(keys + chm_seg<HG>(slot, hl, seg0 + 2 + s)),
+                     "r"(lo[4 * s]), "r"(lo[4 * s + 1]), "r"(lo[4 * s + 2]), "r"(lo[4 * s + 3]) : "memory");
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void chm_store2(void* o, int64_t row, int D, int col, float x, float y) {
+    __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(o);
+    uint32_t hi, lo;
+    chm_split2(x, y, hi, lo);
+    if (MODE == ACT_BF16X2) {
+        *reinterpret_cast<uint32_t*>(b + row * 2 * D + col) = hi;
+        *reinterpret_cast<uint32_t*>(b + row * 2 * D + D + col) = lo;
+    } else {
+        *reinterpret_cast<uint32_t*>(b + row * D + col) = hi;
+    }
+}
+
+template <int MODE, int H>
+__global__ void __launch_bounds__(CHM_THREADS, 3)
+ch_attention_mma_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, const int64_t* __restrict__ chunks,
+                        const int64_t* __restrict__ n_chunks, const int32_t* __restrict__ order,
+                        const int32_t* __restrict__ par, const int64_t* __restrict__ off, int64_t row_base,
+                        const uint8_t* __restrict__ rpos, const uint8_t* __restrict__ rstart,
+                        const float* __restrict__ kv, int L, int l, int cap) {
+    extern __shared__ __align__(128) uint8_t chm_sm[];
+    constexpr int DH = 16, D = H * DH, ld = 3 * D;
+    constexpr int HG = H < CHM_HG ? H : CHM_HG;
+    constexpr int NW = CHM_THREADS / 32;
+    int4* tiles = reinterpret_cast<int4*>(chm_sm);                    // (row0, rows, own0, start)
+    int* s_ntiles = reinterpret_cast<int*>(chm_sm + CHM_MAX_TILES * sizeof(int4));
+    const uint32_t keys = (uint32_t)__cvta_generic_to_shared(chm_sm + CHM_MAX_TILES * sizeof(int4) + 16);
+    (void)rpos;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, c = lane & 3;
+    const float scale = 0.25f * 1.4426950408889634f;                // rsqrt(16) log2(e)
+    const int64_t nck = *n_chunks;
+    for (int64_t wi = blockIdx.x; wi < nck * (H / HG); wi += gridDim.x) {
+        const int64_t ck = wi / (H / HG);
+        const int h0 = (int)(wi % (H / HG)) * HG;
+        const int64_t a = chunks[2 * ck], e = chunks[2 * ck + 1];
+        const int32_t p0 = par[order ? order[a] : a];
+        const int64_t r_lo = off[a] - row_base;
+        const int nrows = (int)(off[e] - off[a]);
+        // own rows -> slots n + r; 15 zero slots after them
+        for (int u = threadIdx.x; u < (nrows + 15) * HG * 2; u += CHM_THREADS) {
+            const int r = u / (2 * HG), hl = (u >> 1) % HG, kvsel = u & 1;
+            float4 v[4];
+            if (r < nrows) {
+                const float4* src = reinterpret_cast<const float4*>(qkv + (r_lo + r) * ld + D + kvsel * D + (h0 + hl) * DH);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = __ldg(src + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            chm_stage16<HG>(keys, n + r, hl, 4 * kvsel, v);
+        }
+        if (p0 >= 0) {
+            const float* pre = kv + (((int64_t)p0 * L + l) * (int64_t)n) * 2 * D;
+            for (int u = threadIdx.x; u < n * HG * 2; u += CHM_THREADS) {
+                const int p = u / (2 * HG), hl = (u >> 1) % HG, kvsel = u & 1;
+                const float4* src = reinterpret_cast<const float4*>(pre + (int64_t)p * 2 * D + kvsel * D + (h0 + hl) * DH);
+                float4 v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = __ldg(src + i);
+                chm_stage16<HG>(keys, p, hl, 4 * kvsel, v);
+            }
+        }
+        // the chunk's 16-row tiles, job by job
+        if (warp == 0) {
+            int base = 0;
+            for (int64_t j0 = a; j0 < e; j0 += 32) {
+                const int64_t j = j0 + lane;
+                int nt = 0, first = 0, rows = 0, st = 0;
+                if (j < e) {
+                    first = (int)(off[j] - off[a]);
+                    rows = (int)(off[j + 1] - off[j]);
+                    st = rows > 0 ? (int)rstart[r_lo + first] : 0;
+                    nt = (rows + 15) >> 4;
+                }
+                int incl = nt;
+#pragma unroll
+                for (int dd = 1; dd < 32; dd <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, dd);
+                    if (lane >= dd) incl += y;
+                }
+                const int ex = base + incl - nt;
+                for (int i = 0; i < nt; ++i)
+                    if (ex + i < CHM_MAX_TILES) tiles[ex + i] = make_int4(first + 16 * i, min(16, rows - 16 * i), first, st);
+                base += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) *s_ntiles = min(base, CHM_MAX_TILES);
+        }
+        __syncthreads();
+        const int ntile = *s_ntiles;
+        for (int it = warp; it < ntile * HG; it += NW) {
+            const int4 tl = tiles[it / HG];
+            const int hl = it % HG, hh = h0 + hl;
+            const int row0 = tl.x, cnt = tl.y, own0 = tl.z, st = tl.w;
+            const int t0 = st + (row0 - own0);                 // position of the tile's first row
+            const int tlast = t0 + cnt - 1;
+            const int ta = g < cnt ? t0 + g : tlast;           // padding rows mirror the last row
+            const int tb = g + 8 < cnt ? t0 + g + 8 : tlast;
+            uint32_t qh[4], ql[4];
+            {
+                const float* qa = qkv + (r_lo + row0 + (ta - t0)) * ld + hh * DH + 2 * c;
+                const float* qb = qkv + (r_lo + row0 + (tb - t0)) * ld + hh * DH + 2 * c;
+                const float2 x0 = __ldg(reinterpret_cast<const float2*>(qa));
+                const float2 x1 = __ldg(reinterpret_cast<const float2*>(qb));
+                const float2 x2 = __ldg(reinterpret_cast<const float2*>(qa + 8));
+                const float2 x3 = __ldg(reinterpret_cast<const float2*>(qb + 8));
+                chm_split2(x0.x * scale, x0.y * scale, qh[0], ql[0]);
+                chm_split2(x1.x * scale, x1.y * scale, qh[1], ql[1]);
+                chm_split2(x2.x * scale, x2.y * scale, qh[2], ql[2]);
+                chm_split2(x3.x * scale, x3.y * scale, qh[3], ql[3]);
+            }
+            float O[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            float m[2] = {-INFINITY, -INFINITY}, lsum[2] = {0.f, 0.f};
+            const int mj = lane >> 3, rr = lane & 7;
+            for (int pb = 0; pb <= tlast; pb += 16) {
+                // per-lane ldmatrix rows: K (matrices: keys 0-7 / 8-15 x dims 0-7 / 8-15), V transposed
+                const int pk = pb + rr + 8 * (mj >> 1), pv = pb + rr + 8 * (mj & 1);
+                const int sk = pk < st ? pk : n + own0 + (pk - st);
+                const int sv = pv < st ? pv : n + own0 + (pv - st);
+                uint32_t kh[4], kl[4];
+                ldsm_x4(keys + chm_seg<HG>(sk, hl, mj & 1), kh);
+                ldsm_x4(keys + chm_seg<HG>(sk, hl, 2 + (mj & 1)), kl);
+                float S[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                chm_mma3(S[0], qh, ql, kh[0], kh[1], kl[0], kl[1]);
+                chm_mma3(S[1], qh, ql, kh[2], kh[3], kl[2], kl[3]);
+                float mx[2] = {-INFINITY, -INFINITY};
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int ee = 0; ee < 2; ++ee) {
+                        const int p = pb + 8 * nt + 2 * c + ee;
+                        S[nt][ee] = p <= ta ? S[nt][ee] : -INFINITY;
+                        S[nt][2 + ee] = p <= tb ? S[nt][2 + ee] : -INFINITY;
+                        mx[0] = fmaxf(mx[0], S[nt][ee]);
+                        mx[1] = fmaxf(mx[1], S[nt][2 + ee]);
+                    }
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    mx[hf] = fmaxf(mx[hf], __shfl_xor_sync(0xffffffffu, mx[hf], 1));
+                    mx[hf] = fmaxf(mx[hf], __shfl_xor_sync(0xffffffffu, mx[hf], 2));
+                    if (mx[hf] > m[hf]) {
+                        const float cr = ex2_approx(m[hf] - mx[hf]);   // 0 on the first step
+                        lsum[hf] *= cr;
+                        O[0][2 * hf] *= cr; O[0][2 * hf + 1] *= cr;
+                        O[1][2 * hf] *= cr; O[1][2 * hf + 1] *= cr;
+                        m[hf] = mx[hf];
+                    }
+                }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int ee = 0; ee < 2; ++ee) {
+                        S[nt][ee] = ex2_approx(S[nt][ee] - m[0]);
+                        S[nt][2 + ee] = ex2_approx(S[nt][2 + ee] - m[1]);
+                        lsum[0] += S[nt][ee];
+                        lsum[1] += S[nt][2 + ee];
+                    }
+                uint32_t ph[4], pl[4];
+                chm_split2(S[0][0], S[0][1], ph[0], pl[0]);
+                chm_split2(S[0][2], S[0][3], ph[1], pl[1]);
+                chm_split2(S[1][0], S[1][1], ph[2], pl[2]);
+                chm_split2(S[1][2], S[1][3], ph[3], pl[3]);
+                uint32_t vh[4], vl[4];
+                ldsm_x4_t(keys + chm_seg<HG>(sv, hl, 4 + (mj >> 1)), vh);
+                ldsm_x4_t(keys + chm_seg<HG>(sv, hl, 6 + (mj >> 1)), vl);
+                chm_mma3(O[0], ph, pl, vh[0], vh[1], vl[0], vl[1]);
+                chm_mma3(O[1], ph, pl, vh[2], vh[3], vl[2], vl[3]);
+            }
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                lsum[hf] += __shfl_xor_sync(0xffffffffu, lsum[hf], 1);
+                lsum[hf] += __shfl_xor_sync(0xffffffffu, lsum[hf], 2);
+            }
+            const float ia = 1.f / lsum[0], ib = 1.f / lsum[1];
+#pragma unroll
+            for (int n2 = 0; n2 < 2; ++n2) {
+                const int col = hh * DH + 8 * n2 + 2 * c;
+                if (g < cnt) chm_store2<MODE>(o, r_lo + row0 + g, D, col, O[n2][0] * ia, O[n2][1] * ia);
+                if (g + 8 < cnt) chm_store2<MODE>(o, r_lo + row0 + g + 8, D, col, O[n2][2] * ib, O[n2][3] * ib);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- heads
 // LNf of row `row` and its output-head logit at position t (the whole warp; every lane gets it).
 template <int DPL>
@@ -666,6 +931,9 @@ int with_dpl_c(int d, F&& f) {
     }
 }
 
+// Rows of one attention chunk at most (a chunk holds whole jobs of one parent; a job has <= n rows).
+inline int ch_chunk_cap(int n) { return std::max(n, 48); }
+
 inline int grid_for(int64_t n, int per, int cap_per_sm = 16) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, (int64_t)num_sms() * cap_per_sm));
 }
@@ -673,7 +941,7 @@ inline int grid_for(int64_t n, int per, int cap_per_sm = 16) {
 template <int MODE, int DH, int H>
 size_t ch_attention_smem(int n) {
     constexpr int HG = H < CH_ATT_HG ? H : CH_ATT_HG;
-    return (size_t)(n + std::max(n, 48)) * (HG * (2 * DH + 4) + 4) * sizeof(float);
+    return (size_t)(n + ch_chunk_cap(n)) * (HG * (2 * DH + 4) + 4) * sizeof(float);
 }
 
 template <int MODE, int DH, int H>
@@ -701,12 +969,47 @@ int ch_attention_launch(const ModelConst& mc, const float* qkv, void* o, const i
     return NQS_OK;
 }
 
+inline size_t ch_attention_mma_smem(int n, int cap, int HG) {
+    return (size_t)CHM_MAX_TILES * 16 + 16 + (size_t)(n + cap + 15) * HG * 128;
+}
+
+template <int MODE, int H>
+int ch_attention_mma_launch(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks,
+                            const int64_t* n_chunks, int64_t max_chunks, const int32_t* order, const int32_t* par,
+                            const int64_t* off, int64_t row_base, const uint8_t* rpos, const uint8_t* rstart,
+                            const float* kv, int l, cudaStream_t s) {
+    constexpr int HG = H < CHM_HG ? H : CHM_HG;
+    const int n = mc.n, cap = ch_chunk_cap(n);
+    const size_t smem = ch_attention_mma_smem(n, cap, HG);
+    static int configured = -1;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (configured != dev) {
+        NQS_CK(cudaFuncSetAttribute(ch_attention_mma_kernel<MODE, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    220 * 1024));
+        configured = dev;
+    }
+    if (smem > 220 * 1024) { set_error("prefix-sharing attention: staging exceeds shared memory"); return NQS_ERR_UNSUPPORTED; }
+    const int per_sm = std::max(1, std::min(3, (int)((227 * 1024) / (smem + 1024))));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks * (H / HG), (int64_t)num_sms() * per_sm));
+    ch_attention_mma_kernel<MODE, H><<<grid, CHM_THREADS, smem, s>>>(qkv, o, n, chunks, n_chunks, order, par, off,
+                                                                    row_base, rpos, rstart, kv, mc.layers, l, cap);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
 template <int MODE>
 int ch_attention(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks, const int64_t* n_chunks,
                  int64_t max_chunks, const int32_t* order, const int32_t* par, const int64_t* off, int64_t row_base,
                  const uint8_t* rpos, const uint8_t* rstart, const float* kv, int l, cudaStream_t s) {
     if (max_chunks <= 0) return NQS_OK;
     const int H = mc.heads, dh = mc.hidden / mc.heads;
+    if ((MODE == ACT_BF16 || MODE == ACT_BF16X2) && dh == 16) {
+        if (H == 1) return ch_attention_mma_launch<MODE, 1>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
+        if (H == 2) return ch_attention_mma_launch<MODE, 2>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
+        if (H == 4) return ch_attention_mma_launch<MODE, 4>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
+        if (H == 8) return ch_attention_mma_launch<MODE, 8>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
+    }
 #define CH_ATT(DH_, H_)                                                                                           \
     if (dh == DH_ && H == H_)                                                                                     \
         return ch_attention_launch<MODE, DH_, H_>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off,      \
@@ -723,7 +1026,7 @@ int ch_attention(const ModelConst& mc, const float* qkv, void* o, const int64_t*
 bool chain_supported(const ModelConst& mc) {
     const int H = mc.heads, dh = mc.hidden / std::max(1, mc.heads);
     const int HG = H < CH_ATT_HG ? H : CH_ATT_HG;
-    const size_t smem = (size_t)(mc.n + std::max(mc.n, 48)) * (HG * (2 * dh + 4) + 4) * sizeof(float);
+    const size_t smem = (size_t)(mc.n + ch_chunk_cap(mc.n)) * (HG * (2 * dh + 4) + 4) * sizeof(float);
     return mc.arch == NQS_ARCH_TRANSFORMER && (dh == 16 || dh == 32) && (H == 1 || H == 2 || H == 4 || H == 8) &&
            smem <= 220 * 1024;
 }
@@ -835,7 +1138,7 @@ static int ch_forward(const ModelConst& mc, const float* P, const TfWeights& w, 
         const int64_t nsl = j1 - j0;
         if (M > 0) {
             ProfScope ps("ch_build", s);
-            const int cap = std::max(n, 48);
+            const int cap = ch_chunk_cap(n);
             ch_chunk_count_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.ccnt);
             NQS_LAUNCHED();
             NQS_TRY(launch_scan_i64(b.ccnt, nsl, nullptr, b.coff, s));

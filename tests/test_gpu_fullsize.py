@@ -51,11 +51,17 @@ def test_fullsize_benched_batch_local_energy(cid, prec):
     hc = counts.cpu().numpy()
     assert len(hb) == BATCH and hc.sum() <= cfg.n_samples
     assert np.all(np.diff(hb.astype(np.float64)) > 0)
-    # the stored samples are the oracle batch's highest counts: all of them are in the GPU batch,
-    # with counts that differ only by draws whose fp32 probabilities straddle a threshold
+    # the stored samples are the oracle batch's highest counts: all of them are in the GPU batch.
+    # Their counts agree in distribution only: a draw whose fp32 and fp64 probabilities straddle
+    # its threshold changes a count by one, and after the next eviction every later nominal
+    # sample index (the Philox counter) shifts, so later draws are independent between the two
+    # runs; the counts then differ like two multinomial draws (a few standard deviations of
+    # sqrt(2 c)).  The local energies below depend on the configurations only.
     idx = np.searchsorted(hb, gb)
     assert np.all(idx < len(hb)) and np.array_equal(hb[idx], gb)
-    assert np.all(np.abs(hc[idx] - gc) <= np.maximum(2, 0.01 * gc))
+    dc = np.abs(hc[idx] - gc)
+    print(f"{cfg.name} {prec}: stored counts {gc.min()}..{gc.max()}, {np.count_nonzero(dc)} differ, max {dc.max()}")
+    assert np.all(dc <= 6.0 * np.sqrt(2.0 * gc) + 2)
     eloc = P.nqs_local_energy(ham, m, bits).cpu().numpy().astype(np.float64)
     assert np.all(np.isfinite(eloc))
     got = eloc[idx, 0] + 1j * eloc[idx, 1]
