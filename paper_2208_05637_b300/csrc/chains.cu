@@ -248,10 +248,10 @@ __device__ __forceinline__ bool ch_seg_first(const int64_t* __restrict__ segend,
 
 __global__ void ch_chunk_count_kernel(const int64_t* __restrict__ off, const int64_t* __restrict__ segend,
                                       const int64_t* __restrict__ n_dev, int64_t i0, int64_t i1, int cap,
-                                      int64_t* __restrict__ cnt) {
+                                      int64_t* __restrict__ cnt, int64_t* __restrict__ tcnt) {
     const int64_t e1 = n_dev ? min(i1, *n_dev) : i1;
     for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e1; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t c = 0;
+        int64_t c = 0, t = 0;
         if (ch_seg_first(segend, i, i0)) {
             const int64_t se = min(segend[i], e1);
             int64_t a = i;
@@ -261,24 +261,44 @@ __global__ void ch_chunk_count_kernel(const int64_t* __restrict__ off, const int
                 ++c;
                 a = e;
             }
+            for (int64_t j = i; j < se; ++j) t += (off[j + 1] - off[j] + 15) >> 4;
         }
         cnt[i - i0] = c;
+        tcnt[i - i0] = t;
     }
 }
 
+// Chunk records (first row offset, rows | parent << 32, first tile, end tile) and the 16-row
+// tiles of each job: (row0, rows, job's first row, job start), rows relative to the chunk.
 __global__ void ch_chunk_write_kernel(const int64_t* __restrict__ off, const int64_t* __restrict__ segend,
                                       const int64_t* __restrict__ n_dev, int64_t i0, int64_t i1, int cap,
-                                      const int64_t* __restrict__ coff, int64_t* __restrict__ chunks) {
+                                      const int64_t* __restrict__ coff, const int64_t* __restrict__ toff,
+                                      const int32_t* __restrict__ order, const int32_t* __restrict__ start,
+                                      const int32_t* __restrict__ par, int64_t* __restrict__ chunks,
+                                      int32_t* __restrict__ tiles) {
     const int64_t e1 = n_dev ? min(i1, *n_dev) : i1;
     for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e1; i += (int64_t)gridDim.x * blockDim.x) {
         if (!ch_seg_first(segend, i, i0)) continue;
         const int64_t se = min(segend[i], e1);
-        int64_t a = i, k = coff[i - i0];
+        int64_t a = i, k = coff[i - i0], t = toff[i - i0];
         while (a < se) {
             int64_t e = a + 1;
             while (e < se && off[e + 1] - off[a] <= cap) ++e;
-            chunks[2 * k] = a;
-            chunks[2 * k + 1] = e;
+            const int32_t p0 = par[order ? order[a] : a];
+            chunks[4 * k] = off[a];
+            chunks[4 * k + 1] = (int64_t)(((uint64_t)(uint32_t)p0 << 32) | (uint64_t)(off[e] - off[a]));
+            chunks[4 * k + 2] = t;
+            for (int64_t j = a; j < e; ++j) {
+                const int first = (int)(off[j] - off[a]), rows = (int)(off[j + 1] - off[j]);
+                const int st = start[order ? order[j] : j];
+                for (int r0 = 0; r0 < rows; r0 += 16, ++t) {
+                    tiles[4 * t] = first + r0;
+                    tiles[4 * t + 1] = min(16, rows - r0);
+                    tiles[4 * t + 2] = first;
+                    tiles[4 * t + 3] = st;
+                }
+            }
+            chunks[4 * k + 3] = t;
             ++k;
             a = e;
         }
@@ -350,10 +370,8 @@ constexpr int CH_ATT_HG = 2;                            // heads per staging gro
 template <int MODE, int DH, int H>
 __global__ void __launch_bounds__(CH_ATT_THREADS, 6)
 ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, const int64_t* __restrict__ chunks,
-                    const int64_t* __restrict__ n_chunks, const int32_t* __restrict__ order,
-                    const int32_t* __restrict__ par, const int64_t* __restrict__ off, int64_t row_base,
-                    const uint8_t* __restrict__ rpos, const uint8_t* __restrict__ rstart, const float* __restrict__ kv,
-                    int L, int l) {
+                    const int64_t* __restrict__ n_chunks, int64_t row_base, const uint8_t* __restrict__ rpos,
+                    const uint8_t* __restrict__ rstart, const float* __restrict__ kv, int L, int l) {
     extern __shared__ __align__(16) float ch_att_sm[];
     constexpr int D = H * DH;
     constexpr int HG = H < CH_ATT_HG ? H : CH_ATT_HG;   // heads per staging group
@@ -370,10 +388,10 @@ ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, 
     for (int64_t wi = blockIdx.x; wi < nck * (H / HG); wi += gridDim.x) {
         const int64_t ck = wi / (H / HG);
         const int h0 = (int)(wi % (H / HG)) * HG;
-        const int64_t a = chunks[2 * ck], e = chunks[2 * ck + 1];
-        const int32_t p0 = par[order ? order[a] : a];
-        const int64_t r_lo = off[a] - row_base;
-        const int nrows = (int)(off[e] - off[a]);
+        const int64_t r_lo = chunks[4 * ck] - row_base;
+        const uint64_t rec = (uint64_t)chunks[4 * ck + 1];
+        const int32_t p0 = (int32_t)(uint32_t)(rec >> 32);
+        const int nrows = (int)(uint32_t)rec;
         for (int c = threadIdx.x; c < nrows * C4; c += blockDim.x) {
             const int r = c / C4, w = c % C4;
             const int kvsel = w / (C4 / 2), col = 4 * (w % (C4 / 2));      // col within the group's heads
@@ -466,25 +484,35 @@ ch_attention_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, 
 // ---------------------------------------------------------------- attention on the mma.sync path
 // The same causal attention for the bf16 forms with head size 16, on the tensor path (mma.sync
 // m16n8k16, bf16 operands, fp32 accumulate) with every product in the compensated form
-// x y ~ x_hi y_hi + x_hi y_lo + x_lo y_hi (hi = bf16(x), lo = bf16(x - hi)).  A warp takes a
-// tile of up to 16 consecutive rows of ONE job and one head, and runs the online softmax over
-// key positions in steps of 16 (positions 16 k .. 16 k + 15 for every row, whatever its job):
-// the keys of a step are gathered by ldmatrix from per-lane row addresses, position p from the
-// staged parent when p < start and from the job's own staged row otherwise, so the arithmetic
-// of a row is the same whichever job (and prefix depth) it is computed in -- the local
-// energies stay independent of the prefix depth bit for bit.  Positions after a row's own are
-// masked (their weights are exactly 0).
+// x y ~ x_hi y_hi + x_hi y_lo + x_lo y_hi (hi = bf16(x), lo = bf16(x - hi)).  The projection
+// writes q, k and v already split (the split layout of tc_gemm_bf16: [Q hi | Q lo | K hi | K lo |
+// V hi | V lo] per row; the caches hold [K hi | K lo | V hi | V lo] per position), so staging is
+// a plain asynchronous copy.  A CTA takes (chunk, head) items, interleaved over the grid, and
+// stages the next item (cp.async, double-buffered) while it computes the current one.  A warp
+// takes a tile of up to 16 consecutive rows of ONE job from the chunk's tile table and runs the
+// online softmax over key positions in steps of 16 (positions 16 k .. 16 k + 15 for every row,
+// whatever its job): the keys of a step are gathered by ldmatrix from per-lane row addresses,
+// position p from the staged parent when p < start and from the job's own staged row
+// otherwise, so the arithmetic of a row is the same whichever job (and prefix depth) it is
+// computed in -- the local energies stay independent of the prefix depth bit for bit.
+// Positions after a row's own are masked (their weights are exactly 0).
 // Fragment layouts (PTX ISA, m16n8k16 .bf16; g = lane / 4, c = lane % 4): A {(g, 2c..2c+1),
 // (g+8, 2c..), (g, 2c+8..), (g+8, 2c+8..)}; B {(k 2c..2c+1, n g), (k 2c+8.., n g)}; C {(g, 2c),
 // (g, 2c+1), (g+8, 2c), (g+8, 2c+1)}.
-// Shared staging: per key slot and head a 128-byte record of eight 16-byte segments (K hi
-// dims 0-7, 8-15, K lo 0-7, 8-15, V hi 0-7, 8-15, V lo 0-7, 8-15), segment s of slot k stored
-// at position s ^ (k & 7) so that eight consecutive slots read by one ldmatrix sit on
-// distinct banks.  Slots [0, n): the parent's positions; slots n + r: the chunk's row r (plus
-// 15 zeroed slots past the last row, read only under the mask).
+// Staging buffer: key slots of 128 bytes = eight 16-byte segments (K hi dims 0-7, 8-15, K lo
+// 0-7, 8-15, V hi 0-7, 8-15, V lo 0-7, 8-15), segment s of slot k at position s ^ (k & 7) so
+// that eight consecutive slots read by one ldmatrix sit on distinct banks; slots [0, n) hold the
+// parent's positions, slot n + r the chunk's row r (then 15 zeroed slots, read only under the
+// mask).  Then the chunk's query rows (hi 0-7, hi 8-15, lo 0-7, lo 8-15 and 16 bytes of padding
+// per row: eight consecutive rows on distinct banks) and its tile table.
 constexpr int CHM_THREADS = 128;
-constexpr int CHM_HG = 4;                // heads per staging group
-constexpr int CHM_MAX_TILES = 64;        // 16-row tiles of one chunk (chunk rows <= 64)
+constexpr int CHM_MAX_TILES = 64;      // 16-row tiles of one chunk (chunk rows <= 64)
+constexpr int CHM_QSTRIDE = 80;        // bytes per staged query row
+
+__host__ __device__ inline int chm_buf_bytes(int n, int cap) {
+    const int b = (n + cap + 15) * 128 + cap * CHM_QSTRIDE + CHM_MAX_TILES * 16;
+    return (b + 127) & ~127;
+}
 
 __device__ __forceinline__ void chm_split2(float x, float y, uint32_t& hi, uint32_t& lo) {
     const __nv_bfloat162 hh = __floats2bfloat162_rn(x, y);
@@ -517,29 +545,16 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
 }
-
-// Byte offset of segment `seg` of key slot `slot`, head `hl` (HG heads per slot).
-template <int HG>
-__device__ __forceinline__ uint32_t chm_seg(int slot, int hl, int seg) {
-    return (uint32_t)((((slot * HG + hl) << 3) + (seg ^ (slot & 7))) << 4);
+__device__ __forceinline__ void cp_async16_s(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// 16 floats -> their hi and lo bf16 halves as two 16-byte segment pairs at slot/head.
-template <int HG>
-__device__ __forceinline__ void chm_stage16(uint32_t keys, int slot, int hl, int seg0, const float4 (&v)[4]) {
-    uint32_t hi[8], lo[8];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        chm_split2(v[i].x, v[i].y, hi[2 * i], lo[2 * i]);
-        chm_split2(v[i].z, v[i].w, hi[2 * i + 1], lo[2 * i + 1]);
-    }
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(keys + chm_seg<HG>(slot, hl, seg0 + s)),
-                     "r"(hi[4 * s]), "r"(hi[4 * s + 1]), "r"(hi[4 * s + 2]), "r"(hi[4 * s + 3]) : "memory");
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(keys + chm_seg<HG>(slot, hl, seg0 + 2 + s)),
-                     "r"(lo[4 * s]), "r"(lo[4 * s + 1]), "r"(lo[4 * s + 2]), "r"(lo[4 * s + 3]) : "memory");
-    }
+// Byte offset of segment `seg` of key slot `slot`.
+__device__ __forceinline__ uint32_t chm_seg(int slot, int seg) {
+    return (uint32_t)(((slot << 3) + (seg ^ (slot & 7))) << 4);
 }
 
 template <int MODE>
@@ -555,116 +570,119 @@ __device__ __forceinline__ void chm_store2(void* o, int64_t row, int D, int col,
     }
 }
 
+struct ChmItem {
+    int64_t r_lo;       // chunk's first row within the pass
+    int nrows, p0;      // chunk rows, parent job (-1: none)
+    int t0, nt;         // tiles: first (in the pass's list), count
+};
+
+__device__ __forceinline__ ChmItem chm_item(const int64_t* __restrict__ chunks, int64_t ck, int64_t row_base) {
+    const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(chunks + 4 * ck));
+    const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(chunks + 4 * ck + 2));
+    ChmItem it;
+    it.r_lo = a.x - row_base;
+    it.nrows = (int)(uint32_t)(uint64_t)a.y;
+    it.p0 = (int)(uint32_t)((uint64_t)a.y >> 32);
+    it.t0 = (int)b.x;
+    it.nt = (int)min(b.y - b.x, (long long)CHM_MAX_TILES);   // a chunk's rows (and tiles) are <= 64
+    return it;
+}
+
+template <int H>
+__device__ __forceinline__ void chm_stage(const ChmItem& it, int hh, uint32_t kb, uint32_t qb, uint32_t tb,
+                                          const uint16_t* __restrict__ qkv, const uint16_t* __restrict__ kv,
+                                          const int32_t* __restrict__ tiles, int n, int L, int l) {
+    constexpr int D = H * 16, RW = 6 * D;
+    // own rows: eight key/value segments (K hi at 2D, K lo 3D, V hi 4D, V lo 5D) and four query
+    // segments (Q hi at 0, Q lo at D) per row
+    for (int u = threadIdx.x; u < it.nrows * 12; u += CHM_THREADS) {
+        const int r = u / 12, k = u - 12 * r;
+        const uint16_t* row = qkv + (it.r_lo + r) * RW + hh * 16;
+        if (k < 8) cp_async16_s(kb + chm_seg(n + r, k), row + 2 * D + (k >> 1) * D + (k & 1) * 8);
+        else cp_async16_s(qb + r * CHM_QSTRIDE + (k - 8) * 16, row + ((k - 8) >> 1) * D + (k & 1) * 8);
+    }
+    for (int u = threadIdx.x; u < 15 * 8; u += CHM_THREADS)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(kb + chm_seg(n + it.nrows + (u >> 3), u & 7)),
+                     "r"(0u) : "memory");
+    if (it.p0 >= 0) {
+        const uint16_t* pre = kv + (((int64_t)it.p0 * L + l) * (int64_t)n) * 4 * D + hh * 16;
+        for (int u = threadIdx.x; u < n * 8; u += CHM_THREADS) {
+            const int p = u >> 3, k = u & 7;
+            cp_async16_s(kb + chm_seg(p, k), pre + (int64_t)p * 4 * D + (k >> 1) * D + (k & 1) * 8);
+        }
+    }
+    for (int u = threadIdx.x; u < it.nt; u += CHM_THREADS) cp_async16_s(tb + u * 16, tiles + 4 * (int64_t)(it.t0 + u));
+}
+
 template <int MODE, int H>
-__global__ void __launch_bounds__(CHM_THREADS, 3)
-ch_attention_mma_kernel(const float* __restrict__ qkv, void* __restrict__ o, int n, const int64_t* __restrict__ chunks,
-                        const int64_t* __restrict__ n_chunks, const int32_t* __restrict__ order,
-                        const int32_t* __restrict__ par, const int64_t* __restrict__ off, int64_t row_base,
-                        const uint8_t* __restrict__ rpos, const uint8_t* __restrict__ rstart,
-                        const float* __restrict__ kv, int L, int l, int cap) {
+__global__ void __launch_bounds__(CHM_THREADS, 4)
+ch_attention_mma_kernel(const uint16_t* __restrict__ qkv, void* __restrict__ o, int n, int cap,
+                        const int64_t* __restrict__ chunks, const int64_t* __restrict__ n_chunks,
+                        const int32_t* __restrict__ tiles, int64_t row_base, const uint16_t* __restrict__ kv, int L,
+                        int l) {
     extern __shared__ __align__(128) uint8_t chm_sm[];
-    constexpr int DH = 16, D = H * DH, ld = 3 * D;
-    constexpr int HG = H < CHM_HG ? H : CHM_HG;
-    constexpr int NW = CHM_THREADS / 32;
-    int4* tiles = reinterpret_cast<int4*>(chm_sm);                    // (row0, rows, own0, start)
-    int* s_ntiles = reinterpret_cast<int*>(chm_sm + CHM_MAX_TILES * sizeof(int4));
-    const uint32_t keys = (uint32_t)__cvta_generic_to_shared(chm_sm + CHM_MAX_TILES * sizeof(int4) + 16);
-    (void)rpos;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, c = lane & 3;
+    __shared__ int grab[2];
+    constexpr int DH = 16, D = H * DH;
+    const int BUF = chm_buf_bytes(n, cap);
+    const uint32_t sm0 = (uint32_t)__cvta_generic_to_shared(chm_sm);
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, c = lane & 3, mj = lane >> 3, rr = lane & 7;
     const float scale = 0.25f * 1.4426950408889634f;                // rsqrt(16) log2(e)
-    const int64_t nck = *n_chunks;
-    for (int64_t wi = blockIdx.x; wi < nck * (H / HG); wi += gridDim.x) {
-        const int64_t ck = wi / (H / HG);
-        const int h0 = (int)(wi % (H / HG)) * HG;
-        const int64_t a = chunks[2 * ck], e = chunks[2 * ck + 1];
-        const int32_t p0 = par[order ? order[a] : a];
-        const int64_t r_lo = off[a] - row_base;
-        const int nrows = (int)(off[e] - off[a]);
-        // own rows -> slots n + r; 15 zero slots after them
-        for (int u = threadIdx.x; u < (nrows + 15) * HG * 2; u += CHM_THREADS) {
-            const int r = u / (2 * HG), hl = (u >> 1) % HG, kvsel = u & 1;
-            float4 v[4];
-            if (r < nrows) {
-                const float4* src = reinterpret_cast<const float4*>(qkv + (r_lo + r) * ld + D + kvsel * D + (h0 + hl) * DH);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = __ldg(src + i);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            chm_stage16<HG>(keys, n + r, hl, 4 * kvsel, v);
+    const int64_t items = *n_chunks * H;
+    const int64_t G = gridDim.x;
+    int64_t wi = blockIdx.x;
+    if (wi >= items) return;
+    ChmItem cur = chm_item(chunks, wi / H, row_base), nxt{};
+    if (wi + G < items) nxt = chm_item(chunks, (wi + G) / H, row_base);
+    chm_stage<H>(cur, (int)(wi % H), sm0, sm0 + (n + cap + 15) * 128, sm0 + (n + cap + 15) * 128 + cap * CHM_QSTRIDE,
+                 qkv, kv, tiles, n, L, l);
+    if (threadIdx.x == 0) grab[0] = 0;
+    cp_async_commit();
+    for (int k = 0; wi < items; ++k, wi += G) {
+        const int b = k & 1;
+        const int64_t wn = wi + G, wn2 = wi + 2 * G;
+        ChmItem nx2{};
+        if (wn2 < items) nx2 = chm_item(chunks, wn2 / H, row_base);
+        const uint32_t kb1 = sm0 + (b ^ 1) * BUF;
+        if (wn < items) {
+            chm_stage<H>(nxt, (int)(wn % H), kb1, kb1 + (n + cap + 15) * 128,
+                         kb1 + (n + cap + 15) * 128 + cap * CHM_QSTRIDE, qkv, kv, tiles, n, L, l);
+            if (threadIdx.x == 0) grab[b ^ 1] = 0;
         }
-        if (p0 >= 0) {
-            const float* pre = kv + (((int64_t)p0 * L + l) * (int64_t)n) * 2 * D;
-            for (int u = threadIdx.x; u < n * HG * 2; u += CHM_THREADS) {
-                const int p = u / (2 * HG), hl = (u >> 1) % HG, kvsel = u & 1;
-                const float4* src = reinterpret_cast<const float4*>(pre + (int64_t)p * 2 * D + kvsel * D + (h0 + hl) * DH);
-                float4 v[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = __ldg(src + i);
-                chm_stage16<HG>(keys, p, hl, 4 * kvsel, v);
-            }
-        }
-        // the chunk's 16-row tiles, job by job
-        if (warp == 0) {
-            int base = 0;
-            for (int64_t j0 = a; j0 < e; j0 += 32) {
-                const int64_t j = j0 + lane;
-                int nt = 0, first = 0, rows = 0, st = 0;
-                if (j < e) {
-                    first = (int)(off[j] - off[a]);
-                    rows = (int)(off[j + 1] - off[j]);
-                    st = rows > 0 ? (int)rstart[r_lo + first] : 0;
-                    nt = (rows + 15) >> 4;
-                }
-                int incl = nt;
-#pragma unroll
-                for (int dd = 1; dd < 32; dd <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, dd);
-                    if (lane >= dd) incl += y;
-                }
-                const int ex = base + incl - nt;
-                for (int i = 0; i < nt; ++i)
-                    if (ex + i < CHM_MAX_TILES) tiles[ex + i] = make_int4(first + 16 * i, min(16, rows - 16 * i), first, st);
-                base += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            if (lane == 0) *s_ntiles = min(base, CHM_MAX_TILES);
-        }
+        cp_async_commit();
+        cp_async_wait<1>();
         __syncthreads();
-        const int ntile = *s_ntiles;
-        for (int it = warp; it < ntile * HG; it += NW) {
-            const int4 tl = tiles[it / HG];
-            const int hl = it % HG, hh = h0 + hl;
-            const int row0 = tl.x, cnt = tl.y, own0 = tl.z, st = tl.w;
+        // compute item wi from buffer b
+        const int hh = (int)(wi % H);
+        const uint32_t kb = sm0 + b * BUF, qb = kb + (n + cap + 15) * 128, tb = qb + cap * CHM_QSTRIDE;
+        for (;;) {
+            int ti = 0;
+            if (lane == 0) ti = atomicAdd(&grab[b], 1);
+            ti = __shfl_sync(0xffffffffu, ti, 0);
+            if (ti >= cur.nt) break;
+            int row0, cnt, own0, st;
+            asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(row0), "=r"(cnt), "=r"(own0), "=r"(st) : "r"(tb + ti * 16));
             const int t0 = st + (row0 - own0);                 // position of the tile's first row
             const int tlast = t0 + cnt - 1;
             const int ta = g < cnt ? t0 + g : tlast;           // padding rows mirror the last row
-            const int tb = g + 8 < cnt ? t0 + g + 8 : tlast;
+            const int tb2 = g + 8 < cnt ? t0 + g + 8 : tlast;
             uint32_t qh[4], ql[4];
             {
-                const float* qa = qkv + (r_lo + row0 + (ta - t0)) * ld + hh * DH + 2 * c;
-                const float* qb = qkv + (r_lo + row0 + (tb - t0)) * ld + hh * DH + 2 * c;
-                const float2 x0 = __ldg(reinterpret_cast<const float2*>(qa));
-                const float2 x1 = __ldg(reinterpret_cast<const float2*>(qb));
-                const float2 x2 = __ldg(reinterpret_cast<const float2*>(qa + 8));
-                const float2 x3 = __ldg(reinterpret_cast<const float2*>(qb + 8));
-                chm_split2(x0.x * scale, x0.y * scale, qh[0], ql[0]);
-                chm_split2(x1.x * scale, x1.y * scale, qh[1], ql[1]);
-                chm_split2(x2.x * scale, x2.y * scale, qh[2], ql[2]);
-                chm_split2(x3.x * scale, x3.y * scale, qh[3], ql[3]);
+                const int qr = row0 + min(rr + 8 * (mj & 1), cnt - 1);
+                ldsm_x4(qb + qr * CHM_QSTRIDE + (mj >> 1) * 16, qh);
+                ldsm_x4(qb + qr * CHM_QSTRIDE + (2 + (mj >> 1)) * 16, ql);
             }
             float O[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
             float m[2] = {-INFINITY, -INFINITY}, lsum[2] = {0.f, 0.f};
-            const int mj = lane >> 3, rr = lane & 7;
             for (int pb = 0; pb <= tlast; pb += 16) {
                 // per-lane ldmatrix rows: K (matrices: keys 0-7 / 8-15 x dims 0-7 / 8-15), V transposed
                 const int pk = pb + rr + 8 * (mj >> 1), pv = pb + rr + 8 * (mj & 1);
                 const int sk = pk < st ? pk : n + own0 + (pk - st);
                 const int sv = pv < st ? pv : n + own0 + (pv - st);
                 uint32_t kh[4], kl[4];
-                ldsm_x4(keys + chm_seg<HG>(sk, hl, mj & 1), kh);
-                ldsm_x4(keys + chm_seg<HG>(sk, hl, 2 + (mj & 1)), kl);
+                ldsm_x4(kb + chm_seg(sk, mj & 1), kh);
+                ldsm_x4(kb + chm_seg(sk, 2 + (mj & 1)), kl);
                 float S[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
                 chm_mma3(S[0], qh, ql, kh[0], kh[1], kl[0], kl[1]);
                 chm_mma3(S[1], qh, ql, kh[2], kh[3], kl[2], kl[3]);
@@ -674,8 +692,8 @@ ch_attention_mma_kernel(const float* __restrict__ qkv, void* __restrict__ o, int
 #pragma unroll
                     for (int ee = 0; ee < 2; ++ee) {
                         const int p = pb + 8 * nt + 2 * c + ee;
-                        S[nt][ee] = p <= ta ? S[nt][ee] : -INFINITY;
-                        S[nt][2 + ee] = p <= tb ? S[nt][2 + ee] : -INFINITY;
+                        S[nt][ee] = p <= ta ? S[nt][ee] * scale : -INFINITY;
+                        S[nt][2 + ee] = p <= tb2 ? S[nt][2 + ee] * scale : -INFINITY;
                         mx[0] = fmaxf(mx[0], S[nt][ee]);
                         mx[1] = fmaxf(mx[1], S[nt][2 + ee]);
                     }
@@ -706,8 +724,8 @@ ch_attention_mma_kernel(const float* __restrict__ qkv, void* __restrict__ o, int
                 chm_split2(S[1][0], S[1][1], ph[2], pl[2]);
                 chm_split2(S[1][2], S[1][3], ph[3], pl[3]);
                 uint32_t vh[4], vl[4];
-                ldsm_x4_t(keys + chm_seg<HG>(sv, hl, 4 + (mj >> 1)), vh);
-                ldsm_x4_t(keys + chm_seg<HG>(sv, hl, 6 + (mj >> 1)), vl);
+                ldsm_x4_t(kb + chm_seg(sv, 4 + (mj >> 1)), vh);
+                ldsm_x4_t(kb + chm_seg(sv, 6 + (mj >> 1)), vl);
                 chm_mma3(O[0], ph, pl, vh[0], vh[1], vl[0], vl[1]);
                 chm_mma3(O[1], ph, pl, vh[2], vh[3], vl[2], vl[3]);
             }
@@ -720,12 +738,15 @@ ch_attention_mma_kernel(const float* __restrict__ qkv, void* __restrict__ o, int
 #pragma unroll
             for (int n2 = 0; n2 < 2; ++n2) {
                 const int col = hh * DH + 8 * n2 + 2 * c;
-                if (g < cnt) chm_store2<MODE>(o, r_lo + row0 + g, D, col, O[n2][0] * ia, O[n2][1] * ia);
-                if (g + 8 < cnt) chm_store2<MODE>(o, r_lo + row0 + g + 8, D, col, O[n2][2] * ib, O[n2][3] * ib);
+                if (g < cnt) chm_store2<MODE>(o, cur.r_lo + row0 + g, D, col, O[n2][0] * ia, O[n2][1] * ia);
+                if (g + 8 < cnt) chm_store2<MODE>(o, cur.r_lo + row0 + g + 8, D, col, O[n2][2] * ib, O[n2][3] * ib);
             }
         }
         __syncthreads();
+        cur = nxt;
+        nxt = nx2;
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- heads
@@ -946,9 +967,8 @@ size_t ch_attention_smem(int n) {
 
 template <int MODE, int DH, int H>
 int ch_attention_launch(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks, const int64_t* n_chunks,
-                        int64_t max_chunks, const int32_t* order, const int32_t* par, const int64_t* off,
-                        int64_t row_base, const uint8_t* rpos, const uint8_t* rstart, const float* kv, int l,
-                        cudaStream_t s) {
+                        int64_t max_chunks, int64_t row_base, const uint8_t* rpos, const uint8_t* rstart,
+                        const float* kv, int l, cudaStream_t s) {
     const int n = mc.n;
     const size_t smem = ch_attention_smem<MODE, DH, H>(n);
     static int configured = -1;
@@ -963,24 +983,19 @@ int ch_attention_launch(const ModelConst& mc, const float* qkv, void* o, const i
     const int per_sm = std::max(1, std::min(6, (int)((227 * 1024) / (smem + 1024))));
     constexpr int GROUPS = H < CH_ATT_HG ? 1 : H / CH_ATT_HG;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks * GROUPS, (int64_t)num_sms() * per_sm));
-    ch_attention_kernel<MODE, DH, H><<<grid, CH_ATT_THREADS, smem, s>>>(qkv, o, n, chunks, n_chunks, order, par, off,
-                                                                       row_base, rpos, rstart, kv, mc.layers, l);
+    ch_attention_kernel<MODE, DH, H><<<grid, CH_ATT_THREADS, smem, s>>>(qkv, o, n, chunks, n_chunks, row_base, rpos,
+                                                                       rstart, kv, mc.layers, l);
     NQS_LAUNCHED();
     return NQS_OK;
 }
 
-inline size_t ch_attention_mma_smem(int n, int cap, int HG) {
-    return (size_t)CHM_MAX_TILES * 16 + 16 + (size_t)(n + cap + 15) * HG * 128;
-}
-
+// Tensor-path attention over the split layout (bf16 forms, head size 16).
 template <int MODE, int H>
-int ch_attention_mma_launch(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks,
-                            const int64_t* n_chunks, int64_t max_chunks, const int32_t* order, const int32_t* par,
-                            const int64_t* off, int64_t row_base, const uint8_t* rpos, const uint8_t* rstart,
-                            const float* kv, int l, cudaStream_t s) {
-    constexpr int HG = H < CHM_HG ? H : CHM_HG;
+int ch_attention_mma_launch(const ModelConst& mc, const void* qkv, void* o, const int64_t* chunks,
+                            const int64_t* n_chunks, int64_t max_chunks, const int32_t* tiles, int64_t row_base,
+                            const void* kv, int l, cudaStream_t s) {
     const int n = mc.n, cap = ch_chunk_cap(n);
-    const size_t smem = ch_attention_mma_smem(n, cap, HG);
+    const size_t smem = 2 * (size_t)chm_buf_bytes(n, cap);
     static int configured = -1;
     int dev = 0;
     NQS_CK(cudaGetDevice(&dev));
@@ -989,31 +1004,46 @@ int ch_attention_mma_launch(const ModelConst& mc, const float* qkv, void* o, con
                                     220 * 1024));
         configured = dev;
     }
-    if (smem > 220 * 1024) { set_error("prefix-sharing attention: staging exceeds shared memory"); return NQS_ERR_UNSUPPORTED; }
-    const int per_sm = std::max(1, std::min(3, (int)((227 * 1024) / (smem + 1024))));
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks * (H / HG), (int64_t)num_sms() * per_sm));
-    ch_attention_mma_kernel<MODE, H><<<grid, CHM_THREADS, smem, s>>>(qkv, o, n, chunks, n_chunks, order, par, off,
-                                                                    row_base, rpos, rstart, kv, mc.layers, l, cap);
+    if (smem > 220 * 1024 || cap > CHM_MAX_TILES) {
+        set_error("prefix-sharing attention: staging exceeds shared memory");
+        return NQS_ERR_UNSUPPORTED;
+    }
+    const int per_sm = std::max(1, std::min(4, (int)((227 * 1024) / (smem + 1024))));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks * H, (int64_t)num_sms() * per_sm));
+    ch_attention_mma_kernel<MODE, H><<<grid, CHM_THREADS, smem, s>>>(
+        reinterpret_cast<const uint16_t*>(qkv), o, n, cap, chunks, n_chunks, tiles, row_base,
+        reinterpret_cast<const uint16_t*>(kv), mc.layers, l);
     NQS_LAUNCHED();
     return NQS_OK;
 }
 
+// The attention of a pass: the tensor path for the bf16 forms with head size 16 (q, k, v and the
+// caches in the split layout), else the CUDA-core kernel (fp32 layout).
+template <int MODE>
+bool ch_split_qkv(const ModelConst& mc) {
+    return (MODE == ACT_BF16 || MODE == ACT_BF16X2) && mc.hidden == 16 * mc.heads &&
+           (mc.heads == 1 || mc.heads == 2 || mc.heads == 4 || mc.heads == 8);
+}
+
 template <int MODE>
 int ch_attention(const ModelConst& mc, const float* qkv, void* o, const int64_t* chunks, const int64_t* n_chunks,
-                 int64_t max_chunks, const int32_t* order, const int32_t* par, const int64_t* off, int64_t row_base,
-                 const uint8_t* rpos, const uint8_t* rstart, const float* kv, int l, cudaStream_t s) {
+                 int64_t max_chunks, const int32_t* tiles, int64_t row_base, const uint8_t* rpos,
+                 const uint8_t* rstart, const float* kv, int l, cudaStream_t s) {
     if (max_chunks <= 0) return NQS_OK;
     const int H = mc.heads, dh = mc.hidden / mc.heads;
-    if ((MODE == ACT_BF16 || MODE == ACT_BF16X2) && dh == 16) {
-        if (H == 1) return ch_attention_mma_launch<MODE, 1>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
-        if (H == 2) return ch_attention_mma_launch<MODE, 2>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
-        if (H == 4) return ch_attention_mma_launch<MODE, 4>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
-        if (H == 8) return ch_attention_mma_launch<MODE, 8>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off, row_base, rpos, rstart, kv, l, s);
+    if constexpr (MODE == ACT_BF16 || MODE == ACT_BF16X2) {
+        if (ch_split_qkv<MODE>(mc)) {
+#define CH_MMA(H_)                                                                                                \
+            if (H == H_) return ch_attention_mma_launch<MODE, H_>(mc, qkv, o, chunks, n_chunks, max_chunks, tiles,  \
+                                                                  row_base, kv, l, s);
+            CH_MMA(1) CH_MMA(2) CH_MMA(4) CH_MMA(8)
+#undef CH_MMA
+        }
     }
 #define CH_ATT(DH_, H_)                                                                                           \
     if (dh == DH_ && H == H_)                                                                                     \
-        return ch_attention_launch<MODE, DH_, H_>(mc, qkv, o, chunks, n_chunks, max_chunks, order, par, off,      \
-                                                  row_base, rpos, rstart, kv, l, s);
+        return ch_attention_launch<MODE, DH_, H_>(mc, qkv, o, chunks, n_chunks, max_chunks, row_base, rpos,       \
+                                                  rstart, kv, l, s);
     CH_ATT(16, 1) CH_ATT(16, 2) CH_ATT(16, 4) CH_ATT(16, 8) CH_ATT(32, 1) CH_ATT(32, 2) CH_ATT(32, 4) CH_ATT(32, 8)
 #undef CH_ATT
     set_error("prefix-sharing attention: head size 16 or 32 with 1, 2, 4 or 8 heads");
@@ -1099,7 +1129,11 @@ void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int
     const int64_t max_slots = std::max(b.jobs_cap, rows_cap);
     b.ccnt = c.take<int64_t>(max_slots);
     b.coff = c.take<int64_t>(max_slots + 1);
-    b.chunks = c.take<int64_t>(2 * max_slots);
+    b.tcnt = c.take<int64_t>(max_slots);
+    b.toff = c.take<int64_t>(max_slots + 1);
+    b.chunks = c.take<int64_t>(4 * max_slots);
+    // 16-row tiles of one pass: at most one per 16 rows plus one per job
+    b.tiles = c.take<int32_t>(4 * (b.pass_rows / 16 + max_slots + 1));
     b.split = c.take<int64_t>(CHAIN_MAX_SPLIT + 1);
     b.split_off = c.take<int64_t>(CHAIN_MAX_SPLIT + 1);
     tf_layout(c, mc, (b.pass_rows + n - 1) / n, b.tf);
@@ -1139,14 +1173,18 @@ static int ch_forward(const ModelConst& mc, const float* P, const TfWeights& w, 
         if (M > 0) {
             ProfScope ps("ch_build", s);
             const int cap = ch_chunk_cap(n);
-            ch_chunk_count_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.ccnt);
+            ch_chunk_count_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.ccnt, b.tcnt);
             NQS_LAUNCHED();
             NQS_TRY(launch_scan_i64(b.ccnt, nsl, nullptr, b.coff, s));
-            ch_chunk_write_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.coff, b.chunks);
+            NQS_TRY(launch_scan_i64(b.tcnt, nsl, nullptr, b.toff, s));
+            ch_chunk_write_kernel<<<grid_for(nsl, 256), 256, 0, s>>>(joff, segend, nullptr, j0, j1, cap, b.coff, b.toff,
+                                                                     order, jstart, jpar, b.chunks, b.tiles);
             NQS_LAUNCHED();
         }
+        // q, k, v (and so the caches) in the split layout where the tensor-path attention runs
+        const int qkv_epi = ch_split_qkv<MODE>(mc) ? TF_EPI_SPLIT : TF_EPI_STORE;
         for (int l = 0; l < mc.layers; ++l) {
-            if (M > 0) NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, t.a, t.qkv, M, 3 * d, d, TF_EPI_STORE, P + mc.bqkv[l], s));
+            if (M > 0) NQS_TRY(tf_gemm(mc, w, TF_WQKV, l, t.a, t.qkv, M, 3 * d, d, qkv_epi, P + mc.bqkv[l], s));
             if (pass_a) {
                 ProfScope ps("ch_cache", s, 0.0, (double)(lev[3]) * n * 2 * d * 4 * 2);
                 for (int v = 0; v < 3; ++v) {
@@ -1159,8 +1197,8 @@ static int ch_forward(const ModelConst& mc, const float* P, const TfWeights& w, 
             if (M > 0) {
                 {
                     ProfScope ps("ch_attention", s, att_flops, (double)M * 3 * d * 4 + (double)M * d * act_b);
-                    NQS_TRY(ch_attention<MODE>(mc, t.qkv, t.o, b.chunks, b.coff + nsl, nsl, order, jpar, joff, row_base,
-                                               b.rpos, b.rstart, b.kv, l, s));
+                    NQS_TRY(ch_attention<MODE>(mc, t.qkv, t.o, b.chunks, b.coff + nsl, nsl, b.tiles, row_base, b.rpos,
+                                               b.rstart, b.kv, l, s));
                 }
                 NQS_TRY(tf_gemm(mc, w, TF_WO, l, t.o, t.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
                 {

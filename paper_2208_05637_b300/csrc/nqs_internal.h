@@ -242,7 +242,8 @@ int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t
 // transformer (transformer.cu, tc_gemm.cu)
 enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3, TF_EPI_GELU2 = 4,
        TF_EPI_RESID_LN = 5,     // h += acc + bias, then a = LayerNorm(h) as hi|lo bf16 (d = 64)
-       TF_EPI_RESID_LN_TAB = 6  // the same with the old h taken from a token-position table
+       TF_EPI_RESID_LN_TAB = 6, // the same with the old h taken from a token-position table
+       TF_EPI_SPLIT = 7         // QKV projection into the split layout (bf16 hi and lo planes; see tc_gemm_bf16)
 };
 // First-block rows that depend on the (token, position) pair only: the token of position t is 2
 // at t = 0 and bit order[t - 1] of the sequence's configuration after it; row (token, t) of a
@@ -324,7 +325,10 @@ int tf_segment_sum(const int64_t* seg, int64_t seg_stride, int64_t nseg, const f
 int tf_logpsi(const ModelConst& mc, const float* P, const TfWeights& w, const uint64_t* bits,
               int64_t B, float* la, float* ph, TfBufs& b, cudaStream_t s);
 // C[M,N] (epi) = A[M,K] (bf16) . W[N,K]^T (bf16) + bias on the tensor cores (tc_gemm.cu).
-// C is fp32 for TF_EPI_STORE / TF_EPI_RESID and bf16 for TF_EPI_GELU.
+// C is fp32 for TF_EPI_STORE / TF_EPI_RESID and bf16 for TF_EPI_GELU.  TF_EPI_SPLIT (N = 3 D, the
+// QKV projection) writes each value v as hi = bf16(v) and lo = bf16(v - hi) into a bf16 row of
+// 2 N: [Q hi | Q lo | K hi | K lo | V hi | V lo], D columns each -- the same 12 D bytes per row
+// as the fp32 [Q | K | V] row, with each of Q, K, V in its own third.
 int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, int64_t M, int N,
                  int K, int epi, cudaStream_t s);
 // transformer backward (tf_backward.cu)
@@ -396,7 +400,10 @@ struct ChainBufs {
     int32_t* rjob = nullptr;                                 // per pass row
     uint8_t* rpos = nullptr;
     uint8_t* rstart = nullptr;                               // per pass row: its job's first own position
-    int64_t *ccnt = nullptr, *coff = nullptr, *chunks = nullptr;   // attention chunks of a pass: [first, end) slots
+    // attention chunks of a pass: per chunk (first row offset, nrows | parent << 32, first tile,
+    // end tile); tiles of 16 rows of one job: (row0, rows, job's first row, job start)
+    int64_t *ccnt = nullptr, *coff = nullptr, *tcnt = nullptr, *toff = nullptr, *chunks = nullptr;
+    int32_t* tiles = nullptr;
     int64_t *split = nullptr, *split_off = nullptr;
     TfBufs tf{};
 };

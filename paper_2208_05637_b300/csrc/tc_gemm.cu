@@ -195,6 +195,18 @@ __device__ __forceinline__ void epilogue16(const float (&v16)[16], const float* 
             }
             *reinterpret_cast<uint4*>(C) = *reinterpret_cast<const uint4*>(hi);
             *reinterpret_cast<uint4*>(C + N) = *reinterpret_cast<const uint4*>(lo);
+        } else if (EPI == TF_EPI_SPLIT) {
+            // split layout: third `reg` of the row holds hi in its first D columns, lo in the next D
+            const int Dq = N / 3, reg = col / Dq, w = col - reg * Dq;
+            __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(Cv) + row * 2 * N + 2 * Dq * reg + w;
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hi[j] = __float2bfloat16_rn(v[j]);
+                lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+            }
+            *reinterpret_cast<uint4*>(C) = *reinterpret_cast<const uint4*>(hi);
+            *reinterpret_cast<uint4*>(C + Dq) = *reinterpret_cast<const uint4*>(lo);
         } else {
             float4* C = reinterpret_cast<float4*>(reinterpret_cast<float*>(Cv) + row * N + col);
             float4 x0 = make_float4(v[0], v[1], v[2], v[3]), x1 = make_float4(v[4], v[5], v[6], v[7]);
@@ -233,14 +245,14 @@ __device__ __forceinline__ void stage16(const float (&v16)[16], const float* __r
             __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float g = gelu_tanh(v[8 * u + j]);
+                const float g = EPI == TF_EPI_SPLIT ? v[8 * u + j] : gelu_tanh(v[8 * u + j]);
                 hi[j] = __float2bfloat16_rn(g);
-                if (EPI == TF_EPI_GELU2) lo[j] = __float2bfloat16_rn(g - __bfloat162float(hi[j]));
+                if (EPI == TF_EPI_GELU2 || EPI == TF_EPI_SPLIT) lo[j] = __float2bfloat16_rn(g - __bfloat162float(hi[j]));
             }
             const uint32_t off = (uint32_t)(((p16 * 2 + u) ^ sw) << 4);
             st_shared_v4(row + off, pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
                          pack_bf16(hi[6], hi[7]));
-            if (EPI == TF_EPI_GELU2)
+            if (EPI == TF_EPI_GELU2 || EPI == TF_EPI_SPLIT)
                 st_shared_v4(row + 4096 + off, pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
                              pack_bf16(lo[6], lo[7]));
         }
@@ -484,10 +496,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 // 128-byte chunks: 32 fp32 or 64 bf16 columns
                 constexpr int CW = (EPI == TF_EPI_STORE || EPI == TF_EPI_RESID) ? 32 : 64;
                 for (int c = 0; c < BN; c += CW, ++chunk) {
-                    uint8_t* sbuf = EPI == TF_EPI_GELU2 ? stg : stg + (chunk & 1) * 4096;
+                    constexpr bool HILO = EPI == TF_EPI_GELU2 || EPI == TF_EPI_SPLIT;
+                    uint8_t* sbuf = HILO ? stg : stg + (chunk & 1) * 4096;
                     // the buffer's previous TMA store must have finished reading it
                     if (lane == 0) {
-                        if (EPI == TF_EPI_GELU2) bulk_wait_read<0>();
+                        if (HILO) bulk_wait_read<0>();
                         else bulk_wait_read<1>();
                     }
                     __syncwarp();
@@ -500,9 +513,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0 && row0 < M) {
-                        if (EPI == TF_EPI_RESID) tma_reduce_add_2d(&tmC, sbuf, n0 + c, (int)row0);
-                        else tma_store_2d(&tmC, sbuf, n0 + c, (int)row0);
-                        if (EPI == TF_EPI_GELU2) tma_store_2d(&tmC, sbuf + 4096, N + n0 + c, (int)row0);
+                        if (EPI == TF_EPI_SPLIT) {
+                            // a 64-column chunk lies within one third of the row (D % 64 == 0)
+                            const int Dq = N / 3, col = n0 + c, reg = col / Dq, w = col - reg * Dq;
+                            tma_store_2d(&tmC, sbuf, 2 * Dq * reg + w, (int)row0);
+                            tma_store_2d(&tmC, sbuf + 4096, 2 * Dq * reg + Dq + w, (int)row0);
+                        } else {
+                            if (EPI == TF_EPI_RESID) tma_reduce_add_2d(&tmC, sbuf, n0 + c, (int)row0);
+                            else tma_store_2d(&tmC, sbuf, n0 + c, (int)row0);
+                            if (EPI == TF_EPI_GELU2) tma_store_2d(&tmC, sbuf + 4096, N + n0 + c, (int)row0);
+                        }
                     }
                     if (lane == 0) bulk_commit();
                 }
@@ -1583,8 +1603,13 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
     int tcols = 64;
     while (tcols < 2 * BN) tcols <<= 1;
     // staged TMA epilogue when the tile splits into 128-byte column chunks (32 fp32, 64 bf16)
+    if (epi == TF_EPI_SPLIT && (N % 48 || ((uintptr_t)C & 15))) {
+        set_error("split-layout GEMM needs N = 3 D with D % 16 == 0 and a 16-byte aligned output");
+        return NQS_ERR_UNSUPPORTED;
+    }
     const bool f32_out = epi == TF_EPI_STORE || epi == TF_EPI_RESID;
-    const bool tma_epi = BN % (f32_out ? 32 : 64) == 0 && ((uintptr_t)C & 15) == 0;
+    const bool tma_epi = BN % (f32_out ? 32 : 64) == 0 && ((uintptr_t)C & 15) == 0 &&
+                         (epi != TF_EPI_SPLIT || (N / 3) % 64 == 0);
     const size_t stage_bytes = TC_BM * 128 + (size_t)BN * 128;
     const size_t staging = tma_epi ? 4 * TC_STAGE_BYTES_PER_WARP : 0;
     // fill ~104 KB per CTA with ring stages (at least two) so that two CTAs share an SM
@@ -1594,7 +1619,7 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
     CUtensorMap ma, mb, mc;
     NQS_TRY(make_map(&ma, A, M, K, TC_BM));
     NQS_TRY(make_map(&mb, W, N, K, BN));
-    if (tma_epi) NQS_TRY(make_map(&mc, C, M, epi == TF_EPI_GELU2 ? 2 * N : N, 32, f32_out));
+    if (tma_epi) NQS_TRY(make_map(&mc, C, M, (epi == TF_EPI_GELU2 || epi == TF_EPI_SPLIT) ? 2 * N : N, 32, f32_out));
     else memset(&mc, 0, sizeof(mc));
     const int n_tiles_n = N / BN;
     const int64_t total_tiles = ((M + TC_BM - 1) / TC_BM) * n_tiles_n;
@@ -1627,6 +1652,8 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
         case TF_EPI_GELU * 2 + 1: return launch(tc_gemm_kernel<TF_EPI_GELU, true>);
         case TF_EPI_GELU2 * 2: return launch(tc_gemm_kernel<TF_EPI_GELU2, false>);
         case TF_EPI_GELU2 * 2 + 1: return launch(tc_gemm_kernel<TF_EPI_GELU2, true>);
+        case TF_EPI_SPLIT * 2: return launch(tc_gemm_kernel<TF_EPI_SPLIT, false>);
+        case TF_EPI_SPLIT * 2 + 1: return launch(tc_gemm_kernel<TF_EPI_SPLIT, true>);
         default: set_error("bad GEMM epilogue"); return NQS_ERR_INVALID_ARG;
     }
 }

@@ -395,7 +395,7 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
     const bool bf = mc.precision == NQS_PREC_BF16;
     const double split = (bf && mc.compensated) ? 2.0 : 1.0;
     const double a_el = bf ? 2.0 * split : 4.0, w_el = bf ? 2.0 * split : 4.0;
-    const double c_el = epi == TF_EPI_GELU ? (bf ? 2.0 * split : 4.0) : 4.0;
+    const double c_el = epi == TF_EPI_GELU ? (bf ? 2.0 * split : 4.0) : 4.0;   // TF_EPI_SPLIT: 2 x bf16
     const double bytes = (double)M * K * a_el + (double)N * K * w_el +
                          (double)M * N * c_el * (epi == TF_EPI_RESID ? 2.0 : 1.0);
     ProfScope ps("tf_gemm", s, 2.0 * (double)M * N * K, bytes);
@@ -405,6 +405,7 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
         const int e = (epi == TF_EPI_GELU && split) ? TF_EPI_GELU2 : epi;
         return tc_gemm_bf16(A, w.bf16 + w.bf16_off[layer][which], bias, C, M, N, split ? 2 * K : K, e, s);
     }
+    if (epi == TF_EPI_SPLIT) { set_error("split-layout projection needs a bf16 model"); return NQS_ERR_UNSUPPORTED; }
     const float* W = w.fp32 + w.fp32_off[layer][which];
     dim3 grid((unsigned)((N + SG_BN - 1) / SG_BN), (unsigned)((M + SG_BM - 1) / SG_BM));
     const float* Af = (const float*)A;
