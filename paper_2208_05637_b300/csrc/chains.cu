@@ -615,7 +615,7 @@ __device__ __forceinline__ void chm_stage(const ChmItem& it, int hh, uint32_t kb
 }
 
 template <int MODE, int H>
-__global__ void __launch_bounds__(CHM_THREADS, 4)
+__global__ void __launch_bounds__(CHM_THREADS, 5)
 ch_attention_mma_kernel(const uint16_t* __restrict__ qkv, void* __restrict__ o, int n, int cap,
                         const int64_t* __restrict__ chunks, const int64_t* __restrict__ n_chunks,
                         const int32_t* __restrict__ tiles, int64_t row_base, const uint16_t* __restrict__ kv, int L,
@@ -624,7 +624,7 @@ ch_attention_mma_kernel(const uint16_t* __restrict__ qkv, void* __restrict__ o, 
     __shared__ int grab[2];
     constexpr int DH = 16, D = H * DH;
     const int BUF = chm_buf_bytes(n, cap);
-    const uint32_t sm0 = (uint32_t)__cvta_generic_to_shared(chm_sm);
+    const uint32_t sm0 = ((uint32_t)__cvta_generic_to_shared(chm_sm) + 127u) & ~127u;   // 128-byte aligned buffers
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, c = lane & 3, mj = lane >> 3, rr = lane & 7;
     const float scale = 0.25f * 1.4426950408889634f;                // rsqrt(16) log2(e)
@@ -674,47 +674,61 @@ ch_attention_mma_kernel(const uint16_t* __restrict__ qkv, void* __restrict__ o, 
                 ldsm_x4(qb + qr * CHM_QSTRIDE + (2 + (mj >> 1)) * 16, ql);
             }
             float O[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            // running maxima of the raw scores q.k (the scale is folded into the exponent) and sums
             float m[2] = {-INFINITY, -INFINITY}, lsum[2] = {0.f, 0.f};
+            // per-lane ldmatrix rows: K (matrices: keys 0-7 / 8-15 x dims 0-7 / 8-15), V transposed;
+            // position p sits in parent slot p (p < start) or own slot n + own0 + p - start, and
+            // one step (+16 positions) moves either by 16 slots = 2048 bytes (the swizzle repeats
+            // every 8 slots).  The lo segment of a hi segment s is s + 2, stored at (s + 2) ^ (slot
+            // & 7) = (s ^ (slot & 7)) ^ 2: the hi address with bit 5 flipped (buffers are
+            // 128-byte aligned).
+            const int pk0 = rr + 8 * (mj >> 1), pv0 = rr + 8 * (mj & 1);
+            const uint32_t kpar = kb + chm_seg(pk0, mj & 1), vpar = kb + chm_seg(pv0, 4 + (mj >> 1));
+            const int ok0 = n + own0 - st;                     // own slot of position p: ok0 + p (>= 1)
+            const uint32_t kown = kb + chm_seg(ok0 + pk0, mj & 1);
+            const uint32_t vown = kb + chm_seg(ok0 + pv0, 4 + (mj >> 1));
             for (int pb = 0; pb <= tlast; pb += 16) {
-                // per-lane ldmatrix rows: K (matrices: keys 0-7 / 8-15 x dims 0-7 / 8-15), V transposed
-                const int pk = pb + rr + 8 * (mj >> 1), pv = pb + rr + 8 * (mj & 1);
-                const int sk = pk < st ? pk : n + own0 + (pk - st);
-                const int sv = pv < st ? pv : n + own0 + (pv - st);
+                const uint32_t ka = (pb + pk0 < st ? kpar : kown) + (uint32_t)pb * 128;
+                const uint32_t va = (pb + pv0 < st ? vpar : vown) + (uint32_t)pb * 128;
                 uint32_t kh[4], kl[4];
-                ldsm_x4(kb + chm_seg(sk, mj & 1), kh);
-                ldsm_x4(kb + chm_seg(sk, 2 + (mj & 1)), kl);
+                ldsm_x4(ka, kh);
+                ldsm_x4(ka ^ 32u, kl);           // K lo
                 float S[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
                 chm_mma3(S[0], qh, ql, kh[0], kh[1], kl[0], kl[1]);
                 chm_mma3(S[1], qh, ql, kh[2], kh[3], kl[2], kl[3]);
-                float mx[2] = {-INFINITY, -INFINITY};
+                if (pb + 15 > t0) {               // the causal edge runs through this step
 #pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
+                    for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                    for (int ee = 0; ee < 2; ++ee) {
-                        const int p = pb + 8 * nt + 2 * c + ee;
-                        S[nt][ee] = p <= ta ? S[nt][ee] * scale : -INFINITY;
-                        S[nt][2 + ee] = p <= tb2 ? S[nt][2 + ee] * scale : -INFINITY;
-                        mx[0] = fmaxf(mx[0], S[nt][ee]);
-                        mx[1] = fmaxf(mx[1], S[nt][2 + ee]);
-                    }
+                        for (int ee = 0; ee < 2; ++ee) {
+                            const int p = pb + 8 * nt + 2 * c + ee;
+                            if (p > ta) S[nt][ee] = -INFINITY;
+                            if (p > tb2) S[nt][2 + ee] = -INFINITY;
+                        }
+                }
+                float mx[2];
+                mx[0] = fmaxf(fmaxf(S[0][0], S[0][1]), fmaxf(S[1][0], S[1][1]));
+                mx[1] = fmaxf(fmaxf(S[0][2], S[0][3]), fmaxf(S[1][2], S[1][3]));
+                float ms[2];
 #pragma unroll
                 for (int hf = 0; hf < 2; ++hf) {
                     mx[hf] = fmaxf(mx[hf], __shfl_xor_sync(0xffffffffu, mx[hf], 1));
                     mx[hf] = fmaxf(mx[hf], __shfl_xor_sync(0xffffffffu, mx[hf], 2));
                     if (mx[hf] > m[hf]) {
-                        const float cr = ex2_approx(m[hf] - mx[hf]);   // 0 on the first step
+                        const float cr = ex2_approx((m[hf] - mx[hf]) * scale);   // 0 on the first step
                         lsum[hf] *= cr;
                         O[0][2 * hf] *= cr; O[0][2 * hf + 1] *= cr;
                         O[1][2 * hf] *= cr; O[1][2 * hf + 1] *= cr;
                         m[hf] = mx[hf];
                     }
+                    ms[hf] = -m[hf] * scale;
                 }
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                     for (int ee = 0; ee < 2; ++ee) {
-                        S[nt][ee] = ex2_approx(S[nt][ee] - m[0]);
-                        S[nt][2 + ee] = ex2_approx(S[nt][2 + ee] - m[1]);
+                        S[nt][ee] = ex2_approx(fmaf(S[nt][ee], scale, ms[0]));
+                        S[nt][2 + ee] = ex2_approx(fmaf(S[nt][2 + ee], scale, ms[1]));
                         lsum[0] += S[nt][ee];
                         lsum[1] += S[nt][2 + ee];
                     }
@@ -724,8 +738,8 @@ ch_attention_mma_kernel(const uint16_t* __restrict__ qkv, void* __restrict__ o, 
                 chm_split2(S[1][0], S[1][1], ph[2], pl[2]);
                 chm_split2(S[1][2], S[1][3], ph[3], pl[3]);
                 uint32_t vh[4], vl[4];
-                ldsm_x4_t(kb + chm_seg(sv, 4 + (mj >> 1)), vh);
-                ldsm_x4_t(kb + chm_seg(sv, 6 + (mj >> 1)), vl);
+                ldsm_x4_t(va, vh);
+                ldsm_x4_t(va ^ 32u, vl);         // V lo
                 chm_mma3(O[0], ph, pl, vh[0], vh[1], vl[0], vl[1]);
                 chm_mma3(O[1], ph, pl, vh[2], vh[3], vl[2], vl[3]);
             }
@@ -995,7 +1009,7 @@ int ch_attention_mma_launch(const ModelConst& mc, const void* qkv, void* o, cons
                             const int64_t* n_chunks, int64_t max_chunks, const int32_t* tiles, int64_t row_base,
                             const void* kv, int l, cudaStream_t s) {
     const int n = mc.n, cap = ch_chunk_cap(n);
-    const size_t smem = 2 * (size_t)chm_buf_bytes(n, cap);
+    const size_t smem = 2 * (size_t)chm_buf_bytes(n, cap) + 128;
     static int configured = -1;
     int dev = 0;
     NQS_CK(cudaGetDevice(&dev));
@@ -1008,7 +1022,7 @@ int ch_attention_mma_launch(const ModelConst& mc, const void* qkv, void* o, cons
         set_error("prefix-sharing attention: staging exceeds shared memory");
         return NQS_ERR_UNSUPPORTED;
     }
-    const int per_sm = std::max(1, std::min(4, (int)((227 * 1024) / (smem + 1024))));
+    const int per_sm = std::max(1, std::min(5, (int)((227 * 1024) / (smem + 1024))));
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks * H, (int64_t)num_sms() * per_sm));
     ch_attention_mma_kernel<MODE, H><<<grid, CHM_THREADS, smem, s>>>(
         reinterpret_cast<const uint16_t*>(qkv), o, n, cap, chunks, n_chunks, tiles, row_base,

@@ -6,13 +6,13 @@
 // which needs two popcounts per (sample, group).  Out-of-sector flips have f(x') = 0 under the
 // Hamming-weight constraint (Section 4), so they contribute exactly zero and are skipped.
 //
-// Work decomposition: a CTA owns a tile of SWEEP_GT groups (one thread per group) and a batch
-// of SWEEP_SB samples held in shared memory.  Pass 1 (count) writes the number of valid
-// groups per (sample, tile); an exclusive scan turns these into row offsets, so rows come out
-// sample-major, tile-major, group-minor -- a deterministic layout independent of scheduling.
-// Pass 2 (emit) compacts the valid (sample, group) pairs of the batch into shared memory with
-// warp ballots and lets every thread take pairs from that list, so no lane idles on an
-// invalid group while its neighbours sum terms.
+// Work decomposition: a CTA owns a tile of SWEEP_GT groups and a batch of SWEEP_SB samples.
+// Pass 1 (count, one thread per group) writes for every sample its validity bitmap over the
+// tile's groups and the number of valid groups per (sample, tile); an exclusive scan turns the
+// counts into row offsets, so rows come out sample-major, tile-major, group-minor -- a
+// deterministic layout independent of scheduling.  Pass 2 (emit, one warp per sample at a
+// time) walks each sample's bitmap in group order, numbering the valid pairs as it goes, and
+// sums their terms from a shared-memory copy of the tile's terms.
 //
 // A sample outside the (n_up, n_dn) sector gets exactly one row, x' = x with S = NaN, in its
 // first group tile and no other: the rows stay within the per-sample bound of the feasible
@@ -33,14 +33,6 @@ __device__ __forceinline__ uint32_t up_bits(uint64_t v) {
 }
 __device__ __forceinline__ uint32_t dn_bits(uint64_t v) {
     return ((uint32_t)v & 0xAAAAAAAAu) | (((uint32_t)(v >> 32) & 0xAAAAAAAAu) >> 1);
-}
-
-// x' = x ^ m stays in the sector iff exactly half of the flipped bits of each species are
-// occupied in x: 2 popc(x & m & A) == n_alpha(m) and the same for spin down.
-__device__ __forceinline__ bool sector_ok(uint64_t x, uint64_t m, uint32_t meta) {
-    const uint64_t v = x & m;
-    return 2u * (uint32_t)__popc(up_bits(v)) == (meta & 0xffu) &&
-           2u * (uint32_t)__popc(dn_bits(v)) == ((meta >> 8) & 0xffu);
 }
 
 __device__ __forceinline__ bool sample_in_sector(uint64_t x, int n_up, int n_dn) {
@@ -99,58 +91,78 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
 }
 
 // Count pass: the sector test of every (sample, group) pair of a tile of SWEEP_GT groups and a
-// batch of SWEEP_SB samples.  Writes the number of valid groups per (sample, tile) and, for the
-// emit pass, each group's validity bits over the batch (one word per group and batch).
+// batch of SWEEP_SB samples (thread = group, the batch's samples in shared memory as their
+// spin-up and spin-down bit words, the group's flip mask split the same way once).  Each warp's
+// ballot of sample s is the validity word of s over the warp's 32 groups; lane s keeps it, so
+// the pass writes the tile's validity bitmap per sample, stored [batch][tile][warp][sample],
+// and the number of valid groups per (sample, tile).
 __global__ void __launch_bounds__(SWEEP_GT)
 sweep_count_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bits,
                    int64_t B, int32_t* __restrict__ cnt, int64_t ntiles, uint32_t* __restrict__ valid) {
-    __shared__ uint64_t xs[SWEEP_SB];
-    __shared__ int32_t wcnt[SWEEP_SB][SWEEP_NW];
-    __shared__ uint32_t oos;              // out-of-sector samples of the batch
+    __shared__ uint2 xs[SWEEP_SB];
+    __shared__ int32_t wcnt[SWEEP_NW][SWEEP_SB];
+    __shared__ uint32_t okm;              // in-sector samples of the batch
     const int tile = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * SWEEP_SB;
     const int nb = (int)(B - s0 < SWEEP_SB ? B - s0 : SWEEP_SB);
     const int64_t g = (int64_t)tile * SWEEP_GT + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool live = g < h.G;
     const uint64_t m = live ? h.grp_mask[g] : 0;
     const uint32_t meta = live ? h.grp_meta[g] : 0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < nb) xs[threadIdx.x] = bits[s0 + threadIdx.x];
-    if (warp == 0) {
-        const bool bad = lane < nb && !sample_in_sector(bits[s0 + min(lane, nb - 1)], n_up, n_dn);
-        const unsigned bb = __ballot_sync(0xffffffffu, bad);
-        if (lane == 0) oos = bb;
+    const uint32_t mu = up_bits(m), md = dn_bits(m);
+    // the occupied flipped bits each species needs: half its flipped bits (an odd count, or a
+    // group past the end, can never match: 64 is out of range)
+    const uint32_t na = meta & 0xffu, nbt = (meta >> 8) & 0xffu;
+    const uint32_t ta = (!live || (na & 1u)) ? 64u : na >> 1, tb = (nbt & 1u) ? 64u : nbt >> 1;
+    if (threadIdx.x < SWEEP_SB) {
+        const uint64_t x = threadIdx.x < nb ? bits[s0 + threadIdx.x] : 0ull;
+        xs[threadIdx.x] = make_uint2(up_bits(x), dn_bits(x));
+        const bool ok = threadIdx.x < nb && sample_in_sector(x, n_up, n_dn);
+        const unsigned bb = __ballot_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) okm = bb;
     }
     __syncthreads();
-    uint32_t vmask = 0;
-    for (int s = 0; s < nb; ++s) {
-        const bool v = live && sector_ok(xs[s], m, meta) && !((oos >> s) & 1u);
-        vmask |= (uint32_t)v << s;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int s = 0; s < SWEEP_SB; ++s) {
+        const uint2 xv = xs[s];
+        const bool v = (uint32_t)__popc(xv.x & mu) == ta && (uint32_t)__popc(xv.y & md) == tb;
         const unsigned bal = __ballot_sync(0xffffffffu, v);
-        if (lane == 0) wcnt[s][warp] = __popc(bal);
+        if (lane == s) mine = bal;
     }
-    valid[(int64_t)blockIdx.x * ntiles * SWEEP_GT + g] = vmask;
+    if (!((okm >> lane) & 1u)) mine = 0;       // samples past the batch or outside the sector
+    valid[(((int64_t)blockIdx.x * ntiles + tile) * SWEEP_NW + warp) * SWEEP_SB + lane] = mine;
+    wcnt[warp][lane] = __popc(mine);
     __syncthreads();
     if (threadIdx.x < nb) {
         int32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < SWEEP_NW; ++w) c += wcnt[threadIdx.x][w];
+        for (int w = 0; w < SWEEP_NW; ++w) c += wcnt[w][threadIdx.x];
         // out-of-sector sample: one NaN row in tile 0
-        if ((oos >> threadIdx.x) & 1u) c = tile == 0 ? 1 : 0;
+        if (!((okm >> threadIdx.x) & 1u)) c = tile == 0 ? 1 : 0;
         cnt[(s0 + threadIdx.x) * ntiles + tile] = c;
     }
 }
 
 // Emit pass.  A CTA takes one tile of SWEEP_GT groups and the SWEEP_SB samples of a count
-// batch, whose validity words it reads back.  The tile's terms (z masks and coefficients,
+// batch, with the batch's validity bitmaps.  The tile's terms (z masks and coefficients,
 // contiguous in the grouped table) are copied once into shared memory by a bulk asynchronous
-// copy (cp.async.bulk, completion on an mbarrier) while the pairs are numbered, and then serve
-// every sample of the batch.  The valid
-// (sample, group) pairs are numbered in the deterministic row order (sample-major, group order)
-// and split by group size: groups of more than SWEEP_SMALL terms (the diagonal and the
-// single-excitation groups) are summed by a whole warp, lanes over terms with a TwoSum warp
-// reduction; the others by one thread each, taken in 32-pair chunks from a shared counter so
-// the warps stay busy until the tile's work is gone.
+// copy (cp.async.bulk, completion on an mbarrier) and serve every sample of the batch.  Warp w
+// takes samples w, w + 8, ...; it walks the sample's validity words in group order, so the row
+// of each valid pair (its rank among the sample's valid groups of the tile) follows from a
+// running count and a popcount -- the deterministic row order sample-major, tile-major,
+// group-minor.  Pairs of small groups (at most SWEEP_SMALL terms: the double excitations) go to
+// a per-warp queue and are summed 32 at a time, one lane per pair; the few large groups (the
+// diagonal and the single excitations) are summed by the whole warp at once, lanes over terms
+// with a TwoSum butterfly.
+template <bool COMP>
+__device__ __forceinline__ void sweep_pair_sum(uint64_t x, uint64_t mg, bool has_imag, const uint64_t* zp,
+                                               const float2* cp, uint32_t a0, uint32_t a1, uint32_t step, float& re,
+                                               float& re_e, float& im, float& im_e) {
+    for (uint32_t k = a0; k < a1; k += step) add_term<COMP>(x, mg, has_imag, zp[k], cp[k], re, re_e, im, im_e);
+}
+
 template <bool COMP>
 __global__ void __launch_bounds__(SWEEP_GT)
 sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bits, int64_t B,
@@ -161,12 +173,11 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     float2* cs = reinterpret_cast<float2*>(sweep_smem + 8 * SWEEP_STAGE);     // staged coefficients
     __shared__ uint64_t xs[SWEEP_SB];
     __shared__ int64_t obase[SWEEP_SB];
-    __shared__ int32_t woff[SWEEP_SB * SWEEP_NW + 1];
-    __shared__ int32_t sstart[SWEEP_SB + 1];
-    __shared__ uint32_t plist[SWEEP_SB * SWEEP_GT];    // small pairs from the front, large from the back
-    __shared__ int32_t n_small, n_large, next_small;
+    __shared__ uint32_t vb[SWEEP_NW * SWEEP_SB];       // validity words [warp][sample]
+    __shared__ uint32_t lmask[SWEEP_NW];               // large groups of each group word
+    __shared__ uint32_t queue[SWEEP_NW][64];           // pending small pairs: rank | group << 8 | sample << 16
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint64_t g_mask[SWEEP_GT];                  // the tile's groups: flip mask, meta, term range
+    __shared__ uint64_t g_mask[SWEEP_GT];              // the tile's groups: flip mask, meta, term range
     __shared__ uint32_t g_meta[SWEEP_GT], g_k0[SWEEP_GT], g_k1[SWEEP_GT];
 
     const int tile = blockIdx.y;
@@ -183,110 +194,34 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     const bool staged = t1 - t0 <= (uint32_t)SWEEP_STAGE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    if (threadIdx.x == 0) {
-        n_small = 0; n_large = 0; next_small = 0;
-        if (staged) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            const uint32_t bytes = (t1 - t0) * 8u;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(smem_u32(&bar)), "r"(2u * bytes) : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(zs)), "l"(h.term_z + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(cs)), "l"(h.term_c + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
-        }
+    if (threadIdx.x == 0 && staged) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint32_t bytes = (t1 - t0) * 8u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(smem_u32(&bar)), "r"(2u * bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(zs)), "l"(h.term_z + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(cs)), "l"(h.term_c + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
     }
     const uint32_t k0 = live ? h.grp_off[g] : 0, k1 = live ? h.grp_off[g + 1] : 0;
-    const bool large = k1 - k0 > (uint32_t)SWEEP_SMALL;
     g_mask[threadIdx.x] = live ? h.grp_mask[g] : 0;
     g_meta[threadIdx.x] = live ? h.grp_meta[g] : 0;
-    g_k0[threadIdx.x] = k0;
-    g_k1[threadIdx.x] = k1;
+    g_k0[threadIdx.x] = k0 - t0;                       // term indices relative to the tile's range
+    g_k1[threadIdx.x] = k1 - t0;
+    const unsigned lg = __ballot_sync(0xffffffffu, live && k1 - k0 > (uint32_t)SWEEP_SMALL);
+    if (lane == 0) lmask[warp] = lg;
+    vb[threadIdx.x] = valid[((int64_t)blockIdx.x * ntiles + tile) * SWEEP_GT + threadIdx.x];
     if (threadIdx.x < nb) {
         xs[threadIdx.x] = bits[s0 + threadIdx.x];
         obase[threadIdx.x] = off[(s0 + threadIdx.x) * ntiles + tile];
-    }
-    __syncthreads();
-
-    // validity bits of this thread's group over the batch (the count pass's); an out-of-sector
-    // sample gets its single NaN row here
-    const uint32_t vmask = valid[(int64_t)blockIdx.x * ntiles * SWEEP_GT + g];
-    if (tile == 0 && threadIdx.x < nb && !sample_in_sector(xs[threadIdx.x], n_up, n_dn)) {
-        xprime[obase[threadIdx.x]] = xs[threadIdx.x];
-        S[obase[threadIdx.x]] = make_float4(__int_as_float(0x7fc00000), 0.f, __int_as_float(0x7fc00000), 0.f);
-    }
-    for (int s = 0; s < SWEEP_SB; ++s) {
-        const unsigned bal = __ballot_sync(0xffffffffu, (vmask >> s) & 1u);
-        if (lane == 0) woff[s * SWEEP_NW + warp] = __popc(bal);
-    }
-    __syncthreads();
-    // exclusive scan of the EB*NW warp counts (sample-major, warp-minor) by one warp
-    if (warp == 0) {
-        constexpr int PER = (SWEEP_SB * SWEEP_NW + 31) / 32;
-        int32_t loc[PER];
-        int32_t run = 0;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int idx = lane * PER + i;
-            loc[i] = idx < SWEEP_SB * SWEEP_NW ? woff[idx] : 0;
-            run += loc[i];
-        }
-        int32_t incl = run;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        int32_t excl = incl - run;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int idx = lane * PER + i;
-            if (idx < SWEEP_SB * SWEEP_NW) woff[idx] = excl;
-            excl += loc[i];
-        }
-        if (lane == 31) woff[SWEEP_SB * SWEEP_NW] = incl;
-    }
-    __syncthreads();
-    // number the pairs and file them by group size: entry = p | s << 13 | group << 18
-    const unsigned lt = (1u << lane) - 1u;
-    const unsigned lbal = __ballot_sync(0xffffffffu, large && vmask != 0);
-    const unsigned sbal = __ballot_sync(0xffffffffu, !large && vmask != 0);
-    const int npairs = __popc(vmask);
-    int base_l = 0, base_s = 0;
-    {
-        // per-warp reservation of list slots (one atomic per warp and list)
-        int tot_l = 0, tot_s = 0;
-        const int mine = npairs;
-        int pl = 0, ps = 0;
-        const int ml = (lbal >> lane) & 1u ? mine : 0, ms = (sbal >> lane) & 1u ? mine : 0;
-        pl = ml; ps = ms;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int yl = __shfl_up_sync(0xffffffffu, pl, d);
-            const int ys = __shfl_up_sync(0xffffffffu, ps, d);
-            if (lane >= d) { pl += yl; ps += ys; }
-        }
-        tot_l = __shfl_sync(0xffffffffu, pl, 31);
-        tot_s = __shfl_sync(0xffffffffu, ps, 31);
-        int wl = 0, ws = 0;
-        if (lane == 0) {
-            wl = tot_l ? atomicAdd(&n_large, tot_l) : 0;
-            ws = tot_s ? atomicAdd(&n_small, tot_s) : 0;
-        }
-        base_l = __shfl_sync(0xffffffffu, wl, 0) + pl - ml;
-        base_s = __shfl_sync(0xffffffffu, ws, 0) + ps - ms;
-    }
-    for (int s = 0; s < SWEEP_SB; ++s) {
-        const unsigned bal = __ballot_sync(0xffffffffu, (vmask >> s) & 1u);
-        if ((vmask >> s) & 1u) {
-            const uint32_t p = (uint32_t)(woff[s * SWEEP_NW + warp] + __popc(bal & lt));
-            const uint32_t e = p | ((uint32_t)s << 13) | ((uint32_t)threadIdx.x << 18);
-            if (large) plist[SWEEP_SB * SWEEP_GT - 1 - base_l++] = e;
-            else plist[base_s++] = e;
+        // an out-of-sector sample gets its single NaN row here
+        if (tile == 0 && !sample_in_sector(xs[threadIdx.x], n_up, n_dn)) {
+            xprime[obase[threadIdx.x]] = xs[threadIdx.x];
+            S[obase[threadIdx.x]] = make_float4(__int_as_float(0x7fc00000), 0.f, __int_as_float(0x7fc00000), 0.f);
         }
     }
-    if (threadIdx.x <= SWEEP_SB) sstart[threadIdx.x] = woff[min((int)threadIdx.x, SWEEP_SB) * SWEEP_NW];
     __syncthreads();
     if (staged && !mbar_wait_bounded(&bar, 0)) {
         // the staging copy did not complete in time: report it, wait (bounded) once more so no
@@ -295,75 +230,83 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
         mbar_wait_bounded(&bar, 0);
         return;
     }
-    const int ns = n_small, nl = n_large;
-
-    // large groups: one warp per pair, lanes over terms, TwoSum butterfly
-    for (int i = warp; i < nl; i += SWEEP_NW) {
-        const uint32_t e = plist[SWEEP_SB * SWEEP_GT - 1 - i];
-        const int p = e & 0x1fff, s = (e >> 13) & 0x1f, gl = e >> 18;
-        const uint64_t x = xs[s];
-        const uint64_t mg = g_mask[gl];
-        const bool has_imag = (g_meta[gl] & META_HAS_IMAG) != 0;
-        const uint32_t a0 = g_k0[gl], a1 = g_k1[gl];
-        float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
-        for (uint32_t k = a0 + lane; k < a1; k += 32) {
-            const uint64_t z = staged ? zs[k - t0] : __ldg(h.term_z + k);
-            const float2 c = staged ? cs[k - t0] : __ldg(h.term_c + k);
-            add_term<COMP>(x, mg, has_imag, z, c, re, re_e, im, im_e);
-        }
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) {
-            const float ore = __shfl_xor_sync(0xffffffffu, re, d), oree = __shfl_xor_sync(0xffffffffu, re_e, d);
-            const float oim = __shfl_xor_sync(0xffffffffu, im, d), oime = __shfl_xor_sync(0xffffffffu, im_e, d);
-            if (COMP) {
-                // both lanes form the same pair sum: order the operands by lane
-                const bool low = (lane & d) == 0;
-                float a = low ? re : ore, b = low ? ore : re;
-                float ae = (low ? re_e : oree) + (low ? oree : re_e);
-                two_sum_acc(a, ae, b);
-                re = a; re_e = ae;
-                float c2 = low ? im : oim, d2 = low ? oim : im;
-                float ce = (low ? im_e : oime) + (low ? oime : im_e);
-                two_sum_acc(c2, ce, d2);
-                im = c2; im_e = ce;
-            } else {
-                const bool low = (lane & d) == 0;
-                re = low ? re + ore : ore + re;
-                im = low ? im + oim : oim + im;
-            }
-        }
-        if (lane == 0) {
-            const int64_t row = obase[s] + (p - sstart[s]);
-            xprime[row] = x ^ mg;
-            S[row] = make_float4(re, re_e, im, im_e);
-        }
-    }
-
-    // small groups: one thread per pair, 32-pair chunks per warp from a shared counter
-    for (;;) {
-        int c0 = 0;
-        if (lane == 0) c0 = atomicAdd(&next_small, 32);
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
-        if (c0 >= ns) break;
-        const int i = c0 + lane;
-        if (i < ns) {
-            const uint32_t e = plist[i];
-            const int p = e & 0x1fff, s = (e >> 13) & 0x1f, gl = e >> 18;
-            const uint64_t x = xs[s];
-            const uint64_t mg = g_mask[gl];
-            const bool has_imag = (g_meta[gl] & META_HAS_IMAG) != 0;
-            const uint32_t a0 = g_k0[gl], a1 = g_k1[gl];
+    const uint64_t* zp = staged ? zs : h.term_z + t0;
+    const float2* cp = staged ? cs : h.term_c + t0;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* q = queue[warp];
+    int qn = 0;
+    // the queued pairs of small groups, one per lane
+    auto drain = [&](int count) {
+        if (lane < count) {
+            const uint32_t e = q[lane];
+            const int s = (int)(e >> 16), gl = (int)((e >> 8) & 0xffu);
+            const uint64_t x = xs[s], mg = g_mask[gl];
             float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
-            for (uint32_t k = a0; k < a1; ++k) {
-                const uint64_t z = staged ? zs[k - t0] : __ldg(h.term_z + k);
-                const float2 c = staged ? cs[k - t0] : __ldg(h.term_c + k);
-                add_term<COMP>(x, mg, has_imag, z, c, re, re_e, im, im_e);
-            }
-            const int64_t row = obase[s] + (p - sstart[s]);
+            sweep_pair_sum<COMP>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, zp, cp, g_k0[gl], g_k1[gl], 1u, re, re_e,
+                                 im, im_e);
+            const int64_t row = obase[s] + (int64_t)(e & 0xffu);
             xprime[row] = x ^ mg;
             S[row] = make_float4(re, re_e, im, im_e);
         }
+    };
+    for (int s = warp; s < nb; s += SWEEP_NW) {
+        const uint64_t x = xs[s];
+        int run = 0;
+#pragma unroll 1
+        for (int j = 0; j < SWEEP_NW; ++j) {
+            const uint32_t bal = vb[j * SWEEP_SB + s];
+            if (bal == 0u) continue;
+            const uint32_t lm = lmask[j], sm = bal & ~lm;
+            if ((sm >> lane) & 1u)
+                q[qn + __popc(sm & lt)] = (uint32_t)(run + __popc(bal & lt)) | ((uint32_t)(32 * j + lane) << 8) |
+                                          ((uint32_t)s << 16);
+            qn += __popc(sm);
+            // large groups: the whole warp per pair
+            for (uint32_t big = bal & lm; big; big &= big - 1u) {
+                const int b = __ffs(big) - 1, gl = 32 * j + b;
+                const uint64_t mg = g_mask[gl];
+                float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
+                sweep_pair_sum<COMP>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, zp, cp, g_k0[gl] + lane, g_k1[gl], 32u,
+                                     re, re_e, im, im_e);
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1) {
+                    const float ore = __shfl_xor_sync(0xffffffffu, re, d), oree = __shfl_xor_sync(0xffffffffu, re_e, d);
+                    const float oim = __shfl_xor_sync(0xffffffffu, im, d), oime = __shfl_xor_sync(0xffffffffu, im_e, d);
+                    // both lanes form the same pair sum: order the operands by lane
+                    const bool low = (lane & d) == 0;
+                    if (COMP) {
+                        float a = low ? re : ore, bb = low ? ore : re;
+                        float ae = (low ? re_e : oree) + (low ? oree : re_e);
+                        two_sum_acc(a, ae, bb);
+                        re = a; re_e = ae;
+                        float c2 = low ? im : oim, d2 = low ? oim : im;
+                        float ce = (low ? im_e : oime) + (low ? oime : im_e);
+                        two_sum_acc(c2, ce, d2);
+                        im = c2; im_e = ce;
+                    } else {
+                        re = low ? re + ore : ore + re;
+                        im = low ? im + oim : oim + im;
+                    }
+                }
+                if (lane == 0) {
+                    const int64_t row = obase[s] + run + __popc(bal & ((1u << b) - 1u));
+                    xprime[row] = x ^ mg;
+                    S[row] = make_float4(re, re_e, im, im_e);
+                }
+            }
+            run += __popc(bal);
+            if (qn >= 32) {
+                __syncwarp();
+                drain(32);
+                __syncwarp();
+                if (lane < qn - 32) q[lane] = q[lane + 32];
+                qn -= 32;
+                __syncwarp();
+            }
+        }
     }
+    __syncwarp();
+    drain(qn);
 }
 
 __global__ void unpack_rows_kernel(const int64_t* __restrict__ off, int64_t ntiles, int64_t B,
