@@ -38,17 +38,20 @@ DEFAULT_WORKLOAD = 5
 # same kernel on the same workload shape (the list is emptied for a kernel when it changes).
 NCU_TRAFFIC = {}
 
-# Tensor-core scopes (useful FLOPs recorded per launch; the compensated split issues twice as many
-# products on the tensor pipe) and the kernels behind each scope.
-TENSOR_SCOPES = {
-    "tf_gemm": "tc_gemm_kernel (tcgen05 + TMA + TMEM: QKV projection, attention output + residual)",
-    "tf_mlp": "tc_mlp_kernel / tc_mlp_res_kernel (fused tcgen05 MLP block, hidden layer on chip)",
-    "tf_qkv_attention": "tc_qkv_attn_kernel (fused QKV projection + causal attention, d_model 64)",
-    "tf_resid_ln": "tc_gemm_kernel<RESID_LN> (attention output + residual + LayerNorm 2, d_model 64)",
-}
-HBM_SCOPES = {
-    "tf_layernorm": "layernorm_kernel / ch_embed_ln_kernel (LayerNorm and embedding rows)",
-    "ch_cache": "ch_cache_fill_kernel (key/value caches of the prefix-sharing jobs)",
+# The library's profiled scopes that record their algorithmic FLOPs and compulsory bytes, with
+# the kernels behind each (bf16 form, fp32 form).
+SCOPE_KERNELS = {
+    "tf_gemm": ("tc_gemm_kernel (tcgen05 + TMA + TMEM: QKV and attention-output projections)",
+                "sgemm_kernel (fp32 SIMT)"),
+    "tf_mlp": ("tc_mlp_kernel / tc_mlp_res_kernel (fused tcgen05 MLP block, hidden layer on chip)",
+               "sgemm_kernel (fp32 SIMT, W1 + GELU and W2 + residual)"),
+    "tf_qkv_attention": ("tc_qkv_attn_kernel (fused QKV projection + causal attention, d_model 64)", None),
+    "tf_resid_ln": ("tc_gemm_kernel<RESID_LN> (attention output + residual + LayerNorm 2, d_model 64)", None),
+    "ch_attention": ("ch_attention_mma_kernel (causal attention of the prefix-sharing jobs, mma.sync m16n8k16, "
+                     "compensated bf16 products)",
+                     "ch_attention_kernel (causal attention of the prefix-sharing jobs, fp32 SIMT)"),
+    "tf_layernorm": ("layernorm_kernel / ch_embed_ln_kernel (LayerNorm and embedding rows)",) * 2,
+    "ch_cache": ("ch_cache_fill_kernel (key/value caches of the prefix-sharing jobs)",) * 2,
 }
 
 
@@ -68,9 +71,14 @@ def parse():
                     "the BF16 one for the speedup (0: skip)")
     ap.add_argument("--sweep-samples", type=int, default=1 << 16,
                     help="samples of the term-sweep microbenchmark (0: skip)")
-    ap.add_argument("--mode", default="step", choices=["step", "sweep"],
+    ap.add_argument("--mode", default="step", choices=["step", "sweep", "eloc"],
                     help="step: the VMC-step benchmark (the JSON line); sweep: the term-sweep "
-                         "microbenchmark alone on --sweep-samples samples (its own JSON line)")
+                         "microbenchmark alone on --sweep-samples samples; eloc: the local energy alone on "
+                         "--eloc-samples seeded in-sector samples (each its own JSON line; small cases for "
+                         "profiler captures)")
+    ap.add_argument("--eloc-samples", type=int, default=64, help="samples of the local-energy microbenchmark")
+    ap.add_argument("--pass-bytes", type=int, default=0,
+                    help="activation bytes of one prefix-sharing sub-pass (0: the library default)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -292,37 +300,38 @@ def run_ours(args, rank, world, local):
     peak_b = peaks.get("hbm_gbs", 6400.0)
     for name, k in kern.items():
         sec = k["ms_total"] / 1e3
-        if sec <= 0:
+        if sec <= 0 or name not in SCOPE_KERNELS or (k["flops"] <= 0 and k["bytes"] <= 0):
             continue
         per = k["launches"]
-        tr = NCU_TRAFFIC.get((cfg.name, name))
-        r = None
-        if name in TENSOR_SCOPES and k["flops"] > 0 and prec == "bf16":
-            ach = k["flops"] / sec / 1e12
-            r = {"kernel": TENSOR_SCOPES[name], "bound": "tensor", "achieved": ach, "peak": peak_t,
-                 "unit": "TFLOP/s", "frac": ach / peak_t, "flops_per_launch": k["flops"] / per,
-                 "peak_source": f"{peak_kind} sustained bf16 cuBLAS (MEASURED_PEAKS.json); useful FLOPs, "
-                                "the compensated hi+lo split issues twice as many"}
-        elif name == "tf_gemm" and k["flops"] > 0:
-            ach = k["flops"] / sec / 1e12
-            r = {"kernel": "sgemm_kernel (fp32 SIMT)", "bound": "alu", "achieved": ach, "peak": ffma_peak,
-                 "unit": "TFLOP/s", "frac": ach / ffma_peak, "flops_per_launch": k["flops"] / per,
-                 "peak_source": f"fp32 FFMA: {sms} SMs x {pipes['ffma']:.1f}/clk (probe) x 2 x {clk_mhz:.0f} MHz"}
-        elif name == "ch_attention" and k["flops"] > 0:
-            ach = k["flops"] / sec / 1e12
-            r = {"kernel": "ch_attention_kernel (causal attention of prefix-sharing jobs, fp32 SIMT)", "bound": "alu",
-                 "achieved": ach, "peak": ffma_peak, "unit": "TFLOP/s", "frac": ach / ffma_peak,
-                 "flops_per_launch": k["flops"] / per,
-                 "peak_source": f"fp32 FFMA: {sms} SMs x {pipes['ffma']:.1f}/clk (probe) x 2 x {clk_mhz:.0f} MHz"}
-        elif name in HBM_SCOPES and k["bytes"] > 0:
-            ach = k["bytes"] / sec / 1e9
-            r = {"kernel": HBM_SCOPES[name], "bound": "hbm", "achieved": ach, "peak": peak_b, "unit": "GB/s",
-                 "frac": ach / peak_b, "bytes_per_launch": k["bytes"] / per,
-                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)"}
-        if r is not None:
-            r["ms_per_step"] = k["ms_per_step"]
-            r["traffic"] = tr * (k["bytes"] / per) if (tr and k["bytes"] > 0) else None
-            rooflines[name] = r
+        tr = NCU_TRAFFIC.get((cfg.name, prec, name))
+        # the two ceilings of the scope: its arithmetic (bf16 tensor pipe in the bf16 form, the
+        # FFMA pipe in the fp32 form) and HBM; the binding one is the larger time at peak
+        kernel = SCOPE_KERNELS[name][0 if prec == "bf16" else 1]
+        if prec == "bf16":
+            pk_c, unit_c, bound_c = peak_t, "TFLOP/s", "tensor"
+            src_c = f"{peak_kind} sustained bf16 cuBLAS (MEASURED_PEAKS.json); useful FLOPs (the compensated " \
+                    "hi+lo split issues twice as many products)"
+        else:
+            pk_c, unit_c, bound_c = ffma_peak, "TFLOP/s", "alu"
+            src_c = f"fp32 FFMA: {sms} SMs x {pipes['ffma']:.1f}/clk (probe) x 2 x {clk_mhz:.0f} MHz"
+        t_c = k["flops"] / (pk_c * 1e12)
+        t_m = k["bytes"] / (peak_b * 1e9)
+        ach_c = k["flops"] / sec / 1e12
+        ach_m = k["bytes"] / sec / 1e9
+        if t_c >= t_m:
+            r = {"kernel": kernel, "bound": bound_c, "achieved": ach_c, "peak": pk_c, "unit": unit_c,
+                 "frac": ach_c / pk_c, "peak_source": src_c}
+        else:
+            r = {"kernel": kernel, "bound": "hbm", "achieved": ach_m, "peak": peak_b, "unit": "GB/s",
+                 "frac": ach_m / peak_b, "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+        r["flops_per_launch"] = k["flops"] / per
+        r["bytes_per_launch"] = k["bytes"] / per
+        r["compute_frac"] = ach_c / pk_c if k["flops"] > 0 else None
+        r["hbm_frac"] = ach_m / peak_b if k["bytes"] > 0 else None
+        r["intensity_flop_per_byte"] = k["flops"] / k["bytes"] if k["bytes"] > 0 else None
+        r["ms_per_step"] = k["ms_per_step"]
+        r["traffic"] = tr * (k["bytes"] / per) if (tr and k["bytes"] > 0) else None
+        rooflines[name] = r
     # backward: tensor roofline from the layer shapes (forward recompute + two backward GEMMs per
     # forward GEMM on U x n rows), the backward scope's time
     if cfg.arch == "transformer" and "tf_backward" in kern:
@@ -481,6 +490,50 @@ def run_sweep(args, local):
                       "clocks": clk.summary()}))
 
 
+def run_eloc(args, local):
+    """The local energy alone (nqs_local_energy) on seeded in-sector samples of the workload: one
+    warm-up call, then one profiled call; per-scope CUDA-event times (one JSON line)."""
+    import torch
+    import paper_2208_05637_b300 as P
+    torch.cuda.set_device(local)
+    cfg = synth.get_config(args.workload)
+    n = cfg.n_qubits
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(n, xm, zm, coef)
+    order = synth.default_order(n)
+    named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
+                              cfg.seed_params, beta=args.beta, order=order)
+    prec = args.precision or ("bf16" if cfg.arch == "transformer" else "fp32")
+    model = P.Model(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
+                    precision=prec, compensated=True, order=order)
+    model.bind(model.pack(named))
+    if args.pass_bytes and cfg.arch == "transformer":
+        model.set_pass_bytes(args.pass_bytes)
+    bits = synth.random_sector_bits(cfg.n_orb, cfg.n_up, cfg.n_dn, args.eloc_samples, seed=77)
+    bt = torch.tensor(bits.view(np.int64), device="cuda")
+    P.nqs_local_energy(ham, model, bt)
+    torch.cuda.synchronize()
+    P.profile_reset(); P.profile_enable(True)
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    e = P.nqs_local_energy(ham, model, bt)
+    b.record()
+    torch.cuda.synchronize()
+    P.profile_enable(False)
+    scopes = {}
+    for name in ("term_sweep", "sweep_count", "ch_build", "ch_cache", "ch_attention", "ch_heads", "tf_gemm", "tf_mlp",
+                 "tf_layernorm", "dedup", "dedup_contrib", "tf_qkv_attention", "tf_resid_ln", "eloc_rows"):
+        ms, c = P.profile_read(name)
+        if c:
+            fl, by = P.profile_work(name)
+            scopes[name] = {"ms": ms, "launches": c, "flops": fl, "bytes": by}
+    print(json.dumps({"metric": "local energy (sample.term/s)", "workload": cfg.name, "precision": prec,
+                      "samples": args.eloc_samples, "ms": a.elapsed_time(b),
+                      "value": args.eloc_samples * ham.info()[0] / (a.elapsed_time(b) / 1e3),
+                      "pass_bytes": args.pass_bytes, "finite": bool(torch.isfinite(e).all().item()),
+                      "scopes": scopes}))
+
+
 # ----------------------------------------------------------------------------- oracle timing
 def cpu_baseline(cfg, args, budget_s=15.0):
     """The FP64 oracle as it stands on this host, on a bounded sample of the workload: local
@@ -558,6 +611,8 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "sweep":
         run_sweep(args, local)
+    elif args.mode == "eloc":
+        run_eloc(args, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and args.impl == "ours":

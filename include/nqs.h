@@ -132,6 +132,14 @@ int nqs_model_bind_params(nqs_model_t model, const float* params_device);
  * (NQS_ERR_UNSUPPORTED otherwise); NQS_ERR_INVALID_ARG outside -1..3. */
 int nqs_model_set_prefix_reuse(nqs_model_t model, int depth);
 
+/* Activation bytes of one sub-pass of the prefix-sharing local energy (the leaves are evaluated
+ * in sub-passes of about this many bytes of layer activations, about 40 d_model bytes a row).
+ * 0 (default): 16 GiB.  Smaller values bound the workspace (query nqs_workspace_size after
+ * setting it) at the cost of more, smaller launches; the local energies do not depend on it.
+ * Transformer models only (NQS_ERR_UNSUPPORTED otherwise); NQS_ERR_INVALID_ARG if negative.
+ * Not part of the paper's method: a memory/throughput setting of this implementation. */
+int nqs_model_set_pass_bytes(nqs_model_t model, int64_t bytes);
+
 void nqs_model_destroy(nqs_model_t model);
 
 /* Workspace bytes that `op` (NQS_OP_*) needs for `batch` rows: samples for LOGPSI,

@@ -36,7 +36,7 @@ EXPORTED = [
     "nqs_model_bind_params", "nqs_model_destroy", "nqs_workspace_size", "nqs_sample",
     "nqs_logpsi", "nqs_term_sweep", "nqs_local_energy", "nqs_logpsi_backward", "nqs_logpsi_backward_phase",
     "nqs_energy_stats", "nqs_adam_step", "nqs_strerror", "nqs_last_error", "nqs_profile_enable",
-    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16", "nqs_profile_work", "nqs_probe_pipes", "nqs_model_set_prefix_reuse",
+    "nqs_profile_reset", "nqs_profile_read", "nqs_launch_count", "nqs_local_energy_noalloc", "nqs_gemm_bf16", "nqs_profile_work", "nqs_probe_pipes", "nqs_model_set_prefix_reuse", "nqs_model_set_pass_bytes",
     "nqs_energy_sums",
 ]
 
@@ -85,6 +85,7 @@ _sig = {
     "nqs_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "nqs_probe_pipes": [_P],
     "nqs_model_set_prefix_reuse": [_P, ctypes.c_int],
+    "nqs_model_set_pass_bytes": [_P, ctypes.c_int64],
     "nqs_energy_sums": [_P, _P, _I64, _P, _P, _P, _P, _P],
 }
 for _name, _args in _sig.items():
@@ -251,6 +252,10 @@ class Model:
     def set_prefix_reuse(self, depth: int):
         """Prefix reuse depth of the transformer local energy (-1 automatic, 0..3; include/nqs.h)."""
         _check(_lib.nqs_model_set_prefix_reuse(self.handle, int(depth)), "nqs_model_set_prefix_reuse")
+
+    def set_pass_bytes(self, nbytes: int):
+        """Activation bytes of one prefix-sharing sub-pass (0: the default, 16 GiB)."""
+        _check(_lib.nqs_model_set_pass_bytes(self.handle, int(nbytes)), "nqs_model_set_pass_bytes")
 
     def workspace(self, op, batch, ham=None):
         import torch

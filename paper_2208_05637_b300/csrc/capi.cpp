@@ -174,7 +174,7 @@ static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int
     if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
         e.contrib = c.take<float2>(e.rows_cap);
         if (e.chain_depth >= 0) {
-            chain_layout(c, m->mc, e.chain_depth, e.chunk, e.rows_cap, e.ch);
+            chain_layout(c, m->mc, e.chain_depth, e.chunk, e.rows_cap, m->pass_bytes, e.ch);
             return;
         }
         tf_layout(c, m->mc, std::min(std::max<int64_t>(B, e.rows_cap), tf_seq_capacity(m->mc)), e.tf);
@@ -334,7 +334,7 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     // the term arrays carry one zero padding term (the sweep stages even-aligned ranges)
     Carver c(nullptr);
     c.take<uint64_t>(h->G); c.take<uint32_t>(h->G + 1); c.take<uint32_t>(h->G);
-    c.take<uint64_t>(h->K + 1); c.take<float2>(h->K + 1);
+    c.take<uint4>(h->K + 1);
     cudaGetDevice(&h->device);
     if (cudaMalloc(&h->d_block, c.used) != cudaSuccess) {
         cudaGetLastError();
@@ -346,29 +346,30 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     auto* d_mask = d.take<uint64_t>(h->G);
     auto* d_off = d.take<uint32_t>(h->G + 1);
     auto* d_meta = d.take<uint32_t>(h->G);
-    auto* d_z = d.take<uint64_t>(h->K + 1);
-    auto* d_c = d.take<float2>(h->K + 1);
+    auto* d_t = d.take<uint4>(h->K + 1);
     std::vector<uint32_t> off32(h->grp_off.begin(), h->grp_off.end());
-    std::vector<float2> cc(h->K + 1, make_float2(0.f, 0.f));
-    std::vector<uint64_t> zz(h->term_z);
-    zz.push_back(0);
+    std::vector<uint4> tt(h->K + 1, make_uint4(0u, 0u, 0u, 0u));
     for (int64_t k = 0; k < h->K; ++k) {
-        float hi = (float)c_signed[k];
-        float lo = (float)(c_signed[k] - (double)hi);
-        cc[k] = make_float2(hi, lo);
+        const float hi = (float)c_signed[k];
+        const float lo = (float)(c_signed[k] - (double)hi);
+        uint32_t hb, lb;
+        std::memcpy(&hb, &hi, 4);
+        std::memcpy(&lb, &lo, 4);
+        tt[k] = make_uint4((uint32_t)h->term_z[k], (uint32_t)(h->term_z[k] >> 32), hb, lb);
     }
+    int any_imag = 0;
+    for (uint32_t mt : h->grp_meta) any_imag |= (mt & META_HAS_IMAG) ? 1 : 0;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpy(d_mask, h->grp_mask.data(), h->G * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_off, off32.data(), (h->G + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_meta, h->grp_meta.data(), h->G * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_z, zz.data(), (h->K + 1) * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_c, cc.data(), (h->K + 1) * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_t, tt.data(), (h->K + 1) * 16, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(h->d_block);
         delete h;
         return cuda_fail(e, "copy of the Hamiltonian tables", __FILE__, __LINE__);
     }
-    h->dev = HamDev{h->n, h->K, h->G, d_mask, d_off, d_meta, d_z, d_c};
+    h->dev = HamDev{h->n, h->K, h->G, d_mask, d_off, d_meta, d_t, any_imag};
     *out = h;
     return NQS_OK;
 }
@@ -558,6 +559,13 @@ int nqs_model_set_prefix_reuse(nqs_model_t m, int depth) {
         return NQS_ERR_UNSUPPORTED;
     }
     m->prefix_depth = depth;
+    return NQS_OK;
+}
+
+int nqs_model_set_pass_bytes(nqs_model_t m, int64_t bytes) {
+    if (!m || bytes < 0) { set_error("need a model and bytes >= 0"); return NQS_ERR_INVALID_ARG; }
+    if (m->mc.arch != NQS_ARCH_TRANSFORMER) { set_error("sub-pass size applies to the transformer"); return NQS_ERR_UNSUPPORTED; }
+    m->pass_bytes = bytes;
     return NQS_OK;
 }
 

@@ -1096,21 +1096,23 @@ int64_t chain_chunk(const ModelConst& mc, int depth) {
     return std::max<int64_t>(1, std::min<int64_t>(CHAIN_MAX_CHUNK, CHAIN_CACHE_BYTES / per));
 }
 
-// Rows of one pass: all of pass A, and pass-B sub-passes of about CHAIN_PASS_BYTES of
-// activations (about 40 d bytes a row), never more than the chunk's leaves can need.
-int64_t chain_pass_rows(const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap) {
+// Rows of one pass: all of pass A, and pass-B sub-passes of about pass_bytes of activations
+// (about 40 d bytes a row; 0: CHAIN_PASS_BYTES), never more than the chunk's leaves can need.
+int64_t chain_pass_rows(const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, int64_t pass_bytes) {
     const int64_t rows_a = chunk * chain_rows_per_sample(mc, depth);
-    const int64_t rows_b = std::min<int64_t>(std::max<int64_t>(CHAIN_PASS_BYTES / ((int64_t)mc.hidden * 40), 4 * (int64_t)mc.n),
+    const int64_t pb = pass_bytes > 0 ? pass_bytes : CHAIN_PASS_BYTES;
+    const int64_t rows_b = std::min<int64_t>(std::max<int64_t>(pb / ((int64_t)mc.hidden * 40), 4 * (int64_t)mc.n),
                                              rows_cap * mc.n + mc.n);
     return std::max(rows_a, rows_b);
 }
 
-void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, ChainBufs& b) {
+void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, int64_t pass_bytes,
+                  ChainBufs& b) {
     const int64_t n = mc.n;
     b.chunk = chunk;
     b.rows_cap = rows_cap;
     b.jobs_cap = chunk * chain_jobs_per_sample(mc, depth);
-    b.pass_rows = chain_pass_rows(mc, depth, chunk, rows_cap);
+    b.pass_rows = chain_pass_rows(mc, depth, chunk, rows_cap, pass_bytes);
     b.l1 = c.take<unsigned long long>(chunk);
     b.l2 = c.take<unsigned long long>(chunk * 64);
     b.cnt1 = c.take<int64_t>(chunk);

@@ -65,8 +65,10 @@ struct HamDev {
     const uint64_t* grp_mask;
     const uint32_t* grp_off;   // G+1
     const uint32_t* grp_meta;  // G
-    const uint64_t* term_z;    // K
-    const float2* term_c;      // K: (hi, lo) of the signed real magnitude
+    // K + 1 records (the last a zero term): {z low word, z high word, bits of the fp32 hi and lo
+    // of the signed real magnitude of c'} -- one 16-byte load per term
+    const uint4* term;
+    int any_imag;              // some group holds a term with an odd sigma_2 count
 };
 
 }  // namespace nqs
@@ -167,6 +169,7 @@ struct nqs_model_s {
     void* d_scache = nullptr;        // sampler cache of the incremental transformer forward
     size_t scache_bytes = 0;
     int prefix_depth = -1;           // transformer local energy: -1 automatic, 0..3 prefix sharing
+    int64_t pass_bytes = 0;          // activations of one prefix-sharing sub-pass (0: CHAIN_PASS_BYTES)
 };
 
 namespace nqs {
@@ -377,7 +380,7 @@ int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, 
 // sweep's rows); see chains.cu.
 constexpr int64_t CHAIN_MAX_CHUNK = 64;                     // samples per chunk
 constexpr int64_t CHAIN_CACHE_BYTES = 24ll << 30;           // key/value caches of one chunk
-constexpr int64_t CHAIN_PASS_BYTES = 16ll << 30;            // activations of one pass-B sub-pass
+constexpr int64_t CHAIN_PASS_BYTES = 16ll << 30;            // activations of one pass-B sub-pass (default)
 constexpr int CHAIN_MAX_SPLIT = 4096;                       // pass-B sub-passes of one chunk
 struct ChainBufs {
     int64_t chunk = 0, rows_cap = 0, jobs_cap = 0, pass_rows = 0;
@@ -410,8 +413,9 @@ struct ChainBufs {
 bool chain_supported(const ModelConst& mc);   // head shape and staging fit the prefix-sharing kernels
 int64_t chain_jobs_per_sample(const ModelConst& mc, int depth);
 int64_t chain_chunk(const ModelConst& mc, int depth);
-int64_t chain_pass_rows(const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap);
-void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, ChainBufs& b);
+int64_t chain_pass_rows(const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, int64_t pass_bytes);
+void chain_layout(Carver& c, const ModelConst& mc, int depth, int64_t chunk, int64_t rows_cap, int64_t pass_bytes,
+                  ChainBufs& b);
 // Ratio-weighted contributions of the chunk's sweep rows (contrib) and the samples' log psi
 // (la_x, ph_x) by prefix sharing at the given depth (0..3).
 int chain_local_energy(const ModelConst& mc, const float* P, const TfWeights& w, ChainBufs& b, int depth,

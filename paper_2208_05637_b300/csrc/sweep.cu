@@ -39,11 +39,11 @@ __device__ __forceinline__ bool sample_in_sector(uint64_t x, int n_up, int n_dn)
     return __popc(up_bits(x)) == n_up && __popc(dn_bits(x)) == n_dn;
 }
 
-// Parity of popcount(x & z) in bit 31 (the float sign bit): the two halves are XOR-folded first,
-// which keeps the parity, so one 32-bit POPC serves a 64-bit mask.
-__device__ __forceinline__ uint32_t sign_flip(uint64_t x, uint64_t z) {
-    const uint64_t v = x & z;
-    return (uint32_t)__popc((uint32_t)v ^ (uint32_t)(v >> 32)) << 31;
+// Parity of popcount(x & z) in bit 31 (the float sign bit), z given as its two 32-bit words: the
+// halves of x & z are XOR-folded first, which keeps the parity, so one 32-bit POPC serves a
+// 64-bit mask.
+__device__ __forceinline__ uint32_t sign_flip(uint32_t xl, uint32_t xh, uint32_t zl, uint32_t zh) {
+    return (uint32_t)__popc((xl & zl) ^ (xh & zh)) << 31;
 }
 
 // Knuth's TwoSum: s + e == a + b exactly, accumulated into the error term.
@@ -55,13 +55,15 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
 }
 
 // One term of S_g(x): c' (-1)^{popc(x & z)} into the real or (odd sigma_2 count) imaginary sum.
-template <bool COMP>
-__device__ __forceinline__ void add_term(uint64_t x, uint64_t mg, bool has_imag, uint64_t z, float2 c,
+// The term is its 16-byte record {z low, z high, c' hi bits, c' lo bits}.  IMAG: the Hamiltonian
+// has odd-sigma_2 terms somewhere (else the imaginary branch is compiled out).
+template <bool COMP, bool IMAG>
+__device__ __forceinline__ void add_term(uint32_t xl, uint32_t xh, uint64_t mg, bool has_imag, uint4 t,
                                          float& re, float& re_e, float& im, float& im_e) {
-    const uint32_t flip = sign_flip(x, z);
-    const float hi = __uint_as_float(__float_as_uint(c.x) ^ flip);
-    const float lo = __uint_as_float(__float_as_uint(c.y) ^ flip);
-    const bool imag = has_imag && (__popcll(mg & z) & 1);
+    const uint32_t flip = sign_flip(xl, xh, t.x, t.y);
+    const float hi = __uint_as_float(t.z ^ flip);
+    const float lo = __uint_as_float(t.w ^ flip);
+    const bool imag = IMAG && has_imag && (__popc(((uint32_t)mg & t.x) ^ ((uint32_t)(mg >> 32) & t.y)) & 1);
     if (COMP) {
         if (imag) { two_sum_acc(im, im_e, hi); im_e += lo; }
         else      { two_sum_acc(re, re_e, hi); re_e += lo; }
@@ -156,21 +158,21 @@ sweep_count_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bi
 // a per-warp queue and are summed 32 at a time, one lane per pair; the few large groups (the
 // diagonal and the single excitations) are summed by the whole warp at once, lanes over terms
 // with a TwoSum butterfly.
-template <bool COMP>
-__device__ __forceinline__ void sweep_pair_sum(uint64_t x, uint64_t mg, bool has_imag, const uint64_t* zp,
-                                               const float2* cp, uint32_t a0, uint32_t a1, uint32_t step, float& re,
+template <bool COMP, bool IMAG>
+__device__ __forceinline__ void sweep_pair_sum(uint64_t x, uint64_t mg, bool has_imag, const uint4* tp,
+                                               uint32_t a0, uint32_t a1, uint32_t step, float& re,
                                                float& re_e, float& im, float& im_e) {
-    for (uint32_t k = a0; k < a1; k += step) add_term<COMP>(x, mg, has_imag, zp[k], cp[k], re, re_e, im, im_e);
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    for (uint32_t k = a0; k < a1; k += step) add_term<COMP, IMAG>(xl, xh, mg, has_imag, tp[k], re, re_e, im, im_e);
 }
 
-template <bool COMP>
+template <bool COMP, bool IMAG>
 __global__ void __launch_bounds__(SWEEP_GT)
 sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bits, int64_t B,
                   const int64_t* __restrict__ off, int64_t ntiles, const uint32_t* __restrict__ valid,
                   uint64_t* __restrict__ xprime, float4* __restrict__ S, int* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char sweep_smem[];
-    uint64_t* zs = reinterpret_cast<uint64_t*>(sweep_smem);                   // staged z masks
-    float2* cs = reinterpret_cast<float2*>(sweep_smem + 8 * SWEEP_STAGE);     // staged coefficients
+    uint4* ts = reinterpret_cast<uint4*>(sweep_smem);                         // staged term records
     __shared__ uint64_t xs[SWEEP_SB];
     __shared__ int64_t obase[SWEEP_SB];
     __shared__ uint32_t vb[SWEEP_NW * SWEEP_SB];       // validity words [warp][sample]
@@ -187,23 +189,21 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     const int64_t g = g0 + threadIdx.x;
     const bool live = g < h.G;
     const int64_t g_end = g0 + SWEEP_GT < h.G ? g0 + SWEEP_GT : h.G;
-    // the tile's term range, widened to even indices (16-byte boundaries of both arrays; the
-    // tables carry one padding term)
-    const uint32_t t0 = h.grp_off[g0] & ~1u;
-    const uint32_t t1 = (h.grp_off[g_end] + 1u) & ~1u;
+    // the tile's term range (16-byte records: every range is a valid bulk copy)
+    const uint32_t t0 = h.grp_off[g0];
+    const uint32_t t1 = h.grp_off[g_end];
     const bool staged = t1 - t0 <= (uint32_t)SWEEP_STAGE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0 && staged) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const uint32_t bytes = (t1 - t0) * 8u;
+        const uint32_t bytes = (t1 - t0) * 16u;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     ::"r"(smem_u32(&bar)), "r"(2u * bytes) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(zs)), "l"(h.term_z + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(cs)), "l"(h.term_c + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
+                     ::"r"(smem_u32(&bar)), "r"(bytes) : "memory");
+        if (bytes)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(ts)), "l"(h.term + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
     }
     const uint32_t k0 = live ? h.grp_off[g] : 0, k1 = live ? h.grp_off[g + 1] : 0;
     g_mask[threadIdx.x] = live ? h.grp_mask[g] : 0;
@@ -230,8 +230,7 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
         mbar_wait_bounded(&bar, 0);
         return;
     }
-    const uint64_t* zp = staged ? zs : h.term_z + t0;
-    const float2* cp = staged ? cs : h.term_c + t0;
+    const uint4* tp = staged ? ts : h.term + t0;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* q = queue[warp];
     int qn = 0;
@@ -242,8 +241,8 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
             const int s = (int)(e >> 16), gl = (int)((e >> 8) & 0xffu);
             const uint64_t x = xs[s], mg = g_mask[gl];
             float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
-            sweep_pair_sum<COMP>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, zp, cp, g_k0[gl], g_k1[gl], 1u, re, re_e,
-                                 im, im_e);
+            sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl], g_k1[gl], 1u, re,
+                                       re_e, im, im_e);
             const int64_t row = obase[s] + (int64_t)(e & 0xffu);
             xprime[row] = x ^ mg;
             S[row] = make_float4(re, re_e, im, im_e);
@@ -266,8 +265,8 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
                 const int b = __ffs(big) - 1, gl = 32 * j + b;
                 const uint64_t mg = g_mask[gl];
                 float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
-                sweep_pair_sum<COMP>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, zp, cp, g_k0[gl] + lane, g_k1[gl], 32u,
-                                     re, re_e, im, im_e);
+                sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl] + lane, g_k1[gl],
+                                           32u, re, re_e, im, im_e);
 #pragma unroll
                 for (int d = 16; d >= 1; d >>= 1) {
                     const float ore = __shfl_xor_sync(0xffffffffu, re, d), oree = __shfl_xor_sync(0xffffffffu, re_e, d);
@@ -352,18 +351,24 @@ int launch_sweep_emit(const HamDev& h, int n_up, int n_dn, int compensated,
     const int64_t T = sweep_tiles(h);
     dim3 grid((unsigned)((B + SWEEP_SB - 1) / SWEEP_SB), (unsigned)T);
     constexpr size_t smem = (size_t)SWEEP_STAGE * 16;
-    static bool attr_set = false;
-    if (!attr_set) {
-        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+    static int attr_dev = -1;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_dev = dev;
     }
     int* status = nullptr;
     NQS_TRY(device_status_ptr(&status));
-    if (compensated)
-        sweep_emit_kernel<true><<<grid, SWEEP_GT, smem, s>>>(h, n_up, n_dn, bits, B, off, T, valid, xprime, S, status);
-    else
-        sweep_emit_kernel<false><<<grid, SWEEP_GT, smem, s>>>(h, n_up, n_dn, bits, B, off, T, valid, xprime, S, status);
+    auto go = [&](auto kernel) { kernel<<<grid, SWEEP_GT, smem, s>>>(h, n_up, n_dn, bits, B, off, T, valid, xprime, S, status); };
+    if (h.any_imag) {
+        if (compensated) go(sweep_emit_kernel<true, true>); else go(sweep_emit_kernel<false, true>);
+    } else {
+        if (compensated) go(sweep_emit_kernel<true, false>); else go(sweep_emit_kernel<false, false>);
+    }
     NQS_LAUNCHED();
     return NQS_OK;
 }

@@ -1,9 +1,10 @@
 """VMC training to convergence (paper Section 5.1 set-up: Adam, lr 1e-3, betas (0.9, 0.99)) on the
-12-qubit workload, checked against the ground energy of its particle-number sector: the exact
-variational energy of the trained wavefunction (all 225 sector states through nqs_logpsi, the
-sector Hamiltonian from the oracle) lies above the ground energy (Rayleigh-Ritz) and within
-20 mHa of it after 4000 iterations in the forward sampling order, and the sampled mean energy of
-the last iterations agrees with that exact energy."""
+12-qubit workload, checked against the ground energy of its particle-number sector, in the three
+sampling orders of the paper's order ablation (Section 4 and Table 2: forward, reverse -- the
+paper's default -- and a seeded random permutation): the exact variational energy of the trained
+wavefunction (all 225 sector states through nqs_logpsi, the sector Hamiltonian from the oracle)
+lies above the ground energy (Rayleigh-Ritz) and within a few mHa to tens of mHa of it after 4000
+iterations, and the sampled mean energy of the last iterations agrees with that exact energy."""
 import numpy as np
 import pytest
 
@@ -14,12 +15,17 @@ from tests.gpu_common import lib, to_dev_bits
 pytestmark = pytest.mark.gpu
 
 
-def test_training_reaches_the_ground_energy_of_the_12_qubit_workload():
+# gap to the sector ground energy allowed after 4000 iterations, per sampling order
+GAP = {"forward": 0.02, "reverse": 0.05, "random": 0.05}
+
+
+@pytest.mark.parametrize("kind", ["forward", "reverse", "random"])
+def test_training_reaches_the_ground_energy_of_the_12_qubit_workload(kind):
     P = lib()
     from paper_2208_05637_b300.train import orders
     cfg = synth.get_config(2)
     n = cfg.n_qubits
-    order = orders(n, "forward")
+    order = orders(n, kind)
     xm, zm, coef = synth.hamiltonian_for(cfg)
     st = sector_states(cfg.n_orb, cfg.n_up, cfg.n_dn)
     H = sector_hamiltonian(xm, zm, coef, n, st).toarray()
@@ -37,7 +43,8 @@ def test_training_reaches_the_ground_energy_of_the_12_qubit_workload():
     la, ph = P.nqs_logpsi(model, to_dev_bits(st))
     psi = np.exp(la.cpu().numpy().astype(np.float64) + 1j * ph.cpu().numpy().astype(np.float64))
     e_var = float(np.real(np.vdot(psi, H @ psi)) / np.real(np.vdot(psi, psi)))
-    print(f"E0 {e0:.6f}  E_var {e_var:.6f}  sampled {np.mean(tail):.6f} +- {np.std(tail):.1e}")
+    print(f"order {kind}: E0 {e0:.6f}  E_var {e_var:.6f}  gap {e_var - e0:.2e}  sampled {np.mean(tail):.6f} "
+          f"+- {np.std(tail):.1e}")
     assert e_var >= e0 - 1e-9 * abs(e0)
-    assert e_var - e0 <= 0.02
+    assert e_var - e0 <= GAP[kind]
     assert abs(np.mean(tail) - e_var) <= 0.01
