@@ -433,32 +433,59 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line))
 
 
+def hamiltonian_of(cfg):
+    """The workload's Pauli strings: one-word masks up to 64 qubits, two-word masks beyond."""
+    return synth.hamiltonian_for(cfg) if cfg.n_qubits <= 64 else synth.hamiltonian_words_for(cfg)
+
+
+def sector_bits_of(cfg, count, seed):
+    """Seeded in-sector configurations of the workload ([count] or [count, 2] uint64)."""
+    if cfg.n_qubits <= 64:
+        return synth.random_sector_bits(cfg.n_orb, cfg.n_up, cfg.n_dn, count, seed=seed)
+    return synth.random_sector_bits_words(cfg.n_orb, cfg.n_up, cfg.n_dn, count, seed=seed, words=2)
+
+
 def sweep_microbench(P, torch, cfg, ham, B, popc_peak, pipes, sms, clk_mhz):
     """The grouped term sweep alone on B seeded in-sector samples (1024 per nqs_term_sweep call),
     count and emit kernels timed with CUDA events; performed (sample, term) pairs counted from the
-    emitted rows.  POPC work: 2 per (sample, group) for the sector test (one per spin species,
-    both 32-bit halves folded into one word) and 1 per performed (sample, term) for the parity."""
+    emitted rows.  POPC work per (sample, group): one per spin species and word (the two 32-bit
+    halves of a word folded into one 32-bit word), so 2 for one-word and 4 for two-word registers;
+    per performed (sample, term): 1 for the parity (all halves XOR-folded into one word)."""
+    W = ham.words
     ex = ham.export()
-    gmask = torch.tensor(ex["group_mask"].view(np.int64), device="cuda")
     gsz = torch.tensor(np.diff(ex["group_offset"]), device="cuda")
+    gm = torch.tensor(np.ascontiguousarray(ex["group_mask"]).view(np.int64), device="cuda")
+    if W > 1:
+        gm = gm.reshape(-1, W)
     K, G = ham.info()
     chunk = 1024
-    bits_all = synth.random_sector_bits(cfg.n_orb, cfg.n_up, cfg.n_dn, B, seed=4242)
+    bits_all = sector_bits_of(cfg, B, 4242)
+
+    def dev(b):
+        t = torch.tensor(np.ascontiguousarray(b).view(np.int64), device="cuda")
+        return t if W == 1 else t.reshape(-1, W)
     # one warm-up call
-    P.nqs_term_sweep(ham, cfg.n_up, cfg.n_dn, torch.tensor(bits_all[:chunk].view(np.int64), device="cuda"))
+    P.nqs_term_sweep(ham, cfg.n_up, cfg.n_dn, dev(bits_all[:chunk]))
     t_ms, terms, rows = 0.0, 0, 0
     for lo in range(0, B, chunk):
-        bt = torch.tensor(bits_all[lo: lo + chunk].view(np.int64), device="cuda")
+        bt = dev(bits_all[lo: lo + chunk])
         P.profile_reset(); P.profile_enable(True)
         ro, xp, _, _ = P.nqs_term_sweep(ham, cfg.n_up, cfg.n_dn, bt)
         P.profile_enable(False)
         t_ms += P.profile_read("sweep_count")[0] + P.profile_read("term_sweep")[0]
         cnt = ro[1:] - ro[:-1]
-        m = torch.repeat_interleave(bt, cnt) ^ xp
-        terms += int(gsz[torch.searchsorted(gmask, m)].sum())
-        rows += xp.numel()
+        m = torch.repeat_interleave(bt, cnt, dim=0) ^ xp
+        if W == 1:
+            terms += int(gsz[torch.searchsorted(gm, m)].sum())
+        else:
+            # group of each row's flip mask: unique over group masks and row masks together
+            _, inv = torch.unique(torch.cat([gm, m]), dim=0, return_inverse=True)
+            size_of_key = torch.zeros(int(inv.max()) + 1, dtype=gsz.dtype, device="cuda")
+            size_of_key[inv[:G]] = gsz
+            terms += int(size_of_key[inv[G:]].sum())
+        rows += xp.shape[0]
     sec = t_ms / 1e3
-    popc_ops = 2.0 * B * G + terms
+    popc_ops = 2.0 * W * B * G + terms
     ach = popc_ops / sec / 1e9
     return {"samples": B, "chunk": chunk, "ms": t_ms,
             "nominal_pairs_per_s": B * K / sec, "performed_terms_per_s": terms / sec,
@@ -466,7 +493,7 @@ def sweep_microbench(P, torch, cfg, ham, B, popc_peak, pipes, sms, clk_mhz):
             "roofline": {"bound": "alu", "kernel": "sweep_count_kernel + sweep_emit_kernel", "achieved": ach,
                          "peak": popc_peak, "unit": "Gpopc/s", "frac": ach / popc_peak,
                          "peak_source": f"POPC: {sms} SMs x {pipes['popc']:.1f}/clk (probe) x {clk_mhz:.0f} MHz",
-                         "work": "2 POPC per (sample, group) + 1 per performed (sample, term)"}}
+                         "work": f"{2 * W} POPC per (sample, group) + 1 per performed (sample, term)"}}
 
 
 def run_sweep(args, local):
@@ -475,7 +502,7 @@ def run_sweep(args, local):
     import paper_2208_05637_b300 as P
     torch.cuda.set_device(local)
     cfg = synth.get_config(args.workload)
-    xm, zm, coef = synth.hamiltonian_for(cfg)
+    xm, zm, coef = hamiltonian_of(cfg)
     ham = P.Hamiltonian(cfg.n_qubits, xm, zm, coef)
     peaks, _ = load_peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2032.0)
@@ -498,7 +525,7 @@ def run_eloc(args, local):
     torch.cuda.set_device(local)
     cfg = synth.get_config(args.workload)
     n = cfg.n_qubits
-    xm, zm, coef = synth.hamiltonian_for(cfg)
+    xm, zm, coef = hamiltonian_of(cfg)
     ham = P.Hamiltonian(n, xm, zm, coef)
     order = synth.default_order(n)
     named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
@@ -509,8 +536,10 @@ def run_eloc(args, local):
     model.bind(model.pack(named))
     if args.pass_bytes and cfg.arch == "transformer":
         model.set_pass_bytes(args.pass_bytes)
-    bits = synth.random_sector_bits(cfg.n_orb, cfg.n_up, cfg.n_dn, args.eloc_samples, seed=77)
-    bt = torch.tensor(bits.view(np.int64), device="cuda")
+    bits = sector_bits_of(cfg, args.eloc_samples, 77)
+    bt = torch.tensor(np.ascontiguousarray(bits).view(np.int64), device="cuda")
+    if bits.ndim == 2:
+        bt = bt.reshape(-1, bits.shape[1])
     P.nqs_local_energy(ham, model, bt)
     torch.cuda.synchronize()
     P.profile_reset(); P.profile_enable(True)

@@ -4,8 +4,14 @@
  * "Scalable neural quantum states architecture for quantum chemistry", arXiv 2208.05637).
  *
  * Conventions shared by every call
- *  - Qubit j is bit j of a uint64 bitstring; 1 <= n_qubits <= 64.  Spin orbital j = 2p + s:
- *    even bits are spin up (alpha), odd bits spin down (beta) (Eq. hamming_weight_constraint).
+ *  - A configuration (bitstring) or Pauli mask of n_qubits <= 64 is one uint64, qubit j in bit j;
+ *    of 64 < n_qubits <= 128 it is W = 2 consecutive uint64 words, qubit j in bit j % 64 of word
+ *    j / 64 (the paper reaches 76 qubits, Table 1).  Arrays of B configurations hold B * W words.
+ *    Two-word registers are served by nqs_ham_*, nqs_term_sweep, nqs_logpsi and
+ *    nqs_local_energy with the PRODUCT and MADE models; the transformer, nqs_sample,
+ *    nqs_logpsi_backward and nqs_local_energy_noalloc take n_qubits <= 64 (NQS_ERR_NQUBITS
+ *    otherwise).  Spin orbital j = 2p + s: even qubits are spin up (alpha), odd qubits spin down
+ *    (beta) (Eq. hamming_weight_constraint).
  *  - A Pauli string is a pair of masks (x_mask, z_mask): qubit j carries I for (0,0), sigma_1
  *    for (1,0), sigma_3 for (0,1) and sigma_2 for (1,1) (Section 3, Eq. hamiltonpauli).
  *  - Pointers documented as "device" must point to memory of the current CUDA device; "host"
@@ -52,7 +58,8 @@ enum nqs_op { NQS_OP_SAMPLE = 0, NQS_OP_LOGPSI = 1, NQS_OP_LOCAL_ENERGY = 2, NQS
  *               `layers` hidden layers of width `hidden` plus the two-layer phase MLP of
  *               Section 4), TRANSFORMER (decoder-only, d_model = hidden, `layers` blocks,
  *               `heads` heads; not in the paper).
- *  n_qubits     even, 4..64.  n_up / n_dn: electrons per spin, the sector of Eq.
+ *  n_qubits     even, 4..128 (PRODUCT, MADE) or 4..64 (TRANSFORMER).  n_up / n_dn: electrons
+ *               per spin, the sector of Eq.
  *               hamming_weight_constraint.
  *  precision    NQS_PREC_FP32 or NQS_PREC_BF16 (bf16 tensor-core contractions, fp32
  *               accumulation; transformer only).
@@ -70,7 +77,7 @@ typedef struct nqs_model_desc {
     int heads;
     int precision;
     int compensated;
-    int order[64];
+    int order[128];
 } nqs_model_desc;
 
 /* ---------------------------------------------------------------- Hamiltonian */
@@ -80,8 +87,9 @@ typedef struct nqs_model_desc {
  * fp64 summation in input order, exact zeros dropped, strings grouped by x_mask (the flip
  * pattern m), and the phase (-i)^r of Eq. mtx_element (r = popcount(x & z)) folded into each
  * coefficient.  The grouped table is copied to the current device.
- *   n_qubits 1..64; n_terms >= 1; x_mask, z_mask, coeff: host arrays of n_terms (copied;
- *   the caller keeps ownership).  Errors: NQS_ERR_NQUBITS, NQS_ERR_INVALID_ARG (null pointer,
+ *   n_qubits 1..128; n_terms >= 1; x_mask, z_mask: host arrays of n_terms masks of W words
+ *   each (W = 1 for n_qubits <= 64, else 2), coeff: host array of n_terms (all copied; the
+ *   caller keeps ownership).  Errors: NQS_ERR_NQUBITS, NQS_ERR_INVALID_ARG (null pointer,
  *   mask bit >= n_qubits), NQS_ERR_NAN (non-finite coefficient), NQS_ERR_ALLOC, NQS_ERR_CUDA.
  *   Synchronous. */
 int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const uint64_t* z_mask,
@@ -90,8 +98,9 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
 /* Merged term count K' and group count G. */
 int nqs_ham_info(nqs_ham_t ham, int64_t* n_terms_merged, int64_t* n_groups);
 
-/* Copy the grouped table to host arrays: grp_mask[G] (ascending), grp_offset[G+1] (terms of
- * group g are [grp_offset[g], grp_offset[g+1])), term_z[K'] (ascending within a group) and the
+/* Copy the grouped table to host arrays: grp_mask[G] (ascending; G * W words), grp_offset[G+1]
+ * (terms of group g are [grp_offset[g], grp_offset[g+1])), term_z[K'] (ascending within a
+ * group; K' * W words) and the
  * phase-folded coefficients c'_k = c_k (-i)^{r_k} as term_c_re[K'], term_c_im[K'].  Any
  * pointer may be NULL to skip that array.  Synchronous. */
 int nqs_ham_export(nqs_ham_t ham, uint64_t* grp_mask, int64_t* grp_offset, uint64_t* term_z,
@@ -176,7 +185,8 @@ int nqs_logpsi(nqs_model_t model, const uint64_t* bits, int64_t B, float* log_ab
 /* Term sweep alone (Eq. mtx_element on grouped strings): for each sample x_i (device,
  * in the model's sector) and each group g whose flip x' = x_i ^ m_g stays in the sector,
  * S_g(x_i) = sum_{k in g} c'_k (-1)^{popcount(x_i & z_k)}.  A sample outside the sector gets
- * one row, x' = x_i with S = NaN + i NaN.  Rows are written per sample in group order: row_offset[B+1] (device int64), xprime[row], s_re[row], s_im[row] (device;
+ * one row, x' = x_i with S = NaN + i NaN.  Rows are written per sample in group order:
+ * row_offset[B+1] (device int64), xprime[row] (W words per row), s_re[row], s_im[row] (device;
  * fp32), capacity rows at most.  If the row count exceeds capacity, returns NQS_ERR_CAPACITY
  * with *n_rows = the count and no rows written.  n_up, n_dn: the sector.  Synchronises
  * `stream` once (to size the output). */

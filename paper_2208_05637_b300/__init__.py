@@ -45,7 +45,7 @@ class ModelDesc(ctypes.Structure):
     _fields_ = [("arch", ctypes.c_int), ("n_qubits", ctypes.c_int), ("n_up", ctypes.c_int),
                 ("n_dn", ctypes.c_int), ("hidden", ctypes.c_int), ("layers", ctypes.c_int),
                 ("heads", ctypes.c_int), ("precision", ctypes.c_int),
-                ("compensated", ctypes.c_int), ("order", ctypes.c_int * 64)]
+                ("compensated", ctypes.c_int), ("order", ctypes.c_int * 128)]
 
 
 _P = ctypes.c_void_p
@@ -155,15 +155,32 @@ def probe_pipes():
 
 
 # ----------------------------------------------------------------- Hamiltonian
+def words_of(n_qubits: int) -> int:
+    """uint64 words per configuration or mask: 1 for n <= 64 qubits, 2 for n <= 128."""
+    return (int(n_qubits) + 63) // 64
+
+
+def _nconf(bits):
+    """Number of configurations in a bits tensor ([B] one-word or [B, 2] two-word)."""
+    return bits.shape[0] if bits.dim() == 2 else bits.numel()
+
+
 class Hamiltonian:
-    """Owner of an nqs_ham_t built by nqs_ham_create from host masks and coefficients."""
+    """Owner of an nqs_ham_t built by nqs_ham_create from host masks and coefficients.  Masks are
+    uint64 arrays of shape [K] (n <= 64 qubits) or [K, 2] (n <= 128; word 0 holds qubits 0..63)."""
 
     def __init__(self, n_qubits, x_mask, z_mask, coeff):
+        W = words_of(n_qubits)
         xm = np.ascontiguousarray(x_mask, dtype=np.uint64)
         zm = np.ascontiguousarray(z_mask, dtype=np.uint64)
         c = np.ascontiguousarray(coeff, dtype=np.float64)
+        if W > 1 and (xm.ndim != 2 or xm.shape[1] != W or zm.shape != xm.shape):
+            raise ValueError(f"{n_qubits} qubits need masks of shape [K, {W}]")
+        if W == 1 and (xm.ndim != 1 or zm.ndim != 1):
+            raise ValueError("masks of n <= 64 qubits are 1-D uint64 arrays")
         if not (len(xm) == len(zm) == len(c)):
             raise ValueError("x_mask, z_mask and coeff must have equal length")
+        self.words = W
         h = _P()
         _check(_lib.nqs_ham_create(int(n_qubits), len(c), xm.ctypes.data_as(_P), zm.ctypes.data_as(_P),
                                    c.ctypes.data_as(_P), ctypes.byref(h)), "nqs_ham_create")
@@ -177,8 +194,10 @@ class Hamiltonian:
 
     def export(self):
         K, G = self.info()
-        out = dict(group_mask=np.zeros(G, np.uint64), group_offset=np.zeros(G + 1, np.int64),
-                   term_z=np.zeros(K, np.uint64), term_c_re=np.zeros(K), term_c_im=np.zeros(K))
+        W = self.words
+        shp = (lambda k: (k,)) if W == 1 else (lambda k: (k, W))
+        out = dict(group_mask=np.zeros(shp(G), np.uint64), group_offset=np.zeros(G + 1, np.int64),
+                   term_z=np.zeros(shp(K), np.uint64), term_c_re=np.zeros(K), term_c_im=np.zeros(K))
         _check(_lib.nqs_ham_export(self.handle, *(out[k].ctypes.data_as(_P) for k in
                                                   ("group_mask", "group_offset", "term_z",
                                                    "term_c_re", "term_c_im"))), "nqs_ham_export")
@@ -294,7 +313,7 @@ def nqs_sample(model, n_samples, max_unique, seed, ws=None, trace=False, stream=
 
 def nqs_logpsi(model, bits, ws=None, stream=None):
     import torch
-    B = bits.numel()
+    B = _nconf(bits)
     la = torch.empty(B, dtype=torch.float32, device="cuda")
     ph = torch.empty(B, dtype=torch.float32, device="cuda")
     ws = model.workspace(OP_LOGPSI, B) if ws is None else ws
@@ -305,9 +324,10 @@ def nqs_logpsi(model, bits, ws=None, stream=None):
 
 
 def nqs_term_sweep(ham, n_up, n_dn, bits, compensated=True, capacity=None, stream=None):
-    """Returns (row_offset[B+1], xprime[rows], s_re[rows], s_im[rows]) on the device."""
+    """Returns (row_offset[B+1], xprime[rows] (or [rows, 2] for two-word registers), s_re[rows],
+    s_im[rows]) on the device."""
     import torch
-    B = bits.numel()
+    B = _nconf(bits)
     K, G = ham.info()
     cap = B * G if capacity is None else int(capacity)
     size = ctypes.c_size_t()
@@ -317,7 +337,8 @@ def nqs_term_sweep(ham, n_up, n_dn, bits, compensated=True, capacity=None, strea
     wsz = 4 * B * T + 8 * (B * T + 1) + 4 * max(1, -(-B // 32)) * T * 256 + 16 * B * G + 4 * 256
     ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
     row_offset = torch.empty(B + 1, dtype=torch.int64, device="cuda")
-    xp = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+    W = ham.words
+    xp = torch.empty((max(cap, 1),) if W == 1 else (max(cap, 1), W), dtype=torch.int64, device="cuda")
     sre = torch.empty(max(cap, 1), dtype=torch.float32, device="cuda")
     sim = torch.empty(max(cap, 1), dtype=torch.float32, device="cuda")
     nr = _I64()
@@ -332,7 +353,7 @@ def nqs_term_sweep(ham, n_up, n_dn, bits, compensated=True, capacity=None, strea
 def nqs_local_energy(ham, model, bits, ws=None, out=None, stream=None):
     """Complex local energies as a [B, 2] fp32 tensor (Re, Im)."""
     import torch
-    B = bits.numel()
+    B = _nconf(bits)
     out = torch.empty((B, 2), dtype=torch.float32, device="cuda") if out is None else out
     ws = model.workspace(OP_LOCAL_ENERGY, B, ham) if ws is None else ws
     wp, wn = _ws(ws)

@@ -167,7 +167,7 @@ static void eloc_layout(Carver& c, const nqs_model_s* m, const nqs_ham_s* h, int
     e.cnt = c.take<int32_t>(e.chunk * e.ntiles);
     e.off = c.take<int64_t>(e.chunk * e.ntiles + 1);
     e.valid = c.take<uint32_t>(sweep_valid_words(h->dev, e.chunk));
-    e.xprime = c.take<uint64_t>(e.rows_cap);
+    e.xprime = c.take<uint64_t>(e.rows_cap * h->words);
     e.S = c.take<float4>(e.rows_cap);
     e.contrib = nullptr;
     e.dedup = false;
@@ -254,14 +254,22 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
                    const double* coeff, nqs_ham_t* out) {
     if (!out) { set_error("out is NULL"); return NQS_ERR_INVALID_ARG; }
     *out = nullptr;
-    if (n_qubits < 1 || n_qubits > 64) { set_error("n_qubits must be in 1..64"); return NQS_ERR_NQUBITS; }
+    if (n_qubits < 1 || n_qubits > 128) { set_error("n_qubits must be in 1..128"); return NQS_ERR_NQUBITS; }
     if (n_terms < 1 || !x_mask || !z_mask || !coeff) {
         set_error("need n_terms >= 1 and non-NULL x_mask, z_mask, coeff");
         return NQS_ERR_INVALID_ARG;
     }
-    const uint64_t valid = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1);
+    const int W = words_of(n_qubits);
+    // masks as 128-bit values (the high word zero for one-word registers)
+    auto valid_word = [&](int w) -> uint64_t {
+        const int bits = std::min(64, n_qubits - 64 * w);
+        return bits >= 64 ? ~0ull : ((1ull << bits) - 1);
+    };
+    std::vector<U128> xs((size_t)n_terms), zs((size_t)n_terms);
     for (int64_t k = 0; k < n_terms; ++k) {
-        if ((x_mask[k] | z_mask[k]) & ~valid) {
+        const uint64_t x0 = x_mask[k * W], z0 = z_mask[k * W];
+        const uint64_t x1 = W > 1 ? x_mask[k * W + 1] : 0, z1 = W > 1 ? z_mask[k * W + 1] : 0;
+        if (((x0 | z0) & ~valid_word(0)) || (W > 1 && ((x1 | z1) & ~valid_word(1)))) {
             set_error("term " + std::to_string(k) + " has a mask bit >= n_qubits");
             return NQS_ERR_INVALID_ARG;
         }
@@ -269,37 +277,47 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
             set_error("term " + std::to_string(k) + " has a non-finite coefficient");
             return NQS_ERR_NAN;
         }
+        xs[k] = U128{x0, x1};
+        zs[k] = U128{z0, z1};
     }
 
     // 1. merge equal (x, z) by fp64 summation in input order (stable sort keeps input order)
     std::vector<int64_t> idx(n_terms);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
-        return x_mask[a] != x_mask[b] ? x_mask[a] < x_mask[b] : z_mask[a] < z_mask[b];
+        return xs[a] != xs[b] ? xs[a] < xs[b] : zs[a] < zs[b];
     });
     auto* h = new (std::nothrow) nqs_ham_s();
     if (!h) return NQS_ERR_ALLOC;
     h->n = n_qubits;
+    h->words = W;
     h->K_in = n_terms;
-    const uint64_t A = spin_mask(n_qubits, 0), Bm = spin_mask(n_qubits, 1);
+    const U128 A{spin_mask_word(n_qubits, 0, 0), spin_mask_word(n_qubits, 0, 1)};
+    const U128 Bm{spin_mask_word(n_qubits, 1, 0), spin_mask_word(n_qubits, 1, 1)};
+    auto popc = [](const U128& v) { return __builtin_popcountll(v.lo) + __builtin_popcountll(v.hi); };
+    auto push = [&](std::vector<uint64_t>& dst, const U128& v) {
+        dst.push_back(v.lo);
+        if (W > 1) dst.push_back(v.hi);
+    };
     std::vector<double> c_signed;
+    U128 last_x{~0ull, ~0ull};
     for (int64_t i = 0; i < n_terms;) {
-        const uint64_t x = x_mask[idx[i]], z = z_mask[idx[i]];
+        const U128 x = xs[idx[i]], z = zs[idx[i]];
         double acc = 0.0;
         int64_t j = i;
-        for (; j < n_terms && x_mask[idx[j]] == x && z_mask[idx[j]] == z; ++j) acc += coeff[idx[j]];
+        for (; j < n_terms && xs[idx[j]] == x && zs[idx[j]] == z; ++j) acc += coeff[idx[j]];
         i = j;
         if (acc == 0.0) continue;   // 2. drop exact zeros
         // 3. group by x (the flip pattern)
-        if (h->grp_mask.empty() || h->grp_mask.back() != x) {
-            h->grp_mask.push_back(x);
-            h->grp_off.push_back((int64_t)h->term_z.size());
-            uint32_t na = (uint32_t)__builtin_popcountll(x & A);
-            uint32_t nb = (uint32_t)__builtin_popcountll(x & Bm);
+        if (h->grp_off.empty() || last_x != x) {
+            push(h->grp_mask, x);
+            last_x = x;
+            h->grp_off.push_back((int64_t)c_signed.size());
+            const uint32_t na = (uint32_t)popc(x & A), nb = (uint32_t)popc(x & Bm);
             h->grp_meta.push_back(na | (nb << 8));
         }
         // 4. fold (-i)^r, r = popcount(x & z), into the coefficient
-        const int r = __builtin_popcountll(x & z) & 3;
+        const int r = popc(x & z) & 3;
         double re = 0.0, im = 0.0, sgn = 1.0;
         switch (r) {
             case 0: re = acc; sgn = 1.0; break;
@@ -308,20 +326,20 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
             default: im = acc; sgn = 1.0; break;
         }
         if (r & 1) h->grp_meta.back() |= META_HAS_IMAG;
-        h->term_z.push_back(z);
+        push(h->term_z, z);
         h->term_c_re.push_back(re);
         h->term_c_im.push_back(im);
         c_signed.push_back(sgn * acc);
     }
-    h->grp_off.push_back((int64_t)h->term_z.size());
-    h->K = (int64_t)h->term_z.size();
-    h->G = (int64_t)h->grp_mask.size();
+    h->K = (int64_t)c_signed.size();
+    h->grp_off.push_back(h->K);
+    h->G = (int64_t)h->grp_meta.size();
     if (h->K == 0) {
         // keep one zero term so the device tables are never empty
-        h->grp_mask.assign(1, 0);
+        h->grp_mask.assign(W, 0);
         h->grp_off.assign({0, 1});
         h->grp_meta.assign(1, 0);
-        h->term_z.assign(1, 0);
+        h->term_z.assign(W, 0);
         h->term_c_re.assign(1, 0.0);
         h->term_c_im.assign(1, 0.0);
         c_signed.assign(1, 0.0);
@@ -330,11 +348,12 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     }
     if (h->K > (int64_t)0xffffffffll) { delete h; set_error("too many terms"); return NQS_ERR_UNSUPPORTED; }
 
-    // device copy: one allocation, arrays 256-byte aligned
-    // the term arrays carry one zero padding term (the sweep stages even-aligned ranges)
+    // device copy: one allocation, arrays 256-byte aligned; the term records carry one zero
+    // padding record
+    const int rec = W;   // uint4 per term record
     Carver c(nullptr);
-    c.take<uint64_t>(h->G); c.take<uint32_t>(h->G + 1); c.take<uint32_t>(h->G);
-    c.take<uint4>(h->K + 1);
+    c.take<uint64_t>(h->G * W); c.take<uint32_t>(h->G + 1); c.take<uint32_t>(h->G);
+    c.take<uint4>((h->K + 1) * rec);
     cudaGetDevice(&h->device);
     if (cudaMalloc(&h->d_block, c.used) != cudaSuccess) {
         cudaGetLastError();
@@ -343,33 +362,40 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
         return NQS_ERR_ALLOC;
     }
     Carver d(h->d_block);
-    auto* d_mask = d.take<uint64_t>(h->G);
+    auto* d_mask = d.take<uint64_t>(h->G * W);
     auto* d_off = d.take<uint32_t>(h->G + 1);
     auto* d_meta = d.take<uint32_t>(h->G);
-    auto* d_t = d.take<uint4>(h->K + 1);
+    auto* d_t = d.take<uint4>((h->K + 1) * rec);
     std::vector<uint32_t> off32(h->grp_off.begin(), h->grp_off.end());
-    std::vector<uint4> tt(h->K + 1, make_uint4(0u, 0u, 0u, 0u));
+    std::vector<uint4> tt((size_t)(h->K + 1) * rec, make_uint4(0u, 0u, 0u, 0u));
     for (int64_t k = 0; k < h->K; ++k) {
         const float hi = (float)c_signed[k];
         const float lo = (float)(c_signed[k] - (double)hi);
         uint32_t hb, lb;
         std::memcpy(&hb, &hi, 4);
         std::memcpy(&lb, &lo, 4);
-        tt[k] = make_uint4((uint32_t)h->term_z[k], (uint32_t)(h->term_z[k] >> 32), hb, lb);
+        const uint64_t z0 = h->term_z[k * W];
+        if (W == 1) {
+            tt[k] = make_uint4((uint32_t)z0, (uint32_t)(z0 >> 32), hb, lb);
+        } else {
+            const uint64_t z1 = h->term_z[k * W + 1];
+            tt[2 * k] = make_uint4((uint32_t)z0, (uint32_t)(z0 >> 32), (uint32_t)z1, (uint32_t)(z1 >> 32));
+            tt[2 * k + 1] = make_uint4(hb, lb, 0u, 0u);
+        }
     }
     int any_imag = 0;
     for (uint32_t mt : h->grp_meta) any_imag |= (mt & META_HAS_IMAG) ? 1 : 0;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpy(d_mask, h->grp_mask.data(), h->G * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_mask, h->grp_mask.data(), h->G * W * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_off, off32.data(), (h->G + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_meta, h->grp_meta.data(), h->G * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_t, tt.data(), (h->K + 1) * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_t, tt.data(), tt.size() * 16, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(h->d_block);
         delete h;
         return cuda_fail(e, "copy of the Hamiltonian tables", __FILE__, __LINE__);
     }
-    h->dev = HamDev{h->n, h->K, h->G, d_mask, d_off, d_meta, d_t, any_imag};
+    h->dev = HamDev{h->n, W, h->K, h->G, d_mask, d_off, d_meta, d_t, any_imag};
     *out = h;
     return NQS_OK;
 }
@@ -384,9 +410,9 @@ int nqs_ham_info(nqs_ham_t ham, int64_t* n_terms_merged, int64_t* n_groups) {
 int nqs_ham_export(nqs_ham_t h, uint64_t* grp_mask, int64_t* grp_offset, uint64_t* term_z,
                    double* term_c_re, double* term_c_im) {
     if (!h) return NQS_ERR_INVALID_ARG;
-    if (grp_mask) std::memcpy(grp_mask, h->grp_mask.data(), h->G * 8);
+    if (grp_mask) std::memcpy(grp_mask, h->grp_mask.data(), h->G * h->words * 8);
     if (grp_offset) std::memcpy(grp_offset, h->grp_off.data(), (h->G + 1) * 8);
-    if (term_z) std::memcpy(term_z, h->term_z.data(), h->K * 8);
+    if (term_z) std::memcpy(term_z, h->term_z.data(), h->K * h->words * 8);
     if (term_c_re) std::memcpy(term_c_re, h->term_c_re.data(), h->K * 8);
     if (term_c_im) std::memcpy(term_c_im, h->term_c_im.data(), h->K * 8);
     return NQS_OK;
@@ -409,7 +435,11 @@ int nqs_model_create(const nqs_model_desc* d, nqs_model_t* out) {
     if (!d || !out) { set_error("desc/out is NULL"); return NQS_ERR_INVALID_ARG; }
     *out = nullptr;
     const int n = d->n_qubits;
-    if (n < 4 || n > 64 || (n & 1)) { set_error("n_qubits must be even and in 4..64"); return NQS_ERR_NQUBITS; }
+    if (n < 4 || n > MAX_Q || (n & 1)) { set_error("n_qubits must be even and in 4..128"); return NQS_ERR_NQUBITS; }
+    if (n > 64 && d->arch == NQS_ARCH_TRANSFORMER) {
+        set_error("the transformer supports n_qubits <= 64 (two-word registers: product and MADE models)");
+        return NQS_ERR_NQUBITS;
+    }
     const int n_orb = n / 2;
     if (d->n_up < 0 || d->n_dn < 0 || d->n_up > n_orb || d->n_dn > n_orb) {
         set_error("n_up/n_dn outside 0..n_qubits/2");
@@ -419,11 +449,11 @@ int nqs_model_create(const nqs_model_desc* d, nqs_model_t* out) {
         set_error("precision must be NQS_PREC_FP32 or NQS_PREC_BF16");
         return NQS_ERR_INVALID_ARG;
     }
-    uint64_t seen = 0;
+    std::vector<char> seen((size_t)n, 0);
     for (int t = 0; t < n; ++t) {
         int q = d->order[t];
-        if (q < 0 || q >= n || ((seen >> q) & 1)) { set_error("order is not a permutation"); return NQS_ERR_INVALID_ARG; }
-        seen |= 1ull << q;
+        if (q < 0 || q >= n || seen[q]) { set_error("order is not a permutation"); return NQS_ERR_INVALID_ARG; }
+        seen[q] = 1;
     }
     auto* m = new (std::nothrow) nqs_model_s();
     if (!m) return NQS_ERR_ALLOC;
@@ -648,6 +678,7 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
                uint64_t* bits_out, int64_t* counts_out, int64_t capacity, int64_t* n_unique,
                float* p_trace, int64_t trace_stride, void* ws, size_t ws_bytes, void* stream) {
     NQS_TRY(need_params(m));
+    if (m->mc.n > 64) { set_error("the sampler supports n_qubits <= 64"); return NQS_ERR_NQUBITS; }
     if (n_samples < 1 || n_samples >= (1ll << 31) || max_unique < 1 || !n_unique || capacity < 0) {
         set_error("need 1 <= n_samples < 2^31, max_unique >= 1, n_unique non-NULL");
         return NQS_ERR_INVALID_ARG;
@@ -902,14 +933,15 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
         }
         return NQS_OK;
     }
+    const int64_t W = h->words;   // uint64 words per configuration
     NQS_TRY(launch_logpsi_rows(m->mc, m->d_params, bits, B, e.la, e.ph, s));
     for (int64_t lo = 0; lo < B; lo += e.chunk) {
         const int64_t nb = std::min(e.chunk, B - lo);
-        NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo, nb, e.cnt, e.off, e.valid,
+        NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo * W, nb, e.cnt, e.off, e.valid,
                                 e.xprime, e.S, s));
         {
             ProfScope ps("eloc_rows", s);
-            NQS_TRY(launch_eloc_rows(m->mc, m->d_params, bits + lo, nb, e.la + lo, e.ph + lo, e.off,
+            NQS_TRY(launch_eloc_rows(m->mc, m->d_params, bits + lo * W, nb, e.la + lo, e.ph + lo, e.off,
                                      e.ntiles, e.xprime, e.S, eloc + 2 * lo, s));
         }
     }
@@ -921,6 +953,7 @@ int nqs_logpsi_backward(nqs_model_t m, const uint64_t* bits, int64_t B, const fl
                         void* stream) {
     NQS_TRY(need_params(m));
     if (B < 0) return NQS_ERR_INVALID_ARG;
+    if (m->mc.n > 64) { set_error("the log psi backward supports n_qubits <= 64"); return NQS_ERR_NQUBITS; }
     if (B == 0) return NQS_OK;
     if (!bits || !g_abs || !g_phase || !grad) { set_error("null pointer argument"); return NQS_ERR_INVALID_ARG; }
     cudaStream_t s = (cudaStream_t)stream;

@@ -25,9 +25,13 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
     s = t;
 }
 
-__device__ __forceinline__ uint64_t to_positions(uint64_t x, const ModelConst& mc, int upto) {
-    uint64_t xo = 0;
-    for (int t = 0; t < upto; ++t) xo |= ((x >> mc.order[t]) & 1ull) << t;
+// The configuration's bits in sampling order (bit t = x_{order[t]}), in the configuration's own
+// width (one word for n <= 64, two for n <= 128).
+template <class BT>
+__device__ __forceinline__ BT to_positions(const BT& x, const ModelConst& mc, int upto) {
+    BT xo = bits_zero<BT>();
+    for (int t = 0; t < upto; ++t)
+        if (qbit(x, mc.order[t])) xo = with_bit(xo, t);
     return xo;
 }
 
@@ -102,13 +106,14 @@ struct MadeRow {
     }
 
     // h <- relu(first layer) for position bits xo
+    template <class PB>
     __device__ static void first_layer(const float* sm, const MadeLay& L, const ModelConst& mc,
-                                       uint64_t xo, float (&h)[H]) {
+                                       const PB& xo, float (&h)[H]) {
         float z[H];
 #pragma unroll
         for (int k = 0; k < H; ++k) z[k] = sm[L.b[0] + k];
         for (int t = 0; t < mc.n; ++t) {
-            const float s = ((xo >> t) & 1ull) ? 1.f : -1.f;
+            const float s = qbit(xo, t) ? 1.f : -1.f;
             const float4* w = reinterpret_cast<const float4*>(sm + L.W[0] + t * H);
 #pragma unroll
             for (int k4 = 0; k4 < H / 4; ++k4) {
@@ -124,8 +129,9 @@ struct MadeRow {
     }
 
     // h <- last hidden layer of the modulus MADE for position bits xo
+    template <class PB>
     __device__ static void hidden(const float* sm, const MadeLay& L, const ModelConst& mc,
-                                  uint64_t xo, float (&h)[H]) {
+                                  const PB& xo, float (&h)[H]) {
         first_layer(sm, L, mc, xo, h);
         float z[H];
         for (int l = 1; l < mc.layers; ++l) {
@@ -163,12 +169,13 @@ struct MadeRow {
     }
 
     // phase MLP output selected by the last two positions; hp receives the hidden layer
+    template <class PB>
     __device__ static float phase(const float* sm, const MadeLay& L, const ModelConst& mc,
-                                  uint64_t xo, float (&hp)[H]) {
+                                  const PB& xo, float (&hp)[H]) {
 #pragma unroll
         for (int k = 0; k < H; ++k) hp[k] = sm[L.pb0 + k];
         for (int t = 0; t < mc.n - 2; ++t) {
-            const float s = ((xo >> t) & 1ull) ? 1.f : -1.f;
+            const float s = qbit(xo, t) ? 1.f : -1.f;
             const float4* w = reinterpret_cast<const float4*>(sm + L.P0 + t * H);
 #pragma unroll
             for (int k4 = 0; k4 < H / 4; ++k4) {
@@ -181,7 +188,7 @@ struct MadeRow {
         }
 #pragma unroll
         for (int k = 0; k < H; ++k) hp[k] = fmaxf(hp[k], 0.f);
-        const int sel = (int)(((xo >> (mc.n - 2)) & 1ull) * 2 + ((xo >> (mc.n - 1)) & 1ull));
+        const int sel = qbit(xo, mc.n - 2) * 2 + qbit(xo, mc.n - 1);
         float a = sm[L.pb1 + sel];
         const float4* w = reinterpret_cast<const float4*>(sm + L.P1 + sel * H);
 #pragma unroll
@@ -195,10 +202,11 @@ struct MadeRow {
         return a;
     }
 
-    __device__ static void logpsi(const float* sm, const ModelConst& mc, uint64_t x, float& la,
+    template <class BT>
+    __device__ static void logpsi(const float* sm, const ModelConst& mc, const BT& x, float& la,
                                   float& ph) {
         const MadeLay L = made_layout(mc, H);
-        const uint64_t xo = to_positions(x, mc, mc.n);
+        const BT xo = to_positions(x, mc, mc.n);
         float h[H];
         hidden(sm, L, mc, xo, h);
         float acc = 0.f, err = 0.f;
@@ -206,7 +214,7 @@ struct MadeRow {
         bool bad = false;
         for (int t = 0; t < mc.n; ++t) {
             const int sp = mc.order[t] & 1;
-            const int b = (int)((xo >> t) & 1ull);
+            const int b = qbit(xo, t);
             const int c = sp ? ones1 : ones0;
             const int need = sp ? mc.n_dn : mc.n_up;
             if (c + mc.after[t] < need) bad |= (b == 0);
@@ -237,14 +245,15 @@ struct ProductRow {
     __device__ static void stage(float* sm, const float* __restrict__ P, const ModelConst& mc) {
         for (int t = threadIdx.x; t < mc.n; t += blockDim.x) sm[t] = fminf(fmaxf(P[mc.p_prob + t], 0.f), 1.f);
     }
-    __device__ static void logpsi(const float* sm, const ModelConst& mc, uint64_t x, float& la,
+    template <class BT>
+    __device__ static void logpsi(const float* sm, const ModelConst& mc, const BT& x, float& la,
                                   float& ph) {
         float acc = 0.f, err = 0.f;
         int ones0 = 0, ones1 = 0;
         bool bad = false;
         for (int t = 0; t < mc.n; ++t) {
             const int sp = mc.order[t] & 1;
-            const int b = (int)((x >> mc.order[t]) & 1ull);
+            const int b = qbit(x, mc.order[t]);
             const int c = sp ? ones1 : ones0;
             const int need = sp ? mc.n_dn : mc.n_up;
             if (c + mc.after[t] < need) bad |= (b == 0);
@@ -262,9 +271,9 @@ struct ProductRow {
 };
 
 // ------------------------------------------------------------------ kernels
-template <class R>
+template <class R, class BT>
 __global__ void __launch_bounds__(128)
-logpsi_rows_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
+logpsi_rows_kernel(ModelConst mc, const float* __restrict__ P, const BT* __restrict__ bits,
                    int64_t B, float* __restrict__ la, float* __restrict__ ph) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
@@ -282,12 +291,12 @@ logpsi_rows_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* _
 // One CTA per sample: evaluate the model on every connected x' of the sample and reduce
 //   E_loc(x) = sum_r S_r exp(log|f(x'_r)| - log|f(x)|) e^{i (phi(x'_r) - phi(x))}
 // with the ratio-weighted (optionally TwoSum-compensated) complex reduction fused in.
-template <class R>
+template <class R, class BT>
 __global__ void __launch_bounds__(128)
-eloc_rows_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
+eloc_rows_kernel(ModelConst mc, const float* __restrict__ P, const BT* __restrict__ bits,
                  int64_t B, const float* __restrict__ la_x, const float* __restrict__ ph_x,
                  const int64_t* __restrict__ off, int64_t ntiles,
-                 const uint64_t* __restrict__ xprime, const float4* __restrict__ S,
+                 const BT* __restrict__ xprime, const float4* __restrict__ S,
                  float* __restrict__ eloc) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
@@ -296,11 +305,11 @@ eloc_rows_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __r
     __syncthreads();
     for (int64_t i = blockIdx.x; i < B; i += gridDim.x) {
         const int64_t r0 = off[i * ntiles], r1 = off[(i + 1) * ntiles];
-        const uint64_t x = bits[i];
+        const BT x = bits[i];
         const float lai = la_x[i], phi = ph_x[i];
         float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
         for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const uint64_t xp = xprime[r];
+            const BT xp = xprime[r];
             const float4 s = S[r];
             const float sre = s.x + s.y, sim = s.z + s.w;
             float cr = sre, ci = sim;
@@ -356,7 +365,7 @@ cond_rows_kernel(ModelConst mc, const float* __restrict__ P, int k,
         const uint64_t xo = to_positions(bits[s], mc, k);
         int ones0 = 0, ones1 = 0;
         for (int t = 0; t < k; ++t) {
-            const int b = (int)((xo >> t) & 1ull);
+            const int b = qbit(xo, t);
             if (mc.order[t] & 1) ones1 += b; else ones0 += b;
         }
         const int sp = mc.order[k] & 1;
@@ -440,7 +449,7 @@ made_backward_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t*
         int ones0 = 0, ones1 = 0;
         for (int t = 0; t < n; ++t) {
             const int sp = mc.order[t] & 1;
-            const int b = (int)((xo >> t) & 1ull);
+            const int b = qbit(xo, t);
             const int c = sp ? ones1 : ones0;
             const int need = sp ? mc.n_dn : mc.n_up;
             float d = 0.f;
@@ -522,7 +531,7 @@ __global__ void product_backward_kernel(ModelConst mc, const float* __restrict__
         for (int u = 0; u < t; ++u)
             if ((mc.order[u] & 1) == sp) c += (int)((x >> mc.order[u]) & 1ull);
         if (!(c + mc.after[t] < need) && !(c >= need)) {
-            const int b = (int)((x >> mc.order[t]) & 1ull);
+            const int b = qbit(x, mc.order[t]);
             acc += 0.5f * g_abs[i] * (b ? 1.f / p : -1.f / (1.f - p));
         }
     }
@@ -567,9 +576,15 @@ int launch_logpsi_rows(const ModelConst& mc, const float* P, const uint64_t* bit
     return with_row_model(mc, [&](auto row) -> int {
         using R = decltype(row);
         const size_t sm = R::smem_bytes(mc);
-        NQS_TRY(prep_smem(logpsi_rows_kernel<R>, sm));
         ProfScope ps("logpsi_rows", s);
-        logpsi_rows_kernel<R><<<grid_for(B, 128), 128, sm, s>>>(mc, P, bits, B, la, ph);
+        if (words_of(mc.n) == 2) {
+            NQS_TRY(prep_smem(logpsi_rows_kernel<R, U128>, sm));
+            logpsi_rows_kernel<R, U128><<<grid_for(B, 128), 128, sm, s>>>(mc, P, reinterpret_cast<const U128*>(bits),
+                                                                           B, la, ph);
+        } else {
+            NQS_TRY(prep_smem(logpsi_rows_kernel<R, uint64_t>, sm));
+            logpsi_rows_kernel<R, uint64_t><<<grid_for(B, 128), 128, sm, s>>>(mc, P, bits, B, la, ph);
+        }
         NQS_LAUNCHED();
         return NQS_OK;
     });
@@ -581,9 +596,15 @@ int launch_eloc_rows(const ModelConst& mc, const float* P, const uint64_t* bits,
     return with_row_model(mc, [&](auto row) -> int {
         using R = decltype(row);
         const size_t sm = R::smem_bytes(mc);
-        NQS_TRY(prep_smem(eloc_rows_kernel<R>, sm));
         const int grid = (int)std::min<int64_t>(B, (int64_t)num_sms() * 8);
-        eloc_rows_kernel<R><<<grid, 128, sm, s>>>(mc, P, bits, B, la_x, ph_x, off, ntiles, xprime, S, eloc);
+        if (words_of(mc.n) == 2) {
+            NQS_TRY(prep_smem(eloc_rows_kernel<R, U128>, sm));
+            eloc_rows_kernel<R, U128><<<grid, 128, sm, s>>>(mc, P, reinterpret_cast<const U128*>(bits), B, la_x, ph_x,
+                                                            off, ntiles, reinterpret_cast<const U128*>(xprime), S, eloc);
+        } else {
+            NQS_TRY(prep_smem(eloc_rows_kernel<R, uint64_t>, sm));
+            eloc_rows_kernel<R, uint64_t><<<grid, 128, sm, s>>>(mc, P, bits, B, la_x, ph_x, off, ntiles, xprime, S, eloc);
+        }
         NQS_LAUNCHED();
         return NQS_OK;
     });

@@ -89,6 +89,7 @@ extern "C" int nqs_local_energy_noalloc(nqs_ham_t h, nqs_model_t m, const uint64
         set_error("nqs_local_energy_noalloc serves the product and MADE models");
         return NQS_ERR_UNSUPPORTED;
     }
+    if (h->words != 1) { set_error("nqs_local_energy_noalloc supports n_qubits <= 64"); return NQS_ERR_NQUBITS; }
     if (B == 0) return NQS_OK;
     if (!bits || !eloc) { set_error("bits/eloc is NULL"); return NQS_ERR_INVALID_ARG; }
 

@@ -54,19 +54,52 @@ struct ProfScope {
 int num_sms();
 bool prof_enabled();   // per-kernel profiling is on (nqs_profile_enable)
 
+// ------------------------------------------------------------------ bit strings
+// Configurations and Pauli masks of n <= 64 qubits are one uint64 (bit j = qubit j); of
+// 64 < n <= 128 qubits two consecutive uint64 words, qubits 0..63 in the first (U128 below).
+// Kernels that serve both widths are templates over the bit-string type.
+struct U128 {
+    uint64_t lo, hi;
+};
+__host__ __device__ __forceinline__ U128 operator^(const U128& a, const U128& b) { return U128{a.lo ^ b.lo, a.hi ^ b.hi}; }
+__host__ __device__ __forceinline__ U128 operator&(const U128& a, const U128& b) { return U128{a.lo & b.lo, a.hi & b.hi}; }
+__host__ __device__ __forceinline__ U128 operator|(const U128& a, const U128& b) { return U128{a.lo | b.lo, a.hi | b.hi}; }
+__host__ __device__ __forceinline__ bool operator==(const U128& a, const U128& b) { return a.lo == b.lo && a.hi == b.hi; }
+__host__ __device__ __forceinline__ bool operator!=(const U128& a, const U128& b) { return !(a == b); }
+__host__ __device__ __forceinline__ bool operator<(const U128& a, const U128& b) {
+    return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo;
+}
+// bit q of a configuration
+__host__ __device__ __forceinline__ int qbit(uint64_t x, int q) { return (int)((x >> q) & 1ull); }
+__host__ __device__ __forceinline__ int qbit(const U128& x, int q) {
+    return q < 64 ? (int)((x.lo >> q) & 1ull) : (int)((x.hi >> (q - 64)) & 1ull);
+}
+// x with bit q set
+__host__ __device__ __forceinline__ uint64_t with_bit(uint64_t x, int q) { return x | (1ull << q); }
+__host__ __device__ __forceinline__ U128 with_bit(U128 x, int q) {
+    if (q < 64) x.lo |= 1ull << q; else x.hi |= 1ull << (q - 64);
+    return x;
+}
+template <class BT> __host__ __device__ __forceinline__ BT bits_zero();
+template <> __host__ __device__ __forceinline__ uint64_t bits_zero<uint64_t>() { return 0ull; }
+template <> __host__ __device__ __forceinline__ U128 bits_zero<U128>() { return U128{0ull, 0ull}; }
+inline int words_of(int n) { return (n + 63) / 64; }
+
 // ------------------------------------------------------------------ Hamiltonian
 // group meta word: bits 0-7 n_alpha, 8-15 n_beta, bit 16 "has sigma_2-odd terms"
 constexpr uint32_t META_HAS_IMAG = 1u << 16;
 
 struct HamDev {
     int n;
+    int words;      // uint64 words per mask (1: n <= 64, 2: n <= 128)
     int64_t K;      // merged terms
     int64_t G;      // groups
-    const uint64_t* grp_mask;
+    const uint64_t* grp_mask;  // G masks of `words` words each
     const uint32_t* grp_off;   // G+1
     const uint32_t* grp_meta;  // G
-    // K + 1 records (the last a zero term): {z low word, z high word, bits of the fp32 hi and lo
-    // of the signed real magnitude of c'} -- one 16-byte load per term
+    // K + 1 records (the last a zero term).  One word: 16 bytes {z low half, z high half, bits of
+    // the fp32 hi and lo of the signed real magnitude of c'} -- one 16-byte load per term.  Two
+    // words: 32 bytes {z word 0 (two halves), z word 1 (two halves)}, {c' hi, c' lo, 0, 0}.
     const uint4* term;
     int any_imag;              // some group holds a term with an odd sigma_2 count
 };
@@ -75,6 +108,8 @@ struct HamDev {
 
 struct nqs_ham_s {
     int n = 0;
+    int words = 1;                              // uint64 words per mask
+    // masks below hold `words` words each (grp_mask: G masks, term_z: K masks)
     int device = 0;
     int64_t K_in = 0, K = 0, G = 0;
     std::vector<uint64_t> grp_mask;
@@ -91,7 +126,14 @@ namespace nqs {
 // Spin masks: bits of one spin species (0: even bits, spin up; 1: odd bits, spin down).
 inline uint64_t spin_mask(int n, int spin) {
     uint64_t m = 0;
-    for (int j = spin; j < n; j += 2) m |= (1ull << j);
+    for (int j = spin; j < n && j < 64; j += 2) m |= (1ull << j);
+    return m;
+}
+// word w of the spin mask of an n-qubit register
+inline uint64_t spin_mask_word(int n, int spin, int w) {
+    uint64_t m = 0;
+    for (int j = spin; j < n; j += 2)
+        if (j / 64 == w) m |= (1ull << (j % 64));
     return m;
 }
 
@@ -111,7 +153,7 @@ inline int64_t feasible_groups(const nqs_ham_s* h, int n_up, int n_dn) {
 }
 
 // ------------------------------------------------------------------ model
-constexpr int MAX_Q = 64;
+constexpr int MAX_Q = 128;   // qubits of the row-wise models (the transformer: 64)
 constexpr int MADE_MAX_LAYERS = 4;
 constexpr int TF_MAX_LAYERS = 8;
 

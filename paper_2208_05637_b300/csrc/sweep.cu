@@ -35,16 +35,45 @@ __device__ __forceinline__ uint32_t dn_bits(uint64_t v) {
     return ((uint32_t)v & 0xAAAAAAAAu) | (((uint32_t)(v >> 32) & 0xAAAAAAAAu) >> 1);
 }
 
-__device__ __forceinline__ bool sample_in_sector(uint64_t x, int n_up, int n_dn) {
-    return __popc(up_bits(x)) == n_up && __popc(dn_bits(x)) == n_dn;
+// Species words of a configuration: {up, dn} for one word, {up of word 0, up of word 1, dn of
+// word 0, dn of word 1} for two words.
+struct Sp1 {
+    uint32_t u, d;
+};
+struct Sp2 {
+    uint32_t u0, u1, d0, d1;
+};
+__device__ __forceinline__ Sp1 species(uint64_t v) { return Sp1{up_bits(v), dn_bits(v)}; }
+__device__ __forceinline__ Sp2 species(const U128& v) {
+    return Sp2{up_bits(v.lo), up_bits(v.hi), dn_bits(v.lo), dn_bits(v.hi)};
+}
+template <class BT> struct SpOf { using type = Sp1; };
+template <> struct SpOf<U128> { using type = Sp2; };
+
+__device__ __forceinline__ int pop_up(const Sp1& a, const Sp1& b) { return __popc(a.u & b.u); }
+__device__ __forceinline__ int pop_dn(const Sp1& a, const Sp1& b) { return __popc(a.d & b.d); }
+__device__ __forceinline__ int pop_up(const Sp2& a, const Sp2& b) { return __popc(a.u0 & b.u0) + __popc(a.u1 & b.u1); }
+__device__ __forceinline__ int pop_dn(const Sp2& a, const Sp2& b) { return __popc(a.d0 & b.d0) + __popc(a.d1 & b.d1); }
+__device__ __forceinline__ int cnt_up(const Sp1& a) { return __popc(a.u); }
+__device__ __forceinline__ int cnt_dn(const Sp1& a) { return __popc(a.d); }
+__device__ __forceinline__ int cnt_up(const Sp2& a) { return __popc(a.u0) + __popc(a.u1); }
+__device__ __forceinline__ int cnt_dn(const Sp2& a) { return __popc(a.d0) + __popc(a.d1); }
+
+template <class BT>
+__device__ __forceinline__ bool sample_in_sector(const BT& x, int n_up, int n_dn) {
+    const auto sp = species(x);
+    return cnt_up(sp) == n_up && cnt_dn(sp) == n_dn;
 }
 
-// Parity of popcount(x & z) in bit 31 (the float sign bit), z given as its two 32-bit words: the
-// halves of x & z are XOR-folded first, which keeps the parity, so one 32-bit POPC serves a
-// 64-bit mask.
+// Parity of popcount(x & z) in bit 31 (the float sign bit), x and z given as their 32-bit
+// halves: the halves of x & z are XOR-folded first, which keeps the parity, so one 32-bit POPC
+// serves a 64-bit mask.
 __device__ __forceinline__ uint32_t sign_flip(uint32_t xl, uint32_t xh, uint32_t zl, uint32_t zh) {
     return (uint32_t)__popc((xl & zl) ^ (xh & zh)) << 31;
 }
+
+// uint4 per term record: one for one-word masks, two for two-word masks
+template <class BT> __host__ __device__ constexpr int rec_of() { return (int)(sizeof(BT) / 8); }
 
 // Knuth's TwoSum: s + e == a + b exactly, accumulated into the error term.
 __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
@@ -55,21 +84,42 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
 }
 
 // One term of S_g(x): c' (-1)^{popc(x & z)} into the real or (odd sigma_2 count) imaginary sum.
-// The term is its 16-byte record {z low, z high, c' hi bits, c' lo bits}.  IMAG: the Hamiltonian
-// has odd-sigma_2 terms somewhere (else the imaginary branch is compiled out).
-template <bool COMP, bool IMAG>
-__device__ __forceinline__ void add_term(uint32_t xl, uint32_t xh, uint64_t mg, bool has_imag, uint4 t,
-                                         float& re, float& re_e, float& im, float& im_e) {
-    const uint32_t flip = sign_flip(xl, xh, t.x, t.y);
-    const float hi = __uint_as_float(t.z ^ flip);
-    const float lo = __uint_as_float(t.w ^ flip);
-    const bool imag = IMAG && has_imag && (__popc(((uint32_t)mg & t.x) ^ ((uint32_t)(mg >> 32) & t.y)) & 1);
+// Term k is its record at tp (see HamDev::term).  IMAG: the Hamiltonian has odd-sigma_2 terms
+// somewhere (else the imaginary branch is compiled out).
+template <bool COMP>
+__device__ __forceinline__ void acc_term(bool imag, float hi, float lo, float& re, float& re_e, float& im,
+                                         float& im_e) {
     if (COMP) {
         if (imag) { two_sum_acc(im, im_e, hi); im_e += lo; }
         else      { two_sum_acc(re, re_e, hi); re_e += lo; }
     } else {
         if (imag) im += hi; else re += hi;
     }
+}
+
+template <bool COMP, bool IMAG>
+__device__ __forceinline__ void add_term(uint64_t x, uint64_t mg, bool has_imag, const uint4* tp, uint32_t k,
+                                         float& re, float& re_e, float& im, float& im_e) {
+    const uint4 t = tp[k];
+    const uint32_t flip = sign_flip((uint32_t)x, (uint32_t)(x >> 32), t.x, t.y);
+    const bool imag = IMAG && has_imag && (__popc(((uint32_t)mg & t.x) ^ ((uint32_t)(mg >> 32) & t.y)) & 1);
+    acc_term<COMP>(imag, __uint_as_float(t.z ^ flip), __uint_as_float(t.w ^ flip), re, re_e, im, im_e);
+}
+
+template <bool COMP, bool IMAG>
+__device__ __forceinline__ void add_term(const U128& x, const U128& mg, bool has_imag, const uint4* tp, uint32_t k,
+                                         float& re, float& re_e, float& im, float& im_e) {
+    const uint4 z = tp[2 * k], c = tp[2 * k + 1];
+    const uint32_t v = ((uint32_t)x.lo & z.x) ^ ((uint32_t)(x.lo >> 32) & z.y) ^ ((uint32_t)x.hi & z.z) ^
+                       ((uint32_t)(x.hi >> 32) & z.w);
+    const uint32_t flip = (uint32_t)__popc(v) << 31;
+    bool imag = false;
+    if (IMAG && has_imag) {
+        const uint32_t u = ((uint32_t)mg.lo & z.x) ^ ((uint32_t)(mg.lo >> 32) & z.y) ^ ((uint32_t)mg.hi & z.z) ^
+                           ((uint32_t)(mg.hi >> 32) & z.w);
+        imag = __popc(u) & 1;
+    }
+    acc_term<COMP>(imag, __uint_as_float(c.x ^ flip), __uint_as_float(c.y ^ flip), re, re_e, im, im_e);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -98,10 +148,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
 // ballot of sample s is the validity word of s over the warp's 32 groups; lane s keeps it, so
 // the pass writes the tile's validity bitmap per sample, stored [batch][tile][warp][sample],
 // and the number of valid groups per (sample, tile).
+template <class BT>
 __global__ void __launch_bounds__(SWEEP_GT)
-sweep_count_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bits,
+sweep_count_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits,
                    int64_t B, int32_t* __restrict__ cnt, int64_t ntiles, uint32_t* __restrict__ valid) {
-    __shared__ uint2 xs[SWEEP_SB];
+    using Sp = typename SpOf<BT>::type;
+    __shared__ Sp xs[SWEEP_SB];
     __shared__ int32_t wcnt[SWEEP_NW][SWEEP_SB];
     __shared__ uint32_t okm;              // in-sector samples of the batch
     const int tile = blockIdx.y;
@@ -110,16 +162,16 @@ sweep_count_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bi
     const int64_t g = (int64_t)tile * SWEEP_GT + threadIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool live = g < h.G;
-    const uint64_t m = live ? h.grp_mask[g] : 0;
+    const BT m = live ? reinterpret_cast<const BT*>(h.grp_mask)[g] : bits_zero<BT>();
     const uint32_t meta = live ? h.grp_meta[g] : 0;
-    const uint32_t mu = up_bits(m), md = dn_bits(m);
+    const Sp ms = species(m);
     // the occupied flipped bits each species needs: half its flipped bits (an odd count, or a
-    // group past the end, can never match: 64 is out of range)
+    // group past the end, can never match: 1024 is out of range)
     const uint32_t na = meta & 0xffu, nbt = (meta >> 8) & 0xffu;
-    const uint32_t ta = (!live || (na & 1u)) ? 64u : na >> 1, tb = (nbt & 1u) ? 64u : nbt >> 1;
+    const int ta = (!live || (na & 1u)) ? 1024 : (int)(na >> 1), tb = (nbt & 1u) ? 1024 : (int)(nbt >> 1);
     if (threadIdx.x < SWEEP_SB) {
-        const uint64_t x = threadIdx.x < nb ? bits[s0 + threadIdx.x] : 0ull;
-        xs[threadIdx.x] = make_uint2(up_bits(x), dn_bits(x));
+        const BT x = threadIdx.x < nb ? bits[s0 + threadIdx.x] : bits_zero<BT>();
+        xs[threadIdx.x] = species(x);
         const bool ok = threadIdx.x < nb && sample_in_sector(x, n_up, n_dn);
         const unsigned bb = __ballot_sync(0xffffffffu, ok);
         if (threadIdx.x == 0) okm = bb;
@@ -128,8 +180,8 @@ sweep_count_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bi
     uint32_t mine = 0;
 #pragma unroll
     for (int s = 0; s < SWEEP_SB; ++s) {
-        const uint2 xv = xs[s];
-        const bool v = (uint32_t)__popc(xv.x & mu) == ta && (uint32_t)__popc(xv.y & md) == tb;
+        const Sp xv = xs[s];
+        const bool v = pop_up(xv, ms) == ta && pop_dn(xv, ms) == tb;
         const unsigned bal = __ballot_sync(0xffffffffu, v);
         if (lane == s) mine = bal;
     }
@@ -158,28 +210,29 @@ sweep_count_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bi
 // a per-warp queue and are summed 32 at a time, one lane per pair; the few large groups (the
 // diagonal and the single excitations) are summed by the whole warp at once, lanes over terms
 // with a TwoSum butterfly.
-template <bool COMP, bool IMAG>
-__device__ __forceinline__ void sweep_pair_sum(uint64_t x, uint64_t mg, bool has_imag, const uint4* tp,
+template <bool COMP, bool IMAG, class BT>
+__device__ __forceinline__ void sweep_pair_sum(const BT& x, const BT& mg, bool has_imag, const uint4* tp,
                                                uint32_t a0, uint32_t a1, uint32_t step, float& re,
                                                float& re_e, float& im, float& im_e) {
-    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
-    for (uint32_t k = a0; k < a1; k += step) add_term<COMP, IMAG>(xl, xh, mg, has_imag, tp[k], re, re_e, im, im_e);
+    for (uint32_t k = a0; k < a1; k += step) add_term<COMP, IMAG>(x, mg, has_imag, tp, k, re, re_e, im, im_e);
 }
 
-template <bool COMP, bool IMAG>
+template <bool COMP, bool IMAG, class BT>
 __global__ void __launch_bounds__(SWEEP_GT)
-sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bits, int64_t B,
+sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int64_t B,
                   const int64_t* __restrict__ off, int64_t ntiles, const uint32_t* __restrict__ valid,
-                  uint64_t* __restrict__ xprime, float4* __restrict__ S, int* __restrict__ status) {
+                  BT* __restrict__ xprime, float4* __restrict__ S, int* __restrict__ status) {
+    constexpr int REC = rec_of<BT>();                   // uint4 per term record
+    constexpr uint32_t STAGE = SWEEP_STAGE / REC;       // terms that fit the staging buffer
     extern __shared__ __align__(128) unsigned char sweep_smem[];
     uint4* ts = reinterpret_cast<uint4*>(sweep_smem);                         // staged term records
-    __shared__ uint64_t xs[SWEEP_SB];
+    __shared__ BT xs[SWEEP_SB];
     __shared__ int64_t obase[SWEEP_SB];
     __shared__ uint32_t vb[SWEEP_NW * SWEEP_SB];       // validity words [warp][sample]
     __shared__ uint32_t lmask[SWEEP_NW];               // large groups of each group word
     __shared__ uint32_t queue[SWEEP_NW][64];           // pending small pairs: rank | group << 8 | sample << 16
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint64_t g_mask[SWEEP_GT];              // the tile's groups: flip mask, meta, term range
+    __shared__ BT g_mask[SWEEP_GT];                    // the tile's groups: flip mask, meta, term range
     __shared__ uint32_t g_meta[SWEEP_GT], g_k0[SWEEP_GT], g_k1[SWEEP_GT];
 
     const int tile = blockIdx.y;
@@ -189,24 +242,25 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
     const int64_t g = g0 + threadIdx.x;
     const bool live = g < h.G;
     const int64_t g_end = g0 + SWEEP_GT < h.G ? g0 + SWEEP_GT : h.G;
-    // the tile's term range (16-byte records: every range is a valid bulk copy)
+    // the tile's term range (16- or 32-byte records: every range is a valid bulk copy)
     const uint32_t t0 = h.grp_off[g0];
     const uint32_t t1 = h.grp_off[g_end];
-    const bool staged = t1 - t0 <= (uint32_t)SWEEP_STAGE;
+    const bool staged = t1 - t0 <= STAGE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0 && staged) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const uint32_t bytes = (t1 - t0) * 16u;
+        const uint32_t bytes = (t1 - t0) * 16u * REC;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                      ::"r"(smem_u32(&bar)), "r"(bytes) : "memory");
         if (bytes)
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(ts)), "l"(h.term + t0), "r"(bytes), "r"(smem_u32(&bar)) : "memory");
+                         ::"r"(smem_u32(ts)), "l"(h.term + (size_t)t0 * REC), "r"(bytes), "r"(smem_u32(&bar))
+                         : "memory");
     }
     const uint32_t k0 = live ? h.grp_off[g] : 0, k1 = live ? h.grp_off[g + 1] : 0;
-    g_mask[threadIdx.x] = live ? h.grp_mask[g] : 0;
+    g_mask[threadIdx.x] = live ? reinterpret_cast<const BT*>(h.grp_mask)[g] : bits_zero<BT>();
     g_meta[threadIdx.x] = live ? h.grp_meta[g] : 0;
     g_k0[threadIdx.x] = k0 - t0;                       // term indices relative to the tile's range
     g_k1[threadIdx.x] = k1 - t0;
@@ -230,7 +284,7 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
         mbar_wait_bounded(&bar, 0);
         return;
     }
-    const uint4* tp = staged ? ts : h.term + t0;
+    const uint4* tp = staged ? ts : h.term + (size_t)t0 * REC;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t* q = queue[warp];
     int qn = 0;
@@ -239,7 +293,7 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
         if (lane < count) {
             const uint32_t e = q[lane];
             const int s = (int)(e >> 16), gl = (int)((e >> 8) & 0xffu);
-            const uint64_t x = xs[s], mg = g_mask[gl];
+            const BT x = xs[s], mg = g_mask[gl];
             float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
             sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl], g_k1[gl], 1u, re,
                                        re_e, im, im_e);
@@ -249,7 +303,7 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
         }
     };
     for (int s = warp; s < nb; s += SWEEP_NW) {
-        const uint64_t x = xs[s];
+        const BT x = xs[s];
         int run = 0;
 #pragma unroll 1
         for (int j = 0; j < SWEEP_NW; ++j) {
@@ -263,7 +317,7 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const uint64_t* __restrict__ bit
             // large groups: the whole warp per pair
             for (uint32_t big = bal & lm; big; big &= big - 1u) {
                 const int b = __ffs(big) - 1, gl = 32 * j + b;
-                const uint64_t mg = g_mask[gl];
+                const BT mg = g_mask[gl];
                 float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
                 sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl] + lane, g_k1[gl],
                                            32u, re, re_e, im, im_e);
@@ -334,12 +388,48 @@ int64_t sweep_valid_words(const HamDev& h, int64_t B) {
     return std::max<int64_t>(1, (B + SWEEP_SB - 1) / SWEEP_SB) * sweep_tiles(h) * SWEEP_GT;
 }
 
+// Bits of one configuration: `words` uint64 (HamDev::words); the kernels take them as uint64_t
+// or U128.
 int launch_sweep_count(const HamDev& h, int n_up, int n_dn, const uint64_t* bits,
                        int64_t B, int32_t* cnt, uint32_t* valid, cudaStream_t s) {
     if (B <= 0) return NQS_OK;
     const int64_t T = sweep_tiles(h);
     dim3 grid((unsigned)((B + SWEEP_SB - 1) / SWEEP_SB), (unsigned)T);
-    sweep_count_kernel<<<grid, SWEEP_GT, 0, s>>>(h, n_up, n_dn, bits, B, cnt, T, valid);
+    if (h.words == 2)
+        sweep_count_kernel<U128><<<grid, SWEEP_GT, 0, s>>>(h, n_up, n_dn, reinterpret_cast<const U128*>(bits), B, cnt, T,
+                                                           valid);
+    else
+        sweep_count_kernel<uint64_t><<<grid, SWEEP_GT, 0, s>>>(h, n_up, n_dn, bits, B, cnt, T, valid);
+    NQS_LAUNCHED();
+    return NQS_OK;
+}
+
+template <class BT>
+static int sweep_emit_as(const HamDev& h, int n_up, int n_dn, int compensated, const uint64_t* bits, int64_t B,
+                         const int64_t* off, const uint32_t* valid, uint64_t* xprime, float4* S, cudaStream_t s) {
+    const int64_t T = sweep_tiles(h);
+    dim3 grid((unsigned)((B + SWEEP_SB - 1) / SWEEP_SB), (unsigned)T);
+    constexpr size_t smem = (size_t)SWEEP_STAGE * 16;
+    static int attr_dev = -1;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true, false, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false, false, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true, true, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false, true, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_dev = dev;
+    }
+    int* status = nullptr;
+    NQS_TRY(device_status_ptr(&status));
+    const BT* b = reinterpret_cast<const BT*>(bits);
+    BT* xp = reinterpret_cast<BT*>(xprime);
+    auto go = [&](auto kernel) { kernel<<<grid, SWEEP_GT, smem, s>>>(h, n_up, n_dn, b, B, off, T, valid, xp, S, status); };
+    if (h.any_imag) {
+        if (compensated) go(sweep_emit_kernel<true, true, BT>); else go(sweep_emit_kernel<false, true, BT>);
+    } else {
+        if (compensated) go(sweep_emit_kernel<true, false, BT>); else go(sweep_emit_kernel<false, false, BT>);
+    }
     NQS_LAUNCHED();
     return NQS_OK;
 }
@@ -348,29 +438,8 @@ int launch_sweep_emit(const HamDev& h, int n_up, int n_dn, int compensated,
                       const uint64_t* bits, int64_t B, const int64_t* off, const uint32_t* valid,
                       uint64_t* xprime, float4* S, cudaStream_t s) {
     if (B <= 0) return NQS_OK;
-    const int64_t T = sweep_tiles(h);
-    dim3 grid((unsigned)((B + SWEEP_SB - 1) / SWEEP_SB), (unsigned)T);
-    constexpr size_t smem = (size_t)SWEEP_STAGE * 16;
-    static int attr_dev = -1;
-    int dev = 0;
-    NQS_CK(cudaGetDevice(&dev));
-    if (attr_dev != dev) {
-        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NQS_CK(cudaFuncSetAttribute(sweep_emit_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_dev = dev;
-    }
-    int* status = nullptr;
-    NQS_TRY(device_status_ptr(&status));
-    auto go = [&](auto kernel) { kernel<<<grid, SWEEP_GT, smem, s>>>(h, n_up, n_dn, bits, B, off, T, valid, xprime, S, status); };
-    if (h.any_imag) {
-        if (compensated) go(sweep_emit_kernel<true, true>); else go(sweep_emit_kernel<false, true>);
-    } else {
-        if (compensated) go(sweep_emit_kernel<true, false>); else go(sweep_emit_kernel<false, false>);
-    }
-    NQS_LAUNCHED();
-    return NQS_OK;
+    if (h.words == 2) return sweep_emit_as<U128>(h, n_up, n_dn, compensated, bits, B, off, valid, xprime, S, s);
+    return sweep_emit_as<uint64_t>(h, n_up, n_dn, compensated, bits, B, off, valid, xprime, S, s);
 }
 
 int launch_unpack_rows(const int64_t* off, int64_t ntiles, int64_t B, const float4* S,

@@ -8,12 +8,12 @@ what it produces.
 """
 from .rng import SplitMix64
 from .configs import CONFIGS, WorkloadConfig, get_config
-from .hamiltonian import integrals, jordan_wigner, hamiltonian_for
+from .hamiltonian import integrals, jordan_wigner, hamiltonian_for, jordan_wigner_words, hamiltonian_words_for
 from .params import init_params, param_shapes, default_order, hf_occupied
-from .samples import random_sector_bits
+from .samples import random_sector_bits, random_sector_bits_words
 
 __all__ = [
     "SplitMix64", "CONFIGS", "WorkloadConfig", "get_config", "integrals", "jordan_wigner",
     "hamiltonian_for", "init_params", "param_shapes", "default_order", "hf_occupied",
-    "random_sector_bits",
+    "random_sector_bits", "jordan_wigner_words", "hamiltonian_words_for", "random_sector_bits_words",
 ]

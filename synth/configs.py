@@ -1,4 +1,4 @@
-"""The five named synthetic workloads (molecule-shaped stand-ins for the paper's Table 1 systems).
+"""The named synthetic workloads (molecule-shaped stand-ins for the paper's Table 1 systems).
 
 Each workload fixes the spatial-orbital count, the electron split, the integral generator's
 symmetry and decay options, the model and the nominal sample count.  Seeds: integrals 1000+id,
@@ -50,6 +50,9 @@ CONFIGS = {
                       ("fp32", "bf16")),
     5: WorkloadConfig(5, "large_52q_tf128x4", 26, 8, 8, 0, True, "transformer", 128, 4, 8, 1 << 18, 16,
                       ("fp32", "bf16")),
+    # two-word registers (64 < n <= 128): the paper's largest system has 76 qubits (Table 1);
+    # the term sweep and the MADE local energy run on seeded in-sector configurations
+    6: WorkloadConfig(6, "wide_76q_made2x64", 38, 8, 8, 2, True, "made", 64, 2, 0, 1 << 14, 1, ("fp32",)),
 }
 
 

@@ -41,9 +41,18 @@ def test_status_strings(lib):
 
 
 def test_ham_create_validation_errors(lib):
+    import ctypes
+    m = np.zeros(3, dtype=np.uint64)
+    c = np.ones(1)
+    h = ctypes.c_void_p()
+    # more than 128 qubits (three words) is out of range
+    assert lib._lib.nqs_ham_create(129, 1, m.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p),
+                                   c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)) == lib.NQS_ERR_NQUBITS
+    with pytest.raises(ValueError):
+        lib.Hamiltonian(65, [0], [0], [1.0])          # 65 qubits need [K, 2] masks
     with pytest.raises(lib.NQSError) as e:
-        lib.Hamiltonian(65, [0], [0], [1.0])
-    assert e.value.status == lib.NQS_ERR_NQUBITS
+        lib.Hamiltonian(66, [[0, 1 << 2]], [[0, 0]], [1.0])   # qubit 66 of a 66-qubit register
+    assert e.value.status == lib.NQS_ERR_INVALID_ARG
     with pytest.raises(lib.NQSError) as e:
         lib.Hamiltonian(4, [1 << 4], [0], [1.0])
     assert e.value.status == lib.NQS_ERR_INVALID_ARG
