@@ -35,8 +35,12 @@ import synth  # noqa: E402
 DEFAULT_WORKLOAD = 5
 
 # DRAM bytes (read + write) per algorithmic byte of a scope's launch, from one ncu capture of the
-# same kernel on the same workload shape (the list is emptied for a kernel when it changes).
-NCU_TRAFFIC = {}
+# same kernel on the same workload shape (an entry is removed when its kernel changes).
+NCU_TRAFFIC = {
+    ("large_52q_tf128x4", "bf16", "tf_mlp"): 0.98,
+    ("large_52q_tf128x4", "bf16", "tf_gemm"): 1.0,
+    ("large_52q_tf128x4", "bf16", "tf_layernorm"): 0.91,
+}
 
 # The library's profiled scopes that record their algorithmic FLOPs and compulsory bytes, with
 # the kernels behind each (bf16 form, fp32 form).

@@ -223,7 +223,7 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
                   const int64_t* __restrict__ off, int64_t ntiles, const uint32_t* __restrict__ valid,
                   BT* __restrict__ xprime, float4* __restrict__ S, int* __restrict__ status) {
     constexpr int REC = rec_of<BT>();                   // uint4 per term record
-    constexpr uint32_t STAGE = SWEEP_STAGE / REC;       // terms that fit the staging buffer
+    constexpr uint32_t STAGE = SWEEP_STAGE;             // terms that fit the staging buffer
     extern __shared__ __align__(128) unsigned char sweep_smem[];
     uint4* ts = reinterpret_cast<uint4*>(sweep_smem);                         // staged term records
     __shared__ BT xs[SWEEP_SB];
@@ -409,7 +409,7 @@ static int sweep_emit_as(const HamDev& h, int n_up, int n_dn, int compensated, c
                          const int64_t* off, const uint32_t* valid, uint64_t* xprime, float4* S, cudaStream_t s) {
     const int64_t T = sweep_tiles(h);
     dim3 grid((unsigned)((B + SWEEP_SB - 1) / SWEEP_SB), (unsigned)T);
-    constexpr size_t smem = (size_t)SWEEP_STAGE * 16;
+    constexpr size_t smem = (size_t)SWEEP_STAGE * 16 * rec_of<BT>();   // 32 KB (one word) or 64 KB (two)
     static int attr_dev = -1;
     int dev = 0;
     NQS_CK(cudaGetDevice(&dev));
