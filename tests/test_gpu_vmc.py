@@ -182,3 +182,36 @@ def test_two_phase_backward_equals_one_call(precision):
     assert torch.equal(sa, sb)
     assert torch.equal(ga_, gb)
     assert torch.equal(pa, pb)
+
+
+@pytest.mark.parametrize("cid", [2, 3])
+def test_data_parallel_gradient_form_on_one_rank(cid):
+    # the data-parallel form of the gradient (nqs_energy_sums, the two backward sums, the
+    # combination of paper_2208_05637_b300.parallel with no process group: one rank) equals the
+    # single-process gradient of the same samples and the oracle's Eq. grad
+    P = lib()
+    cfg = synth.get_config(cid)
+    xm, zm, coef = synth.hamiltonian_for(cfg)
+    ham = P.Hamiltonian(cfg.n_qubits, xm, zm, coef)
+    prec = "bf16" if cfg.arch == "transformer" else "fp32"
+    m, _ = gpu_model(cfg, beta=1.0, precision=prec)
+    p0 = m.params.detach().clone()
+    cap = {2: 512, 3: 64}[cid]
+    vmc = P.VMC(ham, m, p0.clone(), cfg.n_samples, max_unique=cap)
+    bits, counts, _ = P.nqs_sample(m, cfg.n_samples, cap, cfg.seed_sampler)
+    out = vmc.gradient(bits, counts)
+    g_single = vmc.params.grad.detach().clone()
+    U = bits.numel()
+    outp = vmc._gradient_parallel(bits, counts, out["eloc"], U, False)
+    g_par = vmc.params.grad.detach().clone()
+    # the two forms round differently (the data-parallel one subtracts 2 Re(E_bar) second from first,
+    # two fp32 backward sums that partly cancel): the FP32 gradient tolerance, 1e-4
+    assert rel_norm(g_par.cpu().numpy().astype(np.float64), g_single.cpu().numpy().astype(np.float64)) <= 1e-4
+    st1 = out["stats"].cpu().numpy(); st2 = outp["stats"].cpu().numpy()
+    assert abs(st1[0] - st2[0]) <= 1e-9 * abs(st1[0]) and abs(st1[1] - st2[1]) <= 1e-9 * max(1.0, abs(st1[0]))
+    assert abs(st1[2] - st2[2]) <= 1e-6 * abs(st1[2])
+    om, _ = oracle_model(cfg, beta=1.0, quant="bf16x2" if prec == "bf16" else None, requires_grad=True)
+    hb = bits.cpu().numpy().view(np.uint64)
+    hc = counts.cpu().numpy()
+    want = vmc_gradient(om, hb, hc, local_energy(om, xm, zm, coef, hb))
+    assert rel_norm(g_par.cpu().numpy().astype(np.float64), _flat(m, want)) <= (1e-3 if prec == "bf16" else 1e-4)
