@@ -7,10 +7,10 @@
  *  - A configuration (bitstring) or Pauli mask of n_qubits <= 64 is one uint64, qubit j in bit j;
  *    of 64 < n_qubits <= 128 it is W = 2 consecutive uint64 words, qubit j in bit j % 64 of word
  *    j / 64 (the paper reaches 76 qubits, Table 1).  Arrays of B configurations hold B * W words.
- *    Two-word registers are served by nqs_ham_*, nqs_term_sweep, nqs_logpsi and
- *    nqs_local_energy with the PRODUCT and MADE models; the transformer, nqs_sample,
- *    nqs_logpsi_backward and nqs_local_energy_noalloc take n_qubits <= 64 (NQS_ERR_NQUBITS
- *    otherwise).  Spin orbital j = 2p + s: even qubits are spin up (alpha), odd qubits spin down
+ *    Two-word registers are served by every call with the PRODUCT and MADE models (nqs_sample
+ *    then runs its steps as separate launches instead of a captured graph); the transformer and
+ *    nqs_local_energy_noalloc take n_qubits <= 64 (NQS_ERR_NQUBITS otherwise).  Spin orbital
+ *    j = 2p + s: even qubits are spin up (alpha), odd qubits spin down
  *    (beta) (Eq. hamming_weight_constraint).
  *  - A Pauli string is a pair of masks (x_mask, z_mask): qubit j carries I for (0,0), sigma_1
  *    for (1,0), sigma_3 for (0,1) and sigma_2 for (1,1) (Section 3, Eq. hamiltonpauli).

@@ -82,9 +82,14 @@ class Model:
 
     # ----------------------------------------------------------------- inputs
     def positions(self, bits) -> torch.Tensor:
-        """[B, n] float64 of x_{order[t]} in {0, 1}."""
-        b = np.asarray(bits, dtype=np.uint64)[:, None]
-        X = (b >> self.order.astype(np.uint64)[None, :]) & np.uint64(1)
+        """[B, n] float64 of x_{order[t]} in {0, 1}; bits uint64 [B] or, for registers of more
+        than 64 qubits, [B, W] words (qubit j in bit j % 64 of word j // 64)."""
+        b = np.asarray(bits, dtype=np.uint64)
+        q = self.order.astype(np.int64)
+        if b.ndim == 2:
+            X = (b[:, q // 64] >> (q % 64).astype(np.uint64)[None, :]) & np.uint64(1)
+        else:
+            X = (b[:, None] >> q.astype(np.uint64)[None, :]) & np.uint64(1)
         return torch.tensor(X.astype(np.float64))
 
     # ----------------------------------------------------------------- networks
@@ -193,7 +198,11 @@ class Model:
 
     def sampling_p(self, prefix_bits, k: int) -> np.ndarray:
         """pihat(x_{order[k]} = 1 | prefix) in FP64 for parents whose positions < k are set."""
-        X = self.positions(prefix_bits)
+        return self.sampling_p_positions(self.positions(prefix_bits), k)
+
+    def sampling_p_positions(self, X, k: int) -> np.ndarray:
+        """sampling_p from the parents' positions matrix X [B, n] (x_{order[t]} in {0, 1})."""
+        X = X.clone()
         X[:, k:] = 0.0
         with torch.no_grad():
             p = self.cond_p1(X)[:, k]

@@ -149,3 +149,59 @@ def group_terms_words(xm, zm, c, n: int) -> dict:
     return dict(group_mask=words(g_m), group_offset=np.array(g_off, dtype=np.int64),
                 group_n_alpha=np.array(g_na, dtype=np.int64), group_n_beta=np.array(g_nb, dtype=np.int64),
                 term_z=words(t_z), term_c_re=tc.real.copy(), term_c_im=tc.imag.copy())
+
+
+# ----------------------------------------------------------------------------- sampling
+def _order_words(bits):
+    """Indices that sort [U, W] configurations ascending as W-word integers (word W-1 most
+    significant)."""
+    bits = np.asarray(bits, dtype=np.uint64)
+    return np.lexsort([bits[:, w] for w in range(bits.shape[1])])
+
+
+def evict_words(bits, counts, max_unique: int):
+    """oracle.sampler.evict for [U, W] configurations: keep the max_unique highest counts, ties
+    broken by the configuration ascending; input and output in ascending order."""
+    bits = np.asarray(bits, dtype=np.uint64)
+    counts = np.asarray(counts, dtype=np.int64)
+    if len(bits) <= max_unique:
+        return bits, counts
+    keys = [bits[:, w] for w in range(bits.shape[1])] + [-counts]   # last key is primary
+    top = np.lexsort(keys)[:max_unique]
+    top = top[_order_words(bits[top])]
+    return bits[top], counts[top]
+
+
+def sample_words(p_fn, n: int, order, n_samples: int, max_unique: int, seed: int, trace=None):
+    """oracle.sampler.sample for registers of W = ceil(n / 64) words: the same buffer sampler
+    (Section 4, Sampling) with the same Philox draws over the nominal indices in ascending
+    configuration order; p_fn(parent_bits [U, W], k) -> fp32 probabilities.  Returns
+    (bits uint64 [U, W], counts int64 [U]) ascending."""
+    from .sampler import bernoulli_ones, threshold
+    W = words_of(n)
+    bits = np.zeros((1, W), dtype=np.uint64)
+    counts = np.array([n_samples], dtype=np.int64)
+    for k in range(n):
+        q = int(order[k])
+        p32 = np.asarray(p_fn(bits, k), dtype=np.float32)
+        if trace is not None:
+            trace.append((bits.copy(), counts.copy(), p32.copy()))
+        n1 = bernoulli_ones(counts, threshold(p32), k, seed)
+        ones = bits.copy()
+        ones[:, q // 64] |= np.uint64(1) << np.uint64(q % 64)
+        cb = np.concatenate([bits, ones])
+        cc = np.concatenate([counts - n1, n1])
+        keep = cc > 0
+        cb, cc = cb[keep], cc[keep]
+        idx = _order_words(cb)
+        bits, counts = evict_words(cb[idx], cc[idx], max_unique)
+    return bits, counts
+
+
+def model_p_fn_words(model):
+    """p_fn of sample_words backed by an oracle Model: FP64 conditional with the constraint,
+    cast to fp32."""
+    def fn(parent_bits, k):
+        X = bits_of_words(parent_bits, model.n)[:, model.order]
+        return model.sampling_p_positions(torch.tensor(X.astype(np.float64)), k).astype(np.float32)
+    return fn

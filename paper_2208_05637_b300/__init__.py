@@ -299,7 +299,8 @@ def nqs_sample(model, n_samples, max_unique, seed, ws=None, trace=False, stream=
     import torch
     ws = model.workspace(OP_SAMPLE, n_samples) if ws is None else ws
     cap = int(min(n_samples, 2 * max_unique))
-    bits = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+    W = words_of(model.n_qubits)
+    bits = torch.empty((max(cap, 1),) if W == 1 else (max(cap, 1), W), dtype=torch.int64, device="cuda")
     counts = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
     ptrace = torch.zeros((model.n_qubits, cap), dtype=torch.float32, device="cuda") if trace else None
     nu = _I64()
@@ -382,7 +383,7 @@ def nqs_gemm_bf16(A, W, bias, C, epilogue=0, stream=None):
 
 
 def nqs_logpsi_backward(model, bits, g_log_abs, g_phase, grad_accum, ws=None, stream=None):
-    B = bits.numel()
+    B = _nconf(bits)
     ws = model.workspace(OP_BACKWARD, B) if ws is None else ws
     wp, wn = _ws(ws)
     _check(_lib.nqs_logpsi_backward(model.handle, _ptr(bits), B, _ptr(g_log_abs), _ptr(g_phase),
@@ -394,7 +395,7 @@ def nqs_logpsi_backward_phase(model, phase, bits, g_log_abs=None, g_phase=None, 
                               stream=None):
     """nqs_logpsi_backward in two calls: phase 1 recomputes the forward (bits only), phase 2 runs
     the backward from it with the same bits and workspace."""
-    B = bits.numel()
+    B = _nconf(bits)
     ws = model.workspace(OP_BACKWARD, B) if ws is None else ws
     wp, wn = _ws(ws)
     _check(_lib.nqs_logpsi_backward_phase(model.handle, int(phase), _ptr(bits), B, _ptr(g_log_abs), _ptr(g_phase),

@@ -615,7 +615,7 @@ int nqs_workspace_size(nqs_model_t m, nqs_ham_t h, int op, int64_t batch, size_t
     switch (op) {
         case NQS_OP_SAMPLE: {
             SamplerBufs b;
-            NQS_TRY(sampler_layout(c, std::max<int64_t>(batch, 1), std::max<int64_t>(batch, 1), b));
+            NQS_TRY(sampler_layout(c, std::max<int64_t>(batch, 1), std::max<int64_t>(batch, 1), b, words_of(m->mc.n)));
             if (m->mc.arch == NQS_ARCH_TRANSFORMER) {
                 TfBufs tb;
                 tf_layout(c, m->mc, std::min(b.cap, tf_seq_capacity(m->mc)), tb);
@@ -678,7 +678,6 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
                uint64_t* bits_out, int64_t* counts_out, int64_t capacity, int64_t* n_unique,
                float* p_trace, int64_t trace_stride, void* ws, size_t ws_bytes, void* stream) {
     NQS_TRY(need_params(m));
-    if (m->mc.n > 64) { set_error("the sampler supports n_qubits <= 64"); return NQS_ERR_NQUBITS; }
     if (n_samples < 1 || n_samples >= (1ll << 31) || max_unique < 1 || !n_unique || capacity < 0) {
         set_error("need 1 <= n_samples < 2^31, max_unique >= 1, n_unique non-NULL");
         return NQS_ERR_INVALID_ARG;
@@ -687,7 +686,7 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     SamplerBufs b;
-    NQS_TRY(sampler_layout(c, n_samples, max_unique, b));
+    NQS_TRY(sampler_layout(c, n_samples, max_unique, b, words_of(m->mc.n)));
     if (p_trace && trace_stride < b.cap) {
         set_error("trace_stride must be >= min(n_samples, 2*max_unique)");
         return NQS_ERR_INVALID_ARG;
@@ -726,7 +725,8 @@ int nqs_sample(nqs_model_t m, int64_t n_samples, int64_t max_unique, uint64_t se
         }
     }
     int64_t U = 0;
-    const bool graphable = b.cap <= SAMPLER_GRAPH_MAX_CAP;
+    // captured and replayed as a graph: one-word buffers within the one-CTA bookkeeping's size
+    const bool graphable = b.cap <= SAMPLER_GRAPH_MAX_CAP && b.words == 1;
     SamplerGraph& G = m->graph;
     const bool same = G.n_samples == n_samples && G.max_unique == max_unique && G.ws == ws &&
                       G.trace == p_trace && G.trace_stride == trace_stride && G.params == m->d_params &&
@@ -953,7 +953,6 @@ int nqs_logpsi_backward(nqs_model_t m, const uint64_t* bits, int64_t B, const fl
                         void* stream) {
     NQS_TRY(need_params(m));
     if (B < 0) return NQS_ERR_INVALID_ARG;
-    if (m->mc.n > 64) { set_error("the log psi backward supports n_qubits <= 64"); return NQS_ERR_NQUBITS; }
     if (B == 0) return NQS_OK;
     if (!bits || !g_abs || !g_phase || !grad) { set_error("null pointer argument"); return NQS_ERR_INVALID_ARG; }
     cudaStream_t s = (cudaStream_t)stream;

@@ -231,7 +231,8 @@ struct MadeRow {
     }
 
     // unconstrained pi(x_{order[k]} = 1 | prefix) for prefix position bits xo (positions < k)
-    __device__ static float p1(const float* sm, const ModelConst& mc, uint64_t xo, int k) {
+    template <class PB>
+    __device__ static float p1(const float* sm, const ModelConst& mc, const PB& xo, int k) {
         const MadeLay L = made_layout(mc, H);
         float h[H];
         hidden(sm, L, mc, xo, h);
@@ -267,7 +268,8 @@ struct ProductRow {
         la = bad ? -INFINITY : 0.5f * (acc + err);
         ph = 0.f;
     }
-    __device__ static float p1(const float* sm, const ModelConst&, uint64_t, int k) { return sm[k]; }
+    template <class PB>
+    __device__ static float p1(const float* sm, const ModelConst&, const PB&, int k) { return sm[k]; }
 };
 
 // ------------------------------------------------------------------ kernels
@@ -350,10 +352,10 @@ eloc_rows_kernel(ModelConst mc, const float* __restrict__ P, const BT* __restric
 
 // Sampler conditional at step k for each parent prefix: constrained pihat, its 2^32 threshold,
 // and a reset of the per-parent ones counter.
-template <class R>
+template <class R, class BT>
 __global__ void __launch_bounds__(128)
 cond_rows_kernel(ModelConst mc, const float* __restrict__ P, int k,
-                 const uint64_t* __restrict__ bits, const int64_t* __restrict__ Udev,
+                 const BT* __restrict__ bits, const int64_t* __restrict__ Udev,
                  float* __restrict__ p_out, uint64_t* __restrict__ thr, float* __restrict__ trace) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
@@ -362,7 +364,7 @@ cond_rows_kernel(ModelConst mc, const float* __restrict__ P, int k,
     const int64_t U = *Udev;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < U;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t xo = to_positions(bits[s], mc, k);
+        const BT xo = to_positions(bits[s], mc, k);
         int ones0 = 0, ones1 = 0;
         for (int t = 0; t < k; ++t) {
             const int b = qbit(xo, t);
@@ -400,9 +402,9 @@ __host__ __device__ inline ActLay act_layout(const ModelConst& mc) {
     return a;
 }
 
-template <int H>
+template <int H, class BT>
 __global__ void __launch_bounds__(128)
-made_backward_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t* __restrict__ bits,
+made_backward_kernel(ModelConst mc, const float* __restrict__ P, const BT* __restrict__ bits,
                      int64_t B, const float* __restrict__ g_abs, const float* __restrict__ g_phase,
                      float* __restrict__ acts, int64_t ld) {
     extern __shared__ float4 smem4[];
@@ -415,8 +417,8 @@ made_backward_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t*
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B;
          i += (int64_t)gridDim.x * blockDim.x) {
         float* row = acts + i * ld;
-        const uint64_t xo = to_positions(bits[i], mc, n);
-        for (int t = 0; t < n; ++t) row[A.u + t] = ((xo >> t) & 1ull) ? 1.f : -1.f;
+        const BT xo = to_positions(bits[i], mc, n);
+        for (int t = 0; t < n; ++t) row[A.u + t] = qbit(xo, t) ? 1.f : -1.f;
         // forward, storing every hidden layer (outer loops over units stay rolled; the
         // inner loops over the previous layer are unrolled against register arrays)
         float h[H];
@@ -504,7 +506,7 @@ made_backward_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t*
         const float gp = g_phase[i];
         float hp[H];
         MadeRow<H>::phase(sm, L, mc, xo, hp);
-        const int sel = (int)(((xo >> (n - 2)) & 1ull) * 2 + ((xo >> (n - 1)) & 1ull));
+        const int sel = qbit(xo, n - 2) * 2 + qbit(xo, n - 1);
         for (int j = 0; j < 4; ++j) row[A.dpo + j] = j == sel ? gp : 0.f;
 #pragma unroll
         for (int k = 0; k < H; ++k) {
@@ -516,8 +518,9 @@ made_backward_kernel(ModelConst mc, const float* __restrict__ P, const uint64_t*
     }
 }
 
+template <class BT>
 __global__ void product_backward_kernel(ModelConst mc, const float* __restrict__ P,
-                                        const uint64_t* __restrict__ bits, int64_t B,
+                                        const BT* __restrict__ bits, int64_t B,
                                         const float* __restrict__ g_abs, float* __restrict__ grad) {
     __shared__ float red[256];
     const int t = blockIdx.x;   // position
@@ -526,10 +529,10 @@ __global__ void product_backward_kernel(ModelConst mc, const float* __restrict__
     const int need = sp ? mc.n_dn : mc.n_up;
     float acc = 0.f;
     for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
-        const uint64_t x = bits[i];
+        const BT x = bits[i];
         int c = 0;
         for (int u = 0; u < t; ++u)
-            if ((mc.order[u] & 1) == sp) c += (int)((x >> mc.order[u]) & 1ull);
+            if ((mc.order[u] & 1) == sp) c += qbit(x, mc.order[u]);
         if (!(c + mc.after[t] < need) && !(c >= need)) {
             const int b = qbit(x, mc.order[t]);
             acc += 0.5f * g_abs[i] * (b ? 1.f / p : -1.f / (1.f - p));
@@ -616,8 +619,14 @@ int launch_cond_rows(const ModelConst& mc, const float* P, int k, const uint64_t
     return with_row_model(mc, [&](auto row) -> int {
         using R = decltype(row);
         const size_t sm = R::smem_bytes(mc);
-        NQS_TRY(prep_smem(cond_rows_kernel<R>, sm));
-        cond_rows_kernel<R><<<grid_for(cap, 128), 128, sm, s>>>(mc, P, k, bits, U, p_out, thr, trace);
+        if (words_of(mc.n) == 2) {
+            NQS_TRY(prep_smem(cond_rows_kernel<R, U128>, sm));
+            cond_rows_kernel<R, U128><<<grid_for(cap, 128), 128, sm, s>>>(mc, P, k, reinterpret_cast<const U128*>(bits), U,
+                                                                           p_out, thr, trace);
+        } else {
+            NQS_TRY(prep_smem(cond_rows_kernel<R, uint64_t>, sm));
+            cond_rows_kernel<R, uint64_t><<<grid_for(cap, 128), 128, sm, s>>>(mc, P, k, bits, U, p_out, thr, trace);
+        }
         NQS_LAUNCHED();
         return NQS_OK;
     });
@@ -628,14 +637,19 @@ int64_t made_act_stride(const ModelConst& mc) { return act_layout(mc).ld; }
 int launch_made_backward(const ModelConst& mc, const float* P, const uint64_t* bits, int64_t B,
                          const float* g_abs, const float* g_phase, float* acts, int64_t ld,
                          cudaStream_t s) {
-    auto go = [&](auto kernel, size_t sm) -> int {
+    auto go = [&](auto kernel, auto b, size_t sm) -> int {
         NQS_TRY(prep_smem(kernel, sm));
-        kernel<<<grid_for(B, 128), 128, sm, s>>>(mc, P, bits, B, g_abs, g_phase, acts, ld);
+        kernel<<<grid_for(B, 128), 128, sm, s>>>(mc, P, b, B, g_abs, g_phase, acts, ld);
         NQS_LAUNCHED();
         return NQS_OK;
     };
-    if (mc.hidden <= 16) return go(made_backward_kernel<16>, MadeRow<16>::smem_bytes(mc));
-    return go(made_backward_kernel<64>, MadeRow<64>::smem_bytes(mc));
+    const U128* b2 = reinterpret_cast<const U128*>(bits);
+    if (words_of(mc.n) == 2) {
+        if (mc.hidden <= 16) return go(made_backward_kernel<16, U128>, b2, MadeRow<16>::smem_bytes(mc));
+        return go(made_backward_kernel<64, U128>, b2, MadeRow<64>::smem_bytes(mc));
+    }
+    if (mc.hidden <= 16) return go(made_backward_kernel<16, uint64_t>, bits, MadeRow<16>::smem_bytes(mc));
+    return go(made_backward_kernel<64, uint64_t>, bits, MadeRow<64>::smem_bytes(mc));
 }
 
 int made_grad_reduce(const ModelConst& mc, const float* acts, int64_t ld, int64_t B, float* grad,
@@ -659,7 +673,10 @@ int made_grad_reduce(const ModelConst& mc, const float* acts, int64_t ld, int64_
 int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t* bits,
                             int64_t B, const float* g_abs, float* grad, cudaStream_t s) {
     ProfScope ps("product_backward", s);
-    product_backward_kernel<<<mc.n, 256, 0, s>>>(mc, P, bits, B, g_abs, grad);
+    if (words_of(mc.n) == 2)
+        product_backward_kernel<U128><<<mc.n, 256, 0, s>>>(mc, P, reinterpret_cast<const U128*>(bits), B, g_abs, grad);
+    else
+        product_backward_kernel<uint64_t><<<mc.n, 256, 0, s>>>(mc, P, bits, B, g_abs, grad);
     NQS_LAUNCHED();
     return NQS_OK;
 }

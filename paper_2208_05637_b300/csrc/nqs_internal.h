@@ -69,6 +69,7 @@ __host__ __device__ __forceinline__ bool operator!=(const U128& a, const U128& b
 __host__ __device__ __forceinline__ bool operator<(const U128& a, const U128& b) {
     return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo;
 }
+__host__ __device__ __forceinline__ bool operator<=(const U128& a, const U128& b) { return !(b < a); }
 // bit q of a configuration
 __host__ __device__ __forceinline__ int qbit(uint64_t x, int q) { return (int)((x >> q) & 1ull); }
 __host__ __device__ __forceinline__ int qbit(const U128& x, int q) {
@@ -473,7 +474,7 @@ struct TfCtx {
 
 // sampler (sampler.cu)
 struct SamplerBufs {
-    uint64_t *bitsA, *bitsB;
+    uint64_t *bitsA, *bitsB;   // cap configurations of `words` uint64 each
     int64_t *cntA, *cntB;
     int64_t* start;      // cap+1
     int64_t* n1;         // cap
@@ -485,6 +486,7 @@ struct SamplerBufs {
     int64_t* pos1;       // cap+1
     int64_t* U;          // device scalars: U[0] current U
     int64_t cap;
+    int words = 1;       // uint64 words per configuration
     // incremental transformer forward (all null when the conditionals are recomputed from
     // scratch at every step): QKV slabs, ancestor tables (ping-pong), parent slots
     float* kv = nullptr;
@@ -551,7 +553,7 @@ int dedup_contrib(const uint64_t* xp, const int64_t* rows_dev, int64_t rows_max,
 
 // Binds the model-owned cache memory (tf_step_cache_bytes(mc, b.cap) bytes) to b.
 void sampler_bind_cache(SamplerBufs& b, const ModelConst& mc, void* mem);
-int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b);
+int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b, int words = 1);
 int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t max_unique,
                 uint64_t seed, SamplerBufs& b, float* trace, int64_t trace_stride,
                 const TfCtx* tf, bool fixed_rows, cudaStream_t s);

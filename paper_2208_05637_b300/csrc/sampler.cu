@@ -37,9 +37,10 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
 
 // U[0] = unique count, U[2] = eviction flag, U[3] = seed (read by the draws, so that a
 // captured graph of the steps can be replayed with a new seed)
-__global__ void init_kernel(uint64_t* bits, int64_t* cnt, int64_t* U, int64_t n_samples, uint64_t seed,
+template <class BT>
+__global__ void init_kernel(BT* bits, int64_t* cnt, int64_t* U, int64_t n_samples, uint64_t seed,
                             int64_t* start, int64_t* n1) {
-    bits[0] = 0;
+    bits[0] = bits_zero<BT>();
     cnt[0] = n_samples;
     U[0] = 1;
     U[3] = (int64_t)seed;
@@ -108,7 +109,8 @@ __global__ void flags_kernel(const int64_t* __restrict__ cnt, const int64_t* __r
 }
 
 // first index in [0, U) whose key exceeds v, where key(s) = bits[s] | orbit (monotone in s)
-__device__ __forceinline__ int64_t upper(const uint64_t* bits, int64_t U, uint64_t orbit, uint64_t v) {
+template <class BT>
+__device__ __forceinline__ int64_t upper(const BT* bits, int64_t U, BT orbit, BT v) {
     int64_t lo = 0, hi = U;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -117,10 +119,11 @@ __device__ __forceinline__ int64_t upper(const uint64_t* bits, int64_t U, uint64
     return lo;
 }
 
-__global__ void merge_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
+template <class BT>
+__global__ void merge_kernel(const BT* __restrict__ bits, const int64_t* __restrict__ cnt,
                              const int64_t* __restrict__ n1, const int64_t* __restrict__ pos0,
                              const int64_t* __restrict__ pos1, int64_t* __restrict__ Udev,
-                             uint64_t qbit, uint64_t* __restrict__ nbits, int64_t* __restrict__ ncnt,
+                             BT qbit, BT* __restrict__ nbits, int64_t* __restrict__ ncnt,
                              int32_t* __restrict__ npar) {
     const int64_t U = *Udev;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < U; s += (int64_t)gridDim.x * blockDim.x) {
@@ -133,8 +136,8 @@ __global__ void merge_kernel(const uint64_t* __restrict__ bits, const int64_t* _
             if (npar) npar[pos0[s] + r] = (int32_t)s;
         }
         if (c1 > 0) {
-            const uint64_t key = bits[s] | qbit;
-            const int64_t r = pos0[upper(bits, U, 0, key)];
+            const BT key = bits[s] | qbit;
+            const int64_t r = pos0[upper(bits, U, bits_zero<BT>(), key)];
             nbits[pos1[s] + r] = key;
             ncnt[pos1[s] + r] = c1;
             if (npar) npar[pos1[s] + r] = (int32_t)s;
@@ -150,9 +153,10 @@ __global__ void set_u_kernel(int64_t* Udev, const int64_t* pos0, const int64_t* 
 // Keep the top max_unique of the U entries (bits, cnt[, par]) by (count desc, bits asc) into
 // (obits, ocnt[, opar]) with their order preserved; one CTA of 1024 threads, U > max_unique.
 // scnt, when given, holds the U counts (as uint32) in shared memory and replaces the reads of cnt.
-__device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
+template <class BT>
+__device__ void evict_block(const BT* __restrict__ bits, const int64_t* __restrict__ cnt,
                             const int32_t* __restrict__ par, int64_t U, int64_t max_unique,
-                            uint64_t* __restrict__ obits, int64_t* __restrict__ ocnt, int32_t* __restrict__ opar,
+                            BT* __restrict__ obits, int64_t* __restrict__ ocnt, int32_t* __restrict__ opar,
                             const uint32_t* scnt = nullptr) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t s_prefix, s_need, s_max;
@@ -274,9 +278,10 @@ __device__ void evict_block(const uint64_t* __restrict__ bits, const int64_t* __
     }
 }
 
+template <class BT>
 __global__ void __launch_bounds__(1024)
-evict_kernel(const uint64_t* __restrict__ bits, const int64_t* __restrict__ cnt,
-             int64_t* __restrict__ Udev, int64_t max_unique, uint64_t* __restrict__ obits,
+evict_kernel(const BT* __restrict__ bits, const int64_t* __restrict__ cnt,
+             int64_t* __restrict__ Udev, int64_t max_unique, BT* __restrict__ obits,
              int64_t* __restrict__ ocnt, int32_t* __restrict__ did, const int32_t* __restrict__ par,
              int32_t* __restrict__ opar) {
     const int64_t U = *Udev;
@@ -430,9 +435,10 @@ bk_finish_kernel(uint64_t* __restrict__ cb, int64_t* __restrict__ cc, int64_t* _
     if (threadIdx.x == 0) *Udev = Un;
 }
 
+template <class BT>
 __global__ void copy_back_kernel(const int32_t* __restrict__ did, const int64_t* __restrict__ Udev,
-                                 const uint64_t* __restrict__ sb, const int64_t* __restrict__ sc,
-                                 uint64_t* __restrict__ db, int64_t* __restrict__ dc,
+                                 const BT* __restrict__ sb, const int64_t* __restrict__ sc,
+                                 BT* __restrict__ db, int64_t* __restrict__ dc,
                                  const int32_t* __restrict__ sp, int32_t* __restrict__ dp) {
     if (!*did) return;
     const int64_t U = *Udev;
@@ -457,8 +463,9 @@ __global__ void anc_gather_kernel(const int32_t* __restrict__ par, const int32_t
     }
 }
 
-__global__ void copy_out_kernel(const uint64_t* __restrict__ sb, const int64_t* __restrict__ sc,
-                                uint64_t* __restrict__ db, int64_t* __restrict__ dc, int64_t n) {
+template <class BT>
+__global__ void copy_out_kernel(const BT* __restrict__ sb, const int64_t* __restrict__ sc,
+                                BT* __restrict__ db, int64_t* __restrict__ dc, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         db[i] = sb[i];
         dc[i] = sc[i];
@@ -471,11 +478,12 @@ inline int grid_for(int64_t work) {
 
 }  // namespace
 
-int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b) {
+int sampler_layout(Carver& c, int64_t n_samples, int64_t max_unique, SamplerBufs& b, int words) {
     b.cap = std::max<int64_t>(1, std::min<int64_t>(n_samples, 2 * max_unique));
+    b.words = words;
     const int64_t cap = b.cap;
-    b.bitsA = c.take<uint64_t>(cap);
-    b.bitsB = c.take<uint64_t>(cap);
+    b.bitsA = c.take<uint64_t>(cap * words);
+    b.bitsB = c.take<uint64_t>(cap * words);
     b.cntA = c.take<int64_t>(cap);
     b.cntB = c.take<int64_t>(cap);
     b.start = c.take<int64_t>(cap + 1);
@@ -535,8 +543,36 @@ void sampler_bind_cache(SamplerBufs& b, const ModelConst& mc, void* mem) {
     b.par2 = c.take<int32_t>(b.cap);
 }
 
+// Merge of the step-k children into the spare buffer, the unique count, and (when over
+// max_unique) the eviction, on the multi-kernel path; (cb, cc) is current afterwards.
+template <class BT>
+static int merge_evict(const ModelConst& mc, int k, int64_t n_samples, int64_t max_unique, SamplerBufs& b,
+                       uint64_t*& cb, int64_t*& cc, uint64_t*& nb, int64_t*& nc, int32_t* did, cudaStream_t s) {
+    const int g = grid_for(b.cap);
+    merge_kernel<BT><<<g, 256, 0, s>>>(reinterpret_cast<const BT*>(cb), cc, b.n1, b.pos0, b.pos1, b.U,
+                                       with_bit(bits_zero<BT>(), mc.order[k]), reinterpret_cast<BT*>(nb), nc, b.par);
+    NQS_LAUNCHED();
+    set_u_kernel<<<1, 1, 0, s>>>(b.U, b.pos0, b.pos1);
+    NQS_LAUNCHED();
+    std::swap(cb, nb);
+    std::swap(cc, nc);
+    if (max_unique < n_samples) {
+        // evict into the spare buffer, then copy back so (cb, cc) stays current
+        evict_kernel<BT><<<1, 1024, 0, s>>>(reinterpret_cast<const BT*>(cb), cc, b.U, max_unique,
+                                            reinterpret_cast<BT*>(nb), nc, did, b.par, b.par2);
+        NQS_LAUNCHED();
+        copy_back_kernel<BT><<<g, 256, 0, s>>>(did, b.U, reinterpret_cast<const BT*>(nb), nc,
+                                               reinterpret_cast<BT*>(cb), cc, b.par2, b.par);
+        NQS_LAUNCHED();
+    }
+    return NQS_OK;
+}
+
 int sampler_init(SamplerBufs& b, int64_t n_samples, uint64_t seed, cudaStream_t s) {
-    init_kernel<<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples, seed, b.start, b.n1);
+    if (b.words == 2)
+        init_kernel<U128><<<1, 1, 0, s>>>(reinterpret_cast<U128*>(b.bitsA), b.cntA, b.U, n_samples, seed, b.start, b.n1);
+    else
+        init_kernel<uint64_t><<<1, 1, 0, s>>>(b.bitsA, b.cntA, b.U, n_samples, seed, b.start, b.n1);
     NQS_LAUNCHED();
     return NQS_OK;
 }
@@ -548,7 +584,7 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
     uint64_t* cb = b.bitsA; int64_t* cc = b.cntA;
     uint64_t* nb = b.bitsB; int64_t* nc = b.cntB;
     const int g = grid_for(b.cap);
-    const bool one_cta = b.cap <= SAMPLER_GRAPH_MAX_CAP;
+    const bool one_cta = b.cap <= SAMPLER_GRAPH_MAX_CAP && b.words == 1;   // two-word bits: multi-kernel path
     if (one_cta) {
         // the parent bits and counts staged by bk_finish_kernel take up to 160 KB of shared
         // memory; the limit is raised once per device (before any captured launch: the first call
@@ -598,19 +634,8 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         NQS_LAUNCHED();
         NQS_TRY(launch_scan_i64(b.flags0, b.cap, b.U, b.pos0, s));
         NQS_TRY(launch_scan_i64(b.flags1, b.cap, b.U, b.pos1, s));
-        merge_kernel<<<g, 256, 0, s>>>(cb, cc, b.n1, b.pos0, b.pos1, b.U, 1ull << mc.order[k], nb, nc, b.par);
-        NQS_LAUNCHED();
-        set_u_kernel<<<1, 1, 0, s>>>(b.U, b.pos0, b.pos1);
-        NQS_LAUNCHED();
-        std::swap(cb, nb);
-        std::swap(cc, nc);
-        if (max_unique < n_samples) {
-            // evict into the spare buffer, then copy back so (cb, cc) stays current
-            evict_kernel<<<1, 1024, 0, s>>>(cb, cc, b.U, max_unique, nb, nc, did, b.par, b.par2);
-            NQS_LAUNCHED();
-            copy_back_kernel<<<g, 256, 0, s>>>(did, b.U, nb, nc, cb, cc, b.par2, b.par);
-            NQS_LAUNCHED();
-        }
+        NQS_TRY(b.words == 2 ? merge_evict<U128>(mc, k, n_samples, max_unique, b, cb, cc, nb, nc, did, s)
+                             : merge_evict<uint64_t>(mc, k, n_samples, max_unique, b, cb, cc, nb, nc, did, s));
         if (b.kv && k + 1 < mc.n) {
             anc_gather_kernel<<<grid_for(b.cap * (k + 1)), 256, 0, s>>>(b.par, b.ancA, b.ancB, b.U, mc.n, k);
             NQS_LAUNCHED();
@@ -618,7 +643,11 @@ int sampler_steps(const ModelConst& mc, const float* P, int64_t n_samples, int64
         }
     }
     if (cb != b.bitsA) {
-        copy_out_kernel<<<g, 256, 0, s>>>(cb, cc, b.bitsA, b.cntA, b.cap);
+        if (b.words == 2)
+            copy_out_kernel<U128><<<g, 256, 0, s>>>(reinterpret_cast<const U128*>(cb), cc,
+                                                    reinterpret_cast<U128*>(b.bitsA), b.cntA, b.cap);
+        else
+            copy_out_kernel<uint64_t><<<g, 256, 0, s>>>(cb, cc, b.bitsA, b.cntA, b.cap);
         NQS_LAUNCHED();
     }
     return NQS_OK;
@@ -634,7 +663,11 @@ int run_sampler(const ModelConst& mc, const float* P, int64_t n_samples, int64_t
 
 int launch_copy_samples(const SamplerBufs& b, uint64_t* bits_out, int64_t* counts_out, int64_t n,
                         cudaStream_t s) {
-    copy_out_kernel<<<grid_for(n), 256, 0, s>>>(b.bitsA, b.cntA, bits_out, counts_out, n);
+    if (b.words == 2)
+        copy_out_kernel<U128><<<grid_for(n), 256, 0, s>>>(reinterpret_cast<const U128*>(b.bitsA), b.cntA,
+                                                          reinterpret_cast<U128*>(bits_out), counts_out, n);
+    else
+        copy_out_kernel<uint64_t><<<grid_for(n), 256, 0, s>>>(b.bitsA, b.cntA, bits_out, counts_out, n);
     NQS_LAUNCHED();
     return NQS_OK;
 }

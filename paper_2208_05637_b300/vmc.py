@@ -37,8 +37,9 @@ class LogPsi(torch.autograd.Function):
     def backward(ctx, g_la, g_ph):
         (bits,) = ctx.saved_tensors
         model = ctx.model
-        g_la = torch.zeros_like(bits, dtype=torch.float32) if g_la is None else g_la.float().contiguous()
-        g_ph = torch.zeros_like(bits, dtype=torch.float32) if g_ph is None else g_ph.float().contiguous()
+        B = bits.shape[0]
+        g_la = torch.zeros(B, dtype=torch.float32, device=bits.device) if g_la is None else g_la.float().contiguous()
+        g_ph = torch.zeros(B, dtype=torch.float32, device=bits.device) if g_ph is None else g_ph.float().contiguous()
         grad = torch.zeros_like(model.params)
         nqs_logpsi_backward(model, bits, g_la, g_ph, grad)
         return grad, None, None
@@ -120,7 +121,7 @@ class VMC:
         """Local energies (mini-batched), FP64 statistics and the VMC gradient (Eq. grad) of
         the given unique samples and counts, accumulated into params.grad over the mini-batches
         with the forward recomputed in each; no parameter update."""
-        U = bits.numel()
+        U = bits.shape[0]
         eloc = torch.empty((U, 2), dtype=torch.float32, device="cuda")
         per = max(1, -(-U // self.mini_batches))
         ahead = self._recompute_ahead(bits, self._workspace(OP_BACKWARD, per))
@@ -158,7 +159,7 @@ class VMC:
             nqs_logpsi_backward_phase(self.model, 2, bits, ga_e, gp_e, first, ws=self._workspace(OP_BACKWARD, per))
             nqs_logpsi_backward(self.model, bits, ga_w, zero, second, ws=self._workspace(OP_BACKWARD, per))
         else:
-            for sl in self._slices(bits.numel()):
+            for sl in self._slices(bits.shape[0]):
                 ws = self._workspace(OP_BACKWARD, per)
                 nqs_logpsi_backward(self.model, bits[sl], ga_e[sl], gp_e[sl], first, ws=ws)
                 nqs_logpsi_backward(self.model, bits[sl], ga_w[sl], zero[sl], second, ws=ws)
@@ -167,4 +168,4 @@ class VMC:
             self.params.grad = grad
         else:
             self.params.grad.copy_(grad)
-        return dict(bits=bits, counts=counts, eloc=eloc, stats=stats, unique=bits.numel())
+        return dict(bits=bits, counts=counts, eloc=eloc, stats=stats, unique=bits.shape[0])

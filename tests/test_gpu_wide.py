@@ -164,19 +164,93 @@ def test_wide_local_energy_matches_oracle(arch, which):
     check_eloc(got, want, absum, "fp32", label=f"76-qubit {arch} {which}")
 
 
-def test_wide_registers_rejected_where_not_built():
+@pytest.mark.parametrize("arch,n_samples,max_unique", [("made", 20000, 10 ** 6), ("made", 20000, 300),
+                                                      ("product", 5000, 10 ** 6)])
+def test_wide_sampler_trace_replay_bit_exact(arch, n_samples, max_unique):
+    # the GPU's per-step probabilities replayed through the oracle's two-word buffer sampler give
+    # the same samples and counts, bit for bit, with and without eviction
+    from oracle.wide import model_p_fn_words, sample_words
+    P = lib()
+    cfg, m, om = _models(arch)
+    seed = cfg.seed_sampler
+    bits, counts, trace = P.nqs_sample(m, n_samples, max_unique, seed, trace=True)
+    trace = trace.cpu().numpy()
+    orc = model_p_fn_words(om)
+    diffs = []
+
+    def replay(parent_bits, k):
+        p_gpu = trace[k, : len(parent_bits)]
+        diffs.append(float(np.max(np.abs(p_gpu.astype(np.float64) - orc(parent_bits, k)))))
+        return p_gpu
+
+    wb, wc = sample_words(replay, cfg.n_qubits, om.order, n_samples, max_unique, seed)
+    got = _host(bits).reshape(-1, 2)
+    assert np.array_equal(got, wb)
+    assert np.array_equal(counts.cpu().numpy(), wc)
+    assert max(diffs) <= 2e-6
+    assert np.all(in_sector_words(got, cfg.n_qubits, cfg.n_up, cfg.n_dn))
+    assert got[:, 1].any()
+    if max_unique >= n_samples:
+        assert counts.sum().item() == n_samples
+
+
+@pytest.mark.parametrize("arch", ["made", "product"])
+def test_wide_backward_matches_oracle_vjp(arch):
     import torch
+    from oracle.vmc import logpsi_vjp
+    P = lib()
+    cfg, m, _ = _models(arch)
+    n = cfg.n_qubits
+    hidden, layers = (cfg.hidden, cfg.layers) if arch == "made" else (0, 0)
+    named = synth.init_params(arch, n, cfg.n_up, cfg.n_dn, hidden, layers, 0, cfg.seed_params, beta=1.0,
+                              order=synth.default_order(n))
+    om = Model(arch, named, n, cfg.n_up, cfg.n_dn, synth.default_order(n), hidden, layers, 0, requires_grad=True)
+    bits = synth.random_sector_bits_words(cfg.n_orb, cfg.n_up, cfg.n_dn, 96, seed=41, words=2)
+    rng = np.random.default_rng(41)
+    ga = rng.standard_normal(96).astype(np.float32)
+    gp = rng.standard_normal(96).astype(np.float32)
+    grad = torch.zeros(m.param_count, dtype=torch.float32, device="cuda")
+    P.nqs_logpsi_backward(m, _dev(bits).reshape(-1, 2), torch.tensor(ga, device="cuda"),
+                          torch.tensor(gp, device="cuda"), grad)
+    want = logpsi_vjp(om, bits, ga.astype(np.float64), gp.astype(np.float64))
+    flat = np.concatenate([np.asarray(want[nm]).ravel() for nm, _, _ in m.param_layout()])
+    from tests.common import rel_norm
+    assert rel_norm(grad.cpu().numpy().astype(np.float64), flat) <= 1e-4
+
+
+def test_wide_vmc_steps_on_the_76_qubit_workload():
+    # full VMC steps (sample -> local energy over 1.55M strings -> FP64 statistics -> backward ->
+    # Adam) on 76 qubits; the first step's gradient against the oracle's Eq. grad on its samples
+    import torch
+    from oracle.vmc import vmc_gradient
+    from tests.common import rel_norm
     P = lib()
     cfg, m, _ = _models("made")
-    with pytest.raises(P.NQSError) as e:
-        P.nqs_sample(m, 1000, 100, 1)
-    assert e.value.status == P.NQS_ERR_NQUBITS
+    n = cfg.n_qubits
+    xm, zm, c = synth.hamiltonian_words_for(cfg)
+    ham = P.Hamiltonian(n, xm, zm, c)
+    named = synth.init_params("made", n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, 0, cfg.seed_params, beta=1.0,
+                              order=synth.default_order(n))
+    om = Model("made", named, n, cfg.n_up, cfg.n_dn, synth.default_order(n), cfg.hidden, cfg.layers, 0,
+               requires_grad=True)
+    vmc = P.VMC(ham, m, m.params.detach().clone(), cfg.n_samples, max_unique=6)
+    bits, counts, _ = P.nqs_sample(m, cfg.n_samples, 6, cfg.seed_sampler)
+    out = vmc.gradient(bits, counts)
+    hb = _host(bits).reshape(-1, 2)
+    hc = counts.cpu().numpy()
+    e_or = local_energy_words(om, xm, zm, c, hb)
+    want = vmc_gradient(om, hb, hc, e_or)
+    flat = np.concatenate([np.asarray(want[nm]).ravel() for nm, _, _ in m.param_layout()])
+    assert rel_norm(vmc.params.grad.cpu().numpy().astype(np.float64), flat) <= 1e-4
+    e = [vmc.step(seed=cfg.seed_sampler + i)["stats"][0].item() for i in range(3)]
+    assert np.all(np.isfinite(e))
+    assert out["unique"] == len(hb) <= 6
+
+
+def test_wide_registers_rejected_where_not_built():
+    P = lib()
+    cfg, m, _ = _models("made")
     bits = synth.random_sector_bits_words(cfg.n_orb, cfg.n_up, cfg.n_dn, 4, seed=1, words=2)
-    z = torch.zeros(4, dtype=torch.float32, device="cuda")
-    g = torch.zeros(m.param_count, dtype=torch.float32, device="cuda")
-    with pytest.raises(P.NQSError) as e:
-        P.nqs_logpsi_backward(m, _dev(bits), z, z, g)
-    assert e.value.status == P.NQS_ERR_NQUBITS
     with pytest.raises(P.NQSError) as e:
         P.Model("transformer", 76, 8, 8, 128, 4, 8)
     assert e.value.status == P.NQS_ERR_NQUBITS

@@ -178,3 +178,63 @@ def test_hf_energy_helper_agrees_with_determinant_energy():
     h, eri, _ = synth.integrals(cfg.n_orb, cfg.irreps, cfg.decay, cfg.seed_integrals)
     occ = [(a, 0) for a in range(cfg.n_up)] + [(a, 1) for a in range(cfg.n_dn)]
     assert abs(_determinant_energy(h, eri, occ) - fermion.hf_energy(h, eri, cfg.n_up, cfg.n_dn)) < 1e-12
+
+
+def test_words_sampler_matches_one_word_sampler():
+    # the same draws and buffers: the two-word sampler on a 12-qubit register (high word zero)
+    # gives the one-word sampler's samples and counts, with and without eviction
+    from oracle.sampler import model_p_fn, sample
+    from oracle.wide import model_p_fn_words, sample_words
+    cfg = synth.get_config(2)
+    om, _ = oracle_model(cfg, beta=1.0)
+    for max_unique in (10 ** 6, 40):
+        b1, c1 = sample(model_p_fn(om), om.n, om.order, 5000, max_unique, 77)
+        b2, c2 = sample_words(model_p_fn_words(om), om.n, om.order, 5000, max_unique, 77)
+        assert np.array_equal(b2[:, 0], b1) and np.array_equal(c2, c1)
+
+
+def test_words_ordering_and_eviction_are_integer_order():
+    # ascending order and the eviction tie-break follow the configurations as 128-bit integers
+    from oracle.wide import evict_words
+    rng = np.random.default_rng(8)
+    b = rng.integers(0, 2 ** 63, (300, 2), dtype=np.uint64) >> rng.integers(0, 62, (300, 2)).astype(np.uint64)
+    b[:50, 1] = 5                               # many equal high words: order decided by the low word
+    ints = [int(x[0]) + (int(x[1]) << 64) for x in b]
+    srt = np.argsort(np.array(ints, dtype=object), kind="stable")
+    b = b[srt]
+    counts = rng.integers(1, 4, 300)
+    kb, kc = evict_words(b, counts, 100)
+    ki = [int(x[0]) + (int(x[1]) << 64) for x in kb]
+    assert ki == sorted(ki)
+    # survivors by hand: every count above the cut, then the smallest integers at the cut
+    pairs = sorted(zip((-counts).tolist(), [int(x[0]) + (int(x[1]) << 64) for x in b]))[:100]
+    assert sorted(v for _, v in pairs) == ki
+
+
+def test_words_sampler_on_76_qubits_stays_in_the_sector():
+    from oracle.wide import model_p_fn_words, sample_words
+    n, n_up, n_dn = 76, 8, 8
+    order = synth.default_order(n)
+    params = synth.init_params("made", n, n_up, n_dn, 16, 1, 0, 5, beta=1.0, order=order)
+    om = Model("made", params, n, n_up, n_dn, order, 16, 1, 0)
+    bits, counts = sample_words(model_p_fn_words(om), n, order, 400, 10 ** 6, 3)
+    assert counts.sum() == 400 and np.all(counts > 0)
+    assert np.all(in_sector_words(bits, n, n_up, n_dn))
+    assert bits[:, 1].any()                   # electrons above qubit 64 are drawn
+
+
+def test_model_positions_of_words_match_the_word_expansion():
+    # oracle.models.Model accepts [B, W] configurations directly (log psi, VJP, gradient)
+    from oracle.wide import log_psi_words
+    n, n_up, n_dn = 76, 8, 8
+    order = np.random.default_rng(3).permutation(n)
+    params = synth.init_params("made", n, n_up, n_dn, 16, 2, 0, 5, beta=1.0, order=order)
+    om = Model("made", params, n, n_up, n_dn, order, 16, 2, 0)
+    bits = synth.random_sector_bits_words(n // 2, n_up, n_dn, 20, seed=2, words=2)
+    la, ph = om.log_psi(bits)
+    wl, wp = log_psi_words(om, bits)
+    assert np.array_equal(la, wl) and np.array_equal(ph, wp)
+    one = synth.random_sector_bits(10, 3, 3, 20, seed=2)
+    m12 = Model("made", synth.init_params("made", 20, 3, 3, 16, 1, 0, 5, order=np.arange(20)), 20, 3, 3,
+                np.arange(20), 16, 1, 0)
+    assert np.array_equal(m12.positions(one).numpy(), m12.positions(_two_words(one)).numpy())
