@@ -348,12 +348,56 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     }
     if (h->K > (int64_t)0xffffffffll) { delete h; set_error("too many terms"); return NQS_ERR_UNSUPPORTED; }
 
+    // Tabulated groups (Eq. mtx_element factored): a real group whose flip mask m has at most
+    // SWEEP_TAB_BITS bits and whose terms share z outside m has
+    //     S_g(x) = (-1)^{popcount(x & zc)} T_g[bits of x at the positions of m],
+    //     T_g[b] = sum_k c'_k (-1)^{popcount(b & z_k)}   (b, z_k restricted to m),
+    // with zc = z_k & ~m the common part; T_g is summed in fp64 here and stored as fp32 hi + lo.
+    std::vector<int32_t> g_tab((size_t)h->G, -1);
+    std::vector<uint32_t> g_pos((size_t)h->G, 0u);
+    std::vector<uint64_t> g_zc((size_t)h->G * W, 0ull);
+    std::vector<float2> tab;
+    for (int64_t g = 0; g < h->G && h->K > 0; ++g) {
+        const U128 m{h->grp_mask[g * W], W > 1 ? h->grp_mask[g * W + 1] : 0ull};
+        const int nb = popc(m);
+        if (nb < 1 || nb > SWEEP_TAB_BITS || (h->grp_meta[g] & META_HAS_IMAG)) continue;
+        const int64_t k0 = h->grp_off[g], k1 = h->grp_off[g + 1];
+        auto zk = [&](int64_t k) { return U128{h->term_z[k * W], W > 1 ? h->term_z[k * W + 1] : 0ull}; };
+        const U128 notm{~m.lo, ~m.hi};
+        const U128 zc = zk(k0) & notm;
+        bool uniform = true;
+        for (int64_t k = k0 + 1; k < k1 && uniform; ++k) uniform = (zk(k) & notm) == zc;
+        if (!uniform) continue;
+        int pos[SWEEP_TAB_BITS];
+        int np = 0;
+        for (int q = 0; q < 128; ++q)
+            if ((q < 64 ? (m.lo >> q) : (m.hi >> (q - 64))) & 1ull) pos[np++] = q;
+        uint32_t packed = 0;
+        for (int i = 0; i < np; ++i) packed |= (uint32_t)pos[i] << (8 * i);
+        g_tab[g] = (int32_t)(tab.size() / SWEEP_TAB_SIZE);
+        g_pos[g] = packed;
+        g_zc[g * W] = zc.lo;
+        if (W > 1) g_zc[g * W + 1] = zc.hi;
+        for (int b = 0; b < SWEEP_TAB_SIZE; ++b) {
+            U128 xb{0ull, 0ull};
+            for (int i = 0; i < np; ++i)
+                if ((b >> i) & 1) xb = with_bit(xb, pos[i]);
+            double t = 0.0;
+            for (int64_t k = k0; k < k1; ++k) t += (popc(xb & zk(k)) & 1) ? -c_signed[k] : c_signed[k];
+            const float hi = (float)t;
+            tab.push_back(make_float2(hi, (float)(t - (double)hi)));
+        }
+    }
+    if (tab.empty()) tab.assign(SWEEP_TAB_SIZE, make_float2(0.f, 0.f));
+    const int64_t ntab = (int64_t)tab.size();
+
     // device copy: one allocation, arrays 256-byte aligned; the term records carry one zero
     // padding record
     const int rec = W;   // uint4 per term record
     Carver c(nullptr);
     c.take<uint64_t>(h->G * W); c.take<uint32_t>(h->G + 1); c.take<uint32_t>(h->G);
     c.take<uint4>((h->K + 1) * rec);
+    c.take<int32_t>(h->G); c.take<uint32_t>(h->G); c.take<uint64_t>(h->G * W); c.take<float2>(ntab);
     cudaGetDevice(&h->device);
     if (cudaMalloc(&h->d_block, c.used) != cudaSuccess) {
         cudaGetLastError();
@@ -366,6 +410,10 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     auto* d_off = d.take<uint32_t>(h->G + 1);
     auto* d_meta = d.take<uint32_t>(h->G);
     auto* d_t = d.take<uint4>((h->K + 1) * rec);
+    auto* d_gtab = d.take<int32_t>(h->G);
+    auto* d_gpos = d.take<uint32_t>(h->G);
+    auto* d_gzc = d.take<uint64_t>(h->G * W);
+    auto* d_tab = d.take<float2>(ntab);
     std::vector<uint32_t> off32(h->grp_off.begin(), h->grp_off.end());
     std::vector<uint4> tt((size_t)(h->K + 1) * rec, make_uint4(0u, 0u, 0u, 0u));
     for (int64_t k = 0; k < h->K; ++k) {
@@ -390,12 +438,16 @@ int nqs_ham_create(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const 
     if (e == cudaSuccess) e = cudaMemcpy(d_off, off32.data(), (h->G + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_meta, h->grp_meta.data(), h->G * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_t, tt.data(), tt.size() * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_gtab, g_tab.data(), h->G * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_gpos, g_pos.data(), h->G * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_gzc, g_zc.data(), h->G * W * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_tab, tab.data(), ntab * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(h->d_block);
         delete h;
         return cuda_fail(e, "copy of the Hamiltonian tables", __FILE__, __LINE__);
     }
-    h->dev = HamDev{h->n, W, h->K, h->G, d_mask, d_off, d_meta, d_t, any_imag};
+    h->dev = HamDev{h->n, W, h->K, h->G, d_mask, d_off, d_meta, d_t, any_imag, d_gtab, d_gpos, d_gzc, d_tab};
     *out = h;
     return NQS_OK;
 }

@@ -103,7 +103,14 @@ struct HamDev {
     // words: 32 bytes {z word 0 (two halves), z word 1 (two halves)}, {c' hi, c' lo, 0, 0}.
     const uint4* term;
     int any_imag;              // some group holds a term with an odd sigma_2 count
+    // tabulated groups (real, at most SWEEP_TAB_BITS flipped qubits, one z outside the flips):
+    const int32_t* grp_tab;    // G: table index, or -1
+    const uint32_t* grp_pos;   // G: the flipped qubits, one byte each
+    const uint64_t* grp_zc;    // G masks of `words` words: the z bits outside the flips
+    const float2* tab;         // SWEEP_TAB_SIZE (hi, lo) entries per table
 };
+constexpr int SWEEP_TAB_BITS = 4;                    // flipped qubits of a tabulated group
+constexpr int SWEEP_TAB_SIZE = 1 << SWEEP_TAB_BITS;  // entries of its table
 
 }  // namespace nqs
 

@@ -72,6 +72,15 @@ __device__ __forceinline__ uint32_t sign_flip(uint32_t xl, uint32_t xh, uint32_t
     return (uint32_t)__popc((xl & zl) ^ (xh & zh)) << 31;
 }
 
+// (-1)^{popcount(x & z)} as the float sign bit (bit 31)
+__device__ __forceinline__ uint32_t parity_bit(uint64_t x, uint64_t z) {
+    return sign_flip((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+}
+__device__ __forceinline__ uint32_t parity_bit(const U128& x, const U128& z) {
+    const U128 v = x & z;
+    return (uint32_t)__popc((uint32_t)v.lo ^ (uint32_t)(v.lo >> 32) ^ (uint32_t)v.hi ^ (uint32_t)(v.hi >> 32)) << 31;
+}
+
 // uint4 per term record: one for one-word masks, two for two-word masks
 template <class BT> __host__ __device__ constexpr int rec_of() { return (int)(sizeof(BT) / 8); }
 
@@ -234,6 +243,9 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
     __shared__ __align__(8) uint64_t bar;
     __shared__ BT g_mask[SWEEP_GT];                    // the tile's groups: flip mask, meta, term range
     __shared__ uint32_t g_meta[SWEEP_GT], g_k0[SWEEP_GT], g_k1[SWEEP_GT];
+    __shared__ int32_t g_tab[SWEEP_GT];                // tabulated groups: table, flipped qubits, common z
+    __shared__ uint32_t g_pos[SWEEP_GT];
+    __shared__ BT g_zc[SWEEP_GT];
 
     const int tile = blockIdx.y;
     const int64_t s0 = (int64_t)blockIdx.x * SWEEP_SB;
@@ -262,6 +274,9 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
     const uint32_t k0 = live ? h.grp_off[g] : 0, k1 = live ? h.grp_off[g + 1] : 0;
     g_mask[threadIdx.x] = live ? reinterpret_cast<const BT*>(h.grp_mask)[g] : bits_zero<BT>();
     g_meta[threadIdx.x] = live ? h.grp_meta[g] : 0;
+    g_tab[threadIdx.x] = live ? h.grp_tab[g] : -1;
+    g_pos[threadIdx.x] = live ? h.grp_pos[g] : 0u;
+    g_zc[threadIdx.x] = live ? reinterpret_cast<const BT*>(h.grp_zc)[g] : bits_zero<BT>();
     g_k0[threadIdx.x] = k0 - t0;                       // term indices relative to the tile's range
     g_k1[threadIdx.x] = k1 - t0;
     const unsigned lg = __ballot_sync(0xffffffffu, live && k1 - k0 > (uint32_t)SWEEP_SMALL);
@@ -295,8 +310,21 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
             const int s = (int)(e >> 16), gl = (int)((e >> 8) & 0xffu);
             const BT x = xs[s], mg = g_mask[gl];
             float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
-            sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl], g_k1[gl], 1u, re,
-                                       re_e, im, im_e);
+            const int tb = g_tab[gl];
+            if (tb >= 0) {
+                // tabulated group: common parity times the table entry of x's flipped bits
+                const uint32_t pk = g_pos[gl], meta = g_meta[gl];
+                const int nbits = (int)((meta & 0xffu) + ((meta >> 8) & 0xffu));
+                int idx = 0;
+                for (int i = 0; i < nbits; ++i) idx |= qbit(x, (int)((pk >> (8 * i)) & 0xffu)) << i;
+                const uint32_t flip = parity_bit(x, g_zc[gl]);
+                const float2 t = __ldg(h.tab + (int64_t)tb * SWEEP_TAB_SIZE + idx);
+                re = __uint_as_float(__float_as_uint(t.x) ^ flip);
+                re_e = COMP ? __uint_as_float(__float_as_uint(t.y) ^ flip) : 0.f;
+            } else {
+                sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl], g_k1[gl], 1u, re,
+                                           re_e, im, im_e);
+            }
             const int64_t row = obase[s] + (int64_t)(e & 0xffu);
             xprime[row] = x ^ mg;
             S[row] = make_float4(re, re_e, im, im_e);
