@@ -194,7 +194,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     cfg = synth.get_config(args.workload)
     n = cfg.n_qubits
-    xm, zm, coef = synth.hamiltonian_for(cfg)
+    xm, zm, coef = hamiltonian_of(cfg)
     ham = P.Hamiltonian(n, xm, zm, coef)
     K_terms, G = ham.info()
     order = synth.default_order(n)
@@ -575,16 +575,18 @@ def cpu_baseline(cfg, args, budget_s=15.0):
     budget, one sample over a seeded subset of the terms (the rate is per evaluated term).
     Sampling and the gradient are not included, which favours the CPU figure."""
     import torch
-    from oracle.eloc import local_energy
+    from oracle.eloc import local_energy as local_energy_one_word
     from oracle.models import Model
+    from oracle.wide import local_energy_words
 
     n = cfg.n_qubits
     order = synth.default_order(n)
     named = synth.init_params(cfg.arch, n, cfg.n_up, cfg.n_dn, cfg.hidden, cfg.layers, cfg.heads,
                               cfg.seed_params, beta=args.beta, order=order)
-    xm, zm, coef = synth.hamiltonian_for(cfg)
+    xm, zm, coef = hamiltonian_of(cfg)
     om = Model(cfg.arch, named, n, cfg.n_up, cfg.n_dn, order, cfg.hidden, cfg.layers, cfg.heads)
-    bits = synth.random_sector_bits(cfg.n_orb, cfg.n_up, cfg.n_dn, 4096, seed=cfg.seed_sampler)
+    bits = sector_bits_of(cfg, 4096, cfg.seed_sampler)
+    local_energy = local_energy_one_word if n <= 64 else local_energy_words
     # terms per call: all of them, or the share one call can do in about a third of the budget
     frac = 1.0
     if cfg.n_qubits >= 30:
