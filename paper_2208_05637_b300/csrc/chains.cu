@@ -1216,8 +1216,11 @@ static int ch_forward(const ModelConst& mc, const float* P, const TfWeights& w, 
                     NQS_TRY(ch_attention<MODE>(mc, t.qkv, t.o, b.chunks, b.coff + nsl, nsl, b.tiles, row_base, b.rpos,
                                                b.rstart, b.kv, l, s));
                 }
-                NQS_TRY(tf_gemm(mc, w, TF_WO, l, t.o, t.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
-                {
+                if (MODE == ACT_BF16X2 && (d == 64 || d == 128)) {
+                    // attention output + residual + LayerNorm 2 in one tensor-core kernel
+                    NQS_TRY(tf_resid_ln(mc, P, w, l, t.o, t.h, t.a, M, s));
+                } else {
+                    NQS_TRY(tf_gemm(mc, w, TF_WO, l, t.o, t.h, M, d, d, TF_EPI_RESID, P + mc.bo[l], s));
                     ProfScope ps2("tf_layernorm", s, 0.0, ln_bytes);
                     layernorm_kernel<MODE, DPL><<<ln_grid(M), 256, 0, s>>>(t.h, M, d, P + mc.ln2_g[l], P + mc.ln2_b[l], t.a);
                     NQS_LAUNCHED();

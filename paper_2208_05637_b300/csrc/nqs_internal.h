@@ -296,7 +296,8 @@ int launch_product_backward(const ModelConst& mc, const float* P, const uint64_t
 enum { TF_EPI_STORE = 0, TF_EPI_GELU = 1, TF_EPI_RESID = 2, TF_EPI_ACCUM = 3, TF_EPI_GELU2 = 4,
        TF_EPI_RESID_LN = 5,     // h += acc + bias, then a = LayerNorm(h) as hi|lo bf16 (d = 64)
        TF_EPI_RESID_LN_TAB = 6, // the same with the old h taken from a token-position table
-       TF_EPI_SPLIT = 7         // QKV projection into the split layout (bf16 hi and lo planes; see tc_gemm_bf16)
+       TF_EPI_SPLIT = 7,        // QKV projection into the split layout (bf16 hi and lo planes; see tc_gemm_bf16)
+       TF_EPI_RESID_LN128 = 8   // TF_EPI_RESID_LN for d = 128
 };
 // First-block rows that depend on the (token, position) pair only: the token of position t is 2
 // at t = 0 and bit order[t - 1] of the sequence's configuration after it; row (token, t) of a
@@ -407,7 +408,7 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
 // h[M, 64] += A . W^T + bias, then a[M, 2*64] = hi|lo of LayerNorm(h; ln_g, ln_b) (compensated
 // BF16 transformer, d_model 64): the attention-output GEMM with the next LayerNorm fused in.
 int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
-                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s,
+                          const float* ln_g, const float* ln_b, int64_t M, int N, int K, cudaStream_t s,
                           const TcTokTable* h_old = nullptr);
 // o = causal attention of (A . Wqkv^T + bqkv) for the compensated d_model-64 transformer with
 // head size 16, without writing qkv (R sequences of T <= 64 positions; o hi|lo bf16).
@@ -424,6 +425,10 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
             int K, int epi, const float* bias, cudaStream_t s);
 int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* a, void* mid, float* h,
            int64_t M, cudaStream_t s, const TcMlpHead* head = nullptr);
+// Attention-output projection with the residual add and LayerNorm 2 in its epilogue (compensated
+// BF16, d_model 64 or 128; h_old: the first block's old h from the token-position table, d 64).
+int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* o, float* h,
+                void* a, int64_t M, cudaStream_t s, const TcTokTable* h_old = nullptr);
 
 // Prefix-sharing local energy of the transformer (chains.cu).  Jobs of levels 0 (the samples),
 // 1 (one flip) and 2 (two flips) with their per-layer key/value caches, and the leaves (the

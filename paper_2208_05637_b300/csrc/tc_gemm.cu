@@ -274,7 +274,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                const float* __restrict__ bias, void* __restrict__ Cv, const float* __restrict__ ln_g,
                const float* __restrict__ ln_b, int64_t M, int N, int K, int BN, int tmem_cols, int stages,
                int n_tiles_n, int64_t total_tiles, const __grid_constant__ TcTokTable tok) {
-    constexpr bool RLN = EPI == TF_EPI_RESID_LN || EPI == TF_EPI_RESID_LN_TAB;
+    constexpr bool RLN = EPI == TF_EPI_RESID_LN || EPI == TF_EPI_RESID_LN_TAB || EPI == TF_EPI_RESID_LN128;
+    constexpr bool RLN_LOAD = EPI == TF_EPI_RESID_LN || EPI == TF_EPI_RESID_LN128;   // old h through TMA
+    constexpr int RW = EPI == TF_EPI_RESID_LN128 ? 128 : 64;           // row width of the LayerNorm epilogue
+    constexpr int STGB = EPI == TF_EPI_RESID_LN128 ? 2 * TC_STAGE_BYTES_PER_WARP : TC_STAGE_BYTES_PER_WARP;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nkb = (K + TC_BK - 1) / TC_BK;
@@ -283,7 +286,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)stages * a_bytes;
     uint8_t* sC = sB + (size_t)stages * b_bytes;     // 1024-aligned: a_bytes, b_bytes are multiples of 1024
-    uint64_t* full = reinterpret_cast<uint64_t*>(sC + (TMA_EPI ? 4 * TC_STAGE_BYTES_PER_WARP : 0));
+    uint64_t* full = reinterpret_cast<uint64_t*>(sC + (TMA_EPI ? 4 * STGB : 0));
     uint64_t* empty = full + stages;
     uint64_t* tfull = empty + stages;       // [2] accumulator ready for the epilogue
     uint64_t* tempty = tfull + 2;           // [2] accumulator drained by the epilogue
@@ -353,15 +356,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     } else {
         // ---- epilogue: warp w drains TMEM lanes 32*(w%4) .. +31
         const int quad = warp & 3;
-        uint8_t* stg = sC + (size_t)(warp - 2) * TC_STAGE_BYTES_PER_WARP;
+        uint8_t* stg = sC + (size_t)(warp - 2) * STGB;
         int64_t acc = 0;
         int chunk = 0;
-        if (EPI == TF_EPI_RESID_LN && lane == 0 && (int64_t)blockIdx.x < total_tiles) {
-            // residual rows of the first tile
+        if (RLN_LOAD && lane == 0 && (int64_t)blockIdx.x < total_tiles) {
+            // residual rows of the first tile (RW / 32 chunks of 32 rows x 32 fp32)
             const int nrow = (int)((blockIdx.x / n_tiles_n) * TC_BM + quad * 32);
-            mbar_expect_tx(&hbar[quad], 8192);
-            tma_load_2d(stg, &tmC, &hbar[quad], 0, nrow);
-            tma_load_2d(stg + 4096, &tmC, &hbar[quad], 32, nrow);
+            mbar_expect_tx(&hbar[quad], RW * 128);
+#pragma unroll
+            for (int q = 0; q < RW / 32; ++q) tma_load_2d(stg + 4096 * q, &tmC, &hbar[quad], 32 * q, nrow);
         }
         __syncwarp();
         // TAB: the configuration of this lane's row, loaded one tile ahead
@@ -381,7 +384,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const int n0 = (int)(t % n_tiles_n) * BN;
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * (tmem_cols >> 1));
             if constexpr (RLN) {
-                // the tile spans whole rows of d = 64: lane = row.  h_new = h + acc + bias,
+                // the tile spans whole rows of d = RW: lane = row.  h_new = h + acc + bias,
                 // stored back; then a = LayerNorm(h_new) as hi | lo bf16.  The old h comes through
                 // the staging (TMA), or from the token-position table (TAB: first block)
                 const int64_t hrow0 = (t / n_tiles_n) * TC_BM + quad * 32;
@@ -405,7 +408,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 // pass 1: h_new = h + acc + bias, in place in the staging; row sum
                 float sum = 0.f;
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
+                for (int p = 0; p < RW / 16; ++p) {
                     float v16[16];
                     tmem_ld16(tbase + (uint32_t)(16 * p), v16);
 #pragma unroll
@@ -431,25 +434,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) {
                     if (hrow0 < M) {
-                        tma_store_2d(&tmC, stg, 0, (int)hrow0);
-                        tma_store_2d(&tmC, stg + 4096, 32, (int)hrow0);
+#pragma unroll
+                        for (int q = 0; q < RW / 32; ++q) tma_store_2d(&tmC, stg + 4096 * q, 32 * q, (int)hrow0);
                     }
                     bulk_commit();
                 }
-                // pass 2: variance about the mean; pass 3: normalised hi | lo bf16 pairs
-                const float mu = sum * (1.f / 64.f);
+                // pass 2: variance about the mean; pass 3: normalised hi | lo bf16 pairs, 64 columns
+                // at a time (hi rows into the staging chunk 2 v, lo rows into chunk 2 v + 1, each
+                // once the h store has read it and after its own columns were read)
+                const float mu = sum * (1.f / (float)RW);
                 float var = 0.f;
 #pragma unroll
-                for (int c = 0; c < 64; c += 4) {
+                for (int c = 0; c < RW; c += 4) {
                     float4 o;
                     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(saddr(c)));
                     const float d0 = o.x - mu, d1 = o.y - mu, d2 = o.z - mu, d3 = o.w - mu;
                     var = fmaf(d0, d0, var); var = fmaf(d1, d1, var); var = fmaf(d2, d2, var); var = fmaf(d3, d3, var);
                 }
-                const float rstd = rsqrtf(fmaf(var, 1.f / 64.f, LN_EPS));
+                const float rstd = rsqrtf(fmaf(var, 1.f / (float)RW, LN_EPS));
+#pragma unroll 1
+                for (int v = 0; v < RW / 64; ++v) {
                 uint32_t hp[32], lp[32];
 #pragma unroll
-                for (int c = 0; c < 64; c += 4) {
+                for (int c0 = 0; c0 < 64; c0 += 4) {
+                    const int c = 64 * v + c0;
                     float4 o;
                     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w) : "r"(saddr(c)));
                     const float y[4] = {(o.x - mu) * rstd * ln_g[c] + ln_b[c], (o.y - mu) * rstd * ln_g[c + 1] + ln_b[c + 1],
@@ -459,35 +467,37 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         const __nv_bfloat162 hh = __floats2bfloat162_rn(y[q2], y[q2 + 1]);
                         const float2 hf = __bfloat1622float2(hh);
                         const __nv_bfloat162 ll = __floats2bfloat162_rn(y[q2] - hf.x, y[q2 + 1] - hf.y);
-                        hp[(c + q2) / 2] = *reinterpret_cast<const uint32_t*>(&hh);
-                        lp[(c + q2) / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+                        hp[(c0 + q2) / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+                        lp[(c0 + q2) / 2] = *reinterpret_cast<const uint32_t*>(&ll);
                     }
                 }
                 // the staging again, once the h store has read it: hi rows, then lo rows
-                if (lane == 0) bulk_wait_read<0>();
+                if (v == 0 && lane == 0) bulk_wait_read<0>();
                 __syncwarp();
+                const uint32_t hb = st + (uint32_t)(2 * v) * 4096u;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const uint32_t off = (uint32_t)(lane * 128 + ((u ^ sw) << 4));
-                    st_shared_v4(st + off, hp[4 * u], hp[4 * u + 1], hp[4 * u + 2], hp[4 * u + 3]);
-                    st_shared_v4(st + 4096 + off, lp[4 * u], lp[4 * u + 1], lp[4 * u + 2], lp[4 * u + 3]);
+                    st_shared_v4(hb + off, hp[4 * u], hp[4 * u + 1], hp[4 * u + 2], hp[4 * u + 3]);
+                    st_shared_v4(hb + 4096 + off, lp[4 * u], lp[4 * u + 1], lp[4 * u + 2], lp[4 * u + 3]);
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
+                if (lane == 0 && hrow0 < M) {
+                    tma_store_2d(&tmD, stg + 2 * v * 4096, 64 * v, (int)hrow0);
+                    tma_store_2d(&tmD, stg + (2 * v + 1) * 4096, RW + 64 * v, (int)hrow0);
+                }
+                }
                 if (lane == 0) {
-                    if (hrow0 < M) {
-                        tma_store_2d(&tmD, stg, 0, (int)hrow0);
-                        tma_store_2d(&tmD, stg + 4096, 64, (int)hrow0);
-                    }
                     bulk_commit();
                     // the next tile's residual rows into the staging once these stores have read it
                     const int64_t tn = t + gridDim.x;
-                    if (EPI == TF_EPI_RESID_LN && tn < total_tiles) {
+                    if (RLN_LOAD && tn < total_tiles) {
                         bulk_wait_read<0>();
-                        mbar_expect_tx(&hbar[quad], 8192);
+                        mbar_expect_tx(&hbar[quad], RW * 128);
                         const int nrow = (int)((tn / n_tiles_n) * TC_BM + quad * 32);
-                        tma_load_2d(stg, &tmC, &hbar[quad], 0, nrow);
-                        tma_load_2d(stg + 4096, &tmC, &hbar[quad], 32, nrow);
+#pragma unroll
+                        for (int q = 0; q < RW / 32; ++q) tma_load_2d(stg + 4096 * q, &tmC, &hbar[quad], 32 * q, nrow);
                     }
                 }
                 __syncwarp();
@@ -1661,19 +1671,23 @@ int tc_gemm_bf16(const void* A, const uint16_t* W, const float* bias, void* C, i
 // Attention-output GEMM with the next LayerNorm fused into its epilogue (compensated BF16,
 // d_model 64): h += A . W^T + bias; a = hi | lo of LayerNorm(h; ln_g, ln_b).
 int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, float* h, void* a_out,
-                          const float* ln_g, const float* ln_b, int64_t M, int K, cudaStream_t s,
+                          const float* ln_g, const float* ln_b, int64_t M, int N, int K, cudaStream_t s,
                           const TcTokTable* h_old) {
     if (M <= 0) return NQS_OK;
-    constexpr int N = 64, BN = 64, tcols = 128;
-    if (K % 64 || K <= 0 || ((uintptr_t)h & 15) || ((uintptr_t)a_out & 15) || !bias || !ln_g || !ln_b ||
+    // d_model 64 (with or without the token-position table) or 128: the tile spans whole rows
+    if ((N != 64 && N != 128) || (N == 128 && h_old) || K % 64 || K <= 0 || ((uintptr_t)h & 15) ||
+        ((uintptr_t)a_out & 15) || !bias || !ln_g || !ln_b ||
         (h_old && (!h_old->tab || !h_old->bits || h_old->T < 1 || ((uintptr_t)h_old->tab & 15)))) {
         set_error("fused residual + LayerNorm GEMM: bad operand");
         return NQS_ERR_INVALID_ARG;
     }
+    const int BN = N, tcols = 2 * N;
     const size_t stage_bytes = TC_BM * 128 + (size_t)BN * 128;
-    const size_t staging = 4 * TC_STAGE_BYTES_PER_WARP;
-    const int stages = (int)std::max<size_t>(2, std::min<size_t>(6, (104 * 1024 - staging) / stage_bytes));
+    const size_t staging = 4 * (size_t)TC_STAGE_BYTES_PER_WARP * (N / 64);
+    const int stages = (int)std::max<size_t>(2, std::min<size_t>(6, (N == 64 ? 104 * 1024 : 200 * 1024) / stage_bytes -
+                                                                     staging / stage_bytes));
     const size_t smem = 1024 + (size_t)stages * stage_bytes + staging + (2 * stages + 8) * 8 + 16;
+    if (smem > 220 * 1024) { set_error("fused residual + LayerNorm GEMM: shared-memory plan too large"); return NQS_ERR_UNSUPPORTED; }
     CUtensorMap ma, mb, mc, md;
     NQS_TRY(make_map(&ma, A, M, K, TC_BM));
     NQS_TRY(make_map(&mb, W, N, K, BN));
@@ -1691,10 +1705,17 @@ int tc_gemm_bf16_resid_ln(const void* A, const uint16_t* W, const float* bias, f
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(tc_gemm_kernel<TF_EPI_RESID_LN_TAB, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tc_gemm_kernel<TF_EPI_RESID_LN128, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm resid_ln)", __FILE__, __LINE__);
         configured_device = dev;
     }
-    if (h_old)
+    if (N == 128)
+        tc_gemm_kernel<TF_EPI_RESID_LN128, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N,
+                                                                                 K, BN, tcols, stages, 1, total_tiles,
+                                                                                 TcTokTable{});
+    else if (h_old)
         tc_gemm_kernel<TF_EPI_RESID_LN_TAB, true><<<grid, TC_THREADS, smem, s>>>(ma, mb, mc, md, bias, h, ln_g, ln_b, M, N,
                                                                                   K, BN, tcols, stages, 1, total_tiles, *h_old);
     else

@@ -421,9 +421,9 @@ int tf_gemm(const ModelConst& mc, const TfWeights& w, int which, int layer, cons
 }
 
 // Attention-output projection of block l with the residual add and LayerNorm 2 fused
-// (compensated BF16, d_model 64): h += Wo . o + bo; a = LN2(h).
-static int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* o, float* h,
-                       void* a, int64_t M, cudaStream_t s, const TcTokTable* h_old = nullptr) {
+// (compensated BF16, d_model 64 or 128): h += Wo . o + bo; a = LN2(h).
+int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w, int layer, const void* o, float* h,
+                void* a, int64_t M, cudaStream_t s, const TcTokTable* h_old) {
     const int d = mc.hidden;
     // A (hi+lo) read, h read (unless it comes from the token-position table) and written,
     // a (hi+lo) written, weights
@@ -431,7 +431,7 @@ static int tf_resid_ln(const ModelConst& mc, const float* P, const TfWeights& w,
                          2.0 * d * d * 2;
     ProfScope ps("tf_resid_ln", s, 2.0 * (double)M * d * d, bytes);
     return tc_gemm_bf16_resid_ln(o, w.bf16 + w.bf16_off[layer][TF_WO], P + mc.bo[layer], h, a, P + mc.ln2_g[layer],
-                                 P + mc.ln2_b[layer], M, 2 * d, s, h_old);
+                                 P + mc.ln2_b[layer], M, d, 2 * d, s, h_old);
 }
 
 // The first block's rows as functions of the (token, position) pair, for positions 0..T-1 of the
