@@ -212,13 +212,14 @@ sweep_count_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits,
 // batch, with the batch's validity bitmaps.  The tile's terms (z masks and coefficients,
 // contiguous in the grouped table) are copied once into shared memory by a bulk asynchronous
 // copy (cp.async.bulk, completion on an mbarrier) and serve every sample of the batch.  Warp w
-// takes samples w, w + 8, ...; it walks the sample's validity words in group order, so the row
-// of each valid pair (its rank among the sample's valid groups of the tile) follows from a
-// running count and a popcount -- the deterministic row order sample-major, tile-major,
-// group-minor.  Pairs of small groups (at most SWEEP_SMALL terms: the double excitations) go to
-// a per-warp queue and are summed 32 at a time, one lane per pair; the few large groups (the
-// diagonal and the single excitations) are summed by the whole warp at once, lanes over terms
-// with a TwoSum butterfly.
+// takes group word w of the tile (32 groups) for all the batch's samples: lane s holds sample
+// s's validity bits over the word and counts its valid groups in the words before, so the row of
+// each valid pair (its rank among the sample's valid groups of the tile) is that count plus a
+// popcount -- the deterministic row order sample-major, tile-major, group-minor.  The pairs of
+// small groups (at most SWEEP_SMALL terms: the double excitations) are numbered by a warp scan
+// of the per-sample counts and summed 32 at a time, one lane per pair (tabulated groups by one
+// table entry); the few large groups (the diagonal and the single excitations) are summed by the
+// whole warp at once, lanes over terms with a TwoSum butterfly.
 template <bool COMP, bool IMAG, class BT>
 __device__ __forceinline__ void sweep_pair_sum(const BT& x, const BT& mg, bool has_imag, const uint4* tp,
                                                uint32_t a0, uint32_t a1, uint32_t step, float& re,
@@ -239,7 +240,6 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
     __shared__ int64_t obase[SWEEP_SB];
     __shared__ uint32_t vb[SWEEP_NW * SWEEP_SB];       // validity words [warp][sample]
     __shared__ uint32_t lmask[SWEEP_NW];               // large groups of each group word
-    __shared__ uint32_t queue[SWEEP_NW][64];           // pending small pairs: rank | group << 8 | sample << 16
     __shared__ __align__(8) uint64_t bar;
     __shared__ BT g_mask[SWEEP_GT];                    // the tile's groups: flip mask, meta, term range
     __shared__ uint32_t g_meta[SWEEP_GT], g_k0[SWEEP_GT], g_k1[SWEEP_GT];
@@ -300,14 +300,47 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
         return;
     }
     const uint4* tp = staged ? ts : h.term + (size_t)t0 * REC;
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t* q = queue[warp];
-    int qn = 0;
-    // the queued pairs of small groups, one per lane
-    auto drain = [&](int count) {
-        if (lane < count) {
-            const uint32_t e = q[lane];
-            const int s = (int)(e >> 16), gl = (int)((e >> 8) & 0xffu);
+    // Warp w owns the tile's group word w (groups 32 w .. 32 w + 31) for all nb samples; lane s
+    // holds sample s's validity bits over the word and its valid groups in the words before w,
+    // so the row of pair (s, g) is obase[s] + pre_s + (valid groups of s below g in the word).
+    const uint32_t lm = lmask[warp];
+    uint32_t bal = 0u;
+    int pre = 0;
+    if (lane < nb) {
+        bal = vb[warp * SWEEP_SB + lane];
+        for (int j = 0; j < warp; ++j) pre += __popc(vb[j * SWEEP_SB + lane]);
+    }
+    // small groups: the warp's pairs numbered by an exclusive scan of the per-sample counts and
+    // handed out 32 at a time, one per lane
+    const uint32_t smask = bal & ~lm;
+    const int cnt = __popc(smask);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        // the pair's sample: the last lane whose first pair number is <= p
+        int s = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = s + step;
+            const int e = __shfl_sync(0xffffffffu, excl, cand & 31);
+            if (cand < 32 && e <= p) s = cand;
+        }
+        const int es = __shfl_sync(0xffffffffu, excl, s);
+        const uint32_t ms = __shfl_sync(0xffffffffu, smask, s);
+        const uint32_t bs = __shfl_sync(0xffffffffu, bal, s);
+        const int ps = __shfl_sync(0xffffffffu, pre, s);
+        uint32_t v = ms;                                      // the (p - es)-th valid small group
+        for (int i = es; i < p && v; ++i) v &= v - 1u;
+        if (p < total && v) {
+            const int bpos = __ffs(v) - 1;
+            const int gl = 32 * warp + bpos;
             const BT x = xs[s], mg = g_mask[gl];
             float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
             const int tb = g_tab[gl];
@@ -325,69 +358,53 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
                 sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl], g_k1[gl], 1u, re,
                                            re_e, im, im_e);
             }
-            const int64_t row = obase[s] + (int64_t)(e & 0xffu);
+            const int64_t row = obase[s] + ps + __popc(bs & ((1u << bpos) - 1u));
             xprime[row] = x ^ mg;
             S[row] = make_float4(re, re_e, im, im_e);
         }
-    };
-    for (int s = warp; s < nb; s += SWEEP_NW) {
+    }
+    // large groups (the diagonal and the single excitations): the whole warp per pair, lanes over
+    // terms, TwoSum butterfly
+    const uint32_t lgm = bal & lm;
+    for (unsigned who = __ballot_sync(0xffffffffu, lgm != 0u); who; who &= who - 1u) {
+        const int s = __ffs(who) - 1;
+        const uint32_t ls = __shfl_sync(0xffffffffu, lgm, s);
+        const uint32_t bs = __shfl_sync(0xffffffffu, bal, s);
+        const int ps = __shfl_sync(0xffffffffu, pre, s);
         const BT x = xs[s];
-        int run = 0;
-#pragma unroll 1
-        for (int j = 0; j < SWEEP_NW; ++j) {
-            const uint32_t bal = vb[j * SWEEP_SB + s];
-            if (bal == 0u) continue;
-            const uint32_t lm = lmask[j], sm = bal & ~lm;
-            if ((sm >> lane) & 1u)
-                q[qn + __popc(sm & lt)] = (uint32_t)(run + __popc(bal & lt)) | ((uint32_t)(32 * j + lane) << 8) |
-                                          ((uint32_t)s << 16);
-            qn += __popc(sm);
-            // large groups: the whole warp per pair
-            for (uint32_t big = bal & lm; big; big &= big - 1u) {
-                const int b = __ffs(big) - 1, gl = 32 * j + b;
-                const BT mg = g_mask[gl];
-                float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
-                sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl] + lane, g_k1[gl],
-                                           32u, re, re_e, im, im_e);
+        for (uint32_t big = ls; big; big &= big - 1u) {
+            const int bpos = __ffs(big) - 1, gl = 32 * warp + bpos;
+            const BT mg = g_mask[gl];
+            float re = 0.f, re_e = 0.f, im = 0.f, im_e = 0.f;
+            sweep_pair_sum<COMP, IMAG>(x, mg, (g_meta[gl] & META_HAS_IMAG) != 0, tp, g_k0[gl] + lane, g_k1[gl],
+                                       32u, re, re_e, im, im_e);
 #pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) {
-                    const float ore = __shfl_xor_sync(0xffffffffu, re, d), oree = __shfl_xor_sync(0xffffffffu, re_e, d);
-                    const float oim = __shfl_xor_sync(0xffffffffu, im, d), oime = __shfl_xor_sync(0xffffffffu, im_e, d);
-                    // both lanes form the same pair sum: order the operands by lane
-                    const bool low = (lane & d) == 0;
-                    if (COMP) {
-                        float a = low ? re : ore, bb = low ? ore : re;
-                        float ae = (low ? re_e : oree) + (low ? oree : re_e);
-                        two_sum_acc(a, ae, bb);
-                        re = a; re_e = ae;
-                        float c2 = low ? im : oim, d2 = low ? oim : im;
-                        float ce = (low ? im_e : oime) + (low ? oime : im_e);
-                        two_sum_acc(c2, ce, d2);
-                        im = c2; im_e = ce;
-                    } else {
-                        re = low ? re + ore : ore + re;
-                        im = low ? im + oim : oim + im;
-                    }
-                }
-                if (lane == 0) {
-                    const int64_t row = obase[s] + run + __popc(bal & ((1u << b) - 1u));
-                    xprime[row] = x ^ mg;
-                    S[row] = make_float4(re, re_e, im, im_e);
+            for (int d = 16; d >= 1; d >>= 1) {
+                const float ore = __shfl_xor_sync(0xffffffffu, re, d), oree = __shfl_xor_sync(0xffffffffu, re_e, d);
+                const float oim = __shfl_xor_sync(0xffffffffu, im, d), oime = __shfl_xor_sync(0xffffffffu, im_e, d);
+                // both lanes form the same pair sum: order the operands by lane
+                const bool low = (lane & d) == 0;
+                if (COMP) {
+                    float a = low ? re : ore, bb = low ? ore : re;
+                    float ae = (low ? re_e : oree) + (low ? oree : re_e);
+                    two_sum_acc(a, ae, bb);
+                    re = a; re_e = ae;
+                    float c2 = low ? im : oim, d2 = low ? oim : im;
+                    float ce = (low ? im_e : oime) + (low ? oime : im_e);
+                    two_sum_acc(c2, ce, d2);
+                    im = c2; im_e = ce;
+                } else {
+                    re = low ? re + ore : ore + re;
+                    im = low ? im + oim : oim + im;
                 }
             }
-            run += __popc(bal);
-            if (qn >= 32) {
-                __syncwarp();
-                drain(32);
-                __syncwarp();
-                if (lane < qn - 32) q[lane] = q[lane + 32];
-                qn -= 32;
-                __syncwarp();
+            if (lane == 0) {
+                const int64_t row = obase[s] + ps + __popc(bs & ((1u << bpos) - 1u));
+                xprime[row] = x ^ mg;
+                S[row] = make_float4(re, re_e, im, im_e);
             }
         }
     }
-    __syncwarp();
-    drain(qn);
 }
 
 __global__ void unpack_rows_kernel(const int64_t* __restrict__ off, int64_t ntiles, int64_t B,
