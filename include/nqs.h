@@ -165,8 +165,9 @@ int nqs_workspace_size(nqs_model_t model, nqs_ham_t ham, int op, int64_t batch, 
  * hi)) and takes bit 1 iff u < floor(p * 2^32), p the fp32 constrained conditional of its
  * parent; zero-count children are dropped and, if more than max_unique entries remain, the top
  * max_unique by (count desc, bits asc) are kept.
- *   bits_out[capacity] (device, uint64) and counts_out[capacity] (device, int64) receive the
- *   U unique samples in ascending bit order; *n_unique (host) receives U.  If U > capacity,
+ *   bits_out[capacity * W] (device, uint64; W words per configuration) and counts_out[capacity]
+ *   (device, int64) receive the U unique samples in ascending order (as W-word integers);
+ *   *n_unique (host) receives U.  If U > capacity,
  *   returns NQS_ERR_CAPACITY with *n_unique = U and nothing written.
  *   p_trace (device, may be NULL): p_trace[k * trace_stride + s] receives the fp32
  *   probability used for parent s at step k (parents in ascending bit order);
