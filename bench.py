@@ -408,17 +408,9 @@ def run_ours(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 (hi+lo activations, fp32 accumulate)" if prec == "bf16" else "f32",
             "data": "synthetic (seeded molecule-shaped integrals, Jordan-Wigner strings, random-init weights)",
-            "config": {"workload": cfg.name, "n_qubits": n, "electrons": [cfg.n_up, cfg.n_dn],
-                       "terms_K": K_terms, "groups_G": G,
-                       "model": f"{cfg.arch} d={cfg.hidden} L={cfg.layers} H={cfg.heads}",
-                       "n_samples": cfg.n_samples,
-                       "max_unique": args.max_unique,
-                       "batch": "capped: the paper's 1024 unique samples per step (Section 5.1); the sampler "
-                                "draws the nominal count and keeps the 1024 most frequent",
-                       "mini_batches": cfg.mini_batches,
-                       "unique_samples_mean": float(np.mean(units)), "beta": args.beta,
-                       "precision": prec, "compensated": True,
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "config": dict(workload_config(cfg, args, K_terms, G), unique_samples_mean=float(np.mean(units)),
+                           precision=prec, compensated=True, l2="flushed between steps (256 MB write)",
+                           parallelism=f"replicas x{world}"),
             "err_vs_oracle": errors,
             "roofline": roofline,
             "rooflines": rooflines or None,
@@ -567,6 +559,17 @@ def run_eloc(args, local):
                       "scopes": scopes}))
 
 
+def workload_config(cfg, args, K, G):
+    """The workload keys of the JSON line's config (the same for both arms)."""
+    return {"workload": cfg.name, "n_qubits": cfg.n_qubits, "electrons": [cfg.n_up, cfg.n_dn],
+            "terms_K": int(K), "groups_G": int(G),
+            "model": f"{cfg.arch} d={cfg.hidden} L={cfg.layers} H={cfg.heads}",
+            "n_samples": cfg.n_samples, "max_unique": args.max_unique,
+            "batch": "capped: the paper's 1024 unique samples per step (Section 5.1); the sampler "
+                     "draws the nominal count and keeps the 1024 most frequent",
+            "mini_batches": cfg.mini_batches, "beta": args.beta}
+
+
 # ----------------------------------------------------------------------------- oracle timing
 def cpu_baseline(cfg, args, budget_s=15.0):
     """The FP64 oracle as it stands on this host, on a bounded sample of the workload: local
@@ -614,6 +617,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cfg = synth.get_config(args.workload)
+    xm_, _, _ = hamiltonian_of(cfg)
+    K = len(xm_)
+    G = len(np.unique(xm_, axis=0)) if xm_.ndim == 2 else len(np.unique(xm_))
     import torch
     per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
     vals = []
@@ -625,7 +631,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": "sample.Pauli-term local-energy evals/sec (VMC step)",
             "value": value, "unit": "sample.term/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name},
+            "config": dict(workload_config(cfg, args, K, G), precision="f64 (oracle)"),
             "cpu_baseline": {"kind": "oracle", "cores": torch.get_num_threads(), "value": value,
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": value, "unit": "sample.term/s", "h2d_bytes_per_step": 0,
