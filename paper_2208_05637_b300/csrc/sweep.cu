@@ -380,8 +380,12 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
                                        32u, re, re_e, im, im_e);
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) {
-                const float ore = __shfl_xor_sync(0xffffffffu, re, d), oree = __shfl_xor_sync(0xffffffffu, re_e, d);
-                const float oim = __shfl_xor_sync(0xffffffffu, im, d), oime = __shfl_xor_sync(0xffffffffu, im_e, d);
+                // (the imaginary sums are zero unless the Hamiltonian has odd-sigma_2 terms, the
+                // error terms unless the sums are compensated: neither is exchanged then)
+                const float ore = __shfl_xor_sync(0xffffffffu, re, d);
+                const float oree = COMP ? __shfl_xor_sync(0xffffffffu, re_e, d) : 0.f;
+                const float oim = IMAG ? __shfl_xor_sync(0xffffffffu, im, d) : 0.f;
+                const float oime = (IMAG && COMP) ? __shfl_xor_sync(0xffffffffu, im_e, d) : 0.f;
                 // both lanes form the same pair sum: order the operands by lane
                 const bool low = (lane & d) == 0;
                 if (COMP) {
@@ -389,13 +393,15 @@ sweep_emit_kernel(HamDev h, int n_up, int n_dn, const BT* __restrict__ bits, int
                     float ae = (low ? re_e : oree) + (low ? oree : re_e);
                     two_sum_acc(a, ae, bb);
                     re = a; re_e = ae;
-                    float c2 = low ? im : oim, d2 = low ? oim : im;
-                    float ce = (low ? im_e : oime) + (low ? oime : im_e);
-                    two_sum_acc(c2, ce, d2);
-                    im = c2; im_e = ce;
+                    if (IMAG) {
+                        float c2 = low ? im : oim, d2 = low ? oim : im;
+                        float ce = (low ? im_e : oime) + (low ? oime : im_e);
+                        two_sum_acc(c2, ce, d2);
+                        im = c2; im_e = ce;
+                    }
                 } else {
                     re = low ? re + ore : ore + re;
-                    im = low ? im + oim : oim + im;
+                    if (IMAG) im = low ? im + oim : oim + im;
                 }
             }
             if (lane == 0) {
