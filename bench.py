@@ -56,6 +56,8 @@ SCOPE_KERNELS = {
                      "ch_attention_kernel (causal attention of the prefix-sharing jobs, fp32 SIMT)"),
     "tf_layernorm": ("layernorm_kernel / ch_embed_ln_kernel (LayerNorm and embedding rows)",) * 2,
     "ch_cache": ("ch_cache_fill_kernel (key/value caches of the prefix-sharing jobs)",) * 2,
+    "eloc_rows": (None, "eloc_rows_kernel (MADE / product log psi of every connected x' with the ratio-weighted "
+                        "reduction fused, fp32 FFMA, one row per thread)"),
 }
 
 
@@ -311,6 +313,8 @@ def run_ours(args, rank, world, local):
         # the two ceilings of the scope: its arithmetic (bf16 tensor pipe in the bf16 form, the
         # FFMA pipe in the fp32 form) and HBM; the binding one is the larger time at peak
         kernel = SCOPE_KERNELS[name][0 if prec == "bf16" else 1]
+        if kernel is None:
+            continue
         if prec == "bf16":
             pk_c, unit_c, bound_c = peak_t, "TFLOP/s", "tensor"
             src_c = f"{peak_kind} sustained bf16 cuBLAS (MEASURED_PEAKS.json); useful FLOPs (the compensated " \

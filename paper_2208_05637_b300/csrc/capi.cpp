@@ -992,7 +992,23 @@ int nqs_local_energy(nqs_ham_t h, nqs_model_t m, const uint64_t* bits, int64_t B
         NQS_TRY(sweep_chunk(h, m->mc.n_up, m->mc.n_dn, m->mc.compensated, bits + lo * W, nb, e.cnt, e.off, e.valid,
                                 e.xprime, e.S, s));
         {
-            ProfScope ps("eloc_rows", s);
+            // algorithmic work for the profile (read back only while profiling): per connected row
+            // other than the sample itself, the dense MACs of the row's forward (MADE: input and
+            // hidden layers, output logits, phase MLP) -- 2 FLOP each; compulsory bytes: the
+            // row's x' and S
+            double flops = 0.0, bytes = 0.0;
+            if (prof_enabled()) {
+                int64_t rows = 0;
+                NQS_CK(cudaMemcpyAsync(&rows, e.off + nb * e.ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                NQS_CK(cudaStreamSynchronize(s));
+                const double n = m->mc.n, hid = m->mc.hidden, L = m->mc.layers;
+                const double macs = m->mc.arch == NQS_ARCH_MADE
+                                        ? n * hid + (L - 1) * hid * hid + n * hid + (n - 2) * hid + 4 * hid
+                                        : n;
+                flops = 2.0 * macs * (double)std::max<int64_t>(0, rows - nb);
+                bytes = (double)rows * (8.0 * W + 16.0);
+            }
+            ProfScope ps("eloc_rows", s, flops, bytes);
             NQS_TRY(launch_eloc_rows(m->mc, m->d_params, bits + lo * W, nb, e.la + lo, e.ph + lo, e.off,
                                      e.ntiles, e.xprime, e.S, eloc + 2 * lo, s));
         }
