@@ -131,13 +131,8 @@ struct nqs_ham_s {
 
 namespace nqs {
 
-// Spin masks: bits of one spin species (0: even bits, spin up; 1: odd bits, spin down).
-inline uint64_t spin_mask(int n, int spin) {
-    uint64_t m = 0;
-    for (int j = spin; j < n && j < 64; j += 2) m |= (1ull << j);
-    return m;
-}
-// word w of the spin mask of an n-qubit register
+// Spin masks (0: even qubits, spin up; 1: odd qubits, spin down): word w of the mask of an
+// n-qubit register
 inline uint64_t spin_mask_word(int n, int spin, int w) {
     uint64_t m = 0;
     for (int j = spin; j < n; j += 2)
