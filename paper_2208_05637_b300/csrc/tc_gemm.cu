@@ -103,6 +103,12 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
 }
 
+// L2 prefetch of one tensor-map box (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -583,12 +589,19 @@ struct MlpPlan {                                          // epilogue layout (bo
 
 template <int D>
 struct MlpRingPlan {                                      // weights streamed through a ring
-    static constexpr int KB1 = 2 * D / 64;                // 64-wide k-blocks of GEMM1
+    static constexpr int KB1 = 2 * D / 64;                // 64-wide k-blocks of GEMM1 (A hi | lo)
+    static constexpr int KW1 = D / 64;                    // distinct W1 k-blocks per hidden chunk
     static constexpr int A_BYTES = KB1 * 16384;           // 128 rows x 2D bf16
-    static constexpr int STAGES = 3;                      // ring slots of 16 KB
+    // d_model 128: each epilogue warp owns 64 hidden columns of 32 rows of G, two contiguous
+    // 4 KB pieces (hi and lo); the residual is staged there, not in a buffer of its own, and the
+    // 32 KB go to two more ring slots.  The ring carries each weight k-block once (the compensated
+    // form's [W | W] duplicate is never loaded): 256 KB of weights per 128-row tile instead of 512.
+    static constexpr bool STG_IN_G = MlpPlan<D>::SL == 64;
+    static constexpr int STAGES = STG_IN_G ? 5 : 3;       // ring slots of 16 KB
     static constexpr int RING_BYTES = STAGES * 16384;
     static constexpr int G_BYTES = 4 * 16384;             // 128 rows x (128 hi + 128 lo) bf16
-    static constexpr int BIAS_OFF = A_BYTES + RING_BYTES + G_BYTES + MlpPlan<D>::STG_BYTES;
+    static constexpr int STG_BYTES = STG_IN_G ? 0 : MlpPlan<D>::STG_BYTES;
+    static constexpr int BIAS_OFF = A_BYTES + RING_BYTES + G_BYTES + STG_BYTES;
     static constexpr int BAR_OFF = BIAS_OFF + 5 * D * 4;  // b1 (4D) and b2 (D)
     static constexpr int NBAR = 2 + 2 * STAGES + 4 + 2 + 4;
     static constexpr int SMEM = 1024 + BAR_OFF + NBAR * 8 + 16;
@@ -626,7 +639,7 @@ struct MlpEpiArgs {
     const float* sgw;           // head form: lnf_g * head_w [D], sum of it, sum(lnf_b * head_w)
 };
 
-template <int D, bool HEAD = false>
+template <int D, bool HEAD = false, bool STG_IN_G = false>
 __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, int lane) {
     using PL = MlpPlan<D>;
     const uint32_t tmem = E.tmem;
@@ -645,7 +658,9 @@ __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, i
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
         const bool res_warp = HEAD ? sl == 0 : sl < PL::RES_SLICES;
         // head form: one warp per quadrant owns whole rows (64 fp32 = 8 KB of staging)
-        uint8_t* stg = HEAD ? sStg + (size_t)q * 8192 : sStg + (size_t)(q + 4 * (res_warp ? sl : 0)) * 4096;
+        uint8_t* stg = STG_IN_G ? nullptr
+                       : HEAD   ? sStg + (size_t)q * 8192
+                                : sStg + (size_t)(q + 4 * (res_warp ? sl : 0)) * 4096;
         int64_t tt = 0, c1 = 0, cg = 0;
         bool ok = true;
         if (HEAD && res_warp && lane == 0 && (int64_t)blockIdx.x < ntiles) {
@@ -696,8 +711,13 @@ __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, i
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc1_empty[b]);
                 ++c1;
-                // write G once the previous chunk's GEMM2 has read it
+                // write G once the previous chunk's GEMM2 has read it (and, with the residual
+                // staged in G, once the previous tile's reduce-adds have read this warp's rows)
                 if (!mbar_wait_or_abort(g_empty, (uint32_t)((cg & 1) ^ 1), abort)) { ok = false; break; }
+                if (STG_IN_G && j == 0) {
+                    if (lane == 0) bulk_wait_read<0>();
+                    __syncwarp();
+                }
                 const int kb_hi = (sl * PL::SL) >> 6, u0 = ((sl * PL::SL) & 63) >> 3;
                 const uint32_t ghi = su32(sG + kb_hi * 16384) + (uint32_t)r * 128;
                 const uint32_t glo = su32(sG + (2 + kb_hi) * 16384) + (uint32_t)r * 128;
@@ -776,18 +796,21 @@ __device__ __forceinline__ void mlp_epilogue(const MlpEpiArgs<D>& E, int warp, i
 #pragma unroll
                 for (int c = 0; c < PL::RC; c += 32) {
                     const int col = sl * PL::RC + c;
-                    if (lane == 0) bulk_wait_read<0>();
+                    // staged in G: this warp's hi rows for the first 32 columns, its lo rows for
+                    // the next (GEMM2 has read G: acc2 is complete)
+                    uint8_t* st = STG_IN_G ? sG + (size_t)((c == 0 ? 0 : 2) + sl) * 16384 + (size_t)q * 4096 : stg;
+                    if (!STG_IN_G && lane == 0) bulk_wait_read<0>();
                     __syncwarp();
                     float v[32];
                     tmem_ld16_nowait(lane_base + 256u + (uint32_t)(ab * D + col), v);
                     tmem_ld16_nowait(lane_base + 256u + (uint32_t)(ab * D + col + 16), v + 16);
                     tmem_wait_ld();
-                    stage16<TF_EPI_RESID>(*reinterpret_cast<const float(*)[16]>(v), sb2, col, 0, su32(stg), lane);
-                    stage16<TF_EPI_RESID>(*reinterpret_cast<const float(*)[16]>(v + 16), sb2, col + 16, 1, su32(stg), lane);
+                    stage16<TF_EPI_RESID>(*reinterpret_cast<const float(*)[16]>(v), sb2, col, 0, su32(st), lane);
+                    stage16<TF_EPI_RESID>(*reinterpret_cast<const float(*)[16]>(v + 16), sb2, col + 16, 1, su32(st), lane);
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        if (row0 < M) tma_reduce_add_2d(&tmH, stg, col, (int)row0);
+                        if (row0 < M) tma_reduce_add_2d(&tmH, st, col, (int)row0);
                         bulk_commit();
                     }
                 }
@@ -813,7 +836,7 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint8_t* sA = smem;
     uint8_t* ring = smem + RPL::A_BYTES;
     uint8_t* sG = ring + RPL::RING_BYTES;
-    uint8_t* sStg = sG + RPL::G_BYTES;
+    uint8_t* sStg = RPL::STG_IN_G ? nullptr : sG + RPL::G_BYTES;
     float* sb1 = reinterpret_cast<float*>(smem + RPL::BIAS_OFF);
     float* sb2 = sb1 + 4 * D;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RPL::BAR_OFF);
@@ -868,16 +891,16 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 ++it;
                 return true;
             };
+            // the weights' second (duplicate) halves are never loaded: each k-block of W1 / W2
+            // meets both the hi and the lo k-block of A / G (see the MMA issuer)
             auto w1 = [&](int j) -> bool {
-                for (int kb = 0; kb < RPL::KB1; ++kb)
+                for (int kb = 0; kb < RPL::KW1; ++kb)
                     if (!ring_load(&tmW1, kb * 64, j * 128, 16384)) return false;
                 return true;
             };
             auto w2 = [&](int j) -> bool {
-                for (int kb = 0; kb < 4; ++kb) {
-                    const int x = (kb < 2 ? 0 : 4 * D) + j * 128 + (kb & 1) * 64;
-                    if (!ring_load(&tmW2, x, 0, (uint32_t)D * 128)) return false;
-                }
+                for (int kb = 0; kb < 2; ++kb)
+                    if (!ring_load(&tmW2, j * 128 + kb * 64, 0, (uint32_t)D * 128)) return false;
                 return true;
             };
             for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++tt) {
@@ -885,6 +908,9 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 if (!mbar_wait_or_abort(a_empty, (uint32_t)((tt & 1) ^ 1), abort)) break;
                 mbar_expect_tx(a_full, RPL::A_BYTES);
                 for (int kb = 0; kb < RPL::KB1; ++kb) tma_load_2d(sA + kb * 16384, &tmA, a_full, kb * 64, m0);
+                const int64_t tn = t + gridDim.x;          // this CTA's next tile: its A into L2 now
+                if (tn < ntiles)
+                    for (int kb = 0; kb < RPL::KB1; ++kb) tma_prefetch_2d(&tmA, kb * 64, (int)(tn * 128));
                 ok = w1(0) && (PL::NCH < 2 || w1(1));
                 for (int j = 0; ok && j < PL::NCH; ++j) ok = w2(j) && (j + 2 >= PL::NCH || w1(j + 2));
             }
@@ -904,16 +930,21 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 if (!mbar_wait_or_abort(&acc1_empty[b], (uint32_t)(((c1 >> 1) & 1) ^ 1), abort)) return false;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(b * 128);
-                for (int kb = 0; kb < RPL::KB1; ++kb, ++it) {
-                    const int sl = (int)(it % RPL::STAGES);
-                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / RPL::STAGES) & 1), abort)) return false;
-                    tc_fence_after();
-                    const uint32_t a0 = su32(sA + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
+                // the chunk's W1 k-blocks, then A_hi . W1^T followed by A_lo . W1^T (the order of
+                // the duplicated form [A_hi | A_lo] . [W1 | W1]^T)
+                int sl[RPL::KW1];
+                for (int kb = 0; kb < RPL::KW1; ++kb, ++it) {
+                    sl[kb] = (int)(it % RPL::STAGES);
+                    if (!mbar_wait_or_abort(&full[sl[kb]], (uint32_t)((it / RPL::STAGES) & 1), abort)) return false;
+                }
+                tc_fence_after();
+                for (int kb = 0; kb < RPL::KB1; ++kb) {
+                    const uint32_t a0 = su32(sA + kb * 16384), w0 = su32(ring + (size_t)sl[kb % RPL::KW1] * 16384);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         umma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(w0 + kk * 32), id1, (kb | kk) != 0);
-                    umma_commit(&empty[sl]);
                 }
+                for (int kb = 0; kb < RPL::KW1; ++kb) umma_commit(&empty[sl[kb]]);
                 umma_commit(&acc1_full[b]);
                 if (j == PL::NCH - 1) umma_commit(a_empty);
                 ++c1;
@@ -925,16 +956,20 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 if (!mbar_wait_or_abort(g_full, (uint32_t)(cg & 1), abort)) return false;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + 256u + (uint32_t)(ab * D);
-                for (int kb = 0; kb < 4; ++kb, ++it) {
-                    const int sl = (int)(it % RPL::STAGES);
-                    if (!mbar_wait_or_abort(&full[sl], (uint32_t)((it / RPL::STAGES) & 1), abort)) return false;
-                    tc_fence_after();
-                    const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(ring + (size_t)sl * 16384);
+                // the chunk's two W2 k-blocks, then G_hi . W2^T followed by G_lo . W2^T
+                int sl[2];
+                for (int kb = 0; kb < 2; ++kb, ++it) {
+                    sl[kb] = (int)(it % RPL::STAGES);
+                    if (!mbar_wait_or_abort(&full[sl[kb]], (uint32_t)((it / RPL::STAGES) & 1), abort)) return false;
+                }
+                tc_fence_after();
+                for (int kb = 0; kb < 4; ++kb) {
+                    const uint32_t g0 = su32(sG + kb * 16384), w0 = su32(ring + (size_t)sl[kb & 1] * 16384);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         umma_bf16(d_tmem, sw128_desc(g0 + kk * 32), sw128_desc(w0 + kk * 32), id2, (j | kb | kk) != 0);
-                    umma_commit(&empty[sl]);
                 }
+                for (int kb = 0; kb < 2; ++kb) umma_commit(&empty[sl[kb]]);
                 umma_commit(g_empty);
                 if (j == PL::NCH - 1) umma_commit(&acc2_full[ab]);
                 ++cg;
@@ -950,7 +985,7 @@ tc_mlp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     } else {
         MlpEpiArgs<D> E{tmem, sG, sStg, sb1, sb2, acc1_full, acc1_empty, g_full, g_empty, acc2_full, acc2_empty,
                         abort, &tmH, M, ntiles};
-        mlp_epilogue<D>(E, warp, lane);
+        mlp_epilogue<D, false, RPL::STG_IN_G>(E, warp, lane);
     }
     tc_fence_before();
     __syncthreads();
@@ -1790,29 +1825,15 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
     if (D != 64 && D != 128) { set_error("fused MLP needs d_model 64 or 128"); return NQS_ERR_UNSUPPORTED; }
     if (hd && D != 64) { set_error("fused MLP head form needs d_model 64"); return NQS_ERR_UNSUPPORTED; }
     if (((uintptr_t)h & 15) || !b1 || !b2) { set_error("fused MLP: bad operand"); return NQS_ERR_INVALID_ARG; }
-    CUtensorMap ma, m1, m2, mh;
+    CUtensorMap ma, mh;
     NQS_TRY(make_map(&ma, A, M, 2 * D, 128));
-    NQS_TRY(make_map(&m1, W1d, 4 * D, 2 * D, 128));
-    NQS_TRY(make_map(&m2, W2d, D, 8 * D, D));
     NQS_TRY(make_map(&mh, h, M, D, 32, true));
     const int64_t ntiles = (M + 127) / 128;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
-    auto launch = [&](auto kernel, int smem, int threads, int slot) -> int {
-        static int configured_device[2] = {-1, -1};
-        int dev = 0;
-        NQS_CK(cudaGetDevice(&dev));
-        if (configured_device[slot] != dev) {
-            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_mlp)", __FILE__, __LINE__);
-            configured_device[slot] = dev;
-        }
-        kernel<<<grid, threads, smem, s>>>(ma, m1, m2, mh, b1, b2, M, ntiles);
-        NQS_LAUNCHED();
-        return NQS_OK;
-    };
     if (D == 64) {
-        CUtensorMap m1r;   // the whole W1 (first K half of W1d) as one 256-row box
+        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
+        CUtensorMap m1r, m2;   // the whole W1 (first K half of W1d) as one 256-row box; W2
         NQS_TRY(make_map(&m1r, W1d, 4 * D, 2 * D, 256));
+        NQS_TRY(make_map(&m2, W2d, D, 8 * D, D));
         static int configured_res[2] = {-1, -1};
         int dev = 0;
         NQS_CK(cudaGetDevice(&dev));
@@ -1834,7 +1855,23 @@ int tc_mlp_bf16(const void* A, const uint16_t* W1d, const float* b1, const uint1
         NQS_LAUNCHED();
         return NQS_OK;
     }
-    return launch(tc_mlp_kernel<128>, MlpRingPlan<128>::SMEM, MlpPlan<128>::THREADS, 1);
+    // d_model 128: one CTA per SM over the 128-row tiles, the weights streamed through the ring
+    CUtensorMap m1, m2;
+    NQS_TRY(make_map(&m1, W1d, 4 * D, 2 * D, 128));
+    NQS_TRY(make_map(&m2, W2d, D, 8 * D, D));
+    static int configured_device = -1;
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(tc_mlp_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             MlpRingPlan<128>::SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_mlp)", __FILE__, __LINE__);
+        configured_device = dev;
+    }
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms());
+    tc_mlp_kernel<128><<<grid, MlpPlan<128>::THREADS, MlpRingPlan<128>::SMEM, s>>>(ma, m1, m2, mh, b1, b2, M, ntiles);
+    NQS_LAUNCHED();
+    return NQS_OK;
 }
 
 int device_status_ptr(int** out) {

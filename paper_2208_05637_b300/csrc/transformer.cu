@@ -490,8 +490,8 @@ int tf_mlp(const ModelConst& mc, const float* P, const TfWeights& w, int layer, 
     const int d = mc.hidden;
     if (mc.precision == NQS_PREC_BF16 && mc.compensated && (d == 64 || d == 128)) {
         const double flops = 2.0 * 2.0 * (double)M * 4 * d * d;
-        // A (hi+lo) read, h read (and written unless the heads are fused), weights
-        const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * (head ? 1 : 2) + 2.0 * 8.0 * d * d * 2 +
+        // A (hi+lo) read, h read (and written unless the heads are fused), W1 and W2 once
+        const double bytes = (double)M * 2 * d * 2 + (double)M * d * 4 * (head ? 1 : 2) + 8.0 * d * d * 2 +
                              (head ? (double)M * 4 : 0.0);
         ProfScope ps("tf_mlp", s, flops, bytes);
         return tc_mlp_bf16(a, w.bf16 + w.bf16_off[layer][TF_W1], P + mc.b1[layer], w.bf16 + w.bf16_off[layer][TF_W2],
