@@ -40,6 +40,7 @@ NCU_TRAFFIC = {
     ("large_52q_tf128x4", "bf16", "tf_mlp"): 0.98,
     ("large_52q_tf128x4", "bf16", "tf_gemm"): 1.0,
     ("large_52q_tf128x4", "bf16", "tf_layernorm"): 0.91,
+    ("large_52q_tf128x4", "bf16", "ch_attention"): 1.18,
 }
 
 # The library's profiled scopes that record their algorithmic FLOPs and compulsory bytes, with
