@@ -189,6 +189,61 @@ def err_vs_oracle(bits, eloc, gold):
 
 
 # ----------------------------------------------------------------------------- our arm
+def scope_roofline(name, k, prec, cfg_name, ceilings):
+    """Roofline entry of one profiled scope ({ms_total, launches, ms_per_step, flops, bytes} over
+    the profiled steps), or None when the scope records no work or has no kernel of this form.
+    The scope has two ceilings: its arithmetic (the sustained bf16 tensor peak for the bf16 form,
+    the FFMA pipe for the fp32 form) and HBM; `bound` is the one whose time at peak is larger.
+    `traffic` is the measured DRAM-bytes ratio of NCU_TRAFFIC times the launch's compulsory bytes."""
+    sec = k["ms_total"] / 1e3
+    if sec <= 0 or name not in SCOPE_KERNELS or (k["flops"] <= 0 and k["bytes"] <= 0):
+        return None
+    kernel = SCOPE_KERNELS[name][0 if prec == "bf16" else 1]
+    if kernel is None:
+        return None
+    per = k["launches"]
+    tr = NCU_TRAFFIC.get((cfg_name, prec, name))
+    peak_b = ceilings["hbm_gbs"]
+    if prec == "bf16":
+        pk_c, bound_c = ceilings["tensor_tflops"], "tensor"
+        src_c = f"{ceilings['peak_kind']} sustained bf16 cuBLAS (MEASURED_PEAKS.json); useful FLOPs (the " \
+                "compensated hi+lo split issues twice as many products)"
+    else:
+        pk_c, bound_c = ceilings["ffma_tflops"], "alu"
+        src_c = ceilings["ffma_src"]
+    t_c = k["flops"] / (pk_c * 1e12)
+    t_m = k["bytes"] / (peak_b * 1e9)
+    ach_c = k["flops"] / sec / 1e12
+    ach_m = k["bytes"] / sec / 1e9
+    if t_c >= t_m:
+        r = {"kernel": kernel, "bound": bound_c, "achieved": ach_c, "peak": pk_c, "unit": "TFLOP/s",
+             "frac": ach_c / pk_c, "peak_source": src_c}
+    else:
+        r = {"kernel": kernel, "bound": "hbm", "achieved": ach_m, "peak": peak_b, "unit": "GB/s",
+             "frac": ach_m / peak_b, "peak_source": f"{ceilings['peak_kind']} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    r["flops_per_launch"] = k["flops"] / per
+    r["bytes_per_launch"] = k["bytes"] / per
+    r["compute_frac"] = ach_c / pk_c if k["flops"] > 0 else None
+    r["hbm_frac"] = ach_m / peak_b if k["bytes"] > 0 else None
+    r["intensity_flop_per_byte"] = k["flops"] / k["bytes"] if k["bytes"] > 0 else None
+    r["ms_per_step"] = k["ms_per_step"]
+    r["traffic"] = tr * (k["bytes"] / per) if (tr and k["bytes"] > 0) else None
+    return r
+
+
+def dominant_roofline(rooflines):
+    """The entry of the scope with the largest time per step (the line's `roofline`), or None."""
+    if not rooflines:
+        return None
+    top = max(rooflines, key=lambda nm: rooflines[nm]["ms_per_step"])
+    roofline = dict(rooflines[top])
+    roofline["scope"] = top
+    roofline["note"] = ("dominant kernel of the step by time; achieved = the scope's algorithmic FLOPs (or "
+                        "bytes) over its CUDA-event time on the launching stream in a profiled pass of the "
+                        "timed steps")
+    return roofline
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -305,42 +360,12 @@ def run_ours(args, rank, world, local):
     rooflines = {}
     peak_t = peaks.get("bf16_tflops_sustained", 1400.0)
     peak_b = peaks.get("hbm_gbs", 6400.0)
+    ceilings = {"tensor_tflops": peak_t, "hbm_gbs": peak_b, "ffma_tflops": ffma_peak, "peak_kind": peak_kind,
+                "ffma_src": f"fp32 FFMA: {sms} SMs x {pipes['ffma']:.1f}/clk (probe) x 2 x {clk_mhz:.0f} MHz"}
     for name, k in kern.items():
-        sec = k["ms_total"] / 1e3
-        if sec <= 0 or name not in SCOPE_KERNELS or (k["flops"] <= 0 and k["bytes"] <= 0):
-            continue
-        per = k["launches"]
-        tr = NCU_TRAFFIC.get((cfg.name, prec, name))
-        # the two ceilings of the scope: its arithmetic (bf16 tensor pipe in the bf16 form, the
-        # FFMA pipe in the fp32 form) and HBM; the binding one is the larger time at peak
-        kernel = SCOPE_KERNELS[name][0 if prec == "bf16" else 1]
-        if kernel is None:
-            continue
-        if prec == "bf16":
-            pk_c, unit_c, bound_c = peak_t, "TFLOP/s", "tensor"
-            src_c = f"{peak_kind} sustained bf16 cuBLAS (MEASURED_PEAKS.json); useful FLOPs (the compensated " \
-                    "hi+lo split issues twice as many products)"
-        else:
-            pk_c, unit_c, bound_c = ffma_peak, "TFLOP/s", "alu"
-            src_c = f"fp32 FFMA: {sms} SMs x {pipes['ffma']:.1f}/clk (probe) x 2 x {clk_mhz:.0f} MHz"
-        t_c = k["flops"] / (pk_c * 1e12)
-        t_m = k["bytes"] / (peak_b * 1e9)
-        ach_c = k["flops"] / sec / 1e12
-        ach_m = k["bytes"] / sec / 1e9
-        if t_c >= t_m:
-            r = {"kernel": kernel, "bound": bound_c, "achieved": ach_c, "peak": pk_c, "unit": unit_c,
-                 "frac": ach_c / pk_c, "peak_source": src_c}
-        else:
-            r = {"kernel": kernel, "bound": "hbm", "achieved": ach_m, "peak": peak_b, "unit": "GB/s",
-                 "frac": ach_m / peak_b, "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)"}
-        r["flops_per_launch"] = k["flops"] / per
-        r["bytes_per_launch"] = k["bytes"] / per
-        r["compute_frac"] = ach_c / pk_c if k["flops"] > 0 else None
-        r["hbm_frac"] = ach_m / peak_b if k["bytes"] > 0 else None
-        r["intensity_flop_per_byte"] = k["flops"] / k["bytes"] if k["bytes"] > 0 else None
-        r["ms_per_step"] = k["ms_per_step"]
-        r["traffic"] = tr * (k["bytes"] / per) if (tr and k["bytes"] > 0) else None
-        rooflines[name] = r
+        r = scope_roofline(name, k, prec, cfg.name, ceilings)
+        if r is not None:
+            rooflines[name] = r
     # backward: tensor roofline from the layer shapes (forward recompute + two backward GEMMs per
     # forward GEMM on U x n rows), the backward scope's time
     if cfg.arch == "transformer" and "tf_backward" in kern:
@@ -357,14 +382,7 @@ def run_ours(args, rank, world, local):
                                     "unit": "TFLOP/s", "frac": ach / pk, "ms_per_step": sec * 1e3,
                                     "flops_per_step": fl, "traffic": None,
                                     "peak_source": "FLOPs from the layer shapes: 3 x forward"}
-    roofline = None
-    if rooflines:
-        top = max(rooflines, key=lambda nm: rooflines[nm]["ms_per_step"])
-        roofline = dict(rooflines[top])
-        roofline["scope"] = top
-        roofline["note"] = ("dominant kernel of the step by time; achieved = the scope's algorithmic FLOPs (or "
-                            "bytes) over its CUDA-event time on the launching stream in a profiled pass of the "
-                            "timed steps")
+    roofline = dominant_roofline(rooflines)
 
     # term-sweep microbenchmark (B random in-sector samples, 1024 per call)
     sweep = None
