@@ -785,6 +785,62 @@ __device__ __forceinline__ void lnf_row(const ModelConst& mc, const float* __res
     }
 }
 
+// Two rows at once, each with exactly the arithmetic of lnf_row / head_logit (the same butterfly
+// per value), so that the two rows' reductions overlap instead of following each other.
+__device__ __forceinline__ void warp_sum2(float& a, float& b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+}
+
+template <int DPL>
+__device__ __forceinline__ void lnf_row2(const ModelConst& mc, const float* __restrict__ P, const float* __restrict__ h,
+                                         int64_t row0, int64_t row1, int lane, float (&y0)[DPL], float (&y1)[DPL]) {
+    const int d = mc.hidden;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+        y0[i] = h[row0 * d + lane + 32 * i]; s0 += y0[i];
+        y1[i] = h[row1 * d + lane + 32 * i]; s1 += y1[i];
+    }
+    const float inv_d = 1.f / (float)d;
+    warp_sum2(s0, s1);
+    const float mu0 = s0 * inv_d, mu1 = s1 * inv_d;
+    float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+        const float c0 = y0[i] - mu0, c1 = y1[i] - mu1;
+        q0 += c0 * c0;
+        q1 += c1 * c1;
+    }
+    warp_sum2(q0, q1);
+    const float r0 = rsqrtf(fmaf(q0, inv_d, LN_EPS)), r1 = rsqrtf(fmaf(q1, inv_d, LN_EPS));
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+        const int j = lane + 32 * i;
+        const float g = P[mc.lnf_g + j], bb = P[mc.lnf_b + j];
+        y0[i] = (y0[i] - mu0) * r0 * g + bb;
+        y1[i] = (y1[i] - mu1) * r1 * g + bb;
+    }
+}
+
+template <int DPL>
+__device__ __forceinline__ void head_logit2(const ModelConst& mc, const float* __restrict__ P, const float (&y0)[DPL],
+                                            const float (&y1)[DPL], int lane, int t, float& a0, float& a1) {
+    a0 = 0.f; a1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+        const float w = P[mc.head_w + lane + 32 * i];
+        a0 = fmaf(y0[i], w, a0);
+        a1 = fmaf(y1[i], w, a1);
+    }
+    warp_sum2(a0, a1);
+    a0 += P[mc.head_b + t];
+    a1 += P[mc.head_b + t + 1];
+}
+
 template <int DPL>
 __device__ __forceinline__ float head_logit(const ModelConst& mc, const float* __restrict__ P, const float (&y)[DPL],
                                             int lane, int t) {
@@ -937,7 +993,21 @@ ch_leaf_heads_kernel(ModelConst mc, const float* __restrict__ P, const float* __
     const int sel = (int)(((x >> mc.order[n - 2]) & 1ull) * 2 + ((x >> mc.order[n - 1]) & 1ull));
     float phase = s0 > n - 2 ? V.ph4[par * 4 + sel] : 0.f;
     const int64_t q0 = order ? soff[slot] - row_base : 0;
-    for (int t = s0; t < n; ++t) {
+    int t = s0;
+    for (; t + 1 < n; t += 2) {          // two positions per iteration, accumulated in order
+        float y0[DPL], y1[DPL], a0, a1;
+        lnf_row2<DPL>(mc, P, h, q0 + t - s0, q0 + t + 1 - s0, lane, y0, y1);
+        head_logit2<DPL>(mc, P, y0, y1, lane, t, a0, a1);
+        const int b0 = (int)((x >> mc.order[t]) & 1ull);
+        add_lp(s, e, bad, lp_term(forced_at(mc, t, ones[mc.order[t] & 1]), b0, a0), mc.compensated);
+        ones[mc.order[t] & 1] += b0;
+        if (t == n - 2) phase = phase_dot<DPL>(mc, P, y0, lane, sel);
+        const int b1 = (int)((x >> mc.order[t + 1]) & 1ull);
+        add_lp(s, e, bad, lp_term(forced_at(mc, t + 1, ones[mc.order[t + 1] & 1]), b1, a1), mc.compensated);
+        ones[mc.order[t + 1] & 1] += b1;
+        if (t + 1 == n - 2) phase = phase_dot<DPL>(mc, P, y1, lane, sel);
+    }
+    if (t < n) {
         float y[DPL];
         lnf_row<DPL>(mc, P, h, q0 + t - s0, lane, y);
         const float a = head_logit<DPL>(mc, P, y, lane, t);
